@@ -1,0 +1,259 @@
+"""Seeded synthetic inputs for photoacoustic reconstruction workloads.
+
+This module only draws random numbers and rasterises shapes: detector layouts,
+phantom images, side images for directional TV, and standard-normal noise
+arrays.  It contains none of the reconstruction method's arithmetic (no
+projector, no finite differences, no prox maps, no step sizes), so both the CPU
+oracle and the CUDA path can be fed from it without sharing method code.
+
+The workloads stand in for the paper's test objects (Sec. 5.1): piecewise
+constant discs for the TV experiments, a smooth decaying fluence for TGV, and a
+vascular structure.  The paper's vascular phantom came from a retinal image
+database that is not available here; a seeded random vessel tree of line
+segments replaces it.  All images live on the square [-1, 1]^2 with row-major
+layout ``img[iy, ix]`` and pixel centres at ``-1 + (i + 1/2) * 2/N``.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+__all__ = [
+    "Disc",
+    "detectors_full_circle",
+    "detectors_limited_arc",
+    "disc_params",
+    "rasterise_discs",
+    "disc_phantom",
+    "vessel_segments",
+    "rasterise_segments",
+    "vessel_phantom",
+    "side_image",
+    "standard_normal",
+    "uniform",
+    "pixel_centres",
+    "radial_sampling",
+]
+
+
+def _rng(seed: int) -> np.random.Generator:
+    return np.random.default_rng(np.random.PCG64(int(seed)))
+
+
+def pixel_centres(n: int, lo: float = -1.0, hi: float = 1.0) -> np.ndarray:
+    """Coordinates of the n pixel centres along one axis of [lo, hi]."""
+    h = (hi - lo) / n
+    return lo + (np.arange(n, dtype=np.float64) + 0.5) * h
+
+
+# ----------------------------------------------------------------------------
+# detector layouts (point detectors in the image plane, Sec. 3.3.1)
+# ----------------------------------------------------------------------------
+
+def detectors_full_circle(n_det: int, radius: float = 1.2) -> np.ndarray:
+    """``n_det`` point detectors evenly spaced on a full circle; shape (n_det, 2)."""
+    ang = 2.0 * math.pi * np.arange(n_det, dtype=np.float64) / n_det
+    return np.stack([radius * np.cos(ang), radius * np.sin(ang)], axis=1)
+
+
+def detectors_limited_arc(n_total: int, n_keep: int, arc_deg: float, seed: int,
+                          radius: float = 1.2, centre_deg: float = 0.0) -> np.ndarray:
+    """Compressive limited-angle layout.
+
+    ``n_total`` positions spaced evenly over an arc of ``arc_deg`` degrees centred
+    at ``centre_deg``; ``n_keep`` of them are drawn without replacement from the
+    seed and returned in angular order; shape (n_keep, 2).
+    """
+    half = math.radians(arc_deg) / 2.0
+    c = math.radians(centre_deg)
+    if n_total == 1:
+        ang = np.array([c])
+    else:
+        ang = c - half + 2.0 * half * np.arange(n_total, dtype=np.float64) / (n_total - 1)
+    keep = np.sort(_rng(seed).choice(n_total, size=n_keep, replace=False))
+    ang = ang[keep]
+    return np.stack([radius * np.cos(ang), radius * np.sin(ang)], axis=1)
+
+
+# ----------------------------------------------------------------------------
+# disc phantoms (piecewise constant, Sec. 5.1 first phantom)
+# ----------------------------------------------------------------------------
+
+@dataclass(frozen=True)
+class Disc:
+    cx: float
+    cy: float
+    radius: float
+    amplitude: float
+
+
+def disc_params(n_discs: int, seed: int, r_lo: float = 0.05, r_hi: float = 0.2,
+                a_lo: float = 0.5, a_hi: float = 1.0, support: float = 1.0) -> list[Disc]:
+    """Random uniform discs: radius U[r_lo, r_hi], amplitude U[a_lo, a_hi].
+
+    Centres are uniform in the disc |c| <= support - radius, so every disc lies
+    inside the unit circle.
+    """
+    g = _rng(seed)
+    out = []
+    for _ in range(n_discs):
+        rad = g.uniform(r_lo, r_hi)
+        amp = g.uniform(a_lo, a_hi)
+        rho = (support - rad) * math.sqrt(g.uniform(0.0, 1.0))
+        phi = g.uniform(0.0, 2.0 * math.pi)
+        out.append(Disc(rho * math.cos(phi), rho * math.sin(phi), rad, amp))
+    return out
+
+
+def rasterise_discs(discs: list[Disc], n: int, supersample: int = 4) -> np.ndarray:
+    """Sum of disc indicators, averaged over ``supersample``^2 sub-pixel samples."""
+    h = 2.0 / n
+    sub = (np.arange(supersample, dtype=np.float64) + 0.5) / supersample
+    xs = (-1.0 + (np.arange(n)[:, None] + sub[None, :]) * h).reshape(-1)
+    X, Y = np.meshgrid(xs, xs)  # (n*ss, n*ss), Y varies along rows
+    img = np.zeros_like(X)
+    for dsc in discs:
+        img += dsc.amplitude * (((X - dsc.cx) ** 2 + (Y - dsc.cy) ** 2) <= dsc.radius ** 2)
+    return img.reshape(n, supersample, n, supersample).mean(axis=(1, 3))
+
+
+def disc_phantom(n: int, n_discs: int, seed: int, supersample: int = 4) -> tuple[np.ndarray, list[Disc]]:
+    discs = disc_params(n_discs, seed)
+    return rasterise_discs(discs, n, supersample), discs
+
+
+# ----------------------------------------------------------------------------
+# vessel tree (stand-in for the retinal vascular phantom, Sec. 5.1)
+# ----------------------------------------------------------------------------
+
+def vessel_segments(seed: int, n_segments: int = 40, n_pix: int = 256,
+                    w_lo_px: float = 1.0, w_hi_px: float = 4.0,
+                    support: float = 0.95) -> np.ndarray:
+    """A random branching tree of line segments.
+
+    Returns an array (n_segments, 5): x0, y0, x1, y1, width (in image units).
+    The tree grows from a root near the unit circle towards the centre; each new
+    segment starts at the end point of a random earlier segment, turns by a
+    random angle and is thinner than its parent.  Widths are drawn in pixel
+    units of an ``n_pix`` grid so that they stay 1-4 pixels wide.
+    """
+    g = _rng(seed)
+    h = 2.0 / n_pix
+    segs = []
+    ang0 = g.uniform(0.0, 2.0 * math.pi)
+    start = np.array([support * math.cos(ang0), support * math.sin(ang0)])
+    heading = ang0 + math.pi + g.uniform(-0.3, 0.3)
+    widths = []
+    ends = []
+    headings = []
+    w = w_hi_px
+    for s in range(n_segments):
+        if s > 0:
+            parent = int(g.integers(0, len(segs)))
+            start = ends[parent]
+            heading = headings[parent] + g.choice([-1.0, 1.0]) * g.uniform(0.25, 0.9)
+            w = max(w_lo_px, widths[parent] * g.uniform(0.65, 0.95))
+        length = g.uniform(0.15, 0.45)
+        end = start + length * np.array([math.cos(heading), math.sin(heading)])
+        rad = float(np.hypot(*end))
+        if rad > support:  # pull the end point back inside the support
+            end = end * (support / rad)
+        segs.append([start[0], start[1], end[0], end[1], w * h])
+        widths.append(w)
+        ends.append(end)
+        headings.append(heading)
+    return np.asarray(segs, dtype=np.float64)
+
+
+def rasterise_segments(segs: np.ndarray, n: int, supersample: int = 4) -> np.ndarray:
+    """Union of thick segments (capsules) averaged over sub-pixel samples; values in [0, 1]."""
+    h = 2.0 / n
+    m = n * supersample
+    sub_h = h / supersample
+    coords = -1.0 + (np.arange(m, dtype=np.float64) + 0.5) * sub_h
+    mask = np.zeros((m, m), dtype=bool)
+    for x0, y0, x1, y1, w in segs:
+        half = 0.5 * w
+        lo_x = max(0, int((min(x0, x1) - half + 1.0) / sub_h) - 1)
+        hi_x = min(m, int((max(x0, x1) + half + 1.0) / sub_h) + 2)
+        lo_y = max(0, int((min(y0, y1) - half + 1.0) / sub_h) - 1)
+        hi_y = min(m, int((max(y0, y1) + half + 1.0) / sub_h) + 2)
+        if lo_x >= hi_x or lo_y >= hi_y:
+            continue
+        X, Y = np.meshgrid(coords[lo_x:hi_x], coords[lo_y:hi_y])
+        dx, dy = x1 - x0, y1 - y0
+        ll = dx * dx + dy * dy
+        t = np.clip(((X - x0) * dx + (Y - y0) * dy) / ll, 0.0, 1.0) if ll > 0 else np.zeros_like(X)
+        dist2 = (X - x0 - t * dx) ** 2 + (Y - y0 - t * dy) ** 2
+        mask[lo_y:hi_y, lo_x:hi_x] |= dist2 <= half * half
+    return mask.reshape(n, supersample, n, supersample).mean(axis=(1, 3))
+
+
+def vessel_phantom(n: int, seed: int, n_segments: int = 40, mu: float = 3.0,
+                   supersample: int = 4) -> np.ndarray:
+    """Vessel tree times an exponentially decaying fluence exp(-mu * depth).
+
+    depth = max(0, 1 - |x|) is the distance inward from the unit circle, so the
+    absorbed energy is largest near the illuminated boundary.
+    """
+    segs = vessel_segments(seed, n_segments=n_segments, n_pix=n)
+    mask = rasterise_segments(segs, n, supersample)
+    c = pixel_centres(n)
+    X, Y = np.meshgrid(c, c)
+    depth = np.maximum(0.0, 1.0 - np.hypot(X, Y))
+    return mask * np.exp(-mu * depth)
+
+
+def side_image(n: int, seed: int, n_segments: int = 40, blur_px: float = 1.5,
+               background: float = 0.2) -> np.ndarray:
+    """Side image for directional TV sharing the vessel edges of ``vessel_phantom``.
+
+    The vessel mask of the same seed is smoothed with a separable Gaussian of
+    ``blur_px`` pixels and a smooth seeded background (a few low-frequency
+    cosines) is added.
+    """
+    segs = vessel_segments(seed, n_segments=n_segments, n_pix=n)
+    mask = rasterise_segments(segs, n, 4)
+    rad = max(1, int(math.ceil(3 * blur_px)))
+    t = np.arange(-rad, rad + 1, dtype=np.float64)
+    ker = np.exp(-0.5 * (t / blur_px) ** 2)
+    ker /= ker.sum()
+    pad = np.pad(mask, rad, mode="edge")
+    tmp = np.apply_along_axis(lambda v: np.convolve(v, ker, mode="valid"), 1, pad)
+    sm = np.apply_along_axis(lambda v: np.convolve(v, ker, mode="valid"), 0, tmp)
+    g = _rng(seed + 7919)
+    c = pixel_centres(n)
+    X, Y = np.meshgrid(c, c)
+    bg = np.zeros_like(X)
+    for _ in range(3):
+        kx, ky = g.uniform(0.3, 1.5, size=2)
+        ph = g.uniform(0.0, 2.0 * math.pi)
+        bg += np.cos(math.pi * (kx * X + ky * Y) + ph)
+    return sm + background * bg / 3.0
+
+
+# ----------------------------------------------------------------------------
+# noise
+# ----------------------------------------------------------------------------
+
+def standard_normal(shape, seed: int) -> np.ndarray:
+    return _rng(seed).standard_normal(shape)
+
+
+def uniform(shape, seed: int, lo: float = 0.0, hi: float = 1.0) -> np.ndarray:
+    return _rng(seed).uniform(lo, hi, size=shape)
+
+
+def radial_sampling(det_xy: np.ndarray, n_t: int, lo: float = -1.0, hi: float = 1.0) -> tuple[float, float]:
+    """(r0, dr) so that the radii r_k = r0 + (k + 1/2) dr, k < n_t, cover the square.
+
+    r0 = 0 and dr = r_max / n_t with r_max the largest detector-to-corner distance
+    (speed of sound 1, so time samples are radii).
+    """
+    det = np.asarray(det_xy, dtype=np.float64).reshape(-1, 2)
+    corners = np.array([[lo, lo], [lo, hi], [hi, lo], [hi, hi]])
+    rmax = float(np.max(np.hypot(det[:, None, 0] - corners[None, :, 0],
+                                 det[:, None, 1] - corners[None, :, 1])))
+    return 0.0, rmax / n_t
