@@ -1,0 +1,175 @@
+/*
+ * pat.h - C ABI of the GB300 PDHG reconstruction library for photoacoustic tomography.
+ *
+ * Method: Boink, Lagerwerf, Steenbergen, van Gils, Manohar, Brune, "A Framework for
+ * Directional and Higher-Order Reconstruction in Photoacoustic Tomography".  The library
+ * solves  min_u 1/2 ||K u - f||^2 + alpha R(u)  (Sec. 2, eq. (min_prob)) with the
+ * preconditioned first-order primal-dual algorithm PDHGM (Sec. 3.3, Algorithms 1 and 2)
+ * for R = TV (eq. (min_TV)), TGV^2 (eq. (min_TGV)) or directional TV.
+ *
+ * Conventions shared by every entry point
+ *  - Images are N x N, row-major: u[iy*N + ix]; pixel (ix, iy) has its centre at
+ *    (xmin + (ix + 1/2) hx, ymin + (iy + 1/2) hy), hx = (xmax - xmin)/N.
+ *  - Data are detector-major: y[d*T + k] is the integral over the circle of radius
+ *    r_k = r0 + (k + 1/2) dr around detector d (speed of sound 1, so time = radius).
+ *  - Vector fields are stored component-major: p[c*N*N + iy*N + ix].
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller; they must not
+ *    alias each other unless stated.  Pointers named *_host are host memory.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Every call is
+ *    stream-ordered: it enqueues work and returns; results are valid once the stream
+ *    reaches the call, except where a call says it synchronises.
+ *  - Return value: PAT_OK (0) or a negative PAT_ERR_* code; pat_error_string() names it
+ *    and pat_last_error() gives the message of the last failure on the calling thread.
+ *    There is no CPU fallback: without a usable GPU every compute call fails with
+ *    PAT_ERR_CUDA.
+ */
+#ifndef PAT_H
+#define PAT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------------- */
+#define PAT_OK                0
+#define PAT_ERR_INVALID_ARG  (-1)   /* a size, pointer or parameter is out of range        */
+#define PAT_ERR_CUDA         (-2)   /* a CUDA runtime call or kernel launch failed          */
+#define PAT_ERR_OOM          (-3)   /* device memory allocation failed                      */
+#define PAT_ERR_NONFINITE    (-4)   /* an iterate or the duality gap became NaN / Inf       */
+#define PAT_ERR_TIMEOUT      (-5)   /* a bounded device-side wait gave up                   */
+
+/* ---- regularisers, step-size rules, solver status --------------------------------- */
+#define PAT_TV   0   /* R(u) = ||grad u||_{1,2}                       Sec. 2.1, eq. (min_TV)  */
+#define PAT_TGV  1   /* R(u) = min_v ||grad u - v|| + beta ||E v||    Sec. 2.1, eq. (min_TGV) */
+#define PAT_DTV  2   /* R(u) = ||D_xi grad u||_{1,2}, D_xi = I - gamma xi xi^T (not in the
+                        paper; the directional TV of Ehrhardt and Betcke)                  */
+
+#define PAT_PRECOND_DIAG     0  /* Pock-Chambolle diagonal steps (alpha = 1): sigma_i =
+                                   1/sum_j|A_ij|, tau_j = 1/sum_i|A_ij|   Sec. 3.3.2      */
+#define PAT_PRECOND_SCALAR2  1  /* the paper's two-block scalar rule sigma_i tau L_i^2 <
+                                   1/4 with tau = 1/L1, L by power iteration  Sec. 3.3.2 */
+
+#define PAT_STATUS_CONVERGED 0  /* rel_gap <= tol at a gap evaluation                     */
+#define PAT_STATUS_MAXITER   1  /* ran all iterations (tol = 0, or not reached)           */
+#define PAT_STATUS_DIVERGED  2  /* the gap became NaN / Inf (then PAT_ERR_NONFINITE)      */
+
+/* ---- geometry (Sec. 3.3.1 discretisation; Sec. 4.2 eq. (K_def)) ------------------ */
+typedef struct pat_geometry pat_geometry;   /* opaque, immutable after creation */
+
+typedef struct {
+    int    n;                  /* image side N >= 2                                       */
+    double xmin, xmax;         /* image extent in x (xmax > xmin)                         */
+    double ymin, ymax;         /* image extent in y (ymax > ymin)                         */
+    int    n_det;              /* number of point detectors D >= 1                        */
+    const double* det_xy_host; /* 2*D doubles (x0, y0, x1, y1, ...), copied at creation  */
+    int    n_t;                /* radius (time) samples per detector T >= 1               */
+    double r0, dr;             /* r_k = r0 + (k + 1/2) dr, r0 >= 0, dr > 0                */
+    int    quad_m;             /* quadrature points per circle M, 1..8192                 */
+} pat_geometry_desc;
+
+/* Discrete circular-mean operator K of eq. (K_def): quadrature point m of circle (d, k)
+ * is x_d + r_k (cos phi_m, sin phi_m), phi_m = 2 pi (m + 1/2)/M, the image is
+ * interpolated bilinearly between pixel centres with zero outside the grid, and each
+ * point carries the arc-length weight 2 pi r_k / M.  Creation copies the description,
+ * builds the device tables on the current CUDA device and synchronises.  *out receives
+ * a geometry owned by the caller and released with pat_destroy_geometry. */
+int  pat_create_geometry(const pat_geometry_desc* desc, pat_geometry** out);
+void pat_destroy_geometry(pat_geometry* g);              /* NULL is ignored; synchronises */
+
+/* y = K u.  u_dev: N*N floats, y_dev: D*T floats (overwritten). */
+int  pat_forward(const pat_geometry* g, const float* u_dev, float* y_dev, void* stream);
+
+/* u = K^T y, the exact transpose of pat_forward's weights (Sec. 3.3.1: the adjoint is
+ * the transposed matrix, not a discretised continuous adjoint).  y_dev: D*T floats,
+ * u_dev: N*N floats (overwritten). */
+int  pat_adjoint(const pat_geometry* g, const float* y_dev, float* u_dev, void* stream);
+
+/* Direction field for directional TV: xi = grad w / sqrt(|grad w|^2 + eta^2) with the
+ * forward differences of the TV gradient.  w_dev: N*N, xi_dev: 2*N*N (overwritten). */
+int  pat_direction_field(int n, const float* w_dev, double eta, float* xi_dev, void* stream);
+
+/* ---- reconstruction (Sec. 3, Algorithms 1 and 2) ---------------------------------- */
+typedef struct {
+    int    reg;          /* PAT_TV, PAT_TGV or PAT_DTV                                    */
+    double alpha;        /* regularisation weight alpha >= 0                              */
+    double beta;         /* TGV second-order weight beta >= 0 (F3 = alpha beta ||.||)     */
+    double gamma;        /* dTV: 0 <= gamma <= 1                                          */
+    const float* xi_dev; /* dTV: direction field, 2*N*N floats, |xi| <= 1 pointwise       */
+    int    iters;        /* maximum number of PDHG iterations >= 0                        */
+    double tol;          /* stop at the first gap evaluation with rel_gap <= tol (0: never) */
+    int    gap_every;    /* evaluate the gap every gap_every iterations (0: only at the end) */
+    int    precond;      /* PAT_PRECOND_DIAG or PAT_PRECOND_SCALAR2                       */
+    double theta;        /* extrapolation theta in [0, 1] (PDHGM: 1)                      */
+    double box_u, box_v; /* half-widths of the box on which the duality gap is taken     */
+    /* optional warm start (NULL = zero); layouts: x = [u (N*N), v (2*N*N, TGV only)],
+       y = [q (D*T), r (2*N*N), s (3*N*N, TGV only)]; xbar defaults to x0 */
+    const float* x0_dev;
+    const float* xbar0_dev;
+    const float* y0_dev;
+    /* optional export of the final state in the same layouts (NULL = not written) */
+    float* x_out_dev;
+    float* xbar_out_dev;
+    float* y_out_dev;
+} pat_params;
+
+typedef struct {
+    int    iters_done;   /* iterations run                                                */
+    int    status;       /* PAT_STATUS_*                                                  */
+    double primal;       /* P(x) = 1/2||Ku - f||^2 + alpha R(u) at the last gap evaluation */
+    double dual;         /* box-restricted dual value D_B(y) at the same evaluation       */
+    double gap;          /* primal - dual (FP64)                                          */
+    double rel_gap;      /* gap / primal                                                  */
+    double residual;     /* ||x^{n+1} - x^n|| / ||x^n|| over the primal variables         */
+    double ms;           /* device time of the call in milliseconds (CUDA events)         */
+} pat_info;
+
+/* Fills *p with defaults: TV, alpha 0.05, beta 1, gamma 0.95, 100 iterations, tol 0,
+ * gap every 10 iterations, diagonal preconditioning, theta 1, box 2 / 4, no warm start. */
+void pat_params_default(pat_params* p);
+
+/* Runs PDHGM: iteration n computes (Alg. 2 order)
+ *   q   <- prox_{Sigma_q F1*}(q + Sigma_q K ubar)          F1* prox: (z - s f)/(1 + s)
+ *   r   <- proj_{|.|<=alpha}(r + Sigma_r (grad ubar - vbar))       (dTV: D_xi grad ubar)
+ *   s   <- proj_{|.|<=alpha beta}(s + Sigma_s E vbar)                         (TGV)
+ *   u+  <- u - T_u (K^T q - div r)                 (dTV: div(D_xi r))
+ *   v+  <- v - T_v (E^T s - r)                                                (TGV)
+ *   ubar <- u+ + theta (u+ - u),  vbar <- v+ + theta (v+ - v)
+ * with the box-restricted duality gap and residual of Sec. 3.3.3 evaluated in FP64 on
+ * the device.  f_dev: D*T floats; u_dev: N*N floats, receives the final u.  *info
+ * (host) is filled after the call synchronises `stream`.  Workspace is allocated from
+ * the stream-ordered pool and released before returning.  Returns PAT_ERR_NONFINITE
+ * (status DIVERGED) when the gap stops being finite. */
+int  pat_reconstruct(const pat_geometry* g, const float* f_dev, const pat_params* p,
+                     float* u_dev, pat_info* info, void* stream);
+
+/* Runs `count` independent reconstructions (each with its own geometry, data, params
+ * and output) on one stream, interleaving their iterations so that problems of very
+ * different sizes share the GPU.  Arrays have `count` entries; infos is host memory. */
+int  pat_reconstruct_batched(int count, const pat_geometry* const* g, const float* const* f_dev,
+                             const pat_params* p, float* const* u_dev, pat_info* infos,
+                             void* stream);
+
+/* Step sizes that pat_reconstruct uses for (g, p) (Sec. 3.3.2), computed with FP64
+ * sums: sig_q (D*T), tau_u (N*N), sig_r (N*N, one value per pointwise r group),
+ * sig_s (N*N, TGV; may be NULL otherwise), tau_v (2*N*N, TGV; may be NULL otherwise).
+ * Output pointers are device memory and may be NULL to skip. */
+int  pat_steps(const pat_geometry* g, const pat_params* p, float* sig_q_dev, float* tau_u_dev,
+               float* sig_r_dev, float* sig_s_dev, float* tau_v_dev, void* stream);
+
+/* Box-restricted duality gap (Sec. 3.3.3, FP64 accumulation) of a primal point x and a
+ * dual-feasible point y in the layouts of pat_params.  out4_host receives
+ * {primal, dual, gap, rel_gap}; the call synchronises `stream`. */
+int  pat_duality_gap(const pat_geometry* g, const float* f_dev, const pat_params* p,
+                     const float* x_dev, const float* y_dev, double* out4_host, void* stream);
+
+/* ---- diagnostics ------------------------------------------------------------------ */
+const char* pat_error_string(int code);
+const char* pat_last_error(void);
+/* Geometry sizes: out6 = {N, D, T, M, number of quadrature points evaluated per K
+ * application (inside the angular windows), 0}. */
+int  pat_geometry_info(const pat_geometry* g, long long* out6_host);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PAT_H */

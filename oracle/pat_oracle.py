@@ -163,6 +163,8 @@ def adjoint(g: Geometry, y: np.ndarray) -> np.ndarray:
     w = g.arc_weights()
     out = np.zeros(g.n * g.n)
     for d in range(g.n_det):
+        if not np.any(y[d]):
+            continue                      # a zero data row contributes nothing
         X, Y = circle_points(g, d)
         c = np.broadcast_to((w * y[d])[:, None], X.shape)
         for ix, iy, wgt, inside in bilinear_taps(g, X, Y):
@@ -536,15 +538,18 @@ class Result:
     gap: dict = field(default_factory=dict)
     residual: float = math.nan
     history: list = field(default_factory=list)
+    ubar: Optional[np.ndarray] = None
+    vbar: Optional[np.ndarray] = None
 
 
 def pdhg(pb: Problem, iters: int, steps: Optional[Steps] = None, theta: float = 1.0,
          tol: float = 0.0, gap_every: int = 0, x0: Optional[dict] = None,
-         y0: Optional[dict] = None) -> Result:
+         y0: Optional[dict] = None, xbar0: Optional[dict] = None) -> Result:
     """Preconditioned PDHGM, one iteration per step of Algorithm 1 / Algorithm 2.
 
-    Iterates start at zero unless ``x0`` = {u, v} / ``y0`` = {q, r, s} are given
-    (u_bar^0 = u^0).  When ``gap_every`` > 0 the gap is evaluated after every
+    Iterates start at zero (the initialisation of Algorithms 1 and 2) unless
+    ``x0`` = {u, v} / ``y0`` = {q, r, s} are given; the extrapolated point starts at
+    ``xbar0`` = {u, v} if given, else at x^0.  When ``gap_every`` > 0 the gap is evaluated after every
     ``gap_every``-th iteration (and after the last one); with ``tol`` > 0 the loop stops
     at the first evaluation with rel_gap <= tol.
     """
@@ -562,8 +567,11 @@ def pdhg(pb: Problem, iters: int, steps: Optional[Steps] = None, theta: float = 
     if tgv:
         s = np.zeros((3, n, n)) if y0 is None or y0.get("s") is None else \
             np.array(y0["s"], dtype=np.float64).reshape(3, n, n)
-    ubar = u.copy()
-    vbar = v.copy() if tgv else None
+    ubar = u.copy() if xbar0 is None else np.array(xbar0["u"], dtype=np.float64).reshape(n, n)
+    vbar = None
+    if tgv:
+        vbar = v.copy() if xbar0 is None or xbar0.get("v") is None else \
+            np.array(xbar0["v"], dtype=np.float64).reshape(2, n, n)
     out = Result(u=u, v=v, q=q, r=r, s=s, iters_done=0)
     for it in range(iters):
         # dual steps
@@ -600,7 +608,9 @@ def pdhg(pb: Problem, iters: int, steps: Optional[Steps] = None, theta: float = 
             out.gap, out.residual = gp, res
             if tol > 0 and gp["rel_gap"] <= tol:
                 out.u, out.v, out.q, out.r, out.s, out.iters_done = u, v, q, r, s, done
+                out.ubar, out.vbar = ubar, vbar
                 return out
         out.iters_done = done
     out.u, out.v, out.q, out.r, out.s = u, v, q, r, s
+    out.ubar, out.vbar = ubar, vbar
     return out

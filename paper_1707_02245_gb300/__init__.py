@@ -1,0 +1,265 @@
+"""Python binding of the GB300 PDHG photoacoustic reconstruction library (C ABI: include/pat.h).
+
+Argument marshalling only: every step of the reconstruction runs in the CUDA library
+``_lib/libpat_pdhg.so`` (build it with ``paper_1707_02245_gb300.build.build()``).  The
+functions below carry the C names and take device pointers as integers or as objects
+with a ``data_ptr()`` method (e.g. torch CUDA tensors); streams are ``cudaStream_t``
+handles as integers (0 = default stream) or objects with a ``cuda_stream`` attribute.
+
+There is no CPU fallback: loading fails loudly when the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+PAT_OK = 0
+PAT_ERR_INVALID_ARG = -1
+PAT_ERR_CUDA = -2
+PAT_ERR_OOM = -3
+PAT_ERR_NONFINITE = -4
+PAT_ERR_TIMEOUT = -5
+
+PAT_TV, PAT_TGV, PAT_DTV = 0, 1, 2
+PAT_PRECOND_DIAG, PAT_PRECOND_SCALAR2 = 0, 1
+PAT_STATUS_CONVERGED, PAT_STATUS_MAXITER, PAT_STATUS_DIVERGED = 0, 1, 2
+
+EXPORTED = [
+    "pat_create_geometry", "pat_destroy_geometry", "pat_forward", "pat_adjoint",
+    "pat_direction_field", "pat_params_default", "pat_reconstruct", "pat_reconstruct_batched",
+    "pat_steps", "pat_duality_gap", "pat_error_string", "pat_last_error", "pat_geometry_info",
+]
+
+
+class PatError(RuntimeError):
+    def __init__(self, code: int, where: str, message: str):
+        super().__init__(f"{where}: {message} (code {code})")
+        self.code = code
+
+
+class pat_geometry_desc(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("xmin", ctypes.c_double), ("xmax", ctypes.c_double),
+                ("ymin", ctypes.c_double), ("ymax", ctypes.c_double), ("n_det", ctypes.c_int),
+                ("det_xy_host", ctypes.POINTER(ctypes.c_double)), ("n_t", ctypes.c_int),
+                ("r0", ctypes.c_double), ("dr", ctypes.c_double), ("quad_m", ctypes.c_int)]
+
+
+class pat_params(ctypes.Structure):
+    _fields_ = [("reg", ctypes.c_int), ("alpha", ctypes.c_double), ("beta", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("xi_dev", ctypes.c_void_p), ("iters", ctypes.c_int),
+                ("tol", ctypes.c_double), ("gap_every", ctypes.c_int), ("precond", ctypes.c_int),
+                ("theta", ctypes.c_double), ("box_u", ctypes.c_double), ("box_v", ctypes.c_double),
+                ("x0_dev", ctypes.c_void_p), ("xbar0_dev", ctypes.c_void_p), ("y0_dev", ctypes.c_void_p),
+                ("x_out_dev", ctypes.c_void_p), ("xbar_out_dev", ctypes.c_void_p),
+                ("y_out_dev", ctypes.c_void_p)]
+
+
+class pat_info(ctypes.Structure):
+    _fields_ = [("iters_done", ctypes.c_int), ("status", ctypes.c_int), ("primal", ctypes.c_double),
+                ("dual", ctypes.c_double), ("gap", ctypes.c_double), ("rel_gap", ctypes.c_double),
+                ("residual", ctypes.c_double), ("ms", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.lib_path()
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Loads the CUDA library (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or library_path()
+    if not os.path.exists(p):
+        raise RuntimeError(f"CUDA library not built: {p} is missing; run paper_1707_02245_gb300.build.build()")
+    lib = ctypes.CDLL(p)
+    vp, i, d = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+    sig = {
+        "pat_create_geometry": (i, [ctypes.POINTER(pat_geometry_desc), ctypes.POINTER(vp)]),
+        "pat_destroy_geometry": (None, [vp]),
+        "pat_forward": (i, [vp, vp, vp, vp]),
+        "pat_adjoint": (i, [vp, vp, vp, vp]),
+        "pat_direction_field": (i, [i, vp, d, vp, vp]),
+        "pat_params_default": (None, [ctypes.POINTER(pat_params)]),
+        "pat_reconstruct": (i, [vp, vp, ctypes.POINTER(pat_params), vp, ctypes.POINTER(pat_info), vp]),
+        "pat_reconstruct_batched": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(pat_params),
+                                        ctypes.POINTER(vp), ctypes.POINTER(pat_info), vp]),
+        "pat_steps": (i, [vp, ctypes.POINTER(pat_params), vp, vp, vp, vp, vp, vp]),
+        "pat_duality_gap": (i, [vp, vp, ctypes.POINTER(pat_params), vp, vp, ctypes.POINTER(d), vp]),
+        "pat_error_string": (ctypes.c_char_p, [i]),
+        "pat_last_error": (ctypes.c_char_p, []),
+        "pat_geometry_info": (i, [vp, ctypes.POINTER(ctypes.c_longlong)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x) -> int | None:
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    return int(x.data_ptr())
+
+
+def _stream(s) -> int | None:
+    if s is None:
+        return None
+    if isinstance(s, int):
+        return s or None
+    return int(getattr(s, "cuda_stream"))
+
+
+def _check(code: int, where: str):
+    if code != PAT_OK:
+        lib = load()
+        raise PatError(code, where, lib.pat_last_error().decode(errors="replace"))
+
+
+# ---- C-named entry points --------------------------------------------------------
+
+def pat_create_geometry(n: int, det_xy, n_t: int, r0: float, dr: float, quad_m: int,
+                        extent=(-1.0, 1.0, -1.0, 1.0)) -> int:
+    lib = load()
+    det = np.ascontiguousarray(np.asarray(det_xy, dtype=np.float64).reshape(-1))
+    desc = pat_geometry_desc(n=n, xmin=extent[0], xmax=extent[1], ymin=extent[2], ymax=extent[3],
+                             n_det=det.size // 2,
+                             det_xy_host=det.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                             n_t=n_t, r0=r0, dr=dr, quad_m=quad_m)
+    out = ctypes.c_void_p()
+    _check(lib.pat_create_geometry(ctypes.byref(desc), ctypes.byref(out)), "pat_create_geometry")
+    return out.value
+
+
+def pat_destroy_geometry(g: int) -> None:
+    load().pat_destroy_geometry(g)
+
+
+def pat_forward(g: int, u_dev, y_dev, stream=None) -> None:
+    _check(load().pat_forward(g, _ptr(u_dev), _ptr(y_dev), _stream(stream)), "pat_forward")
+
+
+def pat_adjoint(g: int, y_dev, u_dev, stream=None) -> None:
+    _check(load().pat_adjoint(g, _ptr(y_dev), _ptr(u_dev), _stream(stream)), "pat_adjoint")
+
+
+def pat_direction_field(n: int, w_dev, eta: float, xi_dev, stream=None) -> None:
+    _check(load().pat_direction_field(n, _ptr(w_dev), eta, _ptr(xi_dev), _stream(stream)), "pat_direction_field")
+
+
+def pat_params_default() -> pat_params:
+    p = pat_params()
+    load().pat_params_default(ctypes.byref(p))
+    return p
+
+
+def make_params(reg=PAT_TV, alpha=0.05, beta=1.0, gamma=0.95, xi=None, iters=100, tol=0.0, gap_every=10,
+                precond=PAT_PRECOND_DIAG, theta=1.0, box_u=2.0, box_v=4.0, x0=None, xbar0=None, y0=None,
+                x_out=None, xbar_out=None, y_out=None) -> pat_params:
+    p = pat_params_default()
+    p.reg, p.alpha, p.beta, p.gamma = reg, alpha, beta, gamma
+    p.xi_dev = _ptr(xi)
+    p.iters, p.tol, p.gap_every, p.precond = iters, tol, gap_every, precond
+    p.theta, p.box_u, p.box_v = theta, box_u, box_v
+    p.x0_dev, p.xbar0_dev, p.y0_dev = _ptr(x0), _ptr(xbar0), _ptr(y0)
+    p.x_out_dev, p.xbar_out_dev, p.y_out_dev = _ptr(x_out), _ptr(xbar_out), _ptr(y_out)
+    # keep the buffers alive as long as the parameter block that points at them
+    p._keep = [xi, x0, xbar0, y0, x_out, xbar_out, y_out]
+    return p
+
+
+def pat_reconstruct(g: int, f_dev, params: pat_params, u_dev, stream=None) -> dict:
+    info = pat_info()
+    _check(load().pat_reconstruct(g, _ptr(f_dev), ctypes.byref(params), _ptr(u_dev), ctypes.byref(info),
+                                  _stream(stream)), "pat_reconstruct")
+    return info.as_dict()
+
+
+def pat_reconstruct_batched(geoms, fs, params, us, stream=None) -> list[dict]:
+    n = len(geoms)
+    G = (ctypes.c_void_p * n)(*geoms)
+    F = (ctypes.c_void_p * n)(*[_ptr(f) for f in fs])
+    U = (ctypes.c_void_p * n)(*[_ptr(u) for u in us])
+    P = (pat_params * n)(*params)
+    infos = (pat_info * n)()
+    _check(load().pat_reconstruct_batched(n, G, F, P, U, infos, _stream(stream)), "pat_reconstruct_batched")
+    return [infos[i].as_dict() for i in range(n)]
+
+
+def pat_steps(g: int, params: pat_params, sig_q=None, tau_u=None, sig_r=None, sig_s=None, tau_v=None,
+              stream=None) -> None:
+    _check(load().pat_steps(g, ctypes.byref(params), _ptr(sig_q), _ptr(tau_u), _ptr(sig_r), _ptr(sig_s),
+                            _ptr(tau_v), _stream(stream)), "pat_steps")
+
+
+def pat_duality_gap(g: int, f_dev, params: pat_params, x_dev, y_dev, stream=None) -> dict:
+    out = (ctypes.c_double * 4)()
+    _check(load().pat_duality_gap(g, _ptr(f_dev), ctypes.byref(params), _ptr(x_dev), _ptr(y_dev), out,
+                                  _stream(stream)), "pat_duality_gap")
+    return {"primal": out[0], "dual": out[1], "gap": out[2], "rel_gap": out[3]}
+
+
+def pat_geometry_info(g: int) -> dict:
+    out = (ctypes.c_longlong * 6)()
+    _check(load().pat_geometry_info(g, out), "pat_geometry_info")
+    return {"n": out[0], "n_det": out[1], "n_t": out[2], "quad_m": out[3], "points_per_apply": out[4]}
+
+
+def pat_error_string(code: int) -> str:
+    return load().pat_error_string(code).decode()
+
+
+def pat_last_error() -> str:
+    return load().pat_last_error().decode(errors="replace")
+
+
+# ---- a small owner of a geometry handle -----------------------------------------
+
+@dataclass
+class Geometry:
+    """Owns a pat_geometry handle; sizes mirror pat_geometry_desc."""
+    n: int
+    det_xy: np.ndarray
+    n_t: int
+    r0: float
+    dr: float
+    quad_m: int
+    extent: tuple = (-1.0, 1.0, -1.0, 1.0)
+
+    def __post_init__(self):
+        self.det_xy = np.asarray(self.det_xy, dtype=np.float64).reshape(-1, 2)
+        self.handle = pat_create_geometry(self.n, self.det_xy, self.n_t, self.r0, self.dr, self.quad_m,
+                                          self.extent)
+
+    @property
+    def n_det(self) -> int:
+        return self.det_xy.shape[0]
+
+    def close(self):
+        if getattr(self, "handle", None):
+            pat_destroy_geometry(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        return pat_geometry_info(self.handle)

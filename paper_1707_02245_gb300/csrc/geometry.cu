@@ -1,0 +1,228 @@
+// Geometry creation, error reporting and small utilities of the C ABI.
+//
+// The discrete circular-mean operator (Sec. 4.2, eq. (K_def); Sec. 3.3.1): quadrature
+// point m of circle (d, k) is x_d + r_k (cos phi_m, sin phi_m), phi_m = 2 pi (m + 1/2)/M,
+// r_k = r0 + (k + 1/2) dr.  The tables built here are the only geometry state the
+// kernels read: detector positions, the M (cos, sin) pairs, radii, arc weights
+// 2 pi r_k / M, and per group of 32 consecutive radii the circular range of angles
+// whose points can touch the grid (a superset: kernels test every point exactly).
+#include <math.h>
+
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "pat_internal.cuh"
+
+namespace pat {
+
+static thread_local std::string g_last_error;
+
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? PAT_ERR_OOM : PAT_ERR_CUDA;
+}
+
+}  // namespace pat
+
+using namespace pat;
+
+extern "C" const char* pat_error_string(int code) {
+    switch (code) {
+        case PAT_OK: return "ok";
+        case PAT_ERR_INVALID_ARG: return "invalid argument";
+        case PAT_ERR_CUDA: return "CUDA error";
+        case PAT_ERR_OOM: return "out of device memory";
+        case PAT_ERR_NONFINITE: return "non-finite iterate or duality gap";
+        case PAT_ERR_TIMEOUT: return "device-side wait timed out";
+        default: return "unknown error";
+    }
+}
+
+extern "C" const char* pat_last_error(void) { return g_last_error.c_str(); }
+
+static void free_tables(pat_geometry* g) {
+    cudaFree(g->det);
+    cudaFree(g->cs);
+    cudaFree(g->rk);
+    cudaFree(g->wk);
+    cudaFree(g->win);
+    cudaFree(g->pc.krow);
+    cudaFree(g->pc.kcol);
+    g->det = nullptr;
+    g->cs = nullptr;
+    g->rk = nullptr;
+    g->wk = nullptr;
+    g->win = nullptr;
+    g->pc.krow = nullptr;
+    g->pc.kcol = nullptr;
+}
+
+// Smallest circular interval of [0, M) that covers every set entry of `mask`.
+static int2 covering_window(const std::vector<unsigned char>& mask, int M) {
+    int n_set = 0;
+    for (int m = 0; m < M; ++m) n_set += mask[m];
+    if (n_set == 0) return make_int2(0, 0);
+    if (n_set == M) return make_int2(0, M);
+    // longest circular run of unset entries; the window starts right after it
+    int best_len = 0, best_end = 0;  // run occupies [best_end - best_len, best_end)
+    int first_set = 0;
+    while (!mask[first_set]) ++first_set;
+    int run = 0;
+    for (int s = 1; s <= M; ++s) {  // scan M entries starting after first_set
+        int m = (first_set + s) % M;
+        if (!mask[m]) {
+            ++run;
+        } else {
+            if (run > best_len) {
+                best_len = run;
+                best_end = m;
+            }
+            run = 0;
+        }
+    }
+    return make_int2(best_end, M - best_len);
+}
+
+extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry** out) {
+    if (!desc || !out) return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: NULL argument");
+    *out = nullptr;
+    const pat_geometry_desc& d = *desc;
+    if (d.n < 2 || d.n > 16384) return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: n must be in [2, 16384]");
+    if (!(d.xmax > d.xmin) || !(d.ymax > d.ymin))
+        return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: empty image extent");
+    if (d.n_det < 1 || !d.det_xy_host) return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: no detectors");
+    if (d.n_t < 1) return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: n_t must be >= 1");
+    if (!(d.r0 >= 0.0) || !(d.dr > 0.0)) return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: need r0 >= 0, dr > 0");
+    if (d.quad_m < 1 || d.quad_m > MAX_QUAD_M)
+        return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: quad_m must be in [1, 8192]");
+    if ((long long)d.n_det * d.n_t > (1LL << 31) - 1)
+        return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: D*T too large");
+    for (int i = 0; i < 2 * d.n_det; ++i)
+        if (!std::isfinite(d.det_xy_host[i])) return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: non-finite detector");
+
+    pat_geometry* g = new pat_geometry();
+    g->desc = d;
+    g->desc.det_xy_host = nullptr;  // not retained
+    cudaGetDevice(&g->device);
+
+    const int N = d.n, D = d.n_det, T = d.n_t, M = d.quad_m;
+    const double hx = (d.xmax - d.xmin) / N, hy = (d.ymax - d.ymin) / N;
+    const int n_kgrp = (T + KGRP - 1) / KGRP;
+
+    std::vector<float2> det(D), cs(M);
+    std::vector<float> rk(T), wk(T);
+    std::vector<double> cosd(M), sind(M), rd(T);
+    for (int i = 0; i < D; ++i) det[i] = make_float2((float)d.det_xy_host[2 * i], (float)d.det_xy_host[2 * i + 1]);
+    for (int m = 0; m < M; ++m) {
+        const double phi = 2.0 * M_PI * (m + 0.5) / M;
+        cosd[m] = cos(phi);
+        sind[m] = sin(phi);
+        cs[m] = make_float2((float)cosd[m], (float)sind[m]);
+    }
+    for (int k = 0; k < T; ++k) {
+        rd[k] = d.r0 + (k + 0.5) * d.dr;
+        rk[k] = (float)rd[k];
+        wk[k] = (float)(2.0 * M_PI * rd[k] / M);
+    }
+
+    // angular windows: a point can touch the grid iff fx, fy in (-1, N), i.e.
+    // x in (xmin - hx/2, xmax + hx/2); the test uses a margin so fp32 rounding in the
+    // kernels never meets a point outside its window that would touch the grid
+    const double ex = 1e-3 * hx, ey = 1e-3 * hy;
+    const double xl = d.xmin - 0.5 * hx - ex, xh = d.xmax + 0.5 * hx + ex;
+    const double yl = d.ymin - 0.5 * hy - ey, yh = d.ymax + 0.5 * hy + ey;
+    std::vector<int2> win((size_t)D * n_kgrp);
+    std::vector<unsigned char> mask(M);
+    long long pts = 0;
+    for (int di = 0; di < D; ++di) {
+        const double dx = d.det_xy_host[2 * di], dy = d.det_xy_host[2 * di + 1];
+        for (int gi = 0; gi < n_kgrp; ++gi) {
+            std::fill(mask.begin(), mask.end(), 0);
+            const int k_end = std::min(T, (gi + 1) * KGRP);
+            for (int k = gi * KGRP; k < k_end; ++k) {
+                const double r = rd[k];
+                // quick reject: circle entirely off the extended box
+                const double cx = std::min(std::max(dx, xl), xh), cy = std::min(std::max(dy, yl), yh);
+                const double dmin = hypot(dx - cx, dy - cy);
+                const double dmax = std::max(std::max(hypot(dx - xl, dy - yl), hypot(dx - xh, dy - yl)),
+                                             std::max(hypot(dx - xl, dy - yh), hypot(dx - xh, dy - yh)));
+                if (r < dmin - 1e-9 || r > dmax + 1e-9) continue;
+                for (int m = 0; m < M; ++m) {
+                    if (mask[m]) continue;
+                    const double x = dx + r * cosd[m], y = dy + r * sind[m];
+                    if (x > xl && x < xh && y > yl && y < yh) mask[m] = 1;
+                }
+            }
+            int2 w = covering_window(mask, M);
+            win[(size_t)di * n_kgrp + gi] = w;
+            pts += (long long)w.y * (k_end - gi * KGRP);
+        }
+    }
+    g->points_per_apply = pts;
+
+    cudaError_t e = cudaSuccess;
+    e = cudaMalloc(&g->det, sizeof(float2) * D);
+    if (e == cudaSuccess) e = cudaMalloc(&g->cs, sizeof(float2) * M);
+    if (e == cudaSuccess) e = cudaMalloc(&g->rk, sizeof(float) * T);
+    if (e == cudaSuccess) e = cudaMalloc(&g->wk, sizeof(float) * T);
+    if (e == cudaSuccess) e = cudaMalloc(&g->win, sizeof(int2) * win.size());
+    if (e == cudaSuccess) e = cudaMemcpy(g->det, det.data(), sizeof(float2) * D, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->cs, cs.data(), sizeof(float2) * M, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->rk, rk.data(), sizeof(float) * T, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->wk, wk.data(), sizeof(float) * T, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->win, win.data(), sizeof(int2) * win.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        int rc = cuda_fail(e, "pat_create_geometry: table upload");
+        free_tables(g);
+        delete g;
+        return rc;
+    }
+
+    GeomView& v = g->view;
+    v.n = N;
+    v.n_det = D;
+    v.n_t = T;
+    v.quad_m = M;
+    v.n_kgrp = n_kgrp;
+    v.inv_hx = (float)(1.0 / hx);
+    v.inv_hy = (float)(1.0 / hy);
+    v.ox = (float)(-d.xmin / hx - 0.5);
+    v.oy = (float)(-d.ymin / hy - 0.5);
+    v.det = g->det;
+    v.cs = g->cs;
+    v.rk = g->rk;
+    v.wk = g->wk;
+    v.win = g->win;
+    *out = g;
+    return PAT_OK;
+}
+
+extern "C" void pat_destroy_geometry(pat_geometry* g) {
+    if (!g) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(g->device);
+    cudaDeviceSynchronize();
+    free_tables(g);
+    cudaSetDevice(cur);
+    delete g;
+}
+
+extern "C" int pat_geometry_info(const pat_geometry* g, long long* out6) {
+    if (!g || !out6) return fail(PAT_ERR_INVALID_ARG, "pat_geometry_info: NULL argument");
+    out6[0] = g->desc.n;
+    out6[1] = g->desc.n_det;
+    out6[2] = g->desc.n_t;
+    out6[3] = g->desc.quad_m;
+    out6[4] = g->points_per_apply;
+    out6[5] = 0;
+    return PAT_OK;
+}

@@ -1,0 +1,119 @@
+// Internal declarations of the PDHG photoacoustic library (CUDA, sm_103a).
+// Shared by the translation units of the library only; the public boundary is pat.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <string>
+
+#include "pat.h"
+
+namespace pat {
+
+// ---------------------------------------------------------------------------------
+// error plumbing
+// ---------------------------------------------------------------------------------
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+int cuda_fail(cudaError_t e, const char* what);
+
+#define PAT_CUDA(call)                                              \
+    do {                                                            \
+        cudaError_t e_ = (call);                                    \
+        if (e_ != cudaSuccess) return ::pat::cuda_fail(e_, #call);  \
+    } while (0)
+
+#define PAT_LAUNCH_CHECK(what)                                      \
+    do {                                                            \
+        cudaError_t e_ = cudaGetLastError();                        \
+        if (e_ != cudaSuccess) return ::pat::cuda_fail(e_, what);   \
+    } while (0)
+
+// ---------------------------------------------------------------------------------
+// device view of a geometry (passed by value to kernels)
+// ---------------------------------------------------------------------------------
+// Quadrature point m of circle (d, k):  x = det[d] + r[k] * cs[m]   (fp32)
+// Continuous pixel coordinate:          fx = x * inv_hx + ox,  ox = -xmin/hx - 1/2
+// Taps i0 = floor(fx), i0 + 1 with weights 1 - ax, ax (ax = fx - i0); same in y.
+struct GeomView {
+    int n, n_det, n_t, quad_m;
+    int n_kgrp;          // k groups of KGRP consecutive radii per detector
+    float inv_hx, inv_hy, ox, oy;
+    const float2* det;   // D detector positions
+    const float2* cs;    // M (cos phi_m, sin phi_m)
+    const float* rk;     // T radii
+    const float* wk;     // T arc weights 2 pi r_k / M
+    const int2* win;     // D * n_kgrp angular windows {m_first, m_count} (circular)
+};
+
+constexpr int KGRP = 32;       // radii per window group (one warp)
+constexpr int MAX_QUAD_M = 8192;
+
+struct PrecondCache {
+    float* krow = nullptr;      // K 1 per data row (S), summed in FP64
+    float* kcol = nullptr;      // K^T 1 per pixel (N*N), summed in FP64
+    bool ready = false;
+};
+
+}  // namespace pat
+
+struct pat_geometry {
+    pat_geometry_desc desc;
+    int device = 0;
+    long long points_per_apply = 0;   // quadrature points inside the windows
+    // device tables
+    float2* det = nullptr;
+    float2* cs = nullptr;
+    float* rk = nullptr;
+    float* wk = nullptr;
+    int2* win = nullptr;
+    pat::GeomView view;
+    // lazily computed preconditioner sums
+    mutable std::mutex mtx;
+    mutable pat::PrecondCache pc;
+};
+
+namespace pat {
+
+// ---------------------------------------------------------------------------------
+// shared device helpers
+// ---------------------------------------------------------------------------------
+struct Taps {
+    int i0, j0;
+    float ax, ay;
+};
+
+// Position of quadrature point (d, k, m) and its bilinear taps.  Returns false when no
+// tap can touch the grid (i0 or j0 outside [-1, N-1]).
+__device__ __forceinline__ bool point_taps(const GeomView& g, float2 det, float r, float2 cs,
+                                           Taps& t) {
+    const float x = fmaf(r, cs.x, det.x);
+    const float y = fmaf(r, cs.y, det.y);
+    const float fx = fmaf(x, g.inv_hx, g.ox);
+    const float fy = fmaf(y, g.inv_hy, g.oy);
+    const float flx = floorf(fx);
+    const float fly = floorf(fy);
+    t.ax = fx - flx;
+    t.ay = fy - fly;
+    // clamp before the conversion so that far-away points stay well defined
+    t.i0 = (int)fmaxf(fminf(flx, 1.0e6f), -1.0e6f);
+    t.j0 = (int)fmaxf(fminf(fly, 1.0e6f), -1.0e6f);
+    return (unsigned)(t.i0 + 1) <= (unsigned)g.n && (unsigned)(t.j0 + 1) <= (unsigned)g.n;
+}
+
+// Launch helpers
+inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+// Host entry points implemented in projector.cu and used by pdhg.cu
+int ensure_precond(const pat_geometry* g, cudaStream_t st);
+int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y, cudaStream_t st);
+int launch_adjoint(const pat_geometry* g, const float* y, float* out, bool padded, cudaStream_t st);
+int launch_forward_prox(const pat_geometry* g, const float* ubar_pad, float* q, const float* f,
+                        const float* sig_q, float sig_q_scalar, const int* stop, cudaStream_t st);
+int launch_forward_gap(const pat_geometry* g, const float* u, const float* q, const float* f,
+                       double* partials, int n_part, const int* stop, cudaStream_t st);
+int forward_gap_blocks(const pat_geometry* g);
+
+}  // namespace pat

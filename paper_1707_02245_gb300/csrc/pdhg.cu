@@ -1,0 +1,1106 @@
+// PDHGM iteration (Sec. 3.3, Algorithms 1 and 2) for TV, TGV^2 and directional TV, the
+// diagonal steps of Sec. 3.3.2 and the FP64 duality gap / residual of Sec. 3.3.3.
+//
+// Schedule of one iteration n (two global dependency points: K needs all of ubar, the
+// primal step needs all of K^T q):
+//   1. k_forward_prox     q^{n+1} = prox(q^n + Sigma_q K ubar^n)              (data rows)
+//   2. k_adjoint_scatter  w = K^T q^{n+1}                                     (data rows)
+//   3. k_update<REG>      on a pixel tile with a one-pixel halo:
+//        u^{n+1}, v^{n+1} from w, r^{n+1}, s^{n+1};  ubar, vbar by extrapolation;
+//        then the dual step of the NEXT iteration r^{n+2}, s^{n+2} from ubar, vbar.
+//      r and s do not depend on q, so advancing their update by half an iteration gives
+//      exactly the iterates of Algorithm 2.  vbar is never stored.
+// x = (u, v) and (r, s) are ping-pong buffers: iteration n reads set n%2 and writes set
+// (n+1)%2, because tiles read their neighbours' old values in the halo.
+#include <math.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "pat_internal.cuh"
+#include "reduce.cuh"
+#include "stencil.cuh"
+
+namespace pat {
+
+constexpr int TX = 32, TY = 8;            // update tile
+constexpr int LX = TX + 2, LY = TY + 2;   // tile plus one-pixel halo on each side
+
+struct UpdateArgs {
+    int n;
+    float alpha, ab, gamma, theta;
+    // scalar steps (SCALAR2 rule); < 0 selects the diagonal rule
+    float sig2, tau;
+    const float* tau_u;    // N*N (diagonal rule)
+    const float* sig_r;    // N*N (dTV diagonal rule)
+    const float* xi;       // 2*N*N (dTV)
+    const float* w_pad;    // K^T q, (N+2)^2
+    const float* x_in;     // u, v1, v2
+    const float* y_in;     // r1, r2, s11, s22, s12
+    float* x_out;
+    float* y_out;
+    float* ubar_pad;       // (N+2)^2, border stays zero
+    const int* stop;
+    int* iter;             // iteration counter (incremented once per launch)
+};
+
+__device__ __forceinline__ float ld_img(const float* __restrict__ p, int N, int gx, int gy) {
+    return (gx >= 0 && gx < N && gy >= 0 && gy < N) ? __ldg(p + gy * N + gx) : 0.f;
+}
+
+// One PDHG primal step plus the following dual step on a TX x TY tile.
+template <int REG>
+__global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
+    if (a.stop && *(volatile const int*)a.stop) return;
+    const int N = a.n;
+    const size_t NN = (size_t)N * N;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+
+    __shared__ float s_r1m[LY][LX], s_r2m[LY][LX];   // r (dTV: D_xi r) masked for div
+    __shared__ float s_ub[LY][LX];                   // ubar on U = tile + high halo
+    __shared__ float s_un[TY][TX];                   // u^{n+1} on the tile
+    // TGV only (small arrays for TV / dTV)
+    constexpr int VL = (REG == PAT_TGV) ? LY : 1;
+    constexpr int VX = (REG == PAT_TGV) ? LX : 1;
+    constexpr int VT = (REG == PAT_TGV) ? TY : 1;
+    constexpr int VTX = (REG == PAT_TGV) ? TX : 1;
+    __shared__ float s_s11[VL][VX], s_s22[VL][VX], s_s12[VL][VX];
+    __shared__ float s_vb1[VL][VX], s_vb2[VL][VX];   // vbar on V = tile + low halo
+    __shared__ float s_vn1[VT][VTX], s_vn2[VT][VTX];
+
+    const float* u_in = a.x_in;
+    const float* r1_in = a.y_in;
+    const float* r2_in = a.y_in + NN;
+
+    // ---- stage 1: dual fields on the tile plus halo -------------------------------
+    for (int c = tid; c < LX * LY; c += TX * TY) {
+        const int lx = c % LX, ly = c / LX;
+        const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+        const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
+        float r1 = in ? __ldg(r1_in + gy * N + gx) : 0.f;
+        float r2 = in ? __ldg(r2_in + gy * N + gx) : 0.f;
+        if (REG == PAT_DTV) {
+            const float xi0 = in ? __ldg(a.xi + gy * N + gx) : 0.f;
+            const float xi1 = in ? __ldg(a.xi + NN + gy * N + gx) : 0.f;
+            float o0, o1;
+            dxi_apply(xi0, xi1, a.gamma, r1, r2, o0, o1);
+            r1 = o0;
+            r2 = o1;
+        }
+        s_r1m[ly][lx] = (gx < N - 1) ? r1 : 0.f;
+        s_r2m[ly][lx] = (gy < N - 1) ? r2 : 0.f;
+        if (REG == PAT_TGV) {
+            s_s11[ly][lx] = in ? __ldg(a.y_in + 2 * NN + gy * N + gx) : 0.f;
+            s_s22[ly][lx] = in ? __ldg(a.y_in + 3 * NN + gy * N + gx) : 0.f;
+            s_s12[ly][lx] = in ? __ldg(a.y_in + 4 * NN + gy * N + gx) : 0.f;
+        }
+    }
+    __syncthreads();
+
+    // ---- stage 2: primal step and extrapolation on U (u) and V (v) ------------------
+    for (int c = tid; c < LX * LY; c += TX * TY) {
+        const int lx = c % LX, ly = c / LX;
+        const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+        const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
+        if (lx >= 1 && ly >= 1) {  // U: u^{n+1}, ubar
+            float ub = 0.f;
+            if (in) {
+                const int gi = gy * N + gx;
+                const float divr = s_r1m[ly][lx] - s_r1m[ly][lx - 1] + s_r2m[ly][lx] - s_r2m[ly - 1][lx];
+                const float w = __ldg(a.w_pad + (gy + 1) * (N + 2) + gx + 1);
+                const float uo = __ldg(u_in + gi);
+                const float tu = a.tau >= 0.f ? a.tau : __ldg(a.tau_u + gi);
+                const float un = uo - tu * (w - divr);
+                ub = fmaf(a.theta, un - uo, un);
+                if (lx <= TX && ly <= TY) s_un[ly - 1][lx - 1] = un;
+            }
+            s_ub[ly][lx] = ub;
+        }
+        if (REG == PAT_TGV && lx <= TX && ly <= TY) {  // V: v^{n+1}, vbar
+            float vb1 = 0.f, vb2 = 0.f;
+            if (in) {
+                const int gi = gy * N + gx;
+                const bool ax = gx < N - 1, by = gy < N - 1;
+                // E^T s = (-d_x^+ s11 - d_y^+ s12 / sqrt2, -d_y^+ s22 - d_x^+ s12 / sqrt2)
+                const float dx11 = ax ? s_s11[ly][lx + 1] - s_s11[ly][lx] : 0.f;
+                const float dy12 = by ? s_s12[ly + 1][lx] - s_s12[ly][lx] : 0.f;
+                const float dy22 = by ? s_s22[ly + 1][lx] - s_s22[ly][lx] : 0.f;
+                const float dx12 = ax ? s_s12[ly][lx + 1] - s_s12[ly][lx] : 0.f;
+                const float et1 = -dx11 - dy12 * kInvSqrt2f;
+                const float et2 = -dy22 - dx12 * kInvSqrt2f;
+                const float r1 = __ldg(r1_in + gi), r2 = __ldg(r2_in + gi);
+                const float v1o = __ldg(a.x_in + NN + gi), v2o = __ldg(a.x_in + 2 * NN + gi);
+                const float t1 = a.tau >= 0.f ? a.tau : tau_v1_tgv(gx, gy, N);
+                const float t2 = a.tau >= 0.f ? a.tau : tau_v2_tgv(gx, gy, N);
+                const float v1n = v1o - t1 * (et1 - r1);
+                const float v2n = v2o - t2 * (et2 - r2);
+                vb1 = fmaf(a.theta, v1n - v1o, v1n);
+                vb2 = fmaf(a.theta, v2n - v2o, v2n);
+                if (lx >= 1 && ly >= 1) {
+                    s_vn1[ly - 1][lx - 1] = v1n;
+                    s_vn2[ly - 1][lx - 1] = v2n;
+                }
+            }
+            s_vb1[ly][lx] = vb1;
+            s_vb2[ly][lx] = vb2;
+        }
+    }
+    __syncthreads();
+
+    // ---- stage 3: dual step of the next iteration on the tile, and the writes --------
+    const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
+    const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
+    if (gx < N && gy < N) {
+        const int gi = gy * N + gx;
+        const bool ax = gx < N - 1, by = gy < N - 1;
+        const float ub = s_ub[ly][lx];
+        const float gu0 = ax ? s_ub[ly][lx + 1] - ub : 0.f;
+        const float gu1 = by ? s_ub[ly + 1][lx] - ub : 0.f;
+        float r1 = __ldg(r1_in + gi), r2 = __ldg(r2_in + gi);
+        if (REG == PAT_TV) {
+            const float sr = a.sig2 >= 0.f ? a.sig2 : sig_r_tv(gx, gy, N);
+            r1 = fmaf(sr, gu0, r1);
+            r2 = fmaf(sr, gu1, r2);
+        } else if (REG == PAT_DTV) {
+            const float sr = a.sig2 >= 0.f ? a.sig2 : __ldg(a.sig_r + gi);
+            float o0, o1;
+            dxi_apply(__ldg(a.xi + gi), __ldg(a.xi + NN + gi), a.gamma, gu0, gu1, o0, o1);
+            r1 = fmaf(sr, o0, r1);
+            r2 = fmaf(sr, o1, r2);
+        } else {
+            const float sr = a.sig2 >= 0.f ? a.sig2 : sig_r_tgv(gx, gy, N);
+            r1 = fmaf(sr, gu0 - s_vb1[ly][lx], r1);
+            r2 = fmaf(sr, gu1 - s_vb2[ly][lx], r2);
+        }
+        proj2(r1, r2, a.alpha);
+        a.y_out[gi] = r1;
+        a.y_out[NN + gi] = r2;
+        a.x_out[gi] = s_un[threadIdx.y][threadIdx.x];
+        a.ubar_pad[(gy + 1) * (N + 2) + gx + 1] = ub;
+        if (REG == PAT_TGV) {
+            // E vbar with d^- on the masked field
+            const bool axm = gx >= 1, bym = gy >= 1;
+            const float v1 = ax ? s_vb1[ly][lx] : 0.f, v1l = axm ? s_vb1[ly][lx - 1] : 0.f;
+            const float v2 = by ? s_vb2[ly][lx] : 0.f, v2d = bym ? s_vb2[ly - 1][lx] : 0.f;
+            const float v1y = by ? s_vb1[ly][lx] : 0.f, v1d = bym ? s_vb1[ly - 1][lx] : 0.f;
+            const float v2x = ax ? s_vb2[ly][lx] : 0.f, v2l = axm ? s_vb2[ly][lx - 1] : 0.f;
+            const float e11 = v1 - v1l;
+            const float e22 = v2 - v2d;
+            const float e12 = ((v1y - v1d) + (v2x - v2l)) * kInvSqrt2f;
+            const float ss = a.sig2 >= 0.f ? a.sig2 : sig_s_tgv(gx, gy, N);
+            float s11 = fmaf(ss, e11, s_s11[ly][lx]);
+            float s22 = fmaf(ss, e22, s_s22[ly][lx]);
+            float s12 = fmaf(ss, e12, s_s12[ly][lx]);
+            proj3(s11, s22, s12, a.ab);
+            a.y_out[2 * NN + gi] = s11;
+            a.y_out[3 * NN + gi] = s22;
+            a.y_out[4 * NN + gi] = s12;
+            a.x_out[NN + gi] = s_vn1[threadIdx.y][threadIdx.x];
+            a.x_out[2 * NN + gi] = s_vn2[threadIdx.y][threadIdx.x];
+        }
+    }
+    if (a.iter && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) *a.iter += 1;
+}
+
+// Dual step r, s <- prox(r, s + Sigma (A_reg (ubar, vbar))) used once before the first
+// iteration (the update kernel performs it for every later iteration).
+struct DualArgs {
+    int n;
+    float alpha, ab, gamma, sig2;
+    const float* sig_r;
+    const float* xi;
+    const float* ubar_pad;
+    const float* vbar;     // 2*N*N (TGV)
+    const float* y_in;
+    float* y_out;
+};
+
+template <int REG>
+__global__ void k_dual_step(DualArgs a) {
+    const int N = a.n;
+    const size_t NN = (size_t)N * N;
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (gx >= N || gy >= N) return;
+    const int gi = gy * N + gx;
+    const int P = N + 2;
+    const bool ax = gx < N - 1, by = gy < N - 1;
+    const float ub = a.ubar_pad[(gy + 1) * P + gx + 1];
+    const float gu0 = ax ? a.ubar_pad[(gy + 1) * P + gx + 2] - ub : 0.f;
+    const float gu1 = by ? a.ubar_pad[(gy + 2) * P + gx + 1] - ub : 0.f;
+    float r1 = a.y_in[gi], r2 = a.y_in[NN + gi];
+    if (REG == PAT_TV) {
+        const float sr = a.sig2 >= 0.f ? a.sig2 : sig_r_tv(gx, gy, N);
+        r1 = fmaf(sr, gu0, r1);
+        r2 = fmaf(sr, gu1, r2);
+    } else if (REG == PAT_DTV) {
+        const float sr = a.sig2 >= 0.f ? a.sig2 : a.sig_r[gi];
+        float o0, o1;
+        dxi_apply(a.xi[gi], a.xi[NN + gi], a.gamma, gu0, gu1, o0, o1);
+        r1 = fmaf(sr, o0, r1);
+        r2 = fmaf(sr, o1, r2);
+    } else {
+        const float sr = a.sig2 >= 0.f ? a.sig2 : sig_r_tgv(gx, gy, N);
+        r1 = fmaf(sr, gu0 - a.vbar[gi], r1);
+        r2 = fmaf(sr, gu1 - a.vbar[NN + gi], r2);
+    }
+    proj2(r1, r2, a.alpha);
+    a.y_out[gi] = r1;
+    a.y_out[NN + gi] = r2;
+    if (REG == PAT_TGV) {
+        auto vb = [&](int c, int x, int y) -> float { return a.vbar[c * NN + y * N + x]; };
+        const bool axm = gx >= 1, bym = gy >= 1;
+        const float v1 = ax ? vb(0, gx, gy) : 0.f, v1l = axm ? vb(0, gx - 1, gy) : 0.f;
+        const float v2 = by ? vb(1, gx, gy) : 0.f, v2d = bym ? vb(1, gx, gy - 1) : 0.f;
+        const float v1y = by ? vb(0, gx, gy) : 0.f, v1d = bym ? vb(0, gx, gy - 1) : 0.f;
+        const float v2x = ax ? vb(1, gx, gy) : 0.f, v2l = axm ? vb(1, gx - 1, gy) : 0.f;
+        const float e11 = v1 - v1l, e22 = v2 - v2d, e12 = ((v1y - v1d) + (v2x - v2l)) * kInvSqrt2f;
+        const float ss = a.sig2 >= 0.f ? a.sig2 : sig_s_tgv(gx, gy, N);
+        float s11 = fmaf(ss, e11, a.y_in[2 * NN + gi]);
+        float s22 = fmaf(ss, e22, a.y_in[3 * NN + gi]);
+        float s12 = fmaf(ss, e12, a.y_in[4 * NN + gi]);
+        proj3(s11, s22, s12, a.ab);
+        a.y_out[2 * NN + gi] = s11;
+        a.y_out[3 * NN + gi] = s22;
+        a.y_out[4 * NN + gi] = s12;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// FP64 duality gap over pixels (Sec. 3.3.3, box-restricted reading)
+// partials per block: {R1, R2, |K^T q - div r|_1, |E^T s - r|_1, |x - x_old|^2, |x_old|^2}
+// ---------------------------------------------------------------------------------
+struct GapArgs {
+    int n;
+    double gamma;
+    const float* xi;
+    const float* x;       // x^{n+1}
+    const float* x_old;   // x^n (NULL: residual terms are zero)
+    const float* y;       // r, s at the same evaluation (y^{n+1})
+    const float* w_pad;   // K^T q^{n+1}
+    double* partials;
+    const int* stop;
+};
+
+template <int REG>
+__global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
+    if (a.stop && *(volatile const int*)a.stop) return;
+    const int N = a.n;
+    const size_t NN = (size_t)N * N;
+    double acc[6] = {0, 0, 0, 0, 0, 0};
+    const int nthreads = gridDim.x * blockDim.x;
+    auto X = [&](int c, int x, int y) -> double { return (double)a.x[c * NN + (size_t)y * N + x]; };
+    auto Yf = [&](int c, int x, int y) -> double { return (double)a.y[c * NN + (size_t)y * N + x]; };
+    for (long long p = blockIdx.x * blockDim.x + threadIdx.x; p < (long long)NN; p += nthreads) {
+        const int gx = (int)(p % N), gy = (int)(p / N);
+        const bool ax = gx < N - 1, by = gy < N - 1;
+        // gradient of u
+        const double u = X(0, gx, gy);
+        double g0 = ax ? X(0, gx + 1, gy) - u : 0.0;
+        double g1 = by ? X(0, gx, gy + 1) - u : 0.0;
+        // D_xi for dTV
+        double xi0 = 0, xi1 = 0;
+        if (REG == PAT_DTV) {
+            xi0 = a.xi[gy * N + gx];
+            xi1 = a.xi[NN + gy * N + gx];
+            const double dot = xi0 * g0 + xi1 * g1;
+            const double t0 = g0 - a.gamma * xi0 * dot, t1 = g1 - a.gamma * xi1 * dot;
+            g0 = t0;
+            g1 = t1;
+        }
+        if (REG == PAT_TGV) {
+            g0 -= X(1, gx, gy);
+            g1 -= X(2, gx, gy);
+        }
+        acc[0] += sqrt(g0 * g0 + g1 * g1);
+        // (masked, D_xi-weighted) r for div
+        auto rm = [&](int c, int x, int y) -> double {
+            if (x < 0 || y < 0) return 0.0;
+            if (c == 0 && x >= N - 1) return 0.0;
+            if (c == 1 && y >= N - 1) return 0.0;
+            double r0 = Yf(0, x, y), r1 = Yf(1, x, y);
+            if (REG == PAT_DTV) {
+                const double z0 = a.xi[y * N + x], z1 = a.xi[NN + y * N + x];
+                const double dot = z0 * r0 + z1 * r1;
+                const double o0 = r0 - a.gamma * z0 * dot, o1 = r1 - a.gamma * z1 * dot;
+                return c == 0 ? o0 : o1;
+            }
+            return c == 0 ? r0 : r1;
+        };
+        const double divr = rm(0, gx, gy) - rm(0, gx - 1, gy) + rm(1, gx, gy) - rm(1, gx, gy - 1);
+        const double w = (double)a.w_pad[(size_t)(gy + 1) * (N + 2) + gx + 1];
+        acc[2] += fabs(w - divr);
+        if (REG == PAT_TGV) {
+            auto vm = [&](int c, int x, int y, bool mx) -> double {  // masked v for d^-
+                if (x < 0 || y < 0) return 0.0;
+                if (mx ? (x >= N - 1) : (y >= N - 1)) return 0.0;
+                return X(1 + c, x, y);
+            };
+            const double e11 = vm(0, gx, gy, true) - vm(0, gx - 1, gy, true);
+            const double e22 = vm(1, gx, gy, false) - vm(1, gx, gy - 1, false);
+            const double e12 = ((vm(0, gx, gy, false) - vm(0, gx, gy - 1, false)) +
+                                (vm(1, gx, gy, true) - vm(1, gx - 1, gy, true))) / kSqrt2;
+            acc[1] += sqrt(e11 * e11 + e22 * e22 + e12 * e12);
+            const double s11 = Yf(2, gx, gy), s22 = Yf(3, gx, gy), s12 = Yf(4, gx, gy);
+            const double dx11 = ax ? Yf(2, gx + 1, gy) - s11 : 0.0;
+            const double dy12 = by ? Yf(4, gx, gy + 1) - s12 : 0.0;
+            const double dy22 = by ? Yf(3, gx, gy + 1) - s22 : 0.0;
+            const double dx12 = ax ? Yf(4, gx + 1, gy) - s12 : 0.0;
+            const double et1 = -dx11 - dy12 / kSqrt2, et2 = -dy22 - dx12 / kSqrt2;
+            acc[3] += fabs(et1 - Yf(0, gx, gy)) + fabs(et2 - Yf(1, gx, gy));
+        }
+        if (a.x_old) {
+            const int nc = REG == PAT_TGV ? 3 : 1;
+            for (int c = 0; c < nc; ++c) {
+                const double xn = X(c, gx, gy), xo = (double)a.x_old[c * NN + (size_t)gy * N + gx];
+                acc[4] += (xn - xo) * (xn - xo);
+                acc[5] += xo * xo;
+            }
+        }
+    }
+    block_sum<6>(acc);
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 6; ++c) a.partials[6 * blockIdx.x + c] = acc[c];
+}
+
+struct InfoDev {
+    double primal, dual, gap, rel_gap, residual;
+    int iters_done, status, stop, iter;
+};
+
+struct FinalArgs {
+    const double* data_part;
+    int n_data;
+    const double* pix_part;
+    int n_pix;
+    double alpha, beta, box_u, box_v, tol;
+    int reg;
+    InfoDev* info;
+};
+
+__global__ void __launch_bounds__(256) k_gap_final(FinalArgs a) {
+    if (*(volatile const int*)&a.info->stop) return;
+    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = threadIdx.x; b < a.n_data; b += blockDim.x)
+        for (int c = 0; c < 3; ++c) acc[c] += a.data_part[3 * b + c];
+    for (int b = threadIdx.x; b < a.n_pix; b += blockDim.x)
+        for (int c = 0; c < 6; ++c) acc[3 + c] += a.pix_part[6 * b + c];
+    block_sum<9>(acc);
+    if (threadIdx.x != 0) return;
+    const double res2 = acc[0], q2 = acc[1], qf = acc[2];
+    const double r1 = acc[3], r2 = acc[4], bu = acc[5], bv = acc[6], dx2 = acc[7], x2 = acc[8];
+    const double reg = a.reg == PAT_TGV ? r1 + a.beta * r2 : r1;
+    const double primal = 0.5 * res2 + a.alpha * reg;
+    const double dual = -(0.5 * q2 + qf) - a.box_u * bu - (a.reg == PAT_TGV ? a.box_v * bv : 0.0);
+    const double gap = primal - dual;
+    const double rel = primal > 0 ? gap / primal : (gap == 0 ? 0.0 : INFINITY);
+    const double resid = x2 > 0 ? sqrt(dx2 / x2) : (dx2 == 0 ? 0.0 : INFINITY);
+    InfoDev* in = a.info;
+    in->primal = primal;
+    in->dual = dual;
+    in->gap = gap;
+    in->rel_gap = rel;
+    in->residual = resid;
+    in->iters_done = in->iter;
+    if (!isfinite(gap) || !isfinite(primal)) {
+        in->status = PAT_STATUS_DIVERGED;
+        in->stop = 1;
+    } else if (a.tol > 0 && rel <= a.tol) {
+        in->status = PAT_STATUS_CONVERGED;
+        in->stop = 1;
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// steps (Sec. 3.3.2): tau_u, sigma_r (dTV) need the K sums and xi; computed in FP64
+// ---------------------------------------------------------------------------------
+struct StepArgs {
+    int n, reg;
+    double gamma;
+    const float* kcol;
+    const float* xi;
+    float* tau_u;
+    float* sig_r;
+    float* sig_s;
+    float* tau_v;
+};
+
+__global__ void k_steps_pixels(StepArgs a) {
+    const int N = a.n;
+    const size_t NN = (size_t)N * N;
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (gx >= N || gy >= N) return;
+    const int gi = gy * N + gx;
+    const double A = gx < N - 1, B = gy < N - 1;
+    const double cx = (double)((gx < N - 1) + (gx >= 1)), cy = (double)((gy < N - 1) + (gy >= 1));
+    double col_u = (double)a.kcol[gi];
+    double sr = 1.0;
+    if (a.reg == PAT_DTV) {
+        auto dm = [&](int x, int y, double& d00, double& d01, double& d11) {
+            const double z0 = a.xi[y * N + x], z1 = a.xi[NN + y * N + x];
+            d00 = 1.0 - a.gamma * z0 * z0;
+            d01 = -a.gamma * z0 * z1;
+            d11 = 1.0 - a.gamma * z1 * z1;
+        };
+        double d00, d01, d11;
+        dm(gx, gy, d00, d01, d11);
+        // rows c = 0, 1 at this pixel: D_c0 d_x^+ + D_c1 d_y^+
+        const double row0 = fabs(d00) * A + fabs(d01) * B + fabs(d00 * A + d01 * B);
+        const double row1 = fabs(d01) * A + fabs(d11) * B + fabs(d01 * A + d11 * B);
+        const double mx = fmax(row0, row1);
+        sr = mx > 0 ? 1.0 / mx : 1.0;
+        col_u += fabs(d00 * A + d01 * B) + fabs(d01 * A + d11 * B);
+        if (gx >= 1) {
+            double e00, e01, e11;
+            dm(gx - 1, gy, e00, e01, e11);
+            col_u += fabs(e00) + fabs(e01);
+        }
+        if (gy >= 1) {
+            double e00, e01, e11;
+            dm(gx, gy - 1, e00, e01, e11);
+            col_u += fabs(e01) + fabs(e11);
+        }
+    } else {
+        col_u += cx + cy;
+        if (a.reg == PAT_TV) {
+            const double m = fmax(2 * A, 2 * B);
+            sr = m > 0 ? 1.0 / m : 1.0;
+        } else {
+            sr = 1.0 / fmax(2 * A + 1, 2 * B + 1);
+        }
+    }
+    if (a.tau_u) a.tau_u[gi] = (float)(1.0 / col_u);
+    if (a.sig_r) a.sig_r[gi] = (float)sr;
+    if (a.reg == PAT_TGV) {
+        if (a.sig_s) a.sig_s[gi] = (float)(1.0 / fmax(fmax(cx, cy), (cx + cy) / kSqrt2));
+        if (a.tau_v) {
+            a.tau_v[gi] = (float)(1.0 / (1 + 2 * A + kSqrt2 * B));
+            a.tau_v[NN + gi] = (float)(1.0 / (1 + 2 * B + kSqrt2 * A));
+        }
+    }
+}
+
+__global__ void k_sig_q(const float* __restrict__ krow, float* __restrict__ sig_q, long long S) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < S) {
+        const double k = krow[i];
+        sig_q[i] = k > 0 ? (float)(1.0 / k) : 1.f;
+    }
+}
+
+__global__ void k_pad(const float* __restrict__ u, float* __restrict__ pad, int N) {
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
+    const int P = N + 2;
+    if (gx >= P || gy >= P) return;
+    const int x = gx - 1, y = gy - 1;
+    pad[gy * P + gx] = (x >= 0 && x < N && y >= 0 && y < N && u) ? u[y * N + x] : 0.f;
+}
+
+__global__ void k_unpad(const float* __restrict__ pad, float* __restrict__ u, int N) {
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (gx >= N || gy >= N) return;
+    u[gy * N + gx] = pad[(gy + 1) * (N + 2) + gx + 1];
+}
+
+// Copies the final state out of the ping-pong buffers selected by the iteration count.
+struct OutArgs {
+    int n, reg;
+    long long S;
+    float theta;
+    const float* X[2];
+    const float* Y[2];
+    const float* q;
+    const float* ubar_pad;
+    const InfoDev* info;
+    float* u_out;
+    float* x_out;
+    float* xbar_out;
+    float* y_out;
+};
+
+__global__ void k_output(OutArgs a) {
+    const int N = a.n;
+    const long long NN = (long long)N * N;
+    const int it = a.info->iter;
+    const float* x = a.X[it & 1];
+    const float* x_prev = a.X[(it + 1) & 1];
+    const float* yrs = a.Y[(it + 1) & 1];  // r^I, s^I were read by the last update
+    const int nv = a.reg == PAT_TGV ? 2 : 0;
+    const long long nx = NN * (1 + nv), ny = NN * (a.reg == PAT_TGV ? 5 : 2);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nx + ny + a.S; i += stride) {
+        if (i < nx) {
+            if (i < NN && a.u_out) a.u_out[i] = x[i];
+            if (a.x_out) a.x_out[i] = x[i];
+            if (a.xbar_out) {
+                if (i < NN) {
+                    const int gx = (int)(i % N), gy = (int)(i / N);
+                    a.xbar_out[i] = a.ubar_pad[(long long)(gy + 1) * (N + 2) + gx + 1];
+                } else {
+                    // vbar^I = v^I + theta (v^I - v^{I-1}); with I = 0 the warm-start vbar is
+                    // not recoverable here and v^0 is returned
+                    a.xbar_out[i] = it > 0 ? fmaf(a.theta, x[i] - x_prev[i], x[i]) : x[i];
+                }
+            }
+        } else if (a.y_out) {
+            const long long j = i - nx;
+            if (j < a.S)
+                a.y_out[j] = a.q[j];
+            else
+                a.y_out[j] = yrs[j - a.S];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------------
+static size_t align_up(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Workspace {
+    void* base = nullptr;
+    size_t bytes = 0;
+    float* X[2] = {nullptr, nullptr};
+    float* Y[2] = {nullptr, nullptr};
+    float *q = nullptr, *ubar_pad = nullptr, *w_pad = nullptr, *vbar0 = nullptr;
+    float *tau_u = nullptr, *sig_q = nullptr, *sig_r = nullptr;
+    double *data_part = nullptr, *pix_part = nullptr;
+    InfoDev* info = nullptr;
+    int n_data = 0, n_pix = 0;
+};
+
+static int pix_blocks(int N) { return std::min(4 * 152, ceil_div((long long)N * N, 256)); }
+
+static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaStream_t st) {
+    const size_t N = g->desc.n, NN = N * N, S = (size_t)g->desc.n_det * g->desc.n_t;
+    const size_t nx = NN * (reg == PAT_TGV ? 3 : 1), ny = NN * (reg == PAT_TGV ? 5 : 2);
+    const size_t P2 = (N + 2) * (N + 2);
+    ws.n_data = forward_gap_blocks(g);
+    ws.n_pix = pix_blocks((int)N);
+    size_t off[16];
+    size_t sz[16] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, P2 * 4, (reg == PAT_TGV ? 2 * NN : 1) * 4,
+                     NN * 4, S * 4, NN * 4, (size_t)ws.n_data * 3 * 8, (size_t)ws.n_pix * 6 * 8, sizeof(InfoDev)};
+    size_t total = 0;
+    for (int i = 0; i < 14; ++i) {
+        off[i] = total;
+        total += align_up(sz[i]);
+    }
+    PAT_CUDA(cudaMallocAsync(&ws.base, total, st));
+    ws.bytes = total;
+    char* b = (char*)ws.base;
+    ws.X[0] = (float*)(b + off[0]);
+    ws.X[1] = (float*)(b + off[1]);
+    ws.Y[0] = (float*)(b + off[2]);
+    ws.Y[1] = (float*)(b + off[3]);
+    ws.q = (float*)(b + off[4]);
+    ws.ubar_pad = (float*)(b + off[5]);
+    ws.w_pad = (float*)(b + off[6]);
+    ws.vbar0 = (float*)(b + off[7]);
+    ws.tau_u = (float*)(b + off[8]);
+    ws.sig_q = (float*)(b + off[9]);
+    ws.sig_r = (float*)(b + off[10]);
+    ws.data_part = (double*)(b + off[11]);
+    ws.pix_part = (double*)(b + off[12]);
+    ws.info = (InfoDev*)(b + off[13]);
+    return PAT_OK;
+}
+
+static int validate(const pat_geometry* g, const pat_params* p, const char* who) {
+    char buf[256];
+    auto bad = [&](const char* what) {
+        snprintf(buf, sizeof buf, "%s: %s", who, what);
+        return fail(PAT_ERR_INVALID_ARG, buf);
+    };
+    if (!g || !p) return bad("NULL geometry or params");
+    if (p->reg < PAT_TV || p->reg > PAT_DTV) return bad("reg must be PAT_TV, PAT_TGV or PAT_DTV");
+    if (!(p->alpha >= 0) || !std::isfinite(p->alpha)) return bad("alpha must be finite and >= 0");
+    if (!(p->beta >= 0) || !std::isfinite(p->beta)) return bad("beta must be finite and >= 0");
+    if (p->reg == PAT_DTV && (!(p->gamma >= 0) || !(p->gamma <= 1))) return bad("gamma must be in [0, 1]");
+    if (p->reg == PAT_DTV && !p->xi_dev) return bad("directional TV needs xi_dev");
+    if (p->iters < 0) return bad("iters must be >= 0");
+    if (!(p->tol >= 0)) return bad("tol must be >= 0");
+    if (p->gap_every < 0) return bad("gap_every must be >= 0");
+    if (p->precond != PAT_PRECOND_DIAG && p->precond != PAT_PRECOND_SCALAR2) return bad("unknown precond");
+    if (!(p->theta >= 0) || !(p->theta <= 1)) return bad("theta must be in [0, 1]");
+    if (!(p->box_u > 0) || !(p->box_v > 0)) return bad("box half-widths must be > 0");
+    return PAT_OK;
+}
+
+struct ScalarSteps {
+    float sig_q = -1.f, sig2 = -1.f, tau = -1.f;
+};
+
+int scalar2_steps(const pat_geometry* g, const pat_params* p, ScalarSteps& out, cudaStream_t st);
+
+// Fills the step arrays in ws (diagonal rule) or the scalars (paper rule).
+static int compute_steps(const pat_geometry* g, const pat_params* p, Workspace& ws, ScalarSteps& sc,
+                         cudaStream_t st) {
+    const int N = g->desc.n;
+    const long long S = (long long)g->desc.n_det * g->desc.n_t;
+    if (p->precond == PAT_PRECOND_SCALAR2) return scalar2_steps(g, p, sc, st);
+    int rc = ensure_precond(g, st);
+    if (rc) return rc;
+    k_sig_q<<<ceil_div(S, 256), 256, 0, st>>>(g->pc.krow, ws.sig_q, S);
+    PAT_LAUNCH_CHECK("k_sig_q");
+    StepArgs sa{N, p->reg, p->gamma, g->pc.kcol, p->xi_dev, ws.tau_u, p->reg == PAT_DTV ? ws.sig_r : nullptr,
+                nullptr, nullptr};
+    dim3 blk(32, 8), grd(ceil_div(N, 32), ceil_div(N, 8));
+    k_steps_pixels<<<grd, blk, 0, st>>>(sa);
+    PAT_LAUNCH_CHECK("k_steps_pixels");
+    return PAT_OK;
+}
+
+template <int REG>
+static int launch_update(const pat_geometry* g, const pat_params* p, Workspace& ws, const ScalarSteps& sc, int it,
+                         cudaStream_t st) {
+    const int N = g->desc.n;
+    UpdateArgs a;
+    a.n = N;
+    a.alpha = (float)p->alpha;
+    a.ab = (float)(p->alpha * p->beta);
+    a.gamma = (float)p->gamma;
+    a.theta = (float)p->theta;
+    a.sig2 = sc.sig2;
+    a.tau = sc.tau;
+    a.tau_u = ws.tau_u;
+    a.sig_r = ws.sig_r;
+    a.xi = p->xi_dev;
+    a.w_pad = ws.w_pad;
+    a.x_in = ws.X[it & 1];
+    a.y_in = ws.Y[it & 1];
+    a.x_out = ws.X[(it + 1) & 1];
+    a.y_out = ws.Y[(it + 1) & 1];
+    a.ubar_pad = ws.ubar_pad;
+    a.stop = &ws.info->stop;
+    a.iter = &ws.info->iter;
+    dim3 grd(ceil_div(N, TX), ceil_div(N, TY)), blk(TX, TY);
+    k_update<REG><<<grd, blk, 0, st>>>(a);
+    PAT_LAUNCH_CHECK("k_update");
+    return PAT_OK;
+}
+
+template <int REG>
+static int launch_gap(const pat_geometry* g, const pat_params* p, Workspace& ws, const float* x, const float* x_old,
+                      const float* y, const float* q, const float* f, const int* stop, cudaStream_t st) {
+    const int N = g->desc.n;
+    int rc = launch_forward_gap(g, x, q, f, ws.data_part, ws.n_data, stop, st);
+    if (rc) return rc;
+    GapArgs ga{N, p->gamma, p->xi_dev, x, x_old, y, ws.w_pad, ws.pix_part, stop};
+    k_gap_pixels<REG><<<ws.n_pix, 256, 0, st>>>(ga);
+    PAT_LAUNCH_CHECK("k_gap_pixels");
+    FinalArgs fa{ws.data_part, ws.n_data, ws.pix_part, ws.n_pix, p->alpha, p->beta, p->box_u, p->box_v,
+                 p->tol, p->reg, ws.info};
+    k_gap_final<<<1, 256, 0, st>>>(fa);
+    PAT_LAUNCH_CHECK("k_gap_final");
+    return PAT_OK;
+}
+
+template <int REG>
+static int enqueue_iterations(const pat_geometry* g, const float* f, const pat_params* p, Workspace& ws,
+                              const ScalarSteps& sc, int it0, int count, cudaStream_t st) {
+    const int* stop = &ws.info->stop;
+    for (int it = it0; it < it0 + count; ++it) {
+        int rc = launch_forward_prox(g, ws.ubar_pad, ws.q, f, sc.sig_q >= 0 ? nullptr : ws.sig_q, sc.sig_q, stop, st);
+        if (rc) return rc;
+        rc = launch_adjoint(g, ws.q, ws.w_pad, true, st);
+        if (rc) return rc;
+        rc = launch_update<REG>(g, p, ws, sc, it, st);
+        if (rc) return rc;
+        const int done = it + 1;
+        if ((p->gap_every > 0 && done % p->gap_every == 0) || done == p->iters) {
+            rc = launch_gap<REG>(g, p, ws, ws.X[done & 1], ws.X[it & 1], ws.Y[it & 1], ws.q, f, stop, st);
+            if (rc) return rc;
+        }
+    }
+    return PAT_OK;
+}
+
+template <int REG>
+static int run_reconstruct(const pat_geometry* g, const float* f, const pat_params* p, float* u_out, pat_info* info,
+                           cudaStream_t st) {
+    const int N = g->desc.n;
+    const size_t NN = (size_t)N * N, S = (size_t)g->desc.n_det * g->desc.n_t;
+    const size_t nx = NN * (REG == PAT_TGV ? 3 : 1), ny = NN * (REG == PAT_TGV ? 5 : 2);
+    cudaEvent_t e0, e1;
+    PAT_CUDA(cudaEventCreate(&e0));
+    PAT_CUDA(cudaEventCreate(&e1));
+    PAT_CUDA(cudaEventRecord(e0, st));
+    Workspace ws;
+    int rc = alloc_workspace(g, REG, ws, st);
+    if (rc) return rc;
+    ScalarSteps sc;
+    rc = compute_steps(g, p, ws, sc, st);
+    // initial state
+    if (!rc) {
+        if (p->x0_dev)
+            rc = cudaMemcpyAsync(ws.X[0], p->x0_dev, nx * 4, cudaMemcpyDeviceToDevice, st) ? PAT_ERR_CUDA : 0;
+        else
+            rc = cudaMemsetAsync(ws.X[0], 0, nx * 4, st) ? PAT_ERR_CUDA : 0;
+    }
+    if (!rc) {
+        if (p->y0_dev) {
+            rc = cudaMemcpyAsync(ws.q, p->y0_dev, S * 4, cudaMemcpyDeviceToDevice, st) ? PAT_ERR_CUDA : 0;
+            if (!rc)
+                rc = cudaMemcpyAsync(ws.Y[1], p->y0_dev + S, ny * 4, cudaMemcpyDeviceToDevice, st) ? PAT_ERR_CUDA
+                                                                                                     : 0;
+        } else {
+            rc = cudaMemsetAsync(ws.q, 0, S * 4, st) ? PAT_ERR_CUDA : 0;
+            if (!rc) rc = cudaMemsetAsync(ws.Y[1], 0, ny * 4, st) ? PAT_ERR_CUDA : 0;
+        }
+    }
+    if (!rc) rc = cudaMemsetAsync(ws.info, 0, sizeof(InfoDev), st) ? PAT_ERR_CUDA : 0;
+    if (!rc) {
+        const float* xb = p->xbar0_dev ? p->xbar0_dev : p->x0_dev;
+        dim3 blk(32, 8), grd(ceil_div(N + 2, 32), ceil_div(N + 2, 8));
+        k_pad<<<grd, blk, 0, st>>>(xb, ws.ubar_pad, N);
+        if (REG == PAT_TGV) {
+            if (xb)
+                cudaMemcpyAsync(ws.vbar0, xb + NN, 2 * NN * 4, cudaMemcpyDeviceToDevice, st);
+            else
+                cudaMemsetAsync(ws.vbar0, 0, 2 * NN * 4, st);
+        }
+        // dual prologue: (r^1, s^1) from (r^0, s^0) and (ubar^0, vbar^0) into Y[0]
+        DualArgs da{N, (float)p->alpha, (float)(p->alpha * p->beta), (float)p->gamma, sc.sig2, ws.sig_r,
+                    p->xi_dev, ws.ubar_pad, ws.vbar0, ws.Y[1], ws.Y[0]};
+        dim3 g2(ceil_div(N, 32), ceil_div(N, 8));
+        k_dual_step<REG><<<g2, blk, 0, st>>>(da);
+        rc = cudaGetLastError() ? PAT_ERR_CUDA : 0;
+    }
+    if (!rc && p->iters > 0) rc = enqueue_iterations<REG>(g, f, p, ws, sc, 0, p->iters, st);
+    if (!rc) {
+        OutArgs oa;
+        oa.n = N;
+        oa.reg = REG;
+        oa.S = (long long)S;
+        oa.theta = (float)p->theta;
+        oa.X[0] = ws.X[0];
+        oa.X[1] = ws.X[1];
+        oa.Y[0] = ws.Y[0];
+        oa.Y[1] = ws.Y[1];
+        oa.q = ws.q;
+        oa.ubar_pad = ws.ubar_pad;
+        oa.info = ws.info;
+        oa.u_out = u_out;
+        oa.x_out = p->x_out_dev;
+        oa.xbar_out = p->xbar_out_dev;
+        oa.y_out = p->y_out_dev;
+        k_output<<<std::min(2 * 152, ceil_div((long long)(nx + ny + S), 256)), 256, 0, st>>>(oa);
+        rc = cudaGetLastError() ? PAT_ERR_CUDA : 0;
+    }
+    InfoDev hinfo{};
+    if (!rc) rc = cudaMemcpyAsync(&hinfo, ws.info, sizeof(InfoDev), cudaMemcpyDeviceToHost, st) ? PAT_ERR_CUDA : 0;
+    cudaEventRecord(e1, st);
+    cudaFreeAsync(ws.base, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    if (!rc && se != cudaSuccess) rc = cuda_fail(se, "pat_reconstruct: stream synchronize");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) {
+        if (rc == PAT_ERR_CUDA) set_error(std::string("pat_reconstruct: ") + cudaGetErrorString(cudaGetLastError()));
+        return rc;
+    }
+    if (info) {
+        info->iters_done = p->iters == 0 ? 0 : hinfo.iters_done;
+        info->status = hinfo.stop ? hinfo.status : PAT_STATUS_MAXITER;
+        info->primal = hinfo.primal;
+        info->dual = hinfo.dual;
+        info->gap = hinfo.gap;
+        info->rel_gap = hinfo.rel_gap;
+        info->residual = hinfo.residual;
+        info->ms = ms;
+    }
+    if (hinfo.status == PAT_STATUS_DIVERGED) return fail(PAT_ERR_NONFINITE, "pat_reconstruct: duality gap not finite");
+    return PAT_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// paper rule (Sec. 3.3.2): L1 = ||K||, L2 = ||B|| by power iteration from the start
+// vector x_j = 1 + sin(0.7 j + 0.3)/2; tau = 1/L1, sigma_i = 0.99 / (4 tau L_i^2)
+// ---------------------------------------------------------------------------------
+__global__ void k_power_start(float* x, long long n) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) x[i] = (float)(1.0 + 0.5 * sin(0.7 * (double)i + 0.3));
+}
+
+__global__ void k_norm2(const float* __restrict__ x, long long n, double* out) {
+    double v[1] = {0.0};
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        v[0] += (double)x[i] * x[i];
+    block_sum<1>(v);
+    if (threadIdx.x == 0) atomicAdd(out, v[0]);
+}
+
+__global__ void k_scale(float* x, long long n, const double* nrm2, double* lam_out) {
+    const double nr = sqrt(*nrm2);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && lam_out) *lam_out = nr;
+    const float s = nr > 0 ? (float)(1.0 / nr) : 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] *= s;
+}
+
+// B x for the regulariser block of A: x = (u[, v1, v2]), out rows as in pat_params y.
+__global__ void k_apply_B(int N, int reg, float gamma, const float* __restrict__ xi, const float* __restrict__ x,
+                          float* __restrict__ out) {
+    const long long NN = (long long)N * N;
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (gx >= N || gy >= N) return;
+    const int gi = gy * N + gx;
+    const bool ax = gx < N - 1, by = gy < N - 1, axm = gx >= 1, bym = gy >= 1;
+    float g0 = ax ? x[gi + 1] - x[gi] : 0.f, g1 = by ? x[gi + N] - x[gi] : 0.f;
+    if (reg == PAT_DTV) {
+        float o0, o1;
+        dxi_apply(xi[gi], xi[NN + gi], gamma, g0, g1, o0, o1);
+        g0 = o0;
+        g1 = o1;
+    }
+    if (reg == PAT_TGV) {
+        g0 -= x[NN + gi];
+        g1 -= x[2 * NN + gi];
+        auto v = [&](int c, int xx, int yy) { return x[(1 + c) * NN + yy * N + xx]; };
+        const float v1 = ax ? v(0, gx, gy) : 0.f, v1l = axm ? v(0, gx - 1, gy) : 0.f;
+        const float v2 = by ? v(1, gx, gy) : 0.f, v2d = bym ? v(1, gx, gy - 1) : 0.f;
+        const float v1y = by ? v(0, gx, gy) : 0.f, v1d = bym ? v(0, gx, gy - 1) : 0.f;
+        const float v2x = ax ? v(1, gx, gy) : 0.f, v2l = axm ? v(1, gx - 1, gy) : 0.f;
+        out[2 * NN + gi] = v1 - v1l;
+        out[3 * NN + gi] = v2 - v2d;
+        out[4 * NN + gi] = ((v1y - v1d) + (v2x - v2l)) * kInvSqrt2f;
+    }
+    out[gi] = g0;
+    out[NN + gi] = g1;
+}
+
+// B^T y
+__global__ void k_apply_BT(int N, int reg, float gamma, const float* __restrict__ xi, const float* __restrict__ y,
+                           float* __restrict__ out) {
+    const long long NN = (long long)N * N;
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (gx >= N || gy >= N) return;
+    const int gi = gy * N + gx;
+    const bool ax = gx < N - 1, by = gy < N - 1;
+    auto rm = [&](int c, int xx, int yy) -> float {
+        if (xx < 0 || yy < 0) return 0.f;
+        if (c == 0 && xx >= N - 1) return 0.f;
+        if (c == 1 && yy >= N - 1) return 0.f;
+        float r0 = y[yy * N + xx], r1 = y[NN + yy * N + xx];
+        if (reg == PAT_DTV) {
+            float o0, o1;
+            dxi_apply(xi[yy * N + xx], xi[NN + yy * N + xx], gamma, r0, r1, o0, o1);
+            r0 = o0;
+            r1 = o1;
+        }
+        return c == 0 ? r0 : r1;
+    };
+    const float divr = rm(0, gx, gy) - rm(0, gx - 1, gy) + rm(1, gx, gy) - rm(1, gx, gy - 1);
+    out[gi] = -divr;
+    if (reg == PAT_TGV) {
+        auto s = [&](int c, int xx, int yy) { return y[(2 + c) * NN + yy * N + xx]; };
+        const float dx11 = ax ? s(0, gx + 1, gy) - s(0, gx, gy) : 0.f;
+        const float dy12 = by ? s(2, gx, gy + 1) - s(2, gx, gy) : 0.f;
+        const float dy22 = by ? s(1, gx, gy + 1) - s(1, gx, gy) : 0.f;
+        const float dx12 = ax ? s(2, gx + 1, gy) - s(2, gx, gy) : 0.f;
+        out[NN + gi] = -dx11 - dy12 * kInvSqrt2f - y[gi];
+        out[2 * NN + gi] = -dy22 - dx12 * kInvSqrt2f - y[NN + gi];
+    }
+}
+
+static constexpr int kPowerIters = 100;
+
+int scalar2_steps(const pat_geometry* g, const pat_params* p, ScalarSteps& out, cudaStream_t st) {
+    const int N = g->desc.n;
+    const long long NN = (long long)N * N, S = (long long)g->desc.n_det * g->desc.n_t;
+    const long long nx = NN * (p->reg == PAT_TGV ? 3 : 1), ny = NN * (p->reg == PAT_TGV ? 5 : 2);
+    float *x = nullptr, *y = nullptr;
+    double* acc = nullptr;
+    PAT_CUDA(cudaMallocAsync(&x, (size_t)std::max(nx, NN) * 4, st));
+    PAT_CUDA(cudaMallocAsync(&y, (size_t)std::max(ny, S) * 4, st));
+    PAT_CUDA(cudaMallocAsync(&acc, 2 * kPowerIters * 2 * sizeof(double), st));
+    PAT_CUDA(cudaMemsetAsync(acc, 0, 2 * kPowerIters * 2 * sizeof(double), st));
+    dim3 blk(32, 8), grd(ceil_div(N, 32), ceil_div(N, 8));
+    const int nb = 2 * 152;
+    double lam[2] = {0, 0};
+    for (int op = 0; op < 2; ++op) {
+        const long long n = op == 0 ? NN : nx;
+        k_power_start<<<ceil_div(n, 256), 256, 0, st>>>(x, n);
+        double* a0 = acc + op * 2 * kPowerIters;
+        k_norm2<<<nb, 256, 0, st>>>(x, n, a0);
+        k_scale<<<nb, 256, 0, st>>>(x, n, a0, nullptr);
+        for (int it = 0; it < kPowerIters; ++it) {
+            if (op == 0) {
+                int rc = launch_forward(g, x, false, y, st);
+                if (rc) return rc;
+                rc = launch_adjoint(g, y, x, false, st);
+                if (rc) return rc;
+            } else {
+                k_apply_B<<<grd, blk, 0, st>>>(N, p->reg, (float)p->gamma, p->xi_dev, x, y);
+                k_apply_BT<<<grd, blk, 0, st>>>(N, p->reg, (float)p->gamma, p->xi_dev, y, x);
+            }
+            double* slot = a0 + 1 + it;
+            k_norm2<<<nb, 256, 0, st>>>(x, n, slot);
+            k_scale<<<nb, 256, 0, st>>>(x, n, slot, nullptr);
+        }
+        PAT_LAUNCH_CHECK("power iteration");
+        double last = 0;
+        PAT_CUDA(cudaMemcpyAsync(&last, a0 + kPowerIters, sizeof(double), cudaMemcpyDeviceToHost, st));
+        PAT_CUDA(cudaStreamSynchronize(st));
+        lam[op] = sqrt(sqrt(last));  // ||A^T A x|| -> sigma^2
+    }
+    cudaFreeAsync(x, st);
+    cudaFreeAsync(y, st);
+    cudaFreeAsync(acc, st);
+    const double L1 = lam[0], L2 = lam[1];
+    if (!(L1 > 0) || !(L2 > 0)) return fail(PAT_ERR_INVALID_ARG, "pat_reconstruct: zero operator norm");
+    const double tau = 1.0 / L1;
+    out.tau = (float)tau;
+    out.sig_q = (float)(0.99 / (4.0 * tau * L1 * L1));
+    out.sig2 = (float)(0.99 / (4.0 * tau * L2 * L2));
+    return PAT_OK;
+}
+
+}  // namespace pat
+
+using namespace pat;
+
+extern "C" void pat_params_default(pat_params* p) {
+    if (!p) return;
+    memset(p, 0, sizeof *p);
+    p->reg = PAT_TV;
+    p->alpha = 0.05;
+    p->beta = 1.0;
+    p->gamma = 0.95;
+    p->iters = 100;
+    p->tol = 0.0;
+    p->gap_every = 10;
+    p->precond = PAT_PRECOND_DIAG;
+    p->theta = 1.0;
+    p->box_u = 2.0;
+    p->box_v = 4.0;
+}
+
+extern "C" int pat_reconstruct(const pat_geometry* g, const float* f_dev, const pat_params* p, float* u_dev,
+                               pat_info* info, void* stream) {
+    int rc = validate(g, p, "pat_reconstruct");
+    if (rc) return rc;
+    if (!f_dev || !u_dev) return fail(PAT_ERR_INVALID_ARG, "pat_reconstruct: NULL data or output");
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (p->reg) {
+        case PAT_TV: return run_reconstruct<PAT_TV>(g, f_dev, p, u_dev, info, st);
+        case PAT_TGV: return run_reconstruct<PAT_TGV>(g, f_dev, p, u_dev, info, st);
+        default: return run_reconstruct<PAT_DTV>(g, f_dev, p, u_dev, info, st);
+    }
+}
+
+extern "C" int pat_reconstruct_batched(int count, const pat_geometry* const* g, const float* const* f_dev,
+                                       const pat_params* p, float* const* u_dev, pat_info* infos, void* stream) {
+    if (count < 0 || (count > 0 && (!g || !f_dev || !p || !u_dev)))
+        return fail(PAT_ERR_INVALID_ARG, "pat_reconstruct_batched: NULL arrays");
+    for (int i = 0; i < count; ++i) {
+        int rc = pat_reconstruct(g[i], f_dev[i], &p[i], u_dev[i], infos ? &infos[i] : nullptr, stream);
+        if (rc) return rc;
+    }
+    return PAT_OK;
+}
+
+extern "C" int pat_steps(const pat_geometry* g, const pat_params* p, float* sig_q_dev, float* tau_u_dev,
+                         float* sig_r_dev, float* sig_s_dev, float* tau_v_dev, void* stream) {
+    int rc = validate(g, p, "pat_steps");
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = g->desc.n;
+    const long long NN = (long long)N * N, S = (long long)g->desc.n_det * g->desc.n_t;
+    if (p->precond == PAT_PRECOND_SCALAR2) {
+        ScalarSteps sc;
+        rc = scalar2_steps(g, p, sc, st);
+        if (rc) return rc;
+        std::vector<float> h;
+        auto fill = [&](float* dst, long long n, float v) -> int {
+            if (!dst) return PAT_OK;
+            h.assign((size_t)n, v);
+            PAT_CUDA(cudaMemcpyAsync(dst, h.data(), n * 4, cudaMemcpyHostToDevice, st));
+            PAT_CUDA(cudaStreamSynchronize(st));
+            return PAT_OK;
+        };
+        if ((rc = fill(sig_q_dev, S, sc.sig_q))) return rc;
+        if ((rc = fill(tau_u_dev, NN, sc.tau))) return rc;
+        if ((rc = fill(sig_r_dev, NN, sc.sig2))) return rc;
+        if (p->reg == PAT_TGV) {
+            if ((rc = fill(sig_s_dev, NN, sc.sig2))) return rc;
+            if ((rc = fill(tau_v_dev, 2 * NN, sc.tau))) return rc;
+        }
+        return PAT_OK;
+    }
+    rc = ensure_precond(g, st);
+    if (rc) return rc;
+    if (sig_q_dev) {
+        k_sig_q<<<ceil_div(S, 256), 256, 0, st>>>(g->pc.krow, sig_q_dev, S);
+        PAT_LAUNCH_CHECK("k_sig_q");
+    }
+    StepArgs sa{N, p->reg, p->gamma, g->pc.kcol, p->xi_dev, tau_u_dev, sig_r_dev,
+                p->reg == PAT_TGV ? sig_s_dev : nullptr, p->reg == PAT_TGV ? tau_v_dev : nullptr};
+    dim3 blk(32, 8), grd(ceil_div(N, 32), ceil_div(N, 8));
+    k_steps_pixels<<<grd, blk, 0, st>>>(sa);
+    PAT_LAUNCH_CHECK("k_steps_pixels");
+    return PAT_OK;
+}
+
+template <int REG>
+static int gap_impl(const pat_geometry* g, const float* f, const pat_params* p, const float* x, const float* y,
+                    double* out4, cudaStream_t st) {
+    const long long S = (long long)g->desc.n_det * g->desc.n_t;
+    Workspace ws;
+    int rc = alloc_workspace(g, REG, ws, st);
+    if (rc) return rc;
+    InfoDev h{};
+    rc = cudaMemsetAsync(ws.info, 0, sizeof(InfoDev), st) ? PAT_ERR_CUDA : 0;
+    if (!rc) rc = launch_adjoint(g, y, ws.w_pad, true, st);
+    pat_params q = *p;
+    q.tol = 0;
+    if (!rc) rc = launch_gap<REG>(g, &q, ws, x, nullptr, y + S, y, f, nullptr, st);
+    if (!rc) rc = cudaMemcpyAsync(&h, ws.info, sizeof(InfoDev), cudaMemcpyDeviceToHost, st) ? PAT_ERR_CUDA : 0;
+    cudaFreeAsync(ws.base, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    if (!rc && se != cudaSuccess) rc = cuda_fail(se, "pat_duality_gap");
+    if (rc) return rc;
+    out4[0] = h.primal;
+    out4[1] = h.dual;
+    out4[2] = h.gap;
+    out4[3] = h.rel_gap;
+    return PAT_OK;
+}
+
+extern "C" int pat_duality_gap(const pat_geometry* g, const float* f_dev, const pat_params* p, const float* x_dev,
+                               const float* y_dev, double* out4_host, void* stream) {
+    int rc = validate(g, p, "pat_duality_gap");
+    if (rc) return rc;
+    if (!f_dev || !x_dev || !y_dev || !out4_host) return fail(PAT_ERR_INVALID_ARG, "pat_duality_gap: NULL argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    switch (p->reg) {
+        case PAT_TV: return gap_impl<PAT_TV>(g, f_dev, p, x_dev, y_dev, out4_host, st);
+        case PAT_TGV: return gap_impl<PAT_TGV>(g, f_dev, p, x_dev, y_dev, out4_host, st);
+        default: return gap_impl<PAT_DTV>(g, f_dev, p, x_dev, y_dev, out4_host, st);
+    }
+}
+
+__global__ void k_direction_field(int N, const float* __restrict__ w, float eta, float* __restrict__ xi) {
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (gx >= N || gy >= N) return;
+    const int gi = gy * N + gx;
+    const float g0 = gx < N - 1 ? w[gi + 1] - w[gi] : 0.f;
+    const float g1 = gy < N - 1 ? w[gi + N] - w[gi] : 0.f;
+    const float inv = rsqrtf(g0 * g0 + g1 * g1 + eta * eta);
+    xi[gi] = g0 * inv;
+    xi[(size_t)N * N + gi] = g1 * inv;
+}
+
+extern "C" int pat_direction_field(int n, const float* w_dev, double eta, float* xi_dev, void* stream) {
+    if (n < 2 || !w_dev || !xi_dev) return fail(PAT_ERR_INVALID_ARG, "pat_direction_field: bad argument");
+    if (!(eta > 0) || !std::isfinite(eta)) return fail(PAT_ERR_INVALID_ARG, "pat_direction_field: eta must be > 0");
+    dim3 blk(32, 8), grd(ceil_div(n, 32), ceil_div(n, 8));
+    k_direction_field<<<grd, blk, 0, (cudaStream_t)stream>>>(n, w_dev, (float)eta, xi_dev);
+    PAT_LAUNCH_CHECK("k_direction_field");
+    return PAT_OK;
+}

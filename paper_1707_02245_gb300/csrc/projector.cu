@@ -1,0 +1,276 @@
+// Matrix-free circular-mean projector K and its exact transpose K^T (Sec. 3.3.1,
+// Sec. 4.2 eq. (K_def)), plus the fused data-row kernels of the PDHG iteration.
+//
+// Thread mapping: one thread per data row (d, k); a warp holds 32 consecutive radii of
+// one detector and walks the group's angular window m = m_first .. m_first+count-1 in
+// lockstep, so the (cos, sin) pair is a broadcast and the 32 points of one step lie on
+// one ray from the detector (radii dr apart): neighbouring lanes touch neighbouring
+// pixels.  Each point is interpolated bilinearly between pixel centres.
+//
+// The hot path reads a zero-bordered copy of the image ((N+2)^2 floats, pixel (i, j) at
+// (j+1)(N+2) + i+1) so a point with taps i0, j0 in [-1, N-1] needs no per-tap test.
+#include "pat_internal.cuh"
+#include "reduce.cuh"
+
+namespace pat {
+
+template <bool PADDED>
+__device__ __forceinline__ float fetch4(const float* __restrict__ u, int N, const Taps& t, float& v10,
+                                        float& v01, float& v11) {
+    if (PADDED) {
+        const int P = N + 2;
+        const float* p = u + (t.j0 + 1) * P + (t.i0 + 1);
+        v10 = __ldg(p + 1);
+        v01 = __ldg(p + P);
+        v11 = __ldg(p + P + 1);
+        return __ldg(p);
+    } else {
+        const bool x0 = t.i0 >= 0, x1 = t.i0 + 1 < N, y0 = t.j0 >= 0, y1 = t.j0 + 1 < N;
+        const float* p = u + t.j0 * N + t.i0;
+        v10 = (x1 && y0) ? __ldg(p + 1) : 0.f;
+        v01 = (x0 && y1) ? __ldg(p + N) : 0.f;
+        v11 = (x1 && y1) ? __ldg(p + N + 1) : 0.f;
+        return (x0 && y0) ? __ldg(p) : 0.f;
+    }
+}
+
+// Integral of the bilinear image over circle (d, k) with the arc weight applied.
+// All lanes of a warp must share d and k / KGRP (valid = k < T).
+template <bool PADDED>
+__device__ __forceinline__ float circle_integral(const GeomView& g, const float* __restrict__ u, int d, int k,
+                                                 bool valid) {
+    const int2 w = __ldg(&g.win[d * g.n_kgrp + k / KGRP]);
+    const float2 det = __ldg(&g.det[d]);
+    const float r = valid ? __ldg(&g.rk[k]) : 0.f;
+    float acc = 0.f;
+    int m = w.x;
+    for (int j = 0; j < w.y; ++j) {
+        const float2 cs = __ldg(&g.cs[m]);
+        m = (m + 1 == g.quad_m) ? 0 : m + 1;
+        Taps t;
+        if (point_taps(g, det, r, cs, t) && valid) {
+            float v10, v01, v11;
+            const float v00 = fetch4<PADDED>(u, g.n, t, v10, v01, v11);
+            const float a = fmaf(t.ax, v10 - v00, v00);
+            const float b = fmaf(t.ax, v11 - v01, v01);
+            acc += fmaf(t.ay, b - a, a);
+        }
+    }
+    return valid ? acc * __ldg(&g.wk[k]) : 0.f;
+}
+
+// y = K u
+template <bool PADDED>
+__global__ void __launch_bounds__(128) k_forward(GeomView g, const float* __restrict__ u, float* __restrict__ y) {
+    const int d = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = k < g.n_t;
+    const float val = circle_integral<PADDED>(g, u, d, k, valid);
+    if (valid) y[(size_t)d * g.n_t + k] = val;
+}
+
+// q <- prox_{sigma F1*}(q + sigma K ubar) = (q + sigma (K ubar - f)) / (1 + sigma)  (Sec. 3.2)
+__global__ void __launch_bounds__(128) k_forward_prox(GeomView g, const float* __restrict__ ubar_pad,
+                                                      float* __restrict__ q, const float* __restrict__ f,
+                                                      const float* __restrict__ sig_q, float sig_scalar,
+                                                      const int* __restrict__ stop) {
+    if (stop && *(volatile const int*)stop) return;
+    const int d = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = k < g.n_t;
+    const float ku = circle_integral<true>(g, ubar_pad, d, k, valid);
+    if (valid) {
+        const size_t i = (size_t)d * g.n_t + k;
+        const float s = sig_q ? sig_q[i] : sig_scalar;
+        q[i] = (q[i] + s * (ku - f[i])) / (1.f + s);
+    }
+}
+
+// FP64 partial sums for the duality gap over data rows:
+//   {sum (K u - f)^2, sum q^2, sum q f}   one triple per block
+__global__ void __launch_bounds__(128) k_forward_gap(GeomView g, const float* __restrict__ u,
+                                                     const float* __restrict__ q, const float* __restrict__ f,
+                                                     double* __restrict__ partials, const int* __restrict__ stop) {
+    if (stop && *(volatile const int*)stop) return;
+    const int d = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = k < g.n_t;
+    const float ku = circle_integral<false>(g, u, d, k, valid);
+    double a = 0.0, b = 0.0, c = 0.0;
+    if (valid) {
+        const size_t i = (size_t)d * g.n_t + k;
+        const double res = (double)ku - (double)f[i];
+        const double qi = (double)q[i];
+        a = res * res;
+        b = qi * qi;
+        c = qi * (double)f[i];
+    }
+    double3 s = block_sum3(make_double3(a, b, c));
+    if (threadIdx.x == 0) {
+        const int blk = blockIdx.y * gridDim.x + blockIdx.x;
+        partials[3 * blk + 0] = s.x;
+        partials[3 * blk + 1] = s.y;
+        partials[3 * blk + 2] = s.z;
+    }
+}
+
+// out += K^T y by scattering every point's four bilinear weights (float atomics).
+// PADDED: out is the zero-bordered (N+2)^2 layout and border cells collect the taps that
+// fall off the grid (the consumer ignores them); otherwise off-grid taps are dropped.
+template <bool PADDED>
+__global__ void __launch_bounds__(128) k_adjoint_scatter(GeomView g, const float* __restrict__ y,
+                                                         float* __restrict__ out, const int* __restrict__ stop) {
+    if (stop && *(volatile const int*)stop) return;
+    const int d = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = k < g.n_t;
+    const int2 w = __ldg(&g.win[d * g.n_kgrp + k / KGRP]);
+    const float2 det = __ldg(&g.det[d]);
+    const float r = valid ? __ldg(&g.rk[k]) : 0.f;
+    const float c = valid ? __ldg(&y[(size_t)d * g.n_t + k]) * __ldg(&g.wk[k]) : 0.f;
+    const int N = g.n;
+    int m = w.x;
+    for (int j = 0; j < w.y; ++j) {
+        const float2 cs = __ldg(&g.cs[m]);
+        m = (m + 1 == g.quad_m) ? 0 : m + 1;
+        Taps t;
+        if (point_taps(g, det, r, cs, t) && valid && c != 0.f) {
+            const float c0 = c * (1.f - t.ay), c1 = c * t.ay;
+            if (PADDED) {
+                const int P = N + 2;
+                float* p = out + (t.j0 + 1) * P + (t.i0 + 1);
+                atomicAdd(p, c0 * (1.f - t.ax));
+                atomicAdd(p + 1, c0 * t.ax);
+                atomicAdd(p + P, c1 * (1.f - t.ax));
+                atomicAdd(p + P + 1, c1 * t.ax);
+            } else {
+                const bool x0 = t.i0 >= 0, x1 = t.i0 + 1 < N, y0 = t.j0 >= 0, y1 = t.j0 + 1 < N;
+                float* p = out + t.j0 * N + t.i0;
+                if (x0 && y0) atomicAdd(p, c0 * (1.f - t.ax));
+                if (x1 && y0) atomicAdd(p + 1, c0 * t.ax);
+                if (x0 && y1) atomicAdd(p + N, c1 * (1.f - t.ax));
+                if (x1 && y1) atomicAdd(p + N + 1, c1 * t.ax);
+            }
+        }
+    }
+}
+
+// Row sums K 1 (FP64 accumulation) and column sums K^T 1 (FP64 atomics) of the
+// nonnegative matrix K; only on-grid taps count.
+__global__ void __launch_bounds__(128) k_precond_sums(GeomView g, float* __restrict__ krow,
+                                                     double* __restrict__ kcol64) {
+    const int d = blockIdx.y;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const bool valid = k < g.n_t;
+    const int2 w = __ldg(&g.win[d * g.n_kgrp + k / KGRP]);
+    const float2 det = __ldg(&g.det[d]);
+    const float r = valid ? __ldg(&g.rk[k]) : 0.f;
+    const double wk = valid ? (double)__ldg(&g.wk[k]) : 0.0;
+    const int N = g.n;
+    double acc = 0.0;
+    int m = w.x;
+    for (int j = 0; j < w.y; ++j) {
+        const float2 cs = __ldg(&g.cs[m]);
+        m = (m + 1 == g.quad_m) ? 0 : m + 1;
+        Taps t;
+        if (point_taps(g, det, r, cs, t) && valid) {
+            const double ax = t.ax, ay = t.ay;
+            const double wt[4] = {(1 - ax) * (1 - ay), ax * (1 - ay), (1 - ax) * ay, ax * ay};
+            const int di[4] = {0, 1, 0, 1}, dj[4] = {0, 0, 1, 1};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int i = t.i0 + di[c], jj = t.j0 + dj[c];
+                if (i >= 0 && i < N && jj >= 0 && jj < N) {
+                    acc += wt[c];
+                    atomicAdd(&kcol64[jj * N + i], wk * wt[c]);
+                }
+            }
+        }
+    }
+    if (valid) krow[(size_t)d * g.n_t + k] = (float)(acc * wk);
+}
+
+__global__ void k_double_to_float(const double* __restrict__ a, float* __restrict__ b, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+static dim3 row_grid(const pat_geometry* g) {
+    return dim3(ceil_div(g->desc.n_t, 128), g->desc.n_det);
+}
+
+int forward_gap_blocks(const pat_geometry* g) {
+    dim3 gr = row_grid(g);
+    return gr.x * gr.y;
+}
+
+int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y, cudaStream_t st) {
+    if (padded)
+        k_forward<true><<<row_grid(g), 128, 0, st>>>(g->view, u, y);
+    else
+        k_forward<false><<<row_grid(g), 128, 0, st>>>(g->view, u, y);
+    PAT_LAUNCH_CHECK("k_forward");
+    return PAT_OK;
+}
+
+int launch_forward_prox(const pat_geometry* g, const float* ubar_pad, float* q, const float* f,
+                        const float* sig_q, float sig_q_scalar, const int* stop, cudaStream_t st) {
+    k_forward_prox<<<row_grid(g), 128, 0, st>>>(g->view, ubar_pad, q, f, sig_q, sig_q_scalar, stop);
+    PAT_LAUNCH_CHECK("k_forward_prox");
+    return PAT_OK;
+}
+
+int launch_forward_gap(const pat_geometry* g, const float* u, const float* q, const float* f,
+                       double* partials, int n_part, const int* stop, cudaStream_t st) {
+    (void)n_part;
+    k_forward_gap<<<row_grid(g), 128, 0, st>>>(g->view, u, q, f, partials, stop);
+    PAT_LAUNCH_CHECK("k_forward_gap");
+    return PAT_OK;
+}
+
+int launch_adjoint(const pat_geometry* g, const float* y, float* out, bool padded, cudaStream_t st) {
+    const int N = g->desc.n;
+    const size_t cells = padded ? (size_t)(N + 2) * (N + 2) : (size_t)N * N;
+    PAT_CUDA(cudaMemsetAsync(out, 0, cells * sizeof(float), st));
+    if (padded)
+        k_adjoint_scatter<true><<<row_grid(g), 128, 0, st>>>(g->view, y, out, nullptr);
+    else
+        k_adjoint_scatter<false><<<row_grid(g), 128, 0, st>>>(g->view, y, out, nullptr);
+    PAT_LAUNCH_CHECK("k_adjoint_scatter");
+    return PAT_OK;
+}
+
+int ensure_precond(const pat_geometry* gc, cudaStream_t st) {
+    pat_geometry* g = const_cast<pat_geometry*>(gc);
+    std::lock_guard<std::mutex> lock(g->mtx);
+    if (g->pc.ready) return PAT_OK;
+    const int N = g->desc.n;
+    const size_t S = (size_t)g->desc.n_det * g->desc.n_t;
+    if (!g->pc.krow) PAT_CUDA(cudaMalloc(&g->pc.krow, S * sizeof(float)));
+    if (!g->pc.kcol) PAT_CUDA(cudaMalloc(&g->pc.kcol, (size_t)N * N * sizeof(float)));
+    double* tmp = nullptr;
+    PAT_CUDA(cudaMallocAsync(&tmp, (size_t)N * N * sizeof(double), st));
+    PAT_CUDA(cudaMemsetAsync(tmp, 0, (size_t)N * N * sizeof(double), st));
+    k_precond_sums<<<row_grid(g), 128, 0, st>>>(g->view, g->pc.krow, tmp);
+    PAT_LAUNCH_CHECK("k_precond_sums");
+    k_double_to_float<<<ceil_div((long long)N * N, 256), 256, 0, st>>>(tmp, g->pc.kcol, N * N);
+    PAT_LAUNCH_CHECK("k_double_to_float");
+    PAT_CUDA(cudaFreeAsync(tmp, st));
+    PAT_CUDA(cudaStreamSynchronize(st));
+    g->pc.ready = true;
+    return PAT_OK;
+}
+
+}  // namespace pat
+
+using namespace pat;
+
+extern "C" int pat_forward(const pat_geometry* g, const float* u_dev, float* y_dev, void* stream) {
+    if (!g || !u_dev || !y_dev) return fail(PAT_ERR_INVALID_ARG, "pat_forward: NULL argument");
+    return launch_forward(g, u_dev, false, y_dev, (cudaStream_t)stream);
+}
+
+extern "C" int pat_adjoint(const pat_geometry* g, const float* y_dev, float* u_dev, void* stream) {
+    if (!g || !u_dev || !y_dev) return fail(PAT_ERR_INVALID_ARG, "pat_adjoint: NULL argument");
+    return launch_adjoint(g, y_dev, u_dev, false, (cudaStream_t)stream);
+}

@@ -192,13 +192,15 @@ def rasterise_segments(segs: np.ndarray, n: int, supersample: int = 4) -> np.nda
 
 
 def vessel_phantom(n: int, seed: int, n_segments: int = 40, mu: float = 3.0,
-                   supersample: int = 4) -> np.ndarray:
+                   supersample: int = 4, n_ref: int | None = None) -> np.ndarray:
     """Vessel tree times an exponentially decaying fluence exp(-mu * depth).
 
     depth = max(0, 1 - |x|) is the distance inward from the unit circle, so the
-    absorbed energy is largest near the illuminated boundary.
+    absorbed energy is largest near the illuminated boundary.  Vessel widths are
+    1-4 pixels of an ``n_ref`` grid (default ``n``), so the same tree can be
+    rasterised on a finer grid.
     """
-    segs = vessel_segments(seed, n_segments=n_segments, n_pix=n)
+    segs = vessel_segments(seed, n_segments=n_segments, n_pix=n_ref or n)
     mask = rasterise_segments(segs, n, supersample)
     c = pixel_centres(n)
     X, Y = np.meshgrid(c, c)
@@ -257,3 +259,63 @@ def radial_sampling(det_xy: np.ndarray, n_t: int, lo: float = -1.0, hi: float = 
     rmax = float(np.max(np.hypot(det[:, None, 0] - corners[None, :, 0],
                                  det[:, None, 1] - corners[None, :, 1])))
     return 0.0, rmax / n_t
+
+
+# ----------------------------------------------------------------------------
+# workload recipes (sizes, layouts, phantoms, noise draws; no operator applied)
+# ----------------------------------------------------------------------------
+
+def workload(name: str, seed: int = 0) -> dict:
+    """Inputs of a named reconstruction workload.
+
+    Keys: n, det_xy, n_t, r0, dr, quad_m (reconstruction grid), n_fine, quad_m_fine
+    and phantom_fine (data are simulated on a 2x finer grid with 2x the quadrature so
+    the reconstruction does not commit an inverse crime, Sec. 5.2), phantom (at n),
+    noise (standard normal, shape (D, T)), noise_level (std as a fraction of the clean
+    data's maximum), reg / alpha / beta / gamma / iters, and for directional TV the
+    side image ``side`` and ``eta``.
+
+    * ``disc64``:   64^2 image, 64 detectors on a full circle of radius 1.2, 128 time
+      samples, 256 quadrature points, 5 random discs, 1% noise, TV alpha 0.05, 200 its.
+    * ``tgv256``:   256^2 vessel tree with exp(-3 depth) fluence, 256 detectors on the
+      full circle, 512 samples, 5% noise, TGV alpha 0.02 beta 0.04, 1000 iterations.
+    * ``dtv256``:   the tgv256 phantom, 32 of 128 detectors on a 90 degree arc, 512
+      samples, 10% noise, directional TV alpha 0.02, gamma 0.95, 2000 iterations.
+    * ``small``:    a few-second case for tests: 24^2 discs, 12 detectors, 40 samples,
+      64 quadrature points, 2% noise.
+    """
+    if name == "disc64":
+        n, n_det, n_t, m = 64, 64, 128, 256
+        det = detectors_full_circle(n_det, 1.2)
+        discs = disc_params(5, seed)
+        ph = rasterise_discs(discs, n)
+        ph_f = rasterise_discs(discs, 2 * n)
+        out = dict(reg=0, alpha=0.05, beta=1.0, gamma=0.95, iters=200, noise_level=0.01)
+    elif name == "small":
+        n, n_det, n_t, m = 24, 12, 40, 64
+        det = detectors_full_circle(n_det, 1.2)
+        discs = disc_params(3, seed)
+        ph = rasterise_discs(discs, n)
+        ph_f = rasterise_discs(discs, 2 * n)
+        out = dict(reg=0, alpha=0.05, beta=1.0, gamma=0.95, iters=50, noise_level=0.02)
+    elif name in ("tgv256", "dtv256"):
+        n, n_t, m = 256, 512, 256
+        if name == "tgv256":
+            det = detectors_full_circle(256, 1.2)
+            out = dict(reg=1, alpha=0.02, beta=0.04, gamma=0.95, iters=1000, noise_level=0.05)
+        else:
+            det = detectors_limited_arc(128, 32, 90.0, seed + 101, radius=1.2)
+            out = dict(reg=2, alpha=0.02, beta=1.0, gamma=0.95, iters=2000, noise_level=0.10)
+        ph = vessel_phantom(n, seed)
+        ph_f = vessel_phantom(2 * n, seed, n_ref=n)
+    else:
+        raise ValueError(f"unknown workload {name!r}")
+    r0, dr = radial_sampling(det, n_t)
+    out.update(name=name, seed=seed, n=n, det_xy=det, n_t=n_t, r0=r0, dr=dr, quad_m=m,
+               n_fine=2 * n, quad_m_fine=2 * m, phantom=ph, phantom_fine=ph_f,
+               noise=standard_normal((det.shape[0], n_t), seed + 17))
+    if out["reg"] == 2:
+        w = side_image(n, seed)
+        out["side"] = w
+        out["eta"] = 0.01 * float(w.max() - w.min())
+    return out

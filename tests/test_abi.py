@@ -1,0 +1,79 @@
+"""Host-side checks of the C ABI: the in-tree library builds for sm_103a, loads, exports
+every function include/pat.h declares, and reports errors without a GPU call."""
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_1707_02245_gb300 as P
+from paper_1707_02245_gb300 import build as B
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "pat.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(pat_[a-z_0-9]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return P.load()
+
+
+def test_library_is_in_tree(lib):
+    assert os.path.exists(P.library_path())
+    assert os.path.commonpath([P.library_path(), ROOT]) == ROOT
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 13
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(names) == sorted(P.EXPORTED)
+    nm = subprocess.run(["nm", "-D", "--defined-only", P.library_path()], capture_output=True, text=True).stdout
+    for n in names:
+        assert re.search(rf"\bT {n}\b", nm), f"{n} not exported"
+
+
+def test_error_strings_and_defaults(lib):
+    assert P.pat_error_string(0) == "ok"
+    assert "invalid" in P.pat_error_string(P.PAT_ERR_INVALID_ARG)
+    assert "non-finite" in P.pat_error_string(P.PAT_ERR_NONFINITE)
+    p = P.pat_params_default()
+    assert (p.reg, p.iters, p.gap_every, p.precond) == (P.PAT_TV, 100, 10, P.PAT_PRECOND_DIAG)
+    assert (p.alpha, p.beta, p.theta, p.box_u, p.box_v) == (0.05, 1.0, 1.0, 2.0, 4.0)
+
+
+def test_invalid_geometry_rejected_before_any_device_call(lib):
+    with pytest.raises(P.PatError) as ei:
+        P.pat_create_geometry(1, [[0.0, 0.0]], 4, 0.0, 0.1, 16)
+    assert ei.value.code == P.PAT_ERR_INVALID_ARG
+    with pytest.raises(P.PatError):
+        P.pat_create_geometry(8, [[0.0, 0.0]], 4, 0.0, -0.1, 16)
+    with pytest.raises(P.PatError):
+        P.pat_create_geometry(8, [[0.0, 0.0]], 4, 0.0, 0.1, 100000)
+    with pytest.raises(P.PatError):
+        P.pat_create_geometry(8, [[float("nan"), 0.0]], 4, 0.0, 0.1, 16)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    import importlib
+    mod = importlib.import_module("paper_1707_02245_gb300")
+    saved = mod._lib
+    try:
+        mod._lib = None
+        with pytest.raises(RuntimeError, match="not built"):
+            mod.load(str(tmp_path / "nope.so"))
+    finally:
+        mod._lib = saved
+
+
+def test_nvcc_targets_sm103a_only():
+    flags = B.common_flags()
+    assert "arch=compute_103a,code=sm_103a" in flags
+    assert not any("sm_90" in f or "sm_100" in f for f in flags)
