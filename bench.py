@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 PDHG photoacoustic reconstruction.
+
+Metric: PDHG iterations per second of the TGV^2 reconstruction of a 256^2 vessel phantom
+from 256 detectors x 512 time samples (M = 256 quadrature points per circle, alpha 0.02,
+beta 0.04, 1000 iterations per reconstruction, FP64 duality gap every 10 iterations).
+
+One step = one full reconstruction through the C ABI (pat_reconstruct): step sizes,
+initialisation, 1000 PDHG iterations with gap evaluations, output.  Inputs are resident
+in HBM when the step starts; the L2 cache is flushed before every step (a 256 MiB write
+outside the timed events).  Each rank of a multi-GPU run solves its own independent
+problem (weak scaling, no collective on the data path).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gb300|reference]
+
+``--impl reference`` times the FP64 CPU oracle (the reference of this build) on the host
+cores for the same workload and metric, one oracle PDHG iteration per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "PDHG iters/sec (TGV^2 256x256, 256 det x 512 samples)"
+UNIT = "iters/s"
+WORKLOAD_DESC = ("tgv256: TGV^2 PDHG, 256x256 vessel phantom with exp(-3 depth) fluence, 256 detectors on a "
+                 "full circle r=1.2, 512 time samples, M=256, 5% noise, alpha 0.02, beta 0.04, 1000 iterations, "
+                 "diagonal preconditioning, FP64 gap every 10 iterations")
+FLOPS_PER_POINT = 22          # algorithmic FP32 operations of one quadrature point
+SMS, FP32_LANES = 152, 128    # GB300: SMs x FP32 lanes per SM
+
+
+# ---------------------------------------------------------------------------------
+# distributed helpers (host logic; tested with gloo on CPU)
+# ---------------------------------------------------------------------------------
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def init_dist(world: int, backend: str):
+    if world <= 1:
+        return None
+    import torch.distributed as dist
+    if not dist.is_initialized():
+        dist.init_process_group(backend=backend)
+    return dist
+
+
+def barrier(dist, device=None):
+    if dist is not None:
+        if device is not None:
+            dist.barrier(device_ids=[device.index])
+        else:
+            dist.barrier()
+
+
+def aggregate(dist, seconds: float, units: float, device=None) -> tuple[float, float]:
+    """(max seconds over ranks, summed units over ranks)."""
+    if dist is None:
+        return seconds, units
+    import torch
+    t = torch.tensor([seconds], dtype=torch.float64, device=device)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+# ---------------------------------------------------------------------------------
+# clocks sampler
+# ---------------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+        self._t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self._t = threading.Thread(target=self._read, daemon=True)
+        self._t.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self._t:
+            self._t.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------------
+
+def oracle_setup(workload: str, seed: int):
+    """Oracle problem for the workload (data simulated with the oracle on the same grid)."""
+    import numpy as np
+
+    import synthetic as S
+    from oracle import pat_oracle as O
+    w = S.workload(workload, seed)
+    g = O.Geometry(n=w["n"], det_xy=w["det_xy"], n_t=w["n_t"], r0=w["r0"], dr=w["dr"], quad_m=w["quad_m"])
+    clean = O.forward(g, w["phantom"])
+    f = clean + w["noise_level"] * np.abs(clean).max() * w["noise"]
+    n = g.n
+    xi = O.direction_field(w["side"], w["eta"]) if w["reg"] == O.REG_DTV else None
+    pb = O.Problem(n=n, K=lambda u: O.forward(g, u).ravel(), KT=lambda y: O.adjoint(g, y), f=f, reg=w["reg"],
+                   alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"], xi=xi,
+                   k_abs_rows=O.forward(g, np.ones((n, n))).ravel(), k_abs_cols=O.adjoint(g, np.ones((g.n_det, g.n_t))))
+    return pb, O.diag_steps(pb)
+
+
+def oracle_iters_per_s(pb, steps, iters: int) -> tuple[float, float]:
+    from oracle import pat_oracle as O
+    t0 = time.perf_counter()
+    O.pdhg(pb, iters, steps=steps, gap_every=0, final_gap=False)
+    dt = time.perf_counter() - t0
+    return iters / dt, dt
+
+
+def cpu_threads_used() -> int:
+    # the oracle is numpy element-wise code (no BLAS-threaded calls on its hot path)
+    return 1
+
+
+# ---------------------------------------------------------------------------------
+# reference arm
+# ---------------------------------------------------------------------------------
+
+def run_reference(args) -> int:
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    pb, st = oracle_setup(args.workload, seed=0)
+    for _ in range(args.warmup):
+        oracle_iters_per_s(pb, st, 1)
+    times = []
+    for _ in range(args.steps):
+        _, dt = oracle_iters_per_s(pb, st, 1)
+        times.append(dt)
+    total = sum(times)
+    value = args.steps / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "iters_per_step": 1},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads_used(), "kind": "oracle",
+                             "sample": "one FP64 oracle PDHG iteration of the tgv256 workload per step "
+                                       "(matrix-free numpy K and K^T)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------------
+# GB300 arm
+# ---------------------------------------------------------------------------------
+
+def run_gb300(args) -> int:
+    import numpy as np
+    import torch
+
+    import __graft_entry__
+    import paper_1707_02245_gb300 as P
+    import synthetic as S
+
+    rank, world, local = dist_env()
+    if not torch.cuda.is_available():
+        raise RuntimeError("bench.py needs a CUDA GPU")
+    device = torch.device("cuda", local)
+    torch.cuda.set_device(device)
+    dist = init_dist(world, "nccl")
+    __graft_entry__.build()
+    stream = torch.cuda.current_stream(device)
+
+    # ---- inputs (seeded; each rank solves its own problem) ----
+    w = S.workload(args.workload, seed=rank)
+    n = w["n"]
+    fine = P.Geometry(w["n_fine"], w["det_xy"], w["n_t"], w["r0"], w["dr"], w["quad_m_fine"])
+    ph_f = torch.from_numpy(w["phantom_fine"].astype(np.float32)).to(device)
+    clean = torch.empty(w["det_xy"].shape[0], w["n_t"], device=device)
+    P.pat_forward(fine.handle, ph_f, clean, stream)
+    noise = torch.from_numpy(w["noise"].astype(np.float32)).to(device)
+    f = (clean + w["noise_level"] * clean.abs().max() * noise).contiguous()
+    fine.close()
+    geo = P.Geometry(n, w["det_xy"], w["n_t"], w["r0"], w["dr"], w["quad_m"])
+    ginfo = geo.info()
+    xi = None
+    if w["reg"] == P.PAT_DTV:
+        side = torch.from_numpy(w["side"].astype(np.float32)).to(device)
+        xi = torch.empty(2, n, n, device=device)
+        P.pat_direction_field(n, side, w["eta"], xi, stream)
+    u = torch.empty(n, n, device=device)
+    iters = args.iters or w["iters"]
+    prm = P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"], xi=xi,
+                        iters=iters, gap_every=10, tol=0.0)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
+
+    def step():
+        return P.pat_reconstruct(geo.handle, f, prm, u, stream)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize(device)
+
+    # ---- timed region: K steps, per-step CUDA events, per-phase profiling on ----
+    sampler = ClockSampler(device.index if "CUDA_VISIBLE_DEVICES" not in os.environ else local)
+    barrier(dist, device)
+    torch.cuda.synchronize(device)
+    sampler.start()
+    P.pat_profile_read(reset=True)
+    P.pat_profile_enable(True)
+    launches0 = P.pat_kernel_launches()
+    step_ms, infos = [], []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos.append(step())
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize(device)
+    wall = time.perf_counter() - wall0
+    launches = P.pat_kernel_launches() - launches0
+    P.pat_profile_enable(False)
+    prof = P.pat_profile_read(reset=True)
+    barrier(dist, device)
+    clocks = sampler.stop()
+
+    local_s = sum(step_ms) / 1e3
+    max_s, units = aggregate(dist, local_s, float(iters * args.steps), device)
+    value = units / max_s
+
+    # ---- end to end through the public call with host buffers ----
+    f_host = f.cpu().pin_memory()
+    u_host = torch.empty(n, n).pin_memory()
+    f_dev = torch.empty_like(f)
+    prm_e2e = P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"], xi=xi,
+                            iters=iters, gap_every=10, tol=0.0)
+    e2e_ms = []
+    e2e_steps = 0 if args.no_e2e else max(1, min(args.steps, 5))
+    for _ in range(e2e_steps + 1 if e2e_steps else 0):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        f_dev.copy_(f_host, non_blocking=True)
+        P.pat_reconstruct(geo.handle, f_dev, prm_e2e, u, stream)
+        u_host.copy_(u, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_ms.append(e0.elapsed_time(e1))
+    e2e = None
+    if e2e_steps:
+        e2e_ms = e2e_ms[1:]
+        e2e_s, e2e_units = aggregate(dist, sum(e2e_ms) / 1e3, float(iters * e2e_steps), device)
+        e2e = {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": f.numel() * 4,
+               "d2h_bytes_per_step": u.numel() * 4, "steps": e2e_steps}
+
+    # ---- time to relative gap 1e-4 (cold start) ----
+    ttg = None
+    if not args.no_ttg:
+        prm_t = P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"], xi=xi,
+                              iters=args.ttg_max_iters, gap_every=10, tol=1e-4)
+        flush.zero_()
+        info = P.pat_reconstruct(geo.handle, f, prm_t, u, stream)
+        ttg = {"tol": 1e-4, "iters": info["iters_done"], "seconds": info["ms"] / 1e3,
+               "rel_gap": info["rel_gap"], "reached": info["status"] == P.PAT_STATUS_CONVERGED,
+               "max_iters": args.ttg_max_iters}
+
+    # ---- roofline of the dominant phase ----
+    NN = n * n
+    S_ = f.numel()
+    pts = ginfo["points_on_grid"]
+    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    peaks = load_peaks()
+    fp32_peak = SMS * FP32_LANES * 2 * 2070e6 / 1e12       # TFLOP/s at the maximum SM clock
+    per_pixel_floats = {0: 8, 1: 18, 2: 10}[w["reg"]]
+    phases = {}
+    for ph, (ms, cnt) in prof.items():
+        if cnt == 0:
+            continue
+        avg_s = ms / cnt / 1e3
+        ent = {"launches": cnt, "avg_us": avg_s * 1e6, "share": None}
+        if ph in ("forward_prox", "adjoint"):
+            tflops = FLOPS_PER_POINT * pts / avg_s / 1e12
+            ent.update(bound="alu", achieved=tflops, peak=fp32_peak, unit="TFLOP/s", frac=tflops / fp32_peak,
+                       points_per_s=pts / avg_s)
+        elif ph == "update":
+            gbs = 4.0 * per_pixel_floats * NN / avg_s / 1e9
+            ent.update(bound="hbm", achieved=gbs, peak=peaks["hbm_gbs"], unit="GB/s", frac=gbs / peaks["hbm_gbs"])
+        phases[ph] = ent
+    tot = sum(v["avg_us"] * v["launches"] for v in phases.values())
+    for v in phases.values():
+        v["share"] = v["avg_us"] * v["launches"] / tot if tot else None
+    dom_name = max(phases, key=lambda k: phases[k]["share"] if k in ("forward_prox", "adjoint", "update") else -1)
+    dom = phases[dom_name]
+    roofline = {"kernel": dom_name, "bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
+                "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
+                "peak_source": "FP32 152 SMs x 128 lanes x 2 x 2070 MHz" if dom["bound"] == "alu"
+                else peaks["source"]}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        pb, st = oracle_setup(args.workload, seed=0)
+        it_s, dt = oracle_iters_per_s(pb, st, args.cpu_iters)
+        cpu = {"value": it_s, "unit": UNIT, "cores": cpu_threads_used(), "kind": "oracle",
+               "sample": f"{args.cpu_iters} FP64 oracle PDHG iteration(s) of the same workload "
+                         f"({dt:.1f} s; setup untimed)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * max_s / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD_DESC, "iters_per_step": iters, "parallelism": f"replicas{world}",
+                           "l2": "flushed before every step (256 MiB write outside the timed events)",
+                           "points_on_grid_per_K": pts, "final_rel_gap": infos[-1]["rel_gap"]},
+                "roofline": roofline, "phases": phases, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks, "time_to_gap": ttg,
+                "wall_s_timed": wall}
+        print(json.dumps(line), flush=True)
+    geo.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def load_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            pk = json.load(fh)
+        return {"hbm_gbs": float(pk["hbm_gbs"]), "bf16_tflops": float(pk["bf16_tflops"]),
+                "source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
+    except (OSError, KeyError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback (profiling recipe)"}
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    ap.add_argument("--workload", default="tgv256")
+    ap.add_argument("--cpu-iters", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-ttg", action="store_true")
+    ap.add_argument("--ttg-max-iters", type=int, default=30000)
+    ap.add_argument("--iters", type=int, default=0,
+                    help="override the PDHG iterations per step (short runs for the ncu launch list)")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gb300(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

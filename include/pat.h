@@ -163,10 +163,28 @@ int  pat_duality_gap(const pat_geometry* g, const float* f_dev, const pat_params
                      const float* x_dev, const float* y_dev, double* out4_host, void* stream);
 
 /* ---- diagnostics ------------------------------------------------------------------ */
+/* Phases of one PDHG iteration timed by the optional profiler (CUDA events recorded
+ * around each launch on the caller's stream; the events add a few microseconds of host
+ * work per launch and nothing between kernels on the device). */
+#define PAT_PHASE_FORWARD_PROX 0   /* K ubar and the q prox                          */
+#define PAT_PHASE_ADJ_CLEAR    1   /* zeroing the K^T q accumulator                  */
+#define PAT_PHASE_ADJOINT      2   /* K^T q                                          */
+#define PAT_PHASE_UPDATE       3   /* fused primal step, extrapolation, dual step    */
+#define PAT_PHASE_GAP          4   /* FP64 duality gap and residual                  */
+#define PAT_NPHASES            5
+/* Turns per-phase timing of pat_reconstruct on (1) or off (0) for the whole process. */
+int  pat_profile_enable(int on);
+/* ms_host[PAT_NPHASES]: summed device milliseconds per phase; launches_host[PAT_NPHASES]:
+ * number of timed launches per phase (either may be NULL).  reset != 0 clears the sums. */
+int  pat_profile_read(double* ms_host, long long* launches_host, int reset);
+/* Number of kernels this library has launched in the process so far. */
+long long pat_kernel_launches(void);
+
 const char* pat_error_string(int code);
 const char* pat_last_error(void);
 /* Geometry sizes: out6 = {N, D, T, M, number of quadrature points evaluated per K
- * application (inside the angular windows), 0}. */
+ * application (inside the angular windows), number of quadrature points whose
+ * bilinear taps touch the grid (the algorithmic work of one K or K^T)}. */
 int  pat_geometry_info(const pat_geometry* g, long long* out6_host);
 
 #ifdef __cplusplus

@@ -544,12 +544,13 @@ class Result:
 
 def pdhg(pb: Problem, iters: int, steps: Optional[Steps] = None, theta: float = 1.0,
          tol: float = 0.0, gap_every: int = 0, x0: Optional[dict] = None,
-         y0: Optional[dict] = None, xbar0: Optional[dict] = None) -> Result:
+         y0: Optional[dict] = None, xbar0: Optional[dict] = None, final_gap: bool = True) -> Result:
     """Preconditioned PDHGM, one iteration per step of Algorithm 1 / Algorithm 2.
 
     Iterates start at zero (the initialisation of Algorithms 1 and 2) unless
     ``x0`` = {u, v} / ``y0`` = {q, r, s} are given; the extrapolated point starts at
-    ``xbar0`` = {u, v} if given, else at x^0.  When ``gap_every`` > 0 the gap is evaluated after every
+    ``xbar0`` = {u, v} if given, else at x^0.  ``final_gap`` = False skips the gap
+    evaluation after the last iteration when ``gap_every`` does not ask for it.  When ``gap_every`` > 0 the gap is evaluated after every
     ``gap_every``-th iteration (and after the last one); with ``tol`` > 0 the loop stops
     at the first evaluation with rel_gap <= tol.
     """
@@ -600,7 +601,7 @@ def pdhg(pb: Problem, iters: int, steps: Optional[Steps] = None, theta: float = 
         if tgv:
             v = v_new
         done = it + 1
-        check = (gap_every > 0 and done % gap_every == 0) or done == iters
+        check = (gap_every > 0 and done % gap_every == 0) or (final_gap and done == iters)
         if check:
             gp = duality_gap(pb, u, q, r, v, s, KTq=KTq)
             res = residual([u] + ([v] if tgv else []), x_old)

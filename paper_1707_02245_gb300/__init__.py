@@ -33,7 +33,9 @@ EXPORTED = [
     "pat_create_geometry", "pat_destroy_geometry", "pat_forward", "pat_adjoint",
     "pat_direction_field", "pat_params_default", "pat_reconstruct", "pat_reconstruct_batched",
     "pat_steps", "pat_duality_gap", "pat_error_string", "pat_last_error", "pat_geometry_info",
+    "pat_profile_enable", "pat_profile_read", "pat_kernel_launches",
 ]
+PHASES = ["forward_prox", "adj_clear", "adjoint", "update", "gap"]
 
 
 class PatError(RuntimeError):
@@ -100,6 +102,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pat_error_string": (ctypes.c_char_p, [i]),
         "pat_last_error": (ctypes.c_char_p, []),
         "pat_geometry_info": (i, [vp, ctypes.POINTER(ctypes.c_longlong)]),
+        "pat_profile_enable": (i, [i]),
+        "pat_profile_read": (i, [ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong), i]),
+        "pat_kernel_launches": (ctypes.c_longlong, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -217,7 +222,8 @@ def pat_duality_gap(g: int, f_dev, params: pat_params, x_dev, y_dev, stream=None
 def pat_geometry_info(g: int) -> dict:
     out = (ctypes.c_longlong * 6)()
     _check(load().pat_geometry_info(g, out), "pat_geometry_info")
-    return {"n": out[0], "n_det": out[1], "n_t": out[2], "quad_m": out[3], "points_per_apply": out[4]}
+    return {"n": out[0], "n_det": out[1], "n_t": out[2], "quad_m": out[3], "points_per_apply": out[4],
+            "points_on_grid": out[5]}
 
 
 def pat_error_string(code: int) -> str:
@@ -226,6 +232,21 @@ def pat_error_string(code: int) -> str:
 
 def pat_last_error() -> str:
     return load().pat_last_error().decode(errors="replace")
+
+
+def pat_profile_enable(on: bool) -> None:
+    _check(load().pat_profile_enable(1 if on else 0), "pat_profile_enable")
+
+
+def pat_profile_read(reset: bool = False) -> dict:
+    ms = (ctypes.c_double * len(PHASES))()
+    cnt = (ctypes.c_longlong * len(PHASES))()
+    _check(load().pat_profile_read(ms, cnt, 1 if reset else 0), "pat_profile_read")
+    return {ph: (ms[i], cnt[i]) for i, ph in enumerate(PHASES)}
+
+
+def pat_kernel_launches() -> int:
+    return int(load().pat_kernel_launches())
 
 
 # ---- a small owner of a geometry handle -----------------------------------------

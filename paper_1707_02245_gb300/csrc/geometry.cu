@@ -9,6 +9,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstring>
 #include <vector>
 
@@ -30,9 +31,96 @@ int cuda_fail(cudaError_t e, const char* what) {
     return e == cudaErrorMemoryAllocation ? PAT_ERR_OOM : PAT_ERR_CUDA;
 }
 
+static std::atomic<long long> g_launches{0};
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ---- profiler --------------------------------------------------------------------
+static std::atomic<bool> g_prof{false};
+static std::mutex g_prof_mtx;
+static double g_prof_ms[PAT_NPHASES];
+static long long g_prof_n[PAT_NPHASES];
+
+struct PendingMark {
+    int phase;
+    cudaEvent_t e0, e1;
+};
+static thread_local std::vector<cudaEvent_t> t_pool;
+static thread_local std::vector<PendingMark> t_pending;
+static thread_local size_t t_pool_used = 0;
+
+static cudaEvent_t pool_event() {
+    if (t_pool_used == t_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        t_pool.push_back(e);
+    }
+    return t_pool[t_pool_used++];
+}
+
+bool prof_on() { return g_prof.load(std::memory_order_relaxed); }
+
+void prof_mark(int phase, cudaStream_t st, bool begin) {
+    if (!prof_on()) return;
+    cudaEvent_t e = pool_event();
+    if (!e) return;
+    cudaEventRecord(e, st);
+    if (begin) {
+        t_pending.push_back({phase, e, nullptr});
+    } else {
+        for (auto it = t_pending.rbegin(); it != t_pending.rend(); ++it)
+            if (it->phase == phase && it->e1 == nullptr) {
+                it->e1 = e;
+                break;
+            }
+    }
+}
+
+void prof_collect() {
+    if (t_pending.empty()) {
+        t_pool_used = 0;
+        return;
+    }
+    double ms[PAT_NPHASES] = {0};
+    long long n[PAT_NPHASES] = {0};
+    for (auto& m : t_pending) {
+        float t = 0.f;
+        if (m.e1 && cudaEventElapsedTime(&t, m.e0, m.e1) == cudaSuccess) {
+            ms[m.phase] += t;
+            n[m.phase] += 1;
+        }
+    }
+    t_pending.clear();
+    t_pool_used = 0;
+    std::lock_guard<std::mutex> lock(g_prof_mtx);
+    for (int i = 0; i < PAT_NPHASES; ++i) {
+        g_prof_ms[i] += ms[i];
+        g_prof_n[i] += n[i];
+    }
+}
+
 }  // namespace pat
 
 using namespace pat;
+
+extern "C" int pat_profile_enable(int on) {
+    g_prof.store(on != 0);
+    return PAT_OK;
+}
+
+extern "C" int pat_profile_read(double* ms_host, long long* launches_host, int reset) {
+    std::lock_guard<std::mutex> lock(g_prof_mtx);
+    for (int i = 0; i < PAT_NPHASES; ++i) {
+        if (ms_host) ms_host[i] = g_prof_ms[i];
+        if (launches_host) launches_host[i] = g_prof_n[i];
+        if (reset) {
+            g_prof_ms[i] = 0;
+            g_prof_n[i] = 0;
+        }
+    }
+    return PAT_OK;
+}
+
+extern "C" long long pat_kernel_launches(void) { return g_launches.load(); }
 
 extern "C" const char* pat_error_string(int code) {
     switch (code) {
@@ -141,7 +229,8 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     const double yl = d.ymin - 0.5 * hy - ey, yh = d.ymax + 0.5 * hy + ey;
     std::vector<int2> win((size_t)D * n_kgrp);
     std::vector<unsigned char> mask(M);
-    long long pts = 0;
+    long long pts = 0, on_grid = 0;
+    const double gxl = d.xmin - 0.5 * hx, gxh = d.xmax + 0.5 * hx, gyl = d.ymin - 0.5 * hy, gyh = d.ymax + 0.5 * hy;
     for (int di = 0; di < D; ++di) {
         const double dx = d.det_xy_host[2 * di], dy = d.det_xy_host[2 * di + 1];
         for (int gi = 0; gi < n_kgrp; ++gi) {
@@ -156,9 +245,9 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
                                              std::max(hypot(dx - xl, dy - yh), hypot(dx - xh, dy - yh)));
                 if (r < dmin - 1e-9 || r > dmax + 1e-9) continue;
                 for (int m = 0; m < M; ++m) {
-                    if (mask[m]) continue;
                     const double x = dx + r * cosd[m], y = dy + r * sind[m];
-                    if (x > xl && x < xh && y > yl && y < yh) mask[m] = 1;
+                    if (x > gxl && x < gxh && y > gyl && y < gyh) ++on_grid;  // touches the grid
+                    if (!mask[m] && x > xl && x < xh && y > yl && y < yh) mask[m] = 1;
                 }
             }
             int2 w = covering_window(mask, M);
@@ -167,6 +256,7 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
         }
     }
     g->points_per_apply = pts;
+    g->points_on_grid = on_grid;
 
     cudaError_t e = cudaSuccess;
     e = cudaMalloc(&g->det, sizeof(float2) * D);
@@ -223,6 +313,6 @@ extern "C" int pat_geometry_info(const pat_geometry* g, long long* out6) {
     out6[2] = g->desc.n_t;
     out6[3] = g->desc.quad_m;
     out6[4] = g->points_per_apply;
-    out6[5] = 0;
+    out6[5] = g->points_on_grid;
     return PAT_OK;
 }

@@ -25,11 +25,22 @@ int cuda_fail(cudaError_t e, const char* what);
         if (e_ != cudaSuccess) return ::pat::cuda_fail(e_, #call);  \
     } while (0)
 
+void count_launch();
+
+// Every kernel launch of the library is followed by this check, which also counts it.
 #define PAT_LAUNCH_CHECK(what)                                      \
     do {                                                            \
+        ::pat::count_launch();                                      \
         cudaError_t e_ = cudaGetLastError();                        \
         if (e_ != cudaSuccess) return ::pat::cuda_fail(e_, what);   \
     } while (0)
+
+// Optional per-phase timing: marks record a CUDA event pair around a phase when the
+// profiler is on; prof_collect() (after the stream has synchronised) adds the elapsed
+// times to the process-wide sums.
+bool prof_on();
+void prof_mark(int phase, cudaStream_t st, bool begin);
+void prof_collect();
 
 // ---------------------------------------------------------------------------------
 // device view of a geometry (passed by value to kernels)
@@ -62,7 +73,8 @@ struct PrecondCache {
 struct pat_geometry {
     pat_geometry_desc desc;
     int device = 0;
-    long long points_per_apply = 0;   // quadrature points inside the windows
+    long long points_per_apply = 0;   // quadrature points inside the windows (evaluated)
+    long long points_on_grid = 0;     // quadrature points whose taps touch the grid
     // device tables
     float2* det = nullptr;
     float2* cs = nullptr;
@@ -110,6 +122,7 @@ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 int ensure_precond(const pat_geometry* g, cudaStream_t st);
 int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y, cudaStream_t st);
 int launch_adjoint(const pat_geometry* g, const float* y, float* out, bool padded, cudaStream_t st);
+int launch_adjoint_phases(const pat_geometry* g, const float* y, float* out_pad, const int* stop, cudaStream_t st);
 int launch_forward_prox(const pat_geometry* g, const float* ubar_pad, float* q, const float* f,
                         const float* sig_q, float sig_q_scalar, const int* stop, cudaStream_t st);
 int launch_forward_gap(const pat_geometry* g, const float* u, const float* q, const float* f,

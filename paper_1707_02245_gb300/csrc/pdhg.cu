@@ -703,16 +703,22 @@ static int enqueue_iterations(const pat_geometry* g, const float* f, const pat_p
                               const ScalarSteps& sc, int it0, int count, cudaStream_t st) {
     const int* stop = &ws.info->stop;
     for (int it = it0; it < it0 + count; ++it) {
+        prof_mark(PAT_PHASE_FORWARD_PROX, st, true);
         int rc = launch_forward_prox(g, ws.ubar_pad, ws.q, f, sc.sig_q >= 0 ? nullptr : ws.sig_q, sc.sig_q, stop, st);
         if (rc) return rc;
-        rc = launch_adjoint(g, ws.q, ws.w_pad, true, st);
+        prof_mark(PAT_PHASE_FORWARD_PROX, st, false);
+        rc = launch_adjoint_phases(g, ws.q, ws.w_pad, stop, st);
         if (rc) return rc;
+        prof_mark(PAT_PHASE_UPDATE, st, true);
         rc = launch_update<REG>(g, p, ws, sc, it, st);
         if (rc) return rc;
+        prof_mark(PAT_PHASE_UPDATE, st, false);
         const int done = it + 1;
         if ((p->gap_every > 0 && done % p->gap_every == 0) || done == p->iters) {
+            prof_mark(PAT_PHASE_GAP, st, true);
             rc = launch_gap<REG>(g, p, ws, ws.X[done & 1], ws.X[it & 1], ws.Y[it & 1], ws.q, f, stop, st);
             if (rc) return rc;
+            prof_mark(PAT_PHASE_GAP, st, false);
         }
     }
     return PAT_OK;
@@ -756,6 +762,7 @@ static int run_reconstruct(const pat_geometry* g, const float* f, const pat_para
         const float* xb = p->xbar0_dev ? p->xbar0_dev : p->x0_dev;
         dim3 blk(32, 8), grd(ceil_div(N + 2, 32), ceil_div(N + 2, 8));
         k_pad<<<grd, blk, 0, st>>>(xb, ws.ubar_pad, N);
+        count_launch();
         if (REG == PAT_TGV) {
             if (xb)
                 cudaMemcpyAsync(ws.vbar0, xb + NN, 2 * NN * 4, cudaMemcpyDeviceToDevice, st);
@@ -767,6 +774,7 @@ static int run_reconstruct(const pat_geometry* g, const float* f, const pat_para
                     p->xi_dev, ws.ubar_pad, ws.vbar0, ws.Y[1], ws.Y[0]};
         dim3 g2(ceil_div(N, 32), ceil_div(N, 8));
         k_dual_step<REG><<<g2, blk, 0, st>>>(da);
+        count_launch();
         rc = cudaGetLastError() ? PAT_ERR_CUDA : 0;
     }
     if (!rc && p->iters > 0) rc = enqueue_iterations<REG>(g, f, p, ws, sc, 0, p->iters, st);
@@ -788,6 +796,7 @@ static int run_reconstruct(const pat_geometry* g, const float* f, const pat_para
         oa.xbar_out = p->xbar_out_dev;
         oa.y_out = p->y_out_dev;
         k_output<<<std::min(2 * 152, ceil_div((long long)(nx + ny + S), 256)), 256, 0, st>>>(oa);
+        count_launch();
         rc = cudaGetLastError() ? PAT_ERR_CUDA : 0;
     }
     InfoDev hinfo{};
@@ -798,6 +807,7 @@ static int run_reconstruct(const pat_geometry* g, const float* f, const pat_para
     if (!rc && se != cudaSuccess) rc = cuda_fail(se, "pat_reconstruct: stream synchronize");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
+    prof_collect();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) {
@@ -925,10 +935,10 @@ int scalar2_steps(const pat_geometry* g, const pat_params* p, ScalarSteps& out, 
     double lam[2] = {0, 0};
     for (int op = 0; op < 2; ++op) {
         const long long n = op == 0 ? NN : nx;
-        k_power_start<<<ceil_div(n, 256), 256, 0, st>>>(x, n);
+        k_power_start<<<ceil_div(n, 256), 256, 0, st>>>(x, n); count_launch();
         double* a0 = acc + op * 2 * kPowerIters;
-        k_norm2<<<nb, 256, 0, st>>>(x, n, a0);
-        k_scale<<<nb, 256, 0, st>>>(x, n, a0, nullptr);
+        k_norm2<<<nb, 256, 0, st>>>(x, n, a0); count_launch();
+        k_scale<<<nb, 256, 0, st>>>(x, n, a0, nullptr); count_launch();
         for (int it = 0; it < kPowerIters; ++it) {
             if (op == 0) {
                 int rc = launch_forward(g, x, false, y, st);
@@ -936,12 +946,12 @@ int scalar2_steps(const pat_geometry* g, const pat_params* p, ScalarSteps& out, 
                 rc = launch_adjoint(g, y, x, false, st);
                 if (rc) return rc;
             } else {
-                k_apply_B<<<grd, blk, 0, st>>>(N, p->reg, (float)p->gamma, p->xi_dev, x, y);
-                k_apply_BT<<<grd, blk, 0, st>>>(N, p->reg, (float)p->gamma, p->xi_dev, y, x);
+                k_apply_B<<<grd, blk, 0, st>>>(N, p->reg, (float)p->gamma, p->xi_dev, x, y); count_launch();
+                k_apply_BT<<<grd, blk, 0, st>>>(N, p->reg, (float)p->gamma, p->xi_dev, y, x); count_launch();
             }
             double* slot = a0 + 1 + it;
-            k_norm2<<<nb, 256, 0, st>>>(x, n, slot);
-            k_scale<<<nb, 256, 0, st>>>(x, n, slot, nullptr);
+            k_norm2<<<nb, 256, 0, st>>>(x, n, slot); count_launch();
+            k_scale<<<nb, 256, 0, st>>>(x, n, slot, nullptr); count_launch();
         }
         PAT_LAUNCH_CHECK("power iteration");
         double last = 0;

@@ -240,6 +240,19 @@ int launch_adjoint(const pat_geometry* g, const float* y, float* out, bool padde
     return PAT_OK;
 }
 
+// Hot-path K^T q into the zero-bordered accumulator, as two profiled phases.
+int launch_adjoint_phases(const pat_geometry* g, const float* y, float* out_pad, const int* stop, cudaStream_t st) {
+    const int N = g->desc.n;
+    prof_mark(PAT_PHASE_ADJ_CLEAR, st, true);
+    PAT_CUDA(cudaMemsetAsync(out_pad, 0, (size_t)(N + 2) * (N + 2) * sizeof(float), st));
+    prof_mark(PAT_PHASE_ADJ_CLEAR, st, false);
+    prof_mark(PAT_PHASE_ADJOINT, st, true);
+    k_adjoint_scatter<true><<<row_grid(g), 128, 0, st>>>(g->view, y, out_pad, stop);
+    PAT_LAUNCH_CHECK("k_adjoint_scatter");
+    prof_mark(PAT_PHASE_ADJOINT, st, false);
+    return PAT_OK;
+}
+
 int ensure_precond(const pat_geometry* gc, cudaStream_t st) {
     pat_geometry* g = const_cast<pat_geometry*>(gc);
     std::lock_guard<std::mutex> lock(g->mtx);

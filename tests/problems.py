@@ -29,6 +29,9 @@ def make(name, seed=0, **over):
     w.update(over)
     w["f"] = noisy_data(w)
     if w["reg"] == O.REG_DTV:
+        if "side" not in w:
+            w["side"] = S.side_image(w["n"], seed)
+            w["eta"] = 0.01 * float(w["side"].max() - w["side"].min())
         w["xi"] = direction_field32(w)
     return w
 
