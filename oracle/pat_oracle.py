@@ -38,9 +38,10 @@ R4  F1 is the squared half norm (the square is missing in eq. (PD_TV), present i
     eq. (conj_F1)).
 R5  Steps (default): Pock-Chambolle diagonal preconditioning with alpha = 1 on the
     stacked operator A: tau_j = 1 / sum_i |A_ij|, sigma_i = 1 / sum_j |A_ij|.  Dual
-    variables that are projected as a pointwise group (r, s) take the smallest sigma of
-    the group, so the Sigma-weighted prox stays a Euclidean projection; a zero row takes
-    sigma = 1 (any positive value is admissible there).
+    variables that are projected as a pointwise group (r, s) share one sigma, the
+    largest admissible for all rows of the group, 1 / (max row sum of the group), so
+    the Sigma-weighted prox stays a Euclidean projection.  A zero row imposes no bound
+    (any positive sigma is admissible there); an all-zero group or row takes sigma = 1.
 R6  theta = 1 (PDHGM).
 R7  Duality gap: with G = 0 the paper's D^n is +infinity unless A^T y = 0 exactly, so
     the gap is taken on the box |u| <= U, |v| <= V:  gap = P(x) - D_B(y) with
@@ -410,7 +411,7 @@ def diag_steps(pb: Problem) -> Steps:
 
     sigma_i = 1 / sum_j |A_ij| and tau_j = 1 / sum_i |A_ij| for the stacked
     A = (K; B) with B from ``regulariser_operator``.  Pointwise groups (r: 2 rows,
-    s: 3 rows at one pixel) share the group's smallest sigma.
+    s: 3 rows at one pixel) share sigma = 1 / (largest row sum in the group).
     """
     n2 = pb.n * pb.n
     B = abs(regulariser_operator(pb))
@@ -423,11 +424,16 @@ def diag_steps(pb: Problem) -> Steps:
         x = np.asarray(x, dtype=np.float64)
         return np.where(x > 0, 1.0 / np.where(x > 0, x, 1.0), 1.0)
 
+    def group_sigma(sums):
+        # largest sigma admissible for every row of the group: 1 / max row sum; rows
+        # whose sum is zero impose no bound (1 when the whole group is zero)
+        return inv(np.max(sums, axis=0))
+
     sig_q = inv(krow)
     g = 2 if pb.reg != REG_TGV else 5
-    rows = inv(b_rows).reshape(g, pb.n, pb.n)
-    sig_r = np.min(rows[0:2], axis=0)
-    sig_s = np.min(rows[2:5], axis=0) if pb.reg == REG_TGV else None
+    rows = b_rows.reshape(g, pb.n, pb.n)
+    sig_r = group_sigma(rows[0:2])
+    sig_s = group_sigma(rows[2:5]) if pb.reg == REG_TGV else None
     tau_u = inv(kcol + b_cols[:n2]).reshape(pb.n, pb.n)
     tau_v = inv(b_cols[n2:]).reshape(2, pb.n, pb.n) if pb.reg == REG_TGV else None
     return Steps(sig_q=sig_q, sig_r=sig_r, tau_u=tau_u, sig_s=sig_s, tau_v=tau_v)
