@@ -9,6 +9,8 @@
 //
 // The hot path reads a zero-bordered copy of the image ((N+2)^2 floats, pixel (i, j) at
 // (j+1)(N+2) + i+1) so a point with taps i0, j0 in [-1, N-1] needs no per-tap test.
+#include <algorithm>
+
 #include "pat_internal.cuh"
 #include "reduce.cuh"
 
@@ -155,6 +157,180 @@ __global__ void __launch_bounds__(128) k_adjoint_scatter(GeomView g, const float
     }
 }
 
+// ---------------------------------------------------------------------------------
+// K^T by pixel tiles.  A CTA owns a TILE x TILE block of pixels and one group of
+// detectors; its shared accumulator has a one-pixel ring so every point whose taps touch
+// the tile (i0 in [x0-1, x0+TILE-1], j0 in [y0-1, y0+TILE-1]) can add all four weights
+// there.  For each detector the candidate points are the (k, m) in the polar bounding box
+// of that tap region seen from the detector (+-1 index of margin); each candidate is
+// evaluated with the same FP32 position and tap arithmetic as the forward projector, so
+// the CTA adds exactly the entries of K^T that belong to its pixels.  The tile is then
+// added to the output with one atomic per pixel (detector groups share pixels).
+// ---------------------------------------------------------------------------------
+constexpr int ATILE = 16;
+constexpr int ATHREADS = 256;
+constexpr int ABATCH = 32;  // detectors whose windows are computed together
+
+struct AdjArgs {
+    GeomView g;
+    const float* y;
+    float* out;          // padded (N+2)^2 or plain N*N, accumulated with atomics
+    int padded;
+    int tiles_x;
+    int dets_per_group;
+    float xmin, ymin, hx, hy;   // grid extent for the polar boxes
+    const int* stop;
+};
+
+__global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
+    if (a.stop && *(volatile const int*)a.stop) return;
+    const GeomView& g = a.g;
+    const int N = g.n, T = g.n_t, M = g.quad_m;
+    const int tile = blockIdx.x;
+    const int x0 = (tile % a.tiles_x) * ATILE, y0 = (tile / a.tiles_x) * ATILE;
+    const int d_begin = blockIdx.y * a.dets_per_group;
+    const int d_end = min(g.n_det, d_begin + a.dets_per_group);
+    const int tid = threadIdx.x;
+    constexpr int AW = ATILE + 2;
+    __shared__ float acc[AW * AW];
+    __shared__ int s_k0[ABATCH], s_nk[ABATCH], s_m0[ABATCH], s_nm[ABATCH];
+    for (int c = tid; c < AW * AW; c += ATHREADS) acc[c] = 0.f;
+
+    // tap region in world coordinates: fx in [x0 - 1, x0 + TILE)
+    const float rx0 = a.xmin + (x0 - 0.5f) * a.hx, rx1 = a.xmin + (x0 + ATILE + 0.5f) * a.hx;
+    const float ry0 = a.ymin + (y0 - 0.5f) * a.hy, ry1 = a.ymin + (y0 + ATILE + 0.5f) * a.hy;
+    const float inv_dr = 1.f / (g.rk[min(1, T - 1)] - g.rk[0] + (T == 1 ? 1.f : 0.f));
+    const float r_first = g.rk[0];
+    const float two_pi = 6.283185307179586f;
+
+    for (int db = d_begin; db < d_end; db += ABATCH) {
+        const int nb = min(ABATCH, d_end - db);
+        __syncthreads();
+        if (tid < nb) {
+            const float2 det = __ldg(&g.det[db + tid]);
+            const float ex = 1e-3f * a.hx;
+            // radial range
+            const float cx = fminf(fmaxf(det.x, rx0), rx1), cy = fminf(fmaxf(det.y, ry0), ry1);
+            const float rmin = sqrtf((det.x - cx) * (det.x - cx) + (det.y - cy) * (det.y - cy));
+            const float fx0 = fmaxf(fabsf(det.x - rx0), fabsf(det.x - rx1));
+            const float fy0 = fmaxf(fabsf(det.y - ry0), fabsf(det.y - ry1));
+            const float rmax = sqrtf(fx0 * fx0 + fy0 * fy0);
+            // T == 1: inv_dr is irrelevant, the single radius is always a candidate
+            int k0 = T == 1 ? 0 : (int)floorf((rmin - r_first) * inv_dr) - 1;
+            int k1 = T == 1 ? 0 : (int)ceilf((rmax - r_first) * inv_dr) + 1;
+            k0 = max(k0, 0);
+            k1 = min(k1, T - 1);
+            // angular range
+            int m0 = 0, nm = M;
+            const bool inside = det.x >= rx0 - ex && det.x <= rx1 + ex && det.y >= ry0 - ex && det.y <= ry1 + ex;
+            if (!inside) {
+                const float th0 = atan2f(ry0 - det.y, rx0 - det.x);
+                float lo = 0.f, hi = 0.f;
+                const float px[3] = {rx1, rx0, rx1}, py[3] = {ry0, ry1, ry1};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float dth = atan2f(py[c] - det.y, px[c] - det.x) - th0;
+                    if (dth > 3.14159265f) dth -= two_pi;
+                    if (dth < -3.14159265f) dth += two_pi;
+                    lo = fminf(lo, dth);
+                    hi = fmaxf(hi, dth);
+                }
+                const float sc = (float)M / two_pi;
+                const int mlo = (int)floorf((th0 + lo) * sc - 0.5f) - 1;
+                const int mhi = (int)ceilf((th0 + hi) * sc - 0.5f) + 1;
+                if (mhi - mlo + 1 < M) {
+                    nm = mhi - mlo + 1;
+                    m0 = ((mlo % M) + M) % M;
+                }
+            }
+            if (k1 < k0) nm = 0;
+            s_k0[tid] = k0;
+            s_nk[tid] = k1 - k0 + 1;
+            s_m0[tid] = m0;
+            s_nm[tid] = nm;
+        }
+        __syncthreads();
+        for (int b = 0; b < nb; ++b) {
+            const int d = db + b;
+            const int nm = s_nm[b];
+            if (nm <= 0) continue;
+            const int nk = s_nk[b], k0 = s_k0[b], m0 = s_m0[b];
+            const float2 det = __ldg(&g.det[d]);
+            const float* yrow = a.y + (size_t)d * T;
+            // thread -> (k offset, m offset); k advances by kstep
+            const int kstep = nm >= ATHREADS ? 1 : ATHREADS / nm;
+            int mo, ko;
+            if (nm >= ATHREADS) {
+                mo = tid;
+                ko = 0;
+            } else {
+                ko = tid / nm;
+                mo = tid - ko * nm;
+                if (ko >= kstep) continue;
+            }
+            for (int mm = mo; mm < nm; mm += ATHREADS) {
+                int m = m0 + mm;
+                if (m >= M) m -= M;
+                const float2 cs = __ldg(&g.cs[m]);
+                for (int k = k0 + ko; k < k0 + nk; k += kstep) {
+                    Taps t;
+                    const float r = __ldg(&g.rk[k]);
+                    if (!point_taps(g, det, r, cs, t)) continue;
+                    const int li = t.i0 - x0 + 1, lj = t.j0 - y0 + 1;
+                    if ((unsigned)li > (unsigned)ATILE || (unsigned)lj > (unsigned)ATILE) continue;
+                    const float c = __ldg(&yrow[k]) * __ldg(&g.wk[k]);
+                    if (c == 0.f) continue;
+                    const float c0 = c * (1.f - t.ay), c1 = c * t.ay;
+                    float* p = acc + lj * AW + li;
+                    atomicAdd(p, c0 * (1.f - t.ax));
+                    atomicAdd(p + 1, c0 * t.ax);
+                    atomicAdd(p + AW, c1 * (1.f - t.ax));
+                    atomicAdd(p + AW + 1, c1 * t.ax);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    for (int c = tid; c < ATILE * ATILE; c += ATHREADS) {
+        const int lx = c % ATILE, ly = c / ATILE;
+        const int gx = x0 + lx, gy = y0 + ly;
+        if (gx >= N || gy >= N) continue;
+        const float v = acc[(ly + 1) * AW + lx + 1];
+        if (v == 0.f) continue;
+        float* o = a.padded ? a.out + (size_t)(gy + 1) * (N + 2) + gx + 1 : a.out + (size_t)gy * N + gx;
+        if (gridDim.y == 1)
+            *o += v;
+        else
+            atomicAdd(o, v);
+    }
+}
+
+static int launch_adjoint_tiles(const pat_geometry* g, const float* y, float* out, bool padded, const int* stop,
+                                cudaStream_t st) {
+    const int N = g->desc.n;
+    const int tx = ceil_div(N, ATILE);
+    const int tiles = tx * tx;
+    const int target = 4 * 152;
+    int groups = std::max(1, std::min(g->desc.n_det, ceil_div(target, tiles)));
+    const int per = ceil_div(g->desc.n_det, groups);
+    groups = ceil_div(g->desc.n_det, per);
+    AdjArgs a;
+    a.g = g->view;
+    a.y = y;
+    a.out = out;
+    a.padded = padded ? 1 : 0;
+    a.tiles_x = tx;
+    a.dets_per_group = per;
+    a.xmin = (float)g->desc.xmin;
+    a.ymin = (float)g->desc.ymin;
+    a.hx = (float)((g->desc.xmax - g->desc.xmin) / N);
+    a.hy = (float)((g->desc.ymax - g->desc.ymin) / N);
+    a.stop = stop;
+    k_adjoint_tiles<<<dim3(tiles, groups), ATHREADS, 0, st>>>(a);
+    PAT_LAUNCH_CHECK("k_adjoint_tiles");
+    return PAT_OK;
+}
+
 // Row sums K 1 (FP64 accumulation) and column sums K^T 1 (FP64 atomics) of the
 // nonnegative matrix K; only on-grid taps count.
 __global__ void __launch_bounds__(128) k_precond_sums(GeomView g, float* __restrict__ krow,
@@ -232,12 +408,7 @@ int launch_adjoint(const pat_geometry* g, const float* y, float* out, bool padde
     const int N = g->desc.n;
     const size_t cells = padded ? (size_t)(N + 2) * (N + 2) : (size_t)N * N;
     PAT_CUDA(cudaMemsetAsync(out, 0, cells * sizeof(float), st));
-    if (padded)
-        k_adjoint_scatter<true><<<row_grid(g), 128, 0, st>>>(g->view, y, out, nullptr);
-    else
-        k_adjoint_scatter<false><<<row_grid(g), 128, 0, st>>>(g->view, y, out, nullptr);
-    PAT_LAUNCH_CHECK("k_adjoint_scatter");
-    return PAT_OK;
+    return launch_adjoint_tiles(g, y, out, padded, nullptr, st);
 }
 
 // Hot-path K^T q into the zero-bordered accumulator, as two profiled phases.
@@ -247,8 +418,8 @@ int launch_adjoint_phases(const pat_geometry* g, const float* y, float* out_pad,
     PAT_CUDA(cudaMemsetAsync(out_pad, 0, (size_t)(N + 2) * (N + 2) * sizeof(float), st));
     prof_mark(PAT_PHASE_ADJ_CLEAR, st, false);
     prof_mark(PAT_PHASE_ADJOINT, st, true);
-    k_adjoint_scatter<true><<<row_grid(g), 128, 0, st>>>(g->view, y, out_pad, stop);
-    PAT_LAUNCH_CHECK("k_adjoint_scatter");
+    int rc = launch_adjoint_tiles(g, y, out_pad, true, stop, st);
+    if (rc) return rc;
     prof_mark(PAT_PHASE_ADJOINT, st, false);
     return PAT_OK;
 }
