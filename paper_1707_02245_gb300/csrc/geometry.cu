@@ -4,7 +4,7 @@
 // point m of circle (d, k) is x_d + r_k (cos phi_m, sin phi_m), phi_m = 2 pi (m + 1/2)/M,
 // r_k = r0 + (k + 1/2) dr.  The tables built here are the only geometry state the
 // kernels read: detector positions, the M (cos, sin) pairs, radii, arc weights
-// 2 pi r_k / M, and per group of 32 consecutive radii the circular range of angles
+// 2 pi r_k / M, and per group of 8 consecutive radii the circular range of angles
 // whose points can touch the grid (a superset: kernels test every point exactly).
 #include <math.h>
 
@@ -144,6 +144,10 @@ static void free_tables(pat_geometry* g) {
     cudaFree(g->win);
     cudaFree(g->pc.krow);
     cudaFree(g->pc.kcol);
+    cudaFree(g->pc.tile_kmax);
+    cudaFree(g->adj_box);
+    g->adj_box = nullptr;
+    g->pc.tile_kmax = nullptr;
     g->det = nullptr;
     g->cs = nullptr;
     g->rk = nullptr;
@@ -258,12 +262,68 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     g->points_per_apply = pts;
     g->points_on_grid = on_grid;
 
+    // K^T candidate boxes: for every ATILE x ATILE pixel tile and detector, the (k, m)
+    // polar box of the tile's tap region (points with i0 in [x0-1, x0+ATILE-1], same in
+    // y), with one index of margin on every side; FP64 on the host
+    const int tiles_x = (N + ATILE - 1) / ATILE, tiles = tiles_x * tiles_x;
+    std::vector<int4> box((size_t)tiles * D);
+    for (int t = 0; t < tiles; ++t) {
+        const int x0 = (t % tiles_x) * ATILE, y0 = (t / tiles_x) * ATILE;
+        const double rx0 = d.xmin + (x0 - 0.5) * hx - ex, rx1 = d.xmin + (x0 + ATILE + 0.5) * hx + ex;
+        const double ry0 = d.ymin + (y0 - 0.5) * hy - ey, ry1 = d.ymin + (y0 + ATILE + 0.5) * hy + ey;
+        for (int di = 0; di < D; ++di) {
+            const double dx = d.det_xy_host[2 * di], dy = d.det_xy_host[2 * di + 1];
+            const double cx = std::min(std::max(dx, rx0), rx1), cy = std::min(std::max(dy, ry0), ry1);
+            const double rmin = hypot(dx - cx, dy - cy);
+            const double rmax = hypot(std::max(fabs(dx - rx0), fabs(dx - rx1)), std::max(fabs(dy - ry0), fabs(dy - ry1)));
+            int k0 = (int)floor((rmin - d.r0) / d.dr - 0.5) - 1;
+            int k1 = (int)ceil((rmax - d.r0) / d.dr - 0.5) + 1;
+            k0 = std::max(k0, 0);
+            k1 = std::min(k1, T - 1);
+            int m0 = 0, nm = M;
+            const bool inside = dx >= rx0 && dx <= rx1 && dy >= ry0 && dy <= ry1;
+            if (!inside) {
+                const double th0 = atan2(ry0 - dy, rx0 - dx);
+                double lo = 0, hi = 0;
+                const double px[3] = {rx1, rx0, rx1}, py[3] = {ry0, ry1, ry1};
+                for (int c = 0; c < 3; ++c) {
+                    double dth = atan2(py[c] - dy, px[c] - dx) - th0;
+                    if (dth > M_PI) dth -= 2 * M_PI;
+                    if (dth < -M_PI) dth += 2 * M_PI;
+                    lo = std::min(lo, dth);
+                    hi = std::max(hi, dth);
+                }
+                const double sc = M / (2 * M_PI);
+                const long long mlo = (long long)floor((th0 + lo) * sc - 0.5) - 1;
+                const long long mhi = (long long)ceil((th0 + hi) * sc - 0.5) + 1;
+                if (mhi - mlo + 1 < M) {
+                    nm = (int)(mhi - mlo + 1);
+                    m0 = (int)(((mlo % M) + M) % M);
+                }
+            }
+            if (k1 < k0) nm = 0;
+            box[(size_t)t * D + di] = make_int4(k0, std::max(0, k1 - k0 + 1), m0, nm);
+        }
+    }
+    g->adj_tiles_x = tiles_x;
+    g->adj_tiles = tiles;
+    {
+        const int target = 4 * 152;  // CTAs to fill the GPU a few times over
+        int groups = std::max(1, std::min(D, (target + tiles - 1) / tiles));
+        groups = std::min(groups, 8);
+        const int per = (D + groups - 1) / groups;
+        g->adj_per_group = per;
+        g->adj_groups = (D + per - 1) / per;
+    }
+
     cudaError_t e = cudaSuccess;
     e = cudaMalloc(&g->det, sizeof(float2) * D);
     if (e == cudaSuccess) e = cudaMalloc(&g->cs, sizeof(float2) * M);
     if (e == cudaSuccess) e = cudaMalloc(&g->rk, sizeof(float) * T);
     if (e == cudaSuccess) e = cudaMalloc(&g->wk, sizeof(float) * T);
     if (e == cudaSuccess) e = cudaMalloc(&g->win, sizeof(int2) * win.size());
+    if (e == cudaSuccess) e = cudaMalloc(&g->adj_box, sizeof(int4) * box.size());
+    if (e == cudaSuccess) e = cudaMemcpy(g->adj_box, box.data(), sizeof(int4) * box.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->det, det.data(), sizeof(float2) * D, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->cs, cs.data(), sizeof(float2) * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->rk, rk.data(), sizeof(float) * T, cudaMemcpyHostToDevice);

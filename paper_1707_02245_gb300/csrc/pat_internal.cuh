@@ -59,12 +59,14 @@ struct GeomView {
     const int2* win;     // D * n_kgrp angular windows {m_first, m_count} (circular)
 };
 
-constexpr int KGRP = 32;       // radii per window group (one warp)
+constexpr int KGRP = 8;        // radii per angular-window group
 constexpr int MAX_QUAD_M = 8192;
+constexpr int ATILE = 16;      // K^T pixel tile side
 
 struct PrecondCache {
     float* krow = nullptr;      // K 1 per data row (S), summed in FP64
     float* kcol = nullptr;      // K^T 1 per pixel (N*N), summed in FP64
+    float* tile_kmax = nullptr; // max of K^T 1 over each K^T tile
     bool ready = false;
 };
 
@@ -81,6 +83,8 @@ struct pat_geometry {
     float* rk = nullptr;
     float* wk = nullptr;
     int2* win = nullptr;
+    int4* adj_box = nullptr;          // per (tile, detector): {k0, nk, m0, nm} candidate box of K^T
+    int adj_tiles_x = 0, adj_tiles = 0, adj_groups = 1, adj_per_group = 1;
     pat::GeomView view;
     // lazily computed preconditioner sums
     mutable std::mutex mtx;
@@ -121,12 +125,19 @@ inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 // Host entry points implemented in projector.cu and used by pdhg.cu
 int ensure_precond(const pat_geometry* g, cudaStream_t st);
 int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y, cudaStream_t st);
-int launch_adjoint(const pat_geometry* g, const float* y, float* out, bool padded, cudaStream_t st);
-int launch_adjoint_phases(const pat_geometry* g, const float* y, float* out_pad, const int* stop, cudaStream_t st);
+// K^T y into an N*N image (allocates its scratch from the stream-ordered pool).
+int launch_adjoint(const pat_geometry* g, const float* y, float* out, cudaStream_t st);
+// Hot-path K^T q: adj_groups partial images in the zero-bordered (N+2)^2 layout,
+// parts[grp * (N+2)^2 + ...]; ymax_bits holds max |q| as float bits.
+int launch_adjoint_parts(const pat_geometry* g, const float* y, const unsigned* ymax_bits, float* parts,
+                         const int* stop, cudaStream_t st);
 int launch_forward_prox(const pat_geometry* g, const float* ubar_pad, float* q, const float* f,
-                        const float* sig_q, float sig_q_scalar, const int* stop, cudaStream_t st);
+                        const float* sig_q, float sig_q_scalar, unsigned* qmax_bits, const int* stop,
+                        cudaStream_t st);
 int launch_forward_gap(const pat_geometry* g, const float* u, const float* q, const float* f,
                        double* partials, int n_part, const int* stop, cudaStream_t st);
 int forward_gap_blocks(const pat_geometry* g);
+// max |y| as float bits into *out (which must hold 0 or a smaller value beforehand)
+int launch_absmax(const float* y, long long n, unsigned* out, cudaStream_t st);
 
 }  // namespace pat

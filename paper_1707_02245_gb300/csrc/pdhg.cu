@@ -4,7 +4,7 @@
 // Schedule of one iteration n (two global dependency points: K needs all of ubar, the
 // primal step needs all of K^T q):
 //   1. k_forward_prox     q^{n+1} = prox(q^n + Sigma_q K ubar^n)              (data rows)
-//   2. k_adjoint_scatter  w = K^T q^{n+1}                                     (data rows)
+//   2. k_adjoint_tiles    w = K^T q^{n+1}                                    (pixel tiles)
 //   3. k_update<REG>      on a pixel tile with a one-pixel halo:
 //        u^{n+1}, v^{n+1} from w, r^{n+1}, s^{n+1};  ubar, vbar by extrapolation;
 //        then the dual step of the NEXT iteration r^{n+2}, s^{n+2} from ubar, vbar.
@@ -37,7 +37,9 @@ struct UpdateArgs {
     const float* tau_u;    // N*N (diagonal rule)
     const float* sig_r;    // N*N (dTV diagonal rule)
     const float* xi;       // 2*N*N (dTV)
-    const float* w_pad;    // K^T q, (N+2)^2
+    const float* w_parts;  // K^T q as `groups` partial images, (N+2)^2 each
+    int groups;
+    unsigned* qmax_bits;   // max |q| of this iteration; reset here for the next one
     const float* x_in;     // u, v1, v2
     const float* y_in;     // r1, r2, s11, s22, s12
     float* x_out;
@@ -111,7 +113,9 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
             if (in) {
                 const int gi = gy * N + gx;
                 const float divr = s_r1m[ly][lx] - s_r1m[ly][lx - 1] + s_r2m[ly][lx] - s_r2m[ly - 1][lx];
-                const float w = __ldg(a.w_pad + (gy + 1) * (N + 2) + gx + 1);
+                float w = 0.f;
+                const size_t wo = (size_t)(gy + 1) * (N + 2) + gx + 1, P2 = (size_t)(N + 2) * (N + 2);
+                for (int gr = 0; gr < a.groups; ++gr) w += __ldg(a.w_parts + gr * P2 + wo);
                 const float uo = __ldg(u_in + gi);
                 const float tu = a.tau >= 0.f ? a.tau : __ldg(a.tau_u + gi);
                 const float un = uo - tu * (w - divr);
@@ -203,7 +207,10 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
             a.x_out[2 * NN + gi] = s_vn2[threadIdx.y][threadIdx.x];
         }
     }
-    if (a.iter && blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) *a.iter += 1;
+    if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
+        if (a.iter) *a.iter += 1;
+        if (a.qmax_bits) *a.qmax_bits = 0u;
+    }
 }
 
 // Dual step r, s <- prox(r, s + Sigma (A_reg (ubar, vbar))) used once before the first
@@ -280,7 +287,8 @@ struct GapArgs {
     const float* x;       // x^{n+1}
     const float* x_old;   // x^n (NULL: residual terms are zero)
     const float* y;       // r, s at the same evaluation (y^{n+1})
-    const float* w_pad;   // K^T q^{n+1}
+    const float* w_parts; // K^T q^{n+1} as `groups` partial images
+    int groups;
     double* partials;
     const int* stop;
 };
@@ -331,7 +339,13 @@ __global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
             return c == 0 ? r0 : r1;
         };
         const double divr = rm(0, gx, gy) - rm(0, gx - 1, gy) + rm(1, gx, gy) - rm(1, gx, gy - 1);
-        const double w = (double)a.w_pad[(size_t)(gy + 1) * (N + 2) + gx + 1];
+        double w = 0.0;
+        {
+            const size_t wo = (size_t)(gy + 1) * (N + 2) + gx + 1, P2 = (size_t)(N + 2) * (N + 2);
+            float wf = 0.f;
+            for (int gr = 0; gr < a.groups; ++gr) wf += a.w_parts[gr * P2 + wo];
+            w = (double)wf;
+        }
         acc[2] += fabs(w - divr);
         if (REG == PAT_TGV) {
             auto vm = [&](int c, int x, int y, bool mx) -> double {  // masked v for d^-
@@ -369,6 +383,7 @@ __global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
 struct InfoDev {
     double primal, dual, gap, rel_gap, residual;
     int iters_done, status, stop, iter;
+    unsigned qmax_bits;   // max |q| of the current iteration (float bits)
 };
 
 struct FinalArgs {
@@ -565,7 +580,7 @@ struct Workspace {
     size_t bytes = 0;
     float* X[2] = {nullptr, nullptr};
     float* Y[2] = {nullptr, nullptr};
-    float *q = nullptr, *ubar_pad = nullptr, *w_pad = nullptr, *vbar0 = nullptr;
+    float *q = nullptr, *ubar_pad = nullptr, *w_parts = nullptr, *vbar0 = nullptr;
     float *tau_u = nullptr, *sig_q = nullptr, *sig_r = nullptr;
     double *data_part = nullptr, *pix_part = nullptr;
     InfoDev* info = nullptr;
@@ -581,7 +596,8 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     ws.n_data = forward_gap_blocks(g);
     ws.n_pix = pix_blocks((int)N);
     size_t off[16];
-    size_t sz[16] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, P2 * 4, (reg == PAT_TGV ? 2 * NN : 1) * 4,
+    size_t sz[16] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, P2 * 4 * g->adj_groups,
+                     (reg == PAT_TGV ? 2 * NN : 1) * 4,
                      NN * 4, S * 4, NN * 4, (size_t)ws.n_data * 3 * 8, (size_t)ws.n_pix * 6 * 8, sizeof(InfoDev)};
     size_t total = 0;
     for (int i = 0; i < 14; ++i) {
@@ -597,7 +613,7 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     ws.Y[1] = (float*)(b + off[3]);
     ws.q = (float*)(b + off[4]);
     ws.ubar_pad = (float*)(b + off[5]);
-    ws.w_pad = (float*)(b + off[6]);
+    ws.w_parts = (float*)(b + off[6]);
     ws.vbar0 = (float*)(b + off[7]);
     ws.tau_u = (float*)(b + off[8]);
     ws.sig_q = (float*)(b + off[9]);
@@ -668,7 +684,9 @@ static int launch_update(const pat_geometry* g, const pat_params* p, Workspace& 
     a.tau_u = ws.tau_u;
     a.sig_r = ws.sig_r;
     a.xi = p->xi_dev;
-    a.w_pad = ws.w_pad;
+    a.w_parts = ws.w_parts;
+    a.groups = g->adj_groups;
+    a.qmax_bits = &ws.info->qmax_bits;
     a.x_in = ws.X[it & 1];
     a.y_in = ws.Y[it & 1];
     a.x_out = ws.X[(it + 1) & 1];
@@ -688,7 +706,7 @@ static int launch_gap(const pat_geometry* g, const pat_params* p, Workspace& ws,
     const int N = g->desc.n;
     int rc = launch_forward_gap(g, x, q, f, ws.data_part, ws.n_data, stop, st);
     if (rc) return rc;
-    GapArgs ga{N, p->gamma, p->xi_dev, x, x_old, y, ws.w_pad, ws.pix_part, stop};
+    GapArgs ga{N, p->gamma, p->xi_dev, x, x_old, y, ws.w_parts, g->adj_groups, ws.pix_part, stop};
     k_gap_pixels<REG><<<ws.n_pix, 256, 0, st>>>(ga);
     PAT_LAUNCH_CHECK("k_gap_pixels");
     FinalArgs fa{ws.data_part, ws.n_data, ws.pix_part, ws.n_pix, p->alpha, p->beta, p->box_u, p->box_v,
@@ -704,10 +722,11 @@ static int enqueue_iterations(const pat_geometry* g, const float* f, const pat_p
     const int* stop = &ws.info->stop;
     for (int it = it0; it < it0 + count; ++it) {
         prof_mark(PAT_PHASE_FORWARD_PROX, st, true);
-        int rc = launch_forward_prox(g, ws.ubar_pad, ws.q, f, sc.sig_q >= 0 ? nullptr : ws.sig_q, sc.sig_q, stop, st);
+        int rc = launch_forward_prox(g, ws.ubar_pad, ws.q, f, sc.sig_q >= 0 ? nullptr : ws.sig_q, sc.sig_q,
+                                     &ws.info->qmax_bits, stop, st);
         if (rc) return rc;
         prof_mark(PAT_PHASE_FORWARD_PROX, st, false);
-        rc = launch_adjoint_phases(g, ws.q, ws.w_pad, stop, st);
+        rc = launch_adjoint_parts(g, ws.q, &ws.info->qmax_bits, ws.w_parts, stop, st);
         if (rc) return rc;
         prof_mark(PAT_PHASE_UPDATE, st, true);
         rc = launch_update<REG>(g, p, ws, sc, it, st);
@@ -943,7 +962,7 @@ int scalar2_steps(const pat_geometry* g, const pat_params* p, ScalarSteps& out, 
             if (op == 0) {
                 int rc = launch_forward(g, x, false, y, st);
                 if (rc) return rc;
-                rc = launch_adjoint(g, y, x, false, st);
+                rc = launch_adjoint(g, y, x, st);
                 if (rc) return rc;
             } else {
                 k_apply_B<<<grd, blk, 0, st>>>(N, p->reg, (float)p->gamma, p->xi_dev, x, y); count_launch();
@@ -1066,7 +1085,12 @@ static int gap_impl(const pat_geometry* g, const float* f, const pat_params* p, 
     if (rc) return rc;
     InfoDev h{};
     rc = cudaMemsetAsync(ws.info, 0, sizeof(InfoDev), st) ? PAT_ERR_CUDA : 0;
-    if (!rc) rc = launch_adjoint(g, y, ws.w_pad, true, st);
+    if (!rc) rc = ensure_precond(g, st);
+    if (!rc) {
+        const long long S_ = (long long)g->desc.n_det * g->desc.n_t;
+        rc = launch_absmax(y, S_, &ws.info->qmax_bits, st);
+        if (!rc) rc = launch_adjoint_parts(g, y, &ws.info->qmax_bits, ws.w_parts, nullptr, st);
+    }
     pat_params q = *p;
     q.tol = 0;
     if (!rc) rc = launch_gap<REG>(g, &q, ws, x, nullptr, y + S, y, f, nullptr, st);

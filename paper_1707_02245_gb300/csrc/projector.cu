@@ -36,21 +36,44 @@ __device__ __forceinline__ float fetch4(const float* __restrict__ u, int N, cons
     }
 }
 
-// Integral of the bilinear image over circle (d, k) with the arc weight applied.
-// All lanes of a warp must share d and k / KGRP (valid = k < T).
+// Row mapping of the projector kernels: a warp holds KGRP = 8 consecutive radii of one
+// detector times NPH = 4 angular phases; lane = ph * 8 + kl.  Phase ph walks the group's
+// angular window at m = m_first + ph, + ph + 4, ...  so at every step the warp evaluates
+// a 4 (angles) x 8 (radii) patch of the polar grid, which is a compact patch of pixels.
+constexpr int NPH = 4;
+constexpr int ROWS_PER_BLOCK = 32;           // 4 warps x 8 radii
+constexpr int ROW_THREADS = ROWS_PER_BLOCK * NPH;
+
+struct RowLane {
+    int d, k, ph;
+    bool valid;
+};
+
+__device__ __forceinline__ RowLane row_lane(const GeomView& g) {
+    RowLane r;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    r.ph = lane >> 3;
+    r.d = blockIdx.y;
+    r.k = blockIdx.x * ROWS_PER_BLOCK + warp * KGRP + (lane & 7);
+    r.valid = r.k < g.n_t;
+    return r;
+}
+
+// Partial integral of the bilinear image over circle (d, k) for one angular phase.
 template <bool PADDED>
-__device__ __forceinline__ float circle_integral(const GeomView& g, const float* __restrict__ u, int d, int k,
-                                                 bool valid) {
-    const int2 w = __ldg(&g.win[d * g.n_kgrp + k / KGRP]);
-    const float2 det = __ldg(&g.det[d]);
-    const float r = valid ? __ldg(&g.rk[k]) : 0.f;
+__device__ __forceinline__ float circle_partial(const GeomView& g, const float* __restrict__ u, const RowLane& rl) {
+    const int2 w = __ldg(&g.win[rl.d * g.n_kgrp + min(rl.k / KGRP, g.n_kgrp - 1)]);
+    const float2 det = __ldg(&g.det[rl.d]);
+    const float r = rl.valid ? __ldg(&g.rk[rl.k]) : 0.f;
     float acc = 0.f;
-    int m = w.x;
-    for (int j = 0; j < w.y; ++j) {
+    int m = w.x + rl.ph;
+    if (m >= g.quad_m) m -= g.quad_m;
+    for (int j = rl.ph; j < w.y; j += NPH) {
         const float2 cs = __ldg(&g.cs[m]);
-        m = (m + 1 == g.quad_m) ? 0 : m + 1;
+        m += NPH;
+        if (m >= g.quad_m) m -= g.quad_m;
         Taps t;
-        if (point_taps(g, det, r, cs, t) && valid) {
+        if (point_taps(g, det, r, cs, t) && rl.valid) {
             float v10, v01, v11;
             const float v00 = fetch4<PADDED>(u, g.n, t, v10, v01, v11);
             const float a = fmaf(t.ax, v10 - v00, v00);
@@ -58,277 +81,217 @@ __device__ __forceinline__ float circle_integral(const GeomView& g, const float*
             acc += fmaf(t.ay, b - a, a);
         }
     }
-    return valid ? acc * __ldg(&g.wk[k]) : 0.f;
+    return acc;
+}
+
+// Sum over the four phases (lanes kl, kl+8, kl+16, kl+24); valid in every lane.
+__device__ __forceinline__ float phase_sum(float v) {
+    v += __shfl_xor_sync(0xffffffffu, v, 8);
+    v += __shfl_xor_sync(0xffffffffu, v, 16);
+    return v;
 }
 
 // y = K u
 template <bool PADDED>
-__global__ void __launch_bounds__(128) k_forward(GeomView g, const float* __restrict__ u, float* __restrict__ y) {
-    const int d = blockIdx.y;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = k < g.n_t;
-    const float val = circle_integral<PADDED>(g, u, d, k, valid);
-    if (valid) y[(size_t)d * g.n_t + k] = val;
+__global__ void __launch_bounds__(ROW_THREADS) k_forward(GeomView g, const float* __restrict__ u, float* __restrict__ y) {
+    const RowLane rl = row_lane(g);
+    const float s = phase_sum(circle_partial<PADDED>(g, u, rl));
+    if (rl.valid && rl.ph == 0) y[(size_t)rl.d * g.n_t + rl.k] = s * __ldg(&g.wk[rl.k]);
 }
 
 // q <- prox_{sigma F1*}(q + sigma K ubar) = (q + sigma (K ubar - f)) / (1 + sigma)  (Sec. 3.2)
-__global__ void __launch_bounds__(128) k_forward_prox(GeomView g, const float* __restrict__ ubar_pad,
-                                                      float* __restrict__ q, const float* __restrict__ f,
-                                                      const float* __restrict__ sig_q, float sig_scalar,
-                                                      const int* __restrict__ stop) {
+// Also records max |q| (as float bits) for the fixed-point K^T that follows.
+__global__ void __launch_bounds__(ROW_THREADS) k_forward_prox(GeomView g, const float* __restrict__ ubar_pad,
+                                                             float* __restrict__ q, const float* __restrict__ f,
+                                                             const float* __restrict__ sig_q, float sig_scalar,
+                                                             unsigned* __restrict__ qmax_bits,
+                                                             const int* __restrict__ stop) {
     if (stop && *(volatile const int*)stop) return;
-    const int d = blockIdx.y;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = k < g.n_t;
-    const float ku = circle_integral<true>(g, ubar_pad, d, k, valid);
-    if (valid) {
-        const size_t i = (size_t)d * g.n_t + k;
-        const float s = sig_q ? sig_q[i] : sig_scalar;
-        q[i] = (q[i] + s * (ku - f[i])) / (1.f + s);
+    const RowLane rl = row_lane(g);
+    const float s = phase_sum(circle_partial<true>(g, ubar_pad, rl));
+    float aq = 0.f;
+    if (rl.valid && rl.ph == 0) {
+        const size_t i = (size_t)rl.d * g.n_t + rl.k;
+        const float ku = s * __ldg(&g.wk[rl.k]);
+        const float sg = sig_q ? sig_q[i] : sig_scalar;
+        const float qn = (q[i] + sg * (ku - f[i])) / (1.f + sg);
+        q[i] = qn;
+        aq = fabsf(qn);
     }
+    // block max of |q| (a NaN's bits compare greater than every finite value's)
+    unsigned bits = __float_as_uint(aq);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, o));
+    __shared__ unsigned wmax[ROW_THREADS / 32];
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = bits;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned m = 0;
+        for (int w = 0; w < ROW_THREADS / 32; ++w) m = max(m, wmax[w]);
+        if (m) atomicMax(qmax_bits, m);
+    }
+}
+
+// max |y| over n values as float bits (atomicMax; *out must start at 0)
+__global__ void k_absmax(const float* __restrict__ y, long long n, unsigned* __restrict__ out) {
+    unsigned m = 0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = max(m, __float_as_uint(fabsf(y[i])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
 }
 
 // FP64 partial sums for the duality gap over data rows:
 //   {sum (K u - f)^2, sum q^2, sum q f}   one triple per block
-__global__ void __launch_bounds__(128) k_forward_gap(GeomView g, const float* __restrict__ u,
-                                                     const float* __restrict__ q, const float* __restrict__ f,
-                                                     double* __restrict__ partials, const int* __restrict__ stop) {
+__global__ void __launch_bounds__(ROW_THREADS) k_forward_gap(GeomView g, const float* __restrict__ u,
+                                                            const float* __restrict__ q, const float* __restrict__ f,
+                                                            double* __restrict__ partials,
+                                                            const int* __restrict__ stop) {
     if (stop && *(volatile const int*)stop) return;
-    const int d = blockIdx.y;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = k < g.n_t;
-    const float ku = circle_integral<false>(g, u, d, k, valid);
+    const RowLane rl = row_lane(g);
+    const float s = phase_sum(circle_partial<false>(g, u, rl));
     double a = 0.0, b = 0.0, c = 0.0;
-    if (valid) {
-        const size_t i = (size_t)d * g.n_t + k;
+    if (rl.valid && rl.ph == 0) {
+        const float ku = s * __ldg(&g.wk[rl.k]);
+        const size_t i = (size_t)rl.d * g.n_t + rl.k;
         const double res = (double)ku - (double)f[i];
         const double qi = (double)q[i];
         a = res * res;
         b = qi * qi;
         c = qi * (double)f[i];
     }
-    double3 s = block_sum3(make_double3(a, b, c));
+    const double3 sum = block_sum3(make_double3(a, b, c));
     if (threadIdx.x == 0) {
         const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-        partials[3 * blk + 0] = s.x;
-        partials[3 * blk + 1] = s.y;
-        partials[3 * blk + 2] = s.z;
-    }
-}
-
-// out += K^T y by scattering every point's four bilinear weights (float atomics).
-// PADDED: out is the zero-bordered (N+2)^2 layout and border cells collect the taps that
-// fall off the grid (the consumer ignores them); otherwise off-grid taps are dropped.
-template <bool PADDED>
-__global__ void __launch_bounds__(128) k_adjoint_scatter(GeomView g, const float* __restrict__ y,
-                                                         float* __restrict__ out, const int* __restrict__ stop) {
-    if (stop && *(volatile const int*)stop) return;
-    const int d = blockIdx.y;
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const bool valid = k < g.n_t;
-    const int2 w = __ldg(&g.win[d * g.n_kgrp + k / KGRP]);
-    const float2 det = __ldg(&g.det[d]);
-    const float r = valid ? __ldg(&g.rk[k]) : 0.f;
-    const float c = valid ? __ldg(&y[(size_t)d * g.n_t + k]) * __ldg(&g.wk[k]) : 0.f;
-    const int N = g.n;
-    int m = w.x;
-    for (int j = 0; j < w.y; ++j) {
-        const float2 cs = __ldg(&g.cs[m]);
-        m = (m + 1 == g.quad_m) ? 0 : m + 1;
-        Taps t;
-        if (point_taps(g, det, r, cs, t) && valid && c != 0.f) {
-            const float c0 = c * (1.f - t.ay), c1 = c * t.ay;
-            if (PADDED) {
-                const int P = N + 2;
-                float* p = out + (t.j0 + 1) * P + (t.i0 + 1);
-                atomicAdd(p, c0 * (1.f - t.ax));
-                atomicAdd(p + 1, c0 * t.ax);
-                atomicAdd(p + P, c1 * (1.f - t.ax));
-                atomicAdd(p + P + 1, c1 * t.ax);
-            } else {
-                const bool x0 = t.i0 >= 0, x1 = t.i0 + 1 < N, y0 = t.j0 >= 0, y1 = t.j0 + 1 < N;
-                float* p = out + t.j0 * N + t.i0;
-                if (x0 && y0) atomicAdd(p, c0 * (1.f - t.ax));
-                if (x1 && y0) atomicAdd(p + 1, c0 * t.ax);
-                if (x0 && y1) atomicAdd(p + N, c1 * (1.f - t.ax));
-                if (x1 && y1) atomicAdd(p + N + 1, c1 * t.ax);
-            }
-        }
+        partials[3 * blk + 0] = sum.x;
+        partials[3 * blk + 1] = sum.y;
+        partials[3 * blk + 2] = sum.z;
     }
 }
 
 // ---------------------------------------------------------------------------------
-// K^T by pixel tiles.  A CTA owns a TILE x TILE block of pixels and one group of
-// detectors; its shared accumulator has a one-pixel ring so every point whose taps touch
-// the tile (i0 in [x0-1, x0+TILE-1], j0 in [y0-1, y0+TILE-1]) can add all four weights
-// there.  For each detector the candidate points are the (k, m) in the polar bounding box
-// of that tap region seen from the detector (+-1 index of margin); each candidate is
-// evaluated with the same FP32 position and tap arithmetic as the forward projector, so
-// the CTA adds exactly the entries of K^T that belong to its pixels.  The tile is then
-// added to the output with one atomic per pixel (detector groups share pixels).
+// K^T by pixel tiles with exact fixed-point accumulation.
+//
+// A CTA owns an ATILE x ATILE block of pixels and one group of detectors.  Its shared
+// accumulator (with a one-pixel ring, so every point whose taps touch the tile can add
+// all four weights) holds int32 fixed-point values: every pixel satisfies
+//   |(K^T y)(p)| <= max|y| * (K^T 1)(p)        (all entries of K are >= 0),
+// so with the scale S = 2^30 / (max|y| * max over the tile of K^T 1) no partial sum of a
+// tile pixel exceeds 2^30 and integer addition (native shared atomics, associative, hence
+// deterministic) replaces floating-point atomics.  The resolution 2^-30 of that bound is
+// finer than FP32 accumulation of the same terms.  Ring cells may wrap; they are dropped.
+//
+// Candidates: one warp per detector walks the (k, m) box precomputed for (tile, detector)
+// at geometry creation; its lanes split into contiguous chunks of radii times
+// consecutive angles, so lanes that add at the same time touch distinct pixels.  Every
+// candidate uses the forward projector's FP32 position and tap arithmetic, so the CTA
+// adds exactly the entries of K^T that belong to its pixels.  Each detector group writes
+// its partial tile with plain stores; consumers add the groups in a fixed order.
 // ---------------------------------------------------------------------------------
-constexpr int ATILE = 16;
 constexpr int ATHREADS = 256;
-constexpr int ABATCH = 32;  // detectors whose windows are computed together
 
 struct AdjArgs {
     GeomView g;
     const float* y;
-    float* out;          // padded (N+2)^2 or plain N*N, accumulated with atomics
-    int padded;
+    const unsigned* ymax_bits;
+    const float* tile_kmax;
+    const int4* box;
+    float* parts;        // groups x (N+2)^2; the zero border is never written
     int tiles_x;
     int dets_per_group;
-    float xmin, ymin, hx, hy;   // grid extent for the polar boxes
     const int* stop;
 };
 
 __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
     if (a.stop && *(volatile const int*)a.stop) return;
     const GeomView& g = a.g;
-    const int N = g.n, T = g.n_t, M = g.quad_m;
+    const int N = g.n, T = g.n_t, M = g.quad_m, D = g.n_det;
     const int tile = blockIdx.x;
     const int x0 = (tile % a.tiles_x) * ATILE, y0 = (tile / a.tiles_x) * ATILE;
     const int d_begin = blockIdx.y * a.dets_per_group;
-    const int d_end = min(g.n_det, d_begin + a.dets_per_group);
-    const int tid = threadIdx.x;
+    const int d_end = min(D, d_begin + a.dets_per_group);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int AW = ATILE + 2;
-    __shared__ float acc[AW * AW];
-    __shared__ int s_k0[ABATCH], s_nk[ABATCH], s_m0[ABATCH], s_nm[ABATCH];
-    for (int c = tid; c < AW * AW; c += ATHREADS) acc[c] = 0.f;
+    __shared__ int acc[AW * AW];
+    for (int c = tid; c < AW * AW; c += ATHREADS) acc[c] = 0;
+    const float bound = __uint_as_float(*a.ymax_bits) * __ldg(&a.tile_kmax[tile]);
+    const float scale = 1073741824.0f / bound;  // 2^30 / bound
+    __syncthreads();
 
-    // tap region in world coordinates: fx in [x0 - 1, x0 + TILE)
-    const float rx0 = a.xmin + (x0 - 0.5f) * a.hx, rx1 = a.xmin + (x0 + ATILE + 0.5f) * a.hx;
-    const float ry0 = a.ymin + (y0 - 0.5f) * a.hy, ry1 = a.ymin + (y0 + ATILE + 0.5f) * a.hy;
-    const float inv_dr = 1.f / (g.rk[min(1, T - 1)] - g.rk[0] + (T == 1 ? 1.f : 0.f));
-    const float r_first = g.rk[0];
-    const float two_pi = 6.283185307179586f;
-
-    for (int db = d_begin; db < d_end; db += ABATCH) {
-        const int nb = min(ABATCH, d_end - db);
-        __syncthreads();
-        if (tid < nb) {
-            const float2 det = __ldg(&g.det[db + tid]);
-            const float ex = 1e-3f * a.hx;
-            // radial range
-            const float cx = fminf(fmaxf(det.x, rx0), rx1), cy = fminf(fmaxf(det.y, ry0), ry1);
-            const float rmin = sqrtf((det.x - cx) * (det.x - cx) + (det.y - cy) * (det.y - cy));
-            const float fx0 = fmaxf(fabsf(det.x - rx0), fabsf(det.x - rx1));
-            const float fy0 = fmaxf(fabsf(det.y - ry0), fabsf(det.y - ry1));
-            const float rmax = sqrtf(fx0 * fx0 + fy0 * fy0);
-            // T == 1: inv_dr is irrelevant, the single radius is always a candidate
-            int k0 = T == 1 ? 0 : (int)floorf((rmin - r_first) * inv_dr) - 1;
-            int k1 = T == 1 ? 0 : (int)ceilf((rmax - r_first) * inv_dr) + 1;
-            k0 = max(k0, 0);
-            k1 = min(k1, T - 1);
-            // angular range
-            int m0 = 0, nm = M;
-            const bool inside = det.x >= rx0 - ex && det.x <= rx1 + ex && det.y >= ry0 - ex && det.y <= ry1 + ex;
-            if (!inside) {
-                const float th0 = atan2f(ry0 - det.y, rx0 - det.x);
-                float lo = 0.f, hi = 0.f;
-                const float px[3] = {rx1, rx0, rx1}, py[3] = {ry0, ry1, ry1};
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    float dth = atan2f(py[c] - det.y, px[c] - det.x) - th0;
-                    if (dth > 3.14159265f) dth -= two_pi;
-                    if (dth < -3.14159265f) dth += two_pi;
-                    lo = fminf(lo, dth);
-                    hi = fmaxf(hi, dth);
-                }
-                const float sc = (float)M / two_pi;
-                const int mlo = (int)floorf((th0 + lo) * sc - 0.5f) - 1;
-                const int mhi = (int)ceilf((th0 + hi) * sc - 0.5f) + 1;
-                if (mhi - mlo + 1 < M) {
-                    nm = mhi - mlo + 1;
-                    m0 = ((mlo % M) + M) % M;
-                }
-            }
-            if (k1 < k0) nm = 0;
-            s_k0[tid] = k0;
-            s_nk[tid] = k1 - k0 + 1;
-            s_m0[tid] = m0;
-            s_nm[tid] = nm;
-        }
-        __syncthreads();
-        for (int b = 0; b < nb; ++b) {
-            const int d = db + b;
-            const int nm = s_nm[b];
-            if (nm <= 0) continue;
-            const int nk = s_nk[b], k0 = s_k0[b], m0 = s_m0[b];
+    if (bound > 0.f && isfinite(bound)) {
+        for (int d = d_begin + warp; d < d_end; d += ATHREADS / 32) {
+            const int4 bx = __ldg(&a.box[(size_t)tile * D + d]);
+            const int k0 = bx.x, nk = bx.y, m0 = bx.z, nm = bx.w;
+            if (nm <= 0 || nk <= 0) continue;
+            const int per = nm < 32 ? nm : 32;
+            const int groups = 32 / per;
+            const int grp = lane / per, mo = lane - grp * per;
+            if (grp >= groups) continue;
+            const int chunk = (nk + groups - 1) / groups;
+            const int kb = k0 + grp * chunk, ke = min(k0 + nk, kb + chunk);
             const float2 det = __ldg(&g.det[d]);
             const float* yrow = a.y + (size_t)d * T;
-            // thread -> (k offset, m offset); k advances by kstep
-            const int kstep = nm >= ATHREADS ? 1 : ATHREADS / nm;
-            int mo, ko;
-            if (nm >= ATHREADS) {
-                mo = tid;
-                ko = 0;
-            } else {
-                ko = tid / nm;
-                mo = tid - ko * nm;
-                if (ko >= kstep) continue;
-            }
-            for (int mm = mo; mm < nm; mm += ATHREADS) {
+            for (int mm = mo; mm < nm; mm += per) {
                 int m = m0 + mm;
                 if (m >= M) m -= M;
                 const float2 cs = __ldg(&g.cs[m]);
-                for (int k = k0 + ko; k < k0 + nk; k += kstep) {
+                for (int k = kb; k < ke; ++k) {
                     Taps t;
-                    const float r = __ldg(&g.rk[k]);
-                    if (!point_taps(g, det, r, cs, t)) continue;
+                    if (!point_taps(g, det, __ldg(&g.rk[k]), cs, t)) continue;
                     const int li = t.i0 - x0 + 1, lj = t.j0 - y0 + 1;
                     if ((unsigned)li > (unsigned)ATILE || (unsigned)lj > (unsigned)ATILE) continue;
-                    const float c = __ldg(&yrow[k]) * __ldg(&g.wk[k]);
-                    if (c == 0.f) continue;
+                    const float c = __ldg(&yrow[k]) * __ldg(&g.wk[k]) * scale;
                     const float c0 = c * (1.f - t.ay), c1 = c * t.ay;
-                    float* p = acc + lj * AW + li;
-                    atomicAdd(p, c0 * (1.f - t.ax));
-                    atomicAdd(p + 1, c0 * t.ax);
-                    atomicAdd(p + AW, c1 * (1.f - t.ax));
-                    atomicAdd(p + AW + 1, c1 * t.ax);
+                    int* p = acc + lj * AW + li;
+                    atomicAdd(p, __float2int_rn(c0 * (1.f - t.ax)));
+                    atomicAdd(p + 1, __float2int_rn(c0 * t.ax));
+                    atomicAdd(p + AW, __float2int_rn(c1 * (1.f - t.ax)));
+                    atomicAdd(p + AW + 1, __float2int_rn(c1 * t.ax));
                 }
             }
         }
     }
     __syncthreads();
+    // back to floating point: value = acc * bound / 2^30 (NaN / Inf bounds propagate)
+    const float inv = bound > 0.f ? bound * 9.313225746154785e-10f : (bound == 0.f ? 0.f : bound);
+    float* out = a.parts + (size_t)blockIdx.y * (N + 2) * (N + 2);
     for (int c = tid; c < ATILE * ATILE; c += ATHREADS) {
         const int lx = c % ATILE, ly = c / ATILE;
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= N || gy >= N) continue;
-        const float v = acc[(ly + 1) * AW + lx + 1];
-        if (v == 0.f) continue;
-        float* o = a.padded ? a.out + (size_t)(gy + 1) * (N + 2) + gx + 1 : a.out + (size_t)gy * N + gx;
-        if (gridDim.y == 1)
-            *o += v;
-        else
-            atomicAdd(o, v);
+        out[(size_t)(gy + 1) * (N + 2) + gx + 1] = (float)acc[(ly + 1) * AW + lx + 1] * inv;
     }
 }
 
-static int launch_adjoint_tiles(const pat_geometry* g, const float* y, float* out, bool padded, const int* stop,
-                                cudaStream_t st) {
-    const int N = g->desc.n;
-    const int tx = ceil_div(N, ATILE);
-    const int tiles = tx * tx;
-    const int target = 4 * 152;
-    int groups = std::max(1, std::min(g->desc.n_det, ceil_div(target, tiles)));
-    const int per = ceil_div(g->desc.n_det, groups);
-    groups = ceil_div(g->desc.n_det, per);
-    AdjArgs a;
-    a.g = g->view;
-    a.y = y;
-    a.out = out;
-    a.padded = padded ? 1 : 0;
-    a.tiles_x = tx;
-    a.dets_per_group = per;
-    a.xmin = (float)g->desc.xmin;
-    a.ymin = (float)g->desc.ymin;
-    a.hx = (float)((g->desc.xmax - g->desc.xmin) / N);
-    a.hy = (float)((g->desc.ymax - g->desc.ymin) / N);
-    a.stop = stop;
-    k_adjoint_tiles<<<dim3(tiles, groups), ATHREADS, 0, st>>>(a);
-    PAT_LAUNCH_CHECK("k_adjoint_tiles");
-    return PAT_OK;
+// out[i] = sum over the detector groups of the partial images (fixed order)
+__global__ void k_sum_parts(const float* __restrict__ parts, int groups, int N, float* __restrict__ out) {
+    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (gx >= N || gy >= N) return;
+    const size_t P2 = (size_t)(N + 2) * (N + 2), o = (size_t)(gy + 1) * (N + 2) + gx + 1;
+    float v = 0.f;
+    for (int gr = 0; gr < groups; ++gr) v += parts[gr * P2 + o];
+    out[(size_t)gy * N + gx] = v;
+}
+
+// max of K^T 1 over each K^T tile, with headroom for the FP32 rounding of the terms
+__global__ void k_tile_kmax(const float* __restrict__ kcol, int N, int tiles_x, float* __restrict__ tile_kmax) {
+    const int t = blockIdx.x;
+    const int x0 = (t % tiles_x) * ATILE, y0 = (t / tiles_x) * ATILE;
+    float m = 0.f;
+    for (int c = threadIdx.x; c < ATILE * ATILE; c += blockDim.x) {
+        const int gx = x0 + c % ATILE, gy = y0 + c / ATILE;
+        if (gx < N && gy < N) m = fmaxf(m, kcol[(size_t)gy * N + gx]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    __shared__ float wm[32];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) m = fmaxf(m, wm[w]);
+        tile_kmax[t] = m * 1.0001f;
+    }
 }
 
 // Row sums K 1 (FP64 accumulation) and column sums K^T 1 (FP64 atomics) of the
@@ -338,7 +301,7 @@ __global__ void __launch_bounds__(128) k_precond_sums(GeomView g, float* __restr
     const int d = blockIdx.y;
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const bool valid = k < g.n_t;
-    const int2 w = __ldg(&g.win[d * g.n_kgrp + k / KGRP]);
+    const int2 w = __ldg(&g.win[d * g.n_kgrp + min(k / KGRP, g.n_kgrp - 1)]);
     const float2 det = __ldg(&g.det[d]);
     const float r = valid ? __ldg(&g.rk[k]) : 0.f;
     const double wk = valid ? (double)__ldg(&g.wk[k]) : 0.0;
@@ -372,7 +335,7 @@ __global__ void k_double_to_float(const double* __restrict__ a, float* __restric
 }
 
 static dim3 row_grid(const pat_geometry* g) {
-    return dim3(ceil_div(g->desc.n_t, 128), g->desc.n_det);
+    return dim3(ceil_div(g->desc.n_t, ROWS_PER_BLOCK), g->desc.n_det);
 }
 
 int forward_gap_blocks(const pat_geometry* g) {
@@ -382,16 +345,18 @@ int forward_gap_blocks(const pat_geometry* g) {
 
 int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y, cudaStream_t st) {
     if (padded)
-        k_forward<true><<<row_grid(g), 128, 0, st>>>(g->view, u, y);
+        k_forward<true><<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, u, y);
     else
-        k_forward<false><<<row_grid(g), 128, 0, st>>>(g->view, u, y);
+        k_forward<false><<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, u, y);
     PAT_LAUNCH_CHECK("k_forward");
     return PAT_OK;
 }
 
 int launch_forward_prox(const pat_geometry* g, const float* ubar_pad, float* q, const float* f,
-                        const float* sig_q, float sig_q_scalar, const int* stop, cudaStream_t st) {
-    k_forward_prox<<<row_grid(g), 128, 0, st>>>(g->view, ubar_pad, q, f, sig_q, sig_q_scalar, stop);
+                        const float* sig_q, float sig_q_scalar, unsigned* qmax_bits, const int* stop,
+                        cudaStream_t st) {
+    k_forward_prox<<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, ubar_pad, q, f, sig_q, sig_q_scalar, qmax_bits,
+                                                         stop);
     PAT_LAUNCH_CHECK("k_forward_prox");
     return PAT_OK;
 }
@@ -399,29 +364,60 @@ int launch_forward_prox(const pat_geometry* g, const float* ubar_pad, float* q, 
 int launch_forward_gap(const pat_geometry* g, const float* u, const float* q, const float* f,
                        double* partials, int n_part, const int* stop, cudaStream_t st) {
     (void)n_part;
-    k_forward_gap<<<row_grid(g), 128, 0, st>>>(g->view, u, q, f, partials, stop);
+    k_forward_gap<<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, u, q, f, partials, stop);
     PAT_LAUNCH_CHECK("k_forward_gap");
     return PAT_OK;
 }
 
-int launch_adjoint(const pat_geometry* g, const float* y, float* out, bool padded, cudaStream_t st) {
-    const int N = g->desc.n;
-    const size_t cells = padded ? (size_t)(N + 2) * (N + 2) : (size_t)N * N;
-    PAT_CUDA(cudaMemsetAsync(out, 0, cells * sizeof(float), st));
-    return launch_adjoint_tiles(g, y, out, padded, nullptr, st);
+int launch_absmax(const float* y, long long n, unsigned* out, cudaStream_t st) {
+    k_absmax<<<std::min(4 * 152, ceil_div(n, 256)), 256, 0, st>>>(y, n, out);
+    PAT_LAUNCH_CHECK("k_absmax");
+    return PAT_OK;
 }
 
-// Hot-path K^T q into the zero-bordered accumulator, as two profiled phases.
-int launch_adjoint_phases(const pat_geometry* g, const float* y, float* out_pad, const int* stop, cudaStream_t st) {
-    const int N = g->desc.n;
-    prof_mark(PAT_PHASE_ADJ_CLEAR, st, true);
-    PAT_CUDA(cudaMemsetAsync(out_pad, 0, (size_t)(N + 2) * (N + 2) * sizeof(float), st));
-    prof_mark(PAT_PHASE_ADJ_CLEAR, st, false);
+int launch_adjoint_parts(const pat_geometry* g, const float* y, const unsigned* ymax_bits, float* parts,
+                         const int* stop, cudaStream_t st) {
     prof_mark(PAT_PHASE_ADJOINT, st, true);
-    int rc = launch_adjoint_tiles(g, y, out_pad, true, stop, st);
-    if (rc) return rc;
+    AdjArgs a;
+    a.g = g->view;
+    a.y = y;
+    a.ymax_bits = ymax_bits;
+    a.tile_kmax = g->pc.tile_kmax;
+    a.box = g->adj_box;
+    a.parts = parts;
+    a.tiles_x = g->adj_tiles_x;
+    a.dets_per_group = g->adj_per_group;
+    a.stop = stop;
+    k_adjoint_tiles<<<dim3(g->adj_tiles, g->adj_groups), ATHREADS, 0, st>>>(a);
+    PAT_LAUNCH_CHECK("k_adjoint_tiles");
     prof_mark(PAT_PHASE_ADJOINT, st, false);
     return PAT_OK;
+}
+
+int launch_adjoint(const pat_geometry* g, const float* y, float* out, cudaStream_t st) {
+    int rc = ensure_precond(g, st);
+    if (rc) return rc;
+    const int N = g->desc.n;
+    const size_t P2 = (size_t)(N + 2) * (N + 2), S = (size_t)g->desc.n_det * g->desc.n_t;
+    char* scratch = nullptr;
+    const size_t bytes = 256 + P2 * g->adj_groups * sizeof(float);
+    PAT_CUDA(cudaMallocAsync((void**)&scratch, bytes, st));
+    unsigned* ymax = (unsigned*)scratch;
+    float* parts = (float*)(scratch + 256);
+    rc = cudaMemsetAsync(scratch, 0, bytes, st) == cudaSuccess ? PAT_OK : PAT_ERR_CUDA;
+    if (!rc) {
+        rc = launch_absmax(y, (long long)S, ymax, st);
+        if (!rc) rc = launch_adjoint_parts(g, y, ymax, parts, nullptr, st);
+    }
+    if (!rc) {
+        dim3 blk(32, 8), grd(ceil_div(N, 32), ceil_div(N, 8));
+        k_sum_parts<<<grd, blk, 0, st>>>(parts, g->adj_groups, N, out);
+        count_launch();
+        rc = cudaGetLastError() == cudaSuccess ? PAT_OK : PAT_ERR_CUDA;
+    }
+    cudaFreeAsync(scratch, st);
+    if (rc == PAT_ERR_CUDA) set_error("launch_adjoint: kernel launch failed");
+    return rc;
 }
 
 int ensure_precond(const pat_geometry* gc, cudaStream_t st) {
@@ -435,10 +431,13 @@ int ensure_precond(const pat_geometry* gc, cudaStream_t st) {
     double* tmp = nullptr;
     PAT_CUDA(cudaMallocAsync(&tmp, (size_t)N * N * sizeof(double), st));
     PAT_CUDA(cudaMemsetAsync(tmp, 0, (size_t)N * N * sizeof(double), st));
-    k_precond_sums<<<row_grid(g), 128, 0, st>>>(g->view, g->pc.krow, tmp);
+    k_precond_sums<<<dim3(ceil_div(g->desc.n_t, 128), g->desc.n_det), 128, 0, st>>>(g->view, g->pc.krow, tmp);
     PAT_LAUNCH_CHECK("k_precond_sums");
     k_double_to_float<<<ceil_div((long long)N * N, 256), 256, 0, st>>>(tmp, g->pc.kcol, N * N);
     PAT_LAUNCH_CHECK("k_double_to_float");
+    if (!g->pc.tile_kmax) PAT_CUDA(cudaMalloc(&g->pc.tile_kmax, (size_t)g->adj_tiles * sizeof(float)));
+    k_tile_kmax<<<g->adj_tiles, 256, 0, st>>>(g->pc.kcol, N, g->adj_tiles_x, g->pc.tile_kmax);
+    PAT_LAUNCH_CHECK("k_tile_kmax");
     PAT_CUDA(cudaFreeAsync(tmp, st));
     PAT_CUDA(cudaStreamSynchronize(st));
     g->pc.ready = true;
@@ -456,5 +455,5 @@ extern "C" int pat_forward(const pat_geometry* g, const float* u_dev, float* y_d
 
 extern "C" int pat_adjoint(const pat_geometry* g, const float* y_dev, float* u_dev, void* stream) {
     if (!g || !u_dev || !y_dev) return fail(PAT_ERR_INVALID_ARG, "pat_adjoint: NULL argument");
-    return launch_adjoint(g, y_dev, u_dev, false, (cudaStream_t)stream);
+    return launch_adjoint(g, y_dev, u_dev, (cudaStream_t)stream);
 }
