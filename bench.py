@@ -402,7 +402,7 @@ def main(argv=None) -> int:
     ap.add_argument("--cpu-iters", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttg", action="store_true")
-    ap.add_argument("--ttg-max-iters", type=int, default=30000)
+    ap.add_argument("--ttg-max-iters", type=int, default=60000)
     ap.add_argument("--iters", type=int, default=0,
                     help="override the PDHG iterations per step (short runs for the ncu launch list)")
     ap.add_argument("--no-e2e", action="store_true")

@@ -200,6 +200,19 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     for (int i = 0; i < 2 * d.n_det; ++i)
         if (!std::isfinite(d.det_xy_host[i])) return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: non-finite detector");
 
+    {
+        // every quadrature point must have |fx|, |fy| < 2^24 (continuous pixel
+        // coordinates), so the kernels convert them to integers without clamping
+        double ext = 0;
+        const double rmax = d.r0 + d.n_t * d.dr;
+        const double hx0 = (d.xmax - d.xmin) / d.n, hy0 = (d.ymax - d.ymin) / d.n;
+        for (int i = 0; i < d.n_det; ++i) {
+            ext = std::max(ext, (fabs(d.det_xy_host[2 * i] - d.xmin) + rmax) / hx0 + 1.0);
+            ext = std::max(ext, (fabs(d.det_xy_host[2 * i + 1] - d.ymin) + rmax) / hy0 + 1.0);
+        }
+        if (!(ext < 16777216.0))
+            return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: circles reach more than 2^24 pixels from the grid");
+    }
     pat_geometry* g = new pat_geometry();
     g->desc = d;
     g->desc.det_xy_host = nullptr;  // not retained

@@ -113,9 +113,9 @@ __device__ __forceinline__ bool point_taps(const GeomView& g, float2 det, float 
     const float fly = floorf(fy);
     t.ax = fx - flx;
     t.ay = fy - fly;
-    // clamp before the conversion so that far-away points stay well defined
-    t.i0 = (int)fmaxf(fminf(flx, 1.0e6f), -1.0e6f);
-    t.j0 = (int)fmaxf(fminf(fly, 1.0e6f), -1.0e6f);
+    // geometry creation bounds |fx|, |fy| by 2^24, so the conversions are exact
+    t.i0 = (int)flx;
+    t.j0 = (int)fly;
     return (unsigned)(t.i0 + 1) <= (unsigned)g.n && (unsigned)(t.j0 + 1) <= (unsigned)g.n;
 }
 

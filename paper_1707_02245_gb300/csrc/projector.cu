@@ -217,6 +217,13 @@ __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
     for (int c = tid; c < AW * AW; c += ATHREADS) acc[c] = 0;
     const float bound = __uint_as_float(*a.ymax_bits) * __ldg(&a.tile_kmax[tile]);
     const float scale = 1073741824.0f / bound;  // 2^30 / bound
+    // tap region of the tile in world coordinates (fx in [x0 - 1, x0 + ATILE)), widened
+    // by 1e-3 pixel so FP32 rounding never drops a candidate
+    const float hx = 1.f / g.inv_hx, hy = 1.f / g.inv_hy;
+    const float rx0 = (x0 - 1.001f - g.ox) * hx, rx1 = (x0 + ATILE + 0.001f - g.ox) * hx;
+    const float ry0 = (y0 - 1.001f - g.oy) * hy, ry1 = (y0 + ATILE + 0.001f - g.oy) * hy;
+    const float r_first = __ldg(&g.rk[0]);
+    const float inv_dr = T > 1 ? (float)(T - 1) / (__ldg(&g.rk[T - 1]) - r_first) : 0.f;
     __syncthreads();
 
     if (bound > 0.f && isfinite(bound)) {
@@ -236,7 +243,18 @@ __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
                 int m = m0 + mm;
                 if (m >= M) m -= M;
                 const float2 cs = __ldg(&g.cs[m]);
-                for (int k = kb; k < ke; ++k) {
+                // the ray from the detector at angle phi_m meets the (convex) tap region in
+                // one segment [t0, t1]; only radii within it (+-1 index) can touch the tile
+                const float ic = 1.f / cs.x, is = 1.f / cs.y;
+                const float tx0 = (rx0 - det.x) * ic, tx1 = (rx1 - det.x) * ic;
+                const float ty0 = (ry0 - det.y) * is, ty1 = (ry1 - det.y) * is;
+                const float t0 = fmaxf(fminf(tx0, tx1), fminf(ty0, ty1));
+                const float t1 = fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1));
+                if (t1 < t0) continue;  // misses (NaN compares false: keep the box)
+                const float kf0 = (t0 - r_first) * inv_dr, kf1 = (t1 - r_first) * inv_dr;
+                const int kr0 = isfinite(kf0) ? max(kb, (int)floorf(fmaxf(kf0, -1e9f)) - 1) : kb;
+                const int kr1 = isfinite(kf1) ? min(ke, (int)ceilf(fminf(kf1, 1e9f)) + 2) : ke;
+                for (int k = kr0; k < kr1; ++k) {
                     Taps t;
                     if (!point_taps(g, det, __ldg(&g.rk[k]), cs, t)) continue;
                     const int li = t.i0 - x0 + 1, lj = t.j0 - y0 + 1;
