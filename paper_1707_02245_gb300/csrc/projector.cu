@@ -182,9 +182,10 @@ __global__ void __launch_bounds__(ROW_THREADS) k_forward_gap(GeomView g, const f
 // deterministic) replaces floating-point atomics.  The resolution 2^-30 of that bound is
 // finer than FP32 accumulation of the same terms.  Ring cells may wrap; they are dropped.
 //
-// Candidates: one warp per detector walks the (k, m) box precomputed for (tile, detector)
-// at geometry creation; its lanes split into contiguous chunks of radii times
-// consecutive angles, so lanes that add at the same time touch distinct pixels.  Every
+// Candidates: one warp per detector takes the (k, m) box precomputed for (tile, detector)
+// at geometry creation, cuts every ray of the box down to its segment inside the tile's
+// tap region, and splits the concatenated segments into 32 equal contiguous runs, one per
+// lane, so lanes that add at the same time sit on different rays.  Every
 // candidate uses the forward projector's FP32 position and tap arithmetic, so the CTA
 // adds exactly the entries of K^T that belong to its pixels.  Each detector group writes
 // its partial tile with plain stores; consumers add the groups in a fixed order.
@@ -226,47 +227,83 @@ __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
     const float inv_dr = T > 1 ? (float)(T - 1) / (__ldg(&g.rk[T - 1]) - r_first) : 0.f;
     __syncthreads();
 
+    // per-warp ray table: for up to 32 rays, the first radius of the ray's candidate
+    // segment, the segment length, its exclusive prefix in the warp's flattened list
+    __shared__ int s_m[ATHREADS / 32][32], s_ks[ATHREADS / 32][32], s_ex[ATHREADS / 32][33];
     if (bound > 0.f && isfinite(bound)) {
         for (int d = d_begin + warp; d < d_end; d += ATHREADS / 32) {
             const int4 bx = __ldg(&a.box[(size_t)tile * D + d]);
-            const int k0 = bx.x, nk = bx.y, m0 = bx.z, nm = bx.w;
-            if (nm <= 0 || nk <= 0) continue;
-            const int per = nm < 32 ? nm : 32;
-            const int groups = 32 / per;
-            const int grp = lane / per, mo = lane - grp * per;
-            if (grp >= groups) continue;
-            const int chunk = (nk + groups - 1) / groups;
-            const int kb = k0 + grp * chunk, ke = min(k0 + nk, kb + chunk);
+            const int kb = bx.x, ke = bx.x + bx.y, m0 = bx.z, nm = bx.w;
+            if (nm <= 0 || bx.y <= 0) continue;
             const float2 det = __ldg(&g.det[d]);
             const float* yrow = a.y + (size_t)d * T;
-            for (int mm = mo; mm < nm; mm += per) {
-                int m = m0 + mm;
-                if (m >= M) m -= M;
-                const float2 cs = __ldg(&g.cs[m]);
-                // the ray from the detector at angle phi_m meets the (convex) tap region in
-                // one segment [t0, t1]; only radii within it (+-1 index) can touch the tile
-                const float ic = 1.f / cs.x, is = 1.f / cs.y;
-                const float tx0 = (rx0 - det.x) * ic, tx1 = (rx1 - det.x) * ic;
-                const float ty0 = (ry0 - det.y) * is, ty1 = (ry1 - det.y) * is;
-                const float t0 = fmaxf(fminf(tx0, tx1), fminf(ty0, ty1));
-                const float t1 = fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1));
-                if (t1 < t0) continue;  // misses (NaN compares false: keep the box)
-                const float kf0 = (t0 - r_first) * inv_dr, kf1 = (t1 - r_first) * inv_dr;
-                const int kr0 = isfinite(kf0) ? max(kb, (int)floorf(fmaxf(kf0, -1e9f)) - 1) : kb;
-                const int kr1 = isfinite(kf1) ? min(ke, (int)ceilf(fminf(kf1, 1e9f)) + 2) : ke;
-                for (int k = kr0; k < kr1; ++k) {
-                    Taps t;
-                    if (!point_taps(g, det, __ldg(&g.rk[k]), cs, t)) continue;
-                    const int li = t.i0 - x0 + 1, lj = t.j0 - y0 + 1;
-                    if ((unsigned)li > (unsigned)ATILE || (unsigned)lj > (unsigned)ATILE) continue;
-                    const float c = __ldg(&yrow[k]) * __ldg(&g.wk[k]) * scale;
-                    const float c0 = c * (1.f - t.ay), c1 = c * t.ay;
-                    int* p = acc + lj * AW + li;
-                    atomicAdd(p, __float2int_rn(c0 * (1.f - t.ax)));
-                    atomicAdd(p + 1, __float2int_rn(c0 * t.ax));
-                    atomicAdd(p + AW, __float2int_rn(c1 * (1.f - t.ax)));
-                    atomicAdd(p + AW + 1, __float2int_rn(c1 * t.ax));
+            for (int mb = 0; mb < nm; mb += 32) {
+                // 1. lane j finds the radius interval of ray mb + j: the ray meets the
+                //    (convex) tap region in one segment [t0, t1]
+                int len = 0, ks = 0, m = 0;
+                if (mb + lane < nm) {
+                    m = m0 + mb + lane;
+                    if (m >= M) m -= M;
+                    const float2 cs = __ldg(&g.cs[m]);
+                    const float ic = 1.f / cs.x, is = 1.f / cs.y;
+                    const float tx0 = (rx0 - det.x) * ic, tx1 = (rx1 - det.x) * ic;
+                    const float ty0 = (ry0 - det.y) * is, ty1 = (ry1 - det.y) * is;
+                    const float t0 = fmaxf(fminf(tx0, tx1), fminf(ty0, ty1));
+                    const float t1 = fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1));
+                    if (!(t1 < t0)) {  // NaN keeps the whole box
+                        const float kf0 = (t0 - r_first) * inv_dr, kf1 = (t1 - r_first) * inv_dr;
+                        const int kr0 = isfinite(kf0) ? max(kb, (int)floorf(fmaxf(kf0, -1e9f)) - 1) : kb;
+                        const int kr1 = isfinite(kf1) ? min(ke, (int)ceilf(fminf(kf1, 1e9f)) + 2) : ke;
+                        len = max(0, kr1 - kr0);
+                        ks = kr0;
+                    }
                 }
+                // 2. exclusive prefix of the segment lengths over the warp
+                int pre = len;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, pre, o);
+                    if (lane >= o) pre += v;
+                }
+                const int total = __shfl_sync(0xffffffffu, pre, 31);
+                s_m[warp][lane] = m;
+                s_ks[warp][lane] = ks;
+                s_ex[warp][lane] = pre - len;
+                if (lane == 31) s_ex[warp][32] = total;
+                __syncwarp();
+                // 3. lane l takes the contiguous run [l C, (l+1) C) of the flattened list:
+                //    simultaneous lanes sit C candidates apart on different rays
+                const int C = (total + 31) >> 5;
+                const int p0 = lane * C, p1 = min(total, p0 + C);
+                if (p0 < p1) {
+                    int j = 0;  // last ray whose prefix is <= p0 (it contains p0)
+#pragma unroll
+                    for (int step = 16; step > 0; step >>= 1)
+                        if (j + step < 32 && s_ex[warp][j + step] <= p0) j += step;
+                    int seg_end = s_ex[warp][j + 1];
+                    int k = s_ks[warp][j] + (p0 - s_ex[warp][j]);
+                    float2 cs = __ldg(&g.cs[s_m[warp][j]]);
+                    for (int pp = p0; pp < p1; ++pp, ++k) {
+                        while (pp == seg_end) {  // next non-empty ray
+                            ++j;
+                            seg_end = s_ex[warp][j + 1];
+                            k = s_ks[warp][j];
+                            cs = __ldg(&g.cs[s_m[warp][j]]);
+                        }
+                        Taps t;
+                        if (!point_taps(g, det, __ldg(&g.rk[k]), cs, t)) continue;
+                        const int li = t.i0 - x0 + 1, lj = t.j0 - y0 + 1;
+                        if ((unsigned)li > (unsigned)ATILE || (unsigned)lj > (unsigned)ATILE) continue;
+                        const float c = __ldg(&yrow[k]) * __ldg(&g.wk[k]) * scale;
+                        const float c0 = c * (1.f - t.ay), c1 = c * t.ay;
+                        int* q = acc + lj * AW + li;
+                        atomicAdd(q, __float2int_rn(c0 * (1.f - t.ax)));
+                        atomicAdd(q + 1, __float2int_rn(c0 * t.ax));
+                        atomicAdd(q + AW, __float2int_rn(c1 * (1.f - t.ax)));
+                        atomicAdd(q + AW + 1, __float2int_rn(c1 * t.ax));
+                    }
+                }
+                __syncwarp();
             }
         }
     }
