@@ -61,7 +61,7 @@ struct GeomView {
 
 constexpr int KGRP = 8;        // radii per angular-window group
 constexpr int MAX_QUAD_M = 8192;
-constexpr int ATILE = 16;      // K^T pixel tile side
+constexpr int ATILE = 32;      // K^T pixel tile side
 
 struct PrecondCache {
     float* krow = nullptr;      // K 1 per data row (S), summed in FP64
@@ -129,11 +129,12 @@ int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y,
 int launch_adjoint(const pat_geometry* g, const float* y, float* out, cudaStream_t st);
 // Hot-path K^T q: adj_groups partial images in the zero-bordered (N+2)^2 layout,
 // parts[grp * (N+2)^2 + ...]; ymax_bits holds max |q| as float bits.
-int launch_adjoint_parts(const pat_geometry* g, const float* y, const unsigned* ymax_bits, float* parts,
-                         const int* stop, cudaStream_t st);
+// premul (optional): y_k times the arc weight w_k, read instead of y and w.
+int launch_adjoint_parts(const pat_geometry* g, const float* y, const float* premul, const unsigned* ymax_bits,
+                         float* parts, const int* stop, cudaStream_t st);
 int launch_forward_prox(const pat_geometry* g, const float* ubar_pad, float* q, const float* f,
-                        const float* sig_q, float sig_q_scalar, unsigned* qmax_bits, const int* stop,
-                        cudaStream_t st);
+                        const float* sig_q, float sig_q_scalar, float* qw, unsigned* qmax_bits,
+                        const int* stop, cudaStream_t st);
 int launch_forward_gap(const pat_geometry* g, const float* u, const float* q, const float* f,
                        double* partials, int n_part, const int* stop, cudaStream_t st);
 int forward_gap_blocks(const pat_geometry* g);

@@ -581,7 +581,7 @@ struct Workspace {
     float* X[2] = {nullptr, nullptr};
     float* Y[2] = {nullptr, nullptr};
     float *q = nullptr, *ubar_pad = nullptr, *w_parts = nullptr, *vbar0 = nullptr;
-    float *tau_u = nullptr, *sig_q = nullptr, *sig_r = nullptr;
+    float *tau_u = nullptr, *sig_q = nullptr, *sig_r = nullptr, *qw = nullptr;
     double *data_part = nullptr, *pix_part = nullptr;
     InfoDev* info = nullptr;
     int n_data = 0, n_pix = 0;
@@ -598,9 +598,10 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     size_t off[16];
     size_t sz[16] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, P2 * 4 * g->adj_groups,
                      (reg == PAT_TGV ? 2 * NN : 1) * 4,
-                     NN * 4, S * 4, NN * 4, (size_t)ws.n_data * 3 * 8, (size_t)ws.n_pix * 6 * 8, sizeof(InfoDev)};
+                     NN * 4, S * 4, NN * 4, (size_t)ws.n_data * 3 * 8, (size_t)ws.n_pix * 6 * 8, sizeof(InfoDev),
+                     S * 4};
     size_t total = 0;
-    for (int i = 0; i < 14; ++i) {
+    for (int i = 0; i < 15; ++i) {
         off[i] = total;
         total += align_up(sz[i]);
     }
@@ -621,6 +622,7 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     ws.data_part = (double*)(b + off[11]);
     ws.pix_part = (double*)(b + off[12]);
     ws.info = (InfoDev*)(b + off[13]);
+    ws.qw = (float*)(b + off[14]);
     return PAT_OK;
 }
 
@@ -722,11 +724,11 @@ static int enqueue_iterations(const pat_geometry* g, const float* f, const pat_p
     const int* stop = &ws.info->stop;
     for (int it = it0; it < it0 + count; ++it) {
         prof_mark(PAT_PHASE_FORWARD_PROX, st, true);
-        int rc = launch_forward_prox(g, ws.ubar_pad, ws.q, f, sc.sig_q >= 0 ? nullptr : ws.sig_q, sc.sig_q,
+        int rc = launch_forward_prox(g, ws.ubar_pad, ws.q, f, sc.sig_q >= 0 ? nullptr : ws.sig_q, sc.sig_q, ws.qw,
                                      &ws.info->qmax_bits, stop, st);
         if (rc) return rc;
         prof_mark(PAT_PHASE_FORWARD_PROX, st, false);
-        rc = launch_adjoint_parts(g, ws.q, &ws.info->qmax_bits, ws.w_parts, stop, st);
+        rc = launch_adjoint_parts(g, ws.q, ws.qw, &ws.info->qmax_bits, ws.w_parts, stop, st);
         if (rc) return rc;
         prof_mark(PAT_PHASE_UPDATE, st, true);
         rc = launch_update<REG>(g, p, ws, sc, it, st);
@@ -1089,7 +1091,7 @@ static int gap_impl(const pat_geometry* g, const float* f, const pat_params* p, 
     if (!rc) {
         const long long S_ = (long long)g->desc.n_det * g->desc.n_t;
         rc = launch_absmax(y, S_, &ws.info->qmax_bits, st);
-        if (!rc) rc = launch_adjoint_parts(g, y, &ws.info->qmax_bits, ws.w_parts, nullptr, st);
+        if (!rc) rc = launch_adjoint_parts(g, y, nullptr, &ws.info->qmax_bits, ws.w_parts, nullptr, st);
     }
     pat_params q = *p;
     q.tol = 0;

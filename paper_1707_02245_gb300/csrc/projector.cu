@@ -104,6 +104,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_forward(GeomView g, const float
 __global__ void __launch_bounds__(ROW_THREADS) k_forward_prox(GeomView g, const float* __restrict__ ubar_pad,
                                                              float* __restrict__ q, const float* __restrict__ f,
                                                              const float* __restrict__ sig_q, float sig_scalar,
+                                                             float* __restrict__ qw,
                                                              unsigned* __restrict__ qmax_bits,
                                                              const int* __restrict__ stop) {
     if (stop && *(volatile const int*)stop) return;
@@ -112,10 +113,12 @@ __global__ void __launch_bounds__(ROW_THREADS) k_forward_prox(GeomView g, const 
     float aq = 0.f;
     if (rl.valid && rl.ph == 0) {
         const size_t i = (size_t)rl.d * g.n_t + rl.k;
-        const float ku = s * __ldg(&g.wk[rl.k]);
+        const float wk = __ldg(&g.wk[rl.k]);
+        const float ku = s * wk;
         const float sg = sig_q ? sig_q[i] : sig_scalar;
         const float qn = (q[i] + sg * (ku - f[i])) / (1.f + sg);
         q[i] = qn;
+        qw[i] = qn * wk;   // the K^T that follows reads q_k w_k
         aq = fabsf(qn);
     }
     // block max of |q| (a NaN's bits compare greater than every finite value's)
@@ -194,7 +197,8 @@ constexpr int ATHREADS = 256;
 
 struct AdjArgs {
     GeomView g;
-    const float* y;
+    const float* y;          // data rows, or data rows times the arc weights (premul)
+    int premul;
     const unsigned* ymax_bits;
     const float* tile_kmax;
     const int4* box;
@@ -294,7 +298,7 @@ __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
                         if (!point_taps(g, det, __ldg(&g.rk[k]), cs, t)) continue;
                         const int li = t.i0 - x0 + 1, lj = t.j0 - y0 + 1;
                         if ((unsigned)li > (unsigned)ATILE || (unsigned)lj > (unsigned)ATILE) continue;
-                        const float c = __ldg(&yrow[k]) * __ldg(&g.wk[k]) * scale;
+                        const float c = (a.premul ? __ldg(&yrow[k]) : __ldg(&yrow[k]) * __ldg(&g.wk[k])) * scale;
                         const float c0 = c * (1.f - t.ay), c1 = c * t.ay;
                         int* q = acc + lj * AW + li;
                         atomicAdd(q, __float2int_rn(c0 * (1.f - t.ax)));
@@ -408,10 +412,10 @@ int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y,
 }
 
 int launch_forward_prox(const pat_geometry* g, const float* ubar_pad, float* q, const float* f,
-                        const float* sig_q, float sig_q_scalar, unsigned* qmax_bits, const int* stop,
-                        cudaStream_t st) {
-    k_forward_prox<<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, ubar_pad, q, f, sig_q, sig_q_scalar, qmax_bits,
-                                                         stop);
+                        const float* sig_q, float sig_q_scalar, float* qw, unsigned* qmax_bits,
+                        const int* stop, cudaStream_t st) {
+    k_forward_prox<<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, ubar_pad, q, f, sig_q, sig_q_scalar, qw,
+                                                         qmax_bits, stop);
     PAT_LAUNCH_CHECK("k_forward_prox");
     return PAT_OK;
 }
@@ -430,12 +434,13 @@ int launch_absmax(const float* y, long long n, unsigned* out, cudaStream_t st) {
     return PAT_OK;
 }
 
-int launch_adjoint_parts(const pat_geometry* g, const float* y, const unsigned* ymax_bits, float* parts,
-                         const int* stop, cudaStream_t st) {
+int launch_adjoint_parts(const pat_geometry* g, const float* y, const float* premul, const unsigned* ymax_bits,
+                         float* parts, const int* stop, cudaStream_t st) {
     prof_mark(PAT_PHASE_ADJOINT, st, true);
     AdjArgs a;
     a.g = g->view;
-    a.y = y;
+    a.y = premul ? premul : y;
+    a.premul = premul ? 1 : 0;
     a.ymax_bits = ymax_bits;
     a.tile_kmax = g->pc.tile_kmax;
     a.box = g->adj_box;
@@ -462,7 +467,7 @@ int launch_adjoint(const pat_geometry* g, const float* y, float* out, cudaStream
     rc = cudaMemsetAsync(scratch, 0, bytes, st) == cudaSuccess ? PAT_OK : PAT_ERR_CUDA;
     if (!rc) {
         rc = launch_absmax(y, (long long)S, ymax, st);
-        if (!rc) rc = launch_adjoint_parts(g, y, ymax, parts, nullptr, st);
+        if (!rc) rc = launch_adjoint_parts(g, y, nullptr, ymax, parts, nullptr, st);
     }
     if (!rc) {
         dim3 blk(32, 8), grd(ceil_div(N, 32), ceil_div(N, 8));
