@@ -321,9 +321,8 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     g->adj_tiles_x = tiles_x;
     g->adj_tiles = tiles;
     {
-        const int target = 4 * 152;  // CTAs to fill the GPU a few times over
+        const int target = 8 * 152;  // CTAs to fill the GPU several times over
         int groups = std::max(1, std::min(D, (target + tiles - 1) / tiles));
-        groups = std::min(groups, 8);
         const int per = (D + groups - 1) / groups;
         g->adj_per_group = per;
         g->adj_groups = (D + per - 1) / per;

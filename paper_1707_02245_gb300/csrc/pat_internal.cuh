@@ -119,19 +119,34 @@ __device__ __forceinline__ bool point_taps(const GeomView& g, float2 det, float 
     return (unsigned)(t.i0 + 1) <= (unsigned)g.n && (unsigned)(t.j0 + 1) <= (unsigned)g.n;
 }
 
+// K^T y held as int32 fixed point: pixel p stores round((K^T y)(p) * S_t) with the
+// per-tile scale S_t = 2^30 / (max|y| * max over tile t of K^T 1).
+struct KtView {
+    const int* acc;             // N*N
+    const unsigned* ymax_bits;  // max |y| as float bits
+    const float* tile_kmax;     // per tile
+    int tiles_x;
+    __device__ __forceinline__ float at(int gx, int gy, int N) const {
+        const float bound = __uint_as_float(*ymax_bits) * __ldg(&tile_kmax[(gy / ATILE) * tiles_x + gx / ATILE]);
+        const float inv = bound > 0.f ? bound * 9.313225746154785e-10f : (bound == 0.f ? 0.f : bound);
+        return (float)__ldg(&acc[(size_t)gy * N + gx]) * inv;
+    }
+};
+
 // Launch helpers
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
 // Host entry points implemented in projector.cu and used by pdhg.cu
 int ensure_precond(const pat_geometry* g, cudaStream_t st);
 int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y, cudaStream_t st);
-// K^T y into an N*N image (allocates its scratch from the stream-ordered pool).
+// K^T y into an N*N float image (allocates its scratch from the stream-ordered pool).
 int launch_adjoint(const pat_geometry* g, const float* y, float* out, cudaStream_t st);
-// Hot-path K^T q: adj_groups partial images in the zero-bordered (N+2)^2 layout,
-// parts[grp * (N+2)^2 + ...]; ymax_bits holds max |q| as float bits.
-// premul (optional): y_k times the arc weight w_k, read instead of y and w.
-int launch_adjoint_parts(const pat_geometry* g, const float* y, const float* premul, const unsigned* ymax_bits,
-                         float* parts, const int* stop, cudaStream_t st);
+// Hot-path K^T q accumulated into the fixed-point image acc (N*N int32, zero on entry);
+// ymax_bits holds max |y| as float bits; premul (optional) holds y_k times the arc
+// weight w_k and is read instead of y and w.
+int launch_adjoint_fixed(const pat_geometry* g, const float* y, const float* premul, const unsigned* ymax_bits,
+                         int* acc, const int* stop, cudaStream_t st);
+KtView kt_view(const pat_geometry* g, const int* acc, const unsigned* ymax_bits);
 int launch_forward_prox(const pat_geometry* g, const float* ubar_pad, float* q, const float* f,
                         const float* sig_q, float sig_q_scalar, float* qw, unsigned* qmax_bits,
                         const int* stop, cudaStream_t st);

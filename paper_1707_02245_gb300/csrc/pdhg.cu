@@ -37,9 +37,9 @@ struct UpdateArgs {
     const float* tau_u;    // N*N (diagonal rule)
     const float* sig_r;    // N*N (dTV diagonal rule)
     const float* xi;       // 2*N*N (dTV)
-    const float* w_parts;  // K^T q as `groups` partial images, (N+2)^2 each
-    int groups;
-    unsigned* qmax_bits;   // max |q| of this iteration; reset here for the next one
+    KtView kt;             // K^T q of this iteration (fixed point)
+    int* kt_clear;         // the other fixed-point buffer, cleared here for the next iteration
+    unsigned* qmax_next;   // max |q| slot of the next iteration, reset here
     const float* x_in;     // u, v1, v2
     const float* y_in;     // r1, r2, s11, s22, s12
     float* x_out;
@@ -113,9 +113,7 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
             if (in) {
                 const int gi = gy * N + gx;
                 const float divr = s_r1m[ly][lx] - s_r1m[ly][lx - 1] + s_r2m[ly][lx] - s_r2m[ly - 1][lx];
-                float w = 0.f;
-                const size_t wo = (size_t)(gy + 1) * (N + 2) + gx + 1, P2 = (size_t)(N + 2) * (N + 2);
-                for (int gr = 0; gr < a.groups; ++gr) w += __ldg(a.w_parts + gr * P2 + wo);
+                const float w = a.kt.at(gx, gy, N);
                 const float uo = __ldg(u_in + gi);
                 const float tu = a.tau >= 0.f ? a.tau : __ldg(a.tau_u + gi);
                 const float un = uo - tu * (w - divr);
@@ -207,9 +205,10 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
             a.x_out[2 * NN + gi] = s_vn2[threadIdx.y][threadIdx.x];
         }
     }
+    if (gx < N && gy < N) a.kt_clear[gy * N + gx] = 0;
     if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
         if (a.iter) *a.iter += 1;
-        if (a.qmax_bits) *a.qmax_bits = 0u;
+        *a.qmax_next = 0u;
     }
 }
 
@@ -287,8 +286,7 @@ struct GapArgs {
     const float* x;       // x^{n+1}
     const float* x_old;   // x^n (NULL: residual terms are zero)
     const float* y;       // r, s at the same evaluation (y^{n+1})
-    const float* w_parts; // K^T q^{n+1} as `groups` partial images
-    int groups;
+    KtView kt;            // K^T q^{n+1} (fixed point)
     double* partials;
     const int* stop;
 };
@@ -339,13 +337,7 @@ __global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
             return c == 0 ? r0 : r1;
         };
         const double divr = rm(0, gx, gy) - rm(0, gx - 1, gy) + rm(1, gx, gy) - rm(1, gx, gy - 1);
-        double w = 0.0;
-        {
-            const size_t wo = (size_t)(gy + 1) * (N + 2) + gx + 1, P2 = (size_t)(N + 2) * (N + 2);
-            float wf = 0.f;
-            for (int gr = 0; gr < a.groups; ++gr) wf += a.w_parts[gr * P2 + wo];
-            w = (double)wf;
-        }
+        const double w = (double)a.kt.at(gx, gy, N);
         acc[2] += fabs(w - divr);
         if (REG == PAT_TGV) {
             auto vm = [&](int c, int x, int y, bool mx) -> double {  // masked v for d^-
@@ -383,7 +375,7 @@ __global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
 struct InfoDev {
     double primal, dual, gap, rel_gap, residual;
     int iters_done, status, stop, iter;
-    unsigned qmax_bits;   // max |q| of the current iteration (float bits)
+    unsigned qmax_bits[2];  // max |q| of iterations of each parity (float bits)
 };
 
 struct FinalArgs {
@@ -580,7 +572,8 @@ struct Workspace {
     size_t bytes = 0;
     float* X[2] = {nullptr, nullptr};
     float* Y[2] = {nullptr, nullptr};
-    float *q = nullptr, *ubar_pad = nullptr, *w_parts = nullptr, *vbar0 = nullptr;
+    float *q = nullptr, *ubar_pad = nullptr, *vbar0 = nullptr;
+    int* kt[2] = {nullptr, nullptr};   // fixed-point K^T q, by iteration parity
     float *tau_u = nullptr, *sig_q = nullptr, *sig_r = nullptr, *qw = nullptr;
     double *data_part = nullptr, *pix_part = nullptr;
     InfoDev* info = nullptr;
@@ -596,7 +589,7 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     ws.n_data = forward_gap_blocks(g);
     ws.n_pix = pix_blocks((int)N);
     size_t off[16];
-    size_t sz[16] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, P2 * 4 * g->adj_groups,
+    size_t sz[16] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, NN * 4 * 2,
                      (reg == PAT_TGV ? 2 * NN : 1) * 4,
                      NN * 4, S * 4, NN * 4, (size_t)ws.n_data * 3 * 8, (size_t)ws.n_pix * 6 * 8, sizeof(InfoDev),
                      S * 4};
@@ -614,7 +607,8 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     ws.Y[1] = (float*)(b + off[3]);
     ws.q = (float*)(b + off[4]);
     ws.ubar_pad = (float*)(b + off[5]);
-    ws.w_parts = (float*)(b + off[6]);
+    ws.kt[0] = (int*)(b + off[6]);
+    ws.kt[1] = ws.kt[0] + NN;
     ws.vbar0 = (float*)(b + off[7]);
     ws.tau_u = (float*)(b + off[8]);
     ws.sig_q = (float*)(b + off[9]);
@@ -658,9 +652,9 @@ static int compute_steps(const pat_geometry* g, const pat_params* p, Workspace& 
                          cudaStream_t st) {
     const int N = g->desc.n;
     const long long S = (long long)g->desc.n_det * g->desc.n_t;
-    if (p->precond == PAT_PRECOND_SCALAR2) return scalar2_steps(g, p, sc, st);
-    int rc = ensure_precond(g, st);
+    int rc = ensure_precond(g, st);  // K sums also scale the fixed-point K^T
     if (rc) return rc;
+    if (p->precond == PAT_PRECOND_SCALAR2) return scalar2_steps(g, p, sc, st);
     k_sig_q<<<ceil_div(S, 256), 256, 0, st>>>(g->pc.krow, ws.sig_q, S);
     PAT_LAUNCH_CHECK("k_sig_q");
     StepArgs sa{N, p->reg, p->gamma, g->pc.kcol, p->xi_dev, ws.tau_u, p->reg == PAT_DTV ? ws.sig_r : nullptr,
@@ -686,9 +680,9 @@ static int launch_update(const pat_geometry* g, const pat_params* p, Workspace& 
     a.tau_u = ws.tau_u;
     a.sig_r = ws.sig_r;
     a.xi = p->xi_dev;
-    a.w_parts = ws.w_parts;
-    a.groups = g->adj_groups;
-    a.qmax_bits = &ws.info->qmax_bits;
+    a.kt = kt_view(g, ws.kt[it & 1], &ws.info->qmax_bits[it & 1]);
+    a.kt_clear = ws.kt[(it + 1) & 1];
+    a.qmax_next = &ws.info->qmax_bits[(it + 1) & 1];
     a.x_in = ws.X[it & 1];
     a.y_in = ws.Y[it & 1];
     a.x_out = ws.X[(it + 1) & 1];
@@ -703,12 +697,13 @@ static int launch_update(const pat_geometry* g, const pat_params* p, Workspace& 
 }
 
 template <int REG>
-static int launch_gap(const pat_geometry* g, const pat_params* p, Workspace& ws, const float* x, const float* x_old,
-                      const float* y, const float* q, const float* f, const int* stop, cudaStream_t st) {
+static int launch_gap(const pat_geometry* g, const pat_params* p, Workspace& ws, const KtView& kt, const float* x,
+                      const float* x_old, const float* y, const float* q, const float* f, const int* stop,
+                      cudaStream_t st) {
     const int N = g->desc.n;
     int rc = launch_forward_gap(g, x, q, f, ws.data_part, ws.n_data, stop, st);
     if (rc) return rc;
-    GapArgs ga{N, p->gamma, p->xi_dev, x, x_old, y, ws.w_parts, g->adj_groups, ws.pix_part, stop};
+    GapArgs ga{N, p->gamma, p->xi_dev, x, x_old, y, kt, ws.pix_part, stop};
     k_gap_pixels<REG><<<ws.n_pix, 256, 0, st>>>(ga);
     PAT_LAUNCH_CHECK("k_gap_pixels");
     FinalArgs fa{ws.data_part, ws.n_data, ws.pix_part, ws.n_pix, p->alpha, p->beta, p->box_u, p->box_v,
@@ -725,10 +720,10 @@ static int enqueue_iterations(const pat_geometry* g, const float* f, const pat_p
     for (int it = it0; it < it0 + count; ++it) {
         prof_mark(PAT_PHASE_FORWARD_PROX, st, true);
         int rc = launch_forward_prox(g, ws.ubar_pad, ws.q, f, sc.sig_q >= 0 ? nullptr : ws.sig_q, sc.sig_q, ws.qw,
-                                     &ws.info->qmax_bits, stop, st);
+                                     &ws.info->qmax_bits[it & 1], stop, st);
         if (rc) return rc;
         prof_mark(PAT_PHASE_FORWARD_PROX, st, false);
-        rc = launch_adjoint_parts(g, ws.q, ws.qw, &ws.info->qmax_bits, ws.w_parts, stop, st);
+        rc = launch_adjoint_fixed(g, ws.q, ws.qw, &ws.info->qmax_bits[it & 1], ws.kt[it & 1], stop, st);
         if (rc) return rc;
         prof_mark(PAT_PHASE_UPDATE, st, true);
         rc = launch_update<REG>(g, p, ws, sc, it, st);
@@ -737,7 +732,8 @@ static int enqueue_iterations(const pat_geometry* g, const float* f, const pat_p
         const int done = it + 1;
         if ((p->gap_every > 0 && done % p->gap_every == 0) || done == p->iters) {
             prof_mark(PAT_PHASE_GAP, st, true);
-            rc = launch_gap<REG>(g, p, ws, ws.X[done & 1], ws.X[it & 1], ws.Y[it & 1], ws.q, f, stop, st);
+            rc = launch_gap<REG>(g, p, ws, kt_view(g, ws.kt[it & 1], &ws.info->qmax_bits[it & 1]), ws.X[done & 1],
+                                 ws.X[it & 1], ws.Y[it & 1], ws.q, f, stop, st);
             if (rc) return rc;
             prof_mark(PAT_PHASE_GAP, st, false);
         }
@@ -779,6 +775,7 @@ static int run_reconstruct(const pat_geometry* g, const float* f, const pat_para
         }
     }
     if (!rc) rc = cudaMemsetAsync(ws.info, 0, sizeof(InfoDev), st) ? PAT_ERR_CUDA : 0;
+    if (!rc) rc = cudaMemsetAsync(ws.kt[0], 0, 2 * NN * sizeof(int), st) ? PAT_ERR_CUDA : 0;
     if (!rc) {
         const float* xb = p->xbar0_dev ? p->xbar0_dev : p->x0_dev;
         dim3 blk(32, 8), grd(ceil_div(N + 2, 32), ceil_div(N + 2, 8));
@@ -1090,12 +1087,14 @@ static int gap_impl(const pat_geometry* g, const float* f, const pat_params* p, 
     if (!rc) rc = ensure_precond(g, st);
     if (!rc) {
         const long long S_ = (long long)g->desc.n_det * g->desc.n_t;
-        rc = launch_absmax(y, S_, &ws.info->qmax_bits, st);
-        if (!rc) rc = launch_adjoint_parts(g, y, nullptr, &ws.info->qmax_bits, ws.w_parts, nullptr, st);
+        rc = cudaMemsetAsync(ws.kt[0], 0, (size_t)g->desc.n * g->desc.n * sizeof(int), st) ? PAT_ERR_CUDA : 0;
+        if (!rc) rc = launch_absmax(y, S_, &ws.info->qmax_bits[0], st);
+        if (!rc) rc = launch_adjoint_fixed(g, y, nullptr, &ws.info->qmax_bits[0], ws.kt[0], nullptr, st);
     }
     pat_params q = *p;
     q.tol = 0;
-    if (!rc) rc = launch_gap<REG>(g, &q, ws, x, nullptr, y + S, y, f, nullptr, st);
+    if (!rc) rc = launch_gap<REG>(g, &q, ws, kt_view(g, ws.kt[0], &ws.info->qmax_bits[0]), x, nullptr, y + S, y, f,
+                                  nullptr, st);
     if (!rc) rc = cudaMemcpyAsync(&h, ws.info, sizeof(InfoDev), cudaMemcpyDeviceToHost, st) ? PAT_ERR_CUDA : 0;
     cudaFreeAsync(ws.base, st);
     cudaError_t se = cudaStreamSynchronize(st);

@@ -202,7 +202,7 @@ struct AdjArgs {
     const unsigned* ymax_bits;
     const float* tile_kmax;
     const int4* box;
-    float* parts;        // groups x (N+2)^2; the zero border is never written
+    int* acc_out;        // N*N fixed-point image, added to with integer atomics
     int tiles_x;
     int dets_per_group;
     const int* stop;
@@ -312,25 +312,25 @@ __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
         }
     }
     __syncthreads();
-    // back to floating point: value = acc * bound / 2^30 (NaN / Inf bounds propagate)
-    const float inv = bound > 0.f ? bound * 9.313225746154785e-10f : (bound == 0.f ? 0.f : bound);
-    float* out = a.parts + (size_t)blockIdx.y * (N + 2) * (N + 2);
+    // detector groups of one tile share its scale, so their fixed-point partial sums add
+    // exactly (and in any order) with integer atomics
     for (int c = tid; c < ATILE * ATILE; c += ATHREADS) {
         const int lx = c % ATILE, ly = c / ATILE;
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= N || gy >= N) continue;
-        out[(size_t)(gy + 1) * (N + 2) + gx + 1] = (float)acc[(ly + 1) * AW + lx + 1] * inv;
+        const int v = acc[(ly + 1) * AW + lx + 1];
+        if (gridDim.y == 1)
+            a.acc_out[(size_t)gy * N + gx] = v;
+        else if (v)
+            atomicAdd(&a.acc_out[(size_t)gy * N + gx], v);
     }
 }
 
-// out[i] = sum over the detector groups of the partial images (fixed order)
-__global__ void k_sum_parts(const float* __restrict__ parts, int groups, int N, float* __restrict__ out) {
+// out = the fixed-point K^T image in floating point
+__global__ void k_kt_to_float(KtView kt, int N, float* __restrict__ out) {
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
     if (gx >= N || gy >= N) return;
-    const size_t P2 = (size_t)(N + 2) * (N + 2), o = (size_t)(gy + 1) * (N + 2) + gx + 1;
-    float v = 0.f;
-    for (int gr = 0; gr < groups; ++gr) v += parts[gr * P2 + o];
-    out[(size_t)gy * N + gx] = v;
+    out[(size_t)gy * N + gx] = kt.at(gx, gy, N);
 }
 
 // max of K^T 1 over each K^T tile, with headroom for the FP32 rounding of the terms
@@ -434,8 +434,17 @@ int launch_absmax(const float* y, long long n, unsigned* out, cudaStream_t st) {
     return PAT_OK;
 }
 
-int launch_adjoint_parts(const pat_geometry* g, const float* y, const float* premul, const unsigned* ymax_bits,
-                         float* parts, const int* stop, cudaStream_t st) {
+KtView kt_view(const pat_geometry* g, const int* acc, const unsigned* ymax_bits) {
+    KtView v;
+    v.acc = acc;
+    v.ymax_bits = ymax_bits;
+    v.tile_kmax = g->pc.tile_kmax;
+    v.tiles_x = g->adj_tiles_x;
+    return v;
+}
+
+int launch_adjoint_fixed(const pat_geometry* g, const float* y, const float* premul, const unsigned* ymax_bits,
+                         int* acc, const int* stop, cudaStream_t st) {
     prof_mark(PAT_PHASE_ADJOINT, st, true);
     AdjArgs a;
     a.g = g->view;
@@ -444,7 +453,7 @@ int launch_adjoint_parts(const pat_geometry* g, const float* y, const float* pre
     a.ymax_bits = ymax_bits;
     a.tile_kmax = g->pc.tile_kmax;
     a.box = g->adj_box;
-    a.parts = parts;
+    a.acc_out = acc;
     a.tiles_x = g->adj_tiles_x;
     a.dets_per_group = g->adj_per_group;
     a.stop = stop;
@@ -458,20 +467,20 @@ int launch_adjoint(const pat_geometry* g, const float* y, float* out, cudaStream
     int rc = ensure_precond(g, st);
     if (rc) return rc;
     const int N = g->desc.n;
-    const size_t P2 = (size_t)(N + 2) * (N + 2), S = (size_t)g->desc.n_det * g->desc.n_t;
+    const size_t S = (size_t)g->desc.n_det * g->desc.n_t;
     char* scratch = nullptr;
-    const size_t bytes = 256 + P2 * g->adj_groups * sizeof(float);
+    const size_t bytes = 256 + (size_t)N * N * sizeof(int);
     PAT_CUDA(cudaMallocAsync((void**)&scratch, bytes, st));
     unsigned* ymax = (unsigned*)scratch;
-    float* parts = (float*)(scratch + 256);
+    int* acc = (int*)(scratch + 256);
     rc = cudaMemsetAsync(scratch, 0, bytes, st) == cudaSuccess ? PAT_OK : PAT_ERR_CUDA;
     if (!rc) {
         rc = launch_absmax(y, (long long)S, ymax, st);
-        if (!rc) rc = launch_adjoint_parts(g, y, nullptr, ymax, parts, nullptr, st);
+        if (!rc) rc = launch_adjoint_fixed(g, y, nullptr, ymax, acc, nullptr, st);
     }
     if (!rc) {
         dim3 blk(32, 8), grd(ceil_div(N, 32), ceil_div(N, 8));
-        k_sum_parts<<<grd, blk, 0, st>>>(parts, g->adj_groups, N, out);
+        k_kt_to_float<<<grd, blk, 0, st>>>(kt_view(g, acc, ymax), N, out);
         count_launch();
         rc = cudaGetLastError() == cudaSuccess ? PAT_OK : PAT_ERR_CUDA;
     }
