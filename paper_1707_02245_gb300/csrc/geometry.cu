@@ -146,7 +146,11 @@ static void free_tables(pat_geometry* g) {
     cudaFree(g->pc.kcol);
     cudaFree(g->pc.tile_kmax);
     cudaFree(g->adj_box);
+    cudaFree(g->adj_units);
+    cudaFree(g->adj_item);
     g->adj_box = nullptr;
+    g->adj_units = nullptr;
+    g->adj_item = nullptr;
     g->pc.tile_kmax = nullptr;
     g->det = nullptr;
     g->cs = nullptr;
@@ -320,13 +324,81 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     }
     g->adj_tiles_x = tiles_x;
     g->adj_tiles = tiles;
+
+    // K^T work list.  A unit is up to 32 rays of one (tile, detector) box; its cost is the
+    // number of candidate points on those rays (ray-segment lengths in the tile's tap
+    // region) plus a fixed overhead.  Each tile's units are packed into work items of
+    // roughly equal cost (one CTA each); items run heaviest first.
+    std::vector<int4> units;       // {detector, first ray (circular), rays, box index}
+    std::vector<int4> items;       // {tile, first unit, end unit, 0}
+    std::vector<double> item_cost;
     {
-        const int target = 8 * 152;  // CTAs to fill the GPU several times over
-        int groups = std::max(1, std::min(D, (target + tiles - 1) / tiles));
-        const int per = (D + groups - 1) / groups;
-        g->adj_per_group = per;
-        g->adj_groups = (D + per - 1) / per;
+        std::vector<double> ucost;
+        std::vector<int> tile_first(tiles + 1, 0);
+        const double r_first = d.r0 + 0.5 * d.dr;
+        for (int t = 0; t < tiles; ++t) {
+            tile_first[t] = (int)units.size();
+            const int x0 = (t % tiles_x) * ATILE, y0 = (t / tiles_x) * ATILE;
+            const double rx0 = d.xmin + (x0 - 0.5) * hx - ex, rx1 = d.xmin + (x0 + ATILE + 0.5) * hx + ex;
+            const double ry0 = d.ymin + (y0 - 0.5) * hy - ey, ry1 = d.ymin + (y0 + ATILE + 0.5) * hy + ey;
+            for (int di = 0; di < D; ++di) {
+                const int4 bx = box[(size_t)t * D + di];
+                if (bx.w <= 0 || bx.y <= 0) continue;
+                const double dx = d.det_xy_host[2 * di], dy = d.det_xy_host[2 * di + 1];
+                for (int mb = 0; mb < bx.w; mb += 32) {
+                    const int nr = std::min(32, bx.w - mb);
+                    double c = 16.0;
+                    for (int j = 0; j < nr; ++j) {
+                        const int m = (bx.z + mb + j) % M;
+                        const double cx = cosd[m], sy = sind[m];
+                        double t0 = -1e300, t1 = 1e300;
+                        if (cx != 0) {
+                            const double a0 = (rx0 - dx) / cx, a1 = (rx1 - dx) / cx;
+                            t0 = std::max(t0, std::min(a0, a1));
+                            t1 = std::min(t1, std::max(a0, a1));
+                        } else if (dx < rx0 || dx > rx1) {
+                            t1 = -1e300;
+                        }
+                        if (sy != 0) {
+                            const double b0 = (ry0 - dy) / sy, b1 = (ry1 - dy) / sy;
+                            t0 = std::max(t0, std::min(b0, b1));
+                            t1 = std::min(t1, std::max(b0, b1));
+                        } else if (dy < ry0 || dy > ry1) {
+                            t1 = -1e300;
+                        }
+                        if (t1 < t0) continue;
+                        const double k0 = std::max((double)bx.x, floor((t0 - r_first) / d.dr) - 1);
+                        const double k1 = std::min((double)(bx.x + bx.y), ceil((t1 - r_first) / d.dr) + 2);
+                        c += std::max(0.0, k1 - k0);
+                    }
+                    units.push_back(make_int4(di, (bx.z + mb) % M, nr, t * D + di));
+                    ucost.push_back(c);
+                }
+            }
+        }
+        tile_first[tiles] = (int)units.size();
+        double total = 0;
+        for (double c : ucost) total += c;
+        const double target = std::max(64.0, total / (8.0 * 152.0));
+        for (int t = 0; t < tiles; ++t) {
+            int u = tile_first[t];
+            while (u < tile_first[t + 1]) {
+                double c = 0;
+                const int u0 = u;
+                while (u < tile_first[t + 1] && (u == u0 || c + ucost[u] <= target)) c += ucost[u++];
+                items.push_back(make_int4(t, u0, u, 0));
+                item_cost.push_back(c);
+            }
+        }
+        std::vector<int> order(items.size());
+        for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return item_cost[a] > item_cost[b]; });
+        std::vector<int4> sorted(items.size());
+        for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+        items.swap(sorted);
+        if (items.empty()) items.push_back(make_int4(0, 0, 0, 0));
     }
+    g->adj_items = (int)items.size();
 
     cudaError_t e = cudaSuccess;
     e = cudaMalloc(&g->det, sizeof(float2) * D);
@@ -336,6 +408,11 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     if (e == cudaSuccess) e = cudaMalloc(&g->win, sizeof(int2) * win.size());
     if (e == cudaSuccess) e = cudaMalloc(&g->adj_box, sizeof(int4) * box.size());
     if (e == cudaSuccess) e = cudaMemcpy(g->adj_box, box.data(), sizeof(int4) * box.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&g->adj_units, sizeof(int4) * std::max<size_t>(1, units.size()));
+    if (e == cudaSuccess && !units.empty())
+        e = cudaMemcpy(g->adj_units, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&g->adj_item, sizeof(int4) * items.size());
+    if (e == cudaSuccess) e = cudaMemcpy(g->adj_item, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->det, det.data(), sizeof(float2) * D, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->cs, cs.data(), sizeof(float2) * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->rk, rk.data(), sizeof(float) * T, cudaMemcpyHostToDevice);

@@ -84,7 +84,9 @@ struct pat_geometry {
     float* wk = nullptr;
     int2* win = nullptr;
     int4* adj_box = nullptr;          // per (tile, detector): {k0, nk, m0, nm} candidate box of K^T
-    int adj_tiles_x = 0, adj_tiles = 0, adj_groups = 1, adj_per_group = 1;
+    int4* adj_units = nullptr;        // K^T work units {detector, first ray, rays, box index}
+    int4* adj_item = nullptr;         // K^T work items (one CTA each) {tile, first unit, end unit, 0}
+    int adj_tiles_x = 0, adj_tiles = 0, adj_items = 0;
     pat::GeomView view;
     // lazily computed preconditioner sums
     mutable std::mutex mtx;

@@ -185,13 +185,14 @@ __global__ void __launch_bounds__(ROW_THREADS) k_forward_gap(GeomView g, const f
 // deterministic) replaces floating-point atomics.  The resolution 2^-30 of that bound is
 // finer than FP32 accumulation of the same terms.  Ring cells may wrap; they are dropped.
 //
-// Candidates: one warp per detector takes the (k, m) box precomputed for (tile, detector)
-// at geometry creation, cuts every ray of the box down to its segment inside the tile's
-// tap region, and splits the concatenated segments into 32 equal contiguous runs, one per
-// lane, so lanes that add at the same time sit on different rays.  Every
-// candidate uses the forward projector's FP32 position and tap arithmetic, so the CTA
-// adds exactly the entries of K^T that belong to its pixels.  Each detector group writes
-// its partial tile with plain stores; consumers add the groups in a fixed order.
+// Work: each CTA takes one work item (a tile and a list of units; a unit is up to 32 rays
+// of one detector's (k, m) box for the tile), precomputed and cost-balanced at geometry
+// creation.  A warp per unit cuts every ray down to its segment inside the tile's tap
+// region and splits the concatenated segments into 32 equal contiguous runs, one per
+// lane, so lanes that add at the same time sit on different rays.  Every candidate uses
+// the forward projector's FP32 position and tap arithmetic, so the CTA adds exactly the
+// entries of K^T that belong to its pixels.  Items of one tile share its scale, so their
+// fixed-point tiles add exactly (in any order) into one image with integer atomics.
 // ---------------------------------------------------------------------------------
 constexpr int ATHREADS = 256;
 
@@ -202,9 +203,10 @@ struct AdjArgs {
     const unsigned* ymax_bits;
     const float* tile_kmax;
     const int4* box;
+    const int4* units;
+    const int4* items;
     int* acc_out;        // N*N fixed-point image, added to with integer atomics
     int tiles_x;
-    int dets_per_group;
     const int* stop;
 };
 
@@ -212,10 +214,9 @@ __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
     if (a.stop && *(volatile const int*)a.stop) return;
     const GeomView& g = a.g;
     const int N = g.n, T = g.n_t, M = g.quad_m, D = g.n_det;
-    const int tile = blockIdx.x;
+    const int4 item = __ldg(&a.items[blockIdx.x]);
+    const int tile = item.x;
     const int x0 = (tile % a.tiles_x) * ATILE, y0 = (tile / a.tiles_x) * ATILE;
-    const int d_begin = blockIdx.y * a.dets_per_group;
-    const int d_end = min(D, d_begin + a.dets_per_group);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int AW = ATILE + 2;
     __shared__ int acc[AW * AW];
@@ -235,10 +236,11 @@ __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
     // segment, the segment length, its exclusive prefix in the warp's flattened list
     __shared__ int s_m[ATHREADS / 32][32], s_ks[ATHREADS / 32][32], s_ex[ATHREADS / 32][33];
     if (bound > 0.f && isfinite(bound)) {
-        for (int d = d_begin + warp; d < d_end; d += ATHREADS / 32) {
-            const int4 bx = __ldg(&a.box[(size_t)tile * D + d]);
-            const int kb = bx.x, ke = bx.x + bx.y, m0 = bx.z, nm = bx.w;
-            if (nm <= 0 || bx.y <= 0) continue;
+        for (int u = item.y + warp; u < item.z; u += ATHREADS / 32) {
+            const int4 un = __ldg(&a.units[u]);   // {detector, first ray, rays, box}
+            const int d = un.x, m0 = un.y, nm = un.z;
+            const int4 bx = __ldg(&a.box[un.w]);
+            const int kb = bx.x, ke = bx.x + bx.y;
             const float2 det = __ldg(&g.det[d]);
             const float* yrow = a.y + (size_t)d * T;
             for (int mb = 0; mb < nm; mb += 32) {
@@ -319,10 +321,7 @@ __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= N || gy >= N) continue;
         const int v = acc[(ly + 1) * AW + lx + 1];
-        if (gridDim.y == 1)
-            a.acc_out[(size_t)gy * N + gx] = v;
-        else if (v)
-            atomicAdd(&a.acc_out[(size_t)gy * N + gx], v);
+        if (v) atomicAdd(&a.acc_out[(size_t)gy * N + gx], v);
     }
 }
 
@@ -454,10 +453,11 @@ int launch_adjoint_fixed(const pat_geometry* g, const float* y, const float* pre
     a.tile_kmax = g->pc.tile_kmax;
     a.box = g->adj_box;
     a.acc_out = acc;
+    a.units = g->adj_units;
+    a.items = g->adj_item;
     a.tiles_x = g->adj_tiles_x;
-    a.dets_per_group = g->adj_per_group;
     a.stop = stop;
-    k_adjoint_tiles<<<dim3(g->adj_tiles, g->adj_groups), ATHREADS, 0, st>>>(a);
+    k_adjoint_tiles<<<g->adj_items, ATHREADS, 0, st>>>(a);
     PAT_LAUNCH_CHECK("k_adjoint_tiles");
     prof_mark(PAT_PHASE_ADJOINT, st, false);
     return PAT_OK;
