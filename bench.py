@@ -37,7 +37,7 @@ UNIT = "iters/s"
 WORKLOAD_DESC = ("tgv256: TGV^2 PDHG, 256x256 vessel phantom with exp(-3 depth) fluence, 256 detectors on a "
                  "full circle r=1.2, 512 time samples, M=256, 5% noise, alpha 0.02, beta 0.04, 1000 iterations, "
                  "diagonal preconditioning, FP64 gap every 10 iterations")
-FLOPS_PER_POINT = 22          # algorithmic FP32 operations of one quadrature point
+FLOPS_PER_POINT = 22          # FP32 ops of one quadrature point: position 4, coordinates 4, floor/fraction 4, lerps 9, add 1
 SMS, FP32_LANES = 152, 128    # GB300: SMs x FP32 lanes per SM
 
 
