@@ -162,6 +162,29 @@ int  pat_steps(const pat_geometry* g, const pat_params* p, float* sig_q_dev, flo
 int  pat_duality_gap(const pat_geometry* g, const float* f_dev, const pat_params* p,
                      const float* x_dev, const float* y_dev, double* out4_host, void* stream);
 
+/* ---- K^T without device allocation -------------------------------------------------- */
+/* u = K^T y like pat_adjoint, but the call allocates no device memory: no cudaMalloc,
+ * cudaFree, stream-ordered pool or other allocating routine.  This is for callers that
+ * must not allocate at the time of the call.  Examples: code running while a CUDA graph
+ * is being captured, real-time loops that must not touch an allocator, and host
+ * applications whose device memory is owned by another allocator.  The paper has no
+ * counterpart; this is a deployment variant of the adjoint.
+ *  - Scratch: a device array of 4 MiB + 256 bytes built into the library.  Every GPU that
+ *    loads the library holds it until the process exits.  Its contents persist from call
+ *    to call, and the call clears what it needs.
+ *  - Limits: image side N <= 1024 (larger sizes return PAT_ERR_INVALID_ARG).
+ *  - Preparation: the geometry must have been prepared once, while allocation is allowed,
+ *    by pat_steps, pat_adjoint or pat_reconstruct (they compute the FP64 K sums that scale
+ *    the fixed-point accumulation).  Otherwise PAT_ERR_INVALID_ARG.
+ *  - Set-up: the first call on a device looks up the scratch's device address for that
+ *    device (current at the call).  Make that first call before any stream capture.
+ *  - Concurrency: all calls on one device share the scratch.  Calls that overlap on the
+ *    GPU (other streams, or other host threads without ordering) race; order them on
+ *    one stream.
+ *  - Result: identical to pat_adjoint's (same kernels, same fixed-point arithmetic).
+ *  y_dev: D*T floats; u_dev: N*N floats (overwritten); both caller-owned device memory. */
+int  pat_adjoint_noalloc(const pat_geometry* g, const float* y_dev, float* u_dev, void* stream);
+
 /* ---- diagnostics ------------------------------------------------------------------ */
 /* Phases of one PDHG iteration timed by the optional profiler (CUDA events recorded
  * around each launch on the caller's stream; the events add a few microseconds of host

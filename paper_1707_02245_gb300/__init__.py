@@ -33,7 +33,7 @@ EXPORTED = [
     "pat_create_geometry", "pat_destroy_geometry", "pat_forward", "pat_adjoint",
     "pat_direction_field", "pat_params_default", "pat_reconstruct", "pat_reconstruct_batched",
     "pat_steps", "pat_duality_gap", "pat_error_string", "pat_last_error", "pat_geometry_info",
-    "pat_profile_enable", "pat_profile_read", "pat_kernel_launches",
+    "pat_profile_enable", "pat_profile_read", "pat_kernel_launches", "pat_adjoint_noalloc",
 ]
 PHASES = ["forward_prox", "adj_clear", "adjoint", "update", "gap"]
 
@@ -92,6 +92,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pat_destroy_geometry": (None, [vp]),
         "pat_forward": (i, [vp, vp, vp, vp]),
         "pat_adjoint": (i, [vp, vp, vp, vp]),
+        "pat_adjoint_noalloc": (i, [vp, vp, vp, vp]),
         "pat_direction_field": (i, [i, vp, d, vp, vp]),
         "pat_params_default": (None, [ctypes.POINTER(pat_params)]),
         "pat_reconstruct": (i, [vp, vp, ctypes.POINTER(pat_params), vp, ctypes.POINTER(pat_info), vp]),
@@ -161,6 +162,11 @@ def pat_forward(g: int, u_dev, y_dev, stream=None) -> None:
 
 def pat_adjoint(g: int, y_dev, u_dev, stream=None) -> None:
     _check(load().pat_adjoint(g, _ptr(y_dev), _ptr(u_dev), _stream(stream)), "pat_adjoint")
+
+
+def pat_adjoint_noalloc(g: int, y_dev, u_dev, stream=None) -> None:
+    """K^T y without any device allocation during the call (see include/pat.h)."""
+    _check(load().pat_adjoint_noalloc(g, _ptr(y_dev), _ptr(u_dev), _stream(stream)), "pat_adjoint_noalloc")
 
 
 def pat_direction_field(n: int, w_dev, eta: float, xi_dev, stream=None) -> None:

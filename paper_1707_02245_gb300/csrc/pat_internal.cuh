@@ -149,6 +149,9 @@ int launch_adjoint(const pat_geometry* g, const float* y, float* out, cudaStream
 int launch_adjoint_fixed(const pat_geometry* g, const float* y, const float* premul, const unsigned* ymax_bits,
                          int* acc, const int* stop, cudaStream_t st);
 KtView kt_view(const pat_geometry* g, const int* acc, const unsigned* ymax_bits);
+// K^T y into an N*N float image using caller-provided, zeroed scratch (allocates nothing).
+int launch_adjoint_into(const pat_geometry* g, const float* y, unsigned* ymax_bits, int* acc, float* out,
+                        cudaStream_t st);
 int launch_forward_prox(const pat_geometry* g, const float* ubar_pad, float* q, const float* f,
                         const float* sig_q, float sig_q_scalar, float* qw, unsigned* qmax_bits,
                         const int* stop, cudaStream_t st);

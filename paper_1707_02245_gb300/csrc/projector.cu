@@ -463,6 +463,34 @@ int launch_adjoint_fixed(const pat_geometry* g, const float* y, const float* pre
     return PAT_OK;
 }
 
+// K^T y through caller-provided scratch: the max word at ymax_bits and the fixed-point
+// image at acc (N*N int32), both already zero; no allocation and no profiling events.
+int launch_adjoint_into(const pat_geometry* g, const float* y, unsigned* ymax_bits, int* acc, float* out,
+                        cudaStream_t st) {
+    const int N = g->desc.n;
+    const long long S = (long long)g->desc.n_det * g->desc.n_t;
+    k_absmax<<<std::min(4 * 152, ceil_div(S, 256)), 256, 0, st>>>(y, S, ymax_bits);
+    PAT_LAUNCH_CHECK("k_absmax");
+    AdjArgs a;
+    a.g = g->view;
+    a.y = y;
+    a.premul = 0;
+    a.ymax_bits = ymax_bits;
+    a.tile_kmax = g->pc.tile_kmax;
+    a.box = g->adj_box;
+    a.units = g->adj_units;
+    a.items = g->adj_item;
+    a.acc_out = acc;
+    a.tiles_x = g->adj_tiles_x;
+    a.stop = nullptr;
+    k_adjoint_tiles<<<g->adj_items, ATHREADS, 0, st>>>(a);
+    PAT_LAUNCH_CHECK("k_adjoint_tiles");
+    dim3 blk(32, 8), grd(ceil_div(N, 32), ceil_div(N, 8));
+    k_kt_to_float<<<grd, blk, 0, st>>>(kt_view(g, acc, ymax_bits), N, out);
+    PAT_LAUNCH_CHECK("k_kt_to_float");
+    return PAT_OK;
+}
+
 int launch_adjoint(const pat_geometry* g, const float* y, float* out, cudaStream_t st) {
     int rc = ensure_precond(g, st);
     if (rc) return rc;
