@@ -41,8 +41,10 @@ struct UpdateArgs {
     int* kt_clear;         // the other fixed-point buffer, cleared here for the next iteration
     unsigned* qmax_next;   // max |q| slot of the next iteration, reset here
     const float* x_in;     // u, v1, v2
+    const float* xl_in;    // low parts of the compensated primal pair (u, v1, v2)
     const float* y_in;     // r1, r2, s11, s22, s12
     float* x_out;
+    float* xl_out;
     float* y_out;
     float* ubar_pad;       // (N+2)^2, border stays zero
     const int* stop;
@@ -64,7 +66,7 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
 
     __shared__ float s_r1m[LY][LX], s_r2m[LY][LX];   // r (dTV: D_xi r) masked for div
     __shared__ float s_ub[LY][LX];                   // ubar on U = tile + high halo
-    __shared__ float s_un[TY][TX];                   // u^{n+1} on the tile
+    __shared__ float s_un[TY][TX], s_unl[TY][TX];    // u^{n+1} (high, low) on the tile
     // TGV only (small arrays for TV / dTV)
     constexpr int VL = (REG == PAT_TGV) ? LY : 1;
     constexpr int VX = (REG == PAT_TGV) ? LX : 1;
@@ -72,7 +74,7 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
     constexpr int VTX = (REG == PAT_TGV) ? TX : 1;
     __shared__ float s_s11[VL][VX], s_s22[VL][VX], s_s12[VL][VX];
     __shared__ float s_vb1[VL][VX], s_vb2[VL][VX];   // vbar on V = tile + low halo
-    __shared__ float s_vn1[VT][VTX], s_vn2[VT][VTX];
+    __shared__ float s_vn1[VT][VTX], s_vn2[VT][VTX], s_vnl1[VT][VTX], s_vnl2[VT][VTX];
 
     const float* u_in = a.x_in;
     const float* r1_in = a.y_in;
@@ -114,11 +116,15 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
                 const int gi = gy * N + gx;
                 const float divr = s_r1m[ly][lx] - s_r1m[ly][lx - 1] + s_r2m[ly][lx] - s_r2m[ly - 1][lx];
                 const float w = a.kt.at(gx, gy, N);
-                const float uo = __ldg(u_in + gi);
+                const float uo = __ldg(u_in + gi), uol = __ldg(a.xl_in + gi);
                 const float tu = a.tau >= 0.f ? a.tau : __ldg(a.tau_u + gi);
-                const float un = uo - tu * (w - divr);
-                ub = fmaf(a.theta, un - uo, un);
-                if (lx <= TX && ly <= TY) s_un[ly - 1][lx - 1] = un;
+                float un = uo, unl = uol;
+                add_compensated(un, unl, -tu * (w - divr));
+                ub = fmaf(a.theta, (un - uo) + (unl - uol), un + unl);
+                if (lx <= TX && ly <= TY) {
+                    s_un[ly - 1][lx - 1] = un;
+                    s_unl[ly - 1][lx - 1] = unl;
+                }
             }
             s_ub[ly][lx] = ub;
         }
@@ -136,15 +142,19 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
                 const float et2 = -dy22 - dx12 * kInvSqrt2f;
                 const float r1 = __ldg(r1_in + gi), r2 = __ldg(r2_in + gi);
                 const float v1o = __ldg(a.x_in + NN + gi), v2o = __ldg(a.x_in + 2 * NN + gi);
+                const float v1ol = __ldg(a.xl_in + NN + gi), v2ol = __ldg(a.xl_in + 2 * NN + gi);
                 const float t1 = a.tau >= 0.f ? a.tau : tau_v1_tgv(gx, gy, N);
                 const float t2 = a.tau >= 0.f ? a.tau : tau_v2_tgv(gx, gy, N);
-                const float v1n = v1o - t1 * (et1 - r1);
-                const float v2n = v2o - t2 * (et2 - r2);
-                vb1 = fmaf(a.theta, v1n - v1o, v1n);
-                vb2 = fmaf(a.theta, v2n - v2o, v2n);
+                float v1n = v1o, v1nl = v1ol, v2n = v2o, v2nl = v2ol;
+                add_compensated(v1n, v1nl, -t1 * (et1 - r1));
+                add_compensated(v2n, v2nl, -t2 * (et2 - r2));
+                vb1 = fmaf(a.theta, (v1n - v1o) + (v1nl - v1ol), v1n + v1nl);
+                vb2 = fmaf(a.theta, (v2n - v2o) + (v2nl - v2ol), v2n + v2nl);
                 if (lx >= 1 && ly >= 1) {
                     s_vn1[ly - 1][lx - 1] = v1n;
                     s_vn2[ly - 1][lx - 1] = v2n;
+                    s_vnl1[ly - 1][lx - 1] = v1nl;
+                    s_vnl2[ly - 1][lx - 1] = v2nl;
                 }
             }
             s_vb1[ly][lx] = vb1;
@@ -182,6 +192,7 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
         a.y_out[gi] = r1;
         a.y_out[NN + gi] = r2;
         a.x_out[gi] = s_un[threadIdx.y][threadIdx.x];
+        a.xl_out[gi] = s_unl[threadIdx.y][threadIdx.x];
         a.ubar_pad[(gy + 1) * (N + 2) + gx + 1] = ub;
         if (REG == PAT_TGV) {
             // E vbar with d^- on the masked field
@@ -203,6 +214,8 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
             a.y_out[4 * NN + gi] = s12;
             a.x_out[NN + gi] = s_vn1[threadIdx.y][threadIdx.x];
             a.x_out[2 * NN + gi] = s_vn2[threadIdx.y][threadIdx.x];
+            a.xl_out[NN + gi] = s_vnl1[threadIdx.y][threadIdx.x];
+            a.xl_out[2 * NN + gi] = s_vnl2[threadIdx.y][threadIdx.x];
         }
     }
     if (gx < N && gy < N) a.kt_clear[gy * N + gx] = 0;
@@ -571,6 +584,7 @@ struct Workspace {
     void* base = nullptr;
     size_t bytes = 0;
     float* X[2] = {nullptr, nullptr};
+    float* XL[2] = {nullptr, nullptr};   // low parts of the compensated primal pairs
     float* Y[2] = {nullptr, nullptr};
     float *q = nullptr, *ubar_pad = nullptr, *vbar0 = nullptr;
     int* kt[2] = {nullptr, nullptr};   // fixed-point K^T q, by iteration parity
@@ -588,13 +602,13 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     const size_t P2 = (N + 2) * (N + 2);
     ws.n_data = forward_gap_blocks(g);
     ws.n_pix = pix_blocks((int)N);
-    size_t off[16];
-    size_t sz[16] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, NN * 4 * 2,
+    size_t off[17];
+    size_t sz[17] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, NN * 4 * 2,
                      (reg == PAT_TGV ? 2 * NN : 1) * 4,
                      NN * 4, S * 4, NN * 4, (size_t)ws.n_data * 3 * 8, (size_t)ws.n_pix * 6 * 8, sizeof(InfoDev),
-                     S * 4};
+                     S * 4, nx * 4, nx * 4};
     size_t total = 0;
-    for (int i = 0; i < 15; ++i) {
+    for (int i = 0; i < 17; ++i) {
         off[i] = total;
         total += align_up(sz[i]);
     }
@@ -617,6 +631,8 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     ws.pix_part = (double*)(b + off[12]);
     ws.info = (InfoDev*)(b + off[13]);
     ws.qw = (float*)(b + off[14]);
+    ws.XL[0] = (float*)(b + off[15]);
+    ws.XL[1] = (float*)(b + off[16]);
     return PAT_OK;
 }
 
@@ -684,8 +700,10 @@ static int launch_update(const pat_geometry* g, const pat_params* p, Workspace& 
     a.kt_clear = ws.kt[(it + 1) & 1];
     a.qmax_next = &ws.info->qmax_bits[(it + 1) & 1];
     a.x_in = ws.X[it & 1];
+    a.xl_in = ws.XL[it & 1];
     a.y_in = ws.Y[it & 1];
     a.x_out = ws.X[(it + 1) & 1];
+    a.xl_out = ws.XL[(it + 1) & 1];
     a.y_out = ws.Y[(it + 1) & 1];
     a.ubar_pad = ws.ubar_pad;
     a.stop = &ws.info->stop;
@@ -776,6 +794,7 @@ static int run_reconstruct(const pat_geometry* g, const float* f, const pat_para
     }
     if (!rc) rc = cudaMemsetAsync(ws.info, 0, sizeof(InfoDev), st) ? PAT_ERR_CUDA : 0;
     if (!rc) rc = cudaMemsetAsync(ws.kt[0], 0, 2 * NN * sizeof(int), st) ? PAT_ERR_CUDA : 0;
+    if (!rc) rc = cudaMemsetAsync(ws.XL[0], 0, nx * sizeof(float), st) ? PAT_ERR_CUDA : 0;
     if (!rc) {
         const float* xb = p->xbar0_dev ? p->xbar0_dev : p->x0_dev;
         dim3 blk(32, 8), grd(ceil_div(N + 2, 32), ceil_div(N + 2, 8));

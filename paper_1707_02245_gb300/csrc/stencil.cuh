@@ -54,6 +54,20 @@ __device__ __forceinline__ float tau_v2_tgv(int i, int j, int N) {
     return 1.f / (1.f + 2.f * (j < N - 1) + 1.41421356237f * (i < N - 1));
 }
 
+// (hi, lo) += delta by an error-free TwoSum followed by renormalisation: the pair holds
+// hi + lo to about 48 significant bits, so primal updates far below ulp(hi) keep
+// accumulating instead of rounding away (the FP32 iterates would otherwise stall once
+// tau |K^T q - div r| drops below half an ulp of u).
+__device__ __forceinline__ void add_compensated(float& hi, float& lo, float delta) {
+    const float s = __fadd_rn(hi, delta);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(delta, bb));
+    const float t = __fadd_rn(lo, e);
+    const float h2 = __fadd_rn(s, t);
+    lo = __fsub_rn(t, __fsub_rn(h2, s));
+    hi = h2;
+}
+
 // D_xi = I - gamma xi xi^T applied to p (symmetric).
 __device__ __forceinline__ void dxi_apply(float xi0, float xi1, float gamma, float p0, float p1, float& o0,
                                           float& o1) {
