@@ -135,6 +135,20 @@ struct KtView {
     }
 };
 
+// Taps of a point without the grid test (callers that test a tile window instead).
+__device__ __forceinline__ void point_coords(const GeomView& g, float2 det, float r, float2 cs, Taps& t) {
+    const float x = fmaf(r, cs.x, det.x);
+    const float y = fmaf(r, cs.y, det.y);
+    const float fx = fmaf(x, g.inv_hx, g.ox);
+    const float fy = fmaf(y, g.inv_hy, g.oy);
+    const float flx = floorf(fx);
+    const float fly = floorf(fy);
+    t.ax = fx - flx;
+    t.ay = fy - fly;
+    t.i0 = (int)flx;
+    t.j0 = (int)fly;
+}
+
 // Launch helpers
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
@@ -152,7 +166,10 @@ KtView kt_view(const pat_geometry* g, const int* acc, const unsigned* ymax_bits)
 // K^T y into an N*N float image using caller-provided, zeroed scratch (allocates nothing).
 int launch_adjoint_into(const pat_geometry* g, const float* y, unsigned* ymax_bits, int* acc, float* out,
                         cudaStream_t st);
-int launch_forward_prox(const pat_geometry* g, const float* ubar_pad, float* q, const float* f,
+// ubar_quad: (N+1)^2 float4 "quads" Q[(j0+1)(N+1) + i0+1] = (u[j0][i0], u[j0][i0+1],
+// u[j0+1][i0], u[j0+1][i0+1]) with zeros off the grid, so one 16-byte load fetches the
+// four bilinear taps of a point.
+int launch_forward_prox(const pat_geometry* g, const float4* ubar_quad, float* q, const float* f,
                         const float* sig_q, float sig_q_scalar, float* qw, unsigned* qmax_bits,
                         const int* stop, cudaStream_t st);
 int launch_forward_gap(const pat_geometry* g, const float* u, const float* q, const float* f,

@@ -47,6 +47,7 @@ struct UpdateArgs {
     float* xl_out;
     float* y_out;
     float* ubar_pad;       // (N+2)^2, border stays zero
+    float4* ubar_quad;     // (N+1)^2 quads of ubar for the projector
     const int* stop;
     int* iter;             // iteration counter (incremented once per launch)
 };
@@ -194,6 +195,15 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
         a.x_out[gi] = s_un[threadIdx.y][threadIdx.x];
         a.xl_out[gi] = s_unl[threadIdx.y][threadIdx.x];
         a.ubar_pad[(gy + 1) * (N + 2) + gx + 1] = ub;
+        // quads with the upper-left tap at (gx, gy), and the grid's low border quads
+        {
+            const float bx = s_ub[ly][lx + 1], by_ = s_ub[ly + 1][lx], bxy = s_ub[ly + 1][lx + 1];
+            const int Q = N + 1;
+            a.ubar_quad[(size_t)(gy + 1) * Q + gx + 1] = make_float4(ub, bx, by_, bxy);
+            if (gx == 0) a.ubar_quad[(size_t)(gy + 1) * Q] = make_float4(0.f, ub, 0.f, by_);
+            if (gy == 0) a.ubar_quad[gx + 1] = make_float4(0.f, 0.f, ub, bx);
+            if (gx == 0 && gy == 0) a.ubar_quad[0] = make_float4(0.f, 0.f, 0.f, ub);
+        }
         if (REG == PAT_TGV) {
             // E vbar with d^- on the masked field
             const bool axm = gx >= 1, bym = gy >= 1;
@@ -519,6 +529,15 @@ __global__ void k_pad(const float* __restrict__ u, float* __restrict__ pad, int 
     pad[gy * P + gx] = (x >= 0 && x < N && y >= 0 && y < N && u) ? u[y * N + x] : 0.f;
 }
 
+// quads of a zero-bordered image: Q[(j+1)(N+1) + i+1] = taps (i..i+1, j..j+1), i, j >= -1
+__global__ void k_quads_from_pad(const float* __restrict__ pad, float4* __restrict__ quad, int N) {
+    const int qx = blockIdx.x * blockDim.x + threadIdx.x, qy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (qx > N || qy > N) return;
+    const int P = N + 2;  // pad index of pixel (i, j) is (j+1) P + i+1; quad (qx, qy) has i0 = qx-1
+    quad[(size_t)qy * (N + 1) + qx] = make_float4(pad[qy * P + qx], pad[qy * P + qx + 1], pad[(qy + 1) * P + qx],
+                                                  pad[(qy + 1) * P + qx + 1]);
+}
+
 __global__ void k_unpad(const float* __restrict__ pad, float* __restrict__ u, int N) {
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
     if (gx >= N || gy >= N) return;
@@ -587,6 +606,7 @@ struct Workspace {
     float* XL[2] = {nullptr, nullptr};   // low parts of the compensated primal pairs
     float* Y[2] = {nullptr, nullptr};
     float *q = nullptr, *ubar_pad = nullptr, *vbar0 = nullptr;
+    float4* ubar_quad = nullptr;
     int* kt[2] = {nullptr, nullptr};   // fixed-point K^T q, by iteration parity
     float *tau_u = nullptr, *sig_q = nullptr, *sig_r = nullptr, *qw = nullptr;
     double *data_part = nullptr, *pix_part = nullptr;
@@ -602,13 +622,13 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     const size_t P2 = (N + 2) * (N + 2);
     ws.n_data = forward_gap_blocks(g);
     ws.n_pix = pix_blocks((int)N);
-    size_t off[17];
-    size_t sz[17] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, NN * 4 * 2,
+    size_t off[18];
+    size_t sz[18] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, NN * 4 * 2,
                      (reg == PAT_TGV ? 2 * NN : 1) * 4,
                      NN * 4, S * 4, NN * 4, (size_t)ws.n_data * 3 * 8, (size_t)ws.n_pix * 6 * 8, sizeof(InfoDev),
-                     S * 4, nx * 4, nx * 4};
+                     S * 4, nx * 4, nx * 4, (N + 1) * (N + 1) * 16};
     size_t total = 0;
-    for (int i = 0; i < 17; ++i) {
+    for (int i = 0; i < 18; ++i) {
         off[i] = total;
         total += align_up(sz[i]);
     }
@@ -633,6 +653,7 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     ws.qw = (float*)(b + off[14]);
     ws.XL[0] = (float*)(b + off[15]);
     ws.XL[1] = (float*)(b + off[16]);
+    ws.ubar_quad = (float4*)(b + off[17]);
     return PAT_OK;
 }
 
@@ -706,6 +727,7 @@ static int launch_update(const pat_geometry* g, const pat_params* p, Workspace& 
     a.xl_out = ws.XL[(it + 1) & 1];
     a.y_out = ws.Y[(it + 1) & 1];
     a.ubar_pad = ws.ubar_pad;
+    a.ubar_quad = ws.ubar_quad;
     a.stop = &ws.info->stop;
     a.iter = &ws.info->iter;
     dim3 grd(ceil_div(N, TX), ceil_div(N, TY)), blk(TX, TY);
@@ -737,7 +759,7 @@ static int enqueue_iterations(const pat_geometry* g, const float* f, const pat_p
     const int* stop = &ws.info->stop;
     for (int it = it0; it < it0 + count; ++it) {
         prof_mark(PAT_PHASE_FORWARD_PROX, st, true);
-        int rc = launch_forward_prox(g, ws.ubar_pad, ws.q, f, sc.sig_q >= 0 ? nullptr : ws.sig_q, sc.sig_q, ws.qw,
+        int rc = launch_forward_prox(g, ws.ubar_quad, ws.q, f, sc.sig_q >= 0 ? nullptr : ws.sig_q, sc.sig_q, ws.qw,
                                      &ws.info->qmax_bits[it & 1], stop, st);
         if (rc) return rc;
         prof_mark(PAT_PHASE_FORWARD_PROX, st, false);
@@ -799,6 +821,9 @@ static int run_reconstruct(const pat_geometry* g, const float* f, const pat_para
         const float* xb = p->xbar0_dev ? p->xbar0_dev : p->x0_dev;
         dim3 blk(32, 8), grd(ceil_div(N + 2, 32), ceil_div(N + 2, 8));
         k_pad<<<grd, blk, 0, st>>>(xb, ws.ubar_pad, N);
+        count_launch();
+        dim3 gq(ceil_div(N + 1, 32), ceil_div(N + 1, 8));
+        k_quads_from_pad<<<gq, blk, 0, st>>>(ws.ubar_pad, ws.ubar_quad, N);
         count_launch();
         if (REG == PAT_TGV) {
             if (xb)

@@ -60,7 +60,9 @@ __device__ __forceinline__ RowLane row_lane(const GeomView& g) {
 }
 
 // Partial integral of the bilinear image over circle (d, k) for one angular phase.
-template <bool PADDED>
+// QUAD: u points at (N+1)^2 float4 quads (one load per point); otherwise u is the plain
+// N*N image read with per-tap bounds tests.
+template <bool QUAD>
 __device__ __forceinline__ float circle_partial(const GeomView& g, const float* __restrict__ u, const RowLane& rl) {
     const int2 w = __ldg(&g.win[rl.d * g.n_kgrp + min(rl.k / KGRP, g.n_kgrp - 1)]);
     const float2 det = __ldg(&g.det[rl.d]);
@@ -74,8 +76,16 @@ __device__ __forceinline__ float circle_partial(const GeomView& g, const float* 
         if (m >= g.quad_m) m -= g.quad_m;
         Taps t;
         if (point_taps(g, det, r, cs, t) && rl.valid) {
-            float v10, v01, v11;
-            const float v00 = fetch4<PADDED>(u, g.n, t, v10, v01, v11);
+            float v00, v10, v01, v11;
+            if (QUAD) {
+                const float4 v = __ldg(reinterpret_cast<const float4*>(u) + (t.j0 + 1) * (g.n + 1) + (t.i0 + 1));
+                v00 = v.x;
+                v10 = v.y;
+                v01 = v.z;
+                v11 = v.w;
+            } else {
+                v00 = fetch4<false>(u, g.n, t, v10, v01, v11);
+            }
             const float a = fmaf(t.ax, v10 - v00, v00);
             const float b = fmaf(t.ax, v11 - v01, v01);
             acc += fmaf(t.ay, b - a, a);
@@ -92,16 +102,15 @@ __device__ __forceinline__ float phase_sum(float v) {
 }
 
 // y = K u
-template <bool PADDED>
 __global__ void __launch_bounds__(ROW_THREADS) k_forward(GeomView g, const float* __restrict__ u, float* __restrict__ y) {
     const RowLane rl = row_lane(g);
-    const float s = phase_sum(circle_partial<PADDED>(g, u, rl));
+    const float s = phase_sum(circle_partial<false>(g, u, rl));
     if (rl.valid && rl.ph == 0) y[(size_t)rl.d * g.n_t + rl.k] = s * __ldg(&g.wk[rl.k]);
 }
 
 // q <- prox_{sigma F1*}(q + sigma K ubar) = (q + sigma (K ubar - f)) / (1 + sigma)  (Sec. 3.2)
 // Also records max |q| (as float bits) for the fixed-point K^T that follows.
-__global__ void __launch_bounds__(ROW_THREADS) k_forward_prox(GeomView g, const float* __restrict__ ubar_pad,
+__global__ void __launch_bounds__(ROW_THREADS) k_forward_prox(GeomView g, const float4* __restrict__ ubar_quad,
                                                              float* __restrict__ q, const float* __restrict__ f,
                                                              const float* __restrict__ sig_q, float sig_scalar,
                                                              float* __restrict__ qw,
@@ -109,7 +118,7 @@ __global__ void __launch_bounds__(ROW_THREADS) k_forward_prox(GeomView g, const 
                                                              const int* __restrict__ stop) {
     if (stop && *(volatile const int*)stop) return;
     const RowLane rl = row_lane(g);
-    const float s = phase_sum(circle_partial<true>(g, ubar_pad, rl));
+    const float s = phase_sum(circle_partial<true>(g, reinterpret_cast<const float*>(ubar_quad), rl));
     float aq = 0.f;
     if (rl.valid && rl.ph == 0) {
         const size_t i = (size_t)rl.d * g.n_t + rl.k;
@@ -210,6 +219,7 @@ struct AdjArgs {
     const int* stop;
 };
 
+template <bool PREMUL>
 __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
     if (a.stop && *(volatile const int*)a.stop) return;
     const GeomView& g = a.g;
@@ -297,10 +307,11 @@ __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
                             cs = __ldg(&g.cs[s_m[warp][j]]);
                         }
                         Taps t;
-                        if (!point_taps(g, det, __ldg(&g.rk[k]), cs, t)) continue;
+                        point_coords(g, det, __ldg(&g.rk[k]), cs, t);
+                        // taps in the tile window (ring cells off the grid are dropped later)
                         const int li = t.i0 - x0 + 1, lj = t.j0 - y0 + 1;
                         if ((unsigned)li > (unsigned)ATILE || (unsigned)lj > (unsigned)ATILE) continue;
-                        const float c = (a.premul ? __ldg(&yrow[k]) : __ldg(&yrow[k]) * __ldg(&g.wk[k])) * scale;
+                        const float c = (PREMUL ? __ldg(&yrow[k]) : __ldg(&yrow[k]) * __ldg(&g.wk[k])) * scale;
                         const float c0 = c * (1.f - t.ay), c1 = c * t.ay;
                         int* q = acc + lj * AW + li;
                         atomicAdd(q, __float2int_rn(c0 * (1.f - t.ax)));
@@ -402,18 +413,16 @@ int forward_gap_blocks(const pat_geometry* g) {
 }
 
 int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y, cudaStream_t st) {
-    if (padded)
-        k_forward<true><<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, u, y);
-    else
-        k_forward<false><<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, u, y);
+    (void)padded;
+    k_forward<<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, u, y);
     PAT_LAUNCH_CHECK("k_forward");
     return PAT_OK;
 }
 
-int launch_forward_prox(const pat_geometry* g, const float* ubar_pad, float* q, const float* f,
+int launch_forward_prox(const pat_geometry* g, const float4* ubar_quad, float* q, const float* f,
                         const float* sig_q, float sig_q_scalar, float* qw, unsigned* qmax_bits,
                         const int* stop, cudaStream_t st) {
-    k_forward_prox<<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, ubar_pad, q, f, sig_q, sig_q_scalar, qw,
+    k_forward_prox<<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, ubar_quad, q, f, sig_q, sig_q_scalar, qw,
                                                          qmax_bits, stop);
     PAT_LAUNCH_CHECK("k_forward_prox");
     return PAT_OK;
@@ -457,7 +466,10 @@ int launch_adjoint_fixed(const pat_geometry* g, const float* y, const float* pre
     a.items = g->adj_item;
     a.tiles_x = g->adj_tiles_x;
     a.stop = stop;
-    k_adjoint_tiles<<<g->adj_items, ATHREADS, 0, st>>>(a);
+    if (a.premul)
+        k_adjoint_tiles<true><<<g->adj_items, ATHREADS, 0, st>>>(a);
+    else
+        k_adjoint_tiles<false><<<g->adj_items, ATHREADS, 0, st>>>(a);
     PAT_LAUNCH_CHECK("k_adjoint_tiles");
     prof_mark(PAT_PHASE_ADJOINT, st, false);
     return PAT_OK;
@@ -483,7 +495,7 @@ int launch_adjoint_into(const pat_geometry* g, const float* y, unsigned* ymax_bi
     a.acc_out = acc;
     a.tiles_x = g->adj_tiles_x;
     a.stop = nullptr;
-    k_adjoint_tiles<<<g->adj_items, ATHREADS, 0, st>>>(a);
+    k_adjoint_tiles<false><<<g->adj_items, ATHREADS, 0, st>>>(a);
     PAT_LAUNCH_CHECK("k_adjoint_tiles");
     dim3 blk(32, 8), grd(ceil_div(N, 32), ceil_div(N, 8));
     k_kt_to_float<<<grd, blk, 0, st>>>(kt_view(g, acc, ymax_bits), N, out);
