@@ -172,7 +172,8 @@ int launch_adjoint_into(const pat_geometry* g, const float* y, unsigned* ymax_bi
 int launch_forward_prox(const pat_geometry* g, const float4* ubar_quad, float* q, const float* f,
                         const float* sig_q, float sig_q_scalar, float* qw, unsigned* qmax_bits,
                         const int* stop, cudaStream_t st);
-int launch_forward_gap(const pat_geometry* g, const float* u, const float* q, const float* f,
+// u_quad (optional): quads of u read instead of the plain image u.
+int launch_forward_gap(const pat_geometry* g, const float* u, const float4* u_quad, const float* q, const float* f,
                        double* partials, int n_part, const int* stop, cudaStream_t st);
 int forward_gap_blocks(const pat_geometry* g);
 // max |y| as float bits into *out (which must hold 0 or a smaller value beforehand)

@@ -26,7 +26,7 @@
 
 namespace pat {
 
-constexpr int TX = 32, TY = 8;            // update tile
+constexpr int TX = 32, TY = 4;            // update tile
 constexpr int LX = TX + 2, LY = TY + 2;   // tile plus one-pixel halo on each side
 
 struct UpdateArgs {
@@ -48,6 +48,7 @@ struct UpdateArgs {
     float* y_out;
     float* ubar_pad;       // (N+2)^2, border stays zero
     float4* ubar_quad;     // (N+1)^2 quads of ubar for the projector
+    float4* u_quad;        // quads of u^{n+1} for the gap's K u (NULL: not a gap iteration)
     const int* stop;
     int* iter;             // iteration counter (incremented once per launch)
 };
@@ -67,6 +68,7 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
 
     __shared__ float s_r1m[LY][LX], s_r2m[LY][LX];   // r (dTV: D_xi r) masked for div
     __shared__ float s_ub[LY][LX];                   // ubar on U = tile + high halo
+    __shared__ float s_uU[LY][LX];                   // u^{n+1} on U (for the gap's quads)
     __shared__ float s_un[TY][TX], s_unl[TY][TX];    // u^{n+1} (high, low) on the tile
     // TGV only (small arrays for TV / dTV)
     constexpr int VL = (REG == PAT_TGV) ? LY : 1;
@@ -122,11 +124,13 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
                 float un = uo, unl = uol;
                 add_compensated(un, unl, -tu * (w - divr));
                 ub = fmaf(a.theta, (un - uo) + (unl - uol), un + unl);
+                s_uU[ly][lx] = un;
                 if (lx <= TX && ly <= TY) {
                     s_un[ly - 1][lx - 1] = un;
                     s_unl[ly - 1][lx - 1] = unl;
                 }
             }
+            if (!in) s_uU[ly][lx] = 0.f;
             s_ub[ly][lx] = ub;
         }
         if (REG == PAT_TGV && lx <= TX && ly <= TY) {  // V: v^{n+1}, vbar
@@ -203,6 +207,13 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
             if (gx == 0) a.ubar_quad[(size_t)(gy + 1) * Q] = make_float4(0.f, ub, 0.f, by_);
             if (gy == 0) a.ubar_quad[gx + 1] = make_float4(0.f, 0.f, ub, bx);
             if (gx == 0 && gy == 0) a.ubar_quad[0] = make_float4(0.f, 0.f, 0.f, ub);
+            if (a.u_quad) {
+                const float uu = s_uU[ly][lx], ux = s_uU[ly][lx + 1], uy = s_uU[ly + 1][lx], uxy = s_uU[ly + 1][lx + 1];
+                a.u_quad[(size_t)(gy + 1) * Q + gx + 1] = make_float4(uu, ux, uy, uxy);
+                if (gx == 0) a.u_quad[(size_t)(gy + 1) * Q] = make_float4(0.f, uu, 0.f, uy);
+                if (gy == 0) a.u_quad[gx + 1] = make_float4(0.f, 0.f, uu, ux);
+                if (gx == 0 && gy == 0) a.u_quad[0] = make_float4(0.f, 0.f, 0.f, uu);
+            }
         }
         if (REG == PAT_TGV) {
             // E vbar with d^- on the masked field
@@ -344,7 +355,8 @@ __global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
             g0 -= X(1, gx, gy);
             g1 -= X(2, gx, gy);
         }
-        acc[0] += sqrt(g0 * g0 + g1 * g1);
+        // the regulariser terms need only FP32 accuracy per term (they are summed in FP64)
+        acc[0] += (double)sqrtf((float)(g0 * g0 + g1 * g1));
         // (masked, D_xi-weighted) r for div
         auto rm = [&](int c, int x, int y) -> double {
             if (x < 0 || y < 0) return 0.0;
@@ -372,7 +384,7 @@ __global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
             const double e22 = vm(1, gx, gy, false) - vm(1, gx, gy - 1, false);
             const double e12 = ((vm(0, gx, gy, false) - vm(0, gx, gy - 1, false)) +
                                 (vm(1, gx, gy, true) - vm(1, gx - 1, gy, true))) / kSqrt2;
-            acc[1] += sqrt(e11 * e11 + e22 * e22 + e12 * e12);
+            acc[1] += (double)sqrtf((float)(e11 * e11 + e22 * e22 + e12 * e12));
             const double s11 = Yf(2, gx, gy), s22 = Yf(3, gx, gy), s12 = Yf(4, gx, gy);
             const double dx11 = ax ? Yf(2, gx + 1, gy) - s11 : 0.0;
             const double dy12 = by ? Yf(4, gx, gy + 1) - s12 : 0.0;
@@ -411,7 +423,7 @@ struct FinalArgs {
     InfoDev* info;
 };
 
-__global__ void __launch_bounds__(256) k_gap_final(FinalArgs a) {
+__global__ void __launch_bounds__(1024) k_gap_final(FinalArgs a) {
     if (*(volatile const int*)&a.info->stop) return;
     double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int b = threadIdx.x; b < a.n_data; b += blockDim.x)
@@ -607,6 +619,7 @@ struct Workspace {
     float* Y[2] = {nullptr, nullptr};
     float *q = nullptr, *ubar_pad = nullptr, *vbar0 = nullptr;
     float4* ubar_quad = nullptr;
+    float4* u_quad = nullptr;   // quads of u on gap iterations
     int* kt[2] = {nullptr, nullptr};   // fixed-point K^T q, by iteration parity
     float *tau_u = nullptr, *sig_q = nullptr, *sig_r = nullptr, *qw = nullptr;
     double *data_part = nullptr, *pix_part = nullptr;
@@ -622,13 +635,13 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     const size_t P2 = (N + 2) * (N + 2);
     ws.n_data = forward_gap_blocks(g);
     ws.n_pix = pix_blocks((int)N);
-    size_t off[18];
-    size_t sz[18] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, NN * 4 * 2,
+    size_t off[19];
+    size_t sz[19] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, NN * 4 * 2,
                      (reg == PAT_TGV ? 2 * NN : 1) * 4,
                      NN * 4, S * 4, NN * 4, (size_t)ws.n_data * 3 * 8, (size_t)ws.n_pix * 6 * 8, sizeof(InfoDev),
-                     S * 4, nx * 4, nx * 4, (N + 1) * (N + 1) * 16};
+                     S * 4, nx * 4, nx * 4, (N + 1) * (N + 1) * 16, (N + 1) * (N + 1) * 16};
     size_t total = 0;
-    for (int i = 0; i < 18; ++i) {
+    for (int i = 0; i < 19; ++i) {
         off[i] = total;
         total += align_up(sz[i]);
     }
@@ -654,6 +667,7 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     ws.XL[0] = (float*)(b + off[15]);
     ws.XL[1] = (float*)(b + off[16]);
     ws.ubar_quad = (float4*)(b + off[17]);
+    ws.u_quad = (float4*)(b + off[18]);
     return PAT_OK;
 }
 
@@ -728,6 +742,8 @@ static int launch_update(const pat_geometry* g, const pat_params* p, Workspace& 
     a.y_out = ws.Y[(it + 1) & 1];
     a.ubar_pad = ws.ubar_pad;
     a.ubar_quad = ws.ubar_quad;
+    const int done = it + 1;
+    a.u_quad = ((p->gap_every > 0 && done % p->gap_every == 0) || done == p->iters) ? ws.u_quad : nullptr;
     a.stop = &ws.info->stop;
     a.iter = &ws.info->iter;
     dim3 grd(ceil_div(N, TX), ceil_div(N, TY)), blk(TX, TY);
@@ -738,17 +754,17 @@ static int launch_update(const pat_geometry* g, const pat_params* p, Workspace& 
 
 template <int REG>
 static int launch_gap(const pat_geometry* g, const pat_params* p, Workspace& ws, const KtView& kt, const float* x,
-                      const float* x_old, const float* y, const float* q, const float* f, const int* stop,
-                      cudaStream_t st) {
+                      const float4* x_quad, const float* x_old, const float* y, const float* q, const float* f,
+                      const int* stop, cudaStream_t st) {
     const int N = g->desc.n;
-    int rc = launch_forward_gap(g, x, q, f, ws.data_part, ws.n_data, stop, st);
+    int rc = launch_forward_gap(g, x, x_quad, q, f, ws.data_part, ws.n_data, stop, st);
     if (rc) return rc;
     GapArgs ga{N, p->gamma, p->xi_dev, x, x_old, y, kt, ws.pix_part, stop};
     k_gap_pixels<REG><<<ws.n_pix, 256, 0, st>>>(ga);
     PAT_LAUNCH_CHECK("k_gap_pixels");
     FinalArgs fa{ws.data_part, ws.n_data, ws.pix_part, ws.n_pix, p->alpha, p->beta, p->box_u, p->box_v,
                  p->tol, p->reg, ws.info};
-    k_gap_final<<<1, 256, 0, st>>>(fa);
+    k_gap_final<<<1, 1024, 0, st>>>(fa);
     PAT_LAUNCH_CHECK("k_gap_final");
     return PAT_OK;
 }
@@ -773,7 +789,7 @@ static int enqueue_iterations(const pat_geometry* g, const float* f, const pat_p
         if ((p->gap_every > 0 && done % p->gap_every == 0) || done == p->iters) {
             prof_mark(PAT_PHASE_GAP, st, true);
             rc = launch_gap<REG>(g, p, ws, kt_view(g, ws.kt[it & 1], &ws.info->qmax_bits[it & 1]), ws.X[done & 1],
-                                 ws.X[it & 1], ws.Y[it & 1], ws.q, f, stop, st);
+                                 ws.u_quad, ws.X[it & 1], ws.Y[it & 1], ws.q, f, stop, st);
             if (rc) return rc;
             prof_mark(PAT_PHASE_GAP, st, false);
         }
@@ -1137,8 +1153,8 @@ static int gap_impl(const pat_geometry* g, const float* f, const pat_params* p, 
     }
     pat_params q = *p;
     q.tol = 0;
-    if (!rc) rc = launch_gap<REG>(g, &q, ws, kt_view(g, ws.kt[0], &ws.info->qmax_bits[0]), x, nullptr, y + S, y, f,
-                                  nullptr, st);
+    if (!rc) rc = launch_gap<REG>(g, &q, ws, kt_view(g, ws.kt[0], &ws.info->qmax_bits[0]), x, nullptr, nullptr,
+                                  y + S, y, f, nullptr, st);
     if (!rc) rc = cudaMemcpyAsync(&h, ws.info, sizeof(InfoDev), cudaMemcpyDeviceToHost, st) ? PAT_ERR_CUDA : 0;
     cudaFreeAsync(ws.base, st);
     cudaError_t se = cudaStreamSynchronize(st);

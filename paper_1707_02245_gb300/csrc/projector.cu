@@ -70,6 +70,7 @@ __device__ __forceinline__ float circle_partial(const GeomView& g, const float* 
     float acc = 0.f;
     int m = w.x + rl.ph;
     if (m >= g.quad_m) m -= g.quad_m;
+#pragma unroll 2
     for (int j = rl.ph; j < w.y; j += NPH) {
         const float2 cs = __ldg(&g.cs[m]);
         m += NPH;
@@ -156,13 +157,14 @@ __global__ void k_absmax(const float* __restrict__ y, long long n, unsigned* __r
 
 // FP64 partial sums for the duality gap over data rows:
 //   {sum (K u - f)^2, sum q^2, sum q f}   one triple per block
+template <bool QUAD>
 __global__ void __launch_bounds__(ROW_THREADS) k_forward_gap(GeomView g, const float* __restrict__ u,
                                                             const float* __restrict__ q, const float* __restrict__ f,
                                                             double* __restrict__ partials,
                                                             const int* __restrict__ stop) {
     if (stop && *(volatile const int*)stop) return;
     const RowLane rl = row_lane(g);
-    const float s = phase_sum(circle_partial<false>(g, u, rl));
+    const float s = phase_sum(circle_partial<QUAD>(g, u, rl));
     double a = 0.0, b = 0.0, c = 0.0;
     if (rl.valid && rl.ph == 0) {
         const float ku = s * __ldg(&g.wk[rl.k]);
@@ -428,10 +430,14 @@ int launch_forward_prox(const pat_geometry* g, const float4* ubar_quad, float* q
     return PAT_OK;
 }
 
-int launch_forward_gap(const pat_geometry* g, const float* u, const float* q, const float* f,
+int launch_forward_gap(const pat_geometry* g, const float* u, const float4* u_quad, const float* q, const float* f,
                        double* partials, int n_part, const int* stop, cudaStream_t st) {
     (void)n_part;
-    k_forward_gap<<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, u, q, f, partials, stop);
+    if (u_quad)
+        k_forward_gap<true><<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, reinterpret_cast<const float*>(u_quad), q,
+                                                                 f, partials, stop);
+    else
+        k_forward_gap<false><<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, u, q, f, partials, stop);
     PAT_LAUNCH_CHECK("k_forward_gap");
     return PAT_OK;
 }
