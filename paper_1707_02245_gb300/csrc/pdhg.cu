@@ -58,6 +58,9 @@ __device__ __forceinline__ float ld_img(const float* __restrict__ p, int N, int 
 }
 
 // One PDHG primal step plus the following dual step on a TX x TY tile.
+// Stage 1 issues every global load of the tile and its halo at once (one round trip),
+// stage 2 does the primal step and extrapolation from shared memory, stage 3 the next
+// dual step on the tile and all writes.
 template <int REG>
 __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
     if (a.stop && *(volatile const int*)a.stop) return;
@@ -65,45 +68,67 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
     const size_t NN = (size_t)N * N;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int tid = threadIdx.y * TX + threadIdx.x;
+    constexpr bool TGV = REG == PAT_TGV;
+    constexpr int VL = TGV ? LY : 1, VX = TGV ? LX : 1, VT = TGV ? TY : 1, VTX = TGV ? TX : 1;
 
     __shared__ float s_r1m[LY][LX], s_r2m[LY][LX];   // r (dTV: D_xi r) masked for div
+    __shared__ float s_r1[LY][LX], s_r2[LY][LX];     // r as stored
+    __shared__ float s_u[LY][LX], s_ul[LY][LX], s_w[LY][LX], s_tu[LY][LX];
     __shared__ float s_ub[LY][LX];                   // ubar on U = tile + high halo
     __shared__ float s_uU[LY][LX];                   // u^{n+1} on U (for the gap's quads)
     __shared__ float s_un[TY][TX], s_unl[TY][TX];    // u^{n+1} (high, low) on the tile
-    // TGV only (small arrays for TV / dTV)
-    constexpr int VL = (REG == PAT_TGV) ? LY : 1;
-    constexpr int VX = (REG == PAT_TGV) ? LX : 1;
-    constexpr int VT = (REG == PAT_TGV) ? TY : 1;
-    constexpr int VTX = (REG == PAT_TGV) ? TX : 1;
     __shared__ float s_s11[VL][VX], s_s22[VL][VX], s_s12[VL][VX];
+    __shared__ float s_v1[VL][VX], s_v2[VL][VX], s_v1l[VL][VX], s_v2l[VL][VX];
     __shared__ float s_vb1[VL][VX], s_vb2[VL][VX];   // vbar on V = tile + low halo
     __shared__ float s_vn1[VT][VTX], s_vn2[VT][VTX], s_vnl1[VT][VTX], s_vnl2[VT][VTX];
 
-    const float* u_in = a.x_in;
-    const float* r1_in = a.y_in;
-    const float* r2_in = a.y_in + NN;
+    // stage-3 values of this thread's own pixel that stage 1 does not stage
+    const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
+    const int gi = gy * N + gx;
+    const bool mine = gx < N && gy < N;
+    float xi0 = 0.f, xi1 = 0.f, sr_dtv = 0.f;
+    if (REG == PAT_DTV && mine) {
+        xi0 = __ldg(a.xi + gi);
+        xi1 = __ldg(a.xi + NN + gi);
+        sr_dtv = a.sig2 >= 0.f ? a.sig2 : __ldg(a.sig_r + gi);
+    }
 
-    // ---- stage 1: dual fields on the tile plus halo -------------------------------
+    // ---- stage 1: every input of the tile plus halo -----------------------------------
     for (int c = tid; c < LX * LY; c += TX * TY) {
         const int lx = c % LX, ly = c / LX;
-        const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-        const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
-        float r1 = in ? __ldg(r1_in + gy * N + gx) : 0.f;
-        float r2 = in ? __ldg(r2_in + gy * N + gx) : 0.f;
+        const int cx = x0 - 1 + lx, cy = y0 - 1 + ly;
+        const bool in = cx >= 0 && cx < N && cy >= 0 && cy < N;
+        const int ci = in ? cy * N + cx : 0;
+        float r1 = in ? __ldg(a.y_in + ci) : 0.f;
+        float r2 = in ? __ldg(a.y_in + NN + ci) : 0.f;
+        s_r1[ly][lx] = r1;
+        s_r2[ly][lx] = r2;
+        if (lx >= 1 && ly >= 1) {  // U cells
+            s_u[ly][lx] = in ? __ldg(a.x_in + ci) : 0.f;
+            s_ul[ly][lx] = in ? __ldg(a.xl_in + ci) : 0.f;
+            s_w[ly][lx] = in ? a.kt.at(cx, cy, N) : 0.f;
+            s_tu[ly][lx] = in ? (a.tau >= 0.f ? a.tau : __ldg(a.tau_u + ci)) : 0.f;
+        }
         if (REG == PAT_DTV) {
-            const float xi0 = in ? __ldg(a.xi + gy * N + gx) : 0.f;
-            const float xi1 = in ? __ldg(a.xi + NN + gy * N + gx) : 0.f;
+            const float z0 = in ? __ldg(a.xi + ci) : 0.f;
+            const float z1 = in ? __ldg(a.xi + NN + ci) : 0.f;
             float o0, o1;
-            dxi_apply(xi0, xi1, a.gamma, r1, r2, o0, o1);
+            dxi_apply(z0, z1, a.gamma, r1, r2, o0, o1);
             r1 = o0;
             r2 = o1;
         }
-        s_r1m[ly][lx] = (gx < N - 1) ? r1 : 0.f;
-        s_r2m[ly][lx] = (gy < N - 1) ? r2 : 0.f;
-        if (REG == PAT_TGV) {
-            s_s11[ly][lx] = in ? __ldg(a.y_in + 2 * NN + gy * N + gx) : 0.f;
-            s_s22[ly][lx] = in ? __ldg(a.y_in + 3 * NN + gy * N + gx) : 0.f;
-            s_s12[ly][lx] = in ? __ldg(a.y_in + 4 * NN + gy * N + gx) : 0.f;
+        s_r1m[ly][lx] = (cx < N - 1) ? r1 : 0.f;
+        s_r2m[ly][lx] = (cy < N - 1) ? r2 : 0.f;
+        if (TGV) {
+            s_s11[ly][lx] = in ? __ldg(a.y_in + 2 * NN + ci) : 0.f;
+            s_s22[ly][lx] = in ? __ldg(a.y_in + 3 * NN + ci) : 0.f;
+            s_s12[ly][lx] = in ? __ldg(a.y_in + 4 * NN + ci) : 0.f;
+            if (lx <= TX && ly <= TY) {  // V cells
+                s_v1[ly][lx] = in ? __ldg(a.x_in + NN + ci) : 0.f;
+                s_v2[ly][lx] = in ? __ldg(a.x_in + 2 * NN + ci) : 0.f;
+                s_v1l[ly][lx] = in ? __ldg(a.xl_in + NN + ci) : 0.f;
+                s_v2l[ly][lx] = in ? __ldg(a.xl_in + 2 * NN + ci) : 0.f;
+            }
         }
     }
     __syncthreads();
@@ -111,33 +136,29 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
     // ---- stage 2: primal step and extrapolation on U (u) and V (v) ------------------
     for (int c = tid; c < LX * LY; c += TX * TY) {
         const int lx = c % LX, ly = c / LX;
-        const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-        const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
+        const int cx = x0 - 1 + lx, cy = y0 - 1 + ly;
+        const bool in = cx >= 0 && cx < N && cy >= 0 && cy < N;
         if (lx >= 1 && ly >= 1) {  // U: u^{n+1}, ubar
-            float ub = 0.f;
+            float ub = 0.f, un = 0.f;
             if (in) {
-                const int gi = gy * N + gx;
                 const float divr = s_r1m[ly][lx] - s_r1m[ly][lx - 1] + s_r2m[ly][lx] - s_r2m[ly - 1][lx];
-                const float w = a.kt.at(gx, gy, N);
-                const float uo = __ldg(u_in + gi), uol = __ldg(a.xl_in + gi);
-                const float tu = a.tau >= 0.f ? a.tau : __ldg(a.tau_u + gi);
-                float un = uo, unl = uol;
-                add_compensated(un, unl, -tu * (w - divr));
+                const float uo = s_u[ly][lx], uol = s_ul[ly][lx];
+                float unl = uol;
+                un = uo;
+                add_compensated(un, unl, -s_tu[ly][lx] * (s_w[ly][lx] - divr));
                 ub = fmaf(a.theta, (un - uo) + (unl - uol), un + unl);
-                s_uU[ly][lx] = un;
                 if (lx <= TX && ly <= TY) {
                     s_un[ly - 1][lx - 1] = un;
                     s_unl[ly - 1][lx - 1] = unl;
                 }
             }
-            if (!in) s_uU[ly][lx] = 0.f;
+            s_uU[ly][lx] = un;
             s_ub[ly][lx] = ub;
         }
-        if (REG == PAT_TGV && lx <= TX && ly <= TY) {  // V: v^{n+1}, vbar
+        if (TGV && lx <= TX && ly <= TY) {  // V: v^{n+1}, vbar
             float vb1 = 0.f, vb2 = 0.f;
             if (in) {
-                const int gi = gy * N + gx;
-                const bool ax = gx < N - 1, by = gy < N - 1;
+                const bool ax = cx < N - 1, by = cy < N - 1;
                 // E^T s = (-d_x^+ s11 - d_y^+ s12 / sqrt2, -d_y^+ s22 - d_x^+ s12 / sqrt2)
                 const float dx11 = ax ? s_s11[ly][lx + 1] - s_s11[ly][lx] : 0.f;
                 const float dy12 = by ? s_s12[ly + 1][lx] - s_s12[ly][lx] : 0.f;
@@ -145,14 +166,12 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
                 const float dx12 = ax ? s_s12[ly][lx + 1] - s_s12[ly][lx] : 0.f;
                 const float et1 = -dx11 - dy12 * kInvSqrt2f;
                 const float et2 = -dy22 - dx12 * kInvSqrt2f;
-                const float r1 = __ldg(r1_in + gi), r2 = __ldg(r2_in + gi);
-                const float v1o = __ldg(a.x_in + NN + gi), v2o = __ldg(a.x_in + 2 * NN + gi);
-                const float v1ol = __ldg(a.xl_in + NN + gi), v2ol = __ldg(a.xl_in + 2 * NN + gi);
-                const float t1 = a.tau >= 0.f ? a.tau : tau_v1_tgv(gx, gy, N);
-                const float t2 = a.tau >= 0.f ? a.tau : tau_v2_tgv(gx, gy, N);
+                const float t1 = a.tau >= 0.f ? a.tau : tau_v1_tgv(cx, cy, N);
+                const float t2 = a.tau >= 0.f ? a.tau : tau_v2_tgv(cx, cy, N);
+                const float v1o = s_v1[ly][lx], v2o = s_v2[ly][lx], v1ol = s_v1l[ly][lx], v2ol = s_v2l[ly][lx];
                 float v1n = v1o, v1nl = v1ol, v2n = v2o, v2nl = v2ol;
-                add_compensated(v1n, v1nl, -t1 * (et1 - r1));
-                add_compensated(v2n, v2nl, -t2 * (et2 - r2));
+                add_compensated(v1n, v1nl, -t1 * (et1 - s_r1[ly][lx]));
+                add_compensated(v2n, v2nl, -t2 * (et2 - s_r2[ly][lx]));
                 vb1 = fmaf(a.theta, (v1n - v1o) + (v1nl - v1ol), v1n + v1nl);
                 vb2 = fmaf(a.theta, (v2n - v2o) + (v2nl - v2ol), v2n + v2nl);
                 if (lx >= 1 && ly >= 1) {
@@ -170,24 +189,21 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
 
     // ---- stage 3: dual step of the next iteration on the tile, and the writes --------
     const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
-    const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
-    if (gx < N && gy < N) {
-        const int gi = gy * N + gx;
+    if (mine) {
         const bool ax = gx < N - 1, by = gy < N - 1;
         const float ub = s_ub[ly][lx];
         const float gu0 = ax ? s_ub[ly][lx + 1] - ub : 0.f;
         const float gu1 = by ? s_ub[ly + 1][lx] - ub : 0.f;
-        float r1 = __ldg(r1_in + gi), r2 = __ldg(r2_in + gi);
+        float r1 = s_r1[ly][lx], r2 = s_r2[ly][lx];
         if (REG == PAT_TV) {
             const float sr = a.sig2 >= 0.f ? a.sig2 : sig_r_tv(gx, gy, N);
             r1 = fmaf(sr, gu0, r1);
             r2 = fmaf(sr, gu1, r2);
         } else if (REG == PAT_DTV) {
-            const float sr = a.sig2 >= 0.f ? a.sig2 : __ldg(a.sig_r + gi);
             float o0, o1;
-            dxi_apply(__ldg(a.xi + gi), __ldg(a.xi + NN + gi), a.gamma, gu0, gu1, o0, o1);
-            r1 = fmaf(sr, o0, r1);
-            r2 = fmaf(sr, o1, r2);
+            dxi_apply(xi0, xi1, a.gamma, gu0, gu1, o0, o1);
+            r1 = fmaf(sr_dtv, o0, r1);
+            r2 = fmaf(sr_dtv, o1, r2);
         } else {
             const float sr = a.sig2 >= 0.f ? a.sig2 : sig_r_tgv(gx, gy, N);
             r1 = fmaf(sr, gu0 - s_vb1[ly][lx], r1);
@@ -215,7 +231,7 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
                 if (gx == 0 && gy == 0) a.u_quad[0] = make_float4(0.f, 0.f, 0.f, uu);
             }
         }
-        if (REG == PAT_TGV) {
+        if (TGV) {
             // E vbar with d^- on the masked field
             const bool axm = gx >= 1, bym = gy >= 1;
             const float v1 = ax ? s_vb1[ly][lx] : 0.f, v1l = axm ? s_vb1[ly][lx - 1] : 0.f;
@@ -238,8 +254,8 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
             a.xl_out[NN + gi] = s_vnl1[threadIdx.y][threadIdx.x];
             a.xl_out[2 * NN + gi] = s_vnl2[threadIdx.y][threadIdx.x];
         }
+        a.kt_clear[gi] = 0;
     }
-    if (gx < N && gy < N) a.kt_clear[gy * N + gx] = 0;
     if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
         if (a.iter) *a.iter += 1;
         *a.qmax_next = 0u;
@@ -330,75 +346,71 @@ __global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
     if (a.stop && *(volatile const int*)a.stop) return;
     const int N = a.n;
     const size_t NN = (size_t)N * N;
+    const float gam = (float)a.gamma;
     double acc[6] = {0, 0, 0, 0, 0, 0};
     const int nthreads = gridDim.x * blockDim.x;
-    auto X = [&](int c, int x, int y) -> double { return (double)a.x[c * NN + (size_t)y * N + x]; };
-    auto Yf = [&](int c, int x, int y) -> double { return (double)a.y[c * NN + (size_t)y * N + x]; };
+    auto X = [&](int c, int x, int y) -> float { return __ldg(a.x + c * NN + (size_t)y * N + x); };
+    auto Yf = [&](int c, int x, int y) -> float { return __ldg(a.y + c * NN + (size_t)y * N + x); };
+    // r masked for div (dTV: D_xi r), zero outside the grid
+    auto rm = [&](int c, int x, int y) -> float {
+        if (x < 0 || y < 0 || (c == 0 && x >= N - 1) || (c == 1 && y >= N - 1)) return 0.f;
+        float r0 = Yf(0, x, y), r1 = Yf(1, x, y);
+        if (REG == PAT_DTV) {
+            float o0, o1;
+            dxi_apply(__ldg(a.xi + (size_t)y * N + x), __ldg(a.xi + NN + (size_t)y * N + x), gam, r0, r1, o0, o1);
+            r0 = o0;
+            r1 = o1;
+        }
+        return c == 0 ? r0 : r1;
+    };
     for (long long p = blockIdx.x * blockDim.x + threadIdx.x; p < (long long)NN; p += nthreads) {
         const int gx = (int)(p % N), gy = (int)(p / N);
         const bool ax = gx < N - 1, by = gy < N - 1;
-        // gradient of u
-        const double u = X(0, gx, gy);
-        double g0 = ax ? X(0, gx + 1, gy) - u : 0.0;
-        double g1 = by ? X(0, gx, gy + 1) - u : 0.0;
-        // D_xi for dTV
-        double xi0 = 0, xi1 = 0;
+        // regulariser terms: FP32 per term, FP64 sums
+        const float u = X(0, gx, gy);
+        float g0 = ax ? X(0, gx + 1, gy) - u : 0.f;
+        float g1 = by ? X(0, gx, gy + 1) - u : 0.f;
         if (REG == PAT_DTV) {
-            xi0 = a.xi[gy * N + gx];
-            xi1 = a.xi[NN + gy * N + gx];
-            const double dot = xi0 * g0 + xi1 * g1;
-            const double t0 = g0 - a.gamma * xi0 * dot, t1 = g1 - a.gamma * xi1 * dot;
-            g0 = t0;
-            g1 = t1;
+            float o0, o1;
+            dxi_apply(__ldg(a.xi + p), __ldg(a.xi + NN + p), gam, g0, g1, o0, o1);
+            g0 = o0;
+            g1 = o1;
         }
         if (REG == PAT_TGV) {
             g0 -= X(1, gx, gy);
             g1 -= X(2, gx, gy);
         }
-        // the regulariser terms need only FP32 accuracy per term (they are summed in FP64)
-        acc[0] += (double)sqrtf((float)(g0 * g0 + g1 * g1));
-        // (masked, D_xi-weighted) r for div
-        auto rm = [&](int c, int x, int y) -> double {
-            if (x < 0 || y < 0) return 0.0;
-            if (c == 0 && x >= N - 1) return 0.0;
-            if (c == 1 && y >= N - 1) return 0.0;
-            double r0 = Yf(0, x, y), r1 = Yf(1, x, y);
-            if (REG == PAT_DTV) {
-                const double z0 = a.xi[y * N + x], z1 = a.xi[NN + y * N + x];
-                const double dot = z0 * r0 + z1 * r1;
-                const double o0 = r0 - a.gamma * z0 * dot, o1 = r1 - a.gamma * z1 * dot;
-                return c == 0 ? o0 : o1;
-            }
-            return c == 0 ? r0 : r1;
-        };
-        const double divr = rm(0, gx, gy) - rm(0, gx - 1, gy) + rm(1, gx, gy) - rm(1, gx, gy - 1);
-        const double w = (double)a.kt.at(gx, gy, N);
-        acc[2] += fabs(w - divr);
+        acc[0] += (double)sqrtf(g0 * g0 + g1 * g1);
+        // box term of u: |K^T q - div r| in FP64 from the FP32 fields
+        const double divr = ((double)rm(0, gx, gy) - (double)rm(0, gx - 1, gy)) +
+                            ((double)rm(1, gx, gy) - (double)rm(1, gx, gy - 1));
+        acc[2] += fabs((double)a.kt.at(gx, gy, N) - divr);
         if (REG == PAT_TGV) {
-            auto vm = [&](int c, int x, int y, bool mx) -> double {  // masked v for d^-
-                if (x < 0 || y < 0) return 0.0;
-                if (mx ? (x >= N - 1) : (y >= N - 1)) return 0.0;
+            auto vm = [&](int c, int x, int y, bool mx) -> float {  // masked v for d^-
+                if (x < 0 || y < 0 || (mx ? (x >= N - 1) : (y >= N - 1))) return 0.f;
                 return X(1 + c, x, y);
             };
-            const double e11 = vm(0, gx, gy, true) - vm(0, gx - 1, gy, true);
-            const double e22 = vm(1, gx, gy, false) - vm(1, gx, gy - 1, false);
-            const double e12 = ((vm(0, gx, gy, false) - vm(0, gx, gy - 1, false)) +
-                                (vm(1, gx, gy, true) - vm(1, gx - 1, gy, true))) / kSqrt2;
-            acc[1] += (double)sqrtf((float)(e11 * e11 + e22 * e22 + e12 * e12));
+            const float e11 = vm(0, gx, gy, true) - vm(0, gx - 1, gy, true);
+            const float e22 = vm(1, gx, gy, false) - vm(1, gx, gy - 1, false);
+            const float e12 = ((vm(0, gx, gy, false) - vm(0, gx, gy - 1, false)) +
+                               (vm(1, gx, gy, true) - vm(1, gx - 1, gy, true))) * kInvSqrt2f;
+            acc[1] += (double)sqrtf(e11 * e11 + e22 * e22 + e12 * e12);
+            // box term of v: |E^T s - r|_1 in FP64
             const double s11 = Yf(2, gx, gy), s22 = Yf(3, gx, gy), s12 = Yf(4, gx, gy);
-            const double dx11 = ax ? Yf(2, gx + 1, gy) - s11 : 0.0;
-            const double dy12 = by ? Yf(4, gx, gy + 1) - s12 : 0.0;
-            const double dy22 = by ? Yf(3, gx, gy + 1) - s22 : 0.0;
-            const double dx12 = ax ? Yf(4, gx + 1, gy) - s12 : 0.0;
+            const double dx11 = ax ? (double)Yf(2, gx + 1, gy) - s11 : 0.0;
+            const double dy12 = by ? (double)Yf(4, gx, gy + 1) - s12 : 0.0;
+            const double dy22 = by ? (double)Yf(3, gx, gy + 1) - s22 : 0.0;
+            const double dx12 = ax ? (double)Yf(4, gx + 1, gy) - s12 : 0.0;
             const double et1 = -dx11 - dy12 / kSqrt2, et2 = -dy22 - dx12 / kSqrt2;
-            acc[3] += fabs(et1 - Yf(0, gx, gy)) + fabs(et2 - Yf(1, gx, gy));
+            acc[3] += fabs(et1 - (double)Yf(0, gx, gy)) + fabs(et2 - (double)Yf(1, gx, gy));
         }
         if (a.x_old) {
             const int nc = REG == PAT_TGV ? 3 : 1;
             for (int c = 0; c < nc; ++c) {
-                const double xn = X(c, gx, gy), xo = (double)a.x_old[c * NN + (size_t)gy * N + gx];
-                acc[4] += (xn - xo) * (xn - xo);
-                acc[5] += xo * xo;
+                const float xn = X(c, gx, gy), xo = __ldg(a.x_old + c * NN + p);
+                const double dxv = (double)(xn - xo);
+                acc[4] += dxv * dxv;
+                acc[5] += (double)xo * (double)xo;
             }
         }
     }
@@ -407,10 +419,14 @@ __global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
         for (int c = 0; c < 6; ++c) a.partials[6 * blockIdx.x + c] = acc[c];
 }
 
+constexpr int GAP_FINAL_BLOCKS = 32;
+
 struct InfoDev {
     double primal, dual, gap, rel_gap, residual;
     int iters_done, status, stop, iter;
     unsigned qmax_bits[2];  // max |q| of iterations of each parity (float bits)
+    unsigned final_ticket;  // blocks of k_gap_final done (the last one resets it)
+    double level2[GAP_FINAL_BLOCKS][9];
 };
 
 struct FinalArgs {
@@ -423,24 +439,40 @@ struct FinalArgs {
     InfoDev* info;
 };
 
-__global__ void __launch_bounds__(1024) k_gap_final(FinalArgs a) {
+// Two-level FP64 reduction in a fixed order: each of GAP_FINAL_BLOCKS blocks sums a fixed
+// strided subset of the partials, the last block to finish adds the block sums in index
+// order and evaluates the gap, the residual and the stopping test.
+__global__ void __launch_bounds__(256) k_gap_final(FinalArgs a) {
     if (*(volatile const int*)&a.info->stop) return;
     double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int b = threadIdx.x; b < a.n_data; b += blockDim.x)
+    const int stride = gridDim.x * blockDim.x;
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < a.n_data; b += stride)
         for (int c = 0; c < 3; ++c) acc[c] += a.data_part[3 * b + c];
-    for (int b = threadIdx.x; b < a.n_pix; b += blockDim.x)
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < a.n_pix; b += stride)
         for (int c = 0; c < 6; ++c) acc[3 + c] += a.pix_part[6 * b + c];
     block_sum<9>(acc);
-    if (threadIdx.x != 0) return;
-    const double res2 = acc[0], q2 = acc[1], qf = acc[2];
-    const double r1 = acc[3], r2 = acc[4], bu = acc[5], bv = acc[6], dx2 = acc[7], x2 = acc[8];
+    __shared__ bool s_last;
+    InfoDev* in = a.info;
+    if (threadIdx.x == 0) {
+        for (int c = 0; c < 9; ++c) in->level2[blockIdx.x][c] = acc[c];
+        __threadfence();
+        s_last = atomicAdd(&in->final_ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last || threadIdx.x != 0) return;
+    __threadfence();
+    in->final_ticket = 0;
+    double t[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < (int)gridDim.x; ++b)
+        for (int c = 0; c < 9; ++c) t[c] += *(volatile double*)&in->level2[b][c];
+    const double res2 = t[0], q2 = t[1], qf = t[2];
+    const double r1 = t[3], r2 = t[4], bu = t[5], bv = t[6], dx2 = t[7], x2 = t[8];
     const double reg = a.reg == PAT_TGV ? r1 + a.beta * r2 : r1;
     const double primal = 0.5 * res2 + a.alpha * reg;
     const double dual = -(0.5 * q2 + qf) - a.box_u * bu - (a.reg == PAT_TGV ? a.box_v * bv : 0.0);
     const double gap = primal - dual;
     const double rel = primal > 0 ? gap / primal : (gap == 0 ? 0.0 : INFINITY);
     const double resid = x2 > 0 ? sqrt(dx2 / x2) : (dx2 == 0 ? 0.0 : INFINITY);
-    InfoDev* in = a.info;
     in->primal = primal;
     in->dual = dual;
     in->gap = gap;
@@ -764,7 +796,7 @@ static int launch_gap(const pat_geometry* g, const pat_params* p, Workspace& ws,
     PAT_LAUNCH_CHECK("k_gap_pixels");
     FinalArgs fa{ws.data_part, ws.n_data, ws.pix_part, ws.n_pix, p->alpha, p->beta, p->box_u, p->box_v,
                  p->tol, p->reg, ws.info};
-    k_gap_final<<<1, 1024, 0, st>>>(fa);
+    k_gap_final<<<GAP_FINAL_BLOCKS, 256, 0, st>>>(fa);
     PAT_LAUNCH_CHECK("k_gap_final");
     return PAT_OK;
 }
