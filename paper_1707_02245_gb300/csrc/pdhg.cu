@@ -58,9 +58,6 @@ __device__ __forceinline__ float ld_img(const float* __restrict__ p, int N, int 
 }
 
 // One PDHG primal step plus the following dual step on a TX x TY tile.
-// Stage 1 issues every global load of the tile and its halo at once (one round trip),
-// stage 2 does the primal step and extrapolation from shared memory, stage 3 the next
-// dual step on the tile and all writes.
 template <int REG>
 __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
     if (a.stop && *(volatile const int*)a.stop) return;
@@ -68,67 +65,45 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
     const size_t NN = (size_t)N * N;
     const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    constexpr bool TGV = REG == PAT_TGV;
-    constexpr int VL = TGV ? LY : 1, VX = TGV ? LX : 1, VT = TGV ? TY : 1, VTX = TGV ? TX : 1;
 
     __shared__ float s_r1m[LY][LX], s_r2m[LY][LX];   // r (dTV: D_xi r) masked for div
-    __shared__ float s_r1[LY][LX], s_r2[LY][LX];     // r as stored
-    __shared__ float s_u[LY][LX], s_ul[LY][LX], s_w[LY][LX], s_tu[LY][LX];
     __shared__ float s_ub[LY][LX];                   // ubar on U = tile + high halo
     __shared__ float s_uU[LY][LX];                   // u^{n+1} on U (for the gap's quads)
     __shared__ float s_un[TY][TX], s_unl[TY][TX];    // u^{n+1} (high, low) on the tile
+    // TGV only (small arrays for TV / dTV)
+    constexpr int VL = (REG == PAT_TGV) ? LY : 1;
+    constexpr int VX = (REG == PAT_TGV) ? LX : 1;
+    constexpr int VT = (REG == PAT_TGV) ? TY : 1;
+    constexpr int VTX = (REG == PAT_TGV) ? TX : 1;
     __shared__ float s_s11[VL][VX], s_s22[VL][VX], s_s12[VL][VX];
-    __shared__ float s_v1[VL][VX], s_v2[VL][VX], s_v1l[VL][VX], s_v2l[VL][VX];
     __shared__ float s_vb1[VL][VX], s_vb2[VL][VX];   // vbar on V = tile + low halo
     __shared__ float s_vn1[VT][VTX], s_vn2[VT][VTX], s_vnl1[VT][VTX], s_vnl2[VT][VTX];
 
-    // stage-3 values of this thread's own pixel that stage 1 does not stage
-    const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
-    const int gi = gy * N + gx;
-    const bool mine = gx < N && gy < N;
-    float xi0 = 0.f, xi1 = 0.f, sr_dtv = 0.f;
-    if (REG == PAT_DTV && mine) {
-        xi0 = __ldg(a.xi + gi);
-        xi1 = __ldg(a.xi + NN + gi);
-        sr_dtv = a.sig2 >= 0.f ? a.sig2 : __ldg(a.sig_r + gi);
-    }
+    const float* u_in = a.x_in;
+    const float* r1_in = a.y_in;
+    const float* r2_in = a.y_in + NN;
 
-    // ---- stage 1: every input of the tile plus halo -----------------------------------
+    // ---- stage 1: dual fields on the tile plus halo -------------------------------
     for (int c = tid; c < LX * LY; c += TX * TY) {
         const int lx = c % LX, ly = c / LX;
-        const int cx = x0 - 1 + lx, cy = y0 - 1 + ly;
-        const bool in = cx >= 0 && cx < N && cy >= 0 && cy < N;
-        const int ci = in ? cy * N + cx : 0;
-        float r1 = in ? __ldg(a.y_in + ci) : 0.f;
-        float r2 = in ? __ldg(a.y_in + NN + ci) : 0.f;
-        s_r1[ly][lx] = r1;
-        s_r2[ly][lx] = r2;
-        if (lx >= 1 && ly >= 1) {  // U cells
-            s_u[ly][lx] = in ? __ldg(a.x_in + ci) : 0.f;
-            s_ul[ly][lx] = in ? __ldg(a.xl_in + ci) : 0.f;
-            s_w[ly][lx] = in ? a.kt.at(cx, cy, N) : 0.f;
-            s_tu[ly][lx] = in ? (a.tau >= 0.f ? a.tau : __ldg(a.tau_u + ci)) : 0.f;
-        }
+        const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+        const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
+        float r1 = in ? __ldg(r1_in + gy * N + gx) : 0.f;
+        float r2 = in ? __ldg(r2_in + gy * N + gx) : 0.f;
         if (REG == PAT_DTV) {
-            const float z0 = in ? __ldg(a.xi + ci) : 0.f;
-            const float z1 = in ? __ldg(a.xi + NN + ci) : 0.f;
+            const float xi0 = in ? __ldg(a.xi + gy * N + gx) : 0.f;
+            const float xi1 = in ? __ldg(a.xi + NN + gy * N + gx) : 0.f;
             float o0, o1;
-            dxi_apply(z0, z1, a.gamma, r1, r2, o0, o1);
+            dxi_apply(xi0, xi1, a.gamma, r1, r2, o0, o1);
             r1 = o0;
             r2 = o1;
         }
-        s_r1m[ly][lx] = (cx < N - 1) ? r1 : 0.f;
-        s_r2m[ly][lx] = (cy < N - 1) ? r2 : 0.f;
-        if (TGV) {
-            s_s11[ly][lx] = in ? __ldg(a.y_in + 2 * NN + ci) : 0.f;
-            s_s22[ly][lx] = in ? __ldg(a.y_in + 3 * NN + ci) : 0.f;
-            s_s12[ly][lx] = in ? __ldg(a.y_in + 4 * NN + ci) : 0.f;
-            if (lx <= TX && ly <= TY) {  // V cells
-                s_v1[ly][lx] = in ? __ldg(a.x_in + NN + ci) : 0.f;
-                s_v2[ly][lx] = in ? __ldg(a.x_in + 2 * NN + ci) : 0.f;
-                s_v1l[ly][lx] = in ? __ldg(a.xl_in + NN + ci) : 0.f;
-                s_v2l[ly][lx] = in ? __ldg(a.xl_in + 2 * NN + ci) : 0.f;
-            }
+        s_r1m[ly][lx] = (gx < N - 1) ? r1 : 0.f;
+        s_r2m[ly][lx] = (gy < N - 1) ? r2 : 0.f;
+        if (REG == PAT_TGV) {
+            s_s11[ly][lx] = in ? __ldg(a.y_in + 2 * NN + gy * N + gx) : 0.f;
+            s_s22[ly][lx] = in ? __ldg(a.y_in + 3 * NN + gy * N + gx) : 0.f;
+            s_s12[ly][lx] = in ? __ldg(a.y_in + 4 * NN + gy * N + gx) : 0.f;
         }
     }
     __syncthreads();
@@ -136,29 +111,33 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
     // ---- stage 2: primal step and extrapolation on U (u) and V (v) ------------------
     for (int c = tid; c < LX * LY; c += TX * TY) {
         const int lx = c % LX, ly = c / LX;
-        const int cx = x0 - 1 + lx, cy = y0 - 1 + ly;
-        const bool in = cx >= 0 && cx < N && cy >= 0 && cy < N;
+        const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+        const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
         if (lx >= 1 && ly >= 1) {  // U: u^{n+1}, ubar
-            float ub = 0.f, un = 0.f;
+            float ub = 0.f;
             if (in) {
+                const int gi = gy * N + gx;
                 const float divr = s_r1m[ly][lx] - s_r1m[ly][lx - 1] + s_r2m[ly][lx] - s_r2m[ly - 1][lx];
-                const float uo = s_u[ly][lx], uol = s_ul[ly][lx];
-                float unl = uol;
-                un = uo;
-                add_compensated(un, unl, -s_tu[ly][lx] * (s_w[ly][lx] - divr));
+                const float w = a.kt.at(gx, gy, N);
+                const float uo = __ldg(u_in + gi), uol = __ldg(a.xl_in + gi);
+                const float tu = a.tau >= 0.f ? a.tau : __ldg(a.tau_u + gi);
+                float un = uo, unl = uol;
+                add_compensated(un, unl, -tu * (w - divr));
                 ub = fmaf(a.theta, (un - uo) + (unl - uol), un + unl);
+                s_uU[ly][lx] = un;
                 if (lx <= TX && ly <= TY) {
                     s_un[ly - 1][lx - 1] = un;
                     s_unl[ly - 1][lx - 1] = unl;
                 }
             }
-            s_uU[ly][lx] = un;
+            if (!in) s_uU[ly][lx] = 0.f;
             s_ub[ly][lx] = ub;
         }
-        if (TGV && lx <= TX && ly <= TY) {  // V: v^{n+1}, vbar
+        if (REG == PAT_TGV && lx <= TX && ly <= TY) {  // V: v^{n+1}, vbar
             float vb1 = 0.f, vb2 = 0.f;
             if (in) {
-                const bool ax = cx < N - 1, by = cy < N - 1;
+                const int gi = gy * N + gx;
+                const bool ax = gx < N - 1, by = gy < N - 1;
                 // E^T s = (-d_x^+ s11 - d_y^+ s12 / sqrt2, -d_y^+ s22 - d_x^+ s12 / sqrt2)
                 const float dx11 = ax ? s_s11[ly][lx + 1] - s_s11[ly][lx] : 0.f;
                 const float dy12 = by ? s_s12[ly + 1][lx] - s_s12[ly][lx] : 0.f;
@@ -166,12 +145,14 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
                 const float dx12 = ax ? s_s12[ly][lx + 1] - s_s12[ly][lx] : 0.f;
                 const float et1 = -dx11 - dy12 * kInvSqrt2f;
                 const float et2 = -dy22 - dx12 * kInvSqrt2f;
-                const float t1 = a.tau >= 0.f ? a.tau : tau_v1_tgv(cx, cy, N);
-                const float t2 = a.tau >= 0.f ? a.tau : tau_v2_tgv(cx, cy, N);
-                const float v1o = s_v1[ly][lx], v2o = s_v2[ly][lx], v1ol = s_v1l[ly][lx], v2ol = s_v2l[ly][lx];
+                const float r1 = __ldg(r1_in + gi), r2 = __ldg(r2_in + gi);
+                const float v1o = __ldg(a.x_in + NN + gi), v2o = __ldg(a.x_in + 2 * NN + gi);
+                const float v1ol = __ldg(a.xl_in + NN + gi), v2ol = __ldg(a.xl_in + 2 * NN + gi);
+                const float t1 = a.tau >= 0.f ? a.tau : tau_v1_tgv(gx, gy, N);
+                const float t2 = a.tau >= 0.f ? a.tau : tau_v2_tgv(gx, gy, N);
                 float v1n = v1o, v1nl = v1ol, v2n = v2o, v2nl = v2ol;
-                add_compensated(v1n, v1nl, -t1 * (et1 - s_r1[ly][lx]));
-                add_compensated(v2n, v2nl, -t2 * (et2 - s_r2[ly][lx]));
+                add_compensated(v1n, v1nl, -t1 * (et1 - r1));
+                add_compensated(v2n, v2nl, -t2 * (et2 - r2));
                 vb1 = fmaf(a.theta, (v1n - v1o) + (v1nl - v1ol), v1n + v1nl);
                 vb2 = fmaf(a.theta, (v2n - v2o) + (v2nl - v2ol), v2n + v2nl);
                 if (lx >= 1 && ly >= 1) {
@@ -189,21 +170,24 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
 
     // ---- stage 3: dual step of the next iteration on the tile, and the writes --------
     const int lx = threadIdx.x + 1, ly = threadIdx.y + 1;
-    if (mine) {
+    const int gx = x0 + threadIdx.x, gy = y0 + threadIdx.y;
+    if (gx < N && gy < N) {
+        const int gi = gy * N + gx;
         const bool ax = gx < N - 1, by = gy < N - 1;
         const float ub = s_ub[ly][lx];
         const float gu0 = ax ? s_ub[ly][lx + 1] - ub : 0.f;
         const float gu1 = by ? s_ub[ly + 1][lx] - ub : 0.f;
-        float r1 = s_r1[ly][lx], r2 = s_r2[ly][lx];
+        float r1 = __ldg(r1_in + gi), r2 = __ldg(r2_in + gi);
         if (REG == PAT_TV) {
             const float sr = a.sig2 >= 0.f ? a.sig2 : sig_r_tv(gx, gy, N);
             r1 = fmaf(sr, gu0, r1);
             r2 = fmaf(sr, gu1, r2);
         } else if (REG == PAT_DTV) {
+            const float sr = a.sig2 >= 0.f ? a.sig2 : __ldg(a.sig_r + gi);
             float o0, o1;
-            dxi_apply(xi0, xi1, a.gamma, gu0, gu1, o0, o1);
-            r1 = fmaf(sr_dtv, o0, r1);
-            r2 = fmaf(sr_dtv, o1, r2);
+            dxi_apply(__ldg(a.xi + gi), __ldg(a.xi + NN + gi), a.gamma, gu0, gu1, o0, o1);
+            r1 = fmaf(sr, o0, r1);
+            r2 = fmaf(sr, o1, r2);
         } else {
             const float sr = a.sig2 >= 0.f ? a.sig2 : sig_r_tgv(gx, gy, N);
             r1 = fmaf(sr, gu0 - s_vb1[ly][lx], r1);
@@ -231,7 +215,7 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
                 if (gx == 0 && gy == 0) a.u_quad[0] = make_float4(0.f, 0.f, 0.f, uu);
             }
         }
-        if (TGV) {
+        if (REG == PAT_TGV) {
             // E vbar with d^- on the masked field
             const bool axm = gx >= 1, bym = gy >= 1;
             const float v1 = ax ? s_vb1[ly][lx] : 0.f, v1l = axm ? s_vb1[ly][lx - 1] : 0.f;
@@ -254,8 +238,8 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
             a.xl_out[NN + gi] = s_vnl1[threadIdx.y][threadIdx.x];
             a.xl_out[2 * NN + gi] = s_vnl2[threadIdx.y][threadIdx.x];
         }
-        a.kt_clear[gi] = 0;
     }
+    if (gx < N && gy < N) a.kt_clear[gy * N + gx] = 0;
     if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
         if (a.iter) *a.iter += 1;
         *a.qmax_next = 0u;
@@ -347,7 +331,9 @@ __global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
     const int N = a.n;
     const size_t NN = (size_t)N * N;
     const float gam = (float)a.gamma;
-    double acc[6] = {0, 0, 0, 0, 0, 0};
+    // per-thread terms in FP32 (each thread covers few pixels), block sums in FP64: GB300's
+    // FP64 pipe runs at 1/64 of FP32, so FP64 is kept to one conversion per thread and term
+    float acc[6] = {0, 0, 0, 0, 0, 0};
     const int nthreads = gridDim.x * blockDim.x;
     auto X = [&](int c, int x, int y) -> float { return __ldg(a.x + c * NN + (size_t)y * N + x); };
     auto Yf = [&](int c, int x, int y) -> float { return __ldg(a.y + c * NN + (size_t)y * N + x); };
@@ -366,7 +352,6 @@ __global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
     for (long long p = blockIdx.x * blockDim.x + threadIdx.x; p < (long long)NN; p += nthreads) {
         const int gx = (int)(p % N), gy = (int)(p / N);
         const bool ax = gx < N - 1, by = gy < N - 1;
-        // regulariser terms: FP32 per term, FP64 sums
         const float u = X(0, gx, gy);
         float g0 = ax ? X(0, gx + 1, gy) - u : 0.f;
         float g1 = by ? X(0, gx, gy + 1) - u : 0.f;
@@ -380,11 +365,11 @@ __global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
             g0 -= X(1, gx, gy);
             g1 -= X(2, gx, gy);
         }
-        acc[0] += (double)sqrtf(g0 * g0 + g1 * g1);
-        // box term of u: |K^T q - div r| in FP64 from the FP32 fields
-        const double divr = ((double)rm(0, gx, gy) - (double)rm(0, gx - 1, gy)) +
-                            ((double)rm(1, gx, gy) - (double)rm(1, gx, gy - 1));
-        acc[2] += fabs((double)a.kt.at(gx, gy, N) - divr);
+        acc[0] += sqrtf(g0 * g0 + g1 * g1);
+        // box term of u: |K^T q - div r|; near convergence the two sides agree closely and
+        // their FP32 difference is exact (Sterbenz), so FP32 keeps the term's precision
+        const float divr = (rm(0, gx, gy) - rm(0, gx - 1, gy)) + (rm(1, gx, gy) - rm(1, gx, gy - 1));
+        acc[2] += fabsf(a.kt.at(gx, gy, N) - divr);
         if (REG == PAT_TGV) {
             auto vm = [&](int c, int x, int y, bool mx) -> float {  // masked v for d^-
                 if (x < 0 || y < 0 || (mx ? (x >= N - 1) : (y >= N - 1))) return 0.f;
@@ -394,29 +379,29 @@ __global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
             const float e22 = vm(1, gx, gy, false) - vm(1, gx, gy - 1, false);
             const float e12 = ((vm(0, gx, gy, false) - vm(0, gx, gy - 1, false)) +
                                (vm(1, gx, gy, true) - vm(1, gx - 1, gy, true))) * kInvSqrt2f;
-            acc[1] += (double)sqrtf(e11 * e11 + e22 * e22 + e12 * e12);
-            // box term of v: |E^T s - r|_1 in FP64
-            const double s11 = Yf(2, gx, gy), s22 = Yf(3, gx, gy), s12 = Yf(4, gx, gy);
-            const double dx11 = ax ? (double)Yf(2, gx + 1, gy) - s11 : 0.0;
-            const double dy12 = by ? (double)Yf(4, gx, gy + 1) - s12 : 0.0;
-            const double dy22 = by ? (double)Yf(3, gx, gy + 1) - s22 : 0.0;
-            const double dx12 = ax ? (double)Yf(4, gx + 1, gy) - s12 : 0.0;
-            const double et1 = -dx11 - dy12 / kSqrt2, et2 = -dy22 - dx12 / kSqrt2;
-            acc[3] += fabs(et1 - (double)Yf(0, gx, gy)) + fabs(et2 - (double)Yf(1, gx, gy));
+            acc[1] += sqrtf(e11 * e11 + e22 * e22 + e12 * e12);
+            const float s11 = Yf(2, gx, gy), s22 = Yf(3, gx, gy), s12 = Yf(4, gx, gy);
+            const float dx11 = ax ? Yf(2, gx + 1, gy) - s11 : 0.f;
+            const float dy12 = by ? Yf(4, gx, gy + 1) - s12 : 0.f;
+            const float dy22 = by ? Yf(3, gx, gy + 1) - s22 : 0.f;
+            const float dx12 = ax ? Yf(4, gx + 1, gy) - s12 : 0.f;
+            const float et1 = -dx11 - dy12 * kInvSqrt2f, et2 = -dy22 - dx12 * kInvSqrt2f;
+            acc[3] += fabsf(et1 - Yf(0, gx, gy)) + fabsf(et2 - Yf(1, gx, gy));
         }
         if (a.x_old) {
             const int nc = REG == PAT_TGV ? 3 : 1;
             for (int c = 0; c < nc; ++c) {
                 const float xn = X(c, gx, gy), xo = __ldg(a.x_old + c * NN + p);
-                const double dxv = (double)(xn - xo);
-                acc[4] += dxv * dxv;
-                acc[5] += (double)xo * (double)xo;
+                acc[4] += (xn - xo) * (xn - xo);
+                acc[5] += xo * xo;
             }
         }
     }
-    block_sum<6>(acc);
+    double dacc[6];
+    for (int c = 0; c < 6; ++c) dacc[c] = (double)acc[c];
+    block_sum<6>(dacc);
     if (threadIdx.x == 0)
-        for (int c = 0; c < 6; ++c) a.partials[6 * blockIdx.x + c] = acc[c];
+        for (int c = 0; c < 6; ++c) a.partials[6 * blockIdx.x + c] = dacc[c];
 }
 
 constexpr int GAP_FINAL_BLOCKS = 32;
@@ -459,12 +444,21 @@ __global__ void __launch_bounds__(256) k_gap_final(FinalArgs a) {
         s_last = atomicAdd(&in->final_ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!s_last || threadIdx.x != 0) return;
+    if (!s_last) return;
     __threadfence();
+    // warp c adds the block sums of component c with a shuffle tree (fixed order)
+    __shared__ double s_tot[9];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = warp; c < 9; c += blockDim.x >> 5) {
+        double v = lane < (int)gridDim.x ? *(volatile double*)&in->level2[lane][c] : 0.0;
+        v = warp_sum(v);
+        if (lane == 0) s_tot[c] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x != 0) return;
     in->final_ticket = 0;
-    double t[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    for (int b = 0; b < (int)gridDim.x; ++b)
-        for (int c = 0; c < 9; ++c) t[c] += *(volatile double*)&in->level2[b][c];
+    double t[9];
+    for (int c = 0; c < 9; ++c) t[c] = s_tot[c];
     const double res2 = t[0], q2 = t[1], qf = t[2];
     const double r1 = t[3], r2 = t[4], bu = t[5], bv = t[6], dx2 = t[7], x2 = t[8];
     const double reg = a.reg == PAT_TGV ? r1 + a.beta * r2 : r1;

@@ -165,17 +165,18 @@ __global__ void __launch_bounds__(ROW_THREADS) k_forward_gap(GeomView g, const f
     if (stop && *(volatile const int*)stop) return;
     const RowLane rl = row_lane(g);
     const float s = phase_sum(circle_partial<QUAD>(g, u, rl));
-    double a = 0.0, b = 0.0, c = 0.0;
+    // per-row terms in FP32, block sums in FP64 (GB300's FP64 pipe is 1/64 of FP32)
+    float a = 0.f, b = 0.f, c = 0.f;
     if (rl.valid && rl.ph == 0) {
         const float ku = s * __ldg(&g.wk[rl.k]);
         const size_t i = (size_t)rl.d * g.n_t + rl.k;
-        const double res = (double)ku - (double)f[i];
-        const double qi = (double)q[i];
+        const float res = ku - f[i];
+        const float qi = q[i];
         a = res * res;
         b = qi * qi;
-        c = qi * (double)f[i];
+        c = qi * f[i];
     }
-    const double3 sum = block_sum3(make_double3(a, b, c));
+    const double3 sum = block_sum3(make_double3((double)a, (double)b, (double)c));
     if (threadIdx.x == 0) {
         const int blk = blockIdx.y * gridDim.x + blockIdx.x;
         partials[3 * blk + 0] = sum.x;
