@@ -3,7 +3,8 @@
 // The discrete circular-mean operator (Sec. 4.2, eq. (K_def); Sec. 3.3.1): quadrature
 // point m of circle (d, k) is x_d + r_k (cos phi_m, sin phi_m), phi_m = 2 pi (m + 1/2)/M,
 // r_k = r0 + (k + 1/2) dr.  The tables built here are the only geometry state the
-// kernels read: detector positions, the M (cos, sin) pairs, radii, arc weights
+// kernels read: detector positions and the M (cos, sin) pairs (both scaled to pixel
+// units), radii, arc weights
 // 2 pi r_k / M, and per group of 8 consecutive radii the circular range of angles
 // whose points can touch the grid (a superset: kernels test every point exactly).
 #include <math.h>
@@ -229,12 +230,15 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     std::vector<float2> det(D), cs(M);
     std::vector<float> rk(T), wk(T);
     std::vector<double> cosd(M), sind(M), rd(T);
-    for (int i = 0; i < D; ++i) det[i] = make_float2((float)d.det_xy_host[2 * i], (float)d.det_xy_host[2 * i + 1]);
+    // device tables in continuous pixel coordinates (pixel centres at integers)
+    for (int i = 0; i < D; ++i)
+        det[i] = make_float2((float)((d.det_xy_host[2 * i] - d.xmin) / hx - 0.5),
+                             (float)((d.det_xy_host[2 * i + 1] - d.ymin) / hy - 0.5));
     for (int m = 0; m < M; ++m) {
         const double phi = 2.0 * M_PI * (m + 0.5) / M;
         cosd[m] = cos(phi);
         sind[m] = sin(phi);
-        cs[m] = make_float2((float)cosd[m], (float)sind[m]);
+        cs[m] = make_float2((float)(cosd[m] / hx), (float)(sind[m] / hy));
     }
     for (int k = 0; k < T; ++k) {
         rd[k] = d.r0 + (k + 0.5) * d.dr;
@@ -431,10 +435,6 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     v.n_t = T;
     v.quad_m = M;
     v.n_kgrp = n_kgrp;
-    v.inv_hx = (float)(1.0 / hx);
-    v.inv_hy = (float)(1.0 / hy);
-    v.ox = (float)(-d.xmin / hx - 0.5);
-    v.oy = (float)(-d.ymin / hy - 0.5);
     v.det = g->det;
     v.cs = g->cs;
     v.rk = g->rk;

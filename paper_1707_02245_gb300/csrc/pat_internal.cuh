@@ -45,15 +45,16 @@ void prof_collect();
 // ---------------------------------------------------------------------------------
 // device view of a geometry (passed by value to kernels)
 // ---------------------------------------------------------------------------------
-// Quadrature point m of circle (d, k):  x = det[d] + r[k] * cs[m]   (fp32)
-// Continuous pixel coordinate:          fx = x * inv_hx + ox,  ox = -xmin/hx - 1/2
-// Taps i0 = floor(fx), i0 + 1 with weights 1 - ax, ax (ax = fx - i0); same in y.
+// Quadrature point m of circle (d, k) in continuous pixel coordinates (fp32):
+//   fx = det[d].x + r[k] * cs[m].x   with det = ((x_d - xmin)/hx - 1/2, (y_d - ymin)/hy - 1/2)
+//                                    and  cs = (cos(phi_m)/hx, sin(phi_m)/hy)   (from FP64)
+// so pixel (i, j) has its centre at fx = i, fy = j.  Taps i0 = floor(fx), i0 + 1 with
+// weights 1 - ax, ax (ax = fx - i0); same in y.
 struct GeomView {
     int n, n_det, n_t, quad_m;
     int n_kgrp;          // k groups of KGRP consecutive radii per detector
-    float inv_hx, inv_hy, ox, oy;
-    const float2* det;   // D detector positions
-    const float2* cs;    // M (cos phi_m, sin phi_m)
+    const float2* det;   // D detector positions in continuous pixel coordinates
+    const float2* cs;    // M (cos phi_m / hx, sin phi_m / hy)
     const float* rk;     // T radii
     const float* wk;     // T arc weights 2 pi r_k / M
     const int2* win;     // D * n_kgrp angular windows {m_first, m_count} (circular)
@@ -107,10 +108,8 @@ struct Taps {
 // tap can touch the grid (i0 or j0 outside [-1, N-1]).
 __device__ __forceinline__ bool point_taps(const GeomView& g, float2 det, float r, float2 cs,
                                            Taps& t) {
-    const float x = fmaf(r, cs.x, det.x);
-    const float y = fmaf(r, cs.y, det.y);
-    const float fx = fmaf(x, g.inv_hx, g.ox);
-    const float fy = fmaf(y, g.inv_hy, g.oy);
+    const float fx = fmaf(r, cs.x, det.x);
+    const float fy = fmaf(r, cs.y, det.y);
     const float flx = floorf(fx);
     const float fly = floorf(fy);
     t.ax = fx - flx;
@@ -137,10 +136,8 @@ struct KtView {
 
 // Taps of a point without the grid test (callers that test a tile window instead).
 __device__ __forceinline__ void point_coords(const GeomView& g, float2 det, float r, float2 cs, Taps& t) {
-    const float x = fmaf(r, cs.x, det.x);
-    const float y = fmaf(r, cs.y, det.y);
-    const float fx = fmaf(x, g.inv_hx, g.ox);
-    const float fy = fmaf(y, g.inv_hy, g.oy);
+    const float fx = fmaf(r, cs.x, det.x);
+    const float fy = fmaf(r, cs.y, det.y);
     const float flx = floorf(fx);
     const float fly = floorf(fy);
     t.ax = fx - flx;

@@ -236,11 +236,10 @@ __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
     for (int c = tid; c < AW * AW; c += ATHREADS) acc[c] = 0;
     const float bound = __uint_as_float(*a.ymax_bits) * __ldg(&a.tile_kmax[tile]);
     const float scale = 1073741824.0f / bound;  // 2^30 / bound
-    // tap region of the tile in world coordinates (fx in [x0 - 1, x0 + ATILE)), widened
+    // tap region of the tile in pixel coordinates (fx in [x0 - 1, x0 + ATILE)), widened
     // by 1e-3 pixel so FP32 rounding never drops a candidate
-    const float hx = 1.f / g.inv_hx, hy = 1.f / g.inv_hy;
-    const float rx0 = (x0 - 1.001f - g.ox) * hx, rx1 = (x0 + ATILE + 0.001f - g.ox) * hx;
-    const float ry0 = (y0 - 1.001f - g.oy) * hy, ry1 = (y0 + ATILE + 0.001f - g.oy) * hy;
+    const float rx0 = x0 - 1.001f, rx1 = x0 + ATILE + 0.001f;
+    const float ry0 = y0 - 1.001f, ry1 = y0 + ATILE + 0.001f;
     const float r_first = __ldg(&g.rk[0]);
     const float inv_dr = T > 1 ? (float)(T - 1) / (__ldg(&g.rk[T - 1]) - r_first) : 0.f;
     __syncthreads();
