@@ -398,9 +398,16 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
         for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return item_cost[a] > item_cost[b]; });
         std::vector<int4> sorted(items.size());
-        for (size_t i = 0; i < order.size(); ++i) sorted[i] = items[order[i]];
+        g->adj_item_cost.resize(items.size());
+        for (size_t i = 0; i < order.size(); ++i) {
+            sorted[i] = items[order[i]];
+            g->adj_item_cost[i] = (float)item_cost[order[i]];
+        }
         items.swap(sorted);
-        if (items.empty()) items.push_back(make_int4(0, 0, 0, 0));
+        if (items.empty()) {
+            items.push_back(make_int4(0, 0, 0, 0));
+            g->adj_item_cost.push_back(0.f);
+        }
     }
     g->adj_items = (int)items.size();
 

@@ -7,6 +7,7 @@
 
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "pat.h"
 
@@ -88,6 +89,7 @@ struct pat_geometry {
     int4* adj_units = nullptr;        // K^T work units {detector, first ray, rays, box index}
     int4* adj_item = nullptr;         // K^T work items (one CTA each) {tile, first unit, end unit, 0}
     int adj_tiles_x = 0, adj_tiles = 0, adj_items = 0;
+    std::vector<float> adj_item_cost;  // estimated candidates per work item (host)
     pat::GeomView view;
     // lazily computed preconditioner sums
     mutable std::mutex mtx;
@@ -149,30 +151,70 @@ __device__ __forceinline__ void point_coords(const GeomView& g, float2 det, floa
 // Launch helpers
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// ---------------------------------------------------------------------------------
+// per-problem kernel arguments of the batched launches: a launch covers several problems,
+// block b of the launch works on problem map[b].x, local block map[b].y
+// ---------------------------------------------------------------------------------
+struct FwdProxArgs {   // q <- prox(q + Sigma_q K ubar); also q*w and max|q|
+    GeomView g;
+    const float4* ubar_quad;
+    float* q;
+    const float* f;
+    const float* sig_q;   // NULL: sig_scalar
+    float sig_scalar;
+    float* qw;
+    unsigned* qmax_bits;
+    const int* stop;
+};
+
+struct FwdGapArgs {    // FP64 partial sums of 1/2|Ku - f|^2, |q|^2, <q, f> per block
+    GeomView g;
+    const float* u;         // plain N*N image (u_quad NULL) ...
+    const float4* u_quad;   // ... or its quads
+    const float* q;
+    const float* f;
+    double* partials;
+    const int* stop;
+};
+
+struct AdjArgs {       // fixed-point K^T y, one work item per block
+    GeomView g;
+    const float* y;          // data rows, or data rows times the arc weights (premul)
+    int premul;
+    const unsigned* ymax_bits;
+    const float* tile_kmax;
+    const int4* box;
+    const int4* units;
+    const int4* items;
+    int* acc_out;            // N*N fixed-point image, added to with integer atomics
+    int tiles_x;
+    const int* stop;
+};
+
+FwdProxArgs make_fwd_prox_args(const pat_geometry* g, const float4* ubar_quad, float* q, const float* f,
+                               const float* sig_q, float sig_scalar, float* qw, unsigned* qmax_bits, const int* stop);
+FwdGapArgs make_fwd_gap_args(const pat_geometry* g, const float* u, const float4* u_quad, const float* q,
+                             const float* f, double* partials, const int* stop);
+AdjArgs make_adj_args(const pat_geometry* g, const float* y, const float* premul, const unsigned* ymax_bits, int* acc,
+                      const int* stop);
+// batched launches over maps of (problem, local block); args are device arrays by problem
+int launch_forward_prox_b(const FwdProxArgs* args, const int2* map, int nblocks, cudaStream_t st);
+int launch_forward_gap_b(const FwdGapArgs* args, const int2* map, int nblocks, cudaStream_t st);
+int launch_adjoint_b(const AdjArgs* args, const int2* map, int nblocks, bool premul, cudaStream_t st);
+int forward_row_blocks(const pat_geometry* g);    // blocks of one forward launch
+int forward_rows_per_block();
+
 // Host entry points implemented in projector.cu and used by pdhg.cu
 int ensure_precond(const pat_geometry* g, cudaStream_t st);
 int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y, cudaStream_t st);
 // K^T y into an N*N float image (allocates its scratch from the stream-ordered pool).
 int launch_adjoint(const pat_geometry* g, const float* y, float* out, cudaStream_t st);
-// Hot-path K^T q accumulated into the fixed-point image acc (N*N int32, zero on entry);
-// ymax_bits holds max |y| as float bits; premul (optional) holds y_k times the arc
-// weight w_k and is read instead of y and w.
-int launch_adjoint_fixed(const pat_geometry* g, const float* y, const float* premul, const unsigned* ymax_bits,
-                         int* acc, const int* stop, cudaStream_t st);
 KtView kt_view(const pat_geometry* g, const int* acc, const unsigned* ymax_bits);
 // K^T y into an N*N float image using caller-provided, zeroed scratch (allocates nothing).
 int launch_adjoint_into(const pat_geometry* g, const float* y, unsigned* ymax_bits, int* acc, float* out,
                         cudaStream_t st);
-// ubar_quad: (N+1)^2 float4 "quads" Q[(j0+1)(N+1) + i0+1] = (u[j0][i0], u[j0][i0+1],
-// u[j0+1][i0], u[j0+1][i0+1]) with zeros off the grid, so one 16-byte load fetches the
-// four bilinear taps of a point.
-int launch_forward_prox(const pat_geometry* g, const float4* ubar_quad, float* q, const float* f,
-                        const float* sig_q, float sig_q_scalar, float* qw, unsigned* qmax_bits,
-                        const int* stop, cudaStream_t st);
-// u_quad (optional): quads of u read instead of the plain image u.
-int launch_forward_gap(const pat_geometry* g, const float* u, const float4* u_quad, const float* q, const float* f,
-                       double* partials, int n_part, const int* stop, cudaStream_t st);
-int forward_gap_blocks(const pat_geometry* g);
+
+
 // max |y| as float bits into *out (which must hold 0 or a smaller value beforehand)
 int launch_absmax(const float* y, long long n, unsigned* out, cudaStream_t st);
 

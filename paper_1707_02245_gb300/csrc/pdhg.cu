@@ -51,6 +51,7 @@ struct UpdateArgs {
     float4* u_quad;        // quads of u^{n+1} for the gap's K u (NULL: not a gap iteration)
     const int* stop;
     int* iter;             // iteration counter (incremented once per launch)
+    int tiles_x;           // tiles per row of the grid
 };
 
 __device__ __forceinline__ float ld_img(const float* __restrict__ p, int N, int gx, int gy) {
@@ -59,11 +60,10 @@ __device__ __forceinline__ float ld_img(const float* __restrict__ p, int N, int 
 
 // One PDHG primal step plus the following dual step on a TX x TY tile.
 template <int REG>
-__global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
-    if (a.stop && *(volatile const int*)a.stop) return;
+__device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, const int by, const bool first) {
     const int N = a.n;
     const size_t NN = (size_t)N * N;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+    const int x0 = bx * TX, y0 = by * TY;
     const int tid = threadIdx.y * TX + threadIdx.x;
 
     __shared__ float s_r1m[LY][LX], s_r2m[LY][LX];   // r (dTV: D_xi r) masked for div
@@ -240,10 +240,18 @@ __global__ void __launch_bounds__(TX* TY) k_update(UpdateArgs a) {
         }
     }
     if (gx < N && gy < N) a.kt_clear[gy * N + gx] = 0;
-    if (blockIdx.x == 0 && blockIdx.y == 0 && tid == 0) {
+    if (first && tid == 0) {
         if (a.iter) *a.iter += 1;
         *a.qmax_next = 0u;
     }
+}
+
+template <int REG>
+__global__ void __launch_bounds__(TX* TY) k_update_b(const UpdateArgs* __restrict__ args, const int2* __restrict__ map) {
+    const int2 pm = map[blockIdx.x];
+    const UpdateArgs& a = args[pm.x];
+    if (a.stop && *(volatile const int*)a.stop) return;
+    update_tile<REG>(a, pm.y % a.tiles_x, pm.y / a.tiles_x, pm.y == 0);
 }
 
 // Dual step r, s <- prox(r, s + Sigma (A_reg (ubar, vbar))) used once before the first
@@ -323,18 +331,18 @@ struct GapArgs {
     KtView kt;            // K^T q^{n+1} (fixed point)
     double* partials;
     const int* stop;
+    int nblocks;          // blocks of this problem's pixel pass
 };
 
 template <int REG>
-__global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
-    if (a.stop && *(volatile const int*)a.stop) return;
+__device__ __forceinline__ void gap_pixels_block(const GapArgs& a, const int lb) {
     const int N = a.n;
     const size_t NN = (size_t)N * N;
     const float gam = (float)a.gamma;
     // per-thread terms in FP32 (each thread covers few pixels), block sums in FP64: GB300's
     // FP64 pipe runs at 1/64 of FP32, so FP64 is kept to one conversion per thread and term
     float acc[6] = {0, 0, 0, 0, 0, 0};
-    const int nthreads = gridDim.x * blockDim.x;
+    const int nthreads = a.nblocks * blockDim.x;
     auto X = [&](int c, int x, int y) -> float { return __ldg(a.x + c * NN + (size_t)y * N + x); };
     auto Yf = [&](int c, int x, int y) -> float { return __ldg(a.y + c * NN + (size_t)y * N + x); };
     // r masked for div (dTV: D_xi r), zero outside the grid
@@ -349,7 +357,7 @@ __global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
         }
         return c == 0 ? r0 : r1;
     };
-    for (long long p = blockIdx.x * blockDim.x + threadIdx.x; p < (long long)NN; p += nthreads) {
+    for (long long p = (long long)lb * blockDim.x + threadIdx.x; p < (long long)NN; p += nthreads) {
         const int gx = (int)(p % N), gy = (int)(p / N);
         const bool ax = gx < N - 1, by = gy < N - 1;
         const float u = X(0, gx, gy);
@@ -401,7 +409,15 @@ __global__ void __launch_bounds__(256) k_gap_pixels(GapArgs a) {
     for (int c = 0; c < 6; ++c) dacc[c] = (double)acc[c];
     block_sum<6>(dacc);
     if (threadIdx.x == 0)
-        for (int c = 0; c < 6; ++c) a.partials[6 * blockIdx.x + c] = dacc[c];
+        for (int c = 0; c < 6; ++c) a.partials[6 * lb + c] = dacc[c];
+}
+
+template <int REG>
+__global__ void __launch_bounds__(256) k_gap_pixels_b(const GapArgs* __restrict__ args, const int2* __restrict__ map) {
+    const int2 pm = map[blockIdx.x];
+    const GapArgs& a = args[pm.x];
+    if (a.stop && *(volatile const int*)a.stop) return;
+    gap_pixels_block<REG>(a, pm.y);
 }
 
 constexpr int GAP_FINAL_BLOCKS = 32;
@@ -427,21 +443,20 @@ struct FinalArgs {
 // Two-level FP64 reduction in a fixed order: each of GAP_FINAL_BLOCKS blocks sums a fixed
 // strided subset of the partials, the last block to finish adds the block sums in index
 // order and evaluates the gap, the residual and the stopping test.
-__global__ void __launch_bounds__(256) k_gap_final(FinalArgs a) {
-    if (*(volatile const int*)&a.info->stop) return;
+__device__ __forceinline__ void gap_final_block(const FinalArgs& a, const int lb) {
     double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
-    const int stride = gridDim.x * blockDim.x;
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < a.n_data; b += stride)
+    const int stride = GAP_FINAL_BLOCKS * blockDim.x;
+    for (int b = lb * blockDim.x + threadIdx.x; b < a.n_data; b += stride)
         for (int c = 0; c < 3; ++c) acc[c] += a.data_part[3 * b + c];
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < a.n_pix; b += stride)
+    for (int b = lb * blockDim.x + threadIdx.x; b < a.n_pix; b += stride)
         for (int c = 0; c < 6; ++c) acc[3 + c] += a.pix_part[6 * b + c];
     block_sum<9>(acc);
     __shared__ bool s_last;
     InfoDev* in = a.info;
     if (threadIdx.x == 0) {
-        for (int c = 0; c < 9; ++c) in->level2[blockIdx.x][c] = acc[c];
+        for (int c = 0; c < 9; ++c) in->level2[lb][c] = acc[c];
         __threadfence();
-        s_last = atomicAdd(&in->final_ticket, 1u) == gridDim.x - 1;
+        s_last = atomicAdd(&in->final_ticket, 1u) == GAP_FINAL_BLOCKS - 1;
     }
     __syncthreads();
     if (!s_last) return;
@@ -450,7 +465,7 @@ __global__ void __launch_bounds__(256) k_gap_final(FinalArgs a) {
     __shared__ double s_tot[9];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int c = warp; c < 9; c += blockDim.x >> 5) {
-        double v = lane < (int)gridDim.x ? *(volatile double*)&in->level2[lane][c] : 0.0;
+        double v = lane < GAP_FINAL_BLOCKS ? *(volatile double*)&in->level2[lane][c] : 0.0;
         v = warp_sum(v);
         if (lane == 0) s_tot[c] = v;
     }
@@ -480,6 +495,13 @@ __global__ void __launch_bounds__(256) k_gap_final(FinalArgs a) {
         in->status = PAT_STATUS_CONVERGED;
         in->stop = 1;
     }
+}
+
+__global__ void __launch_bounds__(256) k_gap_final_b(const FinalArgs* __restrict__ args, const int2* __restrict__ map) {
+    const int2 pm = map[blockIdx.x];
+    const FinalArgs& a = args[pm.x];
+    if (*(volatile const int*)&a.info->stop) return;
+    gap_final_block(a, pm.y);
 }
 
 // ---------------------------------------------------------------------------------
@@ -659,7 +681,7 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     const size_t N = g->desc.n, NN = N * N, S = (size_t)g->desc.n_det * g->desc.n_t;
     const size_t nx = NN * (reg == PAT_TGV ? 3 : 1), ny = NN * (reg == PAT_TGV ? 5 : 2);
     const size_t P2 = (N + 2) * (N + 2);
-    ws.n_data = forward_gap_blocks(g);
+    ws.n_data = forward_row_blocks(g);
     ws.n_pix = pix_blocks((int)N);
     size_t off[19];
     size_t sz[19] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, NN * 4 * 2,
@@ -742,193 +764,447 @@ static int compute_steps(const pat_geometry* g, const pat_params* p, Workspace& 
     return PAT_OK;
 }
 
-template <int REG>
-static int launch_update(const pat_geometry* g, const pat_params* p, Workspace& ws, const ScalarSteps& sc, int it,
-                         cudaStream_t st) {
-    const int N = g->desc.n;
+// ---------------------------------------------------------------------------------
+// batch engine: problems advance in lockstep; one launch per phase covers all of them
+// through a (problem, local block) map, and the periodic part of the iteration loop is
+// replayed from a captured CUDA graph.  A single reconstruction is a batch of one.
+// ---------------------------------------------------------------------------------
+struct Prob {
+    const pat_geometry* g = nullptr;
+    const float* f = nullptr;
+    pat_params p{};
+    float* u_out = nullptr;
+    Workspace ws;
+    ScalarSteps sc;
+};
+
+// Packs host-side argument structs and maps, then uploads them in one copy.
+struct Arena {
+    std::vector<char>& buf;
+    explicit Arena(std::vector<char>& b) : buf(b) {}
+    template <class T>
+    size_t put(const T* p, size_t n) {
+        const size_t off = align_up(buf.size());
+        buf.resize(off + std::max<size_t>(1, n) * sizeof(T));
+        if (n) memcpy(buf.data() + off, p, n * sizeof(T));
+        return off;
+    }
+    int upload(void** dev, cudaStream_t st) {
+        PAT_CUDA(cudaMallocAsync(dev, buf.size(), st));
+        PAT_CUDA(cudaMemcpyAsync(*dev, buf.data(), buf.size(), cudaMemcpyHostToDevice, st));
+        return PAT_OK;
+    }
+};
+
+struct GapPlan {
+    size_t map_fwd = 0, map_fin = 0;
+    size_t map_pix[3] = {0, 0, 0};
+    int n_fwd = 0, n_fin = 0;
+    int n_pix[3] = {0, 0, 0};
+};
+
+static void build_gap_plan(const Prob* pr, int B, Arena& ar, GapPlan& gp) {
+    std::vector<int2> fwd, fin, pix[3];
+    for (int b = 0; b < B; ++b) {
+        const int nf = forward_row_blocks(pr[b].g);
+        for (int i = 0; i < nf; ++i) fwd.push_back(make_int2(b, i));
+        for (int i = 0; i < pr[b].ws.n_pix; ++i) pix[pr[b].p.reg].push_back(make_int2(b, i));
+        for (int i = 0; i < GAP_FINAL_BLOCKS; ++i) fin.push_back(make_int2(b, i));
+    }
+    gp.map_fwd = ar.put(fwd.data(), fwd.size());
+    gp.n_fwd = (int)fwd.size();
+    gp.map_fin = ar.put(fin.data(), fin.size());
+    gp.n_fin = (int)fin.size();
+    for (int r = 0; r < 3; ++r) {
+        gp.map_pix[r] = ar.put(pix[r].data(), pix[r].size());
+        gp.n_pix[r] = (int)pix[r].size();
+    }
+}
+
+static GapArgs make_gap_args(const Prob& pr, const KtView& kt, const float* x, const float* x_old, const float* y_rs) {
+    GapArgs ga;
+    ga.n = pr.g->desc.n;
+    ga.gamma = pr.p.gamma;
+    ga.xi = pr.p.xi_dev;
+    ga.x = x;
+    ga.x_old = x_old;
+    ga.y = y_rs;
+    ga.kt = kt;
+    ga.partials = pr.ws.pix_part;
+    ga.stop = &pr.ws.info->stop;
+    ga.nblocks = pr.ws.n_pix;
+    return ga;
+}
+
+static FinalArgs make_final_args(const Prob& pr) {
+    FinalArgs fa{pr.ws.data_part, pr.ws.n_data, pr.ws.pix_part, pr.ws.n_pix, pr.p.alpha, pr.p.beta, pr.p.box_u,
+                 pr.p.box_v, pr.p.tol, pr.p.reg, pr.ws.info};
+    return fa;
+}
+
+static UpdateArgs make_update_args(const Prob& pr, int par, bool gap_iter) {
+    const Workspace& ws = pr.ws;
+    const pat_params* p = &pr.p;
+    const int N = pr.g->desc.n;
     UpdateArgs a;
     a.n = N;
     a.alpha = (float)p->alpha;
     a.ab = (float)(p->alpha * p->beta);
     a.gamma = (float)p->gamma;
     a.theta = (float)p->theta;
-    a.sig2 = sc.sig2;
-    a.tau = sc.tau;
+    a.sig2 = pr.sc.sig2;
+    a.tau = pr.sc.tau;
     a.tau_u = ws.tau_u;
     a.sig_r = ws.sig_r;
     a.xi = p->xi_dev;
-    a.kt = kt_view(g, ws.kt[it & 1], &ws.info->qmax_bits[it & 1]);
-    a.kt_clear = ws.kt[(it + 1) & 1];
-    a.qmax_next = &ws.info->qmax_bits[(it + 1) & 1];
-    a.x_in = ws.X[it & 1];
-    a.xl_in = ws.XL[it & 1];
-    a.y_in = ws.Y[it & 1];
-    a.x_out = ws.X[(it + 1) & 1];
-    a.xl_out = ws.XL[(it + 1) & 1];
-    a.y_out = ws.Y[(it + 1) & 1];
+    a.kt = kt_view(pr.g, ws.kt[par], &ws.info->qmax_bits[par]);
+    a.kt_clear = ws.kt[1 - par];
+    a.qmax_next = &ws.info->qmax_bits[1 - par];
+    a.x_in = ws.X[par];
+    a.xl_in = ws.XL[par];
+    a.y_in = ws.Y[par];
+    a.x_out = ws.X[1 - par];
+    a.xl_out = ws.XL[1 - par];
+    a.y_out = ws.Y[1 - par];
     a.ubar_pad = ws.ubar_pad;
     a.ubar_quad = ws.ubar_quad;
-    const int done = it + 1;
-    a.u_quad = ((p->gap_every > 0 && done % p->gap_every == 0) || done == p->iters) ? ws.u_quad : nullptr;
+    a.u_quad = gap_iter ? ws.u_quad : nullptr;
     a.stop = &ws.info->stop;
     a.iter = &ws.info->iter;
-    dim3 grd(ceil_div(N, TX), ceil_div(N, TY)), blk(TX, TY);
-    k_update<REG><<<grd, blk, 0, st>>>(a);
-    PAT_LAUNCH_CHECK("k_update");
+    a.tiles_x = ceil_div(N, TX);
+    return a;
+}
+
+static int launch_update_b(int reg, const UpdateArgs* args, const int2* map, int n, cudaStream_t st) {
+    if (n <= 0) return PAT_OK;
+    prof_mark(PAT_PHASE_UPDATE, st, true);
+    if (reg == PAT_TV)
+        k_update_b<PAT_TV><<<n, TX * TY, 0, st>>>(args, map);
+    else if (reg == PAT_TGV)
+        k_update_b<PAT_TGV><<<n, TX * TY, 0, st>>>(args, map);
+    else
+        k_update_b<PAT_DTV><<<n, TX * TY, 0, st>>>(args, map);
+    PAT_LAUNCH_CHECK("k_update_b");
+    prof_mark(PAT_PHASE_UPDATE, st, false);
     return PAT_OK;
 }
 
-template <int REG>
-static int launch_gap(const pat_geometry* g, const pat_params* p, Workspace& ws, const KtView& kt, const float* x,
-                      const float4* x_quad, const float* x_old, const float* y, const float* q, const float* f,
-                      const int* stop, cudaStream_t st) {
-    const int N = g->desc.n;
-    int rc = launch_forward_gap(g, x, x_quad, q, f, ws.data_part, ws.n_data, stop, st);
+static int launch_gap_phase(const FwdGapArgs* fa, const GapArgs* ga, const FinalArgs* fi, const GapPlan& gp,
+                            const char* base, cudaStream_t st) {
+    prof_mark(PAT_PHASE_GAP, st, true);
+    int rc = launch_forward_gap_b(fa, (const int2*)(base + gp.map_fwd), gp.n_fwd, st);
     if (rc) return rc;
-    GapArgs ga{N, p->gamma, p->xi_dev, x, x_old, y, kt, ws.pix_part, stop};
-    k_gap_pixels<REG><<<ws.n_pix, 256, 0, st>>>(ga);
-    PAT_LAUNCH_CHECK("k_gap_pixels");
-    FinalArgs fa{ws.data_part, ws.n_data, ws.pix_part, ws.n_pix, p->alpha, p->beta, p->box_u, p->box_v,
-                 p->tol, p->reg, ws.info};
-    k_gap_final<<<GAP_FINAL_BLOCKS, 256, 0, st>>>(fa);
-    PAT_LAUNCH_CHECK("k_gap_final");
-    return PAT_OK;
-}
-
-template <int REG>
-static int enqueue_iterations(const pat_geometry* g, const float* f, const pat_params* p, Workspace& ws,
-                              const ScalarSteps& sc, int it0, int count, cudaStream_t st) {
-    const int* stop = &ws.info->stop;
-    for (int it = it0; it < it0 + count; ++it) {
-        prof_mark(PAT_PHASE_FORWARD_PROX, st, true);
-        int rc = launch_forward_prox(g, ws.ubar_quad, ws.q, f, sc.sig_q >= 0 ? nullptr : ws.sig_q, sc.sig_q, ws.qw,
-                                     &ws.info->qmax_bits[it & 1], stop, st);
-        if (rc) return rc;
-        prof_mark(PAT_PHASE_FORWARD_PROX, st, false);
-        rc = launch_adjoint_fixed(g, ws.q, ws.qw, &ws.info->qmax_bits[it & 1], ws.kt[it & 1], stop, st);
-        if (rc) return rc;
-        prof_mark(PAT_PHASE_UPDATE, st, true);
-        rc = launch_update<REG>(g, p, ws, sc, it, st);
-        if (rc) return rc;
-        prof_mark(PAT_PHASE_UPDATE, st, false);
-        const int done = it + 1;
-        if ((p->gap_every > 0 && done % p->gap_every == 0) || done == p->iters) {
-            prof_mark(PAT_PHASE_GAP, st, true);
-            rc = launch_gap<REG>(g, p, ws, kt_view(g, ws.kt[it & 1], &ws.info->qmax_bits[it & 1]), ws.X[done & 1],
-                                 ws.u_quad, ws.X[it & 1], ws.Y[it & 1], ws.q, f, stop, st);
-            if (rc) return rc;
-            prof_mark(PAT_PHASE_GAP, st, false);
-        }
+    for (int r = 0; r < 3; ++r) {
+        if (!gp.n_pix[r]) continue;
+        const int2* map = (const int2*)(base + gp.map_pix[r]);
+        if (r == PAT_TV)
+            k_gap_pixels_b<PAT_TV><<<gp.n_pix[r], 256, 0, st>>>(ga, map);
+        else if (r == PAT_TGV)
+            k_gap_pixels_b<PAT_TGV><<<gp.n_pix[r], 256, 0, st>>>(ga, map);
+        else
+            k_gap_pixels_b<PAT_DTV><<<gp.n_pix[r], 256, 0, st>>>(ga, map);
+        PAT_LAUNCH_CHECK("k_gap_pixels_b");
     }
+    k_gap_final_b<<<gp.n_fin, 256, 0, st>>>(fi, (const int2*)(base + gp.map_fin));
+    PAT_LAUNCH_CHECK("k_gap_final_b");
+    prof_mark(PAT_PHASE_GAP, st, false);
     return PAT_OK;
 }
 
-template <int REG>
-static int run_reconstruct(const pat_geometry* g, const float* f, const pat_params* p, float* u_out, pat_info* info,
-                           cudaStream_t st) {
+struct IterPlan {
+    size_t fwd[2] = {0, 0}, adj[2] = {0, 0}, upd[2][2] = {{0, 0}, {0, 0}}, fgap[2] = {0, 0}, gpix[2] = {0, 0};
+    size_t fin = 0, map_fwd = 0, map_adj = 0;
+    size_t map_upd[3] = {0, 0, 0};
+    int n_fwd = 0, n_adj = 0;
+    int n_upd[3] = {0, 0, 0};
+    GapPlan gp;
+};
+
+static void build_iter_plan(const Prob* pr, int B, Arena& ar, IterPlan& ip) {
+    for (int par = 0; par < 2; ++par) {
+        std::vector<FwdProxArgs> fw;
+        std::vector<AdjArgs> ad;
+        std::vector<UpdateArgs> u0, u1;
+        std::vector<FwdGapArgs> fg;
+        std::vector<GapArgs> gpx;
+        for (int b = 0; b < B; ++b) {
+            const Prob& q = pr[b];
+            const Workspace& ws = q.ws;
+            fw.push_back(make_fwd_prox_args(q.g, ws.ubar_quad, ws.q, q.f, q.sc.sig_q >= 0 ? nullptr : ws.sig_q,
+                                            q.sc.sig_q, ws.qw, &ws.info->qmax_bits[par], &ws.info->stop));
+            ad.push_back(make_adj_args(q.g, ws.q, ws.qw, &ws.info->qmax_bits[par], ws.kt[par], &ws.info->stop));
+            u0.push_back(make_update_args(q, par, false));
+            u1.push_back(make_update_args(q, par, true));
+            fg.push_back(make_fwd_gap_args(q.g, ws.X[1 - par], ws.u_quad, ws.q, q.f, ws.data_part, &ws.info->stop));
+            gpx.push_back(make_gap_args(q, kt_view(q.g, ws.kt[par], &ws.info->qmax_bits[par]), ws.X[1 - par],
+                                        ws.X[par], ws.Y[par]));
+        }
+        ip.fwd[par] = ar.put(fw.data(), fw.size());
+        ip.adj[par] = ar.put(ad.data(), ad.size());
+        ip.upd[par][0] = ar.put(u0.data(), u0.size());
+        ip.upd[par][1] = ar.put(u1.data(), u1.size());
+        ip.fgap[par] = ar.put(fg.data(), fg.size());
+        ip.gpix[par] = ar.put(gpx.data(), gpx.size());
+    }
+    std::vector<FinalArgs> fi;
+    for (int b = 0; b < B; ++b) fi.push_back(make_final_args(pr[b]));
+    ip.fin = ar.put(fi.data(), fi.size());
+    // maps: forward rows problem by problem; K^T items of all problems heaviest first;
+    // update tiles grouped by regulariser
+    std::vector<int2> fwd, upd[3];
+    std::vector<std::pair<float, int2>> adj;
+    for (int b = 0; b < B; ++b) {
+        const pat_geometry* g = pr[b].g;
+        const int nf = forward_row_blocks(g);
+        for (int i = 0; i < nf; ++i) fwd.push_back(make_int2(b, i));
+        for (int i = 0; i < g->adj_items; ++i) adj.push_back({g->adj_item_cost[i], make_int2(b, i)});
+        const int N = g->desc.n, nt = ceil_div(N, TX) * ceil_div(N, TY);
+        for (int i = 0; i < nt; ++i) upd[pr[b].p.reg].push_back(make_int2(b, i));
+    }
+    std::stable_sort(adj.begin(), adj.end(), [](const std::pair<float, int2>& x, const std::pair<float, int2>& y) {
+        return x.first > y.first;
+    });
+    std::vector<int2> adjm;
+    for (auto& e : adj) adjm.push_back(e.second);
+    ip.map_fwd = ar.put(fwd.data(), fwd.size());
+    ip.n_fwd = (int)fwd.size();
+    ip.map_adj = ar.put(adjm.data(), adjm.size());
+    ip.n_adj = (int)adjm.size();
+    for (int r = 0; r < 3; ++r) {
+        ip.map_upd[r] = ar.put(upd[r].data(), upd[r].size());
+        ip.n_upd[r] = (int)upd[r].size();
+    }
+    build_gap_plan(pr, B, ar, ip.gp);
+}
+
+static int enqueue_iteration(const IterPlan& ip, const char* base, int it, bool gap_due, cudaStream_t st) {
+    const int par = it & 1;
+    int rc = launch_forward_prox_b((const FwdProxArgs*)(base + ip.fwd[par]), (const int2*)(base + ip.map_fwd),
+                                   ip.n_fwd, st);
+    if (rc) return rc;
+    rc = launch_adjoint_b((const AdjArgs*)(base + ip.adj[par]), (const int2*)(base + ip.map_adj), ip.n_adj, true, st);
+    if (rc) return rc;
+    const UpdateArgs* ua = (const UpdateArgs*)(base + ip.upd[par][gap_due ? 1 : 0]);
+    for (int r = 0; r < 3; ++r) {
+        rc = launch_update_b(r, ua, (const int2*)(base + ip.map_upd[r]), ip.n_upd[r], st);
+        if (rc) return rc;
+    }
+    if (gap_due)
+        rc = launch_gap_phase((const FwdGapArgs*)(base + ip.fgap[par]), (const GapArgs*)(base + ip.gpix[par]),
+                              (const FinalArgs*)(base + ip.fin), ip.gp, base, st);
+    return rc;
+}
+
+// initial state of one problem (Algorithm 1/2 initialisation, or the warm start)
+static int init_problem(Prob& pr, cudaStream_t st) {
+    const pat_geometry* g = pr.g;
+    const pat_params* p = &pr.p;
+    const int reg = p->reg;
     const int N = g->desc.n;
     const size_t NN = (size_t)N * N, S = (size_t)g->desc.n_det * g->desc.n_t;
-    const size_t nx = NN * (REG == PAT_TGV ? 3 : 1), ny = NN * (REG == PAT_TGV ? 5 : 2);
-    cudaEvent_t e0, e1;
+    const size_t nx = NN * (reg == PAT_TGV ? 3 : 1), ny = NN * (reg == PAT_TGV ? 5 : 2);
+    Workspace& ws = pr.ws;
+    int rc = alloc_workspace(g, reg, ws, st);
+    if (rc) return rc;
+    rc = compute_steps(g, p, ws, pr.sc, st);
+    if (rc) return rc;
+    if (p->x0_dev)
+        PAT_CUDA(cudaMemcpyAsync(ws.X[0], p->x0_dev, nx * 4, cudaMemcpyDeviceToDevice, st));
+    else
+        PAT_CUDA(cudaMemsetAsync(ws.X[0], 0, nx * 4, st));
+    if (p->y0_dev) {
+        PAT_CUDA(cudaMemcpyAsync(ws.q, p->y0_dev, S * 4, cudaMemcpyDeviceToDevice, st));
+        PAT_CUDA(cudaMemcpyAsync(ws.Y[1], p->y0_dev + S, ny * 4, cudaMemcpyDeviceToDevice, st));
+    } else {
+        PAT_CUDA(cudaMemsetAsync(ws.q, 0, S * 4, st));
+        PAT_CUDA(cudaMemsetAsync(ws.Y[1], 0, ny * 4, st));
+    }
+    PAT_CUDA(cudaMemsetAsync(ws.info, 0, sizeof(InfoDev), st));
+    PAT_CUDA(cudaMemsetAsync(ws.kt[0], 0, 2 * NN * sizeof(int), st));
+    PAT_CUDA(cudaMemsetAsync(ws.XL[0], 0, nx * sizeof(float), st));
+    const float* xb = p->xbar0_dev ? p->xbar0_dev : p->x0_dev;
+    dim3 blk(32, 8), grd(ceil_div(N + 2, 32), ceil_div(N + 2, 8));
+    k_pad<<<grd, blk, 0, st>>>(xb, ws.ubar_pad, N);
+    PAT_LAUNCH_CHECK("k_pad");
+    dim3 gq(ceil_div(N + 1, 32), ceil_div(N + 1, 8));
+    k_quads_from_pad<<<gq, blk, 0, st>>>(ws.ubar_pad, ws.ubar_quad, N);
+    PAT_LAUNCH_CHECK("k_quads_from_pad");
+    if (reg == PAT_TGV) {
+        if (xb)
+            PAT_CUDA(cudaMemcpyAsync(ws.vbar0, xb + NN, 2 * NN * 4, cudaMemcpyDeviceToDevice, st));
+        else
+            PAT_CUDA(cudaMemsetAsync(ws.vbar0, 0, 2 * NN * 4, st));
+    }
+    // dual prologue: (r^1, s^1) from (r^0, s^0) and (ubar^0, vbar^0) into Y[0]
+    DualArgs da{N, (float)p->alpha, (float)(p->alpha * p->beta), (float)p->gamma, pr.sc.sig2, ws.sig_r,
+                p->xi_dev, ws.ubar_pad, ws.vbar0, ws.Y[1], ws.Y[0]};
+    dim3 g2(ceil_div(N, 32), ceil_div(N, 8));
+    if (reg == PAT_TV)
+        k_dual_step<PAT_TV><<<g2, blk, 0, st>>>(da);
+    else if (reg == PAT_TGV)
+        k_dual_step<PAT_TGV><<<g2, blk, 0, st>>>(da);
+    else
+        k_dual_step<PAT_DTV><<<g2, blk, 0, st>>>(da);
+    PAT_LAUNCH_CHECK("k_dual_step");
+    return PAT_OK;
+}
+
+static int finish_problem(Prob& pr, cudaStream_t st) {
+    const pat_geometry* g = pr.g;
+    const int reg = pr.p.reg;
+    const int N = g->desc.n;
+    const size_t NN = (size_t)N * N, S = (size_t)g->desc.n_det * g->desc.n_t;
+    const size_t nx = NN * (reg == PAT_TGV ? 3 : 1), ny = NN * (reg == PAT_TGV ? 5 : 2);
+    OutArgs oa;
+    oa.n = N;
+    oa.reg = reg;
+    oa.S = (long long)S;
+    oa.theta = (float)pr.p.theta;
+    oa.X[0] = pr.ws.X[0];
+    oa.X[1] = pr.ws.X[1];
+    oa.Y[0] = pr.ws.Y[0];
+    oa.Y[1] = pr.ws.Y[1];
+    oa.q = pr.ws.q;
+    oa.ubar_pad = pr.ws.ubar_pad;
+    oa.info = pr.ws.info;
+    oa.u_out = pr.u_out;
+    oa.x_out = pr.p.x_out_dev;
+    oa.xbar_out = pr.p.xbar_out_dev;
+    oa.y_out = pr.p.y_out_dev;
+    k_output<<<std::min(2 * 152, ceil_div((long long)(nx + ny + S), 256)), 256, 0, st>>>(oa);
+    PAT_LAUNCH_CHECK("k_output");
+    return PAT_OK;
+}
+
+// A non-blocking stream per device for the iteration loop (capturable, unlike the legacy
+// default stream); it is joined to the caller's stream with events.
+static cudaStream_t loop_stream() {
+    static thread_local cudaStream_t streams[64] = {};
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 0 || dev >= 64) return nullptr;
+    if (!streams[dev]) cudaStreamCreateWithFlags(&streams[dev], cudaStreamNonBlocking);
+    return streams[dev];
+}
+
+static int run_iterations(const IterPlan& ip, const char* base, int iters, int ge, cudaStream_t st) {
+    auto gap_due = [&](int it) { return (ge > 0 && (it + 1) % ge == 0) || it + 1 == iters; };
+    const int P = ge > 0 ? (ge % 2 == 0 ? ge : 2 * ge) : 2;
+    const int nper = iters > 0 ? (iters - 1) / P : 0;
+    int start = 0;
+    if (!prof_on() && nper >= 2) {
+        // one period of the loop as a graph; periods repeat exactly (P is even, so the
+        // ping-pong parity repeats, and a multiple of gap_every, so the gap passes do)
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const long long l0 = pat_kernel_launches();
+        PAT_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        int rc = PAT_OK;
+        for (int it = 0; it < P && !rc; ++it) rc = enqueue_iteration(ip, base, it, ge > 0 && (it + 1) % ge == 0, st);
+        cudaError_t e = cudaStreamEndCapture(st, &graph);
+        if (rc) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc;
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "run_iterations: graph capture");
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        if (e != cudaSuccess) {
+            cudaGraphDestroy(graph);
+            return cuda_fail(e, "run_iterations: graph instantiate");
+        }
+        const long long per_period = pat_kernel_launches() - l0;
+        for (int r = 0; r < nper && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, st);
+        for (int r = 1; r < nper; ++r)
+            for (long long k = 0; k < per_period; ++k) count_launch();
+        cudaGraphExecDestroy(exec);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e, "run_iterations: graph launch");
+        start = nper * P;
+    }
+    for (int it = start; it < iters; ++it) {
+        int rc = enqueue_iteration(ip, base, it, gap_due(it), st);
+        if (rc) return rc;
+    }
+    return PAT_OK;
+}
+
+static int run_batch(int B, const pat_geometry* const* g, const float* const* f, const pat_params* p,
+                     float* const* u_out, pat_info* infos, cudaStream_t st, const char* who) {
+    if (B == 0) return PAT_OK;
+    for (int b = 1; b < B; ++b)
+        if (p[b].iters != p[0].iters || p[b].gap_every != p[0].gap_every)
+            return fail(PAT_ERR_INVALID_ARG, std::string(who) + ": a batch needs equal iters and gap_every");
+    cudaEvent_t e0, e1, fork, join;
     PAT_CUDA(cudaEventCreate(&e0));
     PAT_CUDA(cudaEventCreate(&e1));
+    PAT_CUDA(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+    PAT_CUDA(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
     PAT_CUDA(cudaEventRecord(e0, st));
-    Workspace ws;
-    int rc = alloc_workspace(g, REG, ws, st);
-    if (rc) return rc;
-    ScalarSteps sc;
-    rc = compute_steps(g, p, ws, sc, st);
-    // initial state
-    if (!rc) {
-        if (p->x0_dev)
-            rc = cudaMemcpyAsync(ws.X[0], p->x0_dev, nx * 4, cudaMemcpyDeviceToDevice, st) ? PAT_ERR_CUDA : 0;
-        else
-            rc = cudaMemsetAsync(ws.X[0], 0, nx * 4, st) ? PAT_ERR_CUDA : 0;
+    std::vector<Prob> pr(B);
+    int rc = PAT_OK;
+    for (int b = 0; b < B && !rc; ++b) {
+        pr[b].g = g[b];
+        pr[b].f = f[b];
+        pr[b].p = p[b];
+        pr[b].u_out = u_out[b];
+        rc = init_problem(pr[b], st);
     }
-    if (!rc) {
-        if (p->y0_dev) {
-            rc = cudaMemcpyAsync(ws.q, p->y0_dev, S * 4, cudaMemcpyDeviceToDevice, st) ? PAT_ERR_CUDA : 0;
-            if (!rc)
-                rc = cudaMemcpyAsync(ws.Y[1], p->y0_dev + S, ny * 4, cudaMemcpyDeviceToDevice, st) ? PAT_ERR_CUDA
-                                                                                                     : 0;
-        } else {
-            rc = cudaMemsetAsync(ws.q, 0, S * 4, st) ? PAT_ERR_CUDA : 0;
-            if (!rc) rc = cudaMemsetAsync(ws.Y[1], 0, ny * 4, st) ? PAT_ERR_CUDA : 0;
+    std::vector<char> host;
+    void* dev = nullptr;
+    if (!rc && p[0].iters > 0) {
+        Arena ar(host);
+        IterPlan ip;
+        build_iter_plan(pr.data(), B, ar, ip);
+        rc = ar.upload(&dev, st);
+        cudaStream_t ls = loop_stream();
+        if (!ls) rc = fail(PAT_ERR_CUDA, std::string(who) + ": no loop stream");
+        if (!rc) rc = cudaEventRecord(fork, st) == cudaSuccess ? PAT_OK : PAT_ERR_CUDA;
+        if (!rc) rc = cudaStreamWaitEvent(ls, fork, 0) == cudaSuccess ? PAT_OK : PAT_ERR_CUDA;
+        if (!rc) rc = run_iterations(ip, (const char*)dev, p[0].iters, p[0].gap_every, ls);
+        if (ls) {
+            cudaEventRecord(join, ls);
+            cudaStreamWaitEvent(st, join, 0);
         }
     }
-    if (!rc) rc = cudaMemsetAsync(ws.info, 0, sizeof(InfoDev), st) ? PAT_ERR_CUDA : 0;
-    if (!rc) rc = cudaMemsetAsync(ws.kt[0], 0, 2 * NN * sizeof(int), st) ? PAT_ERR_CUDA : 0;
-    if (!rc) rc = cudaMemsetAsync(ws.XL[0], 0, nx * sizeof(float), st) ? PAT_ERR_CUDA : 0;
-    if (!rc) {
-        const float* xb = p->xbar0_dev ? p->xbar0_dev : p->x0_dev;
-        dim3 blk(32, 8), grd(ceil_div(N + 2, 32), ceil_div(N + 2, 8));
-        k_pad<<<grd, blk, 0, st>>>(xb, ws.ubar_pad, N);
-        count_launch();
-        dim3 gq(ceil_div(N + 1, 32), ceil_div(N + 1, 8));
-        k_quads_from_pad<<<gq, blk, 0, st>>>(ws.ubar_pad, ws.ubar_quad, N);
-        count_launch();
-        if (REG == PAT_TGV) {
-            if (xb)
-                cudaMemcpyAsync(ws.vbar0, xb + NN, 2 * NN * 4, cudaMemcpyDeviceToDevice, st);
-            else
-                cudaMemsetAsync(ws.vbar0, 0, 2 * NN * 4, st);
-        }
-        // dual prologue: (r^1, s^1) from (r^0, s^0) and (ubar^0, vbar^0) into Y[0]
-        DualArgs da{N, (float)p->alpha, (float)(p->alpha * p->beta), (float)p->gamma, sc.sig2, ws.sig_r,
-                    p->xi_dev, ws.ubar_pad, ws.vbar0, ws.Y[1], ws.Y[0]};
-        dim3 g2(ceil_div(N, 32), ceil_div(N, 8));
-        k_dual_step<REG><<<g2, blk, 0, st>>>(da);
-        count_launch();
-        rc = cudaGetLastError() ? PAT_ERR_CUDA : 0;
-    }
-    if (!rc && p->iters > 0) rc = enqueue_iterations<REG>(g, f, p, ws, sc, 0, p->iters, st);
-    if (!rc) {
-        OutArgs oa;
-        oa.n = N;
-        oa.reg = REG;
-        oa.S = (long long)S;
-        oa.theta = (float)p->theta;
-        oa.X[0] = ws.X[0];
-        oa.X[1] = ws.X[1];
-        oa.Y[0] = ws.Y[0];
-        oa.Y[1] = ws.Y[1];
-        oa.q = ws.q;
-        oa.ubar_pad = ws.ubar_pad;
-        oa.info = ws.info;
-        oa.u_out = u_out;
-        oa.x_out = p->x_out_dev;
-        oa.xbar_out = p->xbar_out_dev;
-        oa.y_out = p->y_out_dev;
-        k_output<<<std::min(2 * 152, ceil_div((long long)(nx + ny + S), 256)), 256, 0, st>>>(oa);
-        count_launch();
-        rc = cudaGetLastError() ? PAT_ERR_CUDA : 0;
-    }
-    InfoDev hinfo{};
-    if (!rc) rc = cudaMemcpyAsync(&hinfo, ws.info, sizeof(InfoDev), cudaMemcpyDeviceToHost, st) ? PAT_ERR_CUDA : 0;
+    for (int b = 0; b < B && !rc; ++b) rc = finish_problem(pr[b], st);
+    std::vector<InfoDev> hinfo(B);
+    for (int b = 0; b < B && !rc; ++b)
+        rc = cudaMemcpyAsync(&hinfo[b], pr[b].ws.info, sizeof(InfoDev), cudaMemcpyDeviceToHost, st) ? PAT_ERR_CUDA : 0;
     cudaEventRecord(e1, st);
-    cudaFreeAsync(ws.base, st);
+    if (dev) cudaFreeAsync(dev, st);
+    for (int b = 0; b < B; ++b)
+        if (pr[b].ws.base) cudaFreeAsync(pr[b].ws.base, st);
     cudaError_t se = cudaStreamSynchronize(st);
-    if (!rc && se != cudaSuccess) rc = cuda_fail(se, "pat_reconstruct: stream synchronize");
+    if (!rc && se != cudaSuccess) rc = cuda_fail(se, std::string(who).c_str());
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     prof_collect();
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    cudaEventDestroy(fork);
+    cudaEventDestroy(join);
     if (rc) {
-        if (rc == PAT_ERR_CUDA) set_error(std::string("pat_reconstruct: ") + cudaGetErrorString(cudaGetLastError()));
+        if (rc == PAT_ERR_CUDA && std::string(pat_last_error()).empty())
+            set_error(std::string(who) + ": " + cudaGetErrorString(cudaGetLastError()));
         return rc;
     }
-    if (info) {
-        info->iters_done = p->iters == 0 ? 0 : hinfo.iters_done;
-        info->status = hinfo.stop ? hinfo.status : PAT_STATUS_MAXITER;
-        info->primal = hinfo.primal;
-        info->dual = hinfo.dual;
-        info->gap = hinfo.gap;
-        info->rel_gap = hinfo.rel_gap;
-        info->residual = hinfo.residual;
-        info->ms = ms;
+    bool diverged = false;
+    for (int b = 0; b < B; ++b) {
+        const InfoDev& h = hinfo[b];
+        if (infos) {
+            pat_info& in = infos[b];
+            in.iters_done = p[b].iters == 0 ? 0 : h.iters_done;
+            in.status = h.stop ? h.status : PAT_STATUS_MAXITER;
+            in.primal = h.primal;
+            in.dual = h.dual;
+            in.gap = h.gap;
+            in.rel_gap = h.rel_gap;
+            in.residual = h.residual;
+            in.ms = ms;
+        }
+        diverged = diverged || h.status == PAT_STATUS_DIVERGED;
     }
-    if (hinfo.status == PAT_STATUS_DIVERGED) return fail(PAT_ERR_NONFINITE, "pat_reconstruct: duality gap not finite");
+    if (diverged) return fail(PAT_ERR_NONFINITE, std::string(who) + ": duality gap not finite");
     return PAT_OK;
 }
 
@@ -1100,12 +1376,7 @@ extern "C" int pat_reconstruct(const pat_geometry* g, const float* f_dev, const 
     int rc = validate(g, p, "pat_reconstruct");
     if (rc) return rc;
     if (!f_dev || !u_dev) return fail(PAT_ERR_INVALID_ARG, "pat_reconstruct: NULL data or output");
-    cudaStream_t st = (cudaStream_t)stream;
-    switch (p->reg) {
-        case PAT_TV: return run_reconstruct<PAT_TV>(g, f_dev, p, u_dev, info, st);
-        case PAT_TGV: return run_reconstruct<PAT_TGV>(g, f_dev, p, u_dev, info, st);
-        default: return run_reconstruct<PAT_DTV>(g, f_dev, p, u_dev, info, st);
-    }
+    return run_batch(1, &g, &f_dev, p, &u_dev, info, (cudaStream_t)stream, "pat_reconstruct");
 }
 
 extern "C" int pat_reconstruct_batched(int count, const pat_geometry* const* g, const float* const* f_dev,
@@ -1113,7 +1384,35 @@ extern "C" int pat_reconstruct_batched(int count, const pat_geometry* const* g, 
     if (count < 0 || (count > 0 && (!g || !f_dev || !p || !u_dev)))
         return fail(PAT_ERR_INVALID_ARG, "pat_reconstruct_batched: NULL arrays");
     for (int i = 0; i < count; ++i) {
-        int rc = pat_reconstruct(g[i], f_dev[i], &p[i], u_dev[i], infos ? &infos[i] : nullptr, stream);
+        int rc = validate(g[i], &p[i], "pat_reconstruct_batched");
+        if (rc) return rc;
+        if (!f_dev[i] || !u_dev[i]) return fail(PAT_ERR_INVALID_ARG, "pat_reconstruct_batched: NULL data or output");
+    }
+    // problems advance in lockstep; those sharing (iters, gap_every) run as one batch
+    std::vector<char> done(count, 0);
+    for (int i = 0; i < count; ++i) {
+        if (done[i]) continue;
+        std::vector<int> idx;
+        for (int j = i; j < count; ++j)
+            if (!done[j] && p[j].iters == p[i].iters && p[j].gap_every == p[i].gap_every) {
+                idx.push_back(j);
+                done[j] = 1;
+            }
+        std::vector<const pat_geometry*> gg;
+        std::vector<const float*> ff;
+        std::vector<pat_params> pp;
+        std::vector<float*> uu;
+        std::vector<pat_info> ii(idx.size());
+        for (int j : idx) {
+            gg.push_back(g[j]);
+            ff.push_back(f_dev[j]);
+            pp.push_back(p[j]);
+            uu.push_back(u_dev[j]);
+        }
+        int rc = run_batch((int)idx.size(), gg.data(), ff.data(), pp.data(), uu.data(), ii.data(),
+                           (cudaStream_t)stream, "pat_reconstruct_batched");
+        if (infos)
+            for (size_t k = 0; k < idx.size(); ++k) infos[idx[k]] = ii[k];
         if (rc) return rc;
     }
     return PAT_OK;
@@ -1161,28 +1460,52 @@ extern "C" int pat_steps(const pat_geometry* g, const pat_params* p, float* sig_
     return PAT_OK;
 }
 
-template <int REG>
 static int gap_impl(const pat_geometry* g, const float* f, const pat_params* p, const float* x, const float* y,
                     double* out4, cudaStream_t st) {
-    const long long S = (long long)g->desc.n_det * g->desc.n_t;
-    Workspace ws;
-    int rc = alloc_workspace(g, REG, ws, st);
+    Prob pr;
+    pr.g = g;
+    pr.f = f;
+    pr.p = *p;
+    pr.p.tol = 0;
+    int rc = alloc_workspace(g, p->reg, pr.ws, st);
     if (rc) return rc;
+    const long long S = (long long)g->desc.n_det * g->desc.n_t;
+    const int N = g->desc.n;
     InfoDev h{};
-    rc = cudaMemsetAsync(ws.info, 0, sizeof(InfoDev), st) ? PAT_ERR_CUDA : 0;
-    if (!rc) rc = ensure_precond(g, st);
+    rc = ensure_precond(g, st);
+    if (!rc) rc = cudaMemsetAsync(pr.ws.info, 0, sizeof(InfoDev), st) ? PAT_ERR_CUDA : 0;
+    if (!rc) rc = cudaMemsetAsync(pr.ws.kt[0], 0, (size_t)N * N * sizeof(int), st) ? PAT_ERR_CUDA : 0;
+    if (!rc) rc = launch_absmax(y, S, &pr.ws.info->qmax_bits[0], st);
+    std::vector<char> host;
+    void* dev = nullptr;
     if (!rc) {
-        const long long S_ = (long long)g->desc.n_det * g->desc.n_t;
-        rc = cudaMemsetAsync(ws.kt[0], 0, (size_t)g->desc.n * g->desc.n * sizeof(int), st) ? PAT_ERR_CUDA : 0;
-        if (!rc) rc = launch_absmax(y, S_, &ws.info->qmax_bits[0], st);
-        if (!rc) rc = launch_adjoint_fixed(g, y, nullptr, &ws.info->qmax_bits[0], ws.kt[0], nullptr, st);
+        // one problem, one gap evaluation of (x, y): K^T q then the three gap passes
+        GapPlan gp;
+        Arena ar(host);
+        build_gap_plan(&pr, 1, ar, gp);
+        AdjArgs aa = make_adj_args(g, y, nullptr, &pr.ws.info->qmax_bits[0], pr.ws.kt[0], nullptr);
+        const size_t adj_off = ar.put(&aa, 1);
+        std::vector<int2> amap(g->adj_items);
+        for (int i = 0; i < g->adj_items; ++i) amap[i] = make_int2(0, i);
+        const size_t amap_off = ar.put(amap.data(), amap.size());
+        FwdGapArgs fa = make_fwd_gap_args(g, x, nullptr, y, f, pr.ws.data_part, nullptr);
+        const size_t fa_off = ar.put(&fa, 1);
+        GapArgs ga = make_gap_args(pr, kt_view(g, pr.ws.kt[0], &pr.ws.info->qmax_bits[0]), x, nullptr, y + S);
+        const size_t ga_off = ar.put(&ga, 1);
+        FinalArgs fi = make_final_args(pr);
+        const size_t fi_off = ar.put(&fi, 1);
+        rc = ar.upload(&dev, st);
+        if (!rc) {
+            char* b = (char*)dev;
+            rc = launch_adjoint_b((const AdjArgs*)(b + adj_off), (const int2*)(b + amap_off), g->adj_items, false, st);
+            if (!rc)
+                rc = launch_gap_phase((const FwdGapArgs*)(b + fa_off), (const GapArgs*)(b + ga_off),
+                                      (const FinalArgs*)(b + fi_off), gp, b, st);
+        }
     }
-    pat_params q = *p;
-    q.tol = 0;
-    if (!rc) rc = launch_gap<REG>(g, &q, ws, kt_view(g, ws.kt[0], &ws.info->qmax_bits[0]), x, nullptr, nullptr,
-                                  y + S, y, f, nullptr, st);
-    if (!rc) rc = cudaMemcpyAsync(&h, ws.info, sizeof(InfoDev), cudaMemcpyDeviceToHost, st) ? PAT_ERR_CUDA : 0;
-    cudaFreeAsync(ws.base, st);
+    if (!rc) rc = cudaMemcpyAsync(&h, pr.ws.info, sizeof(InfoDev), cudaMemcpyDeviceToHost, st) ? PAT_ERR_CUDA : 0;
+    if (dev) cudaFreeAsync(dev, st);
+    cudaFreeAsync(pr.ws.base, st);
     cudaError_t se = cudaStreamSynchronize(st);
     if (!rc && se != cudaSuccess) rc = cuda_fail(se, "pat_duality_gap");
     if (rc) return rc;
@@ -1198,12 +1521,7 @@ extern "C" int pat_duality_gap(const pat_geometry* g, const float* f_dev, const 
     int rc = validate(g, p, "pat_duality_gap");
     if (rc) return rc;
     if (!f_dev || !x_dev || !y_dev || !out4_host) return fail(PAT_ERR_INVALID_ARG, "pat_duality_gap: NULL argument");
-    cudaStream_t st = (cudaStream_t)stream;
-    switch (p->reg) {
-        case PAT_TV: return gap_impl<PAT_TV>(g, f_dev, p, x_dev, y_dev, out4_host, st);
-        case PAT_TGV: return gap_impl<PAT_TGV>(g, f_dev, p, x_dev, y_dev, out4_host, st);
-        default: return gap_impl<PAT_DTV>(g, f_dev, p, x_dev, y_dev, out4_host, st);
-    }
+    return gap_impl(g, f_dev, p, x_dev, y_dev, out4_host, (cudaStream_t)stream);
 }
 
 __global__ void k_direction_field(int N, const float* __restrict__ w, float eta, float* __restrict__ xi) {

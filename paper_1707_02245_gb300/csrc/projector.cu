@@ -49,15 +49,18 @@ struct RowLane {
     bool valid;
 };
 
-__device__ __forceinline__ RowLane row_lane(const GeomView& g) {
+// lane of row block kb of detector d
+__device__ __forceinline__ RowLane row_lane(const GeomView& g, int kb, int d) {
     RowLane r;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     r.ph = lane >> 3;
-    r.d = blockIdx.y;
-    r.k = blockIdx.x * ROWS_PER_BLOCK + warp * KGRP + (lane & 7);
+    r.d = d;
+    r.k = kb * ROWS_PER_BLOCK + warp * KGRP + (lane & 7);
     r.valid = r.k < g.n_t;
     return r;
 }
+
+__device__ __forceinline__ int row_blocks(const GeomView& g) { return (g.n_t + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK; }
 
 // Partial integral of the bilinear image over circle (d, k) for one angular phase.
 // QUAD: u points at (N+1)^2 float4 quads (one load per point); otherwise u is the plain
@@ -104,31 +107,27 @@ __device__ __forceinline__ float phase_sum(float v) {
 
 // y = K u
 __global__ void __launch_bounds__(ROW_THREADS) k_forward(GeomView g, const float* __restrict__ u, float* __restrict__ y) {
-    const RowLane rl = row_lane(g);
+    const RowLane rl = row_lane(g, blockIdx.x, blockIdx.y);
     const float s = phase_sum(circle_partial<false>(g, u, rl));
     if (rl.valid && rl.ph == 0) y[(size_t)rl.d * g.n_t + rl.k] = s * __ldg(&g.wk[rl.k]);
 }
 
 // q <- prox_{sigma F1*}(q + sigma K ubar) = (q + sigma (K ubar - f)) / (1 + sigma)  (Sec. 3.2)
-// Also records max |q| (as float bits) for the fixed-point K^T that follows.
-__global__ void __launch_bounds__(ROW_THREADS) k_forward_prox(GeomView g, const float4* __restrict__ ubar_quad,
-                                                             float* __restrict__ q, const float* __restrict__ f,
-                                                             const float* __restrict__ sig_q, float sig_scalar,
-                                                             float* __restrict__ qw,
-                                                             unsigned* __restrict__ qmax_bits,
-                                                             const int* __restrict__ stop) {
-    if (stop && *(volatile const int*)stop) return;
-    const RowLane rl = row_lane(g);
-    const float s = phase_sum(circle_partial<true>(g, reinterpret_cast<const float*>(ubar_quad), rl));
+// for the rows of row block kb of detector d.  Also records q w_k for the K^T that follows
+// and max |q| (as float bits) for its fixed-point scale.
+__device__ __forceinline__ void forward_prox_rows(const FwdProxArgs& a, int kb, int d) {
+    const GeomView& g = a.g;
+    const RowLane rl = row_lane(g, kb, d);
+    const float s = phase_sum(circle_partial<true>(g, reinterpret_cast<const float*>(a.ubar_quad), rl));
     float aq = 0.f;
     if (rl.valid && rl.ph == 0) {
         const size_t i = (size_t)rl.d * g.n_t + rl.k;
         const float wk = __ldg(&g.wk[rl.k]);
         const float ku = s * wk;
-        const float sg = sig_q ? sig_q[i] : sig_scalar;
-        const float qn = (q[i] + sg * (ku - f[i])) / (1.f + sg);
-        q[i] = qn;
-        qw[i] = qn * wk;   // the K^T that follows reads q_k w_k
+        const float sg = a.sig_q ? a.sig_q[i] : a.sig_scalar;
+        const float qn = (a.q[i] + sg * (ku - a.f[i])) / (1.f + sg);
+        a.q[i] = qn;
+        a.qw[i] = qn * wk;
         aq = fabsf(qn);
     }
     // block max of |q| (a NaN's bits compare greater than every finite value's)
@@ -141,8 +140,17 @@ __global__ void __launch_bounds__(ROW_THREADS) k_forward_prox(GeomView g, const 
     if (threadIdx.x == 0) {
         unsigned m = 0;
         for (int w = 0; w < ROW_THREADS / 32; ++w) m = max(m, wmax[w]);
-        if (m) atomicMax(qmax_bits, m);
+        if (m) atomicMax(a.qmax_bits, m);
     }
+}
+
+__global__ void __launch_bounds__(ROW_THREADS) k_forward_prox_b(const FwdProxArgs* __restrict__ args,
+                                                               const int2* __restrict__ map) {
+    const int2 pm = map[blockIdx.x];
+    const FwdProxArgs& a = args[pm.x];
+    if (a.stop && *(volatile const int*)a.stop) return;
+    const int nkb = row_blocks(a.g);
+    forward_prox_rows(a, pm.y % nkb, pm.y / nkb);
 }
 
 // max |y| over n values as float bits (atomicMax; *out must start at 0)
@@ -156,33 +164,42 @@ __global__ void k_absmax(const float* __restrict__ y, long long n, unsigned* __r
 }
 
 // FP64 partial sums for the duality gap over data rows:
-//   {sum (K u - f)^2, sum q^2, sum q f}   one triple per block
+//   {sum (K u - f)^2, sum q^2, sum q f}   one triple per (local) block lb
 template <bool QUAD>
-__global__ void __launch_bounds__(ROW_THREADS) k_forward_gap(GeomView g, const float* __restrict__ u,
-                                                            const float* __restrict__ q, const float* __restrict__ f,
-                                                            double* __restrict__ partials,
-                                                            const int* __restrict__ stop) {
-    if (stop && *(volatile const int*)stop) return;
-    const RowLane rl = row_lane(g);
-    const float s = phase_sum(circle_partial<QUAD>(g, u, rl));
+__device__ __forceinline__ void forward_gap_rows(const FwdGapArgs& a, int kb, int d, int lb) {
+    const GeomView& g = a.g;
+    const RowLane rl = row_lane(g, kb, d);
+    const float* img = QUAD ? reinterpret_cast<const float*>(a.u_quad) : a.u;
+    const float s = phase_sum(circle_partial<QUAD>(g, img, rl));
     // per-row terms in FP32, block sums in FP64 (GB300's FP64 pipe is 1/64 of FP32)
-    float a = 0.f, b = 0.f, c = 0.f;
+    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
     if (rl.valid && rl.ph == 0) {
         const float ku = s * __ldg(&g.wk[rl.k]);
         const size_t i = (size_t)rl.d * g.n_t + rl.k;
-        const float res = ku - f[i];
-        const float qi = q[i];
-        a = res * res;
-        b = qi * qi;
-        c = qi * f[i];
+        const float res = ku - a.f[i];
+        const float qi = a.q[i];
+        t0 = res * res;
+        t1 = qi * qi;
+        t2 = qi * a.f[i];
     }
-    const double3 sum = block_sum3(make_double3((double)a, (double)b, (double)c));
+    const double3 sum = block_sum3(make_double3((double)t0, (double)t1, (double)t2));
     if (threadIdx.x == 0) {
-        const int blk = blockIdx.y * gridDim.x + blockIdx.x;
-        partials[3 * blk + 0] = sum.x;
-        partials[3 * blk + 1] = sum.y;
-        partials[3 * blk + 2] = sum.z;
+        a.partials[3 * lb + 0] = sum.x;
+        a.partials[3 * lb + 1] = sum.y;
+        a.partials[3 * lb + 2] = sum.z;
     }
+}
+
+__global__ void __launch_bounds__(ROW_THREADS) k_forward_gap_b(const FwdGapArgs* __restrict__ args,
+                                                              const int2* __restrict__ map) {
+    const int2 pm = map[blockIdx.x];
+    const FwdGapArgs& a = args[pm.x];
+    if (a.stop && *(volatile const int*)a.stop) return;
+    const int nkb = row_blocks(a.g);
+    if (a.u_quad)
+        forward_gap_rows<true>(a, pm.y % nkb, pm.y / nkb, pm.y);
+    else
+        forward_gap_rows<false>(a, pm.y % nkb, pm.y / nkb, pm.y);
 }
 
 // ---------------------------------------------------------------------------------
@@ -208,26 +225,12 @@ __global__ void __launch_bounds__(ROW_THREADS) k_forward_gap(GeomView g, const f
 // ---------------------------------------------------------------------------------
 constexpr int ATHREADS = 256;
 
-struct AdjArgs {
-    GeomView g;
-    const float* y;          // data rows, or data rows times the arc weights (premul)
-    int premul;
-    const unsigned* ymax_bits;
-    const float* tile_kmax;
-    const int4* box;
-    const int4* units;
-    const int4* items;
-    int* acc_out;        // N*N fixed-point image, added to with integer atomics
-    int tiles_x;
-    const int* stop;
-};
 
 template <bool PREMUL>
-__global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
-    if (a.stop && *(volatile const int*)a.stop) return;
+__device__ __forceinline__ void adjoint_item(const AdjArgs& a, int item_index) {
     const GeomView& g = a.g;
     const int N = g.n, T = g.n_t, M = g.quad_m, D = g.n_det;
-    const int4 item = __ldg(&a.items[blockIdx.x]);
+    const int4 item = __ldg(&a.items[item_index]);
     const int tile = item.x;
     const int x0 = (tile % a.tiles_x) * ATILE, y0 = (tile / a.tiles_x) * ATILE;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -338,6 +341,21 @@ __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
     }
 }
 
+template <bool PREMUL>
+__global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
+    if (a.stop && *(volatile const int*)a.stop) return;
+    adjoint_item<PREMUL>(a, blockIdx.x);
+}
+
+template <bool PREMUL>
+__global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles_b(const AdjArgs* __restrict__ args,
+                                                            const int2* __restrict__ map) {
+    const int2 pm = map[blockIdx.x];
+    const AdjArgs& a = args[pm.x];
+    if (a.stop && *(volatile const int*)a.stop) return;
+    adjoint_item<PREMUL>(a, pm.y);
+}
+
 // out = the fixed-point K^T image in floating point
 __global__ void k_kt_to_float(KtView kt, int N, float* __restrict__ out) {
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
@@ -409,10 +427,12 @@ static dim3 row_grid(const pat_geometry* g) {
     return dim3(ceil_div(g->desc.n_t, ROWS_PER_BLOCK), g->desc.n_det);
 }
 
-int forward_gap_blocks(const pat_geometry* g) {
+int forward_row_blocks(const pat_geometry* g) {
     dim3 gr = row_grid(g);
     return gr.x * gr.y;
 }
+
+int forward_rows_per_block() { return ROWS_PER_BLOCK; }
 
 int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y, cudaStream_t st) {
     (void)padded;
@@ -421,24 +441,47 @@ int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y,
     return PAT_OK;
 }
 
-int launch_forward_prox(const pat_geometry* g, const float4* ubar_quad, float* q, const float* f,
-                        const float* sig_q, float sig_q_scalar, float* qw, unsigned* qmax_bits,
-                        const int* stop, cudaStream_t st) {
-    k_forward_prox<<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, ubar_quad, q, f, sig_q, sig_q_scalar, qw,
-                                                         qmax_bits, stop);
-    PAT_LAUNCH_CHECK("k_forward_prox");
+FwdProxArgs make_fwd_prox_args(const pat_geometry* g, const float4* ubar_quad, float* q, const float* f,
+                               const float* sig_q, float sig_scalar, float* qw, unsigned* qmax_bits, const int* stop) {
+    FwdProxArgs a;
+    a.g = g->view;
+    a.ubar_quad = ubar_quad;
+    a.q = q;
+    a.f = f;
+    a.sig_q = sig_q;
+    a.sig_scalar = sig_scalar;
+    a.qw = qw;
+    a.qmax_bits = qmax_bits;
+    a.stop = stop;
+    return a;
+}
+
+FwdGapArgs make_fwd_gap_args(const pat_geometry* g, const float* u, const float4* u_quad, const float* q,
+                             const float* f, double* partials, const int* stop) {
+    FwdGapArgs a;
+    a.g = g->view;
+    a.u = u;
+    a.u_quad = u_quad;
+    a.q = q;
+    a.f = f;
+    a.partials = partials;
+    a.stop = stop;
+    return a;
+}
+
+int launch_forward_prox_b(const FwdProxArgs* args, const int2* map, int nblocks, cudaStream_t st) {
+    if (nblocks <= 0) return PAT_OK;
+    prof_mark(PAT_PHASE_FORWARD_PROX, st, true);
+    k_forward_prox_b<<<nblocks, ROW_THREADS, 0, st>>>(args, map);
+    PAT_LAUNCH_CHECK("k_forward_prox_b");
+    prof_mark(PAT_PHASE_FORWARD_PROX, st, false);
     return PAT_OK;
 }
 
-int launch_forward_gap(const pat_geometry* g, const float* u, const float4* u_quad, const float* q, const float* f,
-                       double* partials, int n_part, const int* stop, cudaStream_t st) {
-    (void)n_part;
-    if (u_quad)
-        k_forward_gap<true><<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, reinterpret_cast<const float*>(u_quad), q,
-                                                                 f, partials, stop);
-    else
-        k_forward_gap<false><<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, u, q, f, partials, stop);
-    PAT_LAUNCH_CHECK("k_forward_gap");
+int launch_forward_gap_b(const FwdGapArgs* args, const int2* map, int nblocks, cudaStream_t st) {
+    if (nblocks <= 0) return PAT_OK;
+    k_forward_gap_b<<<nblocks, ROW_THREADS, 0, st>>>(args, map);
+    PAT_LAUNCH_CHECK("k_forward_gap_b");
     return PAT_OK;
 }
 
@@ -457,9 +500,37 @@ KtView kt_view(const pat_geometry* g, const int* acc, const unsigned* ymax_bits)
     return v;
 }
 
-int launch_adjoint_fixed(const pat_geometry* g, const float* y, const float* premul, const unsigned* ymax_bits,
-                         int* acc, const int* stop, cudaStream_t st) {
+AdjArgs make_adj_args(const pat_geometry* g, const float* y, const float* premul, const unsigned* ymax_bits, int* acc,
+                      const int* stop) {
+    AdjArgs a;
+    a.g = g->view;
+    a.y = premul ? premul : y;
+    a.premul = premul ? 1 : 0;
+    a.ymax_bits = ymax_bits;
+    a.tile_kmax = g->pc.tile_kmax;
+    a.box = g->adj_box;
+    a.acc_out = acc;
+    a.units = g->adj_units;
+    a.items = g->adj_item;
+    a.tiles_x = g->adj_tiles_x;
+    a.stop = stop;
+    return a;
+}
+
+int launch_adjoint_b(const AdjArgs* args, const int2* map, int nblocks, bool premul, cudaStream_t st) {
+    if (nblocks <= 0) return PAT_OK;
     prof_mark(PAT_PHASE_ADJOINT, st, true);
+    if (premul)
+        k_adjoint_tiles_b<true><<<nblocks, ATHREADS, 0, st>>>(args, map);
+    else
+        k_adjoint_tiles_b<false><<<nblocks, ATHREADS, 0, st>>>(args, map);
+    PAT_LAUNCH_CHECK("k_adjoint_tiles_b");
+    prof_mark(PAT_PHASE_ADJOINT, st, false);
+    return PAT_OK;
+}
+
+static int launch_adjoint_fixed(const pat_geometry* g, const float* y, const float* premul,
+                                const unsigned* ymax_bits, int* acc, const int* stop, cudaStream_t st) {
     AdjArgs a;
     a.g = g->view;
     a.y = premul ? premul : y;
@@ -477,7 +548,6 @@ int launch_adjoint_fixed(const pat_geometry* g, const float* y, const float* pre
     else
         k_adjoint_tiles<false><<<g->adj_items, ATHREADS, 0, st>>>(a);
     PAT_LAUNCH_CHECK("k_adjoint_tiles");
-    prof_mark(PAT_PHASE_ADJOINT, st, false);
     return PAT_OK;
 }
 

@@ -350,3 +350,83 @@ def test_full_size_tgv_one_iteration_from_state():
     assert rel_l2(yg[:S_], ref.q) <= 1e-5
     assert rel_l2(xg[n * n:], ref.v) <= 1e-5
     assert rel_l2(yg[S_ + 2 * n * n:], ref.s) <= 1e-5
+
+
+def _batch_problem(name, seed, reg, **over):
+    w = make(name, seed=seed, reg=reg, **over)
+    pg = P.Geometry(w["n"], w["det_xy"], w["n_t"], w["r0"], w["dr"], w["quad_m"])
+    return w, pg
+
+
+def test_batched_matches_single_runs_bitwise():
+    """Problems of different sizes and regularisers in one lockstep batch give exactly the
+    iterates of their single runs (every kernel is deterministic)."""
+    specs = [("small", 1, 0, {}), ("small", 2, 1, {"beta": 0.5}), ("small", 3, 2, {}),
+             ("small", 4, 1, {"beta": 0.3, "n": 20})]
+    probs = []
+    for name, seed, reg, over in specs:
+        if "n" in over:
+            w = S.workload(name, seed)
+            w.update(over)
+            w["phantom_fine"] = S.rasterise_discs(S.disc_params(3, seed), 2 * w["n"])
+            from tests.problems import noisy_data
+            w["f"] = noisy_data(w)
+            w["reg"], w["beta"] = reg, over["beta"]
+            pg = P.Geometry(w["n"], w["det_xy"], w["n_t"], w["r0"], w["dr"], w["quad_m"])
+        else:
+            w, pg = _batch_problem(name, seed, reg, **over)
+        probs.append((w, pg))
+    iters = 45
+    singles, fs, xis, prms, outs = [], [], [], [], []
+    for w, pg in probs:
+        f = dev(w["f"])
+        xi = dev(w["xi"]) if w["reg"] == 2 else None
+        u = torch.empty(w["n"], w["n"], device=DEV)
+        prm = P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"], xi=xi, iters=iters,
+                            gap_every=10)
+        P.pat_reconstruct(pg.handle, f, prm, u)
+        singles.append(host(u))
+        fs.append(f)
+        xis.append(xi)
+        prms.append(prm)
+        outs.append(torch.zeros(w["n"], w["n"], device=DEV))
+    infos = P.pat_reconstruct_batched([pg.handle for _, pg in probs], fs, prms, outs)
+    for (w, _), s_u, o, inf in zip(probs, singles, outs, infos):
+        assert inf["iters_done"] == iters
+        assert np.array_equal(host(o), s_u)
+
+
+def test_batched_groups_unequal_iteration_counts():
+    w1, g1 = _batch_problem("small", 5, 0)
+    w2, g2 = _batch_problem("small", 6, 1, beta=0.5)
+    f1, f2 = dev(w1["f"]), dev(w2["f"])
+    p1 = P.make_params(reg=0, alpha=w1["alpha"], iters=12, gap_every=4)
+    p2 = P.make_params(reg=1, alpha=w2["alpha"], beta=0.5, iters=30, gap_every=10)
+    o1, o2 = torch.empty(w1["n"], w1["n"], device=DEV), torch.empty(w2["n"], w2["n"], device=DEV)
+    infos = P.pat_reconstruct_batched([g1.handle, g2.handle], [f1, f2], [p1, p2], [o1, o2])
+    assert [i["iters_done"] for i in infos] == [12, 30]
+    s1 = torch.empty_like(o1)
+    P.pat_reconstruct(g1.handle, f1, P.make_params(reg=0, alpha=w1["alpha"], iters=12, gap_every=4), s1)
+    assert np.array_equal(host(o1), host(s1))
+
+
+def test_graph_replay_matches_direct_launches():
+    """The periodic part of the loop is replayed from a CUDA graph; with the profiler on the
+    same iterations run as direct launches.  Both give identical iterates."""
+    w, pg = _batch_problem("small", 7, 1, beta=0.5)
+    f = dev(w["f"])
+    prm = P.make_params(reg=1, alpha=w["alpha"], beta=0.5, iters=57, gap_every=5)
+    u_graph, u_direct = torch.empty(w["n"], w["n"], device=DEV), torch.empty(w["n"], w["n"], device=DEV)
+    n0 = P.pat_kernel_launches()
+    P.pat_reconstruct(pg.handle, f, prm, u_graph)
+    n_graph = P.pat_kernel_launches() - n0
+    P.pat_profile_enable(True)
+    try:
+        n0 = P.pat_kernel_launches()
+        P.pat_reconstruct(pg.handle, f, prm, u_direct)
+        n_direct = P.pat_kernel_launches() - n0
+    finally:
+        P.pat_profile_enable(False)
+        P.pat_profile_read(reset=True)
+    assert np.array_equal(host(u_graph), host(u_direct))
+    assert n_graph == n_direct
