@@ -879,11 +879,11 @@ static int launch_update_b(int reg, const UpdateArgs* args, const int2* map, int
     if (n <= 0) return PAT_OK;
     prof_mark(PAT_PHASE_UPDATE, st, true);
     if (reg == PAT_TV)
-        k_update_b<PAT_TV><<<n, TX * TY, 0, st>>>(args, map);
+        k_update_b<PAT_TV><<<n, dim3(TX, TY), 0, st>>>(args, map);
     else if (reg == PAT_TGV)
-        k_update_b<PAT_TGV><<<n, TX * TY, 0, st>>>(args, map);
+        k_update_b<PAT_TGV><<<n, dim3(TX, TY), 0, st>>>(args, map);
     else
-        k_update_b<PAT_DTV><<<n, TX * TY, 0, st>>>(args, map);
+        k_update_b<PAT_DTV><<<n, dim3(TX, TY), 0, st>>>(args, map);
     PAT_LAUNCH_CHECK("k_update_b");
     prof_mark(PAT_PHASE_UPDATE, st, false);
     return PAT_OK;
