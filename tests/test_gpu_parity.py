@@ -368,6 +368,7 @@ def test_batched_matches_single_runs_bitwise():
         if "n" in over:
             w = S.workload(name, seed)
             w.update(over)
+            w["n_fine"] = 2 * w["n"]
             w["phantom_fine"] = S.rasterise_discs(S.disc_params(3, seed), 2 * w["n"])
             from tests.problems import noisy_data
             w["f"] = noisy_data(w)
