@@ -331,6 +331,14 @@ def run_gb300(args) -> int:
                "rel_gap": info["rel_gap"], "reached": info["status"] == P.PAT_STATUS_CONVERGED,
                "max_iters": args.ttg_max_iters}
 
+    # ---- batched: B TGV 256^2 problems in lockstep, and the 64-problem mixed batch ----
+    batched = None
+    if args.batch > 0:
+        batched = run_batched_tgv(P, S, np, torch, device, stream, args.batch, iters, flush)
+    mixed = None
+    if args.mixed:
+        mixed = run_mixed(P, S, np, torch, device, stream, flush, args.mixed_max_iters)
+
     # ---- roofline of the dominant phase ----
     NN = n * n
     S_ = f.numel()
@@ -381,12 +389,83 @@ def run_gb300(args) -> int:
                            "points_on_grid_per_K": pts, "final_rel_gap": infos[-1]["rel_gap"]},
                 "roofline": roofline, "phases": phases, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "time_to_gap": ttg,
+                "batched": batched, "mixed_batch": mixed,
                 "wall_s_timed": wall, "profiled_ms_per_step": sum(prof_ms) / len(prof_ms)}
         print(json.dumps(line), flush=True)
     geo.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+def make_problem(P, np, torch, device, stream, w):
+    """Geometry, data (K on the 2x finer grid plus the recipe's noise) and parameters."""
+    n = w["n"]
+    fine = P.Geometry(w["n_fine"], w["det_xy"], w["n_t"], w["r0"], w["dr"], w["quad_m_fine"])
+    ph_f = torch.from_numpy(w["phantom_fine"].astype(np.float32)).to(device)
+    clean = torch.empty(w["det_xy"].shape[0], w["n_t"], device=device)
+    P.pat_forward(fine.handle, ph_f, clean, stream)
+    noise = torch.from_numpy(w["noise"].astype(np.float32)).to(device)
+    f = (clean + w["noise_level"] * clean.abs().max() * noise).contiguous()
+    fine.close()
+    geo = P.Geometry(n, w["det_xy"], w["n_t"], w["r0"], w["dr"], w["quad_m"])
+    xi = None
+    if w["reg"] == P.PAT_DTV:
+        side = torch.from_numpy(w["side"].astype(np.float32)).to(device)
+        xi = torch.empty(2, n, n, device=device)
+        P.pat_direction_field(n, side, w["eta"], xi, stream)
+    u = torch.empty(n, n, device=device)
+    return geo, f, xi, u
+
+
+def run_batched_tgv(P, S, np, torch, device, stream, count, iters, flush):
+    """count TGV 256^2 problems (seeds 0..count-1) in one lockstep pat_reconstruct_batched."""
+    probs = [make_problem(P, np, torch, device, stream, S.workload("tgv256", seed=s)) for s in range(count)]
+    w0 = S.workload("tgv256", 0)
+    prms = [P.make_params(reg=w0["reg"], alpha=w0["alpha"], beta=w0["beta"], iters=iters, gap_every=10)
+            for _ in probs]
+    geos, fs, us = [p[0].handle for p in probs], [p[1] for p in probs], [p[3] for p in probs]
+    for _ in range(2):
+        P.pat_reconstruct_batched(geos, fs, prms, us, stream)
+    ms = []
+    for _ in range(3):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.pat_reconstruct_batched(geos, fs, prms, us, stream)
+        e1.record(stream)
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    for p in probs:
+        p[0].close()
+    t = sum(ms) / len(ms) / 1e3
+    return {"problems": count, "iters_per_problem": iters, "ms_per_batch": 1e3 * t,
+            "value": count * iters / t, "unit": "problem-iters/s"}
+
+
+def run_mixed(P, S, np, torch, device, stream, flush, max_iters):
+    """The 64-problem mixed batch solved to relative gap 1e-4 (gap every 10 iterations)."""
+    ws = S.workload_batch(0, 64)
+    probs = [make_problem(P, np, torch, device, stream, w) for w in ws]
+    prms = [P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"], xi=p[2],
+                          iters=max_iters, gap_every=10, tol=1e-4) for w, p in zip(ws, probs)]
+    geos, fs, us = [p[0].handle for p in probs], [p[1] for p in probs], [p[3] for p in probs]
+    P.pat_reconstruct_batched(geos, fs, prms, us, stream)  # warm-up (also computes the K sums)
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    infos = P.pat_reconstruct_batched(geos, fs, prms, us, stream)
+    e1.record(stream)
+    e1.synchronize()
+    t = e0.elapsed_time(e1) / 1e3
+    for p in probs:
+        p[0].close()
+    its = [i["iters_done"] for i in infos]
+    conv = sum(1 for i in infos if i["status"] == P.PAT_STATUS_CONVERGED)
+    return {"problems": len(ws), "seconds": t, "converged": conv, "tol": 1e-4, "max_iters": max_iters,
+            "iters_median": float(np.median(its)), "iters_max": int(max(its)),
+            "problem_iters_per_s": sum(its) / t,
+            "pixels": int(sum(w["n"] ** 2 for w in ws)), "samples": int(sum(w["det_xy"].shape[0] * w["n_t"] for w in ws))}
 
 
 def load_peaks() -> dict:
@@ -414,6 +493,9 @@ def main(argv=None) -> int:
     ap.add_argument("--iters", type=int, default=0,
                     help="override the PDHG iterations per step (short runs for the ncu launch list)")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--batch", type=int, default=16, help="TGV 256^2 problems in the lockstep batch (0: skip)")
+    ap.add_argument("--mixed", type=int, default=1, help="run the 64-problem mixed batch (0: skip)")
+    ap.add_argument("--mixed-max-iters", type=int, default=5000)
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -319,3 +319,44 @@ def workload(name: str, seed: int = 0) -> dict:
         out["side"] = w
         out["eta"] = 0.01 * float(w.max() - w.min())
     return out
+
+
+def workload_batch(seed: int = 0, count: int = 64) -> list[dict]:
+    """A batch of uneven independent reconstructions (the mixed batched workload).
+
+    Per problem: image side N from {128, 192, 256, 384, 512}, detector count from
+    {32, 64, 128, 256, 512} on a full circle of radius 1.2, T = 2N time samples,
+    M = 256; regulariser TV, TGV or directional TV in equal thirds; alpha log-uniform in
+    [1e-3, 1e-1]; phantom a disc set or a vessel tree (alternating); noise level U[1%, 10%].
+    Same keys as ``workload``.
+    """
+    g = _rng(seed + 4242)
+    sizes = [128, 192, 256, 384, 512]
+    dets = [32, 64, 128, 256, 512]
+    out = []
+    for i in range(count):
+        n = int(g.choice(sizes))
+        n_det = int(g.choice(dets))
+        n_t = 2 * n
+        reg = i % 3
+        alpha = float(10.0 ** g.uniform(-3.0, -1.0))
+        level = float(g.uniform(0.01, 0.10))
+        pseed = int(g.integers(0, 2**31 - 1))
+        det = detectors_full_circle(n_det, 1.2)
+        if i % 2 == 0:
+            discs = disc_params(5, pseed)
+            ph, ph_f = rasterise_discs(discs, n, 2), rasterise_discs(discs, 2 * n, 2)
+        else:
+            ph = vessel_phantom(n, pseed, supersample=2)
+            ph_f = vessel_phantom(2 * n, pseed, n_ref=n, supersample=2)
+        r0, dr = radial_sampling(det, n_t)
+        w = dict(name=f"batch{i}", seed=pseed, n=n, det_xy=det, n_t=n_t, r0=r0, dr=dr, quad_m=256,
+                 n_fine=2 * n, quad_m_fine=512, phantom=ph, phantom_fine=ph_f,
+                 noise=standard_normal((n_det, n_t), pseed + 17), noise_level=level,
+                 reg=reg, alpha=alpha, beta=2.0 if reg == 1 else 1.0, gamma=0.95, iters=1000)
+        if reg == 2:
+            side = side_image(n, pseed) if i % 2 == 1 else rasterise_discs(disc_params(5, pseed), n)
+            w["side"] = side
+            w["eta"] = 0.01 * float(side.max() - side.min())
+        out.append(w)
+    return out
