@@ -151,6 +151,20 @@ __device__ __forceinline__ void point_coords(const GeomView& g, float2 det, floa
 // Launch helpers
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// Copies problem p's argument struct into the block's shared copy (one word per thread)
+// so that field reads are shared-memory broadcasts; ends with a block barrier.
+template <class T>
+__device__ __forceinline__ const T& stage_args(const T* __restrict__ args, int p, T& smem) {
+    static_assert(sizeof(T) % 4 == 0, "argument structs are whole words");
+    constexpr int W = (int)(sizeof(T) / 4);
+    const int* src = reinterpret_cast<const int*>(args + p);
+    int* dst = reinterpret_cast<int*>(&smem);
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x, nt = blockDim.x * blockDim.y;
+    for (int i = tid; i < W; i += nt) dst[i] = src[i];
+    __syncthreads();
+    return smem;
+}
+
 // ---------------------------------------------------------------------------------
 // per-problem kernel arguments of the batched launches: a launch covers several problems,
 // block b of the launch works on problem map[b].x, local block map[b].y

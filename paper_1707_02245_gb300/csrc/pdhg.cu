@@ -249,7 +249,8 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
 template <int REG>
 __global__ void __launch_bounds__(TX* TY) k_update_b(const UpdateArgs* __restrict__ args, const int2* __restrict__ map) {
     const int2 pm = map[blockIdx.x];
-    const UpdateArgs& a = args[pm.x];
+    __shared__ UpdateArgs sa;
+    const UpdateArgs& a = stage_args(args, pm.x, sa);
     if (a.stop && *(volatile const int*)a.stop) return;
     update_tile<REG>(a, pm.y % a.tiles_x, pm.y / a.tiles_x, pm.y == 0);
 }
@@ -415,7 +416,8 @@ __device__ __forceinline__ void gap_pixels_block(const GapArgs& a, const int lb)
 template <int REG>
 __global__ void __launch_bounds__(256) k_gap_pixels_b(const GapArgs* __restrict__ args, const int2* __restrict__ map) {
     const int2 pm = map[blockIdx.x];
-    const GapArgs& a = args[pm.x];
+    __shared__ GapArgs sa;
+    const GapArgs& a = stage_args(args, pm.x, sa);
     if (a.stop && *(volatile const int*)a.stop) return;
     gap_pixels_block<REG>(a, pm.y);
 }
@@ -499,7 +501,8 @@ __device__ __forceinline__ void gap_final_block(const FinalArgs& a, const int lb
 
 __global__ void __launch_bounds__(256) k_gap_final_b(const FinalArgs* __restrict__ args, const int2* __restrict__ map) {
     const int2 pm = map[blockIdx.x];
-    const FinalArgs& a = args[pm.x];
+    __shared__ FinalArgs sa;
+    const FinalArgs& a = stage_args(args, pm.x, sa);
     if (*(volatile const int*)&a.info->stop) return;
     gap_final_block(a, pm.y);
 }

@@ -147,7 +147,8 @@ __device__ __forceinline__ void forward_prox_rows(const FwdProxArgs& a, int kb, 
 __global__ void __launch_bounds__(ROW_THREADS) k_forward_prox_b(const FwdProxArgs* __restrict__ args,
                                                                const int2* __restrict__ map) {
     const int2 pm = map[blockIdx.x];
-    const FwdProxArgs& a = args[pm.x];
+    __shared__ FwdProxArgs sa;
+    const FwdProxArgs& a = stage_args(args, pm.x, sa);
     if (a.stop && *(volatile const int*)a.stop) return;
     const int nkb = row_blocks(a.g);
     forward_prox_rows(a, pm.y % nkb, pm.y / nkb);
@@ -193,7 +194,8 @@ __device__ __forceinline__ void forward_gap_rows(const FwdGapArgs& a, int kb, in
 __global__ void __launch_bounds__(ROW_THREADS) k_forward_gap_b(const FwdGapArgs* __restrict__ args,
                                                               const int2* __restrict__ map) {
     const int2 pm = map[blockIdx.x];
-    const FwdGapArgs& a = args[pm.x];
+    __shared__ FwdGapArgs sa;
+    const FwdGapArgs& a = stage_args(args, pm.x, sa);
     if (a.stop && *(volatile const int*)a.stop) return;
     const int nkb = row_blocks(a.g);
     if (a.u_quad)
@@ -348,10 +350,11 @@ __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
 }
 
 template <bool PREMUL>
-__global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles_b(const AdjArgs* __restrict__ args,
+__global__ void __launch_bounds__(ATHREADS, 5) k_adjoint_tiles_b(const AdjArgs* __restrict__ args,
                                                             const int2* __restrict__ map) {
     const int2 pm = map[blockIdx.x];
-    const AdjArgs& a = args[pm.x];
+    __shared__ AdjArgs sa;
+    const AdjArgs& a = stage_args(args, pm.x, sa);
     if (a.stop && *(volatile const int*)a.stop) return;
     adjoint_item<PREMUL>(a, pm.y);
 }
