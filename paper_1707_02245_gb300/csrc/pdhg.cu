@@ -249,8 +249,7 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
 template <int REG>
 __global__ void __launch_bounds__(TX* TY) k_update_b(const UpdateArgs* __restrict__ args, const int2* __restrict__ map) {
     const int2 pm = map[blockIdx.x];
-    __shared__ UpdateArgs sa;
-    const UpdateArgs& a = stage_args(args, pm.x, sa);
+    const UpdateArgs& a = args[pm.x];
     if (a.stop && *(volatile const int*)a.stop) return;
     update_tile<REG>(a, pm.y % a.tiles_x, pm.y / a.tiles_x, pm.y == 0);
 }

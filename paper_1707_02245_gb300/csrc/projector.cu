@@ -73,7 +73,6 @@ __device__ __forceinline__ float circle_partial(const GeomView& g, const float* 
     float acc = 0.f;
     int m = w.x + rl.ph;
     if (m >= g.quad_m) m -= g.quad_m;
-#pragma unroll 2
     for (int j = rl.ph; j < w.y; j += NPH) {
         const float2 cs = __ldg(&g.cs[m]);
         m += NPH;
@@ -350,7 +349,7 @@ __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
 }
 
 template <bool PREMUL>
-__global__ void __launch_bounds__(ATHREADS, 5) k_adjoint_tiles_b(const AdjArgs* __restrict__ args,
+__global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles_b(const AdjArgs* __restrict__ args,
                                                             const int2* __restrict__ map) {
     const int2 pm = map[blockIdx.x];
     __shared__ AdjArgs sa;
