@@ -352,8 +352,7 @@ template <bool PREMUL>
 __global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles_b(const AdjArgs* __restrict__ args,
                                                             const int2* __restrict__ map) {
     const int2 pm = map[blockIdx.x];
-    __shared__ AdjArgs sa;
-    const AdjArgs& a = stage_args(args, pm.x, sa);
+    const AdjArgs& a = args[pm.x];   // (a shared copy would be reloaded after every shared atomic)
     if (a.stop && *(volatile const int*)a.stop) return;
     adjoint_item<PREMUL>(a, pm.y);
 }
