@@ -34,7 +34,14 @@ EXPORTED = [
     "pat_direction_field", "pat_params_default", "pat_reconstruct", "pat_reconstruct_batched",
     "pat_steps", "pat_duality_gap", "pat_error_string", "pat_last_error", "pat_geometry_info",
     "pat_profile_enable", "pat_profile_read", "pat_kernel_launches", "pat_adjoint_noalloc",
+    # learned warm start (include/pat_unet.h)
+    "pat_conv3x3_forward", "pat_conv3x3_backward_data", "pat_conv3x3_backward_weight",
+    "pat_unet_create", "pat_unet_destroy", "pat_unet_num_params", "pat_unet_get_params",
+    "pat_unet_set_params", "pat_unet_forward", "pat_unet_backward", "pat_unet_train_step",
+    "pat_warm_start_features", "pat_warm_start_state", "pat_warm_start_target", "pat_warm_start",
 ]
+PAT_WARM_CHANNELS = 8
+PAT_WARM_V_SCALE = 10.0
 PHASES = ["forward_prox", "adj_clear", "adjoint", "update", "gap"]
 
 
@@ -59,6 +66,11 @@ class pat_params(ctypes.Structure):
                 ("x0_dev", ctypes.c_void_p), ("xbar0_dev", ctypes.c_void_p), ("y0_dev", ctypes.c_void_p),
                 ("x_out_dev", ctypes.c_void_p), ("xbar_out_dev", ctypes.c_void_p),
                 ("y_out_dev", ctypes.c_void_p)]
+
+
+class pat_unet_desc(ctypes.Structure):
+    _fields_ = [("in_ch", ctypes.c_int), ("out_ch", ctypes.c_int), ("base_ch", ctypes.c_int),
+                ("levels", ctypes.c_int), ("seed", ctypes.c_ulonglong)]
 
 
 class pat_info(ctypes.Structure):
@@ -106,6 +118,21 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pat_profile_enable": (i, [i]),
         "pat_profile_read": (i, [ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong), i]),
         "pat_kernel_launches": (ctypes.c_longlong, []),
+        "pat_conv3x3_forward": (i, [vp, i, i, i, i, vp, vp, i, i, vp, vp]),
+        "pat_conv3x3_backward_data": (i, [vp, i, i, i, i, vp, i, vp, vp]),
+        "pat_conv3x3_backward_weight": (i, [vp, vp, i, i, i, i, i, vp, vp, vp]),
+        "pat_unet_create": (i, [ctypes.POINTER(pat_unet_desc), ctypes.POINTER(vp)]),
+        "pat_unet_destroy": (None, [vp]),
+        "pat_unet_num_params": (ctypes.c_longlong, [vp]),
+        "pat_unet_get_params": (i, [vp, vp]),
+        "pat_unet_set_params": (i, [vp, vp]),
+        "pat_unet_forward": (i, [vp, vp, i, i, i, vp, vp]),
+        "pat_unet_backward": (i, [vp, vp, vp, vp]),
+        "pat_unet_train_step": (i, [vp, vp, vp, ctypes.POINTER(ctypes.c_float), i, i, i, ctypes.c_float, vp, vp]),
+        "pat_warm_start_features": (i, [vp, vp, vp, i, vp]),
+        "pat_warm_start_state": (i, [vp, vp, i, ctypes.POINTER(pat_params), vp, vp, vp, vp]),
+        "pat_warm_start_target": (i, [vp, vp, vp, ctypes.POINTER(pat_params), vp, i, vp]),
+        "pat_warm_start": (i, [vp, vp, vp, ctypes.POINTER(pat_params), vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -253,6 +280,87 @@ def pat_profile_read(reset: bool = False) -> dict:
 
 def pat_kernel_launches() -> int:
     return int(load().pat_kernel_launches())
+
+
+# ---- learned warm start (include/pat_unet.h) -------------------------------------
+# bfloat16 tensors are passed by pointer (their 16-bit patterns); torch.bfloat16 CUDA
+# tensors work as they are.
+
+def pat_conv3x3_forward(x_dev, batch, h, w, cin, w_dev, bias_dev, cout, relu, y_dev, stream=None) -> None:
+    _check(load().pat_conv3x3_forward(_ptr(x_dev), batch, h, w, cin, _ptr(w_dev), _ptr(bias_dev), cout,
+                                      1 if relu else 0, _ptr(y_dev), _stream(stream)), "pat_conv3x3_forward")
+
+
+def pat_conv3x3_backward_data(dy_dev, batch, h, w, cout, w_dev, cin, dx_dev, stream=None) -> None:
+    _check(load().pat_conv3x3_backward_data(_ptr(dy_dev), batch, h, w, cout, _ptr(w_dev), cin, _ptr(dx_dev),
+                                            _stream(stream)), "pat_conv3x3_backward_data")
+
+
+def pat_conv3x3_backward_weight(x_dev, dy_dev, batch, h, w, cin, cout, dw_dev, db_dev=None, stream=None) -> None:
+    _check(load().pat_conv3x3_backward_weight(_ptr(x_dev), _ptr(dy_dev), batch, h, w, cin, cout, _ptr(dw_dev),
+                                              _ptr(db_dev), _stream(stream)), "pat_conv3x3_backward_weight")
+
+
+def pat_unet_create(in_ch=8, out_ch=8, base_ch=32, levels=4, seed=0) -> int:
+    desc = pat_unet_desc(in_ch=in_ch, out_ch=out_ch, base_ch=base_ch, levels=levels, seed=seed)
+    out = ctypes.c_void_p()
+    _check(load().pat_unet_create(ctypes.byref(desc), ctypes.byref(out)), "pat_unet_create")
+    return out.value
+
+
+def pat_unet_destroy(net: int) -> None:
+    load().pat_unet_destroy(net)
+
+
+def pat_unet_num_params(net: int) -> int:
+    return int(load().pat_unet_num_params(net))
+
+
+def pat_unet_get_params(net: int) -> np.ndarray:
+    out = np.empty(pat_unet_num_params(net), dtype=np.float32)
+    _check(load().pat_unet_get_params(net, out.ctypes.data), "pat_unet_get_params")
+    return out
+
+
+def pat_unet_set_params(net: int, params) -> None:
+    a = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+    if a.size != pat_unet_num_params(net):
+        raise ValueError("pat_unet_set_params: wrong number of parameters")
+    _check(load().pat_unet_set_params(net, a.ctypes.data), "pat_unet_set_params")
+
+
+def pat_unet_forward(net: int, x_dev, batch, h, w, y_dev, stream=None) -> None:
+    _check(load().pat_unet_forward(net, _ptr(x_dev), batch, h, w, _ptr(y_dev), _stream(stream)), "pat_unet_forward")
+
+
+def pat_unet_backward(net: int, dy_dev, grad_dev, stream=None) -> None:
+    _check(load().pat_unet_backward(net, _ptr(dy_dev), _ptr(grad_dev), _stream(stream)), "pat_unet_backward")
+
+
+def pat_unet_train_step(net: int, x_dev, target_dev, ch_weight, batch, h, w, lr, loss_dev=None, stream=None) -> None:
+    cw = (ctypes.c_float * len(ch_weight))(*[float(v) for v in ch_weight])
+    _check(load().pat_unet_train_step(net, _ptr(x_dev), _ptr(target_dev), cw, batch, h, w, float(lr), _ptr(loss_dev),
+                                      _stream(stream)), "pat_unet_train_step")
+
+
+def pat_warm_start_features(g: int, f_dev, x_dev, in_ch=8, stream=None) -> None:
+    _check(load().pat_warm_start_features(g, _ptr(f_dev), _ptr(x_dev), in_ch, _stream(stream)),
+           "pat_warm_start_features")
+
+
+def pat_warm_start_state(g: int, pred_dev, out_ch, params: pat_params, f_dev, x0_dev, y0_dev, stream=None) -> None:
+    _check(load().pat_warm_start_state(g, _ptr(pred_dev), out_ch, ctypes.byref(params), _ptr(f_dev), _ptr(x0_dev),
+                                       _ptr(y0_dev), _stream(stream)), "pat_warm_start_state")
+
+
+def pat_warm_start_target(g: int, x_dev, y_dev, params: pat_params, target_dev, out_ch=8, stream=None) -> None:
+    _check(load().pat_warm_start_target(g, _ptr(x_dev), _ptr(y_dev), ctypes.byref(params), _ptr(target_dev), out_ch,
+                                        _stream(stream)), "pat_warm_start_target")
+
+
+def pat_warm_start(g: int, net: int, f_dev, params: pat_params, x0_dev, y0_dev, stream=None) -> None:
+    _check(load().pat_warm_start(g, net, _ptr(f_dev), ctypes.byref(params), _ptr(x0_dev), _ptr(y0_dev),
+                                 _stream(stream)), "pat_warm_start")
 
 
 # ---- a small owner of a geometry handle -----------------------------------------

@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIBNAME = "libpat_pdhg.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["geometry.cu", "projector.cu", "pdhg.cu", "noalloc.cu"]
+SOURCES = ["geometry.cu", "projector.cu", "pdhg.cu", "noalloc.cu", "conv.cu", "unet.cu"]
 
 
 def nvcc() -> str:
@@ -49,7 +49,7 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(INCLUDE, "pat.h"))
+    headers += [os.path.join(INCLUDE, h) for h in ("pat.h", "pat_unet.h")]
     flags = common_flags() + (extra or [])
     objs = []
     jobs = []

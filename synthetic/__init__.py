@@ -360,3 +360,22 @@ def workload_batch(seed: int = 0, count: int = 64) -> list[dict]:
             w["eta"] = 0.01 * float(side.max() - side.min())
         out.append(w)
     return out
+
+
+def workload_warm(seed: int, n: int = 256, n_det: int = 128, n_t: int | None = None, quad_m: int = 256) -> dict:
+    """One problem of the learned-warm-start set: an n^2 vessel tree with exp(-3 depth)
+    fluence, ``n_det`` detectors on a full circle of radius 1.2, T = 2n time samples by
+    default, noise level U[1%, 10%] drawn from the seed, TGV alpha 0.02, beta 0.04.
+    Same keys as ``workload``; seeds index the set (training and held-out seeds are
+    disjoint ranges chosen by the caller)."""
+    g = _rng(seed + 90001)
+    level = float(g.uniform(0.01, 0.10))
+    n_t = n_t or 2 * n
+    det = detectors_full_circle(n_det, 1.2)
+    r0, dr = radial_sampling(det, n_t)
+    ph = vessel_phantom(n, seed, supersample=2, n_ref=max(n, 64))
+    ph_f = vessel_phantom(2 * n, seed, n_ref=max(n, 64), supersample=2)
+    return dict(name=f"warm{seed}", seed=seed, n=n, det_xy=det, n_t=n_t, r0=r0, dr=dr, quad_m=quad_m,
+                n_fine=2 * n, quad_m_fine=2 * quad_m, phantom=ph, phantom_fine=ph_f,
+                noise=standard_normal((n_det, n_t), seed + 17), noise_level=level,
+                reg=1, alpha=0.02, beta=0.04, gamma=0.95, iters=1000)

@@ -1,5 +1,5 @@
 """Host-side checks of the C ABI: the in-tree library builds for sm_103a, loads, exports
-every function include/pat.h declares, and reports errors without a GPU call."""
+every function include/*.h declares, and reports errors without a GPU call."""
 import os
 import re
 import subprocess
@@ -13,9 +13,13 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def _declared():
-    txt = open(os.path.join(ROOT, "include", "pat.h")).read()
-    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
-    return sorted(set(re.findall(r"\b(pat_[a-z_0-9]+)\s*\(", txt)))
+    names = set()
+    inc = os.path.join(ROOT, "include")
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            txt = re.sub(r"/\*.*?\*/", "", open(os.path.join(inc, h)).read(), flags=re.S)
+            names |= set(re.findall(r"\b(pat_[a-z_0-9]+)\s*\(", txt))
+    return sorted(names)
 
 
 @pytest.fixture(scope="module")
@@ -77,3 +81,18 @@ def test_nvcc_targets_sm103a_only():
     flags = B.common_flags()
     assert "arch=compute_103a,code=sm_103a" in flags
     assert not any("sm_90" in f or "sm_100" in f for f in flags)
+
+
+def test_unet_arguments_rejected_before_any_device_call(lib):
+    for bad in [dict(in_ch=3), dict(out_ch=0), dict(base_ch=12), dict(levels=0), dict(levels=9)]:
+        kw = dict(in_ch=8, out_ch=8, base_ch=8, levels=2)
+        kw.update(bad)
+        with pytest.raises(P.PatError) as ei:
+            P.pat_unet_create(**kw)
+        assert ei.value.code == P.PAT_ERR_INVALID_ARG
+    with pytest.raises(P.PatError) as ei:
+        P.pat_conv3x3_forward(16, 1, 4, 4, 3, 16, None, 8, False, 16)
+    assert ei.value.code == P.PAT_ERR_INVALID_ARG
+    with pytest.raises(P.PatError) as ei:
+        P.pat_conv3x3_backward_weight(16, 16, 1, 4, 4, 8, 12, 16)
+    assert ei.value.code == P.PAT_ERR_INVALID_ARG
