@@ -110,7 +110,18 @@ typedef struct {
     float* x_out_dev;
     float* xbar_out_dev;
     float* y_out_dev;
+    /* primal-dual balance s > 0 of the diagonal steps: every primal step tau_j becomes
+       s tau_j and every dual step sigma_i becomes sigma_i / s.  This leaves
+       ||Sigma^1/2 A T^1/2|| and so the convergence condition of Sec. 3.3.2 unchanged.
+       Default 1. */
+    double step_ratio;
+    /* PAT_ADAPT_NONE keeps s fixed.  PAT_ADAPT_BALANCE re-balances s at every gap
+       evaluation from the two parts of the duality gap (see pat_reconstruct). */
+    int    adapt;
 } pat_params;
+
+#define PAT_ADAPT_NONE     0
+#define PAT_ADAPT_BALANCE  1
 
 typedef struct {
     int    iters_done;   /* iterations run                                                */

@@ -439,6 +439,16 @@ def diag_steps(pb: Problem) -> Steps:
     return Steps(sig_q=sig_q, sig_r=sig_r, tau_u=tau_u, sig_s=sig_s, tau_v=tau_v)
 
 
+def balanced_steps(st: Steps, ratio: float) -> Steps:
+    """The primal-dual balance of a step choice: every primal step times ``ratio`` and
+    every dual step divided by it.  ||Sigma^1/2 A T^1/2|| is unchanged, so the
+    convergence condition of Sec. 3.3.2 still holds."""
+    def sc(a, m):
+        return None if a is None else np.asarray(a, dtype=np.float64) * m
+    return Steps(sig_q=sc(st.sig_q, 1.0 / ratio), sig_r=sc(st.sig_r, 1.0 / ratio), tau_u=sc(st.tau_u, ratio),
+                 sig_s=sc(st.sig_s, 1.0 / ratio), tau_v=sc(st.tau_v, ratio))
+
+
 def power_norm(apply, apply_t, x0, iters: int) -> float:
     """Largest singular value by power iteration on apply_t(apply(.)) from x0."""
     x = np.asarray(x0, dtype=np.float64)

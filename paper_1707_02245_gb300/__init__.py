@@ -28,6 +28,7 @@ PAT_ERR_TIMEOUT = -5
 PAT_TV, PAT_TGV, PAT_DTV = 0, 1, 2
 PAT_PRECOND_DIAG, PAT_PRECOND_SCALAR2 = 0, 1
 PAT_STATUS_CONVERGED, PAT_STATUS_MAXITER, PAT_STATUS_DIVERGED = 0, 1, 2
+PAT_ADAPT_NONE, PAT_ADAPT_BALANCE = 0, 1
 
 EXPORTED = [
     "pat_create_geometry", "pat_destroy_geometry", "pat_forward", "pat_adjoint",
@@ -65,7 +66,7 @@ class pat_params(ctypes.Structure):
                 ("theta", ctypes.c_double), ("box_u", ctypes.c_double), ("box_v", ctypes.c_double),
                 ("x0_dev", ctypes.c_void_p), ("xbar0_dev", ctypes.c_void_p), ("y0_dev", ctypes.c_void_p),
                 ("x_out_dev", ctypes.c_void_p), ("xbar_out_dev", ctypes.c_void_p),
-                ("y_out_dev", ctypes.c_void_p)]
+                ("y_out_dev", ctypes.c_void_p), ("step_ratio", ctypes.c_double), ("adapt", ctypes.c_int)]
 
 
 class pat_unet_desc(ctypes.Structure):
@@ -208,7 +209,7 @@ def pat_params_default() -> pat_params:
 
 def make_params(reg=PAT_TV, alpha=0.05, beta=1.0, gamma=0.95, xi=None, iters=100, tol=0.0, gap_every=10,
                 precond=PAT_PRECOND_DIAG, theta=1.0, box_u=2.0, box_v=4.0, x0=None, xbar0=None, y0=None,
-                x_out=None, xbar_out=None, y_out=None) -> pat_params:
+                x_out=None, xbar_out=None, y_out=None, step_ratio=1.0, adapt=PAT_ADAPT_NONE) -> pat_params:
     p = pat_params_default()
     p.reg, p.alpha, p.beta, p.gamma = reg, alpha, beta, gamma
     p.xi_dev = _ptr(xi)
@@ -216,6 +217,7 @@ def make_params(reg=PAT_TV, alpha=0.05, beta=1.0, gamma=0.95, xi=None, iters=100
     p.theta, p.box_u, p.box_v = theta, box_u, box_v
     p.x0_dev, p.xbar0_dev, p.y0_dev = _ptr(x0), _ptr(xbar0), _ptr(y0)
     p.x_out_dev, p.xbar_out_dev, p.y_out_dev = _ptr(x_out), _ptr(xbar_out), _ptr(y_out)
+    p.step_ratio, p.adapt = step_ratio, adapt
     # keep the buffers alive as long as the parameter block that points at them
     p._keep = [xi, x0, xbar0, y0, x_out, xbar_out, y_out]
     return p

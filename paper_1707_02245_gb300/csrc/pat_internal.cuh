@@ -176,6 +176,7 @@ struct FwdProxArgs {   // q <- prox(q + Sigma_q K ubar); also q*w and max|q|
     const float* f;
     const float* sig_q;   // NULL: sig_scalar
     float sig_scalar;
+    const float* step_mul; // {tau multiplier s, sigma multiplier 1/s} (device) or NULL
     float* qw;
     unsigned* qmax_bits;
     const int* stop;
@@ -206,7 +207,8 @@ struct AdjArgs {       // fixed-point K^T y, one work item per block
 };
 
 FwdProxArgs make_fwd_prox_args(const pat_geometry* g, const float4* ubar_quad, float* q, const float* f,
-                               const float* sig_q, float sig_scalar, float* qw, unsigned* qmax_bits, const int* stop);
+                               const float* sig_q, float sig_scalar, const float* step_mul, float* qw,
+                               unsigned* qmax_bits, const int* stop);
 FwdGapArgs make_fwd_gap_args(const pat_geometry* g, const float* u, const float4* u_quad, const float* q,
                              const float* f, double* partials, const int* stop);
 AdjArgs make_adj_args(const pat_geometry* g, const float* y, const float* premul, const unsigned* ymax_bits, int* acc,

@@ -37,6 +37,7 @@ struct UpdateArgs {
     const float* tau_u;    // N*N (diagonal rule)
     const float* sig_r;    // N*N (dTV diagonal rule)
     const float* xi;       // 2*N*N (dTV)
+    const float* step_mul; // {s, 1/s}: multipliers of every primal and dual step (device)
     KtView kt;             // K^T q of this iteration (fixed point)
     int* kt_clear;         // the other fixed-point buffer, cleared here for the next iteration
     unsigned* qmax_next;   // max |q| slot of the next iteration, reset here
@@ -82,6 +83,7 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
     const float* u_in = a.x_in;
     const float* r1_in = a.y_in;
     const float* r2_in = a.y_in + NN;
+    const float tmul = __ldg(a.step_mul), smul = __ldg(a.step_mul + 1);
 
     // ---- stage 1: dual fields on the tile plus halo -------------------------------
     for (int c = tid; c < LX * LY; c += TX * TY) {
@@ -120,7 +122,7 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
                 const float divr = s_r1m[ly][lx] - s_r1m[ly][lx - 1] + s_r2m[ly][lx] - s_r2m[ly - 1][lx];
                 const float w = a.kt.at(gx, gy, N);
                 const float uo = __ldg(u_in + gi), uol = __ldg(a.xl_in + gi);
-                const float tu = a.tau >= 0.f ? a.tau : __ldg(a.tau_u + gi);
+                const float tu = (a.tau >= 0.f ? a.tau : __ldg(a.tau_u + gi)) * tmul;
                 float un = uo, unl = uol;
                 add_compensated(un, unl, -tu * (w - divr));
                 ub = fmaf(a.theta, (un - uo) + (unl - uol), un + unl);
@@ -148,8 +150,8 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
                 const float r1 = __ldg(r1_in + gi), r2 = __ldg(r2_in + gi);
                 const float v1o = __ldg(a.x_in + NN + gi), v2o = __ldg(a.x_in + 2 * NN + gi);
                 const float v1ol = __ldg(a.xl_in + NN + gi), v2ol = __ldg(a.xl_in + 2 * NN + gi);
-                const float t1 = a.tau >= 0.f ? a.tau : tau_v1_tgv(gx, gy, N);
-                const float t2 = a.tau >= 0.f ? a.tau : tau_v2_tgv(gx, gy, N);
+                const float t1 = (a.tau >= 0.f ? a.tau : tau_v1_tgv(gx, gy, N)) * tmul;
+                const float t2 = (a.tau >= 0.f ? a.tau : tau_v2_tgv(gx, gy, N)) * tmul;
                 float v1n = v1o, v1nl = v1ol, v2n = v2o, v2nl = v2ol;
                 add_compensated(v1n, v1nl, -t1 * (et1 - r1));
                 add_compensated(v2n, v2nl, -t2 * (et2 - r2));
@@ -179,17 +181,17 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
         const float gu1 = by ? s_ub[ly + 1][lx] - ub : 0.f;
         float r1 = __ldg(r1_in + gi), r2 = __ldg(r2_in + gi);
         if (REG == PAT_TV) {
-            const float sr = a.sig2 >= 0.f ? a.sig2 : sig_r_tv(gx, gy, N);
+            const float sr = (a.sig2 >= 0.f ? a.sig2 : sig_r_tv(gx, gy, N)) * smul;
             r1 = fmaf(sr, gu0, r1);
             r2 = fmaf(sr, gu1, r2);
         } else if (REG == PAT_DTV) {
-            const float sr = a.sig2 >= 0.f ? a.sig2 : __ldg(a.sig_r + gi);
+            const float sr = (a.sig2 >= 0.f ? a.sig2 : __ldg(a.sig_r + gi)) * smul;
             float o0, o1;
             dxi_apply(__ldg(a.xi + gi), __ldg(a.xi + NN + gi), a.gamma, gu0, gu1, o0, o1);
             r1 = fmaf(sr, o0, r1);
             r2 = fmaf(sr, o1, r2);
         } else {
-            const float sr = a.sig2 >= 0.f ? a.sig2 : sig_r_tgv(gx, gy, N);
+            const float sr = (a.sig2 >= 0.f ? a.sig2 : sig_r_tgv(gx, gy, N)) * smul;
             r1 = fmaf(sr, gu0 - s_vb1[ly][lx], r1);
             r2 = fmaf(sr, gu1 - s_vb2[ly][lx], r2);
         }
@@ -225,7 +227,7 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
             const float e11 = v1 - v1l;
             const float e22 = v2 - v2d;
             const float e12 = ((v1y - v1d) + (v2x - v2l)) * kInvSqrt2f;
-            const float ss = a.sig2 >= 0.f ? a.sig2 : sig_s_tgv(gx, gy, N);
+            const float ss = (a.sig2 >= 0.f ? a.sig2 : sig_s_tgv(gx, gy, N)) * smul;
             float s11 = fmaf(ss, e11, s_s11[ly][lx]);
             float s22 = fmaf(ss, e22, s_s22[ly][lx]);
             float s12 = fmaf(ss, e12, s_s12[ly][lx]);
@@ -259,6 +261,7 @@ __global__ void __launch_bounds__(TX* TY) k_update_b(const UpdateArgs* __restric
 struct DualArgs {
     int n;
     float alpha, ab, gamma, sig2;
+    float smul;            // dual step multiplier 1/s
     const float* sig_r;
     const float* xi;
     const float* ubar_pad;
@@ -281,17 +284,17 @@ __global__ void k_dual_step(DualArgs a) {
     const float gu1 = by ? a.ubar_pad[(gy + 2) * P + gx + 1] - ub : 0.f;
     float r1 = a.y_in[gi], r2 = a.y_in[NN + gi];
     if (REG == PAT_TV) {
-        const float sr = a.sig2 >= 0.f ? a.sig2 : sig_r_tv(gx, gy, N);
+        const float sr = (a.sig2 >= 0.f ? a.sig2 : sig_r_tv(gx, gy, N)) * a.smul;
         r1 = fmaf(sr, gu0, r1);
         r2 = fmaf(sr, gu1, r2);
     } else if (REG == PAT_DTV) {
-        const float sr = a.sig2 >= 0.f ? a.sig2 : a.sig_r[gi];
+        const float sr = (a.sig2 >= 0.f ? a.sig2 : a.sig_r[gi]) * a.smul;
         float o0, o1;
         dxi_apply(a.xi[gi], a.xi[NN + gi], a.gamma, gu0, gu1, o0, o1);
         r1 = fmaf(sr, o0, r1);
         r2 = fmaf(sr, o1, r2);
     } else {
-        const float sr = a.sig2 >= 0.f ? a.sig2 : sig_r_tgv(gx, gy, N);
+        const float sr = (a.sig2 >= 0.f ? a.sig2 : sig_r_tgv(gx, gy, N)) * a.smul;
         r1 = fmaf(sr, gu0 - a.vbar[gi], r1);
         r2 = fmaf(sr, gu1 - a.vbar[NN + gi], r2);
     }
@@ -306,7 +309,7 @@ __global__ void k_dual_step(DualArgs a) {
         const float v1y = by ? vb(0, gx, gy) : 0.f, v1d = bym ? vb(0, gx, gy - 1) : 0.f;
         const float v2x = ax ? vb(1, gx, gy) : 0.f, v2l = axm ? vb(1, gx - 1, gy) : 0.f;
         const float e11 = v1 - v1l, e22 = v2 - v2d, e12 = ((v1y - v1d) + (v2x - v2l)) * kInvSqrt2f;
-        const float ss = a.sig2 >= 0.f ? a.sig2 : sig_s_tgv(gx, gy, N);
+        const float ss = (a.sig2 >= 0.f ? a.sig2 : sig_s_tgv(gx, gy, N)) * a.smul;
         float s11 = fmaf(ss, e11, a.y_in[2 * NN + gi]);
         float s22 = fmaf(ss, e22, a.y_in[3 * NN + gi]);
         float s12 = fmaf(ss, e12, a.y_in[4 * NN + gi]);
@@ -428,6 +431,7 @@ struct InfoDev {
     int iters_done, status, stop, iter;
     unsigned qmax_bits[2];  // max |q| of iterations of each parity (float bits)
     unsigned final_ticket;  // blocks of k_gap_final done (the last one resets it)
+    float step_mul[2];      // {s, 1/s}: primal and dual step multipliers
     double level2[GAP_FINAL_BLOCKS][9];
 };
 
@@ -573,6 +577,11 @@ __global__ void k_steps_pixels(StepArgs a) {
             a.tau_v[NN + gi] = (float)(1.0 / (1 + 2 * B + kSqrt2 * A));
         }
     }
+}
+
+__global__ void k_scale_f32(float* __restrict__ a, long long n, float m) {
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) a[i] *= m;
 }
 
 __global__ void k_sig_q(const float* __restrict__ krow, float* __restrict__ sig_q, long long S) {
@@ -739,8 +748,13 @@ static int validate(const pat_geometry* g, const pat_params* p, const char* who)
     if (p->precond != PAT_PRECOND_DIAG && p->precond != PAT_PRECOND_SCALAR2) return bad("unknown precond");
     if (!(p->theta >= 0) || !(p->theta <= 1)) return bad("theta must be in [0, 1]");
     if (!(p->box_u > 0) || !(p->box_v > 0)) return bad("box half-widths must be > 0");
+    if (!(p->step_ratio >= 0) || !std::isfinite(p->step_ratio)) return bad("step_ratio must be finite and >= 0");
+    if (p->adapt != PAT_ADAPT_NONE && p->adapt != PAT_ADAPT_BALANCE) return bad("unknown adapt mode");
     return PAT_OK;
 }
+
+// s of the primal-dual balance; 0 (a zero-initialised struct) means the default 1.
+static double step_ratio_of(const pat_params* p) { return p->step_ratio > 0 ? p->step_ratio : 1.0; }
 
 struct ScalarSteps {
     float sig_q = -1.f, sig2 = -1.f, tau = -1.f;
@@ -859,6 +873,7 @@ static UpdateArgs make_update_args(const Prob& pr, int par, bool gap_iter) {
     a.tau_u = ws.tau_u;
     a.sig_r = ws.sig_r;
     a.xi = p->xi_dev;
+    a.step_mul = ws.info->step_mul;
     a.kt = kt_view(pr.g, ws.kt[par], &ws.info->qmax_bits[par]);
     a.kt_clear = ws.kt[1 - par];
     a.qmax_next = &ws.info->qmax_bits[1 - par];
@@ -933,7 +948,8 @@ static void build_iter_plan(const Prob* pr, int B, Arena& ar, IterPlan& ip) {
             const Prob& q = pr[b];
             const Workspace& ws = q.ws;
             fw.push_back(make_fwd_prox_args(q.g, ws.ubar_quad, ws.q, q.f, q.sc.sig_q >= 0 ? nullptr : ws.sig_q,
-                                            q.sc.sig_q, ws.qw, &ws.info->qmax_bits[par], &ws.info->stop));
+                                            q.sc.sig_q, ws.info->step_mul, ws.qw, &ws.info->qmax_bits[par],
+                                            &ws.info->stop));
             ad.push_back(make_adj_args(q.g, ws.q, ws.qw, &ws.info->qmax_bits[par], ws.kt[par], &ws.info->stop));
             u0.push_back(make_update_args(q, par, false));
             u1.push_back(make_update_args(q, par, true));
@@ -1022,6 +1038,9 @@ static int init_problem(Prob& pr, cudaStream_t st) {
         PAT_CUDA(cudaMemsetAsync(ws.Y[1], 0, ny * 4, st));
     }
     PAT_CUDA(cudaMemsetAsync(ws.info, 0, sizeof(InfoDev), st));
+    const double ratio = step_ratio_of(p);
+    const float mul[2] = {(float)ratio, (float)(1.0 / ratio)};
+    PAT_CUDA(cudaMemcpyAsync(ws.info->step_mul, mul, sizeof mul, cudaMemcpyHostToDevice, st));
     PAT_CUDA(cudaMemsetAsync(ws.kt[0], 0, 2 * NN * sizeof(int), st));
     PAT_CUDA(cudaMemsetAsync(ws.XL[0], 0, nx * sizeof(float), st));
     const float* xb = p->xbar0_dev ? p->xbar0_dev : p->x0_dev;
@@ -1038,7 +1057,7 @@ static int init_problem(Prob& pr, cudaStream_t st) {
             PAT_CUDA(cudaMemsetAsync(ws.vbar0, 0, 2 * NN * 4, st));
     }
     // dual prologue: (r^1, s^1) from (r^0, s^0) and (ubar^0, vbar^0) into Y[0]
-    DualArgs da{N, (float)p->alpha, (float)(p->alpha * p->beta), (float)p->gamma, pr.sc.sig2, ws.sig_r,
+    DualArgs da{N, (float)p->alpha, (float)(p->alpha * p->beta), (float)p->gamma, pr.sc.sig2, mul[1], ws.sig_r,
                 p->xi_dev, ws.ubar_pad, ws.vbar0, ws.Y[1], ws.Y[0]};
     dim3 g2(ceil_div(N, 32), ceil_div(N, 8));
     if (reg == PAT_TV)
@@ -1371,6 +1390,8 @@ extern "C" void pat_params_default(pat_params* p) {
     p->theta = 1.0;
     p->box_u = 2.0;
     p->box_v = 4.0;
+    p->step_ratio = 1.0;
+    p->adapt = PAT_ADAPT_NONE;
 }
 
 extern "C" int pat_reconstruct(const pat_geometry* g, const float* f_dev, const pat_params* p, float* u_dev,
@@ -1439,12 +1460,13 @@ extern "C" int pat_steps(const pat_geometry* g, const pat_params* p, float* sig_
             PAT_CUDA(cudaStreamSynchronize(st));
             return PAT_OK;
         };
-        if ((rc = fill(sig_q_dev, S, sc.sig_q))) return rc;
-        if ((rc = fill(tau_u_dev, NN, sc.tau))) return rc;
-        if ((rc = fill(sig_r_dev, NN, sc.sig2))) return rc;
+        const double s = step_ratio_of(p);
+        if ((rc = fill(sig_q_dev, S, (float)(sc.sig_q / s)))) return rc;
+        if ((rc = fill(tau_u_dev, NN, (float)(sc.tau * s)))) return rc;
+        if ((rc = fill(sig_r_dev, NN, (float)(sc.sig2 / s)))) return rc;
         if (p->reg == PAT_TGV) {
-            if ((rc = fill(sig_s_dev, NN, sc.sig2))) return rc;
-            if ((rc = fill(tau_v_dev, 2 * NN, sc.tau))) return rc;
+            if ((rc = fill(sig_s_dev, NN, (float)(sc.sig2 / s)))) return rc;
+            if ((rc = fill(tau_v_dev, 2 * NN, (float)(sc.tau * s)))) return rc;
         }
         return PAT_OK;
     }
@@ -1459,6 +1481,22 @@ extern "C" int pat_steps(const pat_geometry* g, const pat_params* p, float* sig_
     dim3 blk(32, 8), grd(ceil_div(N, 32), ceil_div(N, 8));
     k_steps_pixels<<<grd, blk, 0, st>>>(sa);
     PAT_LAUNCH_CHECK("k_steps_pixels");
+    const double s = step_ratio_of(p);
+    if (s != 1.0) {
+        auto scale = [&](float* a, long long n, double m) -> int {
+            if (!a) return PAT_OK;
+            k_scale_f32<<<ceil_div(n, 256), 256, 0, st>>>(a, n, (float)m);
+            PAT_LAUNCH_CHECK("k_scale_f32");
+            return PAT_OK;
+        };
+        if ((rc = scale(sig_q_dev, S, 1.0 / s))) return rc;
+        if ((rc = scale(tau_u_dev, NN, s))) return rc;
+        if ((rc = scale(sig_r_dev, NN, 1.0 / s))) return rc;
+        if (p->reg == PAT_TGV) {
+            if ((rc = scale(sig_s_dev, NN, 1.0 / s))) return rc;
+            if ((rc = scale(tau_v_dev, 2 * NN, s))) return rc;
+        }
+    }
     return PAT_OK;
 }
 

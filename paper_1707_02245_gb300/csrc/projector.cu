@@ -123,7 +123,7 @@ __device__ __forceinline__ void forward_prox_rows(const FwdProxArgs& a, int kb, 
         const size_t i = (size_t)rl.d * g.n_t + rl.k;
         const float wk = __ldg(&g.wk[rl.k]);
         const float ku = s * wk;
-        const float sg = a.sig_q ? a.sig_q[i] : a.sig_scalar;
+        const float sg = (a.sig_q ? a.sig_q[i] : a.sig_scalar) * (a.step_mul ? a.step_mul[1] : 1.f);
         const float qn = (a.q[i] + sg * (ku - a.f[i])) / (1.f + sg);
         a.q[i] = qn;
         a.qw[i] = qn * wk;
@@ -443,7 +443,8 @@ int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y,
 }
 
 FwdProxArgs make_fwd_prox_args(const pat_geometry* g, const float4* ubar_quad, float* q, const float* f,
-                               const float* sig_q, float sig_scalar, float* qw, unsigned* qmax_bits, const int* stop) {
+                               const float* sig_q, float sig_scalar, const float* step_mul, float* qw,
+                               unsigned* qmax_bits, const int* stop) {
     FwdProxArgs a;
     a.g = g->view;
     a.ubar_quad = ubar_quad;
@@ -451,6 +452,7 @@ FwdProxArgs make_fwd_prox_args(const pat_geometry* g, const float4* ubar_quad, f
     a.f = f;
     a.sig_q = sig_q;
     a.sig_scalar = sig_scalar;
+    a.step_mul = step_mul;
     a.qw = qw;
     a.qmax_bits = qmax_bits;
     a.stop = stop;

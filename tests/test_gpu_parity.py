@@ -225,6 +225,29 @@ def test_fixed_iterations_small(reg):
     assert abs(info["residual"] - ref.residual) <= 1e-2 * ref.residual + 1e-7
 
 
+@pytest.mark.parametrize("reg,ratio", [(0, 0.3), (1, 4.0), (2, 0.5)])
+def test_step_ratio_matches_oracle_balanced_steps(reg, ratio):
+    """tau -> s tau, sigma -> sigma / s on every block (pat_params.step_ratio)."""
+    w = _with_xi(make("small", seed=9, reg=reg, beta=0.5), reg)
+    iters = 60
+    pb = oracle_problem(w)
+    ref = O.pdhg(pb, iters, steps=O.balanced_steps(O.diag_steps(pb), ratio), gap_every=20)
+    pg = P.Geometry(w["n"], w["det_xy"], w["n_t"], w["r0"], w["dr"], w["quad_m"])
+    u_d = torch.empty(w["n"], w["n"], device=DEV)
+    prm = P.make_params(reg=reg, alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"],
+                        xi=dev(w["xi"]) if reg == 2 else None, iters=iters, gap_every=20, step_ratio=ratio)
+    info = P.pat_reconstruct(pg.handle, dev(w["f"]), prm, u_d)
+    assert rel_l2(host(u_d), ref.u) <= 1e-3
+    assert abs(info["gap"] - ref.gap["gap"]) <= 1e-4 * ref.gap["primal"]
+    # the exported steps carry the balance too
+    st = O.balanced_steps(O.diag_steps(pb), ratio)
+    tau = torch.empty(w["n"], w["n"], device=DEV)
+    sq = torch.empty(w["det_xy"].shape[0] * w["n_t"], device=DEV)
+    P.pat_steps(pg.handle, prm, sig_q=sq, tau_u=tau)
+    assert rel_l2(host(tau), st.tau_u) <= 1e-4
+    assert rel_l2(host(sq), st.sig_q) <= 1e-4
+
+
 def test_disc64_tv_200_iterations():
     """The 64^2 TV disc reconstruction after its 200 iterations."""
     w = make("disc64", seed=0)

@@ -449,6 +449,15 @@ def test_diag_preconditioner_norm_bound(reg):
     T = np.concatenate(tau)
     M = np.sqrt(S)[:, None] * A * np.sqrt(T)[None, :]
     assert np.linalg.norm(M, 2) <= 1 + 1e-9
+    # the primal-dual balance leaves the norm unchanged
+    for ratio in (0.1, 7.0):
+        sb = O.balanced_steps(st, ratio)
+        Sb = np.concatenate([sb.sig_q, sb.sig_r.ravel(), sb.sig_r.ravel()] +
+                            ([sb.sig_s.ravel()] * 3 if reg == O.REG_TGV else []))
+        Tb = np.concatenate([sb.tau_u.ravel()] + ([sb.tau_v.ravel()] if reg == O.REG_TGV else []))
+        assert np.allclose(Sb * ratio, S) and np.allclose(Tb / ratio, T)
+        Mb = np.sqrt(Sb)[:, None] * A * np.sqrt(Tb)[None, :]
+        assert abs(np.linalg.norm(Mb, 2) - np.linalg.norm(M, 2)) < 1e-9
     # and it is the Pock-Chambolle choice: rows of |A| sum to 1/sigma where ungrouped
     np.testing.assert_allclose(np.abs(A[:Km.shape[0]]).sum(1)[Km.getnnz(1) > 0],
                                1 / st.sig_q[Km.getnnz(1) > 0], rtol=1e-12)
