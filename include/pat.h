@@ -116,7 +116,14 @@ typedef struct {
        Default 1. */
     double step_ratio;
     /* PAT_ADAPT_NONE keeps s fixed.  PAT_ADAPT_BALANCE re-balances s at every gap
-       evaluation from the two parts of the duality gap (see pat_reconstruct). */
+       evaluation that does not stop the run (residual balancing after Goldstein, Li, Yuan,
+       Esser and Baraniuk 2015).  The gap splits into
+         stationarity = U ||A_u^T y||_1 + V ||A_v^T y||_1 + <x, A^T y>, reduced by larger
+         primal steps, and
+         the Fenchel-Young part = gap - stationarity, reduced by larger dual steps.
+       When the two differ by more than a factor 2, s is multiplied by the square root of
+       their ratio (clamped to [1/2, 2], raised to 0.97^k after k adjustments; s stays in
+       [1e-3, 1e3]). */
     int    adapt;
 } pat_params;
 
@@ -132,6 +139,7 @@ typedef struct {
     double rel_gap;      /* gap / primal                                                  */
     double residual;     /* ||x^{n+1} - x^n|| / ||x^n|| over the primal variables         */
     double ms;           /* device time of the call in milliseconds (CUDA events)         */
+    double step_ratio;   /* the primal-dual balance s at the end (adapt may have moved it) */
 } pat_info;
 
 /* Fills *p with defaults: TV, alpha 0.05, beta 1, gamma 0.95, 100 iterations, tol 0,

@@ -523,11 +523,73 @@ def duality_gap(pb: Problem, u, q, r, v=None, s=None, KTq=None) -> dict:
     else:
         gu = KTq - div(r)
     dual = -f1c - pb.box_u * float(np.sum(np.abs(gu)))
+    # the part of the gap that measures A^T y != 0 (primal stationarity, G = 0):
+    # U ||A_u^T y||_1 + V ||A_v^T y||_1 + <x, A^T y>; the rest is the Fenchel-Young gap
+    # F(Ax) + F^*(y) - <Ax, y> >= 0 of the dual variables
+    stat = pb.box_u * float(np.sum(np.abs(gu))) + float(np.sum(u * gu))
     if pb.reg == REG_TGV:
-        dual -= pb.box_v * float(np.sum(np.abs(sym_grad_adj(s) - r)))
+        gv = sym_grad_adj(s) - r
+        dual -= pb.box_v * float(np.sum(np.abs(gv)))
+        stat += pb.box_v * float(np.sum(np.abs(gv))) + float(np.sum(v * gv))
     gap = primal - dual
-    return {"primal": primal, "dual": dual, "gap": gap,
+    return {"primal": primal, "dual": dual, "gap": gap, "stationarity": stat,
             "rel_gap": gap / primal if primal > 0 else (0.0 if gap == 0 else math.inf)}
+
+
+def _cone_distance(g, p, radius):
+    """Pointwise distance of g from the normal cone of the radius-ball at p (p inside the
+    ball: the cone is {0}; p on the sphere: the ray through p)."""
+    npn = pointwise_norm(p)
+    on = npn >= radius * (1.0 - 1e-6)
+    lam = np.where(on, np.maximum(0.0, np.sum(g * p, axis=0) / np.where(npn > 0, npn, 1.0)), 0.0)
+    return np.sqrt(np.maximum(np.sum(g * g, axis=0) - lam * lam, 0.0))
+
+
+def pd_residuals(pb: Problem, u, q, r, v=None, s=None, KTq=None) -> tuple[float, float]:
+    """Primal and dual residuals of Goldstein, Li, Yuan, Esser and Baraniuk (2015) at a
+    state, in the L1 norm.  Primal: |A^T y|_1 (G = 0, so 0 = A^T y at a solution).  Dual:
+    the distance of A x from dF^*(y): |q - (K u - f)|_1 for the data term, and for the
+    ball-constrained duals the distance of their argument from the normal cone of the
+    ball at r and s."""
+    n = pb.n
+    if KTq is None:
+        KTq = np.asarray(pb.KT(q)).reshape(n, n)
+    rr = dtv_apply(pb.xi, pb.gamma, r) if pb.reg == REG_DTV else r
+    prim = float(np.sum(np.abs(KTq - div(rr))))
+    Ku = np.asarray(pb.K(u)).reshape(-1)
+    dual = float(np.sum(np.abs(np.asarray(q).reshape(-1) - (Ku - pb.f))))
+    g = grad(u)
+    if pb.reg == REG_DTV:
+        g = dtv_apply(pb.xi, pb.gamma, g)
+    if pb.reg == REG_TGV:
+        g = g - v
+        prim += float(np.sum(np.abs(sym_grad_adj(s) - r)))
+        dual += float(np.sum(_cone_distance(sym_grad(v), s, pb.alpha * pb.beta)))
+    dual += float(np.sum(_cone_distance(g, r, pb.alpha)))
+    return prim, dual
+
+
+# Adaptive primal-dual balance (residual balancing after Goldstein et al. 2015): at every
+# gap evaluation, when the primal residual exceeds the dual one by more than BALANCE_DEAD
+# the primal steps grow (s up), when the dual one dominates they shrink.  s moves by the
+# square root of the residual ratio, at most a factor BALANCE_MAX_STEP, with an exponent
+# that decays by BALANCE_DECAY per adjustment so that s settles.
+BALANCE_DEAD = 2.0
+BALANCE_MAX_STEP = 2.0
+BALANCE_DECAY = 0.97
+BALANCE_RANGE = (1e-3, 1e3)
+
+
+def balance_update(ratio: float, primal_res: float, dual_res: float, n_adjust: int) -> tuple[float, int]:
+    """One adaptive-balance decision; returns (new s, new adjustment count)."""
+    if not (primal_res > 0 and dual_res > 0):
+        return ratio, n_adjust
+    rho = primal_res / dual_res
+    if 1.0 / BALANCE_DEAD <= rho <= BALANCE_DEAD:
+        return ratio, n_adjust
+    f = min(max(math.sqrt(rho), 1.0 / BALANCE_MAX_STEP), BALANCE_MAX_STEP)
+    new = ratio * f ** (BALANCE_DECAY ** n_adjust)
+    return min(max(new, BALANCE_RANGE[0]), BALANCE_RANGE[1]), n_adjust + 1
 
 
 def residual(x_new: list, x_old: list) -> float:
@@ -554,13 +616,15 @@ class Result:
     gap: dict = field(default_factory=dict)
     residual: float = math.nan
     history: list = field(default_factory=list)
+    step_ratio: float = 1.0
     ubar: Optional[np.ndarray] = None
     vbar: Optional[np.ndarray] = None
 
 
 def pdhg(pb: Problem, iters: int, steps: Optional[Steps] = None, theta: float = 1.0,
          tol: float = 0.0, gap_every: int = 0, x0: Optional[dict] = None,
-         y0: Optional[dict] = None, xbar0: Optional[dict] = None, final_gap: bool = True) -> Result:
+         y0: Optional[dict] = None, xbar0: Optional[dict] = None, final_gap: bool = True,
+         step_ratio: float = 1.0, adapt: bool = False) -> Result:
     """Preconditioned PDHGM, one iteration per step of Algorithm 1 / Algorithm 2.
 
     Iterates start at zero (the initialisation of Algorithms 1 and 2) unless
@@ -571,7 +635,9 @@ def pdhg(pb: Problem, iters: int, steps: Optional[Steps] = None, theta: float = 
     at the first evaluation with rel_gap <= tol.
     """
     n = pb.n
-    st = steps if steps is not None else diag_steps(pb)
+    st0 = steps if steps is not None else diag_steps(pb)
+    ratio, n_adjust = float(step_ratio), 0
+    st = balanced_steps(st0, ratio)
     tgv = pb.reg == REG_TGV
     u = np.zeros((n, n)) if x0 is None else np.array(x0["u"], dtype=np.float64).reshape(n, n)
     v = None
@@ -589,7 +655,7 @@ def pdhg(pb: Problem, iters: int, steps: Optional[Steps] = None, theta: float = 
     if tgv:
         vbar = v.copy() if xbar0 is None or xbar0.get("v") is None else \
             np.array(xbar0["v"], dtype=np.float64).reshape(2, n, n)
-    out = Result(u=u, v=v, q=q, r=r, s=s, iters_done=0)
+    out = Result(u=u, v=v, q=q, r=r, s=s, iters_done=0, step_ratio=ratio)
     for it in range(iters):
         # dual steps
         q = prox_f1_conj(q + st.sig_q * np.asarray(pb.K(ubar)).reshape(-1), st.sig_q, pb.f)
@@ -623,6 +689,11 @@ def pdhg(pb: Problem, iters: int, steps: Optional[Steps] = None, theta: float = 
             res = residual([u] + ([v] if tgv else []), x_old)
             out.history.append((done, gp["gap"], gp["rel_gap"], res))
             out.gap, out.residual = gp, res
+            if adapt:
+                pres, dres = pd_residuals(pb, u, q, r, v, s, KTq=KTq)
+                ratio, n_adjust = balance_update(ratio, pres, dres, n_adjust)
+                st = balanced_steps(st0, ratio)
+                out.step_ratio = ratio
             if tol > 0 and gp["rel_gap"] <= tol:
                 out.u, out.v, out.q, out.r, out.s, out.iters_done = u, v, q, r, s, done
                 out.ubar, out.vbar = ubar, vbar

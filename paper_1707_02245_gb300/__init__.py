@@ -77,7 +77,7 @@ class pat_unet_desc(ctypes.Structure):
 class pat_info(ctypes.Structure):
     _fields_ = [("iters_done", ctypes.c_int), ("status", ctypes.c_int), ("primal", ctypes.c_double),
                 ("dual", ctypes.c_double), ("gap", ctypes.c_double), ("rel_gap", ctypes.c_double),
-                ("residual", ctypes.c_double), ("ms", ctypes.c_double)]
+                ("residual", ctypes.c_double), ("ms", ctypes.c_double), ("step_ratio", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}

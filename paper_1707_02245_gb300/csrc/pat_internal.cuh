@@ -182,6 +182,8 @@ struct FwdProxArgs {   // q <- prox(q + Sigma_q K ubar); also q*w and max|q|
     const int* stop;
 };
 
+constexpr int GAP_DATA_TERMS = 4;   // per-block sums of the data pass: |Ku-f|^2, |q|^2, <q,f>, |q-(Ku-f)|_1
+
 struct FwdGapArgs {    // FP64 partial sums of 1/2|Ku - f|^2, |q|^2, <q, f> per block
     GeomView g;
     const float* u;         // plain N*N image (u_quad NULL) ...

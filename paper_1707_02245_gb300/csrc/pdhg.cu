@@ -324,8 +324,27 @@ __global__ void k_dual_step(DualArgs a) {
 // FP64 duality gap over pixels (Sec. 3.3.3, box-restricted reading)
 // partials per block: {R1, R2, |K^T q - div r|_1, |E^T s - r|_1, |x - x_old|^2, |x_old|^2}
 // ---------------------------------------------------------------------------------
+constexpr int GAP_PIX_TERMS = 7;   // per-block sums of the pixel pass
+constexpr int GAP_TERMS = GAP_DATA_TERMS + GAP_PIX_TERMS;
+
+// Distance of g from the normal cone of the radius-ball at p: the cone is {0} inside the
+// ball and the ray through p on its sphere (the dual residual of a ball-constrained dual).
+__device__ __forceinline__ float cone_distance2(float g0, float g1, float p0, float p1, float radius) {
+    const float np = sqrtf(p0 * p0 + p1 * p1);
+    const float lam = np >= radius * (1.f - 1e-6f) && np > 0.f ? fmaxf(0.f, (g0 * p0 + g1 * p1) / np) : 0.f;
+    return sqrtf(fmaxf(g0 * g0 + g1 * g1 - lam * lam, 0.f));
+}
+__device__ __forceinline__ float cone_distance3(float g0, float g1, float g2, float p0, float p1, float p2,
+                                                float radius) {
+    const float np = sqrtf(p0 * p0 + p1 * p1 + p2 * p2);
+    const float lam =
+        np >= radius * (1.f - 1e-6f) && np > 0.f ? fmaxf(0.f, (g0 * p0 + g1 * p1 + g2 * p2) / np) : 0.f;
+    return sqrtf(fmaxf(g0 * g0 + g1 * g1 + g2 * g2 - lam * lam, 0.f));
+}
+
 struct GapArgs {
     int n;
+    float alpha, ab;      // ball radii of r and s
     double gamma;
     const float* xi;
     const float* x;       // x^{n+1}
@@ -342,9 +361,12 @@ __device__ __forceinline__ void gap_pixels_block(const GapArgs& a, const int lb)
     const int N = a.n;
     const size_t NN = (size_t)N * N;
     const float gam = (float)a.gamma;
+    const float alpha = a.alpha, ab = a.ab;
     // per-thread terms in FP32 (each thread covers few pixels), block sums in FP64: GB300's
     // FP64 pipe runs at 1/64 of FP32, so FP64 is kept to one conversion per thread and term
-    float acc[6] = {0, 0, 0, 0, 0, 0};
+    // + the dual residual of the regulariser duals (distance of their argument from the
+    // normal cone of the ball at r and s), for the adaptive balance
+    float acc[7] = {0, 0, 0, 0, 0, 0, 0};
     const int nthreads = a.nblocks * blockDim.x;
     auto X = [&](int c, int x, int y) -> float { return __ldg(a.x + c * NN + (size_t)y * N + x); };
     auto Yf = [&](int c, int x, int y) -> float { return __ldg(a.y + c * NN + (size_t)y * N + x); };
@@ -377,10 +399,12 @@ __device__ __forceinline__ void gap_pixels_block(const GapArgs& a, const int lb)
             g1 -= X(2, gx, gy);
         }
         acc[0] += sqrtf(g0 * g0 + g1 * g1);
+        acc[6] += cone_distance2(g0, g1, Yf(0, gx, gy), Yf(1, gx, gy), alpha);
         // box term of u: |K^T q - div r|; near convergence the two sides agree closely and
         // their FP32 difference is exact (Sterbenz), so FP32 keeps the term's precision
         const float divr = (rm(0, gx, gy) - rm(0, gx - 1, gy)) + (rm(1, gx, gy) - rm(1, gx, gy - 1));
-        acc[2] += fabsf(a.kt.at(gx, gy, N) - divr);
+        const float atu = a.kt.at(gx, gy, N) - divr;
+        acc[2] += fabsf(atu);
         if (REG == PAT_TGV) {
             auto vm = [&](int c, int x, int y, bool mx) -> float {  // masked v for d^-
                 if (x < 0 || y < 0 || (mx ? (x >= N - 1) : (y >= N - 1))) return 0.f;
@@ -392,6 +416,7 @@ __device__ __forceinline__ void gap_pixels_block(const GapArgs& a, const int lb)
                                (vm(1, gx, gy, true) - vm(1, gx - 1, gy, true))) * kInvSqrt2f;
             acc[1] += sqrtf(e11 * e11 + e22 * e22 + e12 * e12);
             const float s11 = Yf(2, gx, gy), s22 = Yf(3, gx, gy), s12 = Yf(4, gx, gy);
+            acc[6] += cone_distance3(e11, e22, e12, s11, s22, s12, ab);
             const float dx11 = ax ? Yf(2, gx + 1, gy) - s11 : 0.f;
             const float dy12 = by ? Yf(4, gx, gy + 1) - s12 : 0.f;
             const float dy22 = by ? Yf(3, gx, gy + 1) - s22 : 0.f;
@@ -408,11 +433,11 @@ __device__ __forceinline__ void gap_pixels_block(const GapArgs& a, const int lb)
             }
         }
     }
-    double dacc[6];
-    for (int c = 0; c < 6; ++c) dacc[c] = (double)acc[c];
-    block_sum<6>(dacc);
+    double dacc[GAP_PIX_TERMS];
+    for (int c = 0; c < GAP_PIX_TERMS; ++c) dacc[c] = (double)acc[c];
+    block_sum<GAP_PIX_TERMS>(dacc);
     if (threadIdx.x == 0)
-        for (int c = 0; c < 6; ++c) a.partials[6 * lb + c] = dacc[c];
+        for (int c = 0; c < GAP_PIX_TERMS; ++c) a.partials[GAP_PIX_TERMS * lb + c] = dacc[c];
 }
 
 template <int REG>
@@ -432,7 +457,8 @@ struct InfoDev {
     unsigned qmax_bits[2];  // max |q| of iterations of each parity (float bits)
     unsigned final_ticket;  // blocks of k_gap_final done (the last one resets it)
     float step_mul[2];      // {s, 1/s}: primal and dual step multipliers
-    double level2[GAP_FINAL_BLOCKS][9];
+    int n_adjust;           // adaptive-balance adjustments so far
+    double level2[GAP_FINAL_BLOCKS][GAP_TERMS];
 };
 
 struct FinalArgs {
@@ -441,25 +467,48 @@ struct FinalArgs {
     const double* pix_part;
     int n_pix;
     double alpha, beta, box_u, box_v, tol;
-    int reg;
+    int reg, adapt;
     InfoDev* info;
 };
+
+// Adaptive primal-dual balance (residual balancing after Goldstein, Li, Yuan, Esser and
+// Baraniuk 2015), in L1 norms at the evaluated state:
+//  - primal residual |A^T y|_1 (G = 0, so A^T y = 0 at a solution);
+//  - dual residual: |q - (Ku - f)|_1, plus the distance of grad u - v (dTV: D_xi grad u)
+//    and of E v from the normal cones of the r- and s-balls.
+// When one exceeds the other by more than BAL_DEAD, s (the primal step multiplier) moves
+// toward balance by the square root of their ratio, clamped to a factor BAL_MAX_STEP.  The
+// exponent decays by BAL_DECAY per adjustment, so s settles.
+constexpr double BAL_DEAD = 2.0, BAL_MAX_STEP = 2.0, BAL_DECAY = 0.97, BAL_MIN = 1e-3, BAL_MAX = 1e3;
+
+__device__ void balance_update(InfoDev* in, double primal_res, double dual_res) {
+    if (!(primal_res > 0 && dual_res > 0)) return;
+    const double rho = primal_res / dual_res;
+    if (rho >= 1.0 / BAL_DEAD && rho <= BAL_DEAD) return;
+    const double f = fmin(fmax(sqrt(rho), 1.0 / BAL_MAX_STEP), BAL_MAX_STEP);
+    double s = (double)in->step_mul[0] * pow(f, pow(BAL_DECAY, (double)in->n_adjust));
+    s = fmin(fmax(s, BAL_MIN), BAL_MAX);
+    in->step_mul[0] = (float)s;
+    in->step_mul[1] = (float)(1.0 / s);
+    in->n_adjust += 1;
+}
 
 // Two-level FP64 reduction in a fixed order: each of GAP_FINAL_BLOCKS blocks sums a fixed
 // strided subset of the partials, the last block to finish adds the block sums in index
 // order and evaluates the gap, the residual and the stopping test.
 __device__ __forceinline__ void gap_final_block(const FinalArgs& a, const int lb) {
-    double acc[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+    double acc[GAP_TERMS];
+    for (int c = 0; c < GAP_TERMS; ++c) acc[c] = 0.0;
     const int stride = GAP_FINAL_BLOCKS * blockDim.x;
     for (int b = lb * blockDim.x + threadIdx.x; b < a.n_data; b += stride)
-        for (int c = 0; c < 3; ++c) acc[c] += a.data_part[3 * b + c];
+        for (int c = 0; c < GAP_DATA_TERMS; ++c) acc[c] += a.data_part[GAP_DATA_TERMS * b + c];
     for (int b = lb * blockDim.x + threadIdx.x; b < a.n_pix; b += stride)
-        for (int c = 0; c < 6; ++c) acc[3 + c] += a.pix_part[6 * b + c];
-    block_sum<9>(acc);
+        for (int c = 0; c < GAP_PIX_TERMS; ++c) acc[GAP_DATA_TERMS + c] += a.pix_part[GAP_PIX_TERMS * b + c];
+    block_sum<GAP_TERMS>(acc);
     __shared__ bool s_last;
     InfoDev* in = a.info;
     if (threadIdx.x == 0) {
-        for (int c = 0; c < 9; ++c) in->level2[lb][c] = acc[c];
+        for (int c = 0; c < GAP_TERMS; ++c) in->level2[lb][c] = acc[c];
         __threadfence();
         s_last = atomicAdd(&in->final_ticket, 1u) == GAP_FINAL_BLOCKS - 1;
     }
@@ -467,9 +516,9 @@ __device__ __forceinline__ void gap_final_block(const FinalArgs& a, const int lb
     if (!s_last) return;
     __threadfence();
     // warp c adds the block sums of component c with a shuffle tree (fixed order)
-    __shared__ double s_tot[9];
+    __shared__ double s_tot[GAP_TERMS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int c = warp; c < 9; c += blockDim.x >> 5) {
+    for (int c = warp; c < GAP_TERMS; c += blockDim.x >> 5) {
         double v = lane < GAP_FINAL_BLOCKS ? *(volatile double*)&in->level2[lane][c] : 0.0;
         v = warp_sum(v);
         if (lane == 0) s_tot[c] = v;
@@ -477,10 +526,10 @@ __device__ __forceinline__ void gap_final_block(const FinalArgs& a, const int lb
     __syncthreads();
     if (threadIdx.x != 0) return;
     in->final_ticket = 0;
-    double t[9];
-    for (int c = 0; c < 9; ++c) t[c] = s_tot[c];
-    const double res2 = t[0], q2 = t[1], qf = t[2];
-    const double r1 = t[3], r2 = t[4], bu = t[5], bv = t[6], dx2 = t[7], x2 = t[8];
+    double t[GAP_TERMS];
+    for (int c = 0; c < GAP_TERMS; ++c) t[c] = s_tot[c];
+    const double res2 = t[0], q2 = t[1], qf = t[2], dres_q = t[3];
+    const double r1 = t[4], r2 = t[5], bu = t[6], bv = t[7], dx2 = t[8], x2 = t[9], dres_rs = t[10];
     const double reg = a.reg == PAT_TGV ? r1 + a.beta * r2 : r1;
     const double primal = 0.5 * res2 + a.alpha * reg;
     const double dual = -(0.5 * q2 + qf) - a.box_u * bu - (a.reg == PAT_TGV ? a.box_v * bv : 0.0);
@@ -499,6 +548,8 @@ __device__ __forceinline__ void gap_final_block(const FinalArgs& a, const int lb
     } else if (a.tol > 0 && rel <= a.tol) {
         in->status = PAT_STATUS_CONVERGED;
         in->stop = 1;
+    } else if (a.adapt == PAT_ADAPT_BALANCE) {
+        balance_update(in, bu + (a.reg == PAT_TGV ? bv : 0.0), dres_q + dres_rs);
     }
 }
 
@@ -697,7 +748,7 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     size_t off[19];
     size_t sz[19] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, NN * 4 * 2,
                      (reg == PAT_TGV ? 2 * NN : 1) * 4,
-                     NN * 4, S * 4, NN * 4, (size_t)ws.n_data * 3 * 8, (size_t)ws.n_pix * 6 * 8, sizeof(InfoDev),
+                     NN * 4, S * 4, NN * 4, (size_t)ws.n_data * GAP_DATA_TERMS * 8, (size_t)ws.n_pix * GAP_PIX_TERMS * 8, sizeof(InfoDev),
                      S * 4, nx * 4, nx * 4, (N + 1) * (N + 1) * 16, (N + 1) * (N + 1) * 16};
     size_t total = 0;
     for (int i = 0; i < 19; ++i) {
@@ -840,6 +891,8 @@ static void build_gap_plan(const Prob* pr, int B, Arena& ar, GapPlan& gp) {
 static GapArgs make_gap_args(const Prob& pr, const KtView& kt, const float* x, const float* x_old, const float* y_rs) {
     GapArgs ga;
     ga.n = pr.g->desc.n;
+    ga.alpha = (float)pr.p.alpha;
+    ga.ab = (float)(pr.p.alpha * pr.p.beta);
     ga.gamma = pr.p.gamma;
     ga.xi = pr.p.xi_dev;
     ga.x = x;
@@ -854,7 +907,7 @@ static GapArgs make_gap_args(const Prob& pr, const KtView& kt, const float* x, c
 
 static FinalArgs make_final_args(const Prob& pr) {
     FinalArgs fa{pr.ws.data_part, pr.ws.n_data, pr.ws.pix_part, pr.ws.n_pix, pr.p.alpha, pr.p.beta, pr.p.box_u,
-                 pr.p.box_v, pr.p.tol, pr.p.reg, pr.ws.info};
+                 pr.p.box_v, pr.p.tol, pr.p.reg, pr.p.adapt, pr.ws.info};
     return fa;
 }
 
@@ -1222,6 +1275,7 @@ static int run_batch(int B, const pat_geometry* const* g, const float* const* f,
             in.rel_gap = h.rel_gap;
             in.residual = h.residual;
             in.ms = ms;
+            in.step_ratio = (double)h.step_mul[0];
         }
         diverged = diverged || h.status == PAT_STATUS_DIVERGED;
     }
@@ -1507,6 +1561,7 @@ static int gap_impl(const pat_geometry* g, const float* f, const pat_params* p, 
     pr.f = f;
     pr.p = *p;
     pr.p.tol = 0;
+    pr.p.adapt = PAT_ADAPT_NONE;
     int rc = alloc_workspace(g, p->reg, pr.ws, st);
     if (rc) return rc;
     const long long S = (long long)g->desc.n_det * g->desc.n_t;

@@ -172,22 +172,22 @@ __device__ __forceinline__ void forward_gap_rows(const FwdGapArgs& a, int kb, in
     const float* img = QUAD ? reinterpret_cast<const float*>(a.u_quad) : a.u;
     const float s = phase_sum(circle_partial<QUAD>(g, img, rl));
     // per-row terms in FP32, block sums in FP64 (GB300's FP64 pipe is 1/64 of FP32)
-    float t0 = 0.f, t1 = 0.f, t2 = 0.f;
+    float t[GAP_DATA_TERMS] = {0.f, 0.f, 0.f, 0.f};
     if (rl.valid && rl.ph == 0) {
         const float ku = s * __ldg(&g.wk[rl.k]);
         const size_t i = (size_t)rl.d * g.n_t + rl.k;
         const float res = ku - a.f[i];
         const float qi = a.q[i];
-        t0 = res * res;
-        t1 = qi * qi;
-        t2 = qi * a.f[i];
+        t[0] = res * res;
+        t[1] = qi * qi;
+        t[2] = qi * a.f[i];
+        t[3] = fabsf(qi - res);   // dual residual of the data term: q - dF1(Ku)
     }
-    const double3 sum = block_sum3(make_double3((double)t0, (double)t1, (double)t2));
-    if (threadIdx.x == 0) {
-        a.partials[3 * lb + 0] = sum.x;
-        a.partials[3 * lb + 1] = sum.y;
-        a.partials[3 * lb + 2] = sum.z;
-    }
+    double sum[GAP_DATA_TERMS];
+    for (int c = 0; c < GAP_DATA_TERMS; ++c) sum[c] = (double)t[c];
+    block_sum<GAP_DATA_TERMS>(sum);
+    if (threadIdx.x == 0)
+        for (int c = 0; c < GAP_DATA_TERMS; ++c) a.partials[GAP_DATA_TERMS * lb + c] = sum[c];
 }
 
 __global__ void __launch_bounds__(ROW_THREADS) k_forward_gap_b(const FwdGapArgs* __restrict__ args,

@@ -213,3 +213,23 @@ def solve(torch, geo: Geometry, fs, workloads, device, stream, tol: float, max_i
     e1.record(stream)
     e1.synchronize()
     return infos, us, e0.elapsed_time(e1) / 1e3
+
+
+def unet_flops(batch: int, h: int, w: int, base_ch: int = 32, levels: int = 4, in_ch: int = IN_CH,
+               out_ch: int = OUT_CH) -> tuple[float, float]:
+    """Multiply-add FLOPs (2 per MAC) of one forward pass and of one training step (forward,
+    weight gradients, and input gradients of every conv but the first)."""
+    ch = [base_ch * 2 ** l for l in range(levels)]
+    convs = []   # (pixels per image, cin, cout)
+    cin = in_ch
+    for l in range(levels):
+        px = (h >> l) * (w >> l)
+        convs += [(px, cin, ch[l]), (px, ch[l], ch[l])]
+        cin = ch[l]
+    for l in range(levels - 2, -1, -1):
+        px = (h >> l) * (w >> l)
+        convs += [(px, ch[l + 1] + ch[l], ch[l]), (px, ch[l], ch[l])]
+    convs.append((h * w, ch[0], out_ch))
+    f = [2.0 * batch * px * 9 * ci * co for px, ci, co in convs]
+    fwd = sum(f)
+    return fwd, 3 * fwd - f[0]

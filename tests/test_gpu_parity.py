@@ -248,6 +248,26 @@ def test_step_ratio_matches_oracle_balanced_steps(reg, ratio):
     assert rel_l2(host(sq), st.sig_q) <= 1e-4
 
 
+@pytest.mark.parametrize("reg", [0, 1, 2])
+def test_adaptive_balance_matches_oracle(reg):
+    """PAT_ADAPT_BALANCE: the same residual-balancing decisions as the oracle (the final s
+    agrees), hence the same iterates."""
+    w = _with_xi(make("small", seed=10, reg=reg, beta=0.5, alpha=0.2), reg)
+    iters = 300
+    pb = oracle_problem(w)
+    ref = O.pdhg(pb, iters, gap_every=10, adapt=True)
+    pg = P.Geometry(w["n"], w["det_xy"], w["n_t"], w["r0"], w["dr"], w["quad_m"])
+    u_d = torch.empty(w["n"], w["n"], device=DEV)
+    prm = P.make_params(reg=reg, alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"],
+                        xi=dev(w["xi"]) if reg == 2 else None, iters=iters, gap_every=10, adapt=P.PAT_ADAPT_BALANCE)
+    info = P.pat_reconstruct(pg.handle, dev(w["f"]), prm, u_d)
+    assert ref.step_ratio != 1.0
+    # each adjustment is sqrt of a residual ratio (FP32 terms, FP64 sums on the GPU), so
+    # equal decisions leave s equal to a few 1e-4
+    assert abs(info["step_ratio"] - ref.step_ratio) <= 2e-3 * ref.step_ratio
+    assert rel_l2(host(u_d), ref.u) <= 1e-3
+
+
 def test_disc64_tv_200_iterations():
     """The 64^2 TV disc reconstruction after its 200 iterations."""
     w = make("disc64", seed=0)

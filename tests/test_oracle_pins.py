@@ -502,6 +502,87 @@ def test_gap_weak_duality_on_random_feasible_pairs(reg):
         assert O.duality_gap(pb, u, q, r, v, s)["gap"] >= -1e-10
 
 
+@pytest.mark.parametrize("reg", [O.REG_TV, O.REG_TGV, O.REG_DTV])
+def test_gap_stationarity_split_is_the_fenchel_young_identity(reg):
+    """gap - stationarity must equal the Fenchel-Young gap F(Ax) + F*(y) - <Ax, y> of the
+    dual variables, written here from F and A directly (the identity needs
+    <Ax, y> = <x, A^T y>, so a wrong adjoint or sign fails it)."""
+    g = _geom(n=6, n_det=3, n_t=8, m=24)
+    Km = O.system_matrix(g)
+    rng = np.random.default_rng(40 + reg)
+    n = g.n
+    xi = rng.standard_normal((2, n, n))
+    xi /= np.sqrt(xi[0] ** 2 + xi[1] ** 2 + 0.2)
+    f = rng.uniform(0, 2, Km.shape[0])
+    pb = O.problem_from_matrix(Km, n, f, reg=reg, alpha=0.3, beta=0.5, xi=xi)
+    for _ in range(5):
+        u = rng.uniform(-1, 1, (n, n))
+        v = rng.uniform(-1, 1, (2, n, n)) if reg == O.REG_TGV else None
+        q = rng.standard_normal(Km.shape[0])
+        r = O.proj_ball(rng.standard_normal((2, n, n)), pb.alpha)
+        s = O.proj_ball(rng.standard_normal((3, n, n)), pb.alpha * pb.beta) if reg == O.REG_TGV else None
+        gp = O.duality_gap(pb, u, q, r, v, s)
+        Ku = Km @ u.ravel()
+        fy = 0.5 * np.sum((Ku - f) ** 2) + 0.5 * q @ q + q @ f - Ku @ q
+        gu = O.grad(u) if reg != O.REG_DTV else O.dtv_apply(xi, pb.gamma, O.grad(u))
+        if reg == O.REG_TGV:
+            gu = gu - v
+        nrm = lambda p: np.sum(np.sqrt(np.sum(p * p, axis=0)))
+        fy += pb.alpha * nrm(gu) - np.sum(gu * r)
+        if reg == O.REG_TGV:
+            e = O.sym_grad(v)
+            fy += pb.alpha * pb.beta * nrm(e) - np.sum(e * s)
+        assert fy >= -1e-10
+        assert abs((gp["gap"] - gp["stationarity"]) - fy) < 1e-9 * (1 + abs(fy))
+
+
+def test_cone_distance_against_brute_force():
+    rng = np.random.default_rng(50)
+    lam = np.linspace(0.0, 20.0, 200001)
+    for _ in range(20):
+        g = rng.standard_normal(3)
+        p = rng.standard_normal(3)
+        p *= 0.7 / np.linalg.norm(p)
+        inside = O.pat_oracle._cone_distance(g[:, None, None], 0.5 * p[:, None, None], 0.7)[0, 0]
+        assert abs(inside - np.linalg.norm(g)) < 1e-12          # interior: the cone is {0}
+        on = O.pat_oracle._cone_distance(g[:, None, None], p[:, None, None], 0.7)[0, 0]
+        brute = np.min(np.linalg.norm(g[:, None] - lam[None, :] * p[:, None] / 0.7, axis=0))
+        assert abs(on - brute) < 1e-6
+
+
+def test_pd_residuals_vanish_at_the_solution():
+    g = _geom(n=6, n_det=3, n_t=8, m=24)
+    Km = O.system_matrix(g)
+    f = Km @ np.random.default_rng(3).uniform(0, 1, g.n * g.n)
+    for reg in (O.REG_TV, O.REG_TGV):
+        pb = O.problem_from_matrix(Km, g.n, f, reg=reg, alpha=0.05, beta=1.0)
+        z = np.zeros((g.n, g.n))
+        p0, d0 = O.pd_residuals(pb, z, np.zeros(f.size), np.zeros((2, g.n, g.n)),
+                                np.zeros((2, g.n, g.n)), np.zeros((3, g.n, g.n)))
+        res = O.pdhg(pb, 40000, tol=1e-9, gap_every=10, step_ratio=0.3 if reg == O.REG_TGV else 1.0)
+        p1, d1 = O.pd_residuals(pb, res.u, res.q, res.r, res.v, res.s)
+        assert p1 < 1e-3 * max(p0, d0) and d1 < 1e-3 * max(p0, d0)
+
+
+def test_adaptive_balance_rule_and_convergence():
+    # the rule: no move inside the dead zone, sqrt of the ratio clamped to [1/2, 2]
+    assert O.balance_update(3.0, 1.0, 1.5, 0) == (3.0, 0)          # ratio 1/1.5: inside
+    s1, k = O.balance_update(1.0, 9.0, 1.0, 0)                       # ratio 9: factor 2 (clamped)
+    assert (s1, k) == (2.0, 1)
+    s2, k = O.balance_update(1.0, 1.0, 4.0, 4)                       # ratio 1/4: factor 1/2, decayed
+    assert abs(s2 - 0.5 ** (0.97 ** 4)) < 1e-15 and k == 5
+    # an adaptive run reaches the same saddle point as a fixed one
+    g = _geom(n=6, n_det=3, n_t=8, m=24)
+    Km = O.system_matrix(g)
+    f = Km @ np.random.default_rng(2).uniform(0, 1, g.n * g.n)
+    pb = O.problem_from_matrix(Km, g.n, f, reg=O.REG_TGV, alpha=0.05, beta=1.0)
+    a = O.pdhg(pb, 20000, tol=1e-6, gap_every=10, adapt=True)
+    b = O.pdhg(pb, 20000, tol=1e-6, gap_every=10)
+    assert a.gap["rel_gap"] <= 1e-6 and b.gap["rel_gap"] <= 1e-6
+    assert a.step_ratio != 1.0
+    assert np.linalg.norm(a.u - b.u) <= 1e-3 * np.linalg.norm(b.u)
+
+
 def test_gap_zero_at_known_saddle_point_and_decays():
     g = _geom(n=6, n_det=3, n_t=8, m=24)
     Km = O.system_matrix(g)
