@@ -175,11 +175,40 @@ int  pat_reconstruct_batched(int count, const pat_geometry* const* g, const floa
 int  pat_steps(const pat_geometry* g, const pat_params* p, float* sig_q_dev, float* tau_u_dev,
                float* sig_r_dev, float* sig_s_dev, float* tau_v_dev, void* stream);
 
+/* Probe-based choice of the primal-dual balance s (pat_params.step_ratio).
+ * Each of the n_candidates values (1..64, each > 0) runs probe_iters PDHG iterations of
+ * (g, f, p) from p's start.  All probes run as one lockstep batch, and the one with the
+ * smallest relative gap after the probe wins.  best_host receives its s, and rel_gaps_host
+ * (may be NULL) each probe's relative gap.  p's iters, tol, gap_every, adapt and outputs
+ * are ignored; nothing is written to the caller's buffers.  The call synchronises
+ * `stream`.  Scratch comes from the stream-ordered pool. */
+int  pat_tune_step_ratio(const pat_geometry* g, const float* f_dev, const pat_params* p,
+                         const double* candidates_host, int n_candidates, int probe_iters,
+                         double* best_host, double* rel_gaps_host, void* stream);
+
 /* Box-restricted duality gap (Sec. 3.3.3, FP64 accumulation) of a primal point x and a
  * dual-feasible point y in the layouts of pat_params.  out4_host receives
  * {primal, dual, gap, rel_gap}; the call synchronises `stream`. */
 int  pat_duality_gap(const pat_geometry* g, const float* f_dev, const pat_params* p,
                      const float* x_dev, const float* y_dev, double* out4_host, void* stream);
+
+/* ---- measurement pre-processing (Sec. 4.3) ------------------------------------------ */
+/* Data f (D*T, detector-major) for the reconstruction from measured pressures p and the
+ * calibration measurements p_cal of an approximate delta pulse at x_p (both D*T, the
+ * samples of pat_geometry_desc: t_k = r0 + (k + 1/2) dr, speed of sound 1).  Per detector:
+ *   f_t = F^-1{ F{p} conj(F{h}) / (|F{h}|^2 + eps) }          (eq. (deconv))
+ * with h the calibration moved to the retarded time t - |x_d - x_p| (eq. (FW_full)),
+ * then f = t / |x_d - x_p| f_t                                   (eq. (f_rewrite)).
+ * Readings where the paper is silent:
+ *  - The transform length is the smallest power of two >= 2T, with zero padding (a linear
+ *    convolution), and the first T samples are kept.
+ *  - The time convolution is dr * sum.
+ *  - The travel-time shift uses the shift theorem (FFT phase ramp).
+ *  - eps = eps_rel * max |F{dr h}|^2 per detector.
+ * Arithmetic: FP32 transforms, FP64 times and delays.
+ * Constraints: T <= 2048, eps_rel > 0, x_p (2 doubles, host) not on a detector. */
+int  pat_preprocess(const pat_geometry* g, const float* p_dev, const float* pcal_dev,
+                    const double* xp_host, double eps_rel, float* f_dev, void* stream);
 
 /* ---- K^T without device allocation -------------------------------------------------- */
 /* u = K^T y like pat_adjoint, but the call allocates no device memory: no cudaMalloc,

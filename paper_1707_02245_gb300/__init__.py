@@ -35,6 +35,7 @@ EXPORTED = [
     "pat_direction_field", "pat_params_default", "pat_reconstruct", "pat_reconstruct_batched",
     "pat_steps", "pat_duality_gap", "pat_error_string", "pat_last_error", "pat_geometry_info",
     "pat_profile_enable", "pat_profile_read", "pat_kernel_launches", "pat_adjoint_noalloc",
+    "pat_tune_step_ratio", "pat_preprocess",
     # learned warm start (include/pat_unet.h)
     "pat_conv3x3_forward", "pat_conv3x3_backward_data", "pat_conv3x3_backward_weight",
     "pat_unet_create", "pat_unet_destroy", "pat_unet_num_params", "pat_unet_get_params",
@@ -113,6 +114,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                         ctypes.POINTER(vp), ctypes.POINTER(pat_info), vp]),
         "pat_steps": (i, [vp, ctypes.POINTER(pat_params), vp, vp, vp, vp, vp, vp]),
         "pat_duality_gap": (i, [vp, vp, ctypes.POINTER(pat_params), vp, vp, ctypes.POINTER(d), vp]),
+        "pat_preprocess": (i, [vp, vp, vp, ctypes.POINTER(d), d, vp, vp]),
+        "pat_tune_step_ratio": (i, [vp, vp, ctypes.POINTER(pat_params), ctypes.POINTER(d), i, i, ctypes.POINTER(d),
+                                    ctypes.POINTER(d), vp]),
         "pat_error_string": (ctypes.c_char_p, [i]),
         "pat_last_error": (ctypes.c_char_p, []),
         "pat_geometry_info": (i, [vp, ctypes.POINTER(ctypes.c_longlong)]),
@@ -252,6 +256,23 @@ def pat_duality_gap(g: int, f_dev, params: pat_params, x_dev, y_dev, stream=None
     _check(load().pat_duality_gap(g, _ptr(f_dev), ctypes.byref(params), _ptr(x_dev), _ptr(y_dev), out,
                                   _stream(stream)), "pat_duality_gap")
     return {"primal": out[0], "dual": out[1], "gap": out[2], "rel_gap": out[3]}
+
+
+def pat_tune_step_ratio(g: int, f_dev, params: pat_params, candidates, probe_iters: int, stream=None):
+    """Returns (best s, [relative gap of each probe])."""
+    c = (ctypes.c_double * len(candidates))(*[float(v) for v in candidates])
+    best = ctypes.c_double()
+    gaps = (ctypes.c_double * len(candidates))()
+    _check(load().pat_tune_step_ratio(g, _ptr(f_dev), ctypes.byref(params), c, len(candidates), probe_iters,
+                                      ctypes.byref(best), gaps, _stream(stream)), "pat_tune_step_ratio")
+    return best.value, list(gaps)
+
+
+def pat_preprocess(g: int, p_dev, pcal_dev, xp, eps_rel: float, f_dev, stream=None) -> None:
+    """Pre-processed data f from pressures p and calibrations p_cal (see include/pat.h)."""
+    x = (ctypes.c_double * 2)(float(xp[0]), float(xp[1]))
+    _check(load().pat_preprocess(g, _ptr(p_dev), _ptr(pcal_dev), x, float(eps_rel), _ptr(f_dev), _stream(stream)),
+           "pat_preprocess")
 
 
 def pat_geometry_info(g: int) -> dict:

@@ -220,7 +220,8 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     }
     pat_geometry* g = new pat_geometry();
     g->desc = d;
-    g->desc.det_xy_host = nullptr;  // not retained
+    g->det_xy.assign(d.det_xy_host, d.det_xy_host + 2 * (size_t)d.n_det);
+    g->desc.det_xy_host = nullptr;  // the caller's array is not retained
     cudaGetDevice(&g->device);
 
     const int N = d.n, D = d.n_det, T = d.n_t, M = d.quad_m;

@@ -90,6 +90,7 @@ struct pat_geometry {
     int4* adj_item = nullptr;         // K^T work items (one CTA each) {tile, first unit, end unit, 0}
     int adj_tiles_x = 0, adj_tiles = 0, adj_items = 0;
     std::vector<float> adj_item_cost;  // estimated candidates per work item (host)
+    std::vector<double> det_xy;        // detector positions (host copy, 2 per detector)
     pat::GeomView view;
     // lazily computed preconditioner sums
     mutable std::mutex mtx;

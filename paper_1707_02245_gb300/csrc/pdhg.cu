@@ -1495,6 +1495,49 @@ extern "C" int pat_reconstruct_batched(int count, const pat_geometry* const* g, 
     return PAT_OK;
 }
 
+// Probe-based choice of the primal-dual balance: every candidate s runs probe_iters
+// iterations from the same start as one lockstep batch, and the one with the smallest
+// relative gap wins.  The probes' images go to scratch; nothing else is written.
+extern "C" int pat_tune_step_ratio(const pat_geometry* g, const float* f_dev, const pat_params* p,
+                                   const double* candidates_host, int n_candidates, int probe_iters,
+                                   double* best_host, double* rel_gaps_host, void* stream) {
+    int rc = validate(g, p, "pat_tune_step_ratio");
+    if (rc) return rc;
+    if (!f_dev || !candidates_host || !best_host || n_candidates <= 0 || n_candidates > 64 || probe_iters <= 0)
+        return fail(PAT_ERR_INVALID_ARG, "pat_tune_step_ratio: NULL argument, 1..64 candidates and probe_iters > 0");
+    for (int i = 0; i < n_candidates; ++i)
+        if (!(candidates_host[i] > 0) || !std::isfinite(candidates_host[i]))
+            return fail(PAT_ERR_INVALID_ARG, "pat_tune_step_ratio: candidates must be finite and > 0");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t NN = (size_t)g->desc.n * g->desc.n;
+    float* scratch = nullptr;
+    PAT_CUDA(cudaMallocAsync(&scratch, NN * sizeof(float) * n_candidates, st));
+    std::vector<const pat_geometry*> gg(n_candidates, g);
+    std::vector<const float*> ff(n_candidates, f_dev);
+    std::vector<pat_params> pp(n_candidates, *p);
+    std::vector<float*> uu(n_candidates);
+    std::vector<pat_info> ii(n_candidates);
+    for (int i = 0; i < n_candidates; ++i) {
+        pp[i].step_ratio = candidates_host[i];
+        pp[i].adapt = PAT_ADAPT_NONE;
+        pp[i].iters = probe_iters;
+        pp[i].tol = 0.0;
+        pp[i].gap_every = 0;
+        pp[i].x_out_dev = pp[i].xbar_out_dev = pp[i].y_out_dev = nullptr;
+        uu[i] = scratch + NN * i;
+    }
+    rc = run_batch(n_candidates, gg.data(), ff.data(), pp.data(), uu.data(), ii.data(), st, "pat_tune_step_ratio");
+    cudaFreeAsync(scratch, st);
+    if (rc) return rc;
+    int best = 0;
+    for (int i = 0; i < n_candidates; ++i) {
+        if (rel_gaps_host) rel_gaps_host[i] = ii[i].rel_gap;
+        if (ii[i].rel_gap < ii[best].rel_gap) best = i;
+    }
+    *best_host = candidates_host[best];
+    return PAT_OK;
+}
+
 extern "C" int pat_steps(const pat_geometry* g, const pat_params* p, float* sig_q_dev, float* tau_u_dev,
                          float* sig_r_dev, float* sig_s_dev, float* tau_v_dev, void* stream) {
     int rc = validate(g, p, "pat_steps");

@@ -105,7 +105,7 @@ def state_sizes(w: dict) -> tuple[int, int]:
 
 @_ordered
 def make_pairs(torch, workloads: list[dict], geo: Geometry, device, stream, iters: int, tol: float = 0.0,
-               batch: int = 16, gap_every: int = 10):
+               batch: int = 16, gap_every: int = 10, step_ratio: float = 1.0):
     """Training pairs from PDHG itself.  Each problem is reconstructed (lockstep batches of
     ``batch``) for ``iters`` iterations, or until rel_gap <= tol.  Returns (features,
     targets, fs, infos):
@@ -127,7 +127,8 @@ def make_pairs(torch, workloads: list[dict], geo: Geometry, device, stream, iter
         ys = [torch.empty(ny, device=device) for _ in ws]
         us = [torch.empty(n, n, device=device) for _ in ws]
         prms = [make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], iters=iters, tol=tol,
-                            gap_every=gap_every, x_out=x, y_out=y) for w, x, y in zip(ws, xs, ys)]
+                            gap_every=gap_every, step_ratio=step_ratio, x_out=x, y_out=y)
+                for w, x, y in zip(ws, xs, ys)]
         infos += pat_reconstruct_batched([geo.handle] * len(ws), f_b, prms, us, stream)
         for k, (w, f, x, y, p) in enumerate(zip(ws, f_b, xs, ys, prms)):
             pat_warm_start_features(geo.handle, f, feats[b0 + k], IN_CH, stream)
@@ -195,7 +196,7 @@ def predict_states(torch, net: UNet, geo: Geometry, feats, fs, params, device, s
 
 @_ordered
 def solve(torch, geo: Geometry, fs, workloads, device, stream, tol: float, max_iters: int, gap_every: int = 10,
-          x0s=None, y0s=None):
+          x0s=None, y0s=None, step_ratio: float = 1.0):
     """Solves every problem to rel_gap <= tol (cold, or from (x0s, y0s)) in one lockstep
     batch.  Returns (infos, images, seconds on the stream's events)."""
     n = workloads[0]["n"]
@@ -206,7 +207,7 @@ def solve(torch, geo: Geometry, fs, workloads, device, stream, tol: float, max_i
         if x0s is not None:
             kw = dict(x0=x0s[i], y0=y0s[i])
         prms.append(make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], iters=max_iters, tol=tol,
-                                gap_every=gap_every, **kw))
+                                gap_every=gap_every, step_ratio=step_ratio, **kw))
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     infos = pat_reconstruct_batched([geo.handle] * len(fs), fs, prms, us, stream)

@@ -379,3 +379,37 @@ def workload_warm(seed: int, n: int = 256, n_det: int = 128, n_t: int | None = N
                 n_fine=2 * n, quad_m_fine=2 * quad_m, phantom=ph, phantom_fine=ph_f,
                 noise=standard_normal((n_det, n_t), seed + 17), noise_level=level,
                 reg=1, alpha=0.02, beta=0.04, gamma=0.95, iters=1000)
+
+
+def calibration_pulse(t, width: float, bipolar: bool = True):
+    """Photoacoustic calibration pulse centred at c = 4 width (causal to within exp(-8)):
+    bipolar, -(t - c) / width * exp(-(t - c)^2 / (2 width^2)) (the time derivative of a
+    Gaussian illumination profile, detector response idealised), or the Gaussian itself."""
+    t = np.asarray(t, dtype=np.float64)
+    c = 4.0 * width
+    g = np.exp(-0.5 * ((t - c) / width) ** 2)
+    return -(t - c) / width * g if bipolar else g
+
+
+def pressure_measurement(f, det_xy, xp, r0: float, dr: float, width: float, noise_level: float, seed: int,
+                         bipolar: bool = True):
+    """Synthetic pressures p and calibrations p_cal (D x T) for data f (D x T) on the samples
+    t_k = r0 + (k + 1/2) dr, the measurement model of Sec. 4.3:
+    p = (|x_d - x_p| / t f) * h with the pulse h(s) = calibration_pulse(s) (time convolution,
+    dr * sum, linear and causal), and p_cal[d, k] = calibration_pulse(t_k - |x_d - x_p|),
+    the calibration measured from the pulse source x_p.  Gaussian noise of std
+    noise_level * max|.| is added to both."""
+    f = np.asarray(f, dtype=np.float64)
+    D, T = f.shape
+    t = r0 + (np.arange(T) + 0.5) * dr
+    dist = np.hypot(det_xy[:, 0] - xp[0], det_xy[:, 1] - xp[1])
+    h = calibration_pulse(np.arange(T) * dr, width, bipolar)
+    p = np.zeros((D, T))
+    for d in range(D):
+        ft = dist[d] / t * f[d]
+        p[d] = dr * np.convolve(ft, h)[:T]
+    pcal = calibration_pulse(t[None, :] - dist[:, None], width, bipolar)
+    g = _rng(seed + 555)
+    p += noise_level * np.abs(p).max() * g.standard_normal(p.shape)
+    pcal += noise_level * np.abs(pcal).max() * g.standard_normal(pcal.shape)
+    return p, pcal

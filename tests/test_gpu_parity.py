@@ -268,6 +268,24 @@ def test_adaptive_balance_matches_oracle(reg):
     assert rel_l2(host(u_d), ref.u) <= 1e-3
 
 
+def test_tune_step_ratio_picks_the_smallest_probe_gap():
+    w = make("small", seed=11, reg=1, beta=0.5)
+    pg = P.Geometry(w["n"], w["det_xy"], w["n_t"], w["r0"], w["dr"], w["quad_m"])
+    f = dev(w["f"])
+    prm = P.make_params(reg=1, alpha=w["alpha"], beta=w["beta"], iters=5, gap_every=1)
+    cands = [0.3, 1.0, 3.0, 10.0]
+    best, gaps = P.pat_tune_step_ratio(pg.handle, f, prm, cands, 40)
+    u_d = torch.empty(w["n"], w["n"], device=DEV)
+    single = []
+    for s_ in cands:
+        p1 = P.make_params(reg=1, alpha=w["alpha"], beta=w["beta"], iters=40, gap_every=0, step_ratio=s_)
+        single.append(P.pat_reconstruct(pg.handle, f, p1, u_d)["rel_gap"])
+    assert gaps == single                       # the probes are the single runs, bitwise
+    assert best == cands[int(np.argmin(single))]
+    with pytest.raises(P.PatError):
+        P.pat_tune_step_ratio(pg.handle, f, prm, [1.0, -2.0], 40)
+
+
 def test_disc64_tv_200_iterations():
     """The 64^2 TV disc reconstruction after its 200 iterations."""
     w = make("disc64", seed=0)
