@@ -320,16 +320,40 @@ def run_gb300(args) -> int:
         e2e = {"value": e2e_units / e2e_s, "unit": UNIT, "h2d_bytes_per_step": f.numel() * 4,
                "d2h_bytes_per_step": u.numel() * 4, "steps": e2e_steps}
 
-    # ---- time to relative gap 1e-4 (cold start) ----
+    # ---- time to relative gap 1e-4 (cold start): the paper's steps, and the balance s
+    # chosen by the probe tuner (probe time included) ----
     ttg = None
     if not args.no_ttg:
-        prm_t = P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"], xi=xi,
-                              iters=args.ttg_max_iters, gap_every=10, tol=1e-4)
-        flush.zero_()
-        info = P.pat_reconstruct(geo.handle, f, prm_t, u, stream)
-        ttg = {"tol": 1e-4, "iters": info["iters_done"], "seconds": info["ms"] / 1e3,
-               "rel_gap": info["rel_gap"], "reached": info["status"] == P.PAT_STATUS_CONVERGED,
+        def to_gap(ratio):
+            prm_t = P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"], xi=xi,
+                                  iters=args.ttg_max_iters, gap_every=10, tol=1e-4, step_ratio=ratio)
+            flush.zero_()
+            return P.pat_reconstruct(geo.handle, f, prm_t, u, stream)
+        info = to_gap(1.0)
+        ttg = {"tol": 1e-4, "paper_steps": {"step_ratio": 1.0, "iters": info["iters_done"],
+                                            "seconds": info["ms"] / 1e3, "rel_gap": info["rel_gap"],
+                                            "reached": info["status"] == P.PAT_STATUS_CONVERGED},
                "max_iters": args.ttg_max_iters}
+        cands = [1.0, 3.0, 10.0, 30.0]
+        prm_p = P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"], xi=xi)
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        best, pg = P.pat_tune_step_ratio(geo.handle, f, prm_p, cands, args.probe_iters, stream)
+        e1.record(stream)
+        e1.synchronize()
+        probe_s = e0.elapsed_time(e1) / 1e3
+        info = to_gap(best)
+        ttg["tuned"] = {"step_ratio": best, "candidates": cands, "probe_iters": args.probe_iters,
+                        "probe_rel_gaps": pg, "probe_seconds": probe_s, "iters": info["iters_done"],
+                        "solve_seconds": info["ms"] / 1e3, "seconds": probe_s + info["ms"] / 1e3,
+                        "rel_gap": info["rel_gap"], "reached": info["status"] == P.PAT_STATUS_CONVERGED}
+        ttg["speedup_vs_paper_steps"] = ttg["paper_steps"]["seconds"] / ttg["tuned"]["seconds"]
+
+    # ---- measurement pre-processing (Sec. 4.3) on this geometry ----
+    prep = None
+    if not args.no_prep:
+        prep = run_preprocess(P, S, np, torch, device, stream, geo, w, flush)
 
     # ---- batched: B TGV 256^2 problems in lockstep, and the 64-problem mixed batch ----
     batched = None
@@ -338,6 +362,9 @@ def run_gb300(args) -> int:
     mixed = None
     if args.mixed:
         mixed = run_mixed(P, S, np, torch, device, stream, flush, args.mixed_max_iters)
+    warm = None
+    if args.warm:
+        warm = run_warm_start(P, S, np, torch, device, stream, args)
 
     # ---- roofline of the dominant phase ----
     NN = n * n
@@ -389,7 +416,7 @@ def run_gb300(args) -> int:
                            "points_on_grid_per_K": pts, "final_rel_gap": infos[-1]["rel_gap"]},
                 "roofline": roofline, "phases": phases, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "time_to_gap": ttg,
-                "batched": batched, "mixed_batch": mixed,
+                "batched": batched, "mixed_batch": mixed, "warm_start": warm, "preprocess": prep,
                 "wall_s_timed": wall, "profiled_ms_per_step": sum(prof_ms) / len(prof_ms)}
         print(json.dumps(line), flush=True)
     geo.close()
@@ -468,6 +495,111 @@ def run_mixed(P, S, np, torch, device, stream, flush, max_iters):
             "pixels": int(sum(w["n"] ** 2 for w in ws)), "samples": int(sum(w["det_xy"].shape[0] * w["n_t"] for w in ws))}
 
 
+def run_preprocess(P, S, np, torch, device, stream, geo, w, flush):
+    """pat_preprocess on the benchmark geometry: synthetic pressures and calibrations of
+    the benchmark's data, timed with CUDA events (mean of 20 calls after 3 warm-ups)."""
+    D, T = w["det_xy"].shape[0], w["n_t"]
+    rng = np.random.default_rng(7)
+    t = w["r0"] + (np.arange(T) + 0.5) * w["dr"]
+    f = np.exp(-((t[None, :] - rng.uniform(0.6, 2.0, D)[:, None]) / 0.1) ** 2)
+    xp = (0.05, -0.1)
+    p, pcal = S.pressure_measurement(f, w["det_xy"], xp, w["r0"], w["dr"], width=2.5 * w["dr"], noise_level=0.01,
+                                     seed=0)
+    pd = torch.from_numpy(p.astype(np.float32)).to(device)
+    cd = torch.from_numpy(pcal.astype(np.float32)).to(device)
+    out = torch.empty(D, T, device=device)
+    for _ in range(3):
+        P.pat_preprocess(geo.handle, pd, cd, xp, 1e-3, out, stream)
+    flush.zero_()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(20):
+        P.pat_preprocess(geo.handle, pd, cd, xp, 1e-3, out, stream)
+    e1.record(stream)
+    e1.synchronize()
+    us = e0.elapsed_time(e1) / 20 * 1e3
+    return {"detectors": D, "samples": T, "us_per_call": us, "gb_per_s": 3 * D * T * 4 / (us * 1e-6) / 1e9}
+
+
+def run_warm_start(P, S, np, torch, device, stream, args):
+    """The learned warm start on TGV^2 256^2 vessel problems with 128 detectors: training
+    pairs from PDHG (the tuned balance s, rel gap 1e-5, at most --warm-label-iters), U-Net
+    training on the GPU, then cold and warm PDHG to rel gap 1e-4 on held-out seeds (one
+    lockstep batch each, the same s).  Warm time includes the features, the network and
+    the state map."""
+    from paper_1707_02245_gb300 import warmstart as WS
+    n, ndet, nt = 256, 128, 512
+    ws = [S.workload_warm(s, n=n, n_det=ndet, n_t=nt) for s in range(args.warm_train)]
+    wv = [S.workload_warm(100000 + s, n=n, n_det=ndet, n_t=nt) for s in range(args.warm_val)]
+    w0 = ws[0]
+    geo = P.Geometry(n, w0["det_xy"], w0["n_t"], w0["r0"], w0["dr"], w0["quad_m"])
+    out = {"workload": f"TGV^2 {n}x{n} vessel phantoms, {ndet} detectors x {nt} samples, noise U[1%,10%], "
+                       f"alpha 0.02 beta 0.04", "train_pairs": len(ws), "held_out": len(wv)}
+    f0 = WS.simulate(torch, w0, device, stream)
+    sr, _ = P.pat_tune_step_ratio(geo.handle, f0, P.make_params(reg=1, alpha=w0["alpha"], beta=w0["beta"]),
+                                  [1.0, 3.0, 10.0, 30.0], args.probe_iters, stream)
+    out["step_ratio"] = sr
+    t0 = time.perf_counter()
+    F, T, _, infos = WS.make_pairs(torch, ws, geo, device, stream, iters=args.warm_label_iters, tol=1e-5, batch=64,
+                                   step_ratio=sr)
+    torch.cuda.synchronize(device)
+    its = [i["iters_done"] for i in infos]
+    out["labels"] = {"seconds": time.perf_counter() - t0, "iters_median": float(np.median(its)),
+                     "converged_1e-5": sum(i["status"] == P.PAT_STATUS_CONVERGED for i in infos)}
+    Fv, Tv, fv, _ = WS.make_pairs(torch, wv, geo, device, stream, iters=1, tol=0.0, batch=64, step_ratio=sr)
+    e = (T ** 2).mean(dim=(0, 1, 2)).cpu().numpy()
+    cw = list((1.0 / np.maximum(e, 1e-12) / len(e)).astype(float))
+    net = WS.UNet(base_ch=32, levels=4, seed=1)
+    lg, tt = WS.train(torch, net, F, T, args.warm_steps, 8, 1e-3, cw, stream, log_every=max(1, args.warm_steps // 4))
+    # tensor-core throughput of the training step (timed separately, 10 steps)
+    x8, t8 = F[:8].contiguous(), T[:8].contiguous()
+    loss = torch.zeros(1, device=device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(10):
+        P.pat_unet_train_step(net.handle, x8, t8, cw, 8, n, n, 1e-6, loss, stream)
+    e1.record(stream)
+    e1.synchronize()
+    step_ms = e0.elapsed_time(e1) / 10
+    fwd_fl, step_fl = WS.unet_flops(8, n, n)
+    peaks = load_peaks()
+    tf = step_fl / (step_ms * 1e-3) / 1e12
+    out["training"] = {"steps": args.warm_steps, "batch": 8, "seconds": tt, "loss_log": lg, "params": net.num_params,
+                       "step_ms": step_ms,
+                       "roofline": {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                                    "frac": tf / peaks["bf16_tflops"], "flop_per_step": step_fl,
+                                    "kernels": "k_conv_fwd / k_conv_wgrad (bf16 mma.sync, FP32 accumulate)",
+                                    "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)"}}
+    prms = [P.make_params(reg=1, alpha=w["alpha"], beta=w["beta"]) for w in wv]
+    # cold
+    ci, us_c, ct = WS.solve(torch, geo, fv, wv, device, stream, tol=1e-4, max_iters=30000, step_ratio=sr)
+    # warm: features (already computed in Fv) are part of the warm path, so time them again
+    e0.record(stream)
+    feats = torch.empty_like(Fv)
+    for k in range(len(wv)):
+        P.pat_warm_start_features(geo.handle, fv[k], feats[k], 8, stream)
+    x0s, y0s = WS.predict_states(torch, net, geo, feats, fv, prms, device, stream)
+    e1.record(stream)
+    e1.synchronize()
+    pred_s = e0.elapsed_time(e1) / 1e3
+    wi, us_w, wt = WS.solve(torch, geo, fv, wv, device, stream, tol=1e-4, max_iters=30000, x0s=x0s, y0s=y0s,
+                            step_ratio=sr)
+    cit = np.array([i["iters_done"] for i in ci], dtype=float)
+    wit = np.array([i["iters_done"] for i in wi], dtype=float)
+    diff = [float((us_c[k] - us_w[k]).norm() / us_c[k].norm()) for k in range(len(wv))]
+    out["cold"] = {"iters_median": float(np.median(cit)), "iters_mean": float(cit.mean()), "seconds": ct,
+                   "converged": sum(i["status"] == P.PAT_STATUS_CONVERGED for i in ci)}
+    out["warm"] = {"iters_median": float(np.median(wit)), "iters_mean": float(wit.mean()), "solve_seconds": wt,
+                   "predict_seconds": pred_s, "seconds": wt + pred_s,
+                   "converged": sum(i["status"] == P.PAT_STATUS_CONVERGED for i in wi)}
+    out["speedup_warm_vs_cold"] = ct / (wt + pred_s)
+    out["iters_ratio_median"] = float(np.median(wit / cit))
+    out["image_rel_diff_warm_vs_cold_median"] = float(np.median(diff))
+    net.close()
+    geo.close()
+    return out
+
+
 def load_peaks() -> dict:
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -496,6 +628,13 @@ def main(argv=None) -> int:
     ap.add_argument("--batch", type=int, default=16, help="TGV 256^2 problems in the lockstep batch (0: skip)")
     ap.add_argument("--mixed", type=int, default=1, help="run the 64-problem mixed batch (0: skip)")
     ap.add_argument("--mixed-max-iters", type=int, default=5000)
+    ap.add_argument("--probe-iters", type=int, default=300, help="iterations of each step-ratio probe")
+    ap.add_argument("--warm", type=int, default=1, help="run the learned warm-start leg (0: skip)")
+    ap.add_argument("--warm-train", type=int, default=128)
+    ap.add_argument("--warm-val", type=int, default=16)
+    ap.add_argument("--warm-steps", type=int, default=2000)
+    ap.add_argument("--warm-label-iters", type=int, default=10000, help="iteration cap of the training labels")
+    ap.add_argument("--no-prep", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
