@@ -469,6 +469,7 @@ struct FinalArgs {
     double alpha, beta, box_u, box_v, tol;
     int reg, adapt;
     InfoDev* info;
+    int* batch_stopped;    // problems of the batch that have stopped (the host polls it)
 };
 
 // Adaptive primal-dual balance (residual balancing after Goldstein, Li, Yuan, Esser and
@@ -545,9 +546,11 @@ __device__ __forceinline__ void gap_final_block(const FinalArgs& a, const int lb
     if (!isfinite(gap) || !isfinite(primal)) {
         in->status = PAT_STATUS_DIVERGED;
         in->stop = 1;
+        if (a.batch_stopped) atomicAdd(a.batch_stopped, 1);
     } else if (a.tol > 0 && rel <= a.tol) {
         in->status = PAT_STATUS_CONVERGED;
         in->stop = 1;
+        if (a.batch_stopped) atomicAdd(a.batch_stopped, 1);
     } else if (a.adapt == PAT_ADAPT_BALANCE) {
         balance_update(in, bu + (a.reg == PAT_TGV ? bv : 0.0), dres_q + dres_rs);
     }
@@ -905,9 +908,9 @@ static GapArgs make_gap_args(const Prob& pr, const KtView& kt, const float* x, c
     return ga;
 }
 
-static FinalArgs make_final_args(const Prob& pr) {
+static FinalArgs make_final_args(const Prob& pr, int* batch_stopped = nullptr) {
     FinalArgs fa{pr.ws.data_part, pr.ws.n_data, pr.ws.pix_part, pr.ws.n_pix, pr.p.alpha, pr.p.beta, pr.p.box_u,
-                 pr.p.box_v, pr.p.tol, pr.p.reg, pr.p.adapt, pr.ws.info};
+                 pr.p.box_v, pr.p.tol, pr.p.reg, pr.p.adapt, pr.ws.info, batch_stopped};
     return fa;
 }
 
@@ -990,7 +993,7 @@ struct IterPlan {
     GapPlan gp;
 };
 
-static void build_iter_plan(const Prob* pr, int B, Arena& ar, IterPlan& ip) {
+static void build_iter_plan(const Prob* pr, int B, Arena& ar, IterPlan& ip, int* batch_stopped) {
     for (int par = 0; par < 2; ++par) {
         std::vector<FwdProxArgs> fw;
         std::vector<AdjArgs> ad;
@@ -1018,7 +1021,7 @@ static void build_iter_plan(const Prob* pr, int B, Arena& ar, IterPlan& ip) {
         ip.gpix[par] = ar.put(gpx.data(), gpx.size());
     }
     std::vector<FinalArgs> fi;
-    for (int b = 0; b < B; ++b) fi.push_back(make_final_args(pr[b]));
+    for (int b = 0; b < B; ++b) fi.push_back(make_final_args(pr[b], batch_stopped));
     ip.fin = ar.put(fi.data(), fi.size());
     // maps: forward rows problem by problem; K^T items of all problems heaviest first;
     // update tiles grouped by regulariser
@@ -1161,11 +1164,29 @@ static cudaStream_t loop_stream() {
     return streams[dev];
 }
 
-static int run_iterations(const IterPlan& ip, const char* base, int iters, int ge, cudaStream_t st) {
+// Pinned host slots for the stop-counter snapshots of run_iterations (one pair per thread).
+static int* stop_snapshots() {
+    thread_local int* h = nullptr;
+    if (!h && cudaHostAlloc((void**)&h, 2 * sizeof(int), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        h = nullptr;
+    }
+    return h;
+}
+
+// Enqueues all iterations.  The periodic part replays a captured graph in chunks of
+// CHUNK periods.  When the batch can stop early (some problem has a tolerance), the
+// counter of stopped problems is copied to pinned memory after every chunk.  Before the
+// next chunk is enqueued, the host reads the previous chunk's copy; the GPU is then busy
+// with the current chunk, so it never idles.  Replays end once every problem has stopped:
+// the kernels of a stopped problem return at entry, but their launches still cost time.
+static int run_iterations(const IterPlan& ip, const char* base, int iters, int ge, cudaStream_t st,
+                          const int* batch_stopped, int B, bool can_stop) {
     auto gap_due = [&](int it) { return (ge > 0 && (it + 1) % ge == 0) || it + 1 == iters; };
     const int P = ge > 0 ? (ge % 2 == 0 ? ge : 2 * ge) : 2;
     const int nper = iters > 0 ? (iters - 1) / P : 0;
     int start = 0;
+    bool all_stopped = false;
     if (!prof_on() && nper >= 2) {
         // one period of the loop as a graph; periods repeat exactly (P is even, so the
         // ping-pong parity repeats, and a multiple of gap_every, so the gap passes do)
@@ -1187,14 +1208,44 @@ static int run_iterations(const IterPlan& ip, const char* base, int iters, int g
             return cuda_fail(e, "run_iterations: graph instantiate");
         }
         const long long per_period = pat_kernel_launches() - l0;
-        for (int r = 0; r < nper && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, st);
-        for (int r = 1; r < nper; ++r)
+        constexpr int CHUNK = 8;
+        int* snap = can_stop && batch_stopped ? stop_snapshots() : nullptr;
+        cudaEvent_t ev[2] = {nullptr, nullptr};
+        bool pending[2] = {false, false};
+        if (snap)
+            for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+        int launched = 0;
+        for (int chunk = 0; launched < nper && e == cudaSuccess; ++chunk) {
+            const int n = std::min(CHUNK, nper - launched);
+            for (int r = 0; r < n && e == cudaSuccess; ++r) e = cudaGraphLaunch(exec, st);
+            launched += n;
+            if (!snap || e != cudaSuccess) continue;
+            const int cur = chunk & 1, prev = cur ^ 1;
+            e = cudaMemcpyAsync(&snap[cur], batch_stopped, sizeof(int), cudaMemcpyDeviceToHost, st);
+            if (e == cudaSuccess) e = cudaEventRecord(ev[cur], st);
+            pending[cur] = e == cudaSuccess;
+            if (pending[prev] && e == cudaSuccess) {
+                e = cudaEventSynchronize(ev[prev]);
+                pending[prev] = false;
+                if (e == cudaSuccess && *(volatile int*)&snap[prev] >= B) {
+                    all_stopped = true;
+                    break;
+                }
+            }
+        }
+        for (int i = 0; i < 2; ++i)
+            if (ev[i]) {
+                if (pending[i]) cudaEventSynchronize(ev[i]);   // the slot is reused by the next call
+                cudaEventDestroy(ev[i]);
+            }
+        for (int r = 1; r < launched; ++r)
             for (long long k = 0; k < per_period; ++k) count_launch();
         cudaGraphExecDestroy(exec);
         cudaGraphDestroy(graph);
         if (e != cudaSuccess) return cuda_fail(e, "run_iterations: graph launch");
         start = nper * P;
     }
+    if (all_stopped) return PAT_OK;
     for (int it = start; it < iters; ++it) {
         int rc = enqueue_iteration(ip, base, it, gap_due(it), st);
         if (rc) return rc;
@@ -1225,16 +1276,25 @@ static int run_batch(int B, const pat_geometry* const* g, const float* const* f,
     }
     std::vector<char> host;
     void* dev = nullptr;
+    int* stopped = nullptr;
+    bool can_stop = false;
+    for (int b = 0; b < B; ++b) can_stop = can_stop || p[b].tol > 0;
+    if (!rc && p[0].iters > 0) {
+        rc = cudaMallocAsync((void**)&stopped, sizeof(int), st) == cudaSuccess &&
+                     cudaMemsetAsync(stopped, 0, sizeof(int), st) == cudaSuccess
+                 ? PAT_OK
+                 : fail(PAT_ERR_CUDA, std::string(who) + ": stop counter");
+    }
     if (!rc && p[0].iters > 0) {
         Arena ar(host);
         IterPlan ip;
-        build_iter_plan(pr.data(), B, ar, ip);
+        build_iter_plan(pr.data(), B, ar, ip, stopped);
         rc = ar.upload(&dev, st);
         cudaStream_t ls = loop_stream();
         if (!ls) rc = fail(PAT_ERR_CUDA, std::string(who) + ": no loop stream");
         if (!rc) rc = cudaEventRecord(fork, st) == cudaSuccess ? PAT_OK : PAT_ERR_CUDA;
         if (!rc) rc = cudaStreamWaitEvent(ls, fork, 0) == cudaSuccess ? PAT_OK : PAT_ERR_CUDA;
-        if (!rc) rc = run_iterations(ip, (const char*)dev, p[0].iters, p[0].gap_every, ls);
+        if (!rc) rc = run_iterations(ip, (const char*)dev, p[0].iters, p[0].gap_every, ls, stopped, B, can_stop);
         if (ls) {
             cudaEventRecord(join, ls);
             cudaStreamWaitEvent(st, join, 0);
@@ -1246,6 +1306,7 @@ static int run_batch(int B, const pat_geometry* const* g, const float* const* f,
         rc = cudaMemcpyAsync(&hinfo[b], pr[b].ws.info, sizeof(InfoDev), cudaMemcpyDeviceToHost, st) ? PAT_ERR_CUDA : 0;
     cudaEventRecord(e1, st);
     if (dev) cudaFreeAsync(dev, st);
+    if (stopped) cudaFreeAsync(stopped, st);
     for (int b = 0; b < B; ++b)
         if (pr[b].ws.base) cudaFreeAsync(pr[b].ws.base, st);
     cudaError_t se = cudaStreamSynchronize(st);

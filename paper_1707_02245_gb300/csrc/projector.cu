@@ -117,13 +117,15 @@ __global__ void __launch_bounds__(ROW_THREADS) k_forward(GeomView g, const float
 __device__ __forceinline__ void forward_prox_rows(const FwdProxArgs& a, int kb, int d) {
     const GeomView& g = a.g;
     const RowLane rl = row_lane(g, kb, d);
+    // issued before the circle sums so that its latency overlaps them
+    const float smul = a.step_mul ? __ldg(a.step_mul + 1) : 1.f;
     const float s = phase_sum(circle_partial<true>(g, reinterpret_cast<const float*>(a.ubar_quad), rl));
     float aq = 0.f;
     if (rl.valid && rl.ph == 0) {
         const size_t i = (size_t)rl.d * g.n_t + rl.k;
         const float wk = __ldg(&g.wk[rl.k]);
         const float ku = s * wk;
-        const float sg = (a.sig_q ? a.sig_q[i] : a.sig_scalar) * (a.step_mul ? a.step_mul[1] : 1.f);
+        const float sg = (a.sig_q ? a.sig_q[i] : a.sig_scalar) * smul;
         const float qn = (a.q[i] + sg * (ku - a.f[i])) / (1.f + sg);
         a.q[i] = qn;
         a.qw[i] = qn * wk;

@@ -286,6 +286,28 @@ def test_tune_step_ratio_picks_the_smallest_probe_gap():
         P.pat_tune_step_ratio(pg.handle, f, prm, [1.0, -2.0], 40)
 
 
+def test_replays_end_once_every_problem_has_stopped():
+    """A generous iteration cap costs nothing after convergence: the graph replays stop
+    within two chunks of the last problem's stop, and the result is unchanged."""
+    w = make("small", seed=12, reg=0)
+    pg = P.Geometry(w["n"], w["det_xy"], w["n_t"], w["r0"], w["dr"], w["quad_m"])
+    f = dev(w["f"])
+    u_a = torch.empty(w["n"], w["n"], device=DEV)
+    u_b = torch.empty_like(u_a)
+    pa = P.make_params(reg=0, alpha=w["alpha"], iters=2000, tol=1e-2, gap_every=10)
+    pb = P.make_params(reg=0, alpha=w["alpha"], iters=400000, tol=1e-2, gap_every=10)
+    ia = P.pat_reconstruct(pg.handle, f, pa, u_a)
+    l0 = P.pat_kernel_launches()
+    ib = P.pat_reconstruct(pg.handle, f, pb, u_b)
+    launches = P.pat_kernel_launches() - l0
+    assert ia["status"] == ib["status"] == P.PAT_STATUS_CONVERGED
+    assert ia["iters_done"] == ib["iters_done"] < 2000
+    assert torch.equal(u_a, u_b)
+    # at most 6 launches per iteration (3 + the gap's 3 every 10th) for the iterations run
+    # plus two chunks of 8 periods of 10 iterations
+    assert launches <= 6 * (ib["iters_done"] + 2 * 8 * 10 + 20) + 50
+
+
 def test_disc64_tv_200_iterations():
     """The 64^2 TV disc reconstruction after its 200 iterations."""
     w = make("disc64", seed=0)
