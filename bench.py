@@ -477,7 +477,10 @@ def run_mixed(P, S, np, torch, device, stream, flush, max_iters):
     prms = [P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"], xi=p[2],
                           iters=max_iters, gap_every=10, tol=1e-4) for w, p in zip(ws, probs)]
     geos, fs, us = [p[0].handle for p in probs], [p[1] for p in probs], [p[3] for p in probs]
-    P.pat_reconstruct_batched(geos, fs, prms, us, stream)  # warm-up (also computes the K sums)
+    # warm-up: computes the K sums of every geometry and loads the kernels
+    P.pat_reconstruct_batched(geos, fs, [P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"],
+                                                       gamma=w["gamma"], xi=p[2], iters=20, gap_every=10)
+                                         for w, p in zip(ws, probs)], us, stream)
     flush.zero_()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -485,14 +488,44 @@ def run_mixed(P, S, np, torch, device, stream, flush, max_iters):
     e1.record(stream)
     e1.synchronize()
     t = e0.elapsed_time(e1) / 1e3
-    for p in probs:
-        p[0].close()
     its = [i["iters_done"] for i in infos]
     conv = sum(1 for i in infos if i["status"] == P.PAT_STATUS_CONVERGED)
-    return {"problems": len(ws), "seconds": t, "converged": conv, "tol": 1e-4, "max_iters": max_iters,
-            "iters_median": float(np.median(its)), "iters_max": int(max(its)),
-            "problem_iters_per_s": sum(its) / t,
-            "pixels": int(sum(w["n"] ** 2 for w in ws)), "samples": int(sum(w["det_xy"].shape[0] * w["n_t"] for w in ws))}
+    out = {"problems": len(ws), "seconds": t, "converged": conv, "tol": 1e-4, "max_iters": max_iters,
+           "iters_median": float(np.median(its)), "iters_max": int(max(its)),
+           "problem_iters_per_s": sum(its) / t, "step_ratio": 1.0,
+           "pixels": int(sum(w["n"] ** 2 for w in ws)), "samples": int(sum(w["det_xy"].shape[0] * w["n_t"] for w in ws))}
+    # the TGV problems with the balance picked by the batched probe tuner (TV and dTV keep
+    # s = 1: short probes overshoot for them); probe time included
+    tg = [k for k, w in enumerate(ws) if w["reg"] == P.PAT_TGV]
+    e0.record(stream)
+    best, _ = P.pat_tune_step_ratio_batched([geos[k] for k in tg], [fs[k] for k in tg], [prms[k] for k in tg],
+                                            [1.0, 3.0, 10.0, 30.0], 300, stream)
+    e1.record(stream)
+    e1.synchronize()
+    probe_s = e0.elapsed_time(e1) / 1e3
+    ratio = [1.0] * len(ws)
+    for k, b in zip(tg, best):
+        ratio[k] = b
+    prms2 = [P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"], xi=p[2],
+                           iters=max_iters, gap_every=10, tol=1e-4, step_ratio=r) for w, p, r in zip(ws, probs, ratio)]
+    flush.zero_()
+    e0.record(stream)
+    infos2 = P.pat_reconstruct_batched(geos, fs, prms2, us, stream)
+    e1.record(stream)
+    e1.synchronize()
+    t2 = e0.elapsed_time(e1) / 1e3
+    its2 = [i["iters_done"] for i in infos2]
+    out["tuned_tgv"] = {"probe_seconds": probe_s, "seconds": t2 + probe_s, "solve_seconds": t2,
+                        "converged": sum(1 for i in infos2 if i["status"] == P.PAT_STATUS_CONVERGED),
+                        "converged_tgv": sum(1 for k in tg if infos2[k]["status"] == P.PAT_STATUS_CONVERGED),
+                        "converged_tgv_paper_steps": sum(1 for k in tg if infos[k]["status"] == P.PAT_STATUS_CONVERGED),
+                        "tgv_problems": len(tg), "iters_median": float(np.median(its2)),
+                        "tgv_iters_median": float(np.median([its2[k] for k in tg])),
+                        "tgv_iters_median_paper_steps": float(np.median([its[k] for k in tg])),
+                        "step_ratios_tgv": best}
+    for p in probs:
+        p[0].close()
+    return out
 
 
 def run_preprocess(P, S, np, torch, device, stream, geo, w, flush):

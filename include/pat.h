@@ -186,6 +186,13 @@ int  pat_tune_step_ratio(const pat_geometry* g, const float* f_dev, const pat_pa
                          const double* candidates_host, int n_candidates, int probe_iters,
                          double* best_host, double* rel_gaps_host, void* stream);
 
+/* The same for `count` problems at once: every (problem, candidate) probe runs in one
+ * lockstep batch.  best_host receives count values, and rel_gaps_host (may be NULL)
+ * count * n_candidates values, problem-major. */
+int  pat_tune_step_ratio_batched(int count, const pat_geometry* const* g, const float* const* f_dev,
+                                 const pat_params* p, const double* candidates_host, int n_candidates,
+                                 int probe_iters, double* best_host, double* rel_gaps_host, void* stream);
+
 /* Box-restricted duality gap (Sec. 3.3.3, FP64 accumulation) of a primal point x and a
  * dual-feasible point y in the layouts of pat_params.  out4_host receives
  * {primal, dual, gap, rel_gap}; the call synchronises `stream`. */

@@ -35,7 +35,7 @@ EXPORTED = [
     "pat_direction_field", "pat_params_default", "pat_reconstruct", "pat_reconstruct_batched",
     "pat_steps", "pat_duality_gap", "pat_error_string", "pat_last_error", "pat_geometry_info",
     "pat_profile_enable", "pat_profile_read", "pat_kernel_launches", "pat_adjoint_noalloc",
-    "pat_tune_step_ratio", "pat_preprocess",
+    "pat_tune_step_ratio", "pat_tune_step_ratio_batched", "pat_preprocess",
     # learned warm start (include/pat_unet.h)
     "pat_conv3x3_forward", "pat_conv3x3_backward_data", "pat_conv3x3_backward_weight",
     "pat_unet_create", "pat_unet_destroy", "pat_unet_num_params", "pat_unet_get_params",
@@ -115,6 +115,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pat_steps": (i, [vp, ctypes.POINTER(pat_params), vp, vp, vp, vp, vp, vp]),
         "pat_duality_gap": (i, [vp, vp, ctypes.POINTER(pat_params), vp, vp, ctypes.POINTER(d), vp]),
         "pat_preprocess": (i, [vp, vp, vp, ctypes.POINTER(d), d, vp, vp]),
+        "pat_tune_step_ratio_batched": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(pat_params),
+                                            ctypes.POINTER(d), i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]),
         "pat_tune_step_ratio": (i, [vp, vp, ctypes.POINTER(pat_params), ctypes.POINTER(d), i, i, ctypes.POINTER(d),
                                     ctypes.POINTER(d), vp]),
         "pat_error_string": (ctypes.c_char_p, [i]),
@@ -266,6 +268,20 @@ def pat_tune_step_ratio(g: int, f_dev, params: pat_params, candidates, probe_ite
     _check(load().pat_tune_step_ratio(g, _ptr(f_dev), ctypes.byref(params), c, len(candidates), probe_iters,
                                       ctypes.byref(best), gaps, _stream(stream)), "pat_tune_step_ratio")
     return best.value, list(gaps)
+
+
+def pat_tune_step_ratio_batched(geoms, fs, params, candidates, probe_iters: int, stream=None):
+    """Returns ([best s per problem], [[relative gap of each probe] per problem])."""
+    n, c = len(geoms), len(candidates)
+    G = (ctypes.c_void_p * n)(*geoms)
+    F = (ctypes.c_void_p * n)(*[_ptr(f) for f in fs])
+    Pp = (pat_params * n)(*params)
+    C = (ctypes.c_double * c)(*[float(v) for v in candidates])
+    best = (ctypes.c_double * n)()
+    gaps = (ctypes.c_double * (n * c))()
+    _check(load().pat_tune_step_ratio_batched(n, G, F, Pp, C, c, probe_iters, best, gaps, _stream(stream)),
+           "pat_tune_step_ratio_batched")
+    return list(best), [list(gaps[i * c:(i + 1) * c]) for i in range(n)]
 
 
 def pat_preprocess(g: int, p_dev, pcal_dev, xp, eps_rel: float, f_dev, stream=None) -> None:

@@ -1556,47 +1556,77 @@ extern "C" int pat_reconstruct_batched(int count, const pat_geometry* const* g, 
     return PAT_OK;
 }
 
-// Probe-based choice of the primal-dual balance: every candidate s runs probe_iters
-// iterations from the same start as one lockstep batch, and the one with the smallest
-// relative gap wins.  The probes' images go to scratch; nothing else is written.
+// Probe-based choice of the primal-dual balance: every (problem, candidate s) pair runs
+// probe_iters iterations from the problem's start, all as one lockstep batch, and for each
+// problem the candidate with the smallest relative gap wins.  The probes' images go to
+// scratch; nothing else is written.
+static int tune_impl(int count, const pat_geometry* const* g, const float* const* f, const pat_params* p,
+                     const double* cand, int n_cand, int probe_iters, double* best, double* gaps, cudaStream_t st,
+                     const char* who) {
+    if (count <= 0 || !g || !f || !p || !cand || !best || n_cand <= 0 || n_cand > 64 || probe_iters <= 0)
+        return fail(PAT_ERR_INVALID_ARG, std::string(who) + ": NULL argument, 1..64 candidates and probe_iters > 0");
+    for (int i = 0; i < n_cand; ++i)
+        if (!(cand[i] > 0) || !std::isfinite(cand[i]))
+            return fail(PAT_ERR_INVALID_ARG, std::string(who) + ": candidates must be finite and > 0");
+    size_t scratch_floats = 0;
+    for (int b = 0; b < count; ++b) {
+        int rc = validate(g[b], &p[b], who);
+        if (rc) return rc;
+        if (!f[b]) return fail(PAT_ERR_INVALID_ARG, std::string(who) + ": NULL data");
+        scratch_floats += (size_t)g[b]->desc.n * g[b]->desc.n * n_cand;
+    }
+    float* scratch = nullptr;
+    PAT_CUDA(cudaMallocAsync(&scratch, scratch_floats * sizeof(float), st));
+    const int B = count * n_cand;
+    std::vector<const pat_geometry*> gg(B);
+    std::vector<const float*> ff(B);
+    std::vector<pat_params> pp(B);
+    std::vector<float*> uu(B);
+    std::vector<pat_info> ii(B);
+    size_t off = 0;
+    for (int b = 0; b < count; ++b)
+        for (int c = 0; c < n_cand; ++c) {
+            const int k = b * n_cand + c;
+            gg[k] = g[b];
+            ff[k] = f[b];
+            pp[k] = p[b];
+            pp[k].step_ratio = cand[c];
+            pp[k].adapt = PAT_ADAPT_NONE;
+            pp[k].iters = probe_iters;
+            pp[k].tol = 0.0;
+            pp[k].gap_every = 0;
+            pp[k].x_out_dev = pp[k].xbar_out_dev = pp[k].y_out_dev = nullptr;
+            uu[k] = scratch + off;
+            off += (size_t)g[b]->desc.n * g[b]->desc.n;
+        }
+    int rc = run_batch(B, gg.data(), ff.data(), pp.data(), uu.data(), ii.data(), st, who);
+    cudaFreeAsync(scratch, st);
+    if (rc) return rc;
+    for (int b = 0; b < count; ++b) {
+        int bi = 0;
+        for (int c = 0; c < n_cand; ++c) {
+            const double gc = ii[b * n_cand + c].rel_gap;
+            if (gaps) gaps[b * n_cand + c] = gc;
+            if (gc < ii[b * n_cand + bi].rel_gap) bi = c;
+        }
+        best[b] = cand[bi];
+    }
+    return PAT_OK;
+}
+
 extern "C" int pat_tune_step_ratio(const pat_geometry* g, const float* f_dev, const pat_params* p,
                                    const double* candidates_host, int n_candidates, int probe_iters,
                                    double* best_host, double* rel_gaps_host, void* stream) {
-    int rc = validate(g, p, "pat_tune_step_ratio");
-    if (rc) return rc;
-    if (!f_dev || !candidates_host || !best_host || n_candidates <= 0 || n_candidates > 64 || probe_iters <= 0)
-        return fail(PAT_ERR_INVALID_ARG, "pat_tune_step_ratio: NULL argument, 1..64 candidates and probe_iters > 0");
-    for (int i = 0; i < n_candidates; ++i)
-        if (!(candidates_host[i] > 0) || !std::isfinite(candidates_host[i]))
-            return fail(PAT_ERR_INVALID_ARG, "pat_tune_step_ratio: candidates must be finite and > 0");
-    cudaStream_t st = (cudaStream_t)stream;
-    const size_t NN = (size_t)g->desc.n * g->desc.n;
-    float* scratch = nullptr;
-    PAT_CUDA(cudaMallocAsync(&scratch, NN * sizeof(float) * n_candidates, st));
-    std::vector<const pat_geometry*> gg(n_candidates, g);
-    std::vector<const float*> ff(n_candidates, f_dev);
-    std::vector<pat_params> pp(n_candidates, *p);
-    std::vector<float*> uu(n_candidates);
-    std::vector<pat_info> ii(n_candidates);
-    for (int i = 0; i < n_candidates; ++i) {
-        pp[i].step_ratio = candidates_host[i];
-        pp[i].adapt = PAT_ADAPT_NONE;
-        pp[i].iters = probe_iters;
-        pp[i].tol = 0.0;
-        pp[i].gap_every = 0;
-        pp[i].x_out_dev = pp[i].xbar_out_dev = pp[i].y_out_dev = nullptr;
-        uu[i] = scratch + NN * i;
-    }
-    rc = run_batch(n_candidates, gg.data(), ff.data(), pp.data(), uu.data(), ii.data(), st, "pat_tune_step_ratio");
-    cudaFreeAsync(scratch, st);
-    if (rc) return rc;
-    int best = 0;
-    for (int i = 0; i < n_candidates; ++i) {
-        if (rel_gaps_host) rel_gaps_host[i] = ii[i].rel_gap;
-        if (ii[i].rel_gap < ii[best].rel_gap) best = i;
-    }
-    *best_host = candidates_host[best];
-    return PAT_OK;
+    return tune_impl(1, &g, &f_dev, p, candidates_host, n_candidates, probe_iters, best_host, rel_gaps_host,
+                     (cudaStream_t)stream, "pat_tune_step_ratio");
+}
+
+extern "C" int pat_tune_step_ratio_batched(int count, const pat_geometry* const* g, const float* const* f_dev,
+                                           const pat_params* p, const double* candidates_host, int n_candidates,
+                                           int probe_iters, double* best_host, double* rel_gaps_host,
+                                           void* stream) {
+    return tune_impl(count, g, f_dev, p, candidates_host, n_candidates, probe_iters, best_host, rel_gaps_host,
+                     (cudaStream_t)stream, "pat_tune_step_ratio_batched");
 }
 
 extern "C" int pat_steps(const pat_geometry* g, const pat_params* p, float* sig_q_dev, float* tau_u_dev,

@@ -308,6 +308,18 @@ def test_replays_end_once_every_problem_has_stopped():
     assert launches <= 6 * (ib["iters_done"] + 2 * 8 * 10 + 20) + 50
 
 
+def test_tune_step_ratio_batched_equals_single_problem_tuning():
+    ws = [make("small", seed=13 + k, reg=k % 2, beta=0.5) for k in range(3)]
+    geos = [P.Geometry(w["n"], w["det_xy"], w["n_t"], w["r0"], w["dr"], w["quad_m"]) for w in ws]
+    fs = [dev(w["f"]) for w in ws]
+    prms = [P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"]) for w in ws]
+    cands = [0.5, 2.0, 8.0]
+    best, gaps = P.pat_tune_step_ratio_batched([g.handle for g in geos], fs, prms, cands, 30)
+    for k in range(3):
+        b1, g1 = P.pat_tune_step_ratio(geos[k].handle, fs[k], prms[k], cands, 30)
+        assert b1 == best[k] and g1 == gaps[k]
+
+
 def test_disc64_tv_200_iterations():
     """The 64^2 TV disc reconstruction after its 200 iterations."""
     w = make("disc64", seed=0)
