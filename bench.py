@@ -350,6 +350,11 @@ def run_gb300(args) -> int:
                         "rel_gap": info["rel_gap"], "reached": info["status"] == P.PAT_STATUS_CONVERGED}
         ttg["speedup_vs_paper_steps"] = ttg["paper_steps"]["seconds"] / ttg["tuned"]["seconds"]
 
+    # ---- the wavelet model (PAT_WAV) on the same data: iterations/s and time to gap ----
+    wav = None
+    if not args.no_wavelet:
+        wav = run_wavelet_leg(P, torch, geo, f, u, stream, flush, args)
+
     # ---- measurement pre-processing (Sec. 4.3) on this geometry ----
     prep = None
     if not args.no_prep:
@@ -416,7 +421,7 @@ def run_gb300(args) -> int:
                            "points_on_grid_per_K": pts, "final_rel_gap": infos[-1]["rel_gap"]},
                 "roofline": roofline, "phases": phases, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "time_to_gap": ttg,
-                "batched": batched, "mixed_batch": mixed, "warm_start": warm, "preprocess": prep,
+                "batched": batched, "mixed_batch": mixed, "warm_start": warm, "preprocess": prep, "wavelet": wav,
                 "wall_s_timed": wall, "profiled_ms_per_step": sum(prof_ms) / len(prof_ms)}
         print(json.dumps(line), flush=True)
     geo.close()
@@ -525,6 +530,35 @@ def run_mixed(P, S, np, torch, device, stream, flush, max_iters):
                         "step_ratios_tgv": best}
     for p in probs:
         p[0].close()
+    return out
+
+
+def run_wavelet_leg(P, torch, geo, f, u, stream, flush, args):
+    """PAT_WAV (Sec. 2.2, alpha 0.02, 4 levels) on the benchmark's geometry and data:
+    1000 fixed iterations (gap every 10), then the time to rel gap 1e-4 with the paper's
+    steps and with the probe-tuned balance (probe time included)."""
+    def run(iters, tol, ratio):
+        prm = P.make_params(reg=P.PAT_WAV, alpha=0.02, iters=iters, tol=tol, gap_every=10, wavelet_levels=4,
+                            step_ratio=ratio)
+        flush.zero_()
+        return P.pat_reconstruct(geo.handle, f, prm, u, stream)
+    run(50, 0.0, 1.0)
+    fixed = run(1000, 0.0, 1.0)
+    out = {"alpha": 0.02, "levels": 4, "iters_per_s": 1000 / (fixed["ms"] / 1e3), "ms_per_1000_iters": fixed["ms"]}
+    paper = run(args.ttg_max_iters, 1e-4, 1.0)
+    out["time_to_gap_paper_steps"] = {"iters": paper["iters_done"], "seconds": paper["ms"] / 1e3,
+                                      "reached": paper["status"] == P.PAT_STATUS_CONVERGED}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    best, gaps = P.pat_tune_step_ratio(geo.handle, f, P.make_params(reg=P.PAT_WAV, alpha=0.02, wavelet_levels=4),
+                                       [1.0, 3.0, 10.0, 30.0], args.probe_iters, stream)
+    e1.record(stream)
+    e1.synchronize()
+    probe_s = e0.elapsed_time(e1) / 1e3
+    tuned = run(args.ttg_max_iters, 1e-4, best)
+    out["time_to_gap_tuned"] = {"step_ratio": best, "probe_seconds": probe_s, "iters": tuned["iters_done"],
+                                "seconds": probe_s + tuned["ms"] / 1e3,
+                                "reached": tuned["status"] == P.PAT_STATUS_CONVERGED}
     return out
 
 
@@ -668,6 +702,7 @@ def main(argv=None) -> int:
     ap.add_argument("--warm-steps", type=int, default=2000)
     ap.add_argument("--warm-label-iters", type=int, default=10000, help="iteration cap of the training labels")
     ap.add_argument("--no-prep", action="store_true")
+    ap.add_argument("--no-wavelet", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -43,6 +43,10 @@ extern "C" {
 #define PAT_TGV  1   /* R(u) = min_v ||grad u - v|| + beta ||E v||    Sec. 2.1, eq. (min_TGV) */
 #define PAT_DTV  2   /* R(u) = ||D_xi grad u||_{1,2}, D_xi = I - gamma xi xi^T (not in the
                         paper; the directional TV of Ehrhardt and Betcke)                  */
+#define PAT_WAV  3   /* R(u) = ||W u||_1, Sec. 2.2 eq. (min_wav): W an orthonormal 2-D
+                        wavelet transform (Daubechies-4, periodic, pat_params.wavelet_levels
+                        levels, Mallat layout) standing in for the paper's dual-tree complex
+                        transform; W^-1 = W^T as for the paper's tight frame              */
 
 #define PAT_PRECOND_DIAG     0  /* Pock-Chambolle diagonal steps (alpha = 1): sigma_i =
                                    1/sum_j|A_ij|, tau_j = 1/sum_i|A_ij|   Sec. 3.3.2      */
@@ -125,6 +129,8 @@ typedef struct {
        their ratio (clamped to [1/2, 2], raised to 0.97^k after k adjustments; s stays in
        [1e-3, 1e3]). */
     int    adapt;
+    /* PAT_WAV: levels J of the transform, 1..12, with N divisible by 2^J (0: 4) */
+    int    wavelet_levels;
 } pat_params;
 
 #define PAT_ADAPT_NONE     0
@@ -198,6 +204,11 @@ int  pat_tune_step_ratio_batched(int count, const pat_geometry* const* g, const 
  * {primal, dual, gap, rel_gap}; the call synchronises `stream`. */
 int  pat_duality_gap(const pat_geometry* g, const float* f_dev, const pat_params* p,
                      const float* x_dev, const float* y_dev, double* out4_host, void* stream);
+
+/* ---- the wavelet transform of PAT_WAV ------------------------------------------------ */
+/* out = W in (inverse = 0) or W^T in = W^-1 in (inverse != 0) for N x N images, with the
+ * transform of PAT_WAV (`levels` levels).  in and out are distinct device buffers. */
+int  pat_wavelet_transform(int n, int levels, const float* in_dev, float* out_dev, int inverse, void* stream);
 
 /* ---- measurement pre-processing (Sec. 4.3) ------------------------------------------ */
 /* Data f (D*T, detector-major) for the reconstruction from measured pressures p and the

@@ -25,7 +25,7 @@ PAT_ERR_OOM = -3
 PAT_ERR_NONFINITE = -4
 PAT_ERR_TIMEOUT = -5
 
-PAT_TV, PAT_TGV, PAT_DTV = 0, 1, 2
+PAT_TV, PAT_TGV, PAT_DTV, PAT_WAV = 0, 1, 2, 3
 PAT_PRECOND_DIAG, PAT_PRECOND_SCALAR2 = 0, 1
 PAT_STATUS_CONVERGED, PAT_STATUS_MAXITER, PAT_STATUS_DIVERGED = 0, 1, 2
 PAT_ADAPT_NONE, PAT_ADAPT_BALANCE = 0, 1
@@ -35,7 +35,7 @@ EXPORTED = [
     "pat_direction_field", "pat_params_default", "pat_reconstruct", "pat_reconstruct_batched",
     "pat_steps", "pat_duality_gap", "pat_error_string", "pat_last_error", "pat_geometry_info",
     "pat_profile_enable", "pat_profile_read", "pat_kernel_launches", "pat_adjoint_noalloc",
-    "pat_tune_step_ratio", "pat_tune_step_ratio_batched", "pat_preprocess",
+    "pat_tune_step_ratio", "pat_tune_step_ratio_batched", "pat_preprocess", "pat_wavelet_transform",
     # learned warm start (include/pat_unet.h)
     "pat_conv3x3_forward", "pat_conv3x3_backward_data", "pat_conv3x3_backward_weight",
     "pat_unet_create", "pat_unet_destroy", "pat_unet_num_params", "pat_unet_get_params",
@@ -67,7 +67,8 @@ class pat_params(ctypes.Structure):
                 ("theta", ctypes.c_double), ("box_u", ctypes.c_double), ("box_v", ctypes.c_double),
                 ("x0_dev", ctypes.c_void_p), ("xbar0_dev", ctypes.c_void_p), ("y0_dev", ctypes.c_void_p),
                 ("x_out_dev", ctypes.c_void_p), ("xbar_out_dev", ctypes.c_void_p),
-                ("y_out_dev", ctypes.c_void_p), ("step_ratio", ctypes.c_double), ("adapt", ctypes.c_int)]
+                ("y_out_dev", ctypes.c_void_p), ("step_ratio", ctypes.c_double), ("adapt", ctypes.c_int),
+                ("wavelet_levels", ctypes.c_int)]
 
 
 class pat_unet_desc(ctypes.Structure):
@@ -115,6 +116,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pat_steps": (i, [vp, ctypes.POINTER(pat_params), vp, vp, vp, vp, vp, vp]),
         "pat_duality_gap": (i, [vp, vp, ctypes.POINTER(pat_params), vp, vp, ctypes.POINTER(d), vp]),
         "pat_preprocess": (i, [vp, vp, vp, ctypes.POINTER(d), d, vp, vp]),
+        "pat_wavelet_transform": (i, [i, i, vp, vp, i, vp]),
         "pat_tune_step_ratio_batched": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(pat_params),
                                             ctypes.POINTER(d), i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]),
         "pat_tune_step_ratio": (i, [vp, vp, ctypes.POINTER(pat_params), ctypes.POINTER(d), i, i, ctypes.POINTER(d),
@@ -215,7 +217,8 @@ def pat_params_default() -> pat_params:
 
 def make_params(reg=PAT_TV, alpha=0.05, beta=1.0, gamma=0.95, xi=None, iters=100, tol=0.0, gap_every=10,
                 precond=PAT_PRECOND_DIAG, theta=1.0, box_u=2.0, box_v=4.0, x0=None, xbar0=None, y0=None,
-                x_out=None, xbar_out=None, y_out=None, step_ratio=1.0, adapt=PAT_ADAPT_NONE) -> pat_params:
+                x_out=None, xbar_out=None, y_out=None, step_ratio=1.0, adapt=PAT_ADAPT_NONE,
+                wavelet_levels=4) -> pat_params:
     p = pat_params_default()
     p.reg, p.alpha, p.beta, p.gamma = reg, alpha, beta, gamma
     p.xi_dev = _ptr(xi)
@@ -223,7 +226,7 @@ def make_params(reg=PAT_TV, alpha=0.05, beta=1.0, gamma=0.95, xi=None, iters=100
     p.theta, p.box_u, p.box_v = theta, box_u, box_v
     p.x0_dev, p.xbar0_dev, p.y0_dev = _ptr(x0), _ptr(xbar0), _ptr(y0)
     p.x_out_dev, p.xbar_out_dev, p.y_out_dev = _ptr(x_out), _ptr(xbar_out), _ptr(y_out)
-    p.step_ratio, p.adapt = step_ratio, adapt
+    p.step_ratio, p.adapt, p.wavelet_levels = step_ratio, adapt, wavelet_levels
     # keep the buffers alive as long as the parameter block that points at them
     p._keep = [xi, x0, xbar0, y0, x_out, xbar_out, y_out]
     return p
@@ -282,6 +285,11 @@ def pat_tune_step_ratio_batched(geoms, fs, params, candidates, probe_iters: int,
     _check(load().pat_tune_step_ratio_batched(n, G, F, Pp, C, c, probe_iters, best, gaps, _stream(stream)),
            "pat_tune_step_ratio_batched")
     return list(best), [list(gaps[i * c:(i + 1) * c]) for i in range(n)]
+
+
+def pat_wavelet_transform(n: int, levels: int, in_dev, out_dev, inverse: bool = False, stream=None) -> None:
+    _check(load().pat_wavelet_transform(n, levels, _ptr(in_dev), _ptr(out_dev), 1 if inverse else 0, _stream(stream)),
+           "pat_wavelet_transform")
 
 
 def pat_preprocess(g: int, p_dev, pcal_dev, xp, eps_rel: float, f_dev, stream=None) -> None:

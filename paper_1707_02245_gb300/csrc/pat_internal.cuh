@@ -224,6 +224,44 @@ int forward_row_blocks(const pat_geometry* g);    // blocks of one forward launc
 int forward_rows_per_block();
 
 // Host entry points implemented in projector.cu and used by pdhg.cu
+// ---- the wavelet model (wavelet.cu) ----
+struct WavPrimalArgs {   // u <- u - T (K^T q + W^T r) / s, ubar, and the next parity's reset
+    int n;
+    float theta;
+    const float* tau_u;
+    const float* step_mul;
+    KtView kt;
+    const float* wtr;
+    float* u;
+    float* u_old;        // NULL, or receives u before the step (gap iterations)
+    float* ubar;         // plain N*N
+    float* ubar_pad;     // (N+2)^2, border zero
+    int* kt_clear;
+    unsigned* qmax_next;
+    const int* stop;
+    int* iter;
+};
+struct WavGapArgs {
+    int n, terms;
+    const float* wu;     // W u
+    KtView kt;
+    const float* wtr;    // W^T r
+    const float* u;
+    const float* u_old;
+    double* partials;
+    const int* stop;
+};
+bool wav_levels_ok(int n, int levels);
+void wav_abs_sums(int n, int levels, std::vector<double>& rows, std::vector<double>& cols);
+int launch_wav_analysis(const float* in, int N, int levels, float* out, float* scratch, const int* stop, cudaStream_t st);
+int launch_wav_synthesis(const float* in, int N, int levels, float* out, float* scratch, const int* stop,
+                         cudaStream_t st);
+int launch_wav_dual(float* r, const float* wub, const float* sig_r, const float* step_mul, float alpha, long long nn,
+                    const int* stop, cudaStream_t st);
+int launch_wav_primal(const WavPrimalArgs& a, cudaStream_t st);
+int launch_wav_gap_pixels(const WavGapArgs& a, int nblocks, cudaStream_t st);
+int launch_wav_tau(const float* kcol, const double* wcol, float* tau, long long nn, cudaStream_t st);
+
 int ensure_precond(const pat_geometry* g, cudaStream_t st);
 int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y, cudaStream_t st);
 // K^T y into an N*N float image (allocates its scratch from the stream-ordered pool).

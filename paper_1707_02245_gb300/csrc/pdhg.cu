@@ -791,7 +791,13 @@ static int validate(const pat_geometry* g, const pat_params* p, const char* who)
         return fail(PAT_ERR_INVALID_ARG, buf);
     };
     if (!g || !p) return bad("NULL geometry or params");
-    if (p->reg < PAT_TV || p->reg > PAT_DTV) return bad("reg must be PAT_TV, PAT_TGV or PAT_DTV");
+    if (p->reg < PAT_TV || p->reg > PAT_WAV) return bad("reg must be PAT_TV, PAT_TGV, PAT_DTV or PAT_WAV");
+    if (p->reg == PAT_WAV) {
+        const int J = p->wavelet_levels > 0 ? p->wavelet_levels : 4;
+        if (!wav_levels_ok(g->desc.n, J)) return bad("PAT_WAV needs 1..12 levels and N divisible by 2^levels");
+        if (p->precond != PAT_PRECOND_DIAG) return bad("PAT_WAV uses the diagonal steps only");
+        if (p->adapt != PAT_ADAPT_NONE) return bad("PAT_WAV has no adaptive balance");
+    }
     if (!(p->alpha >= 0) || !std::isfinite(p->alpha)) return bad("alpha must be finite and >= 0");
     if (!(p->beta >= 0) || !std::isfinite(p->beta)) return bad("beta must be finite and >= 0");
     if (p->reg == PAT_DTV && (!(p->gamma >= 0) || !(p->gamma <= 1))) return bad("gamma must be in [0, 1]");
@@ -1253,9 +1259,306 @@ static int run_iterations(const IterPlan& ip, const char* base, int iters, int g
     return PAT_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// the wavelet model (Sec. 2.2 eq. (min_wav)): Algorithm 1 with grad -> W and div -> -W^T
+// (Sec. 3.3).  One problem at a time; the periodic part of the loop is a captured graph
+// like the batch engine's, and it ends early once the problem has stopped.
+//   q^{n+1} = prox(q^n + S K ubar^n),  r^{n+1} = clip(r^n + S_r W ubar^n, alpha),
+//   u^{n+1} = u^n - T (K^T q^{n+1} + W^T r^{n+1}),  ubar^{n+1} = u^{n+1} + theta (u^{n+1} - u^n)
+// ---------------------------------------------------------------------------------
+static int wav_levels_of(const pat_params* p) { return p->wavelet_levels > 0 ? p->wavelet_levels : 4; }
+
+// sigma_q, tau_u and sigma_r of the wavelet model: the alpha = 1 diagonal rule on A = (K; W)
+static int wav_steps(const pat_geometry* g, int levels, float* sig_q, float* tau_u, float* sig_r, double s_ratio,
+                     cudaStream_t st) {
+    const int N = g->desc.n;
+    const long long NN = (long long)N * N, S = (long long)g->desc.n_det * g->desc.n_t;
+    int rc = ensure_precond(g, st);
+    if (rc) return rc;
+    std::vector<double> rows, cols;
+    wav_abs_sums(N, levels, rows, cols);
+    if (sig_q) {
+        k_sig_q<<<ceil_div(S, 256), 256, 0, st>>>(g->pc.krow, sig_q, S);
+        PAT_LAUNCH_CHECK("k_sig_q");
+        if (s_ratio != 1.0) {
+            k_scale_f32<<<ceil_div(S, 256), 256, 0, st>>>(sig_q, S, (float)(1.0 / s_ratio));
+            PAT_LAUNCH_CHECK("k_scale_f32");
+        }
+    }
+    if (tau_u) {
+        double* wcol = nullptr;
+        PAT_CUDA(cudaMallocAsync(&wcol, NN * sizeof(double), st));
+        rc = cudaMemcpyAsync(wcol, cols.data(), NN * sizeof(double), cudaMemcpyHostToDevice, st) == cudaSuccess
+                 ? launch_wav_tau(g->pc.kcol, wcol, tau_u, NN, st)
+                 : fail(PAT_ERR_CUDA, "wav_steps: copy");
+        if (!rc) PAT_CUDA(cudaStreamSynchronize(st));   // the host vector dies with this call
+        cudaFreeAsync(wcol, st);
+        if (rc) return rc;
+        if (s_ratio != 1.0) {
+            k_scale_f32<<<ceil_div(NN, 256), 256, 0, st>>>(tau_u, NN, (float)s_ratio);
+            PAT_LAUNCH_CHECK("k_scale_f32");
+        }
+    }
+    if (sig_r) {
+        std::vector<float> h((size_t)NN);
+        for (long long i = 0; i < NN; ++i) h[i] = rows[i] > 0 ? (float)(1.0 / rows[i] / s_ratio) : 1.f;
+        PAT_CUDA(cudaMemcpyAsync(sig_r, h.data(), NN * sizeof(float), cudaMemcpyHostToDevice, st));
+        PAT_CUDA(cudaStreamSynchronize(st));
+    }
+    return PAT_OK;
+}
+
+static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* p, float* u_out, pat_info* info,
+                       cudaStream_t st, const char* who) {
+    const int N = g->desc.n, J = wav_levels_of(p);
+    const long long NN = (long long)N * N, S = (long long)g->desc.n_det * g->desc.n_t;
+    const int n_data = forward_row_blocks(g);
+    const int n_pix = pix_blocks(N);
+    // workspace
+    enum { U, UOLD, UBAR, UPAD, UQUAD, Q, QW, KT, R, WB, WTR, SCR, SCR2, WU, TAU, SIGR, SIGQ, DPART, PPART, INFO, NBUF };
+    size_t sz[NBUF] = {NN * 4, NN * 4, NN * 4, (size_t)(N + 2) * (N + 2) * 4, (size_t)(N + 1) * (N + 1) * 16,
+                       (size_t)S * 4, (size_t)S * 4, (size_t)NN * 8, NN * 4, NN * 4, NN * 4, NN * 4, NN * 4, NN * 4,
+                       NN * 4, NN * 4, (size_t)S * 4, (size_t)n_data * GAP_DATA_TERMS * 8,
+                       (size_t)n_pix * GAP_PIX_TERMS * 8, sizeof(InfoDev)};
+    size_t off[NBUF], total = 0;
+    for (int i = 0; i < NBUF; ++i) {
+        off[i] = total;
+        total += align_up(sz[i]);
+    }
+    char* b = nullptr;
+    PAT_CUDA(cudaMallocAsync((void**)&b, total, st));
+    float *u = (float*)(b + off[U]), *u_old = (float*)(b + off[UOLD]), *ubar = (float*)(b + off[UBAR]);
+    float* upad = (float*)(b + off[UPAD]);
+    float4* uquad = (float4*)(b + off[UQUAD]);
+    float *q = (float*)(b + off[Q]), *qw = (float*)(b + off[QW]);
+    int* kt = (int*)(b + off[KT]);
+    float *r = (float*)(b + off[R]), *wb = (float*)(b + off[WB]), *wtr = (float*)(b + off[WTR]);
+    float *scr = (float*)(b + off[SCR]), *scr2 = (float*)(b + off[SCR2]), *wu = (float*)(b + off[WU]);
+    float *tau = (float*)(b + off[TAU]), *sigr = (float*)(b + off[SIGR]), *sigq = (float*)(b + off[SIGQ]);
+    double *dpart = (double*)(b + off[DPART]), *ppart = (double*)(b + off[PPART]);
+    InfoDev* in = (InfoDev*)(b + off[INFO]);
+    cudaEvent_t e0, e1;
+    PAT_CUDA(cudaEventCreate(&e0));
+    PAT_CUDA(cudaEventCreate(&e1));
+    PAT_CUDA(cudaEventRecord(e0, st));
+    int rc = wav_steps(g, J, sigq, tau, sigr, 1.0, st);
+    // start
+    if (!rc) {
+        auto cp = [&](float* dst, const float* src, long long n) -> int {
+            if (src) PAT_CUDA(cudaMemcpyAsync(dst, src, n * 4, cudaMemcpyDeviceToDevice, st));
+            else PAT_CUDA(cudaMemsetAsync(dst, 0, n * 4, st));
+            return PAT_OK;
+        };
+        rc = cp(u, p->x0_dev, NN);
+        if (!rc) rc = cp(ubar, p->xbar0_dev ? p->xbar0_dev : p->x0_dev, NN);
+        if (!rc) rc = cp(q, p->y0_dev, S);
+        if (!rc) rc = cp(r, p->y0_dev ? p->y0_dev + S : nullptr, NN);
+    }
+    if (!rc) {
+        PAT_CUDA(cudaMemsetAsync(in, 0, sizeof(InfoDev), st));
+        const double ratio = step_ratio_of(p);
+        const float mul[2] = {(float)ratio, (float)(1.0 / ratio)};
+        PAT_CUDA(cudaMemcpyAsync(in->step_mul, mul, sizeof mul, cudaMemcpyHostToDevice, st));
+        PAT_CUDA(cudaMemsetAsync(kt, 0, NN * 8, st));
+        dim3 blk(32, 8), grd(ceil_div(N + 2, 32), ceil_div(N + 2, 8));
+        k_pad<<<grd, blk, 0, st>>>(ubar, upad, N);
+        PAT_LAUNCH_CHECK("k_pad");
+        dim3 gq(ceil_div(N + 1, 32), ceil_div(N + 1, 8));
+        k_quads_from_pad<<<gq, blk, 0, st>>>(upad, uquad, N);
+        PAT_LAUNCH_CHECK("k_quads_from_pad");
+    }
+    int* stopped = nullptr;
+    void* dev = nullptr;
+    if (!rc) rc = cudaMallocAsync((void**)&stopped, sizeof(int), st) == cudaSuccess &&
+                          cudaMemsetAsync(stopped, 0, sizeof(int), st) == cudaSuccess
+                      ? PAT_OK
+                      : fail(PAT_ERR_CUDA, std::string(who) + ": stop counter");
+    // device argument blocks of the shared launchers (a batch of one)
+    std::vector<char> host;
+    Arena ar(host);
+    size_t fw_off[2], ad_off[2], fg_off, fi_off, fmap_off, amap_off, finmap_off;
+    const int nf = forward_row_blocks(g);
+    if (!rc) {
+        for (int par = 0; par < 2; ++par) {
+            FwdProxArgs fa = make_fwd_prox_args(g, uquad, q, f, sigq, -1.f, in->step_mul, qw, &in->qmax_bits[par],
+                                                &in->stop);
+            fw_off[par] = ar.put(&fa, 1);
+            AdjArgs aa = make_adj_args(g, q, qw, &in->qmax_bits[par], kt + (size_t)par * NN, &in->stop);
+            ad_off[par] = ar.put(&aa, 1);
+        }
+        FwdGapArgs ga = make_fwd_gap_args(g, u, nullptr, q, f, dpart, &in->stop);
+        fg_off = ar.put(&ga, 1);
+        FinalArgs fi{dpart, n_data, ppart, n_pix, p->alpha, 0.0, p->box_u, p->box_v, p->tol, PAT_WAV, PAT_ADAPT_NONE,
+                     in, stopped};
+        fi_off = ar.put(&fi, 1);
+        std::vector<int2> fm(nf), am(g->adj_items), fin(GAP_FINAL_BLOCKS);
+        for (int i = 0; i < nf; ++i) fm[i] = make_int2(0, i);
+        std::vector<std::pair<float, int>> order;
+        for (int i = 0; i < g->adj_items; ++i) order.push_back({g->adj_item_cost[i], i});
+        std::stable_sort(order.begin(), order.end(), [](const auto& a, const auto& c) { return a.first > c.first; });
+        for (int i = 0; i < g->adj_items; ++i) am[i] = make_int2(0, order[i].second);
+        for (int i = 0; i < GAP_FINAL_BLOCKS; ++i) fin[i] = make_int2(0, i);
+        fmap_off = ar.put(fm.data(), fm.size());
+        amap_off = ar.put(am.data(), am.size());
+        finmap_off = ar.put(fin.data(), fin.size());
+        rc = ar.upload(&dev, st);
+    }
+    const char* base = (const char*)dev;
+    auto iteration = [&](int it, bool gap, cudaStream_t s) -> int {
+        const int par = it & 1;
+        int e = launch_forward_prox_b((const FwdProxArgs*)(base + fw_off[par]), (const int2*)(base + fmap_off), nf, s);
+        if (!e) e = launch_wav_analysis(ubar, N, J, wb, scr, &in->stop, s);
+        if (!e) e = launch_wav_dual(r, wb, sigr, in->step_mul, (float)p->alpha, NN, &in->stop, s);
+        if (!e)
+            e = launch_adjoint_b((const AdjArgs*)(base + ad_off[par]), (const int2*)(base + amap_off), g->adj_items,
+                                 true, s);
+        if (!e) e = launch_wav_synthesis(r, N, J, wtr, scr, &in->stop, s);
+        WavPrimalArgs pa;
+        pa.n = N;
+        pa.theta = (float)p->theta;
+        pa.tau_u = tau;
+        pa.step_mul = in->step_mul;
+        pa.kt = kt_view(g, kt + (size_t)par * NN, &in->qmax_bits[par]);
+        pa.wtr = wtr;
+        pa.u = u;
+        pa.u_old = gap ? u_old : nullptr;
+        pa.ubar = ubar;
+        pa.ubar_pad = upad;
+        pa.kt_clear = kt + (size_t)(1 - par) * NN;
+        pa.qmax_next = &in->qmax_bits[1 - par];
+        pa.stop = &in->stop;
+        pa.iter = &in->iter;
+        if (!e) e = launch_wav_primal(pa, s);
+        if (!e) {
+            dim3 blk(32, 8), gq(ceil_div(N + 1, 32), ceil_div(N + 1, 8));
+            k_quads_from_pad<<<gq, blk, 0, s>>>(upad, uquad, N);
+            count_launch();
+            if (cudaGetLastError() != cudaSuccess) e = fail(PAT_ERR_CUDA, "k_quads_from_pad");
+        }
+        if (gap && !e) {
+            e = launch_wav_analysis(u, N, J, wu, scr2, &in->stop, s);
+            if (!e) e = launch_forward_gap_b((const FwdGapArgs*)(base + fg_off), (const int2*)(base + fmap_off), nf, s);
+            WavGapArgs wg{N, GAP_PIX_TERMS, wu, pa.kt, wtr, u, u_old, ppart, &in->stop};
+            if (!e) e = launch_wav_gap_pixels(wg, n_pix, s);
+            if (!e) {
+                k_gap_final_b<<<GAP_FINAL_BLOCKS, 256, 0, s>>>((const FinalArgs*)(base + fi_off),
+                                                              (const int2*)(base + finmap_off));
+                count_launch();
+                if (cudaGetLastError() != cudaSuccess) e = fail(PAT_ERR_CUDA, "k_gap_final_b");
+            }
+        }
+        return e;
+    };
+    const int iters = p->iters, ge = p->gap_every;
+    if (!rc && iters > 0) {
+        auto gap_due = [&](int it) { return (ge > 0 && (it + 1) % ge == 0) || it + 1 == iters; };
+        const int P = ge > 0 ? (ge % 2 == 0 ? ge : 2 * ge) : 2;
+        const int nper = (iters - 1) / P;
+        int start = 0;
+        bool all_stopped = false;
+        if (!prof_on() && nper >= 2) {
+            cudaGraph_t graph = nullptr;
+            cudaGraphExec_t exec = nullptr;
+            cudaStream_t ls = loop_stream();
+            cudaEvent_t fork = nullptr, join = nullptr;
+            cudaEventCreateWithFlags(&fork, cudaEventDisableTiming);
+            cudaEventCreateWithFlags(&join, cudaEventDisableTiming);
+            cudaEventRecord(fork, st);
+            cudaStreamWaitEvent(ls, fork, 0);
+            const long long l0 = pat_kernel_launches();
+            cudaError_t ce = cudaStreamBeginCapture(ls, cudaStreamCaptureModeThreadLocal);
+            for (int it = 0; it < P && !rc && ce == cudaSuccess; ++it) rc = iteration(it, ge > 0 && (it + 1) % ge == 0, ls);
+            cudaError_t e2 = cudaStreamEndCapture(ls, &graph);
+            if (ce == cudaSuccess) ce = e2;
+            if (!rc && ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+            const long long per_period = pat_kernel_launches() - l0;
+            int* snap = p->tol > 0 ? stop_snapshots() : nullptr;
+            cudaEvent_t ev[2] = {nullptr, nullptr};
+            bool pending[2] = {false, false};
+            if (snap)
+                for (int i = 0; i < 2 && ce == cudaSuccess; ++i) ce = cudaEventCreateWithFlags(&ev[i], cudaEventDisableTiming);
+            int launched = 0;
+            constexpr int CHUNK = 8;
+            for (int chunk = 0; !rc && ce == cudaSuccess && launched < nper; ++chunk) {
+                const int n = std::min(CHUNK, nper - launched);
+                for (int k = 0; k < n && ce == cudaSuccess; ++k) ce = cudaGraphLaunch(exec, ls);
+                launched += n;
+                if (!snap || ce != cudaSuccess) continue;
+                const int cur = chunk & 1, prev = cur ^ 1;
+                ce = cudaMemcpyAsync(&snap[cur], stopped, sizeof(int), cudaMemcpyDeviceToHost, ls);
+                if (ce == cudaSuccess) ce = cudaEventRecord(ev[cur], ls);
+                pending[cur] = ce == cudaSuccess;
+                if (pending[prev] && ce == cudaSuccess) {
+                    ce = cudaEventSynchronize(ev[prev]);
+                    pending[prev] = false;
+                    if (ce == cudaSuccess && *(volatile int*)&snap[prev] >= 1) {
+                        all_stopped = true;
+                        break;
+                    }
+                }
+            }
+            for (int i = 0; i < 2; ++i)
+                if (ev[i]) {
+                    if (pending[i]) cudaEventSynchronize(ev[i]);
+                    cudaEventDestroy(ev[i]);
+                }
+            for (int k = 1; k < launched; ++k)
+                for (long long c = 0; c < per_period; ++c) count_launch();
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+            cudaEventRecord(join, ls);
+            cudaStreamWaitEvent(st, join, 0);
+            cudaEventDestroy(fork);
+            cudaEventDestroy(join);
+            if (!rc && ce != cudaSuccess) rc = cuda_fail(ce, "run_wavelet: graph");
+            start = nper * P;
+        }
+        for (int it = start; !rc && !all_stopped && it < iters; ++it) rc = iteration(it, gap_due(it), st);
+    }
+    // outputs: u, x = [u], xbar = [ubar], y = [q, r]
+    if (!rc) {
+        PAT_CUDA(cudaMemcpyAsync(u_out, u, NN * 4, cudaMemcpyDeviceToDevice, st));
+        if (p->x_out_dev) PAT_CUDA(cudaMemcpyAsync(p->x_out_dev, u, NN * 4, cudaMemcpyDeviceToDevice, st));
+        if (p->xbar_out_dev) PAT_CUDA(cudaMemcpyAsync(p->xbar_out_dev, ubar, NN * 4, cudaMemcpyDeviceToDevice, st));
+        if (p->y_out_dev) {
+            PAT_CUDA(cudaMemcpyAsync(p->y_out_dev, q, S * 4, cudaMemcpyDeviceToDevice, st));
+            PAT_CUDA(cudaMemcpyAsync(p->y_out_dev + S, r, NN * 4, cudaMemcpyDeviceToDevice, st));
+        }
+    }
+    InfoDev h{};
+    if (!rc) rc = cudaMemcpyAsync(&h, in, sizeof(InfoDev), cudaMemcpyDeviceToHost, st) == cudaSuccess ? 0 : PAT_ERR_CUDA;
+    cudaEventRecord(e1, st);
+    if (dev) cudaFreeAsync(dev, st);
+    if (stopped) cudaFreeAsync(stopped, st);
+    cudaFreeAsync(b, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    if (!rc && se != cudaSuccess) rc = cuda_fail(se, who);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    prof_collect();
+    if (rc) return rc;
+    if (info) {
+        info->iters_done = iters == 0 ? 0 : h.iters_done;
+        info->status = h.stop ? h.status : PAT_STATUS_MAXITER;
+        info->primal = h.primal;
+        info->dual = h.dual;
+        info->gap = h.gap;
+        info->rel_gap = h.rel_gap;
+        info->residual = h.residual;
+        info->ms = ms;
+        info->step_ratio = (double)h.step_mul[0];
+    }
+    if (h.status == PAT_STATUS_DIVERGED) return fail(PAT_ERR_NONFINITE, std::string(who) + ": duality gap not finite");
+    return PAT_OK;
+}
+
 static int run_batch(int B, const pat_geometry* const* g, const float* const* f, const pat_params* p,
                      float* const* u_out, pat_info* infos, cudaStream_t st, const char* who) {
     if (B == 0) return PAT_OK;
+    for (int b = 0; b < B; ++b)
+        if (p[b].reg == PAT_WAV) return fail(PAT_ERR_INVALID_ARG, std::string(who) + ": PAT_WAV has no batch engine");
     for (int b = 1; b < B; ++b)
         if (p[b].iters != p[0].iters || p[b].gap_every != p[0].gap_every)
             return fail(PAT_ERR_INVALID_ARG, std::string(who) + ": a batch needs equal iters and gap_every");
@@ -1507,6 +1810,7 @@ extern "C" void pat_params_default(pat_params* p) {
     p->box_v = 4.0;
     p->step_ratio = 1.0;
     p->adapt = PAT_ADAPT_NONE;
+    p->wavelet_levels = 4;
 }
 
 extern "C" int pat_reconstruct(const pat_geometry* g, const float* f_dev, const pat_params* p, float* u_dev,
@@ -1514,6 +1818,7 @@ extern "C" int pat_reconstruct(const pat_geometry* g, const float* f_dev, const 
     int rc = validate(g, p, "pat_reconstruct");
     if (rc) return rc;
     if (!f_dev || !u_dev) return fail(PAT_ERR_INVALID_ARG, "pat_reconstruct: NULL data or output");
+    if (p->reg == PAT_WAV) return run_wavelet(g, f_dev, p, u_dev, info, (cudaStream_t)stream, "pat_reconstruct");
     return run_batch(1, &g, &f_dev, p, &u_dev, info, (cudaStream_t)stream, "pat_reconstruct");
 }
 
@@ -1526,8 +1831,17 @@ extern "C" int pat_reconstruct_batched(int count, const pat_geometry* const* g, 
         if (rc) return rc;
         if (!f_dev[i] || !u_dev[i]) return fail(PAT_ERR_INVALID_ARG, "pat_reconstruct_batched: NULL data or output");
     }
-    // problems advance in lockstep; those sharing (iters, gap_every) run as one batch
+    // wavelet problems run one at a time; the others advance in lockstep, and those
+    // sharing (iters, gap_every) run as one batch
     std::vector<char> done(count, 0);
+    for (int i = 0; i < count; ++i)
+        if (p[i].reg == PAT_WAV) {
+            pat_info ii{};
+            int rc = run_wavelet(g[i], f_dev[i], &p[i], u_dev[i], &ii, (cudaStream_t)stream, "pat_reconstruct_batched");
+            if (infos) infos[i] = ii;
+            if (rc) return rc;
+            done[i] = 1;
+        }
     for (int i = 0; i < count; ++i) {
         if (done[i]) continue;
         std::vector<int> idx;
@@ -1574,6 +1888,37 @@ static int tune_impl(int count, const pat_geometry* const* g, const float* const
         if (rc) return rc;
         if (!f[b]) return fail(PAT_ERR_INVALID_ARG, std::string(who) + ": NULL data");
         scratch_floats += (size_t)g[b]->desc.n * g[b]->desc.n * n_cand;
+    }
+    bool any_wav = false;
+    for (int b = 0; b < count; ++b) any_wav = any_wav || p[b].reg == PAT_WAV;
+    if (any_wav) {
+        // wavelet problems have no batch engine: their probes run one after another
+        for (int b = 0; b < count; ++b) {
+            float* ub = nullptr;
+            PAT_CUDA(cudaMallocAsync(&ub, (size_t)g[b]->desc.n * g[b]->desc.n * sizeof(float), st));
+            int bi = 0;
+            std::vector<double> gc(n_cand);
+            int rc = PAT_OK;
+            for (int c = 0; c < n_cand && !rc; ++c) {
+                pat_params q = p[b];
+                q.step_ratio = cand[c];
+                q.adapt = PAT_ADAPT_NONE;
+                q.iters = probe_iters;
+                q.tol = 0.0;
+                q.gap_every = 0;
+                q.x_out_dev = q.xbar_out_dev = q.y_out_dev = nullptr;
+                pat_info ii{};
+                rc = p[b].reg == PAT_WAV ? run_wavelet(g[b], f[b], &q, ub, &ii, st, who)
+                                         : run_batch(1, &g[b], &f[b], &q, &ub, &ii, st, who);
+                gc[c] = ii.rel_gap;
+                if (gaps) gaps[b * n_cand + c] = ii.rel_gap;
+                if (gc[c] < gc[bi]) bi = c;
+            }
+            cudaFreeAsync(ub, st);
+            if (rc) return rc;
+            best[b] = cand[bi];
+        }
+        return PAT_OK;
     }
     float* scratch = nullptr;
     PAT_CUDA(cudaMallocAsync(&scratch, scratch_floats * sizeof(float), st));
@@ -1634,6 +1979,7 @@ extern "C" int pat_steps(const pat_geometry* g, const pat_params* p, float* sig_
     int rc = validate(g, p, "pat_steps");
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
+    if (p->reg == PAT_WAV) return wav_steps(g, wav_levels_of(p), sig_q_dev, tau_u_dev, sig_r_dev, step_ratio_of(p), st);
     const int N = g->desc.n;
     const long long NN = (long long)N * N, S = (long long)g->desc.n_det * g->desc.n_t;
     if (p->precond == PAT_PRECOND_SCALAR2) {
@@ -1747,6 +2093,8 @@ static int gap_impl(const pat_geometry* g, const float* f, const pat_params* p, 
 
 extern "C" int pat_duality_gap(const pat_geometry* g, const float* f_dev, const pat_params* p, const float* x_dev,
                                const float* y_dev, double* out4_host, void* stream) {
+    if (p && p->reg == PAT_WAV)
+        return fail(PAT_ERR_INVALID_ARG, "pat_duality_gap: not available for PAT_WAV (pat_reconstruct reports its gap)");
     int rc = validate(g, p, "pat_duality_gap");
     if (rc) return rc;
     if (!f_dev || !x_dev || !y_dev || !out4_host) return fail(PAT_ERR_INVALID_ARG, "pat_duality_gap: NULL argument");
