@@ -367,6 +367,9 @@ def run_gb300(args) -> int:
     mixed = None
     if args.mixed:
         mixed = run_mixed(P, S, np, torch, device, stream, flush, args.mixed_max_iters)
+    upd_hbm = None
+    if not args.no_update_hbm:
+        upd_hbm = run_update_hbm(P, S, np, torch, device, stream, flush)
     warm = None
     if args.warm:
         warm = run_warm_start(P, S, np, torch, device, stream, args)
@@ -422,6 +425,7 @@ def run_gb300(args) -> int:
                 "roofline": roofline, "phases": phases, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "time_to_gap": ttg,
                 "batched": batched, "mixed_batch": mixed, "warm_start": warm, "preprocess": prep, "wavelet": wav,
+                "update_hbm": upd_hbm,
                 "wall_s_timed": wall, "profiled_ms_per_step": sum(prof_ms) / len(prof_ms)}
         print(json.dumps(line), flush=True)
     geo.close()
@@ -448,6 +452,39 @@ def make_problem(P, np, torch, device, stream, w):
         P.pat_direction_field(n, side, w["eta"], xi, stream)
     u = torch.empty(n, n, device=device)
     return geo, f, xi, u
+
+
+def run_update_hbm(P, S, np, torch, device, stream, flush, count=16, n=512, iters=40):
+    """The fused update (k_update_b) where its state does not fit in L2: a lockstep batch
+    of ``count`` TGV^2 problems of n x n (vessel phantoms, 128 detectors, T = 2n), ``iters``
+    iterations with per-phase CUDA events.  Bytes per pixel: the algorithmic 18 floats
+    (read u, v2, r2, s3, tau; write u, v2, r2, s3, ubar) and the 30 the kernel moves (the
+    compensated low words, the bordered ubar, the ubar quad and the K^T clear besides)."""
+    ws = [S.workload_warm(700000 + s, n=n, n_det=128) for s in range(count)]
+    probs = [make_problem(P, np, torch, device, stream, w) for w in ws]
+    prms = [P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], iters=iters, gap_every=10) for w in ws]
+    geos, fs, us = [p[0].handle for p in probs], [p[1] for p in probs], [p[3] for p in probs]
+    P.pat_reconstruct_batched(geos, fs, prms, us, stream)        # warm-up (K sums, kernels)
+    flush.zero_()
+    P.pat_profile_read(reset=True)
+    P.pat_profile_enable(True)
+    P.pat_reconstruct_batched(geos, fs, prms, us, stream)
+    P.pat_profile_enable(False)
+    prof = P.pat_profile_read(reset=True)
+    for p in probs:
+        p[0].close()
+    ms, cnt = prof["update"]
+    avg_s = ms / cnt / 1e3
+    px = count * n * n
+    peaks = load_peaks()
+    alg = 18 * 4 * px / avg_s / 1e9
+    moved = 30 * 4 * px / avg_s / 1e9
+    return {"problems": count, "n": n, "pixels": px, "state_bytes": 30 * 4 * px, "launches": cnt,
+            "avg_us": avg_s * 1e6,
+            "roofline": {"bound": "hbm", "achieved": alg, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": alg / peaks["hbm_gbs"], "bytes_per_pixel": 72},
+            "moved_gb_per_s": moved, "moved_frac": moved / peaks["hbm_gbs"],
+            "phases_us": {k: (v[0] / v[1] * 1e3 if v[1] else None) for k, v in prof.items()}}
 
 
 def run_batched_tgv(P, S, np, torch, device, stream, count, iters, flush):
@@ -703,6 +740,7 @@ def main(argv=None) -> int:
     ap.add_argument("--warm-label-iters", type=int, default=10000, help="iteration cap of the training labels")
     ap.add_argument("--no-prep", action="store_true")
     ap.add_argument("--no-wavelet", action="store_true")
+    ap.add_argument("--no-update-hbm", action="store_true")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
