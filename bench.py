@@ -465,26 +465,27 @@ def run_update_hbm(P, S, np, torch, device, stream, flush, count=16, n=512, iter
     prms = [P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], iters=iters, gap_every=10) for w in ws]
     geos, fs, us = [p[0].handle for p in probs], [p[1] for p in probs], [p[3] for p in probs]
     P.pat_reconstruct_batched(geos, fs, prms, us, stream)        # warm-up (K sums, kernels)
+    px = count * n * n
+    peaks = load_peaks()
+    out = {"problems": count, "n": n, "pixels": px, "state_bytes": 30 * 4 * px}
     flush.zero_()
     P.pat_profile_read(reset=True)
     P.pat_profile_enable(True)
     P.pat_reconstruct_batched(geos, fs, prms, us, stream)
     P.pat_profile_enable(False)
     prof = P.pat_profile_read(reset=True)
-    for p in probs:
-        p[0].close()
     ms, cnt = prof["update"]
     avg_s = ms / cnt / 1e3
-    px = count * n * n
-    peaks = load_peaks()
     alg = 18 * 4 * px / avg_s / 1e9
     moved = 30 * 4 * px / avg_s / 1e9
-    return {"problems": count, "n": n, "pixels": px, "state_bytes": 30 * 4 * px, "launches": cnt,
-            "avg_us": avg_s * 1e6,
-            "roofline": {"bound": "hbm", "achieved": alg, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": alg / peaks["hbm_gbs"], "bytes_per_pixel": 72},
-            "moved_gb_per_s": moved, "moved_frac": moved / peaks["hbm_gbs"],
-            "phases_us": {k: (v[0] / v[1] * 1e3 if v[1] else None) for k, v in prof.items()}}
+    out.update({"launches": cnt, "avg_us": avg_s * 1e6,
+                "roofline": {"bound": "hbm", "achieved": alg, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": alg / peaks["hbm_gbs"], "bytes_per_pixel": 72},
+                "moved_gb_per_s": moved, "moved_frac": moved / peaks["hbm_gbs"],
+                "phases_us": {k: (v[0] / v[1] * 1e3 if v[1] else None) for k, v in prof.items()}})
+    for p in probs:
+        p[0].close()
+    return out
 
 
 def run_batched_tgv(P, S, np, torch, device, stream, count, iters, flush):

@@ -130,10 +130,13 @@ struct KtView {
     const unsigned* ymax_bits;  // max |y| as float bits
     const float* tile_kmax;     // per tile
     int tiles_x;
+    // the factor that turns tile (tx, ty)'s fixed-point sums into values: bound * 2^-30
+    __device__ __forceinline__ float inv_scale(int tx, int ty) const {
+        const float bound = __uint_as_float(*ymax_bits) * __ldg(&tile_kmax[ty * tiles_x + tx]);
+        return bound > 0.f ? bound * 9.313225746154785e-10f : (bound == 0.f ? 0.f : bound);
+    }
     __device__ __forceinline__ float at(int gx, int gy, int N) const {
-        const float bound = __uint_as_float(*ymax_bits) * __ldg(&tile_kmax[(gy / ATILE) * tiles_x + gx / ATILE]);
-        const float inv = bound > 0.f ? bound * 9.313225746154785e-10f : (bound == 0.f ? 0.f : bound);
-        return (float)__ldg(&acc[(size_t)gy * N + gx]) * inv;
+        return (float)__ldg(&acc[(size_t)gy * N + gx]) * inv_scale(gx / ATILE, gy / ATILE);
     }
 };
 

@@ -85,6 +85,14 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
     const float* r2_in = a.y_in + NN;
     const float tmul = __ldg(a.step_mul), smul = __ldg(a.step_mul + 1);
 
+    // fixed-point scales of the (at most 2 x 2) K^T tiles that the cells of U touch (the
+    // update tile lies inside one K^T tile; its high halo may reach the next ones)
+    __shared__ float s_kinv[2][2];
+    if (tid < 4) {
+        const int ktx = x0 / ATILE + (tid & 1), kty = y0 / ATILE + (tid >> 1);
+        s_kinv[tid >> 1][tid & 1] = (ktx * ATILE < N && kty * ATILE < N) ? a.kt.inv_scale(ktx, kty) : 0.f;
+    }
+
     // ---- stage 1: dual fields on the tile plus halo -------------------------------
     for (int c = tid; c < LX * LY; c += TX * TY) {
         const int lx = c % LX, ly = c / LX;
@@ -120,7 +128,8 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
             if (in) {
                 const int gi = gy * N + gx;
                 const float divr = s_r1m[ly][lx] - s_r1m[ly][lx - 1] + s_r2m[ly][lx] - s_r2m[ly - 1][lx];
-                const float w = a.kt.at(gx, gy, N);
+                const float w = (float)__ldg(&a.kt.acc[(size_t)gy * N + gx]) *
+                                s_kinv[gy / ATILE - y0 / ATILE][gx / ATILE - x0 / ATILE];
                 const float uo = __ldg(u_in + gi), uol = __ldg(a.xl_in + gi);
                 const float tu = (a.tau >= 0.f ? a.tau : __ldg(a.tau_u + gi)) * tmul;
                 float un = uo, unl = uol;

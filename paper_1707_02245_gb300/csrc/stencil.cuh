@@ -15,17 +15,20 @@ namespace pat {
 constexpr float kInvSqrt2f = 0.70710678118654752f;
 constexpr double kSqrt2 = 1.4142135623730951;
 
-// radius * p / max(radius, |p|) for a 2- or 3-vector (Sec. 3.2); 0 when both are 0.
+// radius * p / max(radius, |p|) for a 2- or 3-vector (Sec. 3.2).  Inside the ball p is
+// kept as it is; outside, the scale radius / |p| comes from one reciprocal square root
+// (a relative error of a few 1e-7, far inside the FP32 iterates' own).  With radius 0 the
+// result is 0.
 __device__ __forceinline__ void proj2(float& a, float& b, float radius) {
-    const float den = fmaxf(radius, sqrtf(a * a + b * b));
-    const float sc = den > 0.f ? radius / den : 0.f;
+    const float n2 = a * a + b * b;
+    const float sc = n2 > radius * radius ? radius * rsqrtf(n2) : 1.f;
     a *= sc;
     b *= sc;
 }
 
 __device__ __forceinline__ void proj3(float& a, float& b, float& c, float radius) {
-    const float den = fmaxf(radius, sqrtf(a * a + b * b + c * c));
-    const float sc = den > 0.f ? radius / den : 0.f;
+    const float n2 = a * a + b * b + c * c;
+    const float sc = n2 > radius * radius ? radius * rsqrtf(n2) : 1.f;
     a *= sc;
     b *= sc;
     c *= sc;
@@ -36,22 +39,37 @@ __device__ __forceinline__ void proj3(float& a, float& b, float& c, float radius
 // TV  r rows: |d_x^+| row sum 2a, |d_y^+| 2b; the group takes 1/max (1 if both vanish).
 // TGV r rows add the -I entry: 2a + 1, 2b + 1.
 // TGV s rows: ex, ey, (ex + ey)/sqrt 2.   v columns: 1 + 2a + sqrt2 b, 1 + 2b + sqrt2 a.
+// Each takes a few values only, so the reciprocals are constants folded at compile time
+// (the same IEEE quotients a run-time division gives) picked by the pixel's edge flags.
 __device__ __forceinline__ float sig_r_tv(int i, int j, int N) {
-    const float m = fmaxf(2.f * (i < N - 1), 2.f * (j < N - 1));
-    return m > 0.f ? 1.f / m : 1.f;
+    return ((i < N - 1) || (j < N - 1)) ? 0.5f : 1.f;   // 1 / max(2a, 2b); 1 if both vanish
 }
 __device__ __forceinline__ float sig_r_tgv(int i, int j, int N) {
-    return 1.f / fmaxf(2.f * (i < N - 1) + 1.f, 2.f * (j < N - 1) + 1.f);
+    return ((i < N - 1) || (j < N - 1)) ? 1.f / 3.f : 1.f;   // 1 / max(2a + 1, 2b + 1)
 }
+constexpr float cmaxf(float x, float y) { return x > y ? x : y; }
+constexpr float sig_s_entry(float ex, float ey) { return 1.f / cmaxf(cmaxf(ex, ey), (ex + ey) * kInvSqrt2f); }
+constexpr float tau_v_entry(float a, float b) { return 1.f / (1.f + 2.f * a + 1.41421356237f * b); }
 __device__ __forceinline__ float sig_s_tgv(int i, int j, int N) {
-    const float ex = (float)((i < N - 1) + (i >= 1)), ey = (float)((j < N - 1) + (j >= 1));
-    return 1.f / fmaxf(fmaxf(ex, ey), (ex + ey) * kInvSqrt2f);
+    // 1 / max(max(ex, ey), (ex + ey) / sqrt 2); with N >= 2 every pixel has ex, ey in {1, 2}
+    const bool x2 = (i < N - 1) && (i >= 1), y2 = (j < N - 1) && (j >= 1);
+    constexpr float t11 = sig_s_entry(1.f, 1.f), t12 = sig_s_entry(1.f, 2.f), t21 = sig_s_entry(2.f, 1.f),
+                    t22 = sig_s_entry(2.f, 2.f);
+    return x2 ? (y2 ? t22 : t21) : (y2 ? t12 : t11);
 }
 __device__ __forceinline__ float tau_v1_tgv(int i, int j, int N) {
-    return 1.f / (1.f + 2.f * (i < N - 1) + 1.41421356237f * (j < N - 1));
+    // 1 / (1 + 2a + sqrt2 b)
+    constexpr float t00 = tau_v_entry(0.f, 0.f), t01 = tau_v_entry(0.f, 1.f), t10 = tau_v_entry(1.f, 0.f),
+                    t11 = tau_v_entry(1.f, 1.f);
+    const bool a = i < N - 1, b = j < N - 1;
+    return a ? (b ? t11 : t10) : (b ? t01 : t00);
 }
 __device__ __forceinline__ float tau_v2_tgv(int i, int j, int N) {
-    return 1.f / (1.f + 2.f * (j < N - 1) + 1.41421356237f * (i < N - 1));
+    // 1 / (1 + 2b + sqrt2 a)
+    constexpr float t00 = tau_v_entry(0.f, 0.f), t01 = tau_v_entry(0.f, 1.f), t10 = tau_v_entry(1.f, 0.f),
+                    t11 = tau_v_entry(1.f, 1.f);
+    const bool a = i < N - 1, b = j < N - 1;
+    return b ? (a ? t11 : t10) : (a ? t01 : t00);
 }
 
 // (hi, lo) += delta by an error-free TwoSum followed by renormalisation: the pair holds
@@ -68,12 +86,14 @@ __device__ __forceinline__ void add_compensated(float& hi, float& lo, float delt
     hi = h2;
 }
 
-// D_xi = I - gamma xi xi^T applied to p (symmetric).
+// D_xi = I - gamma xi xi^T applied to p (symmetric).  The roundings are spelled out so
+// that every kernel that inlines this computes the same bits.
 __device__ __forceinline__ void dxi_apply(float xi0, float xi1, float gamma, float p0, float p1, float& o0,
                                           float& o1) {
-    const float dot = xi0 * p0 + xi1 * p1;
-    o0 = p0 - gamma * xi0 * dot;
-    o1 = p1 - gamma * xi1 * dot;
+    const float dot = __fmaf_rn(xi0, p0, __fmul_rn(xi1, p1));
+    const float gd = __fmul_rn(gamma, dot);
+    o0 = __fmaf_rn(-xi0, gd, p0);
+    o1 = __fmaf_rn(-xi1, gd, p1);
 }
 
 }  // namespace pat
