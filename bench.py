@@ -458,8 +458,8 @@ def run_update_hbm(P, S, np, torch, device, stream, flush, count=16, n=512, iter
     """The fused update (k_update_b) where its state does not fit in L2: a lockstep batch
     of ``count`` TGV^2 problems of n x n (vessel phantoms, 128 detectors, T = 2n), ``iters``
     iterations with per-phase CUDA events.  Bytes per pixel: the algorithmic 18 floats
-    (read u, v2, r2, s3, tau; write u, v2, r2, s3, ubar) and the 30 the kernel moves (the
-    compensated low words, the bordered ubar, the ubar quad and the K^T clear besides)."""
+    (read u, v2, r2, s3, tau; write u, v2, r2, s3, ubar) and the 29 the kernel moves (the
+    compensated low words, the ubar quad and the K^T clear besides)."""
     ws = [S.workload_warm(700000 + s, n=n, n_det=128) for s in range(count)]
     probs = [make_problem(P, np, torch, device, stream, w) for w in ws]
     prms = [P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], iters=iters, gap_every=10) for w in ws]
@@ -467,7 +467,7 @@ def run_update_hbm(P, S, np, torch, device, stream, flush, count=16, n=512, iter
     P.pat_reconstruct_batched(geos, fs, prms, us, stream)        # warm-up (K sums, kernels)
     px = count * n * n
     peaks = load_peaks()
-    out = {"problems": count, "n": n, "pixels": px, "state_bytes": 30 * 4 * px}
+    out = {"problems": count, "n": n, "pixels": px, "state_bytes": 29 * 4 * px}
     flush.zero_()
     P.pat_profile_read(reset=True)
     P.pat_profile_enable(True)
@@ -477,7 +477,7 @@ def run_update_hbm(P, S, np, torch, device, stream, flush, count=16, n=512, iter
     ms, cnt = prof["update"]
     avg_s = ms / cnt / 1e3
     alg = 18 * 4 * px / avg_s / 1e9
-    moved = 30 * 4 * px / avg_s / 1e9
+    moved = 29 * 4 * px / avg_s / 1e9
     out.update({"launches": cnt, "avg_us": avg_s * 1e6,
                 "roofline": {"bound": "hbm", "achieved": alg, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                              "frac": alg / peaks["hbm_gbs"], "bytes_per_pixel": 72},

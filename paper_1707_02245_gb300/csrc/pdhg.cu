@@ -47,7 +47,6 @@ struct UpdateArgs {
     float* x_out;
     float* xl_out;
     float* y_out;
-    float* ubar_pad;       // (N+2)^2, border stays zero
     float4* ubar_quad;     // (N+1)^2 quads of ubar for the projector
     float4* u_quad;        // quads of u^{n+1} for the gap's K u (NULL: not a gap iteration)
     const int* stop;
@@ -80,9 +79,20 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
     __shared__ float s_vb1[VL][VX], s_vb2[VL][VX];   // vbar on V = tile + low halo
     __shared__ float s_vn1[VT][VTX], s_vn2[VT][VTX], s_vnl1[VT][VTX], s_vnl2[VT][VTX];
 
+    // plane pointers, formed once
     const float* u_in = a.x_in;
     const float* r1_in = a.y_in;
     const float* r2_in = a.y_in + NN;
+    const float* s11_in = a.y_in + 2 * NN;
+    const float* s22_in = a.y_in + 3 * NN;
+    const float* s12_in = a.y_in + 4 * NN;
+    const float* v1_in = a.x_in + NN;
+    const float* v2_in = a.x_in + 2 * NN;
+    const float* v1l_in = a.xl_in + NN;
+    const float* v2l_in = a.xl_in + 2 * NN;
+    const float* xi0_in = a.xi;
+    const float* xi1_in = REG == PAT_DTV ? a.xi + NN : a.xi;
+    constexpr int NCELL = (LX * LY + TX * TY - 1) / (TX * TY);   // staged cells per thread
     const float tmul = __ldg(a.step_mul), smul = __ldg(a.step_mul + 1);
 
     // fixed-point scales of the (at most 2 x 2) K^T tiles that the cells of U touch (the
@@ -94,15 +104,18 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
     }
 
     // ---- stage 1: dual fields on the tile plus halo -------------------------------
-    for (int c = tid; c < LX * LY; c += TX * TY) {
+#pragma unroll
+    for (int kc = 0; kc < NCELL; ++kc) {
+        const int c = tid + kc * TX * TY;
+        if (c >= LX * LY) break;
         const int lx = c % LX, ly = c / LX;
         const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
         const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
         float r1 = in ? __ldg(r1_in + gy * N + gx) : 0.f;
         float r2 = in ? __ldg(r2_in + gy * N + gx) : 0.f;
         if (REG == PAT_DTV) {
-            const float xi0 = in ? __ldg(a.xi + gy * N + gx) : 0.f;
-            const float xi1 = in ? __ldg(a.xi + NN + gy * N + gx) : 0.f;
+            const float xi0 = in ? __ldg(xi0_in + gy * N + gx) : 0.f;
+            const float xi1 = in ? __ldg(xi1_in + gy * N + gx) : 0.f;
             float o0, o1;
             dxi_apply(xi0, xi1, a.gamma, r1, r2, o0, o1);
             r1 = o0;
@@ -111,15 +124,18 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
         s_r1m[ly][lx] = (gx < N - 1) ? r1 : 0.f;
         s_r2m[ly][lx] = (gy < N - 1) ? r2 : 0.f;
         if (REG == PAT_TGV) {
-            s_s11[ly][lx] = in ? __ldg(a.y_in + 2 * NN + gy * N + gx) : 0.f;
-            s_s22[ly][lx] = in ? __ldg(a.y_in + 3 * NN + gy * N + gx) : 0.f;
-            s_s12[ly][lx] = in ? __ldg(a.y_in + 4 * NN + gy * N + gx) : 0.f;
+            s_s11[ly][lx] = in ? __ldg(s11_in + gy * N + gx) : 0.f;
+            s_s22[ly][lx] = in ? __ldg(s22_in + gy * N + gx) : 0.f;
+            s_s12[ly][lx] = in ? __ldg(s12_in + gy * N + gx) : 0.f;
         }
     }
     __syncthreads();
 
     // ---- stage 2: primal step and extrapolation on U (u) and V (v) ------------------
-    for (int c = tid; c < LX * LY; c += TX * TY) {
+#pragma unroll
+    for (int kc = 0; kc < NCELL; ++kc) {
+        const int c = tid + kc * TX * TY;
+        if (c >= LX * LY) break;
         const int lx = c % LX, ly = c / LX;
         const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
         const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
@@ -157,8 +173,8 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
                 const float et1 = -dx11 - dy12 * kInvSqrt2f;
                 const float et2 = -dy22 - dx12 * kInvSqrt2f;
                 const float r1 = __ldg(r1_in + gi), r2 = __ldg(r2_in + gi);
-                const float v1o = __ldg(a.x_in + NN + gi), v2o = __ldg(a.x_in + 2 * NN + gi);
-                const float v1ol = __ldg(a.xl_in + NN + gi), v2ol = __ldg(a.xl_in + 2 * NN + gi);
+                const float v1o = __ldg(v1_in + gi), v2o = __ldg(v2_in + gi);
+                const float v1ol = __ldg(v1l_in + gi), v2ol = __ldg(v2l_in + gi);
                 const float t1 = (a.tau >= 0.f ? a.tau : tau_v1_tgv(gx, gy, N)) * tmul;
                 const float t2 = (a.tau >= 0.f ? a.tau : tau_v2_tgv(gx, gy, N)) * tmul;
                 float v1n = v1o, v1nl = v1ol, v2n = v2o, v2nl = v2ol;
@@ -196,7 +212,7 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
         } else if (REG == PAT_DTV) {
             const float sr = (a.sig2 >= 0.f ? a.sig2 : __ldg(a.sig_r + gi)) * smul;
             float o0, o1;
-            dxi_apply(__ldg(a.xi + gi), __ldg(a.xi + NN + gi), a.gamma, gu0, gu1, o0, o1);
+            dxi_apply(__ldg(xi0_in + gi), __ldg(xi1_in + gi), a.gamma, gu0, gu1, o0, o1);
             r1 = fmaf(sr, o0, r1);
             r2 = fmaf(sr, o1, r2);
         } else {
@@ -209,8 +225,8 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
         a.y_out[NN + gi] = r2;
         a.x_out[gi] = s_un[threadIdx.y][threadIdx.x];
         a.xl_out[gi] = s_unl[threadIdx.y][threadIdx.x];
-        a.ubar_pad[(gy + 1) * (N + 2) + gx + 1] = ub;
-        // quads with the upper-left tap at (gx, gy), and the grid's low border quads
+        // quads with the upper-left tap at (gx, gy), and the grid's low border quads (the
+        // quads are the only copy of ubar; the bordered image is filled at the start only)
         {
             const float bx = s_ub[ly][lx + 1], by_ = s_ub[ly + 1][lx], bxy = s_ub[ly + 1][lx + 1];
             const int Q = N + 1;
@@ -686,7 +702,7 @@ struct OutArgs {
     const float* X[2];
     const float* Y[2];
     const float* q;
-    const float* ubar_pad;
+    const float4* ubar_quad;
     const InfoDev* info;
     float* u_out;
     float* x_out;
@@ -711,7 +727,7 @@ __global__ void k_output(OutArgs a) {
             if (a.xbar_out) {
                 if (i < NN) {
                     const int gx = (int)(i % N), gy = (int)(i / N);
-                    a.xbar_out[i] = a.ubar_pad[(long long)(gy + 1) * (N + 2) + gx + 1];
+                    a.xbar_out[i] = a.ubar_quad[(long long)(gy + 1) * (N + 1) + gx + 1].x;
                 } else {
                     // vbar^I = v^I + theta (v^I - v^{I-1}); with I = 0 the warm-start vbar is
                     // not recoverable here and v^0 is returned
@@ -954,7 +970,6 @@ static UpdateArgs make_update_args(const Prob& pr, int par, bool gap_iter) {
     a.x_out = ws.X[1 - par];
     a.xl_out = ws.XL[1 - par];
     a.y_out = ws.Y[1 - par];
-    a.ubar_pad = ws.ubar_pad;
     a.ubar_quad = ws.ubar_quad;
     a.u_quad = gap_iter ? ws.u_quad : nullptr;
     a.stop = &ws.info->stop;
@@ -1157,7 +1172,7 @@ static int finish_problem(Prob& pr, cudaStream_t st) {
     oa.Y[0] = pr.ws.Y[0];
     oa.Y[1] = pr.ws.Y[1];
     oa.q = pr.ws.q;
-    oa.ubar_pad = pr.ws.ubar_pad;
+    oa.ubar_quad = pr.ws.ubar_quad;
     oa.info = pr.ws.info;
     oa.u_out = pr.u_out;
     oa.x_out = pr.p.x_out_dev;
