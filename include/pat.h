@@ -276,6 +276,20 @@ const char* pat_last_error(void);
  * bilinear taps touch the grid (the algorithmic work of one K or K^T)}. */
 int  pat_geometry_info(const pat_geometry* g, long long* out6_host);
 
+/* Host only: the work list of the K^T kernel (Sec. 3.3.1's adjoint, evaluated by pixel
+ * tiles) that pat_create_geometry builds for `desc`, for a GPU that holds `slots` K^T
+ * CTAs at once.  With slots > 0 no CUDA call is made; slots <= 0 sizes it for the
+ * current device.  counts3_host = {ray segments, work items, candidate points}.
+ * rays_host (4 ints per segment: detector, angle index m, first radius index k,
+ * exclusive prefix within its tile; after each tile a sentinel {-1, 0, 0, tile total})
+ * and items_host (5 ints per item: tile, first segment, segment count, first and end
+ * candidate within the tile) are written when not NULL.  Their capacities are in
+ * entries; if one is too small, PAT_ERR_INVALID_ARG is returned after counts3_host is
+ * written, so a first call with NULL outputs gives the sizes.  The caller owns all
+ * buffers. */
+int  pat_adjoint_worklist(const pat_geometry_desc* desc, int slots, int* rays_host, long long rays_cap,
+                          int* items_host, long long items_cap, long long* counts3_host);
+
 #ifdef __cplusplus
 }
 #endif

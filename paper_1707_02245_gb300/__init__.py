@@ -34,6 +34,7 @@ EXPORTED = [
     "pat_create_geometry", "pat_destroy_geometry", "pat_forward", "pat_adjoint",
     "pat_direction_field", "pat_params_default", "pat_reconstruct", "pat_reconstruct_batched",
     "pat_steps", "pat_duality_gap", "pat_error_string", "pat_last_error", "pat_geometry_info",
+    "pat_adjoint_worklist",
     "pat_profile_enable", "pat_profile_read", "pat_kernel_launches", "pat_adjoint_noalloc",
     "pat_tune_step_ratio", "pat_tune_step_ratio_batched", "pat_preprocess", "pat_wavelet_transform",
     # learned warm start (include/pat_unet.h)
@@ -124,6 +125,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pat_error_string": (ctypes.c_char_p, [i]),
         "pat_last_error": (ctypes.c_char_p, []),
         "pat_geometry_info": (i, [vp, ctypes.POINTER(ctypes.c_longlong)]),
+        "pat_adjoint_worklist": (i, [ctypes.POINTER(pat_geometry_desc), i, vp, ctypes.c_longlong, vp,
+                                     ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
         "pat_profile_enable": (i, [i]),
         "pat_profile_read": (i, [ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong), i]),
         "pat_kernel_launches": (ctypes.c_longlong, []),
@@ -175,17 +178,39 @@ def _check(code: int, where: str):
 
 # ---- C-named entry points --------------------------------------------------------
 
-def pat_create_geometry(n: int, det_xy, n_t: int, r0: float, dr: float, quad_m: int,
-                        extent=(-1.0, 1.0, -1.0, 1.0)) -> int:
-    lib = load()
+def _geometry_desc(n, det_xy, n_t, r0, dr, quad_m, extent):
+    """(desc, detector array); the array must outlive every use of desc."""
     det = np.ascontiguousarray(np.asarray(det_xy, dtype=np.float64).reshape(-1))
     desc = pat_geometry_desc(n=n, xmin=extent[0], xmax=extent[1], ymin=extent[2], ymax=extent[3],
                              n_det=det.size // 2,
                              det_xy_host=det.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                              n_t=n_t, r0=r0, dr=dr, quad_m=quad_m)
+    return desc, det
+
+
+def pat_create_geometry(n: int, det_xy, n_t: int, r0: float, dr: float, quad_m: int,
+                        extent=(-1.0, 1.0, -1.0, 1.0)) -> int:
+    lib = load()
+    desc, _det = _geometry_desc(n, det_xy, n_t, r0, dr, quad_m, extent)
     out = ctypes.c_void_p()
     _check(lib.pat_create_geometry(ctypes.byref(desc), ctypes.byref(out)), "pat_create_geometry")
     return out.value
+
+
+def pat_adjoint_worklist(n: int, det_xy, n_t: int, r0: float, dr: float, quad_m: int, slots: int,
+                         extent=(-1.0, 1.0, -1.0, 1.0)) -> dict:
+    """The K^T work list (host only when slots > 0): rays (S x 4: detector, angle, first
+    radius index, prefix in the tile; sentinels {-1, 0, 0, tile total}), items (I x 5:
+    tile, first segment, segments, first and end candidate) and the candidate count."""
+    lib = load()
+    desc, _det = _geometry_desc(n, det_xy, n_t, r0, dr, quad_m, extent)
+    cnt = (ctypes.c_longlong * 3)()
+    _check(lib.pat_adjoint_worklist(ctypes.byref(desc), slots, None, 0, None, 0, cnt), "pat_adjoint_worklist")
+    rays = np.zeros((cnt[0], 4), dtype=np.int32)
+    items = np.zeros((cnt[1], 5), dtype=np.int32)
+    _check(lib.pat_adjoint_worklist(ctypes.byref(desc), slots, rays.ctypes.data, cnt[0], items.ctypes.data, cnt[1],
+                                    cnt), "pat_adjoint_worklist")
+    return {"rays": rays, "items": items, "candidates": int(cnt[2])}
 
 
 def pat_destroy_geometry(g: int) -> None:

@@ -146,11 +146,9 @@ static void free_tables(pat_geometry* g) {
     cudaFree(g->pc.krow);
     cudaFree(g->pc.kcol);
     cudaFree(g->pc.tile_kmax);
-    cudaFree(g->adj_box);
-    cudaFree(g->adj_units);
+    cudaFree(g->adj_rays);
     cudaFree(g->adj_item);
-    g->adj_box = nullptr;
-    g->adj_units = nullptr;
+    g->adj_rays = nullptr;
     g->adj_item = nullptr;
     g->pc.tile_kmax = nullptr;
     g->det = nullptr;
@@ -188,10 +186,8 @@ static int2 covering_window(const std::vector<unsigned char>& mask, int M) {
     return make_int2(best_end, M - best_len);
 }
 
-extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry** out) {
-    if (!desc || !out) return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: NULL argument");
-    *out = nullptr;
-    const pat_geometry_desc& d = *desc;
+// Checks a geometry description; returns PAT_OK or the error (with its message set).
+static int check_desc(const pat_geometry_desc& d) {
     if (d.n < 2 || d.n > 16384) return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: n must be in [2, 16384]");
     if (!(d.xmax > d.xmin) || !(d.ymax > d.ymin))
         return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: empty image extent");
@@ -218,72 +214,60 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
         if (!(ext < 16777216.0))
             return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: circles reach more than 2^24 pixels from the grid");
     }
-    pat_geometry* g = new pat_geometry();
-    g->desc = d;
-    g->det_xy.assign(d.det_xy_host, d.det_xy_host + 2 * (size_t)d.n_det);
-    g->desc.det_xy_host = nullptr;  // the caller's array is not retained
-    cudaGetDevice(&g->device);
+    return PAT_OK;
+}
 
+// The FP32 device tables in continuous pixel coordinates (pixel centres at integers), and
+// their FP64 counterparts (cos, sin of the angles; radii).
+struct PointTables {
+    std::vector<float2> det, cs;
+    std::vector<float> rk, wk;
+    std::vector<double> cosd, sind, rd;
+};
+
+static PointTables point_tables(const pat_geometry_desc& d) {
     const int N = d.n, D = d.n_det, T = d.n_t, M = d.quad_m;
     const double hx = (d.xmax - d.xmin) / N, hy = (d.ymax - d.ymin) / N;
-    const int n_kgrp = (T + KGRP - 1) / KGRP;
-
-    std::vector<float2> det(D), cs(M);
-    std::vector<float> rk(T), wk(T);
-    std::vector<double> cosd(M), sind(M), rd(T);
-    // device tables in continuous pixel coordinates (pixel centres at integers)
+    PointTables pt;
+    pt.det.resize(D);
+    pt.cs.resize(M);
+    pt.rk.resize(T);
+    pt.wk.resize(T);
+    pt.cosd.resize(M);
+    pt.sind.resize(M);
+    pt.rd.resize(T);
     for (int i = 0; i < D; ++i)
-        det[i] = make_float2((float)((d.det_xy_host[2 * i] - d.xmin) / hx - 0.5),
-                             (float)((d.det_xy_host[2 * i + 1] - d.ymin) / hy - 0.5));
+        pt.det[i] = make_float2((float)((d.det_xy_host[2 * i] - d.xmin) / hx - 0.5),
+                                (float)((d.det_xy_host[2 * i + 1] - d.ymin) / hy - 0.5));
     for (int m = 0; m < M; ++m) {
         const double phi = 2.0 * M_PI * (m + 0.5) / M;
-        cosd[m] = cos(phi);
-        sind[m] = sin(phi);
-        cs[m] = make_float2((float)(cosd[m] / hx), (float)(sind[m] / hy));
+        pt.cosd[m] = cos(phi);
+        pt.sind[m] = sin(phi);
+        pt.cs[m] = make_float2((float)(pt.cosd[m] / hx), (float)(pt.sind[m] / hy));
     }
     for (int k = 0; k < T; ++k) {
-        rd[k] = d.r0 + (k + 0.5) * d.dr;
-        rk[k] = (float)rd[k];
-        wk[k] = (float)(2.0 * M_PI * rd[k] / M);
+        pt.rd[k] = d.r0 + (k + 0.5) * d.dr;
+        pt.rk[k] = (float)pt.rd[k];
+        pt.wk[k] = (float)(2.0 * M_PI * pt.rd[k] / M);
     }
+    return pt;
+}
 
-    // angular windows: a point can touch the grid iff fx, fy in (-1, N), i.e.
-    // x in (xmin - hx/2, xmax + hx/2); the test uses a margin so fp32 rounding in the
-    // kernels never meets a point outside its window that would touch the grid
+struct AdjWork {
+    int tiles_x = 0, tiles = 0;
+    long long candidates = 0;
+    std::vector<int4> rays;
+    std::vector<AdjItem> items;
+    std::vector<float> cost;
+};
+
+// The K^T work list of geometry d for a GPU that holds `slots` K^T CTAs at once.
+static int adjoint_worklist(const pat_geometry_desc& d, const PointTables& pt, double slots, AdjWork& w) {
+    const int N = d.n, D = d.n_det, T = d.n_t, M = d.quad_m;
+    const double hx = (d.xmax - d.xmin) / N, hy = (d.ymax - d.ymin) / N;
     const double ex = 1e-3 * hx, ey = 1e-3 * hy;
-    const double xl = d.xmin - 0.5 * hx - ex, xh = d.xmax + 0.5 * hx + ex;
-    const double yl = d.ymin - 0.5 * hy - ey, yh = d.ymax + 0.5 * hy + ey;
-    std::vector<int2> win((size_t)D * n_kgrp);
-    std::vector<unsigned char> mask(M);
-    long long pts = 0, on_grid = 0;
-    const double gxl = d.xmin - 0.5 * hx, gxh = d.xmax + 0.5 * hx, gyl = d.ymin - 0.5 * hy, gyh = d.ymax + 0.5 * hy;
-    for (int di = 0; di < D; ++di) {
-        const double dx = d.det_xy_host[2 * di], dy = d.det_xy_host[2 * di + 1];
-        for (int gi = 0; gi < n_kgrp; ++gi) {
-            std::fill(mask.begin(), mask.end(), 0);
-            const int k_end = std::min(T, (gi + 1) * KGRP);
-            for (int k = gi * KGRP; k < k_end; ++k) {
-                const double r = rd[k];
-                // quick reject: circle entirely off the extended box
-                const double cx = std::min(std::max(dx, xl), xh), cy = std::min(std::max(dy, yl), yh);
-                const double dmin = hypot(dx - cx, dy - cy);
-                const double dmax = std::max(std::max(hypot(dx - xl, dy - yl), hypot(dx - xh, dy - yl)),
-                                             std::max(hypot(dx - xl, dy - yh), hypot(dx - xh, dy - yh)));
-                if (r < dmin - 1e-9 || r > dmax + 1e-9) continue;
-                for (int m = 0; m < M; ++m) {
-                    const double x = dx + r * cosd[m], y = dy + r * sind[m];
-                    if (x > gxl && x < gxh && y > gyl && y < gyh) ++on_grid;  // touches the grid
-                    if (!mask[m] && x > xl && x < xh && y > yl && y < yh) mask[m] = 1;
-                }
-            }
-            int2 w = covering_window(mask, M);
-            win[(size_t)di * n_kgrp + gi] = w;
-            pts += (long long)w.y * (k_end - gi * KGRP);
-        }
-    }
-    g->points_per_apply = pts;
-    g->points_on_grid = on_grid;
-
+    const std::vector<float2>& det = pt.det;
+    const std::vector<float2>& cs = pt.cs;
     // K^T candidate boxes: for every ATILE x ATILE pixel tile and detector, the (k, m)
     // polar box of the tile's tap region (points with i0 in [x0-1, x0+ATILE-1], same in
     // y), with one index of margin on every side; FP64 on the host
@@ -327,89 +311,218 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
             box[(size_t)t * D + di] = make_int4(k0, std::max(0, k1 - k0 + 1), m0, nm);
         }
     }
-    g->adj_tiles_x = tiles_x;
-    g->adj_tiles = tiles;
+    w.tiles_x = tiles_x;
+    w.tiles = tiles;
 
-    // K^T work list.  A unit is up to 32 rays of one (tile, detector) box; its cost is the
-    // number of candidate points on those rays (ray-segment lengths in the tile's tap
-    // region) plus a fixed overhead.  Each tile's units are packed into work items of
-    // roughly equal cost (one CTA each); items run heaviest first.
-    std::vector<int4> units;       // {detector, first ray (circular), rays, box index}
-    std::vector<int4> items;       // {tile, first unit, end unit, 0}
+    // K^T work list.  Every ray (detector d, angle m) of a tile's polar box is cut to the
+    // radius interval where its points can have taps in the tile's window [x0 - 1, x0 +
+    // ATILE) x [y0 - 1, y0 + ATILE) (the window is convex, so the interval is one
+    // segment).  The cut is FP64 arithmetic on the same FP32 tables the kernels read, with
+    // a margin of 1e-3 pixel on the window and of one radius before and two after the
+    // segment, far beyond the FP32 rounding of a point's position; the kernel still tests
+    // every candidate exactly.  A tile's non-empty segments, concatenated, are its
+    // candidate list: rays[] holds {d, m, first k, exclusive prefix} per segment and a
+    // sentinel {-1, 0, 0, total} after each tile.  A work item (one CTA) is an equal share
+    // of one tile's list; the shares are sized so that the items fill whole waves of the
+    // GPU's resident CTAs.
+    std::vector<int4>& rays = w.rays;
+    std::vector<AdjItem>& items = w.items;
     std::vector<double> item_cost;
     {
-        std::vector<double> ucost;
-        std::vector<int> tile_first(tiles + 1, 0);
-        const double r_first = d.r0 + 0.5 * d.dr;
+        std::vector<long long> tile_base(tiles + 1, 0), tile_total(tiles, 0);
         for (int t = 0; t < tiles; ++t) {
-            tile_first[t] = (int)units.size();
+            tile_base[t] = (long long)rays.size();
             const int x0 = (t % tiles_x) * ATILE, y0 = (t / tiles_x) * ATILE;
-            const double rx0 = d.xmin + (x0 - 0.5) * hx - ex, rx1 = d.xmin + (x0 + ATILE + 0.5) * hx + ex;
-            const double ry0 = d.ymin + (y0 - 0.5) * hy - ey, ry1 = d.ymin + (y0 + ATILE + 0.5) * hy + ey;
+            const double wx0 = x0 - 1.001, wx1 = x0 + ATILE + 0.001;
+            const double wy0 = y0 - 1.001, wy1 = y0 + ATILE + 0.001;
+            long long pre = 0;
             for (int di = 0; di < D; ++di) {
                 const int4 bx = box[(size_t)t * D + di];
                 if (bx.w <= 0 || bx.y <= 0) continue;
-                const double dx = d.det_xy_host[2 * di], dy = d.det_xy_host[2 * di + 1];
-                for (int mb = 0; mb < bx.w; mb += 32) {
-                    const int nr = std::min(32, bx.w - mb);
-                    double c = 16.0;
-                    for (int j = 0; j < nr; ++j) {
-                        const int m = (bx.z + mb + j) % M;
-                        const double cx = cosd[m], sy = sind[m];
-                        double t0 = -1e300, t1 = 1e300;
-                        if (cx != 0) {
-                            const double a0 = (rx0 - dx) / cx, a1 = (rx1 - dx) / cx;
-                            t0 = std::max(t0, std::min(a0, a1));
-                            t1 = std::min(t1, std::max(a0, a1));
-                        } else if (dx < rx0 || dx > rx1) {
-                            t1 = -1e300;
-                        }
-                        if (sy != 0) {
-                            const double b0 = (ry0 - dy) / sy, b1 = (ry1 - dy) / sy;
-                            t0 = std::max(t0, std::min(b0, b1));
-                            t1 = std::min(t1, std::max(b0, b1));
-                        } else if (dy < ry0 || dy > ry1) {
-                            t1 = -1e300;
-                        }
-                        if (t1 < t0) continue;
-                        const double k0 = std::max((double)bx.x, floor((t0 - r_first) / d.dr) - 1);
-                        const double k1 = std::min((double)(bx.x + bx.y), ceil((t1 - r_first) / d.dr) + 2);
-                        c += std::max(0.0, k1 - k0);
+                const long long kb = bx.x, ke = (long long)bx.x + bx.y;
+                const double px = det[di].x, py = det[di].y;
+                for (int j = 0; j < bx.w; ++j) {
+                    const int m = (bx.z + j) % M;
+                    const double cx = cs[m].x, cy = cs[m].y;
+                    double t0 = -1e300, t1 = 1e300;
+                    if (cx != 0) {
+                        const double a0 = (wx0 - px) / cx, a1 = (wx1 - px) / cx;
+                        t0 = std::max(t0, std::min(a0, a1));
+                        t1 = std::min(t1, std::max(a0, a1));
+                    } else if (px < wx0 || px > wx1) {
+                        continue;
                     }
-                    units.push_back(make_int4(di, (bx.z + mb) % M, nr, t * D + di));
-                    ucost.push_back(c);
+                    if (cy != 0) {
+                        const double b0 = (wy0 - py) / cy, b1 = (wy1 - py) / cy;
+                        t0 = std::max(t0, std::min(b0, b1));
+                        t1 = std::min(t1, std::max(b0, b1));
+                    } else if (py < wy0 || py > wy1) {
+                        continue;
+                    }
+                    if (t1 < t0) continue;
+                    const double kf0 = (t0 - d.r0) / d.dr - 0.5, kf1 = (t1 - d.r0) / d.dr - 0.5;
+                    const long long k0 = (long long)std::max((double)kb, std::floor(std::max(kf0, -1e15)) - 1);
+                    const long long k1 = (long long)std::min((double)ke, std::ceil(std::min(kf1, 1e15)) + 2);
+                    if (k1 <= k0) continue;
+                    rays.push_back(make_int4(di, m, (int)k0, (int)pre));
+                    pre += k1 - k0;
                 }
             }
+            if (pre > (1LL << 30))
+                return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: too many K^T candidates in one pixel tile");
+            tile_total[t] = pre;
+            rays.push_back(make_int4(-1, 0, 0, (int)pre));
         }
-        tile_first[tiles] = (int)units.size();
-        double total = 0;
-        for (double c : ucost) total += c;
-        const double target = std::max(64.0, total / (8.0 * 152.0));
+        tile_base[tiles] = (long long)rays.size();
+        if (rays.size() > (size_t)((1LL << 31) - 1))
+            return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: K^T work list too large");
+        long long total = 0;
+        for (int t = 0; t < tiles; ++t) total += tile_total[t];
+        w.candidates = total;
+        // pieces per tile: two waves of resident CTAs shared in proportion to the tiles'
+        // candidate counts (largest remainders), at least 1024 candidates a piece
+        const long long Q = std::max(1LL, std::min((long long)(2.0 * slots), total / 1024));
+        std::vector<long long> n_piece(tiles, 0);
+        {
+            long long assigned = 0;
+            std::vector<std::pair<double, int>> rem;
+            for (int t = 0; t < tiles; ++t) {
+                if (tile_total[t] <= 0) continue;
+                const double exact = (double)Q * (double)tile_total[t] / (double)total;
+                n_piece[t] = std::max(1LL, (long long)std::floor(exact));
+                assigned += n_piece[t];
+                rem.push_back({exact - (double)n_piece[t], t});
+            }
+            std::stable_sort(rem.begin(), rem.end(), [](const std::pair<double, int>& a,
+                                                        const std::pair<double, int>& b) { return a.first > b.first; });
+            for (size_t i = 0; i < rem.size() && assigned < Q; ++i, ++assigned) ++n_piece[rem[i].second];
+        }
         for (int t = 0; t < tiles; ++t) {
-            int u = tile_first[t];
-            while (u < tile_first[t + 1]) {
-                double c = 0;
-                const int u0 = u;
-                while (u < tile_first[t + 1] && (u == u0 || c + ucost[u] <= target)) c += ucost[u++];
-                items.push_back(make_int4(t, u0, u, 0));
-                item_cost.push_back(c);
+            const long long cost = tile_total[t];
+            if (cost <= 0) continue;
+            const long long n_p = n_piece[t];
+            long long r = tile_base[t];                  // segment holding the piece's start
+            for (long long j = 0; j < n_p; ++j) {
+                long long b0 = cost * j / n_p;
+                const long long b1 = cost * (j + 1) / n_p;
+                if (b1 <= b0) continue;
+                while (rays[r + 1].w <= b0) ++r;
+                long long r_last = r;                    // segment holding b1 - 1
+                while (rays[r_last + 1].w <= b1 - 1) ++r_last;
+                while (b0 < b1) {                        // at most ARAYS segments per item
+                    const long long re = std::min(r_last, r + ARAYS - 1);
+                    const long long e1 = re == r_last ? b1 : rays[re + 1].w;
+                    AdjItem it{};
+                    it.tile = t;
+                    it.ray0 = (int)r;
+                    it.nray = (int)(re - r + 1);
+                    it.c0 = (int)b0;
+                    it.c1 = (int)e1;
+                    items.push_back(it);
+                    item_cost.push_back((double)(e1 - b0) + 4.0 * it.nray + 64.0);
+                    b0 = e1;
+                    if (b0 < b1) r = re + 1;
+                }
             }
         }
         std::vector<int> order(items.size());
         for (size_t i = 0; i < order.size(); ++i) order[i] = (int)i;
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return item_cost[a] > item_cost[b]; });
-        std::vector<int4> sorted(items.size());
-        g->adj_item_cost.resize(items.size());
+        std::vector<AdjItem> sorted(items.size());
+        w.cost.resize(items.size());
         for (size_t i = 0; i < order.size(); ++i) {
             sorted[i] = items[order[i]];
-            g->adj_item_cost[i] = (float)item_cost[order[i]];
+            w.cost[i] = (float)item_cost[order[i]];
         }
         items.swap(sorted);
-        if (items.empty()) {
-            items.push_back(make_int4(0, 0, 0, 0));
-            g->adj_item_cost.push_back(0.f);
+        if (items.empty()) {   // one empty item keeps the launches well-formed
+            AdjItem it{};
+            it.ray0 = 0;
+            items.push_back(it);
+            w.cost.push_back(0.f);
         }
     }
+    return PAT_OK;
+}
+
+extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry** out) {
+    if (!desc || !out) return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: NULL argument");
+    *out = nullptr;
+    const pat_geometry_desc& d = *desc;
+    const int vrc = check_desc(d);
+    if (vrc) return vrc;
+    pat_geometry* g = new pat_geometry();
+    g->desc = d;
+    g->det_xy.assign(d.det_xy_host, d.det_xy_host + 2 * (size_t)d.n_det);
+    g->desc.det_xy_host = nullptr;  // the caller's array is not retained
+    cudaGetDevice(&g->device);
+
+    const int N = d.n, D = d.n_det, T = d.n_t, M = d.quad_m;
+    const double hx = (d.xmax - d.xmin) / N, hy = (d.ymax - d.ymin) / N;
+    const int n_kgrp = (T + KGRP - 1) / KGRP;
+
+    const PointTables pt = point_tables(d);
+    const std::vector<float2>& det = pt.det;
+    const std::vector<float2>& cs = pt.cs;
+    const std::vector<float>& rk = pt.rk;
+    const std::vector<float>& wk = pt.wk;
+    const std::vector<double>& cosd = pt.cosd;
+    const std::vector<double>& sind = pt.sind;
+    const std::vector<double>& rd = pt.rd;
+
+    // angular windows: a point can touch the grid iff fx, fy in (-1, N), i.e.
+    // x in (xmin - hx/2, xmax + hx/2); the test uses a margin so fp32 rounding in the
+    // kernels never meets a point outside its window that would touch the grid
+    const double ex = 1e-3 * hx, ey = 1e-3 * hy;
+    const double xl = d.xmin - 0.5 * hx - ex, xh = d.xmax + 0.5 * hx + ex;
+    const double yl = d.ymin - 0.5 * hy - ey, yh = d.ymax + 0.5 * hy + ey;
+    std::vector<int2> win((size_t)D * n_kgrp);
+    std::vector<unsigned char> mask(M);
+    long long pts = 0, on_grid = 0;
+    const double gxl = d.xmin - 0.5 * hx, gxh = d.xmax + 0.5 * hx, gyl = d.ymin - 0.5 * hy, gyh = d.ymax + 0.5 * hy;
+    for (int di = 0; di < D; ++di) {
+        const double dx = d.det_xy_host[2 * di], dy = d.det_xy_host[2 * di + 1];
+        for (int gi = 0; gi < n_kgrp; ++gi) {
+            std::fill(mask.begin(), mask.end(), 0);
+            const int k_end = std::min(T, (gi + 1) * KGRP);
+            for (int k = gi * KGRP; k < k_end; ++k) {
+                const double r = rd[k];
+                // quick reject: circle entirely off the extended box
+                const double cx = std::min(std::max(dx, xl), xh), cy = std::min(std::max(dy, yl), yh);
+                const double dmin = hypot(dx - cx, dy - cy);
+                const double dmax = std::max(std::max(hypot(dx - xl, dy - yl), hypot(dx - xh, dy - yl)),
+                                             std::max(hypot(dx - xl, dy - yh), hypot(dx - xh, dy - yh)));
+                if (r < dmin - 1e-9 || r > dmax + 1e-9) continue;
+                for (int m = 0; m < M; ++m) {
+                    const double x = dx + r * cosd[m], y = dy + r * sind[m];
+                    if (x > gxl && x < gxh && y > gyl && y < gyh) ++on_grid;  // touches the grid
+                    if (!mask[m] && x > xl && x < xh && y > yl && y < yh) mask[m] = 1;
+                }
+            }
+            int2 w = covering_window(mask, M);
+            win[(size_t)di * n_kgrp + gi] = w;
+            pts += (long long)w.y * (k_end - gi * KGRP);
+        }
+    }
+    g->points_per_apply = pts;
+    g->points_on_grid = on_grid;
+
+    AdjWork aw;
+    {
+        int sms = 152;
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
+        const int rc = adjoint_worklist(d, pt, (double)std::max(1, sms) * adjoint_blocks_per_sm(), aw);
+        if (rc) {
+            delete g;
+            return rc;
+        }
+    }
+    g->adj_tiles_x = aw.tiles_x;
+    g->adj_tiles = aw.tiles;
+    g->adj_candidates = aw.candidates;
+    g->adj_item_cost = aw.cost;
+    const std::vector<int4>& rays = aw.rays;
+    const std::vector<AdjItem>& items = aw.items;
     g->adj_items = (int)items.size();
 
     cudaError_t e = cudaSuccess;
@@ -418,13 +531,11 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     if (e == cudaSuccess) e = cudaMalloc(&g->rk, sizeof(float) * T);
     if (e == cudaSuccess) e = cudaMalloc(&g->wk, sizeof(float) * T);
     if (e == cudaSuccess) e = cudaMalloc(&g->win, sizeof(int2) * win.size());
-    if (e == cudaSuccess) e = cudaMalloc(&g->adj_box, sizeof(int4) * box.size());
-    if (e == cudaSuccess) e = cudaMemcpy(g->adj_box, box.data(), sizeof(int4) * box.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&g->adj_units, sizeof(int4) * std::max<size_t>(1, units.size()));
-    if (e == cudaSuccess && !units.empty())
-        e = cudaMemcpy(g->adj_units, units.data(), sizeof(int4) * units.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMalloc(&g->adj_item, sizeof(int4) * items.size());
-    if (e == cudaSuccess) e = cudaMemcpy(g->adj_item, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&g->adj_rays, sizeof(int4) * rays.size());
+    if (e == cudaSuccess) e = cudaMemcpy(g->adj_rays, rays.data(), sizeof(int4) * rays.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&g->adj_item, sizeof(AdjItem) * items.size());
+    if (e == cudaSuccess)
+        e = cudaMemcpy(g->adj_item, items.data(), sizeof(AdjItem) * items.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->det, det.data(), sizeof(float2) * D, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->cs, cs.data(), sizeof(float2) * M, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->rk, rk.data(), sizeof(float) * T, cudaMemcpyHostToDevice);
@@ -449,6 +560,49 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     v.wk = g->wk;
     v.win = g->win;
     *out = g;
+    return PAT_OK;
+}
+
+extern "C" int pat_adjoint_worklist(const pat_geometry_desc* desc, int slots, int* rays_host, long long rays_cap,
+                                    int* items_host, long long items_cap, long long* counts3_host) {
+    if (!desc || !counts3_host) return fail(PAT_ERR_INVALID_ARG, "pat_adjoint_worklist: NULL argument");
+    const int vrc = check_desc(*desc);
+    if (vrc) return vrc;
+    double s = slots;
+    if (slots <= 0) {
+        int dev = 0, sms = 152;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PAT_ERR_CUDA, "pat_adjoint_worklist: no device to size the work list for (pass slots > 0)");
+        }
+        s = (double)sms * adjoint_blocks_per_sm();
+    }
+    AdjWork aw;
+    const int rc = adjoint_worklist(*desc, point_tables(*desc), s, aw);
+    if (rc) return rc;
+    counts3_host[0] = (long long)aw.rays.size();
+    counts3_host[1] = (long long)aw.items.size();
+    counts3_host[2] = aw.candidates;
+    if ((rays_host && rays_cap < counts3_host[0]) || (items_host && items_cap < counts3_host[1]))
+        return fail(PAT_ERR_INVALID_ARG, "pat_adjoint_worklist: output capacity too small");
+    if (rays_host)
+        for (size_t i = 0; i < aw.rays.size(); ++i) {
+            rays_host[4 * i] = aw.rays[i].x;
+            rays_host[4 * i + 1] = aw.rays[i].y;
+            rays_host[4 * i + 2] = aw.rays[i].z;
+            rays_host[4 * i + 3] = aw.rays[i].w;
+        }
+    if (items_host)
+        for (size_t i = 0; i < aw.items.size(); ++i) {
+            const AdjItem& it = aw.items[i];
+            int* o = items_host + 5 * i;
+            o[0] = it.tile;
+            o[1] = it.ray0;
+            o[2] = it.nray;
+            o[3] = it.c0;
+            o[4] = it.c1;
+        }
     return PAT_OK;
 }
 

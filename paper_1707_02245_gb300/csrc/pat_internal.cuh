@@ -64,6 +64,14 @@ struct GeomView {
 constexpr int KGRP = 8;        // radii per angular-window group
 constexpr int MAX_QUAD_M = 8192;
 constexpr int ATILE = 32;      // K^T pixel tile side
+constexpr int ARAYS = 512;     // most ray segments one K^T work item holds
+
+// One K^T work item: candidates [c0, c1) of tile `tile`'s concatenated ray segments,
+// which lie on the nray segments rays[ray0 .. ray0 + nray); rays[ray0 + nray] is the next
+// segment of the tile or its sentinel, whose prefix ends the last segment.
+struct AdjItem {
+    int tile, ray0, nray, c0, c1, pad0, pad1, pad2;
+};
 
 struct PrecondCache {
     float* krow = nullptr;      // K 1 per data row (S), summed in FP64
@@ -85,11 +93,11 @@ struct pat_geometry {
     float* rk = nullptr;
     float* wk = nullptr;
     int2* win = nullptr;
-    int4* adj_box = nullptr;          // per (tile, detector): {k0, nk, m0, nm} candidate box of K^T
-    int4* adj_units = nullptr;        // K^T work units {detector, first ray, rays, box index}
-    int4* adj_item = nullptr;         // K^T work items (one CTA each) {tile, first unit, end unit, 0}
+    int4* adj_rays = nullptr;         // K^T ray segments {detector, angle, first k, prefix}, per tile + sentinel
+    pat::AdjItem* adj_item = nullptr;  // K^T work items, one CTA each
     int adj_tiles_x = 0, adj_tiles = 0, adj_items = 0;
-    std::vector<float> adj_item_cost;  // estimated candidates per work item (host)
+    long long adj_candidates = 0;     // candidate points of one K^T application
+    std::vector<float> adj_item_cost;  // estimated cost per work item (host)
     std::vector<double> det_xy;        // detector positions (host copy, 2 per detector)
     pat::GeomView view;
     // lazily computed preconditioner sums
@@ -204,9 +212,8 @@ struct AdjArgs {       // fixed-point K^T y, one work item per block
     int premul;
     const unsigned* ymax_bits;
     const float* tile_kmax;
-    const int4* box;
-    const int4* units;
-    const int4* items;
+    const int4* rays;
+    const AdjItem* items;
     int* acc_out;            // N*N fixed-point image, added to with integer atomics
     int tiles_x;
     const int* stop;
@@ -223,6 +230,8 @@ AdjArgs make_adj_args(const pat_geometry* g, const float* y, const float* premul
 int launch_forward_prox_b(const FwdProxArgs* args, const int2* map, int nblocks, cudaStream_t st);
 int launch_forward_gap_b(const FwdGapArgs* args, const int2* map, int nblocks, cudaStream_t st);
 int launch_adjoint_b(const AdjArgs* args, const int2* map, int nblocks, bool premul, cudaStream_t st);
+// CTAs of the K^T kernel that one SM holds at once (sizes the work items)
+int adjoint_blocks_per_sm();
 int forward_row_blocks(const pat_geometry* g);    // blocks of one forward launch
 int forward_rows_per_block();
 

@@ -227,113 +227,83 @@ __global__ void __launch_bounds__(ROW_THREADS) k_forward_gap_b(const FwdGapArgs*
 // fixed-point tiles add exactly (in any order) into one image with integer atomics.
 // ---------------------------------------------------------------------------------
 constexpr int ATHREADS = 256;
+#ifndef PAT_ADJ_MIN_BLOCKS
+#define PAT_ADJ_MIN_BLOCKS 5
+#endif
+constexpr int ADJ_MIN_BLOCKS = PAT_ADJ_MIN_BLOCKS;   // resident CTAs per SM the register budget allows
 
 
+// One work item of K^T: an equal share [c0, c1) of one tile's candidate list (the
+// concatenated ray segments the host cut to the tile's tap window).  Thread t takes the
+// contiguous run [c0 + t C, c0 + (t + 1) C), C = ceil((c1 - c0) / ATHREADS), so every
+// thread has the same number of candidates and lanes that add at the same time sit C
+// candidates apart (different pixels).  Each candidate is evaluated with the forward's
+// FP32 point arithmetic; one whose taps fall outside the tile window is skipped.
 template <bool PREMUL>
 __device__ __forceinline__ void adjoint_item(const AdjArgs& a, int item_index) {
     const GeomView& g = a.g;
-    const int N = g.n, T = g.n_t, M = g.quad_m, D = g.n_det;
-    const int4 item = __ldg(&a.items[item_index]);
-    const int tile = item.x;
+    const int N = g.n, T = g.n_t;
+    const AdjItem* ip = a.items + item_index;
+    const int tile = __ldg(&ip->tile), ray0 = __ldg(&ip->ray0), nray = __ldg(&ip->nray);
+    const int c0 = __ldg(&ip->c0), c1 = __ldg(&ip->c1);
     const int x0 = (tile % a.tiles_x) * ATILE, y0 = (tile / a.tiles_x) * ATILE;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     constexpr int AW = ATILE + 2;
     __shared__ int acc[AW * AW];
+    __shared__ int4 s_ray[ARAYS + 1];   // {detector, angle, first k, prefix}
     for (int c = tid; c < AW * AW; c += ATHREADS) acc[c] = 0;
+    for (int i = tid; i <= nray; i += ATHREADS) s_ray[i] = __ldg(&a.rays[ray0 + i]);
     const float bound = __uint_as_float(*a.ymax_bits) * __ldg(&a.tile_kmax[tile]);
     const float scale = 1073741824.0f / bound;  // 2^30 / bound
-    // tap region of the tile in pixel coordinates (fx in [x0 - 1, x0 + ATILE)), widened
-    // by 1e-3 pixel so FP32 rounding never drops a candidate
-    const float rx0 = x0 - 1.001f, rx1 = x0 + ATILE + 0.001f;
-    const float ry0 = y0 - 1.001f, ry1 = y0 + ATILE + 0.001f;
-    const float r_first = __ldg(&g.rk[0]);
-    const float inv_dr = T > 1 ? (float)(T - 1) / (__ldg(&g.rk[T - 1]) - r_first) : 0.f;
+    const float* __restrict__ rk = g.rk;
+    const float* __restrict__ wk = g.wk;
+    const float* __restrict__ y = a.y;
     __syncthreads();
 
-    // per-warp ray table: for up to 32 rays, the first radius of the ray's candidate
-    // segment, the segment length, its exclusive prefix in the warp's flattened list
-    __shared__ int s_m[ATHREADS / 32][32], s_ks[ATHREADS / 32][32], s_ex[ATHREADS / 32][33];
-    if (bound > 0.f && isfinite(bound)) {
-        for (int u = item.y + warp; u < item.z; u += ATHREADS / 32) {
-            const int4 un = __ldg(&a.units[u]);   // {detector, first ray, rays, box}
-            const int d = un.x, m0 = un.y, nm = un.z;
-            const int4 bx = __ldg(&a.box[un.w]);
-            const int kb = bx.x, ke = bx.x + bx.y;
-            const float2 det = __ldg(&g.det[d]);
-            const float* yrow = a.y + (size_t)d * T;
-            for (int mb = 0; mb < nm; mb += 32) {
-                // 1. lane j finds the radius interval of ray mb + j: the ray meets the
-                //    (convex) tap region in one segment [t0, t1]
-                int len = 0, ks = 0, m = 0;
-                if (mb + lane < nm) {
-                    m = m0 + mb + lane;
-                    if (m >= M) m -= M;
-                    const float2 cs = __ldg(&g.cs[m]);
-                    const float ic = 1.f / cs.x, is = 1.f / cs.y;
-                    const float tx0 = (rx0 - det.x) * ic, tx1 = (rx1 - det.x) * ic;
-                    const float ty0 = (ry0 - det.y) * is, ty1 = (ry1 - det.y) * is;
-                    const float t0 = fmaxf(fminf(tx0, tx1), fminf(ty0, ty1));
-                    const float t1 = fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1));
-                    if (!(t1 < t0)) {  // NaN keeps the whole box
-                        const float kf0 = (t0 - r_first) * inv_dr, kf1 = (t1 - r_first) * inv_dr;
-                        const int kr0 = isfinite(kf0) ? max(kb, (int)floorf(fmaxf(kf0, -1e9f)) - 1) : kb;
-                        const int kr1 = isfinite(kf1) ? min(ke, (int)ceilf(fminf(kf1, 1e9f)) + 2) : ke;
-                        len = max(0, kr1 - kr0);
-                        ks = kr0;
-                    }
-                }
-                // 2. exclusive prefix of the segment lengths over the warp
-                int pre = len;
+    if (bound > 0.f && isfinite(bound) && nray > 0) {
+        const int C = (c1 - c0 + ATHREADS - 1) / ATHREADS;
+        int p = c0 + tid * C;
+        const int p_end = min(c1, p + C);
+        if (p < p_end) {
+            int j = 0;  // last segment whose prefix is <= p (the one holding p)
 #pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const int v = __shfl_up_sync(0xffffffffu, pre, o);
-                    if (lane >= o) pre += v;
+            for (int step = ARAYS / 2; step > 0; step >>= 1)
+                if (j + step < nray && s_ray[j + step].w <= p) j += step;
+            // one flat loop over the run: a segment change is a short branch, so the lanes
+            // of a warp stay converged on the point arithmetic
+            int4 ray = s_ray[j];
+            int seg_end = s_ray[j + 1].w;
+            float2 det = __ldg(&g.det[ray.x]);
+            float2 cs = __ldg(&g.cs[ray.y]);
+            const float* __restrict__ yrow = y + (size_t)ray.x * T;
+            int k = ray.z + (p - ray.w);
+            for (; p < p_end; ++p, ++k) {
+                if (p == seg_end) {  // segments are never empty
+                    ++j;
+                    ray = s_ray[j];
+                    seg_end = s_ray[j + 1].w;
+                    det = __ldg(&g.det[ray.x]);
+                    cs = __ldg(&g.cs[ray.y]);
+                    yrow = y + (size_t)ray.x * T;
+                    k = ray.z;
                 }
-                const int total = __shfl_sync(0xffffffffu, pre, 31);
-                s_m[warp][lane] = m;
-                s_ks[warp][lane] = ks;
-                s_ex[warp][lane] = pre - len;
-                if (lane == 31) s_ex[warp][32] = total;
-                __syncwarp();
-                // 3. lane l takes the contiguous run [l C, (l+1) C) of the flattened list:
-                //    simultaneous lanes sit C candidates apart on different rays
-                const int C = (total + 31) >> 5;
-                const int p0 = lane * C, p1 = min(total, p0 + C);
-                if (p0 < p1) {
-                    int j = 0;  // last ray whose prefix is <= p0 (it contains p0)
-#pragma unroll
-                    for (int step = 16; step > 0; step >>= 1)
-                        if (j + step < 32 && s_ex[warp][j + step] <= p0) j += step;
-                    int seg_end = s_ex[warp][j + 1];
-                    int k = s_ks[warp][j] + (p0 - s_ex[warp][j]);
-                    float2 cs = __ldg(&g.cs[s_m[warp][j]]);
-                    for (int pp = p0; pp < p1; ++pp, ++k) {
-                        while (pp == seg_end) {  // next non-empty ray
-                            ++j;
-                            seg_end = s_ex[warp][j + 1];
-                            k = s_ks[warp][j];
-                            cs = __ldg(&g.cs[s_m[warp][j]]);
-                        }
-                        Taps t;
-                        point_coords(g, det, __ldg(&g.rk[k]), cs, t);
-                        // taps in the tile window (ring cells off the grid are dropped later)
-                        const int li = t.i0 - x0 + 1, lj = t.j0 - y0 + 1;
-                        if ((unsigned)li > (unsigned)ATILE || (unsigned)lj > (unsigned)ATILE) continue;
-                        const float c = (PREMUL ? __ldg(&yrow[k]) : __ldg(&yrow[k]) * __ldg(&g.wk[k])) * scale;
-                        const float c0 = c * (1.f - t.ay), c1 = c * t.ay;
-                        int* q = acc + lj * AW + li;
-                        atomicAdd(q, __float2int_rn(c0 * (1.f - t.ax)));
-                        atomicAdd(q + 1, __float2int_rn(c0 * t.ax));
-                        atomicAdd(q + AW, __float2int_rn(c1 * (1.f - t.ax)));
-                        atomicAdd(q + AW + 1, __float2int_rn(c1 * t.ax));
-                    }
-                }
-                __syncwarp();
+                Taps t;
+                point_coords(g, det, __ldg(&rk[k]), cs, t);
+                // taps in the tile window (ring cells off the tile are dropped later)
+                const int li = t.i0 - x0 + 1, lj = t.j0 - y0 + 1;
+                if ((unsigned)li > (unsigned)ATILE || (unsigned)lj > (unsigned)ATILE) continue;
+                const float c = (PREMUL ? __ldg(&yrow[k]) : __ldg(&yrow[k]) * __ldg(&wk[k])) * scale;
+                const float cy0 = c * (1.f - t.ay), cy1 = c * t.ay;
+                int* q = acc + lj * AW + li;
+                atomicAdd(q, __float2int_rn(cy0 * (1.f - t.ax)));
+                atomicAdd(q + 1, __float2int_rn(cy0 * t.ax));
+                atomicAdd(q + AW, __float2int_rn(cy1 * (1.f - t.ax)));
+                atomicAdd(q + AW + 1, __float2int_rn(cy1 * t.ax));
             }
         }
     }
     __syncthreads();
-    // detector groups of one tile share its scale, so their fixed-point partial sums add
+    // work items of one tile share its scale, so their fixed-point partial sums add
     // exactly (and in any order) with integer atomics
     for (int c = tid; c < ATILE * ATILE; c += ATHREADS) {
         const int lx = c % ATILE, ly = c / ATILE;
@@ -345,13 +315,13 @@ __device__ __forceinline__ void adjoint_item(const AdjArgs& a, int item_index) {
 }
 
 template <bool PREMUL>
-__global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles(AdjArgs a) {
+__global__ void __launch_bounds__(ATHREADS, ADJ_MIN_BLOCKS) k_adjoint_tiles(AdjArgs a) {
     if (a.stop && *(volatile const int*)a.stop) return;
     adjoint_item<PREMUL>(a, blockIdx.x);
 }
 
 template <bool PREMUL>
-__global__ void __launch_bounds__(ATHREADS) k_adjoint_tiles_b(const AdjArgs* __restrict__ args,
+__global__ void __launch_bounds__(ATHREADS, ADJ_MIN_BLOCKS) k_adjoint_tiles_b(const AdjArgs* __restrict__ args,
                                                             const int2* __restrict__ map) {
     const int2 pm = map[blockIdx.x];
     const AdjArgs& a = args[pm.x];   // (a shared copy would be reloaded after every shared atomic)
@@ -513,13 +483,21 @@ AdjArgs make_adj_args(const pat_geometry* g, const float* y, const float* premul
     a.premul = premul ? 1 : 0;
     a.ymax_bits = ymax_bits;
     a.tile_kmax = g->pc.tile_kmax;
-    a.box = g->adj_box;
-    a.acc_out = acc;
-    a.units = g->adj_units;
+    a.rays = g->adj_rays;
     a.items = g->adj_item;
+    a.acc_out = acc;
     a.tiles_x = g->adj_tiles_x;
     a.stop = stop;
     return a;
+}
+
+int adjoint_blocks_per_sm() {
+    int n = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_adjoint_tiles_b<true>, ATHREADS, 0) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = 4;
+    }
+    return n;
 }
 
 int launch_adjoint_b(const AdjArgs* args, const int2* map, int nblocks, bool premul, cudaStream_t st) {
@@ -536,18 +514,7 @@ int launch_adjoint_b(const AdjArgs* args, const int2* map, int nblocks, bool pre
 
 static int launch_adjoint_fixed(const pat_geometry* g, const float* y, const float* premul,
                                 const unsigned* ymax_bits, int* acc, const int* stop, cudaStream_t st) {
-    AdjArgs a;
-    a.g = g->view;
-    a.y = premul ? premul : y;
-    a.premul = premul ? 1 : 0;
-    a.ymax_bits = ymax_bits;
-    a.tile_kmax = g->pc.tile_kmax;
-    a.box = g->adj_box;
-    a.acc_out = acc;
-    a.units = g->adj_units;
-    a.items = g->adj_item;
-    a.tiles_x = g->adj_tiles_x;
-    a.stop = stop;
+    const AdjArgs a = make_adj_args(g, y, premul, ymax_bits, acc, stop);
     if (a.premul)
         k_adjoint_tiles<true><<<g->adj_items, ATHREADS, 0, st>>>(a);
     else
@@ -564,18 +531,7 @@ int launch_adjoint_into(const pat_geometry* g, const float* y, unsigned* ymax_bi
     const long long S = (long long)g->desc.n_det * g->desc.n_t;
     k_absmax<<<std::min(4 * 152, ceil_div(S, 256)), 256, 0, st>>>(y, S, ymax_bits);
     PAT_LAUNCH_CHECK("k_absmax");
-    AdjArgs a;
-    a.g = g->view;
-    a.y = y;
-    a.premul = 0;
-    a.ymax_bits = ymax_bits;
-    a.tile_kmax = g->pc.tile_kmax;
-    a.box = g->adj_box;
-    a.units = g->adj_units;
-    a.items = g->adj_item;
-    a.acc_out = acc;
-    a.tiles_x = g->adj_tiles_x;
-    a.stop = nullptr;
+    const AdjArgs a = make_adj_args(g, y, nullptr, ymax_bits, acc, nullptr);
     k_adjoint_tiles<false><<<g->adj_items, ATHREADS, 0, st>>>(a);
     PAT_LAUNCH_CHECK("k_adjoint_tiles");
     dim3 blk(32, 8), grd(ceil_div(N, 32), ceil_div(N, 8));
