@@ -233,7 +233,6 @@ int launch_adjoint_b(const AdjArgs* args, const int2* map, int nblocks, bool pre
 // CTAs of the K^T kernel that one SM holds at once (sizes the work items)
 int adjoint_blocks_per_sm();
 int forward_row_blocks(const pat_geometry* g);    // blocks of one forward launch
-int forward_rows_per_block();
 
 // Host entry points implemented in projector.cu and used by pdhg.cu
 // ---- the wavelet model (wavelet.cu) ----

@@ -41,7 +41,25 @@ __device__ __forceinline__ float fetch4(const float* __restrict__ u, int N, cons
 // angular window at m = m_first + ph, + ph + 4, ...  so at every step the warp evaluates
 // a 4 (angles) x 8 (radii) patch of the polar grid, which is a compact patch of pixels.
 constexpr int NPH = 4;
-constexpr int ROWS_PER_BLOCK = 32;           // 4 warps x 8 radii
+// unroll factors of the forward's angular loop and of the K^T candidate loop (0: the
+// compiler's choice)
+#ifndef PAT_FWD_UNROLL
+#define PAT_FWD_UNROLL 0
+#endif
+#ifndef PAT_ADJ_UNROLL
+#define PAT_ADJ_UNROLL 0
+#endif
+constexpr int FWD_UNROLL = PAT_FWD_UNROLL;
+constexpr int ADJ_UNROLL = PAT_ADJ_UNROLL;
+// A row block is 4 warps: FWD_DW adjacent detectors times FWD_KW groups of 8 radii.
+#ifndef PAT_FWD_DW
+#define PAT_FWD_DW 4
+#endif
+constexpr int ROW_WARPS = 4;
+constexpr int FWD_DW = PAT_FWD_DW;
+constexpr int FWD_KW = ROW_WARPS / FWD_DW;
+static_assert(FWD_DW * FWD_KW == ROW_WARPS, "a row block is 4 warps");
+constexpr int ROWS_PER_BLOCK = ROW_WARPS * KGRP;
 constexpr int ROW_THREADS = ROWS_PER_BLOCK * NPH;
 
 struct RowLane {
@@ -49,18 +67,24 @@ struct RowLane {
     bool valid;
 };
 
-// lane of row block kb of detector d
-__device__ __forceinline__ RowLane row_lane(const GeomView& g, int kb, int d) {
+// lane of row block (kb, db): warp w takes detector db FWD_DW + w / FWD_KW and the radii
+// group kb FWD_KW + w % FWD_KW; lanes past the last detector or radius are not valid
+// (their detector index is clamped so that table reads stay in range)
+__device__ __forceinline__ RowLane row_lane(const GeomView& g, int kb, int db) {
     RowLane r;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int d = db * FWD_DW + warp / FWD_KW;
     r.ph = lane >> 3;
-    r.d = d;
-    r.k = kb * ROWS_PER_BLOCK + warp * KGRP + (lane & 7);
-    r.valid = r.k < g.n_t;
+    r.k = (kb * FWD_KW + warp % FWD_KW) * KGRP + (lane & 7);
+    r.valid = r.k < g.n_t && d < g.n_det;
+    r.d = min(d, g.n_det - 1);
     return r;
 }
 
-__device__ __forceinline__ int row_blocks(const GeomView& g) { return (g.n_t + ROWS_PER_BLOCK - 1) / ROWS_PER_BLOCK; }
+// row blocks along the radii (the grid's other dimension runs over detector groups)
+__device__ __forceinline__ int row_blocks(const GeomView& g) {
+    return (g.n_t + FWD_KW * KGRP - 1) / (FWD_KW * KGRP);
+}
 
 // Partial integral of the bilinear image over circle (d, k) for one angular phase.
 // QUAD: u points at (N+1)^2 float4 quads (one load per point); otherwise u is the plain
@@ -73,6 +97,9 @@ __device__ __forceinline__ float circle_partial(const GeomView& g, const float* 
     float acc = 0.f;
     int m = w.x + rl.ph;
     if (m >= g.quad_m) m -= g.quad_m;
+#if PAT_FWD_UNROLL > 0
+#pragma unroll FWD_UNROLL
+#endif
     for (int j = rl.ph; j < w.y; j += NPH) {
         const float2 cs = __ldg(&g.cs[m]);
         m += NPH;
@@ -277,6 +304,9 @@ __device__ __forceinline__ void adjoint_item(const AdjArgs& a, int item_index) {
             float2 cs = __ldg(&g.cs[ray.y]);
             const float* __restrict__ yrow = y + (size_t)ray.x * T;
             int k = ray.z + (p - ray.w);
+#if PAT_ADJ_UNROLL > 0
+#pragma unroll ADJ_UNROLL
+#endif
             for (; p < p_end; ++p, ++k) {
                 if (p == seg_end) {  // segments are never empty
                     ++j;
@@ -397,7 +427,7 @@ __global__ void k_double_to_float(const double* __restrict__ a, float* __restric
 }
 
 static dim3 row_grid(const pat_geometry* g) {
-    return dim3(ceil_div(g->desc.n_t, ROWS_PER_BLOCK), g->desc.n_det);
+    return dim3(ceil_div(g->desc.n_t, FWD_KW * KGRP), ceil_div(g->desc.n_det, FWD_DW));
 }
 
 int forward_row_blocks(const pat_geometry* g) {
@@ -405,7 +435,6 @@ int forward_row_blocks(const pat_geometry* g) {
     return gr.x * gr.y;
 }
 
-int forward_rows_per_block() { return ROWS_PER_BLOCK; }
 
 int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y, cudaStream_t st) {
     (void)padded;
