@@ -51,14 +51,17 @@ constexpr int NPH = 4;
 #endif
 constexpr int FWD_UNROLL = PAT_FWD_UNROLL;
 constexpr int ADJ_UNROLL = PAT_ADJ_UNROLL;
-// A row block is 4 warps: FWD_DW adjacent detectors times FWD_KW groups of 8 radii.
+// A row block is ROW_WARPS warps: FWD_DW adjacent detectors times FWD_KW groups of 8 radii.
 #ifndef PAT_FWD_DW
-#define PAT_FWD_DW 4
+#define PAT_FWD_DW 8
 #endif
-constexpr int ROW_WARPS = 4;
+#ifndef PAT_FWD_WARPS
+#define PAT_FWD_WARPS 16
+#endif
+constexpr int ROW_WARPS = PAT_FWD_WARPS;
 constexpr int FWD_DW = PAT_FWD_DW;
 constexpr int FWD_KW = ROW_WARPS / FWD_DW;
-static_assert(FWD_DW * FWD_KW == ROW_WARPS, "a row block is 4 warps");
+static_assert(FWD_DW * FWD_KW == ROW_WARPS, "FWD_DW must divide ROW_WARPS");
 constexpr int ROWS_PER_BLOCK = ROW_WARPS * KGRP;
 constexpr int ROW_THREADS = ROWS_PER_BLOCK * NPH;
 
