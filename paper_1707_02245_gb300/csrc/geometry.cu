@@ -12,6 +12,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cstring>
+#include <queue>
 #include <vector>
 
 #include "pat_internal.cuh"
@@ -254,7 +255,8 @@ static PointTables point_tables(const pat_geometry_desc& d) {
 }
 
 struct AdjWork {
-    int tiles_x = 0, tiles = 0;
+    int tiles_x = 0, tiles = 0;     // scale tiles
+    int wtiles_x = 0, wtiles = 0;   // work tiles
     long long candidates = 0;
     std::vector<int4> rays;
     std::vector<AdjItem> items;
@@ -268,15 +270,19 @@ static int adjoint_worklist(const pat_geometry_desc& d, const PointTables& pt, d
     const double ex = 1e-3 * hx, ey = 1e-3 * hy;
     const std::vector<float2>& det = pt.det;
     const std::vector<float2>& cs = pt.cs;
-    // K^T candidate boxes: for every ATILE x ATILE pixel tile and detector, the (k, m)
-    // polar box of the tile's tap region (points with i0 in [x0-1, x0+ATILE-1], same in
+    // K^T candidate boxes: for every WTILE x WTILE work tile and detector, the (k, m)
+    // polar box of the tile's tap region (points with i0 in [x0-1, x0+WTILE-1], same in
     // y), with one index of margin on every side; FP64 on the host
-    const int tiles_x = (N + ATILE - 1) / ATILE, tiles = tiles_x * tiles_x;
+    w.tiles_x = (N + ATILE - 1) / ATILE;
+    w.tiles = w.tiles_x * w.tiles_x;
+    const int tiles_x = (N + WTILE - 1) / WTILE, tiles = tiles_x * tiles_x;
+    w.wtiles_x = tiles_x;
+    w.wtiles = tiles;
     std::vector<int4> box((size_t)tiles * D);
     for (int t = 0; t < tiles; ++t) {
-        const int x0 = (t % tiles_x) * ATILE, y0 = (t / tiles_x) * ATILE;
-        const double rx0 = d.xmin + (x0 - 0.5) * hx - ex, rx1 = d.xmin + (x0 + ATILE + 0.5) * hx + ex;
-        const double ry0 = d.ymin + (y0 - 0.5) * hy - ey, ry1 = d.ymin + (y0 + ATILE + 0.5) * hy + ey;
+        const int x0 = (t % tiles_x) * WTILE, y0 = (t / tiles_x) * WTILE;
+        const double rx0 = d.xmin + (x0 - 0.5) * hx - ex, rx1 = d.xmin + (x0 + WTILE + 0.5) * hx + ex;
+        const double ry0 = d.ymin + (y0 - 0.5) * hy - ey, ry1 = d.ymin + (y0 + WTILE + 0.5) * hy + ey;
         for (int di = 0; di < D; ++di) {
             const double dx = d.det_xy_host[2 * di], dy = d.det_xy_host[2 * di + 1];
             const double cx = std::min(std::max(dx, rx0), rx1), cy = std::min(std::max(dy, ry0), ry1);
@@ -311,16 +317,13 @@ static int adjoint_worklist(const pat_geometry_desc& d, const PointTables& pt, d
             box[(size_t)t * D + di] = make_int4(k0, std::max(0, k1 - k0 + 1), m0, nm);
         }
     }
-    w.tiles_x = tiles_x;
-    w.tiles = tiles;
 
     // K^T work list.  Every ray (detector d, angle m) of a tile's polar box is cut to the
     // radius interval where its points can have taps in the tile's window [x0 - 1, x0 +
-    // ATILE) x [y0 - 1, y0 + ATILE) (the window is convex, so the interval is one
-    // segment).  The cut is FP64 arithmetic on the same FP32 tables the kernels read, with
-    // a margin of 1e-3 pixel on the window and of one radius before and two after the
-    // segment, far beyond the FP32 rounding of a point's position; the kernel still tests
-    // every candidate exactly.  A tile's non-empty segments, concatenated, are its
+    // WTILE) x [y0 - 1, y0 + WTILE) (the window is convex, so the interval is one
+    // segment).  The cut is FP64 arithmetic on the same FP32 tables the kernels read, on
+    // the window widened by 1e-3 pixel, far beyond the FP32 rounding of a point's position
+    // (about 1e-5 pixel); the kernel still tests every candidate exactly.  A tile's non-empty segments, concatenated, are its
     // candidate list: rays[] holds {d, m, first k, exclusive prefix} per segment and a
     // sentinel {-1, 0, 0, total} after each tile.  A work item (one CTA) is an equal share
     // of one tile's list; the shares are sized so that the items fill whole waves of the
@@ -332,9 +335,9 @@ static int adjoint_worklist(const pat_geometry_desc& d, const PointTables& pt, d
         std::vector<long long> tile_base(tiles + 1, 0), tile_total(tiles, 0);
         for (int t = 0; t < tiles; ++t) {
             tile_base[t] = (long long)rays.size();
-            const int x0 = (t % tiles_x) * ATILE, y0 = (t / tiles_x) * ATILE;
-            const double wx0 = x0 - 1.001, wx1 = x0 + ATILE + 0.001;
-            const double wy0 = y0 - 1.001, wy1 = y0 + ATILE + 0.001;
+            const int x0 = (t % tiles_x) * WTILE, y0 = (t / tiles_x) * WTILE;
+            const double wx0 = x0 - 1.001, wx1 = x0 + WTILE + 0.001;
+            const double wy0 = y0 - 1.001, wy1 = y0 + WTILE + 0.001;
             long long pre = 0;
             for (int di = 0; di < D; ++di) {
                 const int4 bx = box[(size_t)t * D + di];
@@ -361,8 +364,8 @@ static int adjoint_worklist(const pat_geometry_desc& d, const PointTables& pt, d
                     }
                     if (t1 < t0) continue;
                     const double kf0 = (t0 - d.r0) / d.dr - 0.5, kf1 = (t1 - d.r0) / d.dr - 0.5;
-                    const long long k0 = (long long)std::max((double)kb, std::floor(std::max(kf0, -1e15)) - 1);
-                    const long long k1 = (long long)std::min((double)ke, std::ceil(std::min(kf1, 1e15)) + 2);
+                    const long long k0 = (long long)std::max((double)kb, std::ceil(std::max(kf0, -1e15)));
+                    const long long k1 = (long long)std::min((double)ke, std::floor(std::min(kf1, 1e15)) + 1);
                     if (k1 <= k0) continue;
                     rays.push_back(make_int4(di, m, (int)k0, (int)pre));
                     pre += k1 - k0;
@@ -379,23 +382,26 @@ static int adjoint_worklist(const pat_geometry_desc& d, const PointTables& pt, d
         long long total = 0;
         for (int t = 0; t < tiles; ++t) total += tile_total[t];
         w.candidates = total;
-        // pieces per tile: two waves of resident CTAs shared in proportion to the tiles'
-        // candidate counts (largest remainders), at least 1024 candidates a piece
+        // pieces per tile: two waves of resident CTAs (at least 1024 candidates a piece),
+        // each piece going to the tile whose pieces are largest at that point, which
+        // minimises the largest piece
         const long long Q = std::max(1LL, std::min((long long)(2.0 * slots), total / 1024));
         std::vector<long long> n_piece(tiles, 0);
         {
+            std::priority_queue<std::pair<double, int>> heap;   // (piece size, tile)
             long long assigned = 0;
-            std::vector<std::pair<double, int>> rem;
-            for (int t = 0; t < tiles; ++t) {
-                if (tile_total[t] <= 0) continue;
-                const double exact = (double)Q * (double)tile_total[t] / (double)total;
-                n_piece[t] = std::max(1LL, (long long)std::floor(exact));
-                assigned += n_piece[t];
-                rem.push_back({exact - (double)n_piece[t], t});
+            for (int t = 0; t < tiles; ++t)
+                if (tile_total[t] > 0) {
+                    n_piece[t] = 1;
+                    ++assigned;
+                    heap.push({(double)tile_total[t], t});
+                }
+            for (; assigned < Q && !heap.empty(); ++assigned) {
+                const int t = heap.top().second;
+                heap.pop();
+                ++n_piece[t];
+                heap.push({(double)tile_total[t] / (double)n_piece[t], t});
             }
-            std::stable_sort(rem.begin(), rem.end(), [](const std::pair<double, int>& a,
-                                                        const std::pair<double, int>& b) { return a.first > b.first; });
-            for (size_t i = 0; i < rem.size() && assigned < Q; ++i, ++assigned) ++n_piece[rem[i].second];
         }
         for (int t = 0; t < tiles; ++t) {
             const long long cost = tile_total[t];
@@ -519,6 +525,7 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     }
     g->adj_tiles_x = aw.tiles_x;
     g->adj_tiles = aw.tiles;
+    g->adj_wtiles_x = aw.wtiles_x;
     g->adj_candidates = aw.candidates;
     g->adj_item_cost = aw.cost;
     const std::vector<int4>& rays = aw.rays;

@@ -63,10 +63,12 @@ struct GeomView {
 
 constexpr int KGRP = 8;        // radii per angular-window group
 constexpr int MAX_QUAD_M = 8192;
-constexpr int ATILE = 32;      // K^T pixel tile side
+constexpr int ATILE = 32;      // side of the pixel tiles that share one K^T fixed-point scale
+constexpr int WTILE = 32;      // side of the pixel tiles one K^T work item accumulates
+static_assert(ATILE % WTILE == 0, "work tiles nest in scale tiles");
 constexpr int ARAYS = 512;     // most ray segments one K^T work item holds
 
-// One K^T work item: candidates [c0, c1) of tile `tile`'s concatenated ray segments,
+// One K^T work item: candidates [c0, c1) of work tile `tile`'s concatenated ray segments,
 // which lie on the nray segments rays[ray0 .. ray0 + nray); rays[ray0 + nray] is the next
 // segment of the tile or its sentinel, whose prefix ends the last segment.
 struct AdjItem {
@@ -95,7 +97,8 @@ struct pat_geometry {
     int2* win = nullptr;
     int4* adj_rays = nullptr;         // K^T ray segments {detector, angle, first k, prefix}, per tile + sentinel
     pat::AdjItem* adj_item = nullptr;  // K^T work items, one CTA each
-    int adj_tiles_x = 0, adj_tiles = 0, adj_items = 0;
+    int adj_tiles_x = 0, adj_tiles = 0, adj_items = 0;   // scale tiles (ATILE) per row, in all; items
+    int adj_wtiles_x = 0;              // work tiles (WTILE) per row
     long long adj_candidates = 0;     // candidate points of one K^T application
     std::vector<float> adj_item_cost;  // estimated cost per work item (host)
     std::vector<double> det_xy;        // detector positions (host copy, 2 per detector)
@@ -215,7 +218,8 @@ struct AdjArgs {       // fixed-point K^T y, one work item per block
     const int4* rays;
     const AdjItem* items;
     int* acc_out;            // N*N fixed-point image, added to with integer atomics
-    int tiles_x;
+    int tiles_x;             // scale tiles per row
+    int wtiles_x;            // work tiles per row
     const int* stop;
 };
 

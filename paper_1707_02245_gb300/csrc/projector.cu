@@ -261,6 +261,11 @@ constexpr int ATHREADS = 256;
 #define PAT_ADJ_MIN_BLOCKS 5
 #endif
 constexpr int ADJ_MIN_BLOCKS = PAT_ADJ_MIN_BLOCKS;   // resident CTAs per SM the register budget allows
+// first step of the binary search over an item's segments: a power of two with
+// 2 * ASTEP >= ARAYS, so that the halving steps reach every index below ARAYS
+constexpr int pow2_at_least(int x) { return x <= 1 ? 1 : 2 * pow2_at_least((x + 1) / 2); }
+constexpr int ASTEP = pow2_at_least(ARAYS) / 2;
+static_assert(2 * ASTEP >= ARAYS && (ASTEP & (ASTEP - 1)) == 0, "binary search steps");
 
 
 // One work item of K^T: an equal share [c0, c1) of one tile's candidate list (the
@@ -276,14 +281,15 @@ __device__ __forceinline__ void adjoint_item(const AdjArgs& a, int item_index) {
     const AdjItem* ip = a.items + item_index;
     const int tile = __ldg(&ip->tile), ray0 = __ldg(&ip->ray0), nray = __ldg(&ip->nray);
     const int c0 = __ldg(&ip->c0), c1 = __ldg(&ip->c1);
-    const int x0 = (tile % a.tiles_x) * ATILE, y0 = (tile / a.tiles_x) * ATILE;
+    const int x0 = (tile % a.wtiles_x) * WTILE, y0 = (tile / a.wtiles_x) * WTILE;
     const int tid = threadIdx.x;
-    constexpr int AW = ATILE + 2;
+    constexpr int AW = WTILE + 2;
     __shared__ int acc[AW * AW];
     __shared__ int4 s_ray[ARAYS + 1];   // {detector, angle, first k, prefix}
     for (int c = tid; c < AW * AW; c += ATHREADS) acc[c] = 0;
     for (int i = tid; i <= nray; i += ATHREADS) s_ray[i] = __ldg(&a.rays[ray0 + i]);
-    const float bound = __uint_as_float(*a.ymax_bits) * __ldg(&a.tile_kmax[tile]);
+    // the scale of the ATILE tile that holds this work tile
+    const float bound = __uint_as_float(*a.ymax_bits) * __ldg(&a.tile_kmax[(y0 / ATILE) * a.tiles_x + x0 / ATILE]);
     const float scale = 1073741824.0f / bound;  // 2^30 / bound
     const float* __restrict__ rk = g.rk;
     const float* __restrict__ wk = g.wk;
@@ -297,7 +303,7 @@ __device__ __forceinline__ void adjoint_item(const AdjArgs& a, int item_index) {
         if (p < p_end) {
             int j = 0;  // last segment whose prefix is <= p (the one holding p)
 #pragma unroll
-            for (int step = ARAYS / 2; step > 0; step >>= 1)
+            for (int step = ASTEP; step > 0; step >>= 1)
                 if (j + step < nray && s_ray[j + step].w <= p) j += step;
             // one flat loop over the run: a segment change is a short branch, so the lanes
             // of a warp stay converged on the point arithmetic
@@ -324,7 +330,7 @@ __device__ __forceinline__ void adjoint_item(const AdjArgs& a, int item_index) {
                 point_coords(g, det, __ldg(&rk[k]), cs, t);
                 // taps in the tile window (ring cells off the tile are dropped later)
                 const int li = t.i0 - x0 + 1, lj = t.j0 - y0 + 1;
-                if ((unsigned)li > (unsigned)ATILE || (unsigned)lj > (unsigned)ATILE) continue;
+                if ((unsigned)li > (unsigned)WTILE || (unsigned)lj > (unsigned)WTILE) continue;
                 const float c = (PREMUL ? __ldg(&yrow[k]) : __ldg(&yrow[k]) * __ldg(&wk[k])) * scale;
                 const float cy0 = c * (1.f - t.ay), cy1 = c * t.ay;
                 int* q = acc + lj * AW + li;
@@ -338,8 +344,8 @@ __device__ __forceinline__ void adjoint_item(const AdjArgs& a, int item_index) {
     __syncthreads();
     // work items of one tile share its scale, so their fixed-point partial sums add
     // exactly (and in any order) with integer atomics
-    for (int c = tid; c < ATILE * ATILE; c += ATHREADS) {
-        const int lx = c % ATILE, ly = c / ATILE;
+    for (int c = tid; c < WTILE * WTILE; c += ATHREADS) {
+        const int lx = c % WTILE, ly = c / WTILE;
         const int gx = x0 + lx, gy = y0 + ly;
         if (gx >= N || gy >= N) continue;
         const int v = acc[(ly + 1) * AW + lx + 1];
@@ -519,6 +525,7 @@ AdjArgs make_adj_args(const pat_geometry* g, const float* y, const float* premul
     a.items = g->adj_item;
     a.acc_out = acc;
     a.tiles_x = g->adj_tiles_x;
+    a.wtiles_x = g->adj_wtiles_x;
     a.stop = stop;
     return a;
 }

@@ -15,7 +15,7 @@ import pytest
 import paper_1707_02245_gb300 as P
 import synthetic as S
 
-ATILE = 32
+WTILE = 32   # side of the K^T work tiles
 ARAYS = 512
 
 
@@ -34,7 +34,7 @@ def _check_worklist(n, det_xy, n_t, r0, dr, quad_m, slots):
     wl = P.pat_adjoint_worklist(n, det_xy, n_t, r0, dr, quad_m, slots)
     rays, items = wl["rays"], wl["items"]
     D, T, M = det_xy.shape[0], n_t, quad_m
-    tiles_x = (n + ATILE - 1) // ATILE
+    tiles_x = (n + WTILE - 1) // WTILE
     tiles = tiles_x * tiles_x
 
     # per tile: segments with increasing prefixes, then a sentinel with the total
@@ -96,7 +96,7 @@ def _check_worklist(n, det_xy, n_t, r0, dr, quad_m, slots):
         for dj in (0, 1):
             ti, tj = i0 + di, j0 + dj
             on = (ti >= 0) & (ti < n) & (tj >= 0) & (tj < n)
-            tile = (tj[on] // ATILE) * tiles_x + ti[on] // ATILE
+            tile = (tj[on] // WTILE) * tiles_x + ti[on] // WTILE
             d_, k_, m_ = dd[on], kk[on], mm[on]
             ok = (k0[tile, d_, m_] <= k_) & (k_ < k1[tile, d_, m_])
             missing += int(np.count_nonzero(~ok))
@@ -138,7 +138,7 @@ def test_worklist_pieces_fill_two_waves():
         it = wl["items"]
         sizes = it[:, 4] - it[:, 3]
         assert it.shape[0] == 2 * slots
-        assert sizes.max() <= 1.1 * wl["candidates"] / (2 * slots)
+        assert sizes.max() <= 1.15 * wl["candidates"] / (2 * slots)
         assert sizes.sum() == wl["candidates"]
 
 
