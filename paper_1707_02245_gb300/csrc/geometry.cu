@@ -382,10 +382,10 @@ static int adjoint_worklist(const pat_geometry_desc& d, const PointTables& pt, d
         long long total = 0;
         for (int t = 0; t < tiles; ++t) total += tile_total[t];
         w.candidates = total;
-        // pieces per tile: two waves of resident CTAs (at least 1024 candidates a piece),
+        // pieces per tile: ADJ_WAVES waves of resident CTAs (at least 1024 candidates a piece),
         // each piece going to the tile whose pieces are largest at that point, which
         // minimises the largest piece
-        const long long Q = std::max(1LL, std::min((long long)(2.0 * slots), total / 1024));
+        const long long Q = std::max(1LL, std::min((long long)(ADJ_WAVES * slots), total / 1024));
         std::vector<long long> n_piece(tiles, 0);
         {
             std::priority_queue<std::pair<double, int>> heap;   // (piece size, tile)

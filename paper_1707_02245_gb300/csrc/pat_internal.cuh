@@ -67,6 +67,10 @@ constexpr int ATILE = 32;      // side of the pixel tiles that share one K^T fix
 constexpr int WTILE = 32;      // side of the pixel tiles one K^T work item accumulates
 static_assert(ATILE % WTILE == 0, "work tiles nest in scale tiles");
 constexpr int ARAYS = 512;     // most ray segments one K^T work item holds
+#ifndef PAT_ADJ_WAVES
+#define PAT_ADJ_WAVES 1
+#endif
+constexpr int ADJ_WAVES = PAT_ADJ_WAVES;   // waves of resident CTAs the K^T work items fill
 
 // One K^T work item: candidates [c0, c1) of work tile `tile`'s concatenated ray segments,
 // which lie on the nray segments rays[ray0 .. ray0 + nray); rays[ray0 + nray] is the next

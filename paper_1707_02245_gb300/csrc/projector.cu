@@ -256,7 +256,10 @@ __global__ void __launch_bounds__(ROW_THREADS) k_forward_gap_b(const FwdGapArgs*
 // entries of K^T that belong to its pixels.  Items of one tile share its scale, so their
 // fixed-point tiles add exactly (in any order) into one image with integer atomics.
 // ---------------------------------------------------------------------------------
-constexpr int ATHREADS = 256;
+#ifndef PAT_ADJ_THREADS
+#define PAT_ADJ_THREADS 256
+#endif
+constexpr int ATHREADS = PAT_ADJ_THREADS;   // threads of a K^T CTA
 #ifndef PAT_ADJ_MIN_BLOCKS
 #define PAT_ADJ_MIN_BLOCKS 5
 #endif

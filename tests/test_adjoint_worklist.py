@@ -129,16 +129,16 @@ def test_worklist_detectors_inside_the_image():
     _check_worklist(40, det, 80, r0, dr, 96, slots=64)
 
 
-def test_worklist_pieces_fill_two_waves():
-    # at the benchmark's geometry the items are exactly two waves of resident CTAs, of
+def test_worklist_pieces_fill_one_wave():
+    # at the benchmark's geometry the items are exactly one wave of resident CTAs, of
     # nearly equal size (no partial wave)
     w = S.workload("tgv256")
     for slots in (5 * 152, 6 * 152):
         wl = P.pat_adjoint_worklist(w["n"], w["det_xy"], w["n_t"], w["r0"], w["dr"], w["quad_m"], slots)
         it = wl["items"]
         sizes = it[:, 4] - it[:, 3]
-        assert it.shape[0] == 2 * slots
-        assert sizes.max() <= 1.15 * wl["candidates"] / (2 * slots)
+        assert it.shape[0] == slots
+        assert sizes.max() <= 1.15 * wl["candidates"] / slots
         assert sizes.sum() == wl["candidates"]
 
 
