@@ -66,7 +66,7 @@ constexpr int MAX_QUAD_M = 8192;
 constexpr int ATILE = 32;      // side of the pixel tiles that share one K^T fixed-point scale
 constexpr int WTILE = 32;      // side of the pixel tiles one K^T work item accumulates
 static_assert(ATILE % WTILE == 0, "work tiles nest in scale tiles");
-constexpr int ARAYS = 512;     // most ray segments one K^T work item holds
+constexpr int ARAYS = 1024;    // most ray segments one K^T work item holds
 #ifndef PAT_ADJ_WAVES
 #define PAT_ADJ_WAVES 1
 #endif

@@ -16,7 +16,7 @@ import paper_1707_02245_gb300 as P
 import synthetic as S
 
 WTILE = 32   # side of the K^T work tiles
-ARAYS = 512
+ARAYS = 1024
 
 
 def _tables(n, det_xy, n_t, r0, dr, quad_m, extent=(-1.0, 1.0, -1.0, 1.0)):
