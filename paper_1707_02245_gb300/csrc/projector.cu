@@ -1,11 +1,12 @@
 // Matrix-free circular-mean projector K and its exact transpose K^T (Sec. 3.3.1,
 // Sec. 4.2 eq. (K_def)), plus the fused data-row kernels of the PDHG iteration.
 //
-// Thread mapping: one thread per data row (d, k); a warp holds 32 consecutive radii of
-// one detector and walks the group's angular window m = m_first .. m_first+count-1 in
-// lockstep, so the (cos, sin) pair is a broadcast and the 32 points of one step lie on
-// one ray from the detector (radii dr apart): neighbouring lanes touch neighbouring
-// pixels.  Each point is interpolated bilinearly between pixel centres.
+// Thread mapping of K: four lanes per data row (d, k), one per angular phase; a warp
+// holds 8 consecutive radii of one detector and walks the group's angular window in
+// lockstep, so at every step its 32 points form a 4-angle x 8-radius patch of the polar
+// grid (neighbouring lanes touch neighbouring pixels).  A block holds adjacent detectors
+// at the same radii, whose arcs cross the same pixels, so its warps share L1 lines.  Each
+// point is interpolated bilinearly between pixel centres.
 //
 // The hot path reads a zero-bordered copy of the image ((N+2)^2 floats, pixel (i, j) at
 // (j+1)(N+2) + i+1) so a point with taps i0, j0 in [-1, N-1] needs no per-tap test.
@@ -238,23 +239,22 @@ __global__ void __launch_bounds__(ROW_THREADS) k_forward_gap_b(const FwdGapArgs*
 // ---------------------------------------------------------------------------------
 // K^T by pixel tiles with exact fixed-point accumulation.
 //
-// A CTA owns an ATILE x ATILE block of pixels and one group of detectors.  Its shared
+// A CTA owns a share of one WTILE x WTILE pixel tile's candidate points.  Its shared
 // accumulator (with a one-pixel ring, so every point whose taps touch the tile can add
 // all four weights) holds int32 fixed-point values: every pixel satisfies
 //   |(K^T y)(p)| <= max|y| * (K^T 1)(p)        (all entries of K are >= 0),
-// so with the scale S = 2^30 / (max|y| * max over the tile of K^T 1) no partial sum of a
-// tile pixel exceeds 2^30 and integer addition (native shared atomics, associative, hence
-// deterministic) replaces floating-point atomics.  The resolution 2^-30 of that bound is
-// finer than FP32 accumulation of the same terms.  Ring cells may wrap; they are dropped.
+// so with the scale S = 2^30 / (max|y| * max over the ATILE tile of K^T 1) no partial sum
+// of a tile pixel exceeds 2^30 and integer addition (native shared atomics, associative,
+// hence deterministic) replaces floating-point atomics.  The resolution 2^-30 of that
+// bound is finer than FP32 accumulation of the same terms.  Ring cells are dropped.
 //
-// Work: each CTA takes one work item (a tile and a list of units; a unit is up to 32 rays
-// of one detector's (k, m) box for the tile), precomputed and cost-balanced at geometry
-// creation.  A warp per unit cuts every ray down to its segment inside the tile's tap
-// region and splits the concatenated segments into 32 equal contiguous runs, one per
-// lane, so lanes that add at the same time sit on different rays.  Every candidate uses
-// the forward projector's FP32 position and tap arithmetic, so the CTA adds exactly the
-// entries of K^T that belong to its pixels.  Items of one tile share its scale, so their
-// fixed-point tiles add exactly (in any order) into one image with integer atomics.
+// Work: geometry creation cuts every ray (detector, angle) of a tile's polar box to the
+// segment of radii whose points can have taps in the tile, concatenates the segments
+// into the tile's candidate list, and cuts the lists into equal work items that fill one
+// wave of resident CTAs (see the work-item function below).  Every candidate uses the
+// forward projector's FP32 position and tap arithmetic, so the CTA adds exactly the
+// entries of K^T that belong to its pixels.  Items of one scale tile share its scale, so
+// their fixed-point tiles add exactly (in any order) into one image with integer atomics.
 // ---------------------------------------------------------------------------------
 #ifndef PAT_ADJ_THREADS
 #define PAT_ADJ_THREADS 256
