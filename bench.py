@@ -38,6 +38,10 @@ WORKLOAD_DESC = ("tgv256: TGV^2 PDHG, 256x256 vessel phantom with exp(-3 depth) 
                  "full circle r=1.2, 512 time samples, M=256, 5% noise, alpha 0.02, beta 0.04, 1000 iterations, "
                  "diagonal preconditioning, FP64 gap every 10 iterations")
 FLOPS_PER_POINT = 22          # FP32 ops of one quadrature point: position 4, coordinates 4, floor/fraction 4, lerps 9, add 1
+# DRAM bytes (read + write) per launch of the projector kernels at the tgv256 workload, from
+# one ncu capture of the current kernels (profiles/projector_kernels_tgv256.md; cold-cache
+# replay, the working set otherwise lives in L2)
+DRAM_BYTES_TGV256 = {"adjoint": 4509952, "forward_prox": 2789632}
 SMS, FP32_LANES = 152, 128    # GB300: SMs x FP32 lanes per SM
 
 
@@ -401,8 +405,11 @@ def run_gb300(args) -> int:
         v["share"] = v["avg_us"] * v["launches"] / tot if tot else None
     dom_name = max(phases, key=lambda k: phases[k]["share"] if k in ("forward_prox", "adjoint", "update") else -1)
     dom = phases[dom_name]
+    traffic = DRAM_BYTES_TGV256.get(dom_name) if args.workload == "tgv256" else None
     roofline = {"kernel": dom_name, "bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
-                "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
+                "unit": dom["unit"], "frac": dom["frac"], "traffic": traffic,
+                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold-cache replay "
+                                  "(profiles/projector_kernels_tgv256.md)" if traffic else None,
                 "measured": "CUDA events around every launch in a profiled replay of the timed steps",
                 "peak_source": "FP32 152 SMs x 128 lanes x 2 x 2070 MHz" if dom["bound"] == "alu"
                 else peaks["source"]}
