@@ -387,11 +387,12 @@ __device__ __forceinline__ void gap_pixels_block(const GapArgs& a, const int lb)
     const size_t NN = (size_t)N * N;
     const float gam = (float)a.gamma;
     const float alpha = a.alpha, ab = a.ab;
-    // per-thread terms in FP32 (each thread covers few pixels), block sums in FP64: GB300's
-    // FP64 pipe runs at 1/64 of FP32, so FP64 is kept to one conversion per thread and term
+    // per-thread terms in FP32 (each thread covers few pixels); warp sums as FP32 pairs and
+    // block sums in FP64: GB300's FP64 pipe runs at 1/64 of FP32, so FP64 is kept to one
+    // warp per block
     // + the dual residual of the regulariser duals (distance of their argument from the
     // normal cone of the ball at r and s), for the adaptive balance
-    float acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    float acc[GAP_PIX_TERMS] = {0, 0, 0, 0, 0, 0, 0};
     const int nthreads = a.nblocks * blockDim.x;
     auto X = [&](int c, int x, int y) -> float { return __ldg(a.x + c * NN + (size_t)y * N + x); };
     auto Yf = [&](int c, int x, int y) -> float { return __ldg(a.y + c * NN + (size_t)y * N + x); };
@@ -459,8 +460,7 @@ __device__ __forceinline__ void gap_pixels_block(const GapArgs& a, const int lb)
         }
     }
     double dacc[GAP_PIX_TERMS];
-    for (int c = 0; c < GAP_PIX_TERMS; ++c) dacc[c] = (double)acc[c];
-    block_sum<GAP_PIX_TERMS>(dacc);
+    block_sum_pair<GAP_PIX_TERMS>(acc, dacc);
     if (threadIdx.x == 0)
         for (int c = 0; c < GAP_PIX_TERMS; ++c) a.partials[GAP_PIX_TERMS * lb + c] = dacc[c];
 }
@@ -475,6 +475,7 @@ __global__ void __launch_bounds__(256) k_gap_pixels_b(const GapArgs* __restrict_
 }
 
 constexpr int GAP_FINAL_BLOCKS = 32;
+constexpr int GAP_FINAL_THREADS = 32;   // one warp: the final sums are FP64, kept to few lanes
 
 struct InfoDev {
     double primal, dual, gap, rel_gap, residual;
@@ -581,7 +582,7 @@ __device__ __forceinline__ void gap_final_block(const FinalArgs& a, const int lb
     }
 }
 
-__global__ void __launch_bounds__(256) k_gap_final_b(const FinalArgs* __restrict__ args, const int2* __restrict__ map) {
+__global__ void __launch_bounds__(GAP_FINAL_THREADS) k_gap_final_b(const FinalArgs* __restrict__ args, const int2* __restrict__ map) {
     const int2 pm = map[blockIdx.x];
     __shared__ FinalArgs sa;
     const FinalArgs& a = stage_args(args, pm.x, sa);
@@ -1008,7 +1009,7 @@ static int launch_gap_phase(const FwdGapArgs* fa, const GapArgs* ga, const Final
             k_gap_pixels_b<PAT_DTV><<<gp.n_pix[r], 256, 0, st>>>(ga, map);
         PAT_LAUNCH_CHECK("k_gap_pixels_b");
     }
-    k_gap_final_b<<<gp.n_fin, 256, 0, st>>>(fi, (const int2*)(base + gp.map_fin));
+    k_gap_final_b<<<gp.n_fin, GAP_FINAL_THREADS, 0, st>>>(fi, (const int2*)(base + gp.map_fin));
     PAT_LAUNCH_CHECK("k_gap_final_b");
     prof_mark(PAT_PHASE_GAP, st, false);
     return PAT_OK;
@@ -1465,7 +1466,7 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
             WavGapArgs wg{N, GAP_PIX_TERMS, wu, pa.kt, wtr, u, u_old, ppart, &in->stop};
             if (!e) e = launch_wav_gap_pixels(wg, n_pix, s);
             if (!e) {
-                k_gap_final_b<<<GAP_FINAL_BLOCKS, 256, 0, s>>>((const FinalArgs*)(base + fi_off),
+                k_gap_final_b<<<GAP_FINAL_BLOCKS, GAP_FINAL_THREADS, 0, s>>>((const FinalArgs*)(base + fi_off),
                                                               (const int2*)(base + finmap_off));
                 count_launch();
                 if (cudaGetLastError() != cudaSuccess) e = fail(PAT_ERR_CUDA, "k_gap_final_b");

@@ -204,7 +204,8 @@ __device__ __forceinline__ void forward_gap_rows(const FwdGapArgs& a, int kb, in
     const RowLane rl = row_lane(g, kb, d);
     const float* img = QUAD ? reinterpret_cast<const float*>(a.u_quad) : a.u;
     const float s = phase_sum(circle_partial<QUAD>(g, img, rl));
-    // per-row terms in FP32, block sums in FP64 (GB300's FP64 pipe is 1/64 of FP32)
+    // per-row terms in FP32; warp sums as FP32 pairs, block sums in FP64 (GB300's FP64 pipe
+    // is 1/64 of FP32)
     float t[GAP_DATA_TERMS] = {0.f, 0.f, 0.f, 0.f};
     if (rl.valid && rl.ph == 0) {
         const float ku = s * __ldg(&g.wk[rl.k]);
@@ -217,8 +218,7 @@ __device__ __forceinline__ void forward_gap_rows(const FwdGapArgs& a, int kb, in
         t[3] = fabsf(qi - res);   // dual residual of the data term: q - dF1(Ku)
     }
     double sum[GAP_DATA_TERMS];
-    for (int c = 0; c < GAP_DATA_TERMS; ++c) sum[c] = (double)t[c];
-    block_sum<GAP_DATA_TERMS>(sum);
+    block_sum_pair<GAP_DATA_TERMS>(t, sum);
     if (threadIdx.x == 0)
         for (int c = 0; c < GAP_DATA_TERMS; ++c) a.partials[GAP_DATA_TERMS * lb + c] = sum[c];
 }
