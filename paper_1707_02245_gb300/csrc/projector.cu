@@ -65,6 +65,15 @@ constexpr int FWD_KW = ROW_WARPS / FWD_DW;
 static_assert(FWD_DW * FWD_KW == ROW_WARPS, "FWD_DW must divide ROW_WARPS");
 constexpr int ROWS_PER_BLOCK = ROW_WARPS * KGRP;
 constexpr int ROW_THREADS = ROWS_PER_BLOCK * NPH;
+// resident row blocks per SM that the register budget must allow (0: the compiler's choice)
+#ifndef PAT_FWD_MIN_BLOCKS
+#define PAT_FWD_MIN_BLOCKS 0
+#endif
+#if PAT_FWD_MIN_BLOCKS > 0
+#define PAT_ROW_BOUNDS __launch_bounds__(ROW_THREADS, PAT_FWD_MIN_BLOCKS)
+#else
+#define PAT_ROW_BOUNDS __launch_bounds__(ROW_THREADS)
+#endif
 
 struct RowLane {
     int d, k, ph;
@@ -136,7 +145,7 @@ __device__ __forceinline__ float phase_sum(float v) {
 }
 
 // y = K u
-__global__ void __launch_bounds__(ROW_THREADS) k_forward(GeomView g, const float* __restrict__ u, float* __restrict__ y) {
+__global__ void PAT_ROW_BOUNDS k_forward(GeomView g, const float* __restrict__ u, float* __restrict__ y) {
     const RowLane rl = row_lane(g, blockIdx.x, blockIdx.y);
     const float s = phase_sum(circle_partial<false>(g, u, rl));
     if (rl.valid && rl.ph == 0) y[(size_t)rl.d * g.n_t + rl.k] = s * __ldg(&g.wk[rl.k]);
@@ -176,7 +185,7 @@ __device__ __forceinline__ void forward_prox_rows(const FwdProxArgs& a, int kb, 
     }
 }
 
-__global__ void __launch_bounds__(ROW_THREADS) k_forward_prox_b(const FwdProxArgs* __restrict__ args,
+__global__ void PAT_ROW_BOUNDS k_forward_prox_b(const FwdProxArgs* __restrict__ args,
                                                                const int2* __restrict__ map) {
     const int2 pm = map[blockIdx.x];
     __shared__ FwdProxArgs sa;
@@ -223,7 +232,7 @@ __device__ __forceinline__ void forward_gap_rows(const FwdGapArgs& a, int kb, in
         for (int c = 0; c < GAP_DATA_TERMS; ++c) a.partials[GAP_DATA_TERMS * lb + c] = sum[c];
 }
 
-__global__ void __launch_bounds__(ROW_THREADS) k_forward_gap_b(const FwdGapArgs* __restrict__ args,
+__global__ void PAT_ROW_BOUNDS k_forward_gap_b(const FwdGapArgs* __restrict__ args,
                                                               const int2* __restrict__ map) {
     const int2 pm = map[blockIdx.x];
     __shared__ FwdGapArgs sa;
