@@ -117,6 +117,27 @@ namespace pat {
 // ---------------------------------------------------------------------------------
 // shared device helpers
 // ---------------------------------------------------------------------------------
+// K reads the image as quads: quad (x, y), x, y in [0, N], holds the pixels (x-1, y-1),
+// (x, y-1), (x-1, y), (x, y) (zero off the grid), so a point with upper-left tap (i0, j0)
+// reads quad (i0 + 1, j0 + 1) in one 16-byte load.  The quads are stored row by row;
+// PAT_QUAD_BLOCKED 1 stores them in blocks of 4 (x) by 2 (y), one 128-byte line each,
+// which measured slower for K (38.9 us against 31.6 us at 256^2).
+#ifndef PAT_QUAD_BLOCKED
+#define PAT_QUAD_BLOCKED 0
+#endif
+__host__ __device__ __forceinline__ size_t quad_index(int x, int y, int N) {
+#if PAT_QUAD_BLOCKED
+    const int nbx = (N + 4) >> 2;  // blocks per row of quads: ceil((N + 1) / 4)
+    return ((size_t)(y >> 1) * nbx + (x >> 2)) * 8 + ((y & 1) << 2) + (x & 3);
+#else
+    return (size_t)y * (N + 1) + x;
+#endif
+}
+// quads to allocate (the blocked layout pads the grid of quads to whole blocks)
+__host__ __device__ __forceinline__ size_t quad_count(int N) {
+    return (size_t)((N + 4) >> 2) * 8 * (size_t)((N + 2) >> 1);
+}
+
 struct Taps {
     int i0, j0;
     float ax, ay;

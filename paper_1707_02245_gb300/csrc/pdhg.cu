@@ -229,17 +229,16 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
         // quads are the only copy of ubar; the bordered image is filled at the start only)
         {
             const float bx = s_ub[ly][lx + 1], by_ = s_ub[ly + 1][lx], bxy = s_ub[ly + 1][lx + 1];
-            const int Q = N + 1;
-            a.ubar_quad[(size_t)(gy + 1) * Q + gx + 1] = make_float4(ub, bx, by_, bxy);
-            if (gx == 0) a.ubar_quad[(size_t)(gy + 1) * Q] = make_float4(0.f, ub, 0.f, by_);
-            if (gy == 0) a.ubar_quad[gx + 1] = make_float4(0.f, 0.f, ub, bx);
-            if (gx == 0 && gy == 0) a.ubar_quad[0] = make_float4(0.f, 0.f, 0.f, ub);
+            a.ubar_quad[quad_index(gx + 1, gy + 1, N)] = make_float4(ub, bx, by_, bxy);
+            if (gx == 0) a.ubar_quad[quad_index(0, gy + 1, N)] = make_float4(0.f, ub, 0.f, by_);
+            if (gy == 0) a.ubar_quad[quad_index(gx + 1, 0, N)] = make_float4(0.f, 0.f, ub, bx);
+            if (gx == 0 && gy == 0) a.ubar_quad[quad_index(0, 0, N)] = make_float4(0.f, 0.f, 0.f, ub);
             if (a.u_quad) {
                 const float uu = s_uU[ly][lx], ux = s_uU[ly][lx + 1], uy = s_uU[ly + 1][lx], uxy = s_uU[ly + 1][lx + 1];
-                a.u_quad[(size_t)(gy + 1) * Q + gx + 1] = make_float4(uu, ux, uy, uxy);
-                if (gx == 0) a.u_quad[(size_t)(gy + 1) * Q] = make_float4(0.f, uu, 0.f, uy);
-                if (gy == 0) a.u_quad[gx + 1] = make_float4(0.f, 0.f, uu, ux);
-                if (gx == 0 && gy == 0) a.u_quad[0] = make_float4(0.f, 0.f, 0.f, uu);
+                a.u_quad[quad_index(gx + 1, gy + 1, N)] = make_float4(uu, ux, uy, uxy);
+                if (gx == 0) a.u_quad[quad_index(0, gy + 1, N)] = make_float4(0.f, uu, 0.f, uy);
+                if (gy == 0) a.u_quad[quad_index(gx + 1, 0, N)] = make_float4(0.f, 0.f, uu, ux);
+                if (gx == 0 && gy == 0) a.u_quad[quad_index(0, 0, N)] = make_float4(0.f, 0.f, 0.f, uu);
             }
         }
         if (REG == PAT_TGV) {
@@ -680,12 +679,12 @@ __global__ void k_pad(const float* __restrict__ u, float* __restrict__ pad, int 
     pad[gy * P + gx] = (x >= 0 && x < N && y >= 0 && y < N && u) ? u[y * N + x] : 0.f;
 }
 
-// quads of a zero-bordered image: Q[(j+1)(N+1) + i+1] = taps (i..i+1, j..j+1), i, j >= -1
+// quads of a zero-bordered image: quad (i+1, j+1) = taps (i..i+1, j..j+1), i, j >= -1
 __global__ void k_quads_from_pad(const float* __restrict__ pad, float4* __restrict__ quad, int N) {
     const int qx = blockIdx.x * blockDim.x + threadIdx.x, qy = blockIdx.y * blockDim.y + threadIdx.y;
     if (qx > N || qy > N) return;
     const int P = N + 2;  // pad index of pixel (i, j) is (j+1) P + i+1; quad (qx, qy) has i0 = qx-1
-    quad[(size_t)qy * (N + 1) + qx] = make_float4(pad[qy * P + qx], pad[qy * P + qx + 1], pad[(qy + 1) * P + qx],
+    quad[quad_index(qx, qy, N)] = make_float4(pad[qy * P + qx], pad[qy * P + qx + 1], pad[(qy + 1) * P + qx],
                                                   pad[(qy + 1) * P + qx + 1]);
 }
 
@@ -728,7 +727,7 @@ __global__ void k_output(OutArgs a) {
             if (a.xbar_out) {
                 if (i < NN) {
                     const int gx = (int)(i % N), gy = (int)(i / N);
-                    a.xbar_out[i] = a.ubar_quad[(long long)(gy + 1) * (N + 1) + gx + 1].x;
+                    a.xbar_out[i] = a.ubar_quad[quad_index(gx + 1, gy + 1, N)].x;
                 } else {
                     // vbar^I = v^I + theta (v^I - v^{I-1}); with I = 0 the warm-start vbar is
                     // not recoverable here and v^0 is returned
@@ -778,7 +777,7 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     size_t sz[19] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, NN * 4 * 2,
                      (reg == PAT_TGV ? 2 * NN : 1) * 4,
                      NN * 4, S * 4, NN * 4, (size_t)ws.n_data * GAP_DATA_TERMS * 8, (size_t)ws.n_pix * GAP_PIX_TERMS * 8, sizeof(InfoDev),
-                     S * 4, nx * 4, nx * 4, (N + 1) * (N + 1) * 16, (N + 1) * (N + 1) * 16};
+                     S * 4, nx * 4, nx * 4, quad_count((int)N) * 16, quad_count((int)N) * 16};
     size_t total = 0;
     for (int i = 0; i < 19; ++i) {
         off[i] = total;
@@ -1341,7 +1340,7 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
     const int n_pix = pix_blocks(N);
     // workspace
     enum { U, UOLD, UBAR, UPAD, UQUAD, Q, QW, KT, R, WB, WTR, SCR, SCR2, WU, TAU, SIGR, SIGQ, DPART, PPART, INFO, NBUF };
-    size_t sz[NBUF] = {NN * 4, NN * 4, NN * 4, (size_t)(N + 2) * (N + 2) * 4, (size_t)(N + 1) * (N + 1) * 16,
+    size_t sz[NBUF] = {NN * 4, NN * 4, NN * 4, (size_t)(N + 2) * (N + 2) * 4, quad_count(N) * 16,
                        (size_t)S * 4, (size_t)S * 4, (size_t)NN * 8, NN * 4, NN * 4, NN * 4, NN * 4, NN * 4, NN * 4,
                        NN * 4, NN * 4, (size_t)S * 4, (size_t)n_data * GAP_DATA_TERMS * 8,
                        (size_t)n_pix * GAP_PIX_TERMS * 8, sizeof(InfoDev)};

@@ -100,7 +100,7 @@ __device__ __forceinline__ int row_blocks(const GeomView& g) {
 }
 
 // Partial integral of the bilinear image over circle (d, k) for one angular phase.
-// QUAD: u points at (N+1)^2 float4 quads (one load per point); otherwise u is the plain
+// QUAD: u points at the float4 quads (one load per point; layout quad_index); otherwise u is the plain
 // N*N image read with per-tap bounds tests.
 template <bool QUAD>
 __device__ __forceinline__ float circle_partial(const GeomView& g, const float* __restrict__ u, const RowLane& rl) {
@@ -121,7 +121,7 @@ __device__ __forceinline__ float circle_partial(const GeomView& g, const float* 
         if (point_taps(g, det, r, cs, t) && rl.valid) {
             float v00, v10, v01, v11;
             if (QUAD) {
-                const float4 v = __ldg(reinterpret_cast<const float4*>(u) + (t.j0 + 1) * (g.n + 1) + (t.i0 + 1));
+                const float4 v = __ldg(reinterpret_cast<const float4*>(u) + quad_index(t.i0 + 1, t.j0 + 1, g.n));
                 v00 = v.x;
                 v10 = v.y;
                 v01 = v.z;
