@@ -125,12 +125,14 @@ namespace pat {
 #ifndef PAT_QUAD_BLOCKED
 #define PAT_QUAD_BLOCKED 0
 #endif
-__host__ __device__ __forceinline__ size_t quad_index(int x, int y, int N) {
+// 32-bit arithmetic: geometry creation bounds N by 16384, so every index is below 2^31
+// (64-bit index math cost K's gap kernel two registers and a third of its occupancy)
+__host__ __device__ __forceinline__ int quad_index(int x, int y, int N) {
 #if PAT_QUAD_BLOCKED
     const int nbx = (N + 4) >> 2;  // blocks per row of quads: ceil((N + 1) / 4)
-    return ((size_t)(y >> 1) * nbx + (x >> 2)) * 8 + ((y & 1) << 2) + (x & 3);
+    return ((y >> 1) * nbx + (x >> 2)) * 8 + ((y & 1) << 2) + (x & 3);
 #else
-    return (size_t)y * (N + 1) + x;
+    return y * (N + 1) + x;
 #endif
 }
 // quads to allocate (the blocked layout pads the grid of quads to whole blocks)

@@ -26,7 +26,13 @@
 
 namespace pat {
 
-constexpr int TX = 32, TY = 4;            // update tile
+#ifndef PAT_UPD_TX
+#define PAT_UPD_TX 32
+#endif
+#ifndef PAT_UPD_TY
+#define PAT_UPD_TY 4
+#endif
+constexpr int TX = PAT_UPD_TX, TY = PAT_UPD_TY;   // update tile
 constexpr int LX = TX + 2, LY = TY + 2;   // tile plus one-pixel halo on each side
 
 struct UpdateArgs {
