@@ -41,7 +41,7 @@ FLOPS_PER_POINT = 22          # FP32 ops of one quadrature point: position 4, co
 # DRAM bytes (read + write) per launch of the projector kernels at the tgv256 workload, from
 # one ncu capture of the current kernels (profiles/projector_kernels_tgv256.md; cold-cache
 # replay, the working set otherwise lives in L2)
-DRAM_BYTES_TGV256 = {"adjoint": 4509952, "forward_prox": 2789632}
+DRAM_BYTES_TGV256 = {"forward_prox": 2789632}
 SMS, FP32_LANES = 152, 128    # GB300: SMs x FP32 lanes per SM
 
 

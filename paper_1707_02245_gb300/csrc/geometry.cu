@@ -248,7 +248,7 @@ static PointTables point_tables(const pat_geometry_desc& d) {
     }
     for (int k = 0; k < T; ++k) {
         pt.rd[k] = d.r0 + (k + 0.5) * d.dr;
-        pt.rk[k] = (float)pt.rd[k];
+        pt.rk[k] = radius(k, (float)d.dr, (float)(d.r0 + 0.5 * d.dr));
         pt.wk[k] = (float)(2.0 * M_PI * pt.rd[k] / M);
     }
     return pt;
@@ -565,6 +565,8 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     v.cs = g->cs;
     v.rk = g->rk;
     v.wk = g->wk;
+    v.dr_f = (float)d.dr;
+    v.rh_f = (float)(d.r0 + 0.5 * d.dr);
     v.win = g->win;
     *out = g;
     return PAT_OK;

@@ -56,10 +56,18 @@ struct GeomView {
     int n_kgrp;          // k groups of KGRP consecutive radii per detector
     const float2* det;   // D detector positions in continuous pixel coordinates
     const float2* cs;    // M (cos phi_m / hx, sin phi_m / hy)
-    const float* rk;     // T radii
+    const float* rk;     // T radii, rk[k] = fmaf(k, dr_f, rh_f) (see radius())
     const float* wk;     // T arc weights 2 pi r_k / M
     const int2* win;     // D * n_kgrp angular windows {m_first, m_count} (circular)
+    float dr_f, rh_f;    // FP32 radius step dr and first radius r0 + dr/2
 };
+
+// Radius r_k = r0 + (k + 1/2) dr in FP32, as one correctly rounded fused multiply-add of
+// FP32 constants; the host builds the radius table with the same expression (std::fmaf is
+// correctly rounded too), so a kernel may evaluate it instead of loading rk[k].
+__host__ __device__ __forceinline__ float radius(int k, float dr_f, float rh_f) {
+    return fmaf((float)k, dr_f, rh_f);
+}
 
 constexpr int KGRP = 8;        // radii per angular-window group
 constexpr int MAX_QUAD_M = 8192;

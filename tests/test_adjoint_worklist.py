@@ -26,7 +26,9 @@ def _tables(n, det_xy, n_t, r0, dr, quad_m, extent=(-1.0, 1.0, -1.0, 1.0)):
     det = np.stack([(det_xy[:, 0] - xmin) / hx - 0.5, (det_xy[:, 1] - ymin) / hy - 0.5], 1).astype(np.float32)
     phi = 2 * math.pi * (np.arange(quad_m) + 0.5) / quad_m
     cs = np.stack([np.cos(phi) / hx, np.sin(phi) / hy], 1).astype(np.float32)
-    rk = (r0 + (np.arange(n_t) + 0.5) * dr).astype(np.float32)
+    # r_k = fmaf(k, dr, r0 + dr/2) in FP32: the exact product plus the constant, rounded once
+    k = np.arange(n_t, dtype=np.float64)
+    rk = (k * np.float64(np.float32(dr)) + np.float64(np.float32(r0 + 0.5 * dr))).astype(np.float32)
     return det, cs, rk
 
 
