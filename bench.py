@@ -39,9 +39,9 @@ WORKLOAD_DESC = ("tgv256: TGV^2 PDHG, 256x256 vessel phantom with exp(-3 depth) 
                  "diagonal preconditioning, FP64 gap every 10 iterations")
 FLOPS_PER_POINT = 22          # FP32 ops of one quadrature point: position 4, coordinates 4, floor/fraction 4, lerps 9, add 1
 # DRAM bytes (read + write) per launch of the projector kernels at the tgv256 workload, from
-# one ncu capture of the current kernels (profiles/projector_kernels_tgv256.md; cold-cache
+# ncu captures of the current kernels (profiles/projector_kernels_tgv256.md; cold-cache
 # replay, the working set otherwise lives in L2)
-DRAM_BYTES_TGV256 = {"forward_prox": 2789632}
+DRAM_BYTES_TGV256 = {"forward_prox": 2789632, "adjoint": 4508416}
 SMS, FP32_LANES = 152, 128    # GB300: SMs x FP32 lanes per SM
 
 
