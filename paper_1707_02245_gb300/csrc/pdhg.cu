@@ -1346,9 +1346,10 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
     const int n_pix = pix_blocks(N);
     // workspace
     enum { U, UOLD, UBAR, UPAD, UQUAD, Q, QW, KT, R, WB, WTR, SCR, SCR2, WU, TAU, SIGR, SIGQ, DPART, PPART, INFO, NBUF };
-    size_t sz[NBUF] = {NN * 4, NN * 4, NN * 4, (size_t)(N + 2) * (N + 2) * 4, quad_count(N) * 16,
-                       (size_t)S * 4, (size_t)S * 4, (size_t)NN * 8, NN * 4, NN * 4, NN * 4, NN * 4, NN * 4, NN * 4,
-                       NN * 4, NN * 4, (size_t)S * 4, (size_t)n_data * GAP_DATA_TERMS * 8,
+    const size_t nn4 = (size_t)NN * 4;
+    size_t sz[NBUF] = {nn4, nn4, nn4, (size_t)(N + 2) * (N + 2) * 4, quad_count(N) * 16,
+                       (size_t)S * 4, (size_t)S * 4, (size_t)NN * 8, nn4, nn4, nn4, nn4, nn4, nn4,
+                       nn4, nn4, (size_t)S * 4, (size_t)n_data * GAP_DATA_TERMS * 8,
                        (size_t)n_pix * GAP_PIX_TERMS * 8, sizeof(InfoDev)};
     size_t off[NBUF], total = 0;
     for (int i = 0; i < NBUF; ++i) {
