@@ -512,6 +512,7 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     }
     g->points_per_apply = pts;
     g->points_on_grid = on_grid;
+    g->fwd_block_cost = forward_block_costs(d, win);
 
     AdjWork aw;
     {

@@ -113,6 +113,7 @@ struct pat_geometry {
     int adj_wtiles_x = 0;              // work tiles (WTILE) per row
     long long adj_candidates = 0;     // candidate points of one K^T application
     std::vector<float> adj_item_cost;  // estimated cost per work item (host)
+    std::vector<float> fwd_block_cost; // angular steps of each row block of K (host)
     std::vector<double> det_xy;        // detector positions (host copy, 2 per detector)
     pat::GeomView view;
     // lazily computed preconditioner sums
@@ -272,6 +273,9 @@ int launch_adjoint_b(const AdjArgs* args, const int2* map, int nblocks, bool pre
 // CTAs of the K^T kernel that one SM holds at once (sizes the work items)
 int adjoint_blocks_per_sm();
 int forward_row_blocks(const pat_geometry* g);    // blocks of one forward launch
+// Work of each row block of K (local block index as the kernels decode it): the angular
+// steps of its warps, from the host copy of the angular windows (D x n_kgrp)
+std::vector<float> forward_block_costs(const pat_geometry_desc& d, const std::vector<int2>& win);
 
 // Host entry points implemented in projector.cu and used by pdhg.cu
 // ---- the wavelet model (wavelet.cu) ----

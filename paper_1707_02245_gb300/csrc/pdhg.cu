@@ -910,11 +910,29 @@ struct GapPlan {
     int n_pix[3] = {0, 0, 0};
 };
 
-static void build_gap_plan(const Prob* pr, int B, Arena& ar, GapPlan& gp) {
-    std::vector<int2> fwd, fin, pix[3];
+// (problem, row block) pairs of a batch's K launch, longest first: the blocks' angular
+// work differs several-fold, and the launch spans a few waves of resident blocks, so the
+// order sets the length of the last wave (each block's rows do not depend on it)
+static std::vector<int2> forward_block_map(const Prob* pr, int B) {
+    std::vector<std::pair<float, int2>> v;
     for (int b = 0; b < B; ++b) {
-        const int nf = forward_row_blocks(pr[b].g);
-        for (int i = 0; i < nf; ++i) fwd.push_back(make_int2(b, i));
+        const pat_geometry* g = pr[b].g;
+        const int nf = forward_row_blocks(g);
+        for (int i = 0; i < nf; ++i)
+            v.push_back({i < (int)g->fwd_block_cost.size() ? g->fwd_block_cost[i] : 0.f, make_int2(b, i)});
+    }
+    std::stable_sort(v.begin(), v.end(), [](const std::pair<float, int2>& x, const std::pair<float, int2>& y) {
+        return x.first > y.first;
+    });
+    std::vector<int2> m;
+    m.reserve(v.size());
+    for (auto& e : v) m.push_back(e.second);
+    return m;
+}
+
+static void build_gap_plan(const Prob* pr, int B, Arena& ar, GapPlan& gp) {
+    std::vector<int2> fwd = forward_block_map(pr, B), fin, pix[3];
+    for (int b = 0; b < B; ++b) {
         for (int i = 0; i < pr[b].ws.n_pix; ++i) pix[pr[b].p.reg].push_back(make_int2(b, i));
         for (int i = 0; i < GAP_FINAL_BLOCKS; ++i) fin.push_back(make_int2(b, i));
     }
@@ -1065,8 +1083,6 @@ static void build_iter_plan(const Prob* pr, int B, Arena& ar, IterPlan& ip, int*
     std::vector<std::pair<float, int2>> adj;
     for (int b = 0; b < B; ++b) {
         const pat_geometry* g = pr[b].g;
-        const int nf = forward_row_blocks(g);
-        for (int i = 0; i < nf; ++i) fwd.push_back(make_int2(b, i));
         for (int i = 0; i < g->adj_items; ++i) adj.push_back({g->adj_item_cost[i], make_int2(b, i)});
         const int N = g->desc.n, nt = ceil_div(N, TX) * ceil_div(N, TY);
         for (int i = 0; i < nt; ++i) upd[pr[b].p.reg].push_back(make_int2(b, i));
@@ -1076,6 +1092,7 @@ static void build_iter_plan(const Prob* pr, int B, Arena& ar, IterPlan& ip, int*
     });
     std::vector<int2> adjm;
     for (auto& e : adj) adjm.push_back(e.second);
+    fwd = forward_block_map(pr, B);
     ip.map_fwd = ar.put(fwd.data(), fwd.size());
     ip.n_fwd = (int)fwd.size();
     ip.map_adj = ar.put(adjm.data(), adjm.size());
@@ -1423,7 +1440,12 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
                      in, stopped};
         fi_off = ar.put(&fi, 1);
         std::vector<int2> fm(nf), am(g->adj_items), fin(GAP_FINAL_BLOCKS);
-        for (int i = 0; i < nf; ++i) fm[i] = make_int2(0, i);
+        {
+            std::vector<std::pair<float, int>> fo;   // row blocks of K, longest first
+            for (int i = 0; i < nf; ++i) fo.push_back({i < (int)g->fwd_block_cost.size() ? g->fwd_block_cost[i] : 0.f, i});
+            std::stable_sort(fo.begin(), fo.end(), [](const auto& a, const auto& c) { return a.first > c.first; });
+            for (int i = 0; i < nf; ++i) fm[i] = make_int2(0, fo[i].second);
+        }
         std::vector<std::pair<float, int>> order;
         for (int i = 0; i < g->adj_items; ++i) order.push_back({g->adj_item_cost[i], i});
         std::stable_sort(order.begin(), order.end(), [](const auto& a, const auto& c) { return a.first > c.first; });

@@ -471,6 +471,22 @@ int forward_row_blocks(const pat_geometry* g) {
     return gr.x * gr.y;
 }
 
+std::vector<float> forward_block_costs(const pat_geometry_desc& d, const std::vector<int2>& win) {
+    const int D = d.n_det, n_kgrp = (d.n_t + KGRP - 1) / KGRP;
+    const int nkb = ceil_div(d.n_t, FWD_KW * KGRP), ndb = ceil_div(D, FWD_DW);
+    std::vector<float> cost((size_t)nkb * ndb, 0.f);
+    for (int db = 0; db < ndb; ++db)
+        for (int kb = 0; kb < nkb; ++kb) {
+            float c = 0.f;
+            for (int w = 0; w < ROW_WARPS; ++w) {   // the warp -> (detector, radii group) map of row_lane
+                const int det = db * FWD_DW + w / FWD_KW, kg = kb * FWD_KW + w % FWD_KW;
+                if (det < D && kg < n_kgrp) c += (float)win[(size_t)det * n_kgrp + kg].y;
+            }
+            cost[(size_t)db * nkb + kb] = c;   // local block index kb + nkb * db
+        }
+    return cost;
+}
+
 
 int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y, cudaStream_t st) {
     (void)padded;
