@@ -6,6 +6,8 @@ point that has a tap in the tile (else a term of K^T y is lost), and the work it
 cut each tile's list into disjoint pieces that cover it (else a term is lost or counted
 twice).  Both are checked here by brute force over every quadrature point
 (d, k, m) of Sec. 4.2's discretisation, with the FP32 point arithmetic of the kernels.
+A mirror of the kernel's traversal (per-thread runs, the binary search for a run's first
+segment, the segment switches) checks that every candidate of an item is visited once.
 """
 import math
 
@@ -147,3 +149,84 @@ def test_worklist_pieces_fill_one_wave():
 def test_worklist_rejects_bad_input():
     with pytest.raises(P.PatError):
         P.pat_adjoint_worklist(1, np.zeros((1, 2)), 10, 0.0, 0.1, 16, slots=8)
+
+
+ATHREADS = 256   # threads of a K^T CTA
+
+
+def _pow2_at_least(x):
+    return 1 if x <= 1 else 2 * _pow2_at_least((x + 1) // 2)
+
+
+def _kernel_visits(rays, item):
+    """The (segment, k) pairs the K^T kernel's threads visit for one work item: thread t
+    takes the run [c0 + tC, c0 + (t+1)C), finds its first segment by the kernel's binary
+    search (halving steps from the power of two ASTEP), then walks the run in one loop that
+    moves to the next segment when the run crosses a segment end."""
+    tile, ray0, nray, c0, c1 = (int(v) for v in item)
+    s_ray = rays[ray0:ray0 + nray + 1]
+    astep = _pow2_at_least(ARAYS) // 2
+    C = (c1 - c0 + ATHREADS - 1) // ATHREADS
+    out = []
+    for t in range(ATHREADS):
+        p = c0 + t * C
+        p_end = min(c1, p + C)
+        if p >= p_end:
+            continue
+        j, step = 0, astep
+        while step > 0:
+            if j + step < nray and s_ray[j + step, 3] <= p:
+                j += step
+            step >>= 1
+        seg_end = int(s_ray[j + 1, 3])
+        k = int(s_ray[j, 2]) + (p - int(s_ray[j, 3]))
+        while p < p_end:
+            if p == seg_end:
+                j += 1
+                assert j < nray, "run left the item's segments"
+                seg_end = int(s_ray[j + 1, 3])
+                k = int(s_ray[j, 2])
+            out.append((ray0 + j, k))
+            p += 1
+            k += 1
+    return out
+
+
+@pytest.mark.parametrize("slots", [3, 40, 608])
+def test_kernel_traversal_visits_each_candidate_once(slots):
+    # the candidates of every item, visited as the kernel's threads do, are exactly the
+    # item's slice of its tile's list; over all items every candidate appears once
+    det = S.detectors_limited_arc(128, 24, 90.0, 5, radius=1.2)
+    r0, dr = S.radial_sampling(det, 96)
+    wl = P.pat_adjoint_worklist(72, det, 96, r0, dr, 128, slots)
+    rays, items = wl["rays"], wl["items"]
+    seen = []
+    for it in items:
+        tile, ray0, nray, c0, c1 = (int(v) for v in it)
+        if nray == 0:
+            continue
+        got = _kernel_visits(rays, it)
+        # expected: walk the tile's segments from the one holding c0
+        exp = []
+        j = ray0
+        for c in range(c0, c1):
+            while rays[j + 1, 3] <= c:
+                j += 1
+            exp.append((j, int(rays[j, 2]) + c - int(rays[j, 3])))
+        assert got == exp
+        seen += got
+    assert len(seen) == len(set(seen)) == wl["candidates"]
+
+
+def test_kernel_traversal_binary_search_many_segments():
+    # items with hundreds of segments (short rays near a detector inside the image) reach
+    # deep into the binary search; each run must start on the segment that holds it
+    det = _full_circle(16, 0.55)
+    r0, dr = S.radial_sampling(det, 80)
+    wl = P.pat_adjoint_worklist(40, det, 80, r0, dr, 96, slots=2)
+    items = wl["items"]
+    assert items[:, 2].max() > 64
+    total = 0
+    for it in items:
+        total += len(_kernel_visits(wl["rays"], it))
+    assert total == wl["candidates"]
