@@ -34,8 +34,8 @@ def _tables(n, det_xy, n_t, r0, dr, quad_m, extent=(-1.0, 1.0, -1.0, 1.0)):
     return det, cs, rk
 
 
-def _check_worklist(n, det_xy, n_t, r0, dr, quad_m, slots):
-    wl = P.pat_adjoint_worklist(n, det_xy, n_t, r0, dr, quad_m, slots)
+def _check_worklist(n, det_xy, n_t, r0, dr, quad_m, slots, extent=(-1.0, 1.0, -1.0, 1.0)):
+    wl = P.pat_adjoint_worklist(n, det_xy, n_t, r0, dr, quad_m, slots, extent)
     rays, items = wl["rays"], wl["items"]
     D, T, M = det_xy.shape[0], n_t, quad_m
     tiles_x = (n + WTILE - 1) // WTILE
@@ -88,7 +88,7 @@ def _check_worklist(n, det_xy, n_t, r0, dr, quad_m, slots):
         assert all(a[1] == b[0] for a, b in zip(iv, iv[1:])), f"tile {t}: pieces overlap or leave a gap"
 
     # every point with a tap in a tile is a candidate of that tile (FP32 point arithmetic)
-    det, cs, rk = _tables(n, det_xy, n_t, r0, dr, quad_m)
+    det, cs, rk = _tables(n, det_xy, n_t, r0, dr, quad_m, extent)
     dd, kk, mm = np.meshgrid(np.arange(D), np.arange(T), np.arange(M), indexing="ij")
     dd, kk, mm = dd.ravel(), kk.ravel(), mm.ravel()
     fx = (rk[kk].astype(np.float64) * cs[mm, 0] + det[dd, 0]).astype(np.float32)
@@ -131,6 +131,15 @@ def test_worklist_detectors_inside_the_image():
     det = _full_circle(16, 0.55)
     r0, dr = S.radial_sampling(det, 80)
     _check_worklist(40, det, 80, r0, dr, 96, slots=64)
+
+
+def test_worklist_non_square_extent():
+    # rectangular pixels (h_x != h_y) and detectors off-centre on both sides
+    det = np.array([[2.0, 0.0], [0.0, 2.5], [-1.5, -1.0], [0.3, 1.2]])
+    extent = (-1.5, 1.0, -0.5, 1.5)
+    far = max(math.hypot(dx - cx, dy - cy) for dx, dy in det for cx in extent[:2] for cy in extent[2:])
+    n_t = 90
+    _check_worklist(40, det, n_t, 0.1, far / n_t, 112, slots=24, extent=extent)
 
 
 def test_worklist_pieces_fill_one_wave():
