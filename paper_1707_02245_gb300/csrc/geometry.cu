@@ -4,9 +4,10 @@
 // point m of circle (d, k) is x_d + r_k (cos phi_m, sin phi_m), phi_m = 2 pi (m + 1/2)/M,
 // r_k = r0 + (k + 1/2) dr.  The tables built here are the only geometry state the
 // kernels read: detector positions and the M (cos, sin) pairs (both scaled to pixel
-// units), radii, arc weights
-// 2 pi r_k / M, and per group of 8 consecutive radii the circular range of angles
-// whose points can touch the grid (a superset: kernels test every point exactly).
+// units), the FP32 radii (one FMA each, see radius()), arc weights 2 pi r_k / M, per
+// group of 8 consecutive radii the circular range of angles whose points can touch the
+// grid (a superset: kernels test every point exactly), and the K^T work list (ray
+// segments per pixel tile and equal work items).
 #include <math.h>
 
 #include <algorithm>

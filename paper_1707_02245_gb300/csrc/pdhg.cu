@@ -53,7 +53,7 @@ struct UpdateArgs {
     float* x_out;
     float* xl_out;
     float* y_out;
-    float4* ubar_quad;     // (N+1)^2 quads of ubar for the projector
+    float4* ubar_quad;     // (N+1)^2 quads of ubar for the projector (layout quad_index)
     float4* u_quad;        // quads of u^{n+1} for the gap's K u (NULL: not a gap iteration)
     const int* stop;
     int* iter;             // iteration counter (incremented once per launch)
