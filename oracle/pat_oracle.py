@@ -51,7 +51,8 @@ R8  Residual: ||x^{n+1} - x^n||_2 / ||x^n||_2 over the primal variables.
 R9  Directional TV (not in this version of the paper): R(u) = ||D_xi grad u||_{1,2},
     D_xi = I - gamma xi xi^T, xi = grad w / sqrt(|grad w|^2 + eta^2).
 
-Parity pins live in tests/test_oracle_pins.py (closed forms, adjoint identities,
+Parity pins live in tests/test_oracle_pins.py (closed forms, adjoint identities, hand-worked
+residual sequences, the direction field of a ramp,
 independent solvers, limits).  No function here is unpinned.
 """
 from __future__ import annotations

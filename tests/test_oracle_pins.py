@@ -614,3 +614,98 @@ def test_pdhg_tolerance_stop_and_warm_start_resume():
     b1 = O.pdhg(pb, 25, theta=0.0)
     b2 = O.pdhg(pb, 15, theta=0.0, x0={"u": b1.u, "v": b1.v}, y0={"q": b1.q, "r": b1.r, "s": b1.s})
     np.testing.assert_allclose(b2.u, a.u, atol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# residual (reading R8) and the dTV direction field (reading R9)
+# ---------------------------------------------------------------------------
+
+def test_residual_hand_computed_two_step_sequence():
+    """||x^{n+1} - x^n|| / ||x^n|| on a hand-worked sequence x^0 -> x^1 -> x^2 of a primal
+    pair (u, v); the numbers are chosen so that dividing by ||x^{n+1}|| (or by the squared
+    norm, or dropping v) gives a different value."""
+    u0 = np.array([[2.0, 0.0], [1.0, 2.0]])            # |u0| = 3
+    v0 = np.zeros((2, 2, 2))
+    v0[1, 0, 1] = 4.0                                   # |x^0| = 5
+    u1 = u0.copy()
+    u1[1, 1] += 3.0                                     # step (3, 4): |x^1 - x^0| = 5
+    v1 = v0.copy()
+    v1[0, 1, 0] = 4.0                                   # |x^1|^2 = 4+1+25+16+16 = 62
+    assert O.residual([u1, v1], [u0, v0]) == pytest.approx(5.0 / 5.0, rel=1e-15)
+    u2 = u1.copy()
+    u2[0, 1] = 6.0                                      # step (6, 0): |x^2 - x^1| = 6
+    assert O.residual([u2, v1], [u1, v1]) == pytest.approx(6.0 / math.sqrt(62.0), rel=1e-15)
+    # the wrong denominator |x^{n+1}| = sqrt(98) would give 6 / 9.899, not 6 / 7.874
+    assert abs(O.residual([u2, v1], [u1, v1]) - 6.0 / math.sqrt(98.0)) > 0.1
+    # order matters: the old iterate is the second argument
+    assert abs(O.residual([u1, v1], [u2, v1]) - O.residual([u2, v1], [u1, v1])) > 0.1
+    # zero old iterate: 0 / 0 is 0, a step away from 0 is infinite
+    z = np.zeros((2, 2))
+    assert O.residual([z], [z]) == 0.0
+    assert O.residual([u0], [z]) == math.inf
+
+
+@pytest.mark.parametrize("reg", [O.REG_TV, O.REG_TGV])
+def test_pdhg_residual_history_against_consecutive_runs(reg):
+    """The residual the PDHG loop records after iteration n equals ||x^n - x^{n-1}|| /
+    ||x^{n-1}|| computed from two independent runs of n-1 and n iterations."""
+    rng = np.random.default_rng(11 + reg)
+    n = 6
+    Km = sp.csr_matrix(rng.uniform(0.0, 1.0, (20, n * n)) * (rng.uniform(size=(20, n * n)) < 0.3))
+    f = Km @ rng.uniform(0.0, 1.0, n * n)
+    pb = O.problem_from_matrix(Km, n, f, reg=reg, alpha=0.05, beta=1.0)
+    k = 7
+    res = O.pdhg(pb, k, gap_every=1)
+    prev = O.pdhg(pb, k - 1, gap_every=0, final_gap=False)
+    cur = O.pdhg(pb, k, gap_every=0, final_gap=False)
+    xo = [prev.u] + ([prev.v] if reg == O.REG_TGV else [])
+    xn = [cur.u] + ([cur.v] if reg == O.REG_TGV else [])
+    num = math.sqrt(sum(float(np.sum((a - b) ** 2)) for a, b in zip(xn, xo)))
+    den = math.sqrt(sum(float(np.sum(b * b)) for b in xo))
+    assert res.history[-1][0] == k
+    assert res.history[-1][3] == pytest.approx(num / den, rel=1e-12)
+    assert res.residual == pytest.approx(num / den, rel=1e-12)
+
+
+def test_direction_field_of_a_ramp():
+    """w = a ix + b iy has forward differences (a, b) inside the grid and zero difference
+    across the last column / row (reading R2), so xi = (a, b) / sqrt(a^2 + b^2 + eta^2)
+    inside, (0, b) / sqrt(b^2 + eta^2) on the last column, (a, 0) / sqrt(a^2 + eta^2) on
+    the last row and 0 at the last pixel.  eta = 0.5 separates eta from eta^2."""
+    n, a, b, eta = 7, -0.3, 0.4, 0.5
+    iy, ix = np.mgrid[0:n, 0:n].astype(np.float64)
+    w = a * ix + b * iy
+    xi = O.direction_field(w, eta)
+    assert xi.shape == (2, n, n)
+    inner = np.array([a, b]) / math.sqrt(a * a + b * b + eta * eta)     # (-0.4243, 0.5657)
+    np.testing.assert_allclose(xi[:, :-1, :-1], np.broadcast_to(inner[:, None, None], (2, n - 1, n - 1)),
+                               rtol=0, atol=1e-15)
+    np.testing.assert_allclose(xi[0, :-1, -1], 0.0, atol=0)
+    np.testing.assert_allclose(xi[1, :-1, -1], b / math.sqrt(b * b + eta * eta), rtol=1e-15)
+    np.testing.assert_allclose(xi[0, -1, :-1], a / math.sqrt(a * a + eta * eta), rtol=1e-15)
+    np.testing.assert_allclose(xi[1, -1, :-1], 0.0, atol=0)
+    assert xi[0, -1, -1] == 0.0 and xi[1, -1, -1] == 0.0
+    # eta (not squared) would give |xi| = 0.5 / sqrt(0.75) = 0.577 instead of 0.707
+    assert np.hypot(xi[0, 0, 0], xi[1, 0, 0]) == pytest.approx(math.sqrt(0.5), rel=1e-15)
+    # the sign follows the gradient, and the field scales out: xi(c w, c eta) = xi(w, eta)
+    np.testing.assert_allclose(O.direction_field(-3.0 * w, 3.0 * eta), -xi, rtol=1e-14, atol=1e-16)
+
+
+def test_direction_field_limits():
+    """|xi| < 1 everywhere, |xi| -> 1 where grad w != 0 as eta -> 0, and xi -> grad w / eta
+    as eta -> infinity (the first-order term of 1/sqrt(g^2 + eta^2))."""
+    rng = np.random.default_rng(5)
+    w = rng.standard_normal((9, 9))
+    xi = O.direction_field(w, 0.2)
+    assert np.all(np.hypot(xi[0], xi[1]) < 1.0)
+    gx = np.zeros_like(w)
+    gx[:, :-1] = w[:, 1:] - w[:, :-1]
+    gy = np.zeros_like(w)
+    gy[:-1, :] = w[1:, :] - w[:-1, :]
+    g = np.hypot(gx, gy)
+    xi0 = O.direction_field(w, 1e-12)
+    np.testing.assert_allclose(np.hypot(xi0[0], xi0[1])[g > 0], 1.0, rtol=1e-12)
+    big = 1e6
+    xib = O.direction_field(w, big)
+    np.testing.assert_allclose(xib[0] * big, gx, rtol=1e-10, atol=1e-12)
+    np.testing.assert_allclose(xib[1] * big, gy, rtol=1e-10, atol=1e-12)
