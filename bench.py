@@ -37,12 +37,13 @@ UNIT = "iters/s"
 WORKLOAD_DESC = ("tgv256: TGV^2 PDHG, 256x256 vessel phantom with exp(-3 depth) fluence, 256 detectors on a "
                  "full circle r=1.2, 512 time samples, M=256, 5% noise, alpha 0.02, beta 0.04, 1000 iterations, "
                  "diagonal preconditioning, FP64 gap every 10 iterations")
-FLOPS_PER_POINT = 22          # FP32 ops of one quadrature point: position 4, coordinates 4, floor/fraction 4, lerps 9, add 1
-# DRAM bytes (read + write) per launch of the projector kernels at the tgv256 workload, from
-# ncu captures of the current kernels (profiles/projector_kernels_tgv256.md; cold-cache
-# replay, the working set otherwise lives in L2)
-DRAM_BYTES_TGV256 = {"forward_prox": 2789632, "adjoint": 4508416}
-SMS, FP32_LANES = 152, 128    # GB300: SMs x FP32 lanes per SM
+# Algorithmic work of one quadrature point of K or K^T: about 15 FP32 operations
+# (position 2 FMA, floor and fraction 4, bilinear weights and lerps 8, accumulate 1) and
+# 4 gathered (K) or scattered (K^T) taps.  The projector bound is the smaller of the FP32
+# issue rate over 15 and the load/store rate over 4 (per SM and clock: 128 FP32 lanes,
+# 32 shared or L1 lane accesses).
+OPS_PER_POINT, TAPS_PER_POINT = 15, 4
+FP32_LANES, LSU_LANES = 128, 32
 
 
 # ---------------------------------------------------------------------------------
@@ -148,22 +149,22 @@ class ClockSampler:
 # CPU baseline: the FP64 oracle on the host cores
 # ---------------------------------------------------------------------------------
 
-def oracle_setup(workload: str, seed: int):
-    """Oracle problem for the workload (data simulated with the oracle on the same grid)."""
+def oracle_setup(workload: str, seed: int, workers: int):
+    """Oracle problem for the workload (data simulated with the oracle on the same grid),
+    with K and K^T applied over ``workers`` host processes (detector subsets)."""
     import numpy as np
 
     import synthetic as S
     from oracle import pat_oracle as O
+    from oracle.parallel import OraclePool
     w = S.workload(workload, seed)
     g = O.Geometry(n=w["n"], det_xy=w["det_xy"], n_t=w["n_t"], r0=w["r0"], dr=w["dr"], quad_m=w["quad_m"])
-    clean = O.forward(g, w["phantom"])
+    pool = OraclePool(g, workers)
+    clean = pool.forward(w["phantom"])
     f = clean + w["noise_level"] * np.abs(clean).max() * w["noise"]
-    n = g.n
     xi = O.direction_field(w["side"], w["eta"]) if w["reg"] == O.REG_DTV else None
-    pb = O.Problem(n=n, K=lambda u: O.forward(g, u).ravel(), KT=lambda y: O.adjoint(g, y), f=f, reg=w["reg"],
-                   alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"], xi=xi,
-                   k_abs_rows=O.forward(g, np.ones((n, n))).ravel(), k_abs_cols=O.adjoint(g, np.ones((g.n_det, g.n_t))))
-    return pb, O.diag_steps(pb)
+    pb = pool.problem(f, reg=w["reg"], alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"], xi=xi)
+    return pb, O.diag_steps(pb), pool
 
 
 def oracle_iters_per_s(pb, steps, iters: int) -> tuple[float, float]:
@@ -174,9 +175,21 @@ def oracle_iters_per_s(pb, steps, iters: int) -> tuple[float, float]:
     return iters / dt, dt
 
 
-def cpu_threads_used() -> int:
-    # the oracle is numpy element-wise code (no BLAS-threaded calls on its hot path)
-    return 1
+def oracle_baseline(workload: str, iters: int) -> dict:
+    """The FP64 oracle's PDHG iterations/s on all host cores (K and K^T over detector
+    subsets in worker processes) and on one core; setup untimed."""
+    from oracle.parallel import host_cores
+    cores = host_cores()
+    out = {}
+    for key, workers in (("all", cores), ("one", 1)):
+        pb, st, pool = oracle_setup(workload, 0, workers)
+        try:
+            oracle_iters_per_s(pb, st, 1) if workers > 1 else None     # start the workers
+            it_s, dt = oracle_iters_per_s(pb, st, iters)
+        finally:
+            pool.close()
+        out[key] = {"value": it_s, "cores": len(pool.spans), "seconds": dt}
+    return out
 
 
 # ---------------------------------------------------------------------------------
@@ -187,22 +200,26 @@ def run_reference(args) -> int:
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    pb, st = oracle_setup(args.workload, seed=0)
-    for _ in range(args.warmup):
-        oracle_iters_per_s(pb, st, 1)
-    times = []
-    for _ in range(args.steps):
-        _, dt = oracle_iters_per_s(pb, st, 1)
-        times.append(dt)
+    from oracle.parallel import host_cores
+    pb, st, pool = oracle_setup(args.workload, 0, host_cores())
+    try:
+        for _ in range(args.warmup):
+            oracle_iters_per_s(pb, st, 1)
+        times = []
+        for _ in range(args.steps):
+            _, dt = oracle_iters_per_s(pb, st, 1)
+            times.append(dt)
+    finally:
+        pool.close()
     total = sum(times)
     value = args.steps / total
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD_DESC, "iters_per_step": 1},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cpu_threads_used(), "kind": "oracle",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": len(pool.spans), "kind": "oracle",
                              "sample": "one FP64 oracle PDHG iteration of the tgv256 workload per step "
-                                       "(matrix-free numpy K and K^T)"},
+                                       "(matrix-free numpy K and K^T over detector subsets on all host cores)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -286,12 +303,11 @@ def run_gb300(args) -> int:
     wall = time.perf_counter() - wall0
     launches = P.pat_kernel_launches() - launches0
     barrier(dist, device)
-    # profiled replay of the same steps: CUDA events around every phase on the stream
-    P.pat_profile_read(reset=True)
-    P.pat_profile_enable(True)
-    prof_ms, _ = timed_steps(args.steps)
-    P.pat_profile_enable(False)
-    prof = P.pat_profile_read(reset=True)
+    # per-launch device time of each phase: every phase captured alone in a CUDA graph of
+    # 200 launches after 100 iterations of the same problem, replayed between CUDA events
+    prm_ph = P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], gamma=w["gamma"], xi=xi,
+                           iters=100, gap_every=10)
+    phase_us = P.pat_time_phases([geo.handle], [f], [prm_ph], 200, stream)
     clocks = sampler.stop()
 
     local_s = sum(step_ms) / 1e3
@@ -380,47 +396,53 @@ def run_gb300(args) -> int:
 
     # ---- roofline of the dominant phase ----
     NN = n * n
-    S_ = f.numel()
     pts = ginfo["points_on_grid"]
-    sm_mhz = clocks.get("sm_mhz") or 2070.0
+    sms = torch.cuda.get_device_properties(device).multi_processor_count
     peaks = load_peaks()
-    fp32_peak = SMS * FP32_LANES * 2 * 2070e6 / 1e12       # TFLOP/s at the maximum SM clock
+    f_max = (clocks.get("sm_max_mhz") or peaks["sm_max_mhz"]) * 1e6
+    fp32_pts = sms * FP32_LANES * f_max / OPS_PER_POINT        # points/s at full FP32 issue
+    lsu_pts = sms * LSU_LANES * f_max / TAPS_PER_POINT         # points/s at full load/store rate
+    proj_peak = min(fp32_pts, lsu_pts)
     per_pixel_floats = {0: 8, 1: 18, 2: 10}[w["reg"]]
+    per_step = {"forward_prox": iters, "adjoint": iters, "update": iters, "gap": iters // 10}
     phases = {}
-    for ph, (ms, cnt) in prof.items():
-        if cnt == 0:
+    for ph, cnt in per_step.items():
+        us = phase_us.get(ph) or 0.0
+        if cnt == 0 or us <= 0:
             continue
-        avg_s = ms / cnt / 1e3
-        ent = {"launches": cnt, "avg_us": avg_s * 1e6, "share": None}
+        ent = {"avg_us": us, "launches_per_step": cnt, "share": None}
         if ph in ("forward_prox", "adjoint"):
-            tflops = FLOPS_PER_POINT * pts / avg_s / 1e12
-            ent.update(bound="alu", achieved=tflops, peak=fp32_peak, unit="TFLOP/s", frac=tflops / fp32_peak,
-                       points_per_s=pts / avg_s)
+            rate = pts / (us * 1e-6)
+            ent.update(bound="alu", achieved=rate / 1e9, peak=proj_peak / 1e9, unit="Gpoint/s",
+                       frac=rate / proj_peak, fp32_issue_frac=rate / fp32_pts, lsu_frac=rate / lsu_pts)
         elif ph == "update":
-            gbs = 4.0 * per_pixel_floats * NN / avg_s / 1e9
+            gbs = 4.0 * per_pixel_floats * NN / (us * 1e-6) / 1e9
             ent.update(bound="hbm", achieved=gbs, peak=peaks["hbm_gbs"], unit="GB/s", frac=gbs / peaks["hbm_gbs"])
         phases[ph] = ent
-    tot = sum(v["avg_us"] * v["launches"] for v in phases.values())
+    tot = sum(v["avg_us"] * v["launches_per_step"] for v in phases.values())
     for v in phases.values():
-        v["share"] = v["avg_us"] * v["launches"] / tot if tot else None
-    dom_name = max(phases, key=lambda k: phases[k]["share"] if k in ("forward_prox", "adjoint", "update") else -1)
+        v["share"] = v["avg_us"] * v["launches_per_step"] / tot if tot else None
+    dom_name = max(("forward_prox", "adjoint", "update"), key=lambda k: phases[k]["share"] if k in phases else -1)
     dom = phases[dom_name]
-    traffic = DRAM_BYTES_TGV256.get(dom_name) if args.workload == "tgv256" else None
     roofline = {"kernel": dom_name, "bound": dom["bound"], "achieved": dom["achieved"], "peak": dom["peak"],
-                "unit": dom["unit"], "frac": dom["frac"], "traffic": traffic,
-                "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum per launch, cold-cache replay "
-                                  "(profiles/projector_kernels_tgv256.md)" if traffic else None,
-                "measured": "CUDA events around every launch in a profiled replay of the timed steps",
-                "peak_source": "FP32 152 SMs x 128 lanes x 2 x 2070 MHz" if dom["bound"] == "alu"
-                else peaks["source"]}
+                "unit": dom["unit"], "frac": dom["frac"], "traffic": None,
+                "measured": "pat_time_phases: the phase alone in a CUDA graph of 200 launches, CUDA events on its "
+                            "stream, after 100 iterations of the benchmark problem",
+                "peak_source": (f"min(FP32 issue / {OPS_PER_POINT}, load-store lanes / {TAPS_PER_POINT}) per "
+                                f"quadrature point: {sms} SMs x min({FP32_LANES}/{OPS_PER_POINT}, "
+                                f"{LSU_LANES}/{TAPS_PER_POINT}) x {f_max / 1e6:.0f} MHz")
+                if dom["bound"] == "alu" else peaks["source"]}
+    phase_ms_per_step = tot / 1e3
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        pb, st = oracle_setup(args.workload, seed=0)
-        it_s, dt = oracle_iters_per_s(pb, st, args.cpu_iters)
-        cpu = {"value": it_s, "unit": UNIT, "cores": cpu_threads_used(), "kind": "oracle",
-               "sample": f"{args.cpu_iters} FP64 oracle PDHG iteration(s) of the same workload "
-                         f"({dt:.1f} s; setup untimed)"}
+        ob = oracle_baseline(args.workload, args.cpu_iters)
+        cpu = {"value": ob["all"]["value"], "unit": UNIT, "cores": ob["all"]["cores"], "kind": "oracle",
+               "sample": f"{args.cpu_iters} FP64 oracle PDHG iteration(s) of the same workload, K and K^T over "
+                         f"detector subsets on {ob['all']['cores']} worker processes ({ob['all']['seconds']:.1f} s; "
+                         f"setup untimed)",
+               "single_core": {"value": ob["one"]["value"], "unit": UNIT, "cores": 1,
+                               "sample": f"the same iterations on one core ({ob['one']['seconds']:.1f} s)"}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -429,11 +451,12 @@ def run_gb300(args) -> int:
                 "config": {"workload": WORKLOAD_DESC, "iters_per_step": iters, "parallelism": f"replicas{world}",
                            "l2": "flushed before every step (256 MiB write outside the timed events)",
                            "points_on_grid_per_K": pts, "final_rel_gap": infos[-1]["rel_gap"]},
-                "roofline": roofline, "phases": phases, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roofline, "phases": phases, "phase_ms_per_step": phase_ms_per_step,
+                "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "time_to_gap": ttg,
                 "batched": batched, "mixed_batch": mixed, "warm_start": warm, "preprocess": prep, "wavelet": wav,
                 "update_hbm": upd_hbm,
-                "wall_s_timed": wall, "profiled_ms_per_step": sum(prof_ms) / len(prof_ms)}
+                "wall_s_timed": wall}
         print(json.dumps(line), flush=True)
     geo.close()
     if dist is not None:
@@ -475,21 +498,16 @@ def run_update_hbm(P, S, np, torch, device, stream, flush, count=16, n=512, iter
     px = count * n * n
     peaks = load_peaks()
     out = {"problems": count, "n": n, "pixels": px, "state_bytes": 29 * 4 * px}
-    flush.zero_()
-    P.pat_profile_read(reset=True)
-    P.pat_profile_enable(True)
-    P.pat_reconstruct_batched(geos, fs, prms, us, stream)
-    P.pat_profile_enable(False)
-    prof = P.pat_profile_read(reset=True)
-    ms, cnt = prof["update"]
-    avg_s = ms / cnt / 1e3
+    phase_us = P.pat_time_phases(geos, fs, prms, 20, stream)
+    avg_s = phase_us["update"] * 1e-6
     alg = 18 * 4 * px / avg_s / 1e9
     moved = 29 * 4 * px / avg_s / 1e9
-    out.update({"launches": cnt, "avg_us": avg_s * 1e6,
+    out.update({"avg_us": avg_s * 1e6,
                 "roofline": {"bound": "hbm", "achieved": alg, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                              "frac": alg / peaks["hbm_gbs"], "bytes_per_pixel": 72},
                 "moved_gb_per_s": moved, "moved_frac": moved / peaks["hbm_gbs"],
-                "phases_us": {k: (v[0] / v[1] * 1e3 if v[1] else None) for k, v in prof.items()}})
+                "measured": "pat_time_phases: 20 launches in a CUDA graph after the batch's iterations",
+                "phases_us": phase_us})
     for p in probs:
         p[0].close()
     return out
@@ -718,9 +736,10 @@ def load_peaks() -> dict:
         with open(path) as fh:
             pk = json.load(fh)
         return {"hbm_gbs": float(pk["hbm_gbs"]), "bf16_tflops": float(pk["bf16_tflops"]),
+                "sm_max_mhz": float(pk.get("sm_max_mhz", 2070.0)),
                 "source": "measured (MEASURED_PEAKS.json hbm_gbs)"}
     except (OSError, KeyError, ValueError):
-        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "source": "fallback (profiling recipe)"}
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0, "source": "fallback (profiling recipe)"}
 
 
 def main(argv=None) -> int:
@@ -730,7 +749,7 @@ def main(argv=None) -> int:
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
     ap.add_argument("--workload", default="tgv256")
-    ap.add_argument("--cpu-iters", type=int, default=1)
+    ap.add_argument("--cpu-iters", type=int, default=2, help="oracle iterations of the CPU baseline")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-ttg", action="store_true")
     ap.add_argument("--ttg-max-iters", type=int, default=60000)

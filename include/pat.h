@@ -131,6 +131,16 @@ typedef struct {
     int    adapt;
     /* PAT_WAV: levels J of the transform, 1..12, with N divisible by 2^J (0: 4) */
     int    wavelet_levels;
+    /* The primal iterates x = (u, v) are kept as compensated pairs hi + lo (every update
+       is added with an error-free two-sum), and x_out_dev receives the high words.
+       x_lo_out_dev (layout of x, NULL = not written) receives the low words, and
+       x_lo0_dev (layout of x, NULL = zero) starts a run from them.  Passing x_out,
+       xbar_out, y_out and x_lo_out of one run as x0, xbar0, y0 and x_lo0 of the next
+       continues it bit for bit (the gap schedule restarts at the resumed iteration).
+       PAT_WAV iterates are plain FP32: its low words are zero.  Not Sec. 3: a numerical
+       device of this library. */
+    const float* x_lo0_dev;
+    float* x_lo_out_dev;
 } pat_params;
 
 #define PAT_ADAPT_NONE     0
@@ -231,10 +241,10 @@ int  pat_preprocess(const pat_geometry* g, const float* p_dev, const float* pcal
 /* ---- K^T without device allocation -------------------------------------------------- */
 /* u = K^T y like pat_adjoint, but the call allocates no device memory: no cudaMalloc,
  * cudaFree, stream-ordered pool or other allocating routine.  This is for callers that
- * must not allocate at the time of the call.  Examples: code running while a CUDA graph
- * is being captured, real-time loops that must not touch an allocator, and host
- * applications whose device memory is owned by another allocator.  The paper has no
- * counterpart; this is a deployment variant of the adjoint.
+ * must not allocate at the time of the call.  Examples: real-time loops that must not
+ * touch an allocator, and host applications whose device memory is owned by another
+ * allocator or fixed at start-up.  The paper has no counterpart; this is a deployment
+ * variant of the adjoint.
  *  - Scratch: a device array of 4 MiB + 256 bytes built into the library.  Every GPU that
  *    loads the library holds it until the process exits.  Its contents persist from call
  *    to call, and the call clears what it needs.
@@ -243,7 +253,9 @@ int  pat_preprocess(const pat_geometry* g, const float* p_dev, const float* pcal
  *    by pat_steps, pat_adjoint or pat_reconstruct (they compute the FP64 K sums that scale
  *    the fixed-point accumulation).  Otherwise PAT_ERR_INVALID_ARG.
  *  - Set-up: the first call on a device looks up the scratch's device address for that
- *    device (current at the call).  Make that first call before any stream capture.
+ *    device (current at the call) and keeps it for the life of the process.  Make that
+ *    first call before any stream capture.  The kept address does not survive
+ *    cudaDeviceReset: do not call this entry point after resetting the device.
  *  - Concurrency: all calls on one device share the scratch.  Calls that overlap on the
  *    GPU (other streams, or other host threads without ordering) race; order them on
  *    one stream.
@@ -266,6 +278,18 @@ int  pat_profile_enable(int on);
 /* ms_host[PAT_NPHASES]: summed device milliseconds per phase; launches_host[PAT_NPHASES]:
  * number of timed launches per phase (either may be NULL).  reset != 0 clears the sums. */
 int  pat_profile_read(double* ms_host, long long* launches_host, int reset);
+/* Device time of each phase of the batched iteration, measured without per-launch
+ * bracketing: the `count` problems (arrays as in pat_reconstruct_batched) first run
+ * p[0].iters iterations as pat_reconstruct_batched would (tol and adapt ignored), then
+ * each phase's launch (one launch over all problems; the update counts its per-regulariser
+ * launches together, the gap its three kernels) is captured `reps` times (1..100000) in a
+ * CUDA graph and replayed once to warm up and once between two CUDA events on the
+ * library's loop stream.  us_host[PAT_NPHASES] receives microseconds per launch
+ * (PAT_PHASE_ADJ_CLEAR: 0).  Nothing is written to the caller's buffers; the call
+ * synchronises `stream`.  Fails if the per-launch profiler is on.  Not Sec. 3: a
+ * measurement aid. */
+int  pat_time_phases(int count, const pat_geometry* const* g, const float* const* f_dev,
+                     const pat_params* p, int reps, double* us_host, void* stream);
 /* Number of kernels this library has launched in the process so far. */
 long long pat_kernel_launches(void);
 

@@ -37,6 +37,7 @@ EXPORTED = [
     "pat_adjoint_worklist",
     "pat_profile_enable", "pat_profile_read", "pat_kernel_launches", "pat_adjoint_noalloc",
     "pat_tune_step_ratio", "pat_tune_step_ratio_batched", "pat_preprocess", "pat_wavelet_transform",
+    "pat_time_phases",
     # learned warm start (include/pat_unet.h)
     "pat_conv3x3_forward", "pat_conv3x3_backward_data", "pat_conv3x3_backward_weight",
     "pat_unet_create", "pat_unet_destroy", "pat_unet_num_params", "pat_unet_get_params",
@@ -69,7 +70,8 @@ class pat_params(ctypes.Structure):
                 ("x0_dev", ctypes.c_void_p), ("xbar0_dev", ctypes.c_void_p), ("y0_dev", ctypes.c_void_p),
                 ("x_out_dev", ctypes.c_void_p), ("xbar_out_dev", ctypes.c_void_p),
                 ("y_out_dev", ctypes.c_void_p), ("step_ratio", ctypes.c_double), ("adapt", ctypes.c_int),
-                ("wavelet_levels", ctypes.c_int)]
+                ("wavelet_levels", ctypes.c_int), ("x_lo0_dev", ctypes.c_void_p),
+                ("x_lo_out_dev", ctypes.c_void_p)]
 
 
 class pat_unet_desc(ctypes.Structure):
@@ -122,6 +124,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                             ctypes.POINTER(d), i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]),
         "pat_tune_step_ratio": (i, [vp, vp, ctypes.POINTER(pat_params), ctypes.POINTER(d), i, i, ctypes.POINTER(d),
                                     ctypes.POINTER(d), vp]),
+        "pat_time_phases": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(pat_params), i,
+                                ctypes.POINTER(d), vp]),
         "pat_error_string": (ctypes.c_char_p, [i]),
         "pat_last_error": (ctypes.c_char_p, []),
         "pat_geometry_info": (i, [vp, ctypes.POINTER(ctypes.c_longlong)]),
@@ -243,7 +247,7 @@ def pat_params_default() -> pat_params:
 def make_params(reg=PAT_TV, alpha=0.05, beta=1.0, gamma=0.95, xi=None, iters=100, tol=0.0, gap_every=10,
                 precond=PAT_PRECOND_DIAG, theta=1.0, box_u=2.0, box_v=4.0, x0=None, xbar0=None, y0=None,
                 x_out=None, xbar_out=None, y_out=None, step_ratio=1.0, adapt=PAT_ADAPT_NONE,
-                wavelet_levels=4) -> pat_params:
+                wavelet_levels=4, x_lo0=None, x_lo_out=None) -> pat_params:
     p = pat_params_default()
     p.reg, p.alpha, p.beta, p.gamma = reg, alpha, beta, gamma
     p.xi_dev = _ptr(xi)
@@ -252,8 +256,9 @@ def make_params(reg=PAT_TV, alpha=0.05, beta=1.0, gamma=0.95, xi=None, iters=100
     p.x0_dev, p.xbar0_dev, p.y0_dev = _ptr(x0), _ptr(xbar0), _ptr(y0)
     p.x_out_dev, p.xbar_out_dev, p.y_out_dev = _ptr(x_out), _ptr(xbar_out), _ptr(y_out)
     p.step_ratio, p.adapt, p.wavelet_levels = step_ratio, adapt, wavelet_levels
+    p.x_lo0_dev, p.x_lo_out_dev = _ptr(x_lo0), _ptr(x_lo_out)
     # keep the buffers alive as long as the parameter block that points at them
-    p._keep = [xi, x0, xbar0, y0, x_out, xbar_out, y_out]
+    p._keep = [xi, x0, xbar0, y0, x_out, xbar_out, y_out, x_lo0, x_lo_out]
     return p
 
 
@@ -310,6 +315,19 @@ def pat_tune_step_ratio_batched(geoms, fs, params, candidates, probe_iters: int,
     _check(load().pat_tune_step_ratio_batched(n, G, F, Pp, C, c, probe_iters, best, gaps, _stream(stream)),
            "pat_tune_step_ratio_batched")
     return list(best), [list(gaps[i * c:(i + 1) * c]) for i in range(n)]
+
+
+def pat_time_phases(geoms, fs, params, reps: int, stream=None) -> dict:
+    """Microseconds per launch of each phase of the batched iteration, each phase timed
+    alone in a CUDA graph of ``reps`` launches after ``params[0].iters`` iterations
+    (see include/pat.h).  Returns {phase name: us}."""
+    n = len(geoms)
+    G = (ctypes.c_void_p * n)(*geoms)
+    F = (ctypes.c_void_p * n)(*[_ptr(f) for f in fs])
+    Pp = (pat_params * n)(*params)
+    us = (ctypes.c_double * len(PHASES))()
+    _check(load().pat_time_phases(n, G, F, Pp, int(reps), us, _stream(stream)), "pat_time_phases")
+    return {name: us[k] for k, name in enumerate(PHASES)}
 
 
 def pat_wavelet_transform(n: int, levels: int, in_dev, out_dev, inverse: bool = False, stream=None) -> None:

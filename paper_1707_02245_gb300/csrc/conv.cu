@@ -414,7 +414,7 @@ SplitPlan plan_splits(int B, int H, int W, int cin, int cout) {
     const long long chunks = std::max<long long>(1, (P + WBK - 1) / WBK);
     const int bm = cout <= 32 ? 32 : 64;
     const long long tiles = (long long)((9 * cin + WBN - 1) / WBN) * ((cout + bm - 1) / bm);
-    long long want = std::max<long long>(1, (2 * 152 + tiles - 1) / tiles);
+    long long want = std::max<long long>(1, (2LL * sm_count() + tiles - 1) / tiles);
     want = std::min<long long>(want, std::max<long long>(1, chunks / 8));   // >= 8 chunks per split
     want = std::min<long long>(want, 512);
     const long long per = (chunks + want - 1) / want;

@@ -37,6 +37,25 @@ int cuda_fail(cudaError_t e, const char* what) {
 static std::atomic<long long> g_launches{0};
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+// Streaming multiprocessors of the current device, queried once per device.
+int sm_count() {
+    static std::atomic<int> cached[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        dev = 0;
+    }
+    const int slot = dev >= 0 && dev < 64 ? dev : 0;
+    int n = cached[slot].load(std::memory_order_relaxed);
+    if (n > 0) return n;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        return 1;   // no device: launch sizes only need a positive count
+    }
+    cached[slot].store(n, std::memory_order_relaxed);
+    return n;
+}
+
 // ---- profiler --------------------------------------------------------------------
 static std::atomic<bool> g_prof{false};
 static std::mutex g_prof_mtx;
@@ -517,9 +536,7 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
 
     AdjWork aw;
     {
-        int sms = 152;
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, g->device);
-        const int rc = adjoint_worklist(d, pt, (double)std::max(1, sms) * adjoint_blocks_per_sm(), aw);
+        const int rc = adjoint_worklist(d, pt, (double)sm_count() * adjoint_blocks_per_sm(), aw);
         if (rc) {
             delete g;
             return rc;
@@ -581,7 +598,7 @@ extern "C" int pat_adjoint_worklist(const pat_geometry_desc* desc, int slots, in
     if (vrc) return vrc;
     double s = slots;
     if (slots <= 0) {
-        int dev = 0, sms = 152;
+        int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
             cudaGetLastError();

@@ -27,6 +27,7 @@ int cuda_fail(cudaError_t e, const char* what);
     } while (0)
 
 void count_launch();
+int sm_count();   // SMs of the current device (sizes grid-stride launches)
 
 // Every kernel launch of the library is followed by this check, which also counts it.
 #define PAT_LAUNCH_CHECK(what)                                      \

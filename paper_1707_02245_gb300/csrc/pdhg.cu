@@ -706,12 +706,14 @@ struct OutArgs {
     long long S;
     float theta;
     const float* X[2];
+    const float* XL[2];   // low words of the compensated primal pairs
     const float* Y[2];
     const float* q;
     const float4* ubar_quad;
     const InfoDev* info;
     float* u_out;
     float* x_out;
+    float* x_lo_out;
     float* xbar_out;
     float* y_out;
 };
@@ -722,6 +724,8 @@ __global__ void k_output(OutArgs a) {
     const int it = a.info->iter;
     const float* x = a.X[it & 1];
     const float* x_prev = a.X[(it + 1) & 1];
+    const float* xl = a.XL[it & 1];
+    const float* xl_prev = a.XL[(it + 1) & 1];
     const float* yrs = a.Y[(it + 1) & 1];  // r^I, s^I were read by the last update
     const int nv = a.reg == PAT_TGV ? 2 : 0;
     const long long nx = NN * (1 + nv), ny = NN * (a.reg == PAT_TGV ? 5 : 2);
@@ -730,14 +734,17 @@ __global__ void k_output(OutArgs a) {
         if (i < nx) {
             if (i < NN && a.u_out) a.u_out[i] = x[i];
             if (a.x_out) a.x_out[i] = x[i];
+            if (a.x_lo_out) a.x_lo_out[i] = xl[i];
             if (a.xbar_out) {
                 if (i < NN) {
                     const int gx = (int)(i % N), gy = (int)(i / N);
                     a.xbar_out[i] = a.ubar_quad[quad_index(gx + 1, gy + 1, N)].x;
                 } else {
-                    // vbar^I = v^I + theta (v^I - v^{I-1}); with I = 0 the warm-start vbar is
-                    // not recoverable here and v^0 is returned
-                    a.xbar_out[i] = it > 0 ? fmaf(a.theta, x[i] - x_prev[i], x[i]) : x[i];
+                    // vbar^I = v^I + theta (v^I - v^{I-1}) from the compensated pairs, the
+                    // same expression as the update kernel's; with I = 0 the warm-start
+                    // vbar is not recoverable here and v^0 is returned
+                    a.xbar_out[i] = it > 0 ? fmaf(a.theta, (x[i] - x_prev[i]) + (xl[i] - xl_prev[i]), x[i] + xl[i])
+                                           : x[i];
                 }
             }
         } else if (a.y_out) {
@@ -771,7 +778,7 @@ struct Workspace {
     int n_data = 0, n_pix = 0;
 };
 
-static int pix_blocks(int N) { return std::min(4 * 152, ceil_div((long long)N * N, 256)); }
+static int pix_blocks(int N) { return std::min(4 * sm_count(), ceil_div((long long)N * N, 256)); }
 
 static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaStream_t st) {
     const size_t N = g->desc.n, NN = N * N, S = (size_t)g->desc.n_det * g->desc.n_t;
@@ -1151,7 +1158,10 @@ static int init_problem(Prob& pr, cudaStream_t st) {
     const float mul[2] = {(float)ratio, (float)(1.0 / ratio)};
     PAT_CUDA(cudaMemcpyAsync(ws.info->step_mul, mul, sizeof mul, cudaMemcpyHostToDevice, st));
     PAT_CUDA(cudaMemsetAsync(ws.kt[0], 0, 2 * NN * sizeof(int), st));
-    PAT_CUDA(cudaMemsetAsync(ws.XL[0], 0, nx * sizeof(float), st));
+    if (p->x_lo0_dev)
+        PAT_CUDA(cudaMemcpyAsync(ws.XL[0], p->x_lo0_dev, nx * 4, cudaMemcpyDeviceToDevice, st));
+    else
+        PAT_CUDA(cudaMemsetAsync(ws.XL[0], 0, nx * sizeof(float), st));
     const float* xb = p->xbar0_dev ? p->xbar0_dev : p->x0_dev;
     dim3 blk(32, 8), grd(ceil_div(N + 2, 32), ceil_div(N + 2, 8));
     k_pad<<<grd, blk, 0, st>>>(xb, ws.ubar_pad, N);
@@ -1192,6 +1202,8 @@ static int finish_problem(Prob& pr, cudaStream_t st) {
     oa.theta = (float)pr.p.theta;
     oa.X[0] = pr.ws.X[0];
     oa.X[1] = pr.ws.X[1];
+    oa.XL[0] = pr.ws.XL[0];
+    oa.XL[1] = pr.ws.XL[1];
     oa.Y[0] = pr.ws.Y[0];
     oa.Y[1] = pr.ws.Y[1];
     oa.q = pr.ws.q;
@@ -1199,9 +1211,10 @@ static int finish_problem(Prob& pr, cudaStream_t st) {
     oa.info = pr.ws.info;
     oa.u_out = pr.u_out;
     oa.x_out = pr.p.x_out_dev;
+    oa.x_lo_out = pr.p.x_lo_out_dev;
     oa.xbar_out = pr.p.xbar_out_dev;
     oa.y_out = pr.p.y_out_dev;
-    k_output<<<std::min(2 * 152, ceil_div((long long)(nx + ny + S), 256)), 256, 0, st>>>(oa);
+    k_output<<<std::min(2 * sm_count(), ceil_div((long long)(nx + ny + S), 256)), 256, 0, st>>>(oa);
     PAT_LAUNCH_CHECK("k_output");
     return PAT_OK;
 }
@@ -1572,6 +1585,7 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
     if (!rc) {
         PAT_CUDA(cudaMemcpyAsync(u_out, u, NN * 4, cudaMemcpyDeviceToDevice, st));
         if (p->x_out_dev) PAT_CUDA(cudaMemcpyAsync(p->x_out_dev, u, NN * 4, cudaMemcpyDeviceToDevice, st));
+        if (p->x_lo_out_dev) PAT_CUDA(cudaMemsetAsync(p->x_lo_out_dev, 0, NN * 4, st));
         if (p->xbar_out_dev) PAT_CUDA(cudaMemcpyAsync(p->xbar_out_dev, ubar, NN * 4, cudaMemcpyDeviceToDevice, st));
         if (p->y_out_dev) {
             PAT_CUDA(cudaMemcpyAsync(p->y_out_dev, q, S * 4, cudaMemcpyDeviceToDevice, st));
@@ -1701,6 +1715,118 @@ static int run_batch(int B, const pat_geometry* const* g, const float* const* f,
 }
 
 // ---------------------------------------------------------------------------------
+// Phase timing: the batch runs its iterations as usual, then each phase's launch (all
+// problems, iteration parity 0) is captured `reps` times in a graph of its own and
+// replayed between two CUDA events.  Launches of one graph follow each other with no
+// host work in between, as in the iteration loop's graph, so the per-launch times add up
+// to the loop's time per iteration.  Repeated K^T launches accumulate without the clear
+// that an iteration performs (integer wrap-around, same work), so the state is not used
+// afterwards and nothing is written to the caller's buffers.
+// ---------------------------------------------------------------------------------
+static int time_phases(int B, const pat_geometry* const* g, const float* const* f, const pat_params* p, int reps,
+                       double* us, cudaStream_t st, const char* who) {
+    std::vector<Prob> pr(B);
+    int rc = PAT_OK;
+    for (int b = 0; b < B && !rc; ++b) {
+        pr[b].g = g[b];
+        pr[b].f = f[b];
+        pr[b].p = p[b];
+        pr[b].p.tol = 0.0;
+        pr[b].p.adapt = PAT_ADAPT_NONE;
+        pr[b].p.x_out_dev = pr[b].p.xbar_out_dev = pr[b].p.y_out_dev = pr[b].p.x_lo_out_dev = nullptr;
+        rc = init_problem(pr[b], st);
+    }
+    std::vector<char> host;
+    void* dev = nullptr;
+    cudaStream_t ls = loop_stream();
+    cudaEvent_t fork = nullptr, join = nullptr, e0 = nullptr, e1 = nullptr;
+    if (!rc && !ls) rc = fail(PAT_ERR_CUDA, std::string(who) + ": no loop stream");
+    if (!rc) rc = cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+                          cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess &&
+                          cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess
+                      ? PAT_OK
+                      : fail(PAT_ERR_CUDA, std::string(who) + ": events");
+    IterPlan ip;
+    if (!rc) {
+        Arena ar(host);
+        build_iter_plan(pr.data(), B, ar, ip, nullptr);
+        rc = ar.upload(&dev, st);
+    }
+    if (!rc) rc = cudaEventRecord(fork, st) == cudaSuccess && cudaStreamWaitEvent(ls, fork, 0) == cudaSuccess
+                      ? PAT_OK
+                      : fail(PAT_ERR_CUDA, std::string(who) + ": stream join");
+    const char* base = (const char*)dev;
+    if (!rc) rc = run_iterations(ip, base, p[0].iters, p[0].gap_every, ls, nullptr, B, false);
+    for (int ph = 0; ph < PAT_NPHASES; ++ph) us[ph] = 0.0;
+    // state-preserving phases first; K^T (accumulates) and the update (reads it) last
+    const int order[4] = {PAT_PHASE_FORWARD_PROX, PAT_PHASE_GAP, PAT_PHASE_ADJOINT, PAT_PHASE_UPDATE};
+    for (int oi = 0; oi < 4 && !rc; ++oi) {
+        const int ph = order[oi];
+        auto enqueue = [&]() -> int {
+            if (ph == PAT_PHASE_FORWARD_PROX)
+                return launch_forward_prox_b((const FwdProxArgs*)(base + ip.fwd[0]), (const int2*)(base + ip.map_fwd),
+                                             ip.n_fwd, ls);
+            if (ph == PAT_PHASE_ADJOINT)
+                return launch_adjoint_b((const AdjArgs*)(base + ip.adj[0]), (const int2*)(base + ip.map_adj), ip.n_adj,
+                                        true, ls);
+            if (ph == PAT_PHASE_UPDATE) {
+                const UpdateArgs* ua = (const UpdateArgs*)(base + ip.upd[0][0]);
+                for (int r = 0; r < 3; ++r) {
+                    const int e = launch_update_b(r, ua, (const int2*)(base + ip.map_upd[r]), ip.n_upd[r], ls);
+                    if (e) return e;
+                }
+                return PAT_OK;
+            }
+            return launch_gap_phase((const FwdGapArgs*)(base + ip.fgap[0]), (const GapArgs*)(base + ip.gpix[0]),
+                                    (const FinalArgs*)(base + ip.fin), ip.gp, base, ls);
+        };
+        for (int b = 0; b < B; ++b) cudaMemsetAsync(&pr[b].ws.info->stop, 0, sizeof(int), ls);
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        const long long l0 = pat_kernel_launches();
+        cudaError_t e = cudaStreamBeginCapture(ls, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) {
+            rc = cuda_fail(e, "time_phases: capture");
+            break;
+        }
+        for (int r = 0; r < reps && !rc; ++r) rc = enqueue();
+        e = cudaStreamEndCapture(ls, &graph);
+        if (!rc && e != cudaSuccess) rc = cuda_fail(e, "time_phases: capture");
+        if (!rc) {
+            e = cudaGraphInstantiate(&exec, graph, 0);
+            if (e != cudaSuccess) rc = cuda_fail(e, "time_phases: instantiate");
+        }
+        const long long per_graph = pat_kernel_launches() - l0;
+        if (!rc) {
+            e = cudaGraphLaunch(exec, ls);   // warm-up replay
+            if (e == cudaSuccess) e = cudaEventRecord(e0, ls);
+            if (e == cudaSuccess) e = cudaGraphLaunch(exec, ls);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, ls);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) rc = cuda_fail(e, "time_phases: replay");
+            us[ph] = 1e3 * (double)ms / reps;
+            for (long long k = 0; k < per_graph; ++k) count_launch();   // the second replay
+        }
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+    }
+    if (join && ls) {
+        cudaEventRecord(join, ls);
+        cudaStreamWaitEvent(st, join, 0);
+    }
+    if (dev) cudaFreeAsync(dev, st);
+    for (int b = 0; b < B; ++b)
+        if (pr[b].ws.base) cudaFreeAsync(pr[b].ws.base, st);
+    cudaError_t se = cudaStreamSynchronize(st);
+    if (!rc && se != cudaSuccess) rc = cuda_fail(se, who);
+    for (cudaEvent_t ev : {fork, join, e0, e1})
+        if (ev) cudaEventDestroy(ev);
+    return rc;
+}
+
+// ---------------------------------------------------------------------------------
 // paper rule (Sec. 3.3.2): L1 = ||K||, L2 = ||B|| by power iteration from the start
 // vector x_j = 1 + sin(0.7 j + 0.3)/2; tau = 1/L1, sigma_i = 0.99 / (4 tau L_i^2)
 // ---------------------------------------------------------------------------------
@@ -1803,7 +1929,7 @@ int scalar2_steps(const pat_geometry* g, const pat_params* p, ScalarSteps& out, 
     PAT_CUDA(cudaMallocAsync(&acc, 2 * kPowerIters * 2 * sizeof(double), st));
     PAT_CUDA(cudaMemsetAsync(acc, 0, 2 * kPowerIters * 2 * sizeof(double), st));
     dim3 blk(32, 8), grd(ceil_div(N, 32), ceil_div(N, 8));
-    const int nb = 2 * 152;
+    const int nb = 2 * sm_count();
     double lam[2] = {0, 0};
     for (int op = 0; op < 2; ++op) {
         const long long n = op == 0 ? NN : nx;
@@ -1959,7 +2085,7 @@ static int tune_impl(int count, const pat_geometry* const* g, const float* const
                 q.iters = probe_iters;
                 q.tol = 0.0;
                 q.gap_every = 0;
-                q.x_out_dev = q.xbar_out_dev = q.y_out_dev = nullptr;
+                q.x_out_dev = q.xbar_out_dev = q.y_out_dev = q.x_lo_out_dev = nullptr;
                 pat_info ii{};
                 rc = p[b].reg == PAT_WAV ? run_wavelet(g[b], f[b], &q, ub, &ii, st, who)
                                          : run_batch(1, &g[b], &f[b], &q, &ub, &ii, st, who);
@@ -1993,7 +2119,7 @@ static int tune_impl(int count, const pat_geometry* const* g, const float* const
             pp[k].iters = probe_iters;
             pp[k].tol = 0.0;
             pp[k].gap_every = 0;
-            pp[k].x_out_dev = pp[k].xbar_out_dev = pp[k].y_out_dev = nullptr;
+            pp[k].x_out_dev = pp[k].xbar_out_dev = pp[k].y_out_dev = pp[k].x_lo_out_dev = nullptr;
             uu[k] = scratch + off;
             off += (size_t)g[b]->desc.n * g[b]->desc.n;
         }
@@ -2025,6 +2151,22 @@ extern "C" int pat_tune_step_ratio_batched(int count, const pat_geometry* const*
                                            void* stream) {
     return tune_impl(count, g, f_dev, p, candidates_host, n_candidates, probe_iters, best_host, rel_gaps_host,
                      (cudaStream_t)stream, "pat_tune_step_ratio_batched");
+}
+
+extern "C" int pat_time_phases(int count, const pat_geometry* const* g, const float* const* f_dev,
+                               const pat_params* p, int reps, double* us_host, void* stream) {
+    if (count < 1 || !g || !f_dev || !p || !us_host || reps < 1 || reps > 100000)
+        return fail(PAT_ERR_INVALID_ARG, "pat_time_phases: bad count, pointer or reps");
+    if (prof_on()) return fail(PAT_ERR_INVALID_ARG, "pat_time_phases: turn the per-launch profiler off first");
+    for (int b = 0; b < count; ++b) {
+        const int rc = validate(g[b], &p[b], "pat_time_phases");
+        if (rc) return rc;
+        if (!f_dev[b]) return fail(PAT_ERR_INVALID_ARG, "pat_time_phases: NULL data");
+        if (p[b].reg == PAT_WAV) return fail(PAT_ERR_INVALID_ARG, "pat_time_phases: PAT_WAV has no batch engine");
+        if (p[b].iters != p[0].iters || p[b].gap_every != p[0].gap_every)
+            return fail(PAT_ERR_INVALID_ARG, "pat_time_phases: a batch needs equal iters and gap_every");
+    }
+    return time_phases(count, g, f_dev, p, reps, us_host, (cudaStream_t)stream, "pat_time_phases");
 }
 
 extern "C" int pat_steps(const pat_geometry* g, const pat_params* p, float* sig_q_dev, float* tau_u_dev,

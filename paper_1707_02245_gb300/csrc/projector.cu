@@ -542,7 +542,7 @@ int launch_forward_gap_b(const FwdGapArgs* args, const int2* map, int nblocks, c
 }
 
 int launch_absmax(const float* y, long long n, unsigned* out, cudaStream_t st) {
-    k_absmax<<<std::min(4 * 152, ceil_div(n, 256)), 256, 0, st>>>(y, n, out);
+    k_absmax<<<std::min(4 * sm_count(), ceil_div(n, 256)), 256, 0, st>>>(y, n, out);
     PAT_LAUNCH_CHECK("k_absmax");
     return PAT_OK;
 }
@@ -611,7 +611,7 @@ int launch_adjoint_into(const pat_geometry* g, const float* y, unsigned* ymax_bi
                         cudaStream_t st) {
     const int N = g->desc.n;
     const long long S = (long long)g->desc.n_det * g->desc.n_t;
-    k_absmax<<<std::min(4 * 152, ceil_div(S, 256)), 256, 0, st>>>(y, S, ymax_bits);
+    k_absmax<<<std::min(4 * sm_count(), ceil_div(S, 256)), 256, 0, st>>>(y, S, ymax_bits);
     PAT_LAUNCH_CHECK("k_absmax");
     const AdjArgs a = make_adj_args(g, y, nullptr, ymax_bits, acc, nullptr);
     k_adjoint_tiles<false><<<g->adj_items, ATHREADS, 0, st>>>(a);

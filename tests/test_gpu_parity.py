@@ -363,22 +363,34 @@ def test_tolerance_stop_matches_oracle():
         assert rel_l2(host(u_d), ref.u) <= 1e-3
 
 
-def test_resume_from_exported_state():
-    w = make("small", seed=10, reg=1, beta=0.5)
+@pytest.mark.parametrize("reg", [0, 1, 2])
+def test_resume_from_exported_state_is_bit_exact(reg):
+    """A run of 40 iterations equals, bit for bit, a run of 25 whose exported state (high
+    and low words of the compensated primal pairs, xbar, y) starts a run of 15."""
+    w = make("small", seed=10, reg=reg, beta=0.5)
     n = w["n"]
     pg = P.Geometry(w["n"], w["det_xy"], w["n_t"], w["r0"], w["dr"], w["quad_m"])
     f = dev(w["f"])
-    nx, ny = 3 * n * n, w["f"].size + 5 * n * n
-    u_full = torch.empty(n, n, device=DEV)
-    P.pat_reconstruct(pg.handle, f, P.make_params(reg=1, alpha=w["alpha"], beta=0.5, iters=40, gap_every=0), u_full)
-    xo, xbo, yo = (torch.empty(k, device=DEV) for k in (nx, nx, ny))
-    u1 = torch.empty(n, n, device=DEV)
-    P.pat_reconstruct(pg.handle, f, P.make_params(reg=1, alpha=w["alpha"], beta=0.5, iters=25, gap_every=0,
-                                                  x_out=xo, xbar_out=xbo, y_out=yo), u1)
-    u2 = torch.empty(n, n, device=DEV)
-    P.pat_reconstruct(pg.handle, f, P.make_params(reg=1, alpha=w["alpha"], beta=0.5, iters=15, gap_every=0,
-                                                  x0=xo, xbar0=xbo, y0=yo), u2)
-    assert rel_l2(host(u2), host(u_full)) <= 1e-5
+    xi = dev(w["xi"]) if reg == 2 else None
+    nx = (3 if reg == 1 else 1) * n * n
+    ny = w["f"].size + (5 if reg == 1 else 2) * n * n
+
+    def run(iters, **kw):
+        out = {k: torch.full((m,), float("nan"), device=DEV) for k, m in
+               (("x", nx), ("xlo", nx), ("xbar", nx), ("y", ny))}
+        u = torch.empty(n, n, device=DEV)
+        P.pat_reconstruct(pg.handle, f, P.make_params(reg=reg, alpha=w["alpha"], beta=0.5, xi=xi, iters=iters,
+                                                      gap_every=0, x_out=out["x"], x_lo_out=out["xlo"],
+                                                      xbar_out=out["xbar"], y_out=out["y"], **kw), u)
+        out["u"] = u
+        return out
+
+    full = run(40)
+    half = run(25)
+    rest = run(15, x0=half["x"], x_lo0=half["xlo"], xbar0=half["xbar"], y0=half["y"])
+    for k in ("u", "x", "xlo", "xbar", "y"):
+        assert torch.equal(rest[k], full[k]), k
+    assert torch.count_nonzero(full["xlo"]) > 0   # the low words carry information
 
 
 def test_zero_iterations_returns_start():
