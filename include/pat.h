@@ -314,6 +314,31 @@ int  pat_geometry_info(const pat_geometry* g, long long* out6_host);
 int  pat_adjoint_worklist(const pat_geometry_desc* desc, int slots, int* rays_host, long long rays_cap,
                           int* items_host, long long items_cap, long long* counts3_host);
 
+/* Host only: the work plan of the forward projector K (Sec. 3.3.1, eq. (K_def)) that
+ * pat_create_geometry builds for `desc`.  Row group rg = d * ceil(T/8) + k/8 holds 8
+ * consecutive radii of one detector.  The image is cut into S horizontal slabs of R rows
+ * of upper tap rows (slab s holds the quadrature points whose upper-left tap row j0 lies
+ * in [s R - 1, (s + 1) R - 1); R = 0 means one slab read from global memory).  K runs as
+ * clusters of S CTAs: rank s stages slab s in shared memory, and a cluster owns a list of
+ * row groups, processed in rounds of 256.  A work unit is one row group restricted to one
+ * slab: at most two circular angular windows.  `sms` is the SM count to plan for (<= 0:
+ * the current device, with its cluster occupancy; with sms > 0 no CUDA call is made).
+ * budget_bytes > 0 caps a slab's staged image (for tests); 0 uses the library's budget.
+ * info8_host = {S, R, shared-memory row stride in floats, units, CTAs, points inside the
+ * units' windows, dynamic shared memory of a CTA in bytes, round offsets}.  When not NULL:
+ *   units_host: 4 ints per unit {detector, window 0, window 1, (k / 8) << 16 | the row
+ *     group's index in its round}; a window is m_first | count << 16, a circular range of
+ *     angles;
+ *   ctas_host: 4 ints per CTA, cluster-major and rank-minor {first entry in rgs, row
+ *     groups of the cluster, first entry in roff, 0};
+ *   roff_host: per CTA, unit offsets of its rounds (rounds + 1 entries);
+ *   rgs_host: every cluster's row groups in processing order.
+ * Capacities are in entries; too small a capacity returns PAT_ERR_INVALID_ARG after
+ * info8_host is written.  The caller owns all buffers. */
+int  pat_forward_plan(const pat_geometry_desc* desc, int budget_bytes, int sms, int* units_host,
+                      long long units_cap, int* ctas_host, long long ctas_cap, int* roff_host,
+                      long long roff_cap, int* rgs_host, long long rgs_cap, long long* info8_host);
+
 #ifdef __cplusplus
 }
 #endif

@@ -37,7 +37,7 @@ EXPORTED = [
     "pat_adjoint_worklist",
     "pat_profile_enable", "pat_profile_read", "pat_kernel_launches", "pat_adjoint_noalloc",
     "pat_tune_step_ratio", "pat_tune_step_ratio_batched", "pat_preprocess", "pat_wavelet_transform",
-    "pat_time_phases",
+    "pat_time_phases", "pat_forward_plan",
     # learned warm start (include/pat_unet.h)
     "pat_conv3x3_forward", "pat_conv3x3_backward_data", "pat_conv3x3_backward_weight",
     "pat_unet_create", "pat_unet_destroy", "pat_unet_num_params", "pat_unet_get_params",
@@ -131,6 +131,9 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pat_geometry_info": (i, [vp, ctypes.POINTER(ctypes.c_longlong)]),
         "pat_adjoint_worklist": (i, [ctypes.POINTER(pat_geometry_desc), i, vp, ctypes.c_longlong, vp,
                                      ctypes.c_longlong, ctypes.POINTER(ctypes.c_longlong)]),
+        "pat_forward_plan": (i, [ctypes.POINTER(pat_geometry_desc), i, i, vp, ctypes.c_longlong, vp,
+                                 ctypes.c_longlong, vp, ctypes.c_longlong, vp, ctypes.c_longlong,
+                                 ctypes.POINTER(ctypes.c_longlong)]),
         "pat_profile_enable": (i, [i]),
         "pat_profile_read": (i, [ctypes.POINTER(d), ctypes.POINTER(ctypes.c_longlong), i]),
         "pat_kernel_launches": (ctypes.c_longlong, []),
@@ -215,6 +218,29 @@ def pat_adjoint_worklist(n: int, det_xy, n_t: int, r0: float, dr: float, quad_m:
     _check(lib.pat_adjoint_worklist(ctypes.byref(desc), slots, rays.ctypes.data, cnt[0], items.ctypes.data, cnt[1],
                                     cnt), "pat_adjoint_worklist")
     return {"rays": rays, "items": items, "candidates": int(cnt[2])}
+
+
+def pat_forward_plan(n: int, det_xy, n_t: int, r0: float, dr: float, quad_m: int, sms: int,
+                     budget_bytes: int = 0, extent=(-1.0, 1.0, -1.0, 1.0)) -> dict:
+    """The K work plan (host only when sms > 0; see include/pat.h): slabs (= CTAs per
+    cluster), rows per slab, shared-memory row stride, units (U x 4), CTAs (C x 4), round
+    offsets, the clusters' row groups, the points inside the windows and the CTA's shared
+    memory."""
+    lib = load()
+    desc, _det = _geometry_desc(n, det_xy, n_t, r0, dr, quad_m, extent)
+    info = (ctypes.c_longlong * 8)()
+    _check(lib.pat_forward_plan(ctypes.byref(desc), budget_bytes, sms, None, 0, None, 0, None, 0, None, 0, info),
+           "pat_forward_plan")
+    U, C, O = int(info[3]), int(info[4]), int(info[7])
+    G = det_xy.shape[0] * ((n_t + 7) // 8)
+    units = np.zeros((U, 4), dtype=np.int32)
+    ctas = np.zeros((C, 4), dtype=np.int32)
+    roff = np.zeros(O, dtype=np.int32)
+    rgs = np.zeros(G, dtype=np.int32)
+    _check(lib.pat_forward_plan(ctypes.byref(desc), budget_bytes, sms, units.ctypes.data, U, ctas.ctypes.data, C,
+                                roff.ctypes.data, O, rgs.ctypes.data, G, info), "pat_forward_plan")
+    return {"slabs": int(info[0]), "rows": int(info[1]), "stride": int(info[2]), "units": units, "ctas": ctas,
+            "roff": roff, "rgs": rgs, "evaluated": int(info[5]), "smem": int(info[6])}
 
 
 def pat_destroy_geometry(g: int) -> None:

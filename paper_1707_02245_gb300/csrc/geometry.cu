@@ -169,6 +169,14 @@ static void free_tables(pat_geometry* g) {
     cudaFree(g->pc.tile_kmax);
     cudaFree(g->adj_rays);
     cudaFree(g->adj_item);
+    cudaFree(g->fwd_units);
+    cudaFree(g->fwd_ctas);
+    cudaFree(g->fwd_roff);
+    cudaFree(g->fwd_rgs);
+    g->fwd_units = nullptr;
+    g->fwd_ctas = nullptr;
+    g->fwd_roff = nullptr;
+    g->fwd_rgs = nullptr;
     g->adj_rays = nullptr;
     g->adj_item = nullptr;
     g->pc.tile_kmax = nullptr;
@@ -223,8 +231,8 @@ static int check_desc(const pat_geometry_desc& d) {
         if (!std::isfinite(d.det_xy_host[i])) return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: non-finite detector");
 
     {
-        // every quadrature point must have |fx|, |fy| < 2^24 (continuous pixel
-        // coordinates), so the kernels convert them to integers without clamping
+        // every quadrature point must have |fx|, |fy| < 2^22 (continuous pixel
+        // coordinates), so the kernels' floors are exact and convert without clamping
         double ext = 0;
         const double rmax = d.r0 + d.n_t * d.dr;
         const double hx0 = (d.xmax - d.xmin) / d.n, hy0 = (d.ymax - d.ymin) / d.n;
@@ -232,8 +240,8 @@ static int check_desc(const pat_geometry_desc& d) {
             ext = std::max(ext, (fabs(d.det_xy_host[2 * i] - d.xmin) + rmax) / hx0 + 1.0);
             ext = std::max(ext, (fabs(d.det_xy_host[2 * i + 1] - d.ymin) + rmax) / hy0 + 1.0);
         }
-        if (!(ext < 16777216.0))
-            return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: circles reach more than 2^24 pixels from the grid");
+        if (!(ext < 4194304.0))
+            return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: circles reach more than 2^22 pixels from the grid");
     }
     return PAT_OK;
 }
@@ -272,6 +280,222 @@ static PointTables point_tables(const pat_geometry_desc& d) {
         pt.wk[k] = (float)(2.0 * M_PI * pt.rd[k] / M);
     }
     return pt;
+}
+
+// Two circular intervals of [0, M) that cover the set entries of mask: the complement of
+// its two longest runs of unset entries.  Each is encoded m_first | count << 16.
+static void cover_two(const unsigned char* mask, int M, unsigned& w0, unsigned& w1) {
+    w0 = w1 = 0u;
+    int first = -1, n_set = 0;
+    for (int m = 0; m < M; ++m)
+        if (mask[m]) {
+            ++n_set;
+            if (first < 0) first = m;
+        }
+    if (n_set == 0) return;
+    if (n_set == M) {
+        w0 = (unsigned)M << 16;
+        return;
+    }
+    // runs of unset entries, in positions relative to `first` (a set entry)
+    struct Run {
+        int start, len;
+    };
+    Run best[2] = {{0, 0}, {0, 0}};
+    int run_start = -1;
+    for (int s = 1; s <= M; ++s) {   // position M is `first` again: it closes a trailing run
+        const bool set = s == M || mask[(first + s) % M] != 0;
+        if (!set) {
+            if (run_start < 0) run_start = s;
+        } else if (run_start >= 0) {
+            const Run r{run_start, s - run_start};
+            if (r.len > best[0].len) {
+                best[1] = best[0];
+                best[0] = r;
+            } else if (r.len > best[1].len) {
+                best[1] = r;
+            }
+            run_start = -1;
+        }
+    }
+    if (best[1].len == 0) {   // one run of unset entries: one window, its complement
+        const int s0 = best[0].start + best[0].len;
+        w0 = (unsigned)((first + s0) % M) | ((unsigned)(M - best[0].len) << 16);
+        return;
+    }
+    Run a = best[0], b = best[1];
+    if (b.start < a.start) std::swap(a, b);
+    const int s1 = a.start + a.len, c1 = b.start - s1;       // from the end of a to b
+    const int s2 = b.start + b.len, c2 = a.start + M - s2;   // from the end of b round to a
+    w0 = (unsigned)((first + s1) % M) | ((unsigned)c1 << 16);
+    w1 = (unsigned)((first + s2) % M) | ((unsigned)c2 << 16);
+}
+
+struct SlabPlan {
+    int slabs = 1, rows = 0, stride = 0, smem = 0;
+    std::vector<int4> units;     // per CTA, round by round: {detector, window 0, window 1, k group << 16 | index}
+    std::vector<int4> ctas;      // per CTA (cluster-major, rank-minor): {first rg entry, row groups, first roff entry, 0}
+    std::vector<int> roff;       // per CTA: unit offsets of its rounds
+    std::vector<int> rgs;        // per cluster: its row groups in processing order
+    std::vector<float> cluster_cost;
+    long long evaluated = 0;
+};
+
+// Slab count S (= CTAs per cluster) and rows R of geometry d: the fewest slabs (at most
+// FWD_MAX_CLUSTER) whose CTA fits two per SM, else one per SM; budget_bytes > 0 instead
+// caps the staged image of a slab (for tests).  R = 0: the global-memory variant.
+static void slab_shape(const pat_geometry_desc& d, int budget_bytes, int& S, int& R, int& W, int& smem) {
+    const int N = d.n, M = d.quad_m, D = d.n_det;
+    W = (N + 6 + 3) / 4 * 4;   // columns -1 .. N + 1 at floats 3 .. N + 5
+    if (W % 8 == 0) W += 4;   // W = 4 mod 8: 8 consecutive rows start in 8 different bank groups
+    const bool staged = M <= FWD_STAGE_MAX && D <= FWD_STAGE_MAX;
+    const int budgets[2] = {FWD_SMEM_TWO, FWD_SMEM_ONE};
+    for (int bi = 0; bi < 2 && staged; ++bi)
+        for (int s = 1; s <= FWD_MAX_CLUSTER; ++s) {
+            const int r = (N + 1 + s - 1) / s;
+            if (r < 8) break;
+            const int need = forward_smem_bytes(r, W, M, D, true);
+            const bool fits = budget_bytes > 0 ? (r + 1) * W * 4 <= budget_bytes && need <= FWD_SMEM_ONE
+                                               : need <= budgets[bi];
+            if (fits) {
+                S = s;
+                R = r;
+                smem = need;
+                return;
+            }
+        }
+    S = 1;
+    R = 0;
+    smem = forward_smem_bytes(0, W, M, D, false);
+}
+
+// The K work plan of geometry d for `n_clusters` clusters.
+//  - Units: one per (row group, slab) with a point that can touch the grid in the slab,
+//    covered by at most two angular windows.  Membership is decided in FP64 on the tables'
+//    exact values with a margin of 1e-3 pixel, far above the FP32 rounding of a point's
+//    position (about 1e-5 pixel), so every point the kernel counts in a slab lies inside
+//    that slab's windows.
+//  - Clusters: row groups dealt longest first onto the cluster whose slowest rank stays
+//    least loaded; each cluster's list is shuffled (a fixed generator) so that every round
+//    mixes detectors from all sides, and cut into rounds of FWD_ROUND.
+static void build_slab_plan(const pat_geometry_desc& d, const PointTables& pt, const std::vector<int2>& win,
+                            int n_clusters, int budget_bytes, SlabPlan& sp) {
+    const int N = d.n, D = d.n_det, T = d.n_t, M = d.quad_m;
+    const int n_kgrp = (T + KGRP - 1) / KGRP, n_rg = D * n_kgrp;
+    const double hx = (d.xmax - d.xmin) / N, hy = (d.ymax - d.ymin) / N;
+    int S, R, W, smem;
+    slab_shape(d, budget_bytes, S, R, W, smem);
+    sp.slabs = S;
+    sp.rows = R;
+    sp.stride = W;
+    sp.smem = smem;
+    n_clusters = std::max(1, std::min(n_clusters, n_rg));
+    const double eps = 1e-3;
+    struct U {
+        unsigned w0, w1;
+        float cost;
+    };
+    // units[rg * S + s] (cost < 0: none)
+    std::vector<U> units((size_t)n_rg * S, U{0u, 0u, -1.f});
+    std::vector<unsigned char> mask((size_t)S * M);
+    std::vector<char> touched(S);
+    for (int di = 0; di < D; ++di) {
+        const double px = (d.det_xy_host[2 * di] - d.xmin) / hx - 0.5;
+        const double py = (d.det_xy_host[2 * di + 1] - d.ymin) / hy - 0.5;
+        for (int gi = 0; gi < n_kgrp; ++gi) {
+            const int rg = di * n_kgrp + gi;
+            const int k0 = gi * KGRP, nk = std::min(T, k0 + KGRP) - k0;
+            const int2 w = win[(size_t)rg];
+            std::fill(touched.begin(), touched.end(), 0);
+            for (int j = 0; j < w.y; ++j) {
+                const int m = (w.x + j) % M;
+                const double cx = pt.cosd[m] / hx, cy = pt.sind[m] / hy;
+                for (int k = k0; k < k0 + nk; ++k) {
+                    const double fx = px + pt.rd[k] * cx, fy = py + pt.rd[k] * cy;
+                    if (!(fx > -1 - eps && fx < N + eps && fy > -1 - eps && fy < N + eps)) continue;
+                    int s_lo = 0, s_hi = 0;
+                    if (R > 0 && S > 1) {
+                        s_lo = std::max(0, (int)std::floor((fy + 1 - eps) / R));
+                        s_hi = std::min(S - 1, (int)std::floor((fy + 1 + eps) / R));
+                    }
+                    for (int s = s_lo; s <= s_hi; ++s) {
+                        if (!touched[s]) {
+                            touched[s] = 1;
+                            std::fill(mask.begin() + (size_t)s * M, mask.begin() + (size_t)(s + 1) * M, 0);
+                        }
+                        mask[(size_t)s * M + m] = 1;
+                    }
+                }
+            }
+            for (int s = 0; s < S; ++s) {
+                if (!touched[s]) continue;
+                U& u = units[(size_t)rg * S + s];
+                cover_two(&mask[(size_t)s * M], M, u.w0, u.w1);
+                const long long pts = (long long)((u.w0 >> 16) + (u.w1 >> 16)) * nk;
+                u.cost = (float)pts + 16.f;   // a unit's fixed work (fetch, phase sum)
+                sp.evaluated += pts;
+            }
+        }
+    }
+    auto cost = [&](int rg, int s) { return std::max(0.f, units[(size_t)rg * S + s].cost); };
+    // row groups to clusters
+    std::vector<double> rg_total(n_rg, 0.0);
+    for (int rg = 0; rg < n_rg; ++rg)
+        for (int s = 0; s < S; ++s) rg_total[rg] += cost(rg, s);
+    std::vector<int> order(n_rg);
+    for (int i = 0; i < n_rg; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return rg_total[x] > rg_total[y]; });
+    std::vector<double> load((size_t)n_clusters * S, 0.0);
+    std::vector<std::vector<int>> members(n_clusters);
+    for (int rg : order) {
+        int best = 0;
+        double best_max = 1e300;
+        for (int c = 0; c < n_clusters; ++c) {
+            double mx = 0.0;
+            for (int s = 0; s < S; ++s) mx = std::max(mx, load[(size_t)c * S + s] + cost(rg, s));
+            if (mx < best_max) {
+                best_max = mx;
+                best = c;
+            }
+        }
+        for (int s = 0; s < S; ++s) load[(size_t)best * S + s] += cost(rg, s) + 1.0;   // + the epilogue
+        members[best].push_back(rg);
+    }
+    unsigned long long lcg = 0x9E3779B97F4A7C15ull;
+    for (int c = 0; c < n_clusters; ++c) {
+        std::vector<int>& mem = members[c];
+        if (mem.empty()) continue;
+        std::sort(mem.begin(), mem.end());
+        for (int i = (int)mem.size() - 1; i > 0; --i) {   // Fisher-Yates with a fixed LCG
+            lcg = lcg * 6364136223846793005ull + 1442695040888963407ull;
+            std::swap(mem[i], mem[(int)((lcg >> 33) % (unsigned long long)(i + 1))]);
+        }
+        const int rg0 = (int)sp.rgs.size();
+        sp.rgs.insert(sp.rgs.end(), mem.begin(), mem.end());
+        const int nrg = (int)mem.size(), n_rounds = (nrg + FWD_ROUND - 1) / FWD_ROUND;
+        double worst = 0.0;
+        for (int s = 0; s < S; ++s) {
+            sp.ctas.push_back(make_int4(rg0, nrg, (int)sp.roff.size(), 0));
+            double tot = 0.0;
+            for (int rd = 0; rd < n_rounds; ++rd) {
+                sp.roff.push_back((int)sp.units.size());
+                std::vector<std::pair<float, int>> lst;   // (cost, index in the round)
+                for (int i = rd * FWD_ROUND; i < std::min(nrg, (rd + 1) * FWD_ROUND); ++i)
+                    if (units[(size_t)mem[i] * S + s].cost >= 0) lst.push_back({units[(size_t)mem[i] * S + s].cost, i});
+                std::stable_sort(lst.begin(), lst.end(), [](const auto& x, const auto& y) { return x.first > y.first; });
+                for (auto& e : lst) {
+                    const int rg = mem[e.second];
+                    const U& u = units[(size_t)rg * S + s];
+                    const int dd = rg / n_kgrp, kg = rg - dd * n_kgrp;
+                    sp.units.push_back(make_int4(dd, (int)u.w0, (int)u.w1, (kg << 16) | (e.second - rd * FWD_ROUND)));
+                    tot += e.first;
+                }
+            }
+            sp.roff.push_back((int)sp.units.size());
+            worst = std::max(worst, tot);
+        }
+        sp.cluster_cost.push_back((float)worst);
+    }
 }
 
 struct AdjWork {
@@ -471,6 +695,45 @@ static int adjoint_worklist(const pat_geometry_desc& d, const PointTables& pt, d
     return PAT_OK;
 }
 
+// Angular windows of every (detector, group of KGRP radii): the smallest circular interval
+// of angles whose points can touch the grid (FP64 with a margin of 1e-3 pixel).  Also
+// counts the points whose taps touch the grid.
+static std::vector<int2> grid_windows(const pat_geometry_desc& d, const PointTables& pt, long long* on_grid_out) {
+    const int N = d.n, D = d.n_det, T = d.n_t, M = d.quad_m;
+    const double hx = (d.xmax - d.xmin) / N, hy = (d.ymax - d.ymin) / N;
+    const int n_kgrp = (T + KGRP - 1) / KGRP;
+    const double ex = 1e-3 * hx, ey = 1e-3 * hy;
+    const double xl = d.xmin - 0.5 * hx - ex, xh = d.xmax + 0.5 * hx + ex;
+    const double yl = d.ymin - 0.5 * hy - ey, yh = d.ymax + 0.5 * hy + ey;
+    const double gxl = d.xmin - 0.5 * hx, gxh = d.xmax + 0.5 * hx, gyl = d.ymin - 0.5 * hy, gyh = d.ymax + 0.5 * hy;
+    std::vector<int2> win((size_t)D * n_kgrp);
+    std::vector<unsigned char> mask(M);
+    long long on_grid = 0;
+    for (int di = 0; di < D; ++di) {
+        const double dx = d.det_xy_host[2 * di], dy = d.det_xy_host[2 * di + 1];
+        for (int gi = 0; gi < n_kgrp; ++gi) {
+            std::fill(mask.begin(), mask.end(), 0);
+            const int k_end = std::min(T, (gi + 1) * KGRP);
+            for (int k = gi * KGRP; k < k_end; ++k) {
+                const double r = pt.rd[k];
+                const double cx = std::min(std::max(dx, xl), xh), cy = std::min(std::max(dy, yl), yh);
+                const double dmin = hypot(dx - cx, dy - cy);
+                const double dmax = std::max(std::max(hypot(dx - xl, dy - yl), hypot(dx - xh, dy - yl)),
+                                             std::max(hypot(dx - xl, dy - yh), hypot(dx - xh, dy - yh)));
+                if (r < dmin - 1e-9 || r > dmax + 1e-9) continue;
+                for (int m = 0; m < M; ++m) {
+                    const double x = dx + r * pt.cosd[m], y = dy + r * pt.sind[m];
+                    if (x > gxl && x < gxh && y > gyl && y < gyh) ++on_grid;
+                    if (!mask[m] && x > xl && x < xh && y > yl && y < yh) mask[m] = 1;
+                }
+            }
+            win[(size_t)di * n_kgrp + gi] = covering_window(mask, M);
+        }
+    }
+    if (on_grid_out) *on_grid_out = on_grid;
+    return win;
+}
+
 extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry** out) {
     if (!desc || !out) return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: NULL argument");
     *out = nullptr;
@@ -496,43 +759,20 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     const std::vector<double>& sind = pt.sind;
     const std::vector<double>& rd = pt.rd;
 
-    // angular windows: a point can touch the grid iff fx, fy in (-1, N), i.e.
-    // x in (xmin - hx/2, xmax + hx/2); the test uses a margin so fp32 rounding in the
-    // kernels never meets a point outside its window that would touch the grid
-    const double ex = 1e-3 * hx, ey = 1e-3 * hy;
-    const double xl = d.xmin - 0.5 * hx - ex, xh = d.xmax + 0.5 * hx + ex;
-    const double yl = d.ymin - 0.5 * hy - ey, yh = d.ymax + 0.5 * hy + ey;
-    std::vector<int2> win((size_t)D * n_kgrp);
-    std::vector<unsigned char> mask(M);
-    long long pts = 0, on_grid = 0;
-    const double gxl = d.xmin - 0.5 * hx, gxh = d.xmax + 0.5 * hx, gyl = d.ymin - 0.5 * hy, gyh = d.ymax + 0.5 * hy;
-    for (int di = 0; di < D; ++di) {
-        const double dx = d.det_xy_host[2 * di], dy = d.det_xy_host[2 * di + 1];
-        for (int gi = 0; gi < n_kgrp; ++gi) {
-            std::fill(mask.begin(), mask.end(), 0);
-            const int k_end = std::min(T, (gi + 1) * KGRP);
-            for (int k = gi * KGRP; k < k_end; ++k) {
-                const double r = rd[k];
-                // quick reject: circle entirely off the extended box
-                const double cx = std::min(std::max(dx, xl), xh), cy = std::min(std::max(dy, yl), yh);
-                const double dmin = hypot(dx - cx, dy - cy);
-                const double dmax = std::max(std::max(hypot(dx - xl, dy - yl), hypot(dx - xh, dy - yl)),
-                                             std::max(hypot(dx - xl, dy - yh), hypot(dx - xh, dy - yh)));
-                if (r < dmin - 1e-9 || r > dmax + 1e-9) continue;
-                for (int m = 0; m < M; ++m) {
-                    const double x = dx + r * cosd[m], y = dy + r * sind[m];
-                    if (x > gxl && x < gxh && y > gyl && y < gyh) ++on_grid;  // touches the grid
-                    if (!mask[m] && x > xl && x < xh && y > yl && y < yh) mask[m] = 1;
-                }
-            }
-            int2 w = covering_window(mask, M);
-            win[(size_t)di * n_kgrp + gi] = w;
-            pts += (long long)w.y * (k_end - gi * KGRP);
-        }
-    }
-    g->points_per_apply = pts;
+    // angular windows of every (detector, radius group) over the grid
+    long long on_grid = 0;
+    const std::vector<int2> win = grid_windows(d, pt, &on_grid);
     g->points_on_grid = on_grid;
-    g->fwd_block_cost = forward_block_costs(d, win);
+    SlabPlan sp;
+    {
+        int S, R, W, smem;
+        slab_shape(d, 0, S, R, W, smem);
+        build_slab_plan(d, pt, win, forward_clusters_per_gpu(S, smem), 0, sp);
+    }
+    g->points_per_apply = sp.evaluated;
+    g->fwd_evaluated = sp.evaluated;
+    g->fwd_cluster_cost = sp.cluster_cost;
+    g->fwd_n_ctas = (int)sp.ctas.size();
 
     AdjWork aw;
     {
@@ -557,6 +797,14 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     if (e == cudaSuccess) e = cudaMalloc(&g->rk, sizeof(float) * T);
     if (e == cudaSuccess) e = cudaMalloc(&g->wk, sizeof(float) * T);
     if (e == cudaSuccess) e = cudaMalloc(&g->win, sizeof(int2) * win.size());
+    auto upload = [&](void** dst, const void* src, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+        if (e == cudaSuccess && bytes) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    upload((void**)&g->fwd_units, sp.units.data(), sizeof(int4) * sp.units.size());
+    upload((void**)&g->fwd_ctas, sp.ctas.data(), sizeof(int4) * sp.ctas.size());
+    upload((void**)&g->fwd_roff, sp.roff.data(), sizeof(int) * sp.roff.size());
+    upload((void**)&g->fwd_rgs, sp.rgs.data(), sizeof(int) * sp.rgs.size());
     if (e == cudaSuccess) e = cudaMalloc(&g->adj_rays, sizeof(int4) * rays.size());
     if (e == cudaSuccess) e = cudaMemcpy(g->adj_rays, rays.data(), sizeof(int4) * rays.size(), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMalloc(&g->adj_item, sizeof(AdjItem) * items.size());
@@ -587,7 +835,60 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     v.dr_f = (float)d.dr;
     v.rh_f = (float)(d.r0 + 0.5 * d.dr);
     v.win = g->win;
+    v.n_slabs = sp.slabs;
+    v.slab_rows = sp.rows;
+    v.slab_stride = sp.stride;
+    v.smem_bytes = sp.smem;
+    v.units = g->fwd_units;
+    v.ctas = g->fwd_ctas;
+    v.roff = g->fwd_roff;
+    v.rgs = g->fwd_rgs;
+    g->fwd_smem = sp.smem;
     *out = g;
+    return PAT_OK;
+}
+
+extern "C" int pat_forward_plan(const pat_geometry_desc* desc, int budget_bytes, int sms, int* units_host,
+                                long long units_cap, int* ctas_host, long long ctas_cap, int* roff_host,
+                                long long roff_cap, int* rgs_host, long long rgs_cap, long long* info8_host) {
+    if (!desc || !info8_host) return fail(PAT_ERR_INVALID_ARG, "pat_forward_plan: NULL argument");
+    const int vrc = check_desc(*desc);
+    if (vrc) return vrc;
+    if (budget_bytes < 0 || budget_bytes > FWD_SMEM_ONE)
+        return fail(PAT_ERR_INVALID_ARG, "pat_forward_plan: budget exceeds the K CTA's shared memory");
+    int S, R, W, smem;
+    slab_shape(*desc, budget_bytes, S, R, W, smem);
+    const int clusters = sms > 0 ? std::max(1, sms * (smem <= FWD_SMEM_TWO ? 2 : 1) / S)
+                                 : forward_clusters_per_gpu(S, smem);
+    const PointTables pt = point_tables(*desc);
+    const std::vector<int2> win = grid_windows(*desc, pt, nullptr);
+    SlabPlan sp;
+    build_slab_plan(*desc, pt, win, clusters, budget_bytes, sp);
+    info8_host[0] = sp.slabs;
+    info8_host[1] = sp.rows;
+    info8_host[2] = sp.stride;
+    info8_host[3] = (long long)sp.units.size();
+    info8_host[4] = (long long)sp.ctas.size();
+    info8_host[5] = sp.evaluated;
+    info8_host[6] = sp.smem;
+    info8_host[7] = (long long)sp.roff.size();
+    if ((units_host && units_cap < info8_host[3]) || (ctas_host && ctas_cap < info8_host[4]) ||
+        (roff_host && roff_cap < info8_host[7]) || (rgs_host && rgs_cap < (long long)sp.rgs.size()))
+        return fail(PAT_ERR_INVALID_ARG, "pat_forward_plan: output capacity too small");
+    for (size_t i = 0; units_host && i < sp.units.size(); ++i) {
+        units_host[4 * i] = sp.units[i].x;
+        units_host[4 * i + 1] = sp.units[i].y;
+        units_host[4 * i + 2] = sp.units[i].z;
+        units_host[4 * i + 3] = sp.units[i].w;
+    }
+    for (size_t i = 0; ctas_host && i < sp.ctas.size(); ++i) {
+        ctas_host[4 * i] = sp.ctas[i].x;
+        ctas_host[4 * i + 1] = sp.ctas[i].y;
+        ctas_host[4 * i + 2] = sp.ctas[i].z;
+        ctas_host[4 * i + 3] = sp.ctas[i].w;
+    }
+    for (size_t i = 0; roff_host && i < sp.roff.size(); ++i) roff_host[i] = sp.roff[i];
+    for (size_t i = 0; rgs_host && i < sp.rgs.size(); ++i) rgs_host[i] = sp.rgs[i];
     return PAT_OK;
 }
 

@@ -52,6 +52,16 @@ void prof_collect();
 //                                    and  cs = (cos(phi_m)/hx, sin(phi_m)/hy)   (from FP64)
 // so pixel (i, j) has its centre at fx = i, fy = j.  Taps i0 = floor(fx), i0 + 1 with
 // weights 1 - ax, ax (ax = fx - i0); same in y.
+// K works on row groups: KGRP consecutive radii of one detector (row group rg = d *
+// n_kgrp + k / KGRP).  The image is cut into S horizontal slabs of R rows of upper tap
+// rows j0 (slab s holds the points with j0 in [s R - 1, (s + 1) R - 1)).  K runs as
+// clusters of S CTAs: CTA rank s stages slab s in shared memory once, and the cluster owns
+// a list of row groups, processed in rounds of at most FWD_ROUND row groups.  In a round,
+// each CTA evaluates its slab's work units (one row group restricted to one slab: at most
+// two circular angular windows) into its shared accumulators; after a cluster barrier the
+// rows' S partial sums are added in rank order through distributed shared memory and the
+// epilogue runs.  slab_rows = 0 marks the global-memory variant (S = 1, no staging) used
+// when the image does not fit a cluster of at most 8 CTAs.
 struct GeomView {
     int n, n_det, n_t, quad_m;
     int n_kgrp;          // k groups of KGRP consecutive radii per detector
@@ -61,6 +71,16 @@ struct GeomView {
     const float* wk;     // T arc weights 2 pi r_k / M
     const int2* win;     // D * n_kgrp angular windows {m_first, m_count} (circular)
     float dr_f, rh_f;    // FP32 radius step dr and first radius r0 + dr/2
+    int n_slabs;         // S >= 1: slabs, and CTAs per cluster
+    int slab_rows;       // R (0: global-memory variant)
+    int slab_stride;     // shared-memory row stride in floats (W = 4 mod 8, >= N + 6)
+    int smem_bytes;      // dynamic shared memory of a K CTA of this plan
+    // units {detector, window 0, window 1, (k group << 16) | row group's index in its
+    // round}; a window is m_first | count << 16.  A CTA's units are stored round by round.
+    const int4* units;
+    const int4* ctas;    // per K CTA (cluster-major, rank-minor): {first entry in rgs, row groups, first entry in roff, 0}
+    const int* roff;     // per CTA: unit offsets of its rounds (rounds + 1 entries)
+    const int* rgs;      // per cluster: its row groups in processing order
 };
 
 // Radius r_k = r0 + (k + 1/2) dr in FP32, as one correctly rounded fused multiply-add of
@@ -71,6 +91,12 @@ __host__ __device__ __forceinline__ float radius(int k, float dr_f, float rh_f) 
 }
 
 constexpr int KGRP = 8;        // radii per angular-window group
+constexpr int SLAB_THREADS = 512;                // threads of a K CTA
+constexpr int FWD_SMEM_TWO = 112 * 1024;         // dynamic shared memory of a K CTA, two per SM
+constexpr int FWD_SMEM_ONE = 220 * 1024;         // ... one per SM
+constexpr int FWD_MAX_CLUSTER = 8;               // portable cluster size
+constexpr int FWD_ROUND = 256;                   // row groups of a cluster per round
+constexpr int FWD_STAGE_MAX = 1024;              // slabs need the cs and det tables staged: M, D <= this
 constexpr int MAX_QUAD_M = 8192;
 constexpr int ATILE = 32;      // side of the pixel tiles that share one K^T fixed-point scale
 constexpr int WTILE = 32;      // side of the pixel tiles one K^T work item accumulates
@@ -114,7 +140,13 @@ struct pat_geometry {
     int adj_wtiles_x = 0;              // work tiles (WTILE) per row
     long long adj_candidates = 0;     // candidate points of one K^T application
     std::vector<float> adj_item_cost;  // estimated cost per work item (host)
-    std::vector<float> fwd_block_cost; // angular steps of each row block of K (host)
+    int4* fwd_units = nullptr;         // K work units (see GeomView)
+    int4* fwd_ctas = nullptr;          // K CTAs
+    int* fwd_roff = nullptr;           // per CTA: unit offsets of its rounds
+    int* fwd_rgs = nullptr;            // per cluster: its row groups
+    int fwd_n_ctas = 0, fwd_smem = 0;  // K CTAs of one application (clusters x S); dynamic shared memory
+    long long fwd_evaluated = 0;       // quadrature points inside the units' windows
+    std::vector<float> fwd_cluster_cost; // points each K cluster's slowest CTA evaluates (host)
     std::vector<double> det_xy;        // detector positions (host copy, 2 per detector)
     pat::GeomView view;
     // lazily computed preconditioner sums
@@ -127,29 +159,6 @@ namespace pat {
 // ---------------------------------------------------------------------------------
 // shared device helpers
 // ---------------------------------------------------------------------------------
-// K reads the image as quads: quad (x, y), x, y in [0, N], holds the pixels (x-1, y-1),
-// (x, y-1), (x-1, y), (x, y) (zero off the grid), so a point with upper-left tap (i0, j0)
-// reads quad (i0 + 1, j0 + 1) in one 16-byte load.  The quads are stored row by row;
-// PAT_QUAD_BLOCKED 1 stores them in blocks of 4 (x) by 2 (y), one 128-byte line each,
-// which measured slower for K (38.9 us against 31.6 us at 256^2).
-#ifndef PAT_QUAD_BLOCKED
-#define PAT_QUAD_BLOCKED 0
-#endif
-// 32-bit arithmetic: geometry creation bounds N by 16384, so every index is below 2^31
-// (64-bit index math cost K's gap kernel two registers and a third of its occupancy)
-__host__ __device__ __forceinline__ int quad_index(int x, int y, int N) {
-#if PAT_QUAD_BLOCKED
-    const int nbx = (N + 4) >> 2;  // blocks per row of quads: ceil((N + 1) / 4)
-    return ((y >> 1) * nbx + (x >> 2)) * 8 + ((y & 1) << 2) + (x & 3);
-#else
-    return y * (N + 1) + x;
-#endif
-}
-// quads to allocate (the blocked layout pads the grid of quads to whole blocks)
-__host__ __device__ __forceinline__ size_t quad_count(int N) {
-    return (size_t)((N + 4) >> 2) * 8 * (size_t)((N + 2) >> 1);
-}
-
 struct Taps {
     int i0, j0;
     float ax, ay;
@@ -165,7 +174,7 @@ __device__ __forceinline__ bool point_taps(const GeomView& g, float2 det, float 
     const float fly = floorf(fy);
     t.ax = fx - flx;
     t.ay = fy - fly;
-    // geometry creation bounds |fx|, |fy| by 2^24, so the conversions are exact
+    // geometry creation bounds |fx|, |fy| by 2^22, so the conversions are exact
     t.i0 = (int)flx;
     t.j0 = (int)fly;
     return (unsigned)(t.i0 + 1) <= (unsigned)g.n && (unsigned)(t.j0 + 1) <= (unsigned)g.n;
@@ -188,16 +197,23 @@ struct KtView {
     }
 };
 
+// Exact floor of x and its integer for |x| < 2^22, on the FMA and integer pipes (no
+// conversion instructions): t = x + 1.5 * 2^23 rounded down lies in [2^23, 2^24), where the
+// spacing of floats is 1, so t = floor(x) + 1.5 * 2^23 exactly; then floor(x) = t - 1.5 *
+// 2^23 (exact) and its integer is the low bits of t.  Geometry creation bounds the
+// continuous pixel coordinates of every quadrature point by 2^22.
+constexpr float FLOOR_MAGIC = 12582912.0f;   // 1.5 * 2^23, bits 0x4B400000
+constexpr int FLOOR_MAGIC_BITS = 0x4B400000;
+
 // Taps of a point without the grid test (callers that test a tile window instead).
 __device__ __forceinline__ void point_coords(const GeomView& g, float2 det, float r, float2 cs, Taps& t) {
     const float fx = fmaf(r, cs.x, det.x);
     const float fy = fmaf(r, cs.y, det.y);
-    const float flx = floorf(fx);
-    const float fly = floorf(fy);
-    t.ax = fx - flx;
-    t.ay = fy - fly;
-    t.i0 = (int)flx;
-    t.j0 = (int)fly;
+    const float tx = __fadd_rd(fx, FLOOR_MAGIC), ty = __fadd_rd(fy, FLOOR_MAGIC);
+    t.ax = fx - (tx - FLOOR_MAGIC);
+    t.ay = fy - (ty - FLOOR_MAGIC);
+    t.i0 = __float_as_int(tx) - FLOOR_MAGIC_BITS;
+    t.j0 = __float_as_int(ty) - FLOOR_MAGIC_BITS;
 }
 
 // Launch helpers
@@ -221,28 +237,25 @@ __device__ __forceinline__ const T& stage_args(const T* __restrict__ args, int p
 // per-problem kernel arguments of the batched launches: a launch covers several problems,
 // block b of the launch works on problem map[b].x, local block map[b].y
 // ---------------------------------------------------------------------------------
-struct FwdProxArgs {   // q <- prox(q + Sigma_q K ubar); also q*w and max|q|
+// K applied to an N*N image for every row group of one problem, with one of three
+// epilogues on the finished rows: FWD_Y writes y = K img; FWD_PROX performs the data prox
+// q <- (q + sigma (K ubar - f)) / (1 + sigma) and records q w_k and max |q| for the K^T
+// that follows; FWD_GAP writes the per-row-group sums of the gap's data terms.
+enum { FWD_Y = 0, FWD_PROX = 1, FWD_GAP = 2 };
+constexpr int GAP_DATA_TERMS = 4;   // per-row-group sums of the data pass: |Ku-f|^2, |q|^2, <q,f>, |q-(Ku-f)|_1
+
+struct FwdArgs {
     GeomView g;
-    const float4* ubar_quad;
-    float* q;
+    const float* img;      // N*N row-major image (ubar, or u for the gap)
+    float* y;              // FWD_Y: D*T
+    float* q;              // FWD_PROX, FWD_GAP
     const float* f;
-    const float* sig_q;   // NULL: sig_scalar
+    const float* sig_q;    // NULL: sig_scalar
     float sig_scalar;
     const float* step_mul; // {tau multiplier s, sigma multiplier 1/s} (device) or NULL
     float* qw;
     unsigned* qmax_bits;
-    const int* stop;
-};
-
-constexpr int GAP_DATA_TERMS = 4;   // per-block sums of the data pass: |Ku-f|^2, |q|^2, <q,f>, |q-(Ku-f)|_1
-
-struct FwdGapArgs {    // FP64 partial sums of 1/2|Ku - f|^2, |q|^2, <q, f> per block
-    GeomView g;
-    const float* u;         // plain N*N image (u_quad NULL) ...
-    const float4* u_quad;   // ... or its quads
-    const float* q;
-    const float* f;
-    double* partials;
+    double* partials;      // FWD_GAP: one GAP_DATA_TERMS block of sums per K CTA
     const int* stop;
 };
 
@@ -260,23 +273,21 @@ struct AdjArgs {       // fixed-point K^T y, one work item per block
     const int* stop;
 };
 
-FwdProxArgs make_fwd_prox_args(const pat_geometry* g, const float4* ubar_quad, float* q, const float* f,
-                               const float* sig_q, float sig_scalar, const float* step_mul, float* qw,
-                               unsigned* qmax_bits, const int* stop);
-FwdGapArgs make_fwd_gap_args(const pat_geometry* g, const float* u, const float4* u_quad, const float* q,
-                             const float* f, double* partials, const int* stop);
+FwdArgs make_fwd_args(const pat_geometry* g, const float* img);
 AdjArgs make_adj_args(const pat_geometry* g, const float* y, const float* premul, const unsigned* ymax_bits, int* acc,
                       const int* stop);
 // batched launches over maps of (problem, local block); args are device arrays by problem
-int launch_forward_prox_b(const FwdProxArgs* args, const int2* map, int nblocks, cudaStream_t st);
-int launch_forward_gap_b(const FwdGapArgs* args, const int2* map, int nblocks, cudaStream_t st);
+// K launch over a map of (problem, CTA) pairs: cluster-major, the S ranks of a cluster
+// consecutive; every problem of one launch has the same S (cluster size).  smem: dynamic
+// shared memory of the launch (the largest plan of its problems).
+int launch_forward_b(int epi, const FwdArgs* args, const int2* map, int nblocks, int cluster, int smem,
+                     cudaStream_t st);
+int forward_smem_bytes(int rows, int stride, int M, int D, bool staged);
+int forward_clusters_per_gpu(int cluster, int smem);   // K clusters the GPU holds at once
 int launch_adjoint_b(const AdjArgs* args, const int2* map, int nblocks, bool premul, cudaStream_t st);
 // CTAs of the K^T kernel that one SM holds at once (sizes the work items)
 int adjoint_blocks_per_sm();
-int forward_row_blocks(const pat_geometry* g);    // blocks of one forward launch
-// Work of each row block of K (local block index as the kernels decode it): the angular
-// steps of its warps, from the host copy of the angular windows (D x n_kgrp)
-std::vector<float> forward_block_costs(const pat_geometry_desc& d, const std::vector<int2>& win);
+
 
 // Host entry points implemented in projector.cu and used by pdhg.cu
 // ---- the wavelet model (wavelet.cu) ----
@@ -290,7 +301,6 @@ struct WavPrimalArgs {   // u <- u - T (K^T q + W^T r) / s, ubar, and the next p
     float* u;
     float* u_old;        // NULL, or receives u before the step (gap iterations)
     float* ubar;         // plain N*N
-    float* ubar_pad;     // (N+2)^2, border zero
     int* kt_clear;
     unsigned* qmax_next;
     const int* stop;
@@ -318,7 +328,8 @@ int launch_wav_gap_pixels(const WavGapArgs& a, int nblocks, cudaStream_t st);
 int launch_wav_tau(const float* kcol, const double* wcol, float* tau, long long nn, cudaStream_t st);
 
 int ensure_precond(const pat_geometry* g, cudaStream_t st);
-int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y, cudaStream_t st);
+// y = K u for a plain N*N image (allocates its scratch from the stream-ordered pool)
+int launch_forward(const pat_geometry* g, const float* u, float* y, cudaStream_t st);
 // K^T y into an N*N float image (allocates its scratch from the stream-ordered pool).
 int launch_adjoint(const pat_geometry* g, const float* y, float* out, cudaStream_t st);
 KtView kt_view(const pat_geometry* g, const int* acc, const unsigned* ymax_bits);

@@ -53,8 +53,7 @@ struct UpdateArgs {
     float* x_out;
     float* xl_out;
     float* y_out;
-    float4* ubar_quad;     // (N+1)^2 quads of ubar for the projector (layout quad_index)
-    float4* u_quad;        // quads of u^{n+1} for the gap's K u (NULL: not a gap iteration)
+    float* ubar;           // N*N: ubar for the next K
     const int* stop;
     int* iter;             // iteration counter (incremented once per launch)
     int tiles_x;           // tiles per row of the grid
@@ -74,7 +73,6 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
 
     __shared__ float s_r1m[LY][LX], s_r2m[LY][LX];   // r (dTV: D_xi r) masked for div
     __shared__ float s_ub[LY][LX];                   // ubar on U = tile + high halo
-    __shared__ float s_uU[LY][LX];                   // u^{n+1} on U (for the gap's quads)
     __shared__ float s_un[TY][TX], s_unl[TY][TX];    // u^{n+1} (high, low) on the tile
     // TGV only (small arrays for TV / dTV)
     constexpr int VL = (REG == PAT_TGV) ? LY : 1;
@@ -157,13 +155,11 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
                 float un = uo, unl = uol;
                 add_compensated(un, unl, -tu * (w - divr));
                 ub = fmaf(a.theta, (un - uo) + (unl - uol), un + unl);
-                s_uU[ly][lx] = un;
                 if (lx <= TX && ly <= TY) {
                     s_un[ly - 1][lx - 1] = un;
                     s_unl[ly - 1][lx - 1] = unl;
                 }
             }
-            if (!in) s_uU[ly][lx] = 0.f;
             s_ub[ly][lx] = ub;
         }
         if (REG == PAT_TGV && lx <= TX && ly <= TY) {  // V: v^{n+1}, vbar
@@ -231,22 +227,7 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
         a.y_out[NN + gi] = r2;
         a.x_out[gi] = s_un[threadIdx.y][threadIdx.x];
         a.xl_out[gi] = s_unl[threadIdx.y][threadIdx.x];
-        // quads with the upper-left tap at (gx, gy), and the grid's low border quads (the
-        // quads are the only copy of ubar; the bordered image is filled at the start only)
-        {
-            const float bx = s_ub[ly][lx + 1], by_ = s_ub[ly + 1][lx], bxy = s_ub[ly + 1][lx + 1];
-            a.ubar_quad[quad_index(gx + 1, gy + 1, N)] = make_float4(ub, bx, by_, bxy);
-            if (gx == 0) a.ubar_quad[quad_index(0, gy + 1, N)] = make_float4(0.f, ub, 0.f, by_);
-            if (gy == 0) a.ubar_quad[quad_index(gx + 1, 0, N)] = make_float4(0.f, 0.f, ub, bx);
-            if (gx == 0 && gy == 0) a.ubar_quad[quad_index(0, 0, N)] = make_float4(0.f, 0.f, 0.f, ub);
-            if (a.u_quad) {
-                const float uu = s_uU[ly][lx], ux = s_uU[ly][lx + 1], uy = s_uU[ly + 1][lx], uxy = s_uU[ly + 1][lx + 1];
-                a.u_quad[quad_index(gx + 1, gy + 1, N)] = make_float4(uu, ux, uy, uxy);
-                if (gx == 0) a.u_quad[quad_index(0, gy + 1, N)] = make_float4(0.f, uu, 0.f, uy);
-                if (gy == 0) a.u_quad[quad_index(gx + 1, 0, N)] = make_float4(0.f, 0.f, uu, ux);
-                if (gx == 0 && gy == 0) a.u_quad[quad_index(0, 0, N)] = make_float4(0.f, 0.f, 0.f, uu);
-            }
-        }
+        a.ubar[gi] = ub;
         if (REG == PAT_TGV) {
             // E vbar with d^- on the masked field
             const bool axm = gx >= 1, bym = gy >= 1;
@@ -294,7 +275,7 @@ struct DualArgs {
     float smul;            // dual step multiplier 1/s
     const float* sig_r;
     const float* xi;
-    const float* ubar_pad;
+    const float* ubar;     // N*N
     const float* vbar;     // 2*N*N (TGV)
     const float* y_in;
     float* y_out;
@@ -307,11 +288,10 @@ __global__ void k_dual_step(DualArgs a) {
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
     if (gx >= N || gy >= N) return;
     const int gi = gy * N + gx;
-    const int P = N + 2;
     const bool ax = gx < N - 1, by = gy < N - 1;
-    const float ub = a.ubar_pad[(gy + 1) * P + gx + 1];
-    const float gu0 = ax ? a.ubar_pad[(gy + 1) * P + gx + 2] - ub : 0.f;
-    const float gu1 = by ? a.ubar_pad[(gy + 2) * P + gx + 1] - ub : 0.f;
+    const float ub = a.ubar[gi];
+    const float gu0 = ax ? a.ubar[gi + 1] - ub : 0.f;
+    const float gu1 = by ? a.ubar[gi + N] - ub : 0.f;
     float r1 = a.y_in[gi], r2 = a.y_in[NN + gi];
     if (REG == PAT_TV) {
         const float sr = (a.sig2 >= 0.f ? a.sig2 : sig_r_tv(gx, gy, N)) * a.smul;
@@ -677,27 +657,10 @@ __global__ void k_sig_q(const float* __restrict__ krow, float* __restrict__ sig_
     }
 }
 
-__global__ void k_pad(const float* __restrict__ u, float* __restrict__ pad, int N) {
-    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
-    const int P = N + 2;
-    if (gx >= P || gy >= P) return;
-    const int x = gx - 1, y = gy - 1;
-    pad[gy * P + gx] = (x >= 0 && x < N && y >= 0 && y < N && u) ? u[y * N + x] : 0.f;
-}
-
-// quads of a zero-bordered image: quad (i+1, j+1) = taps (i..i+1, j..j+1), i, j >= -1
-__global__ void k_quads_from_pad(const float* __restrict__ pad, float4* __restrict__ quad, int N) {
-    const int qx = blockIdx.x * blockDim.x + threadIdx.x, qy = blockIdx.y * blockDim.y + threadIdx.y;
-    if (qx > N || qy > N) return;
-    const int P = N + 2;  // pad index of pixel (i, j) is (j+1) P + i+1; quad (qx, qy) has i0 = qx-1
-    quad[quad_index(qx, qy, N)] = make_float4(pad[qy * P + qx], pad[qy * P + qx + 1], pad[(qy + 1) * P + qx],
-                                                  pad[(qy + 1) * P + qx + 1]);
-}
-
-__global__ void k_unpad(const float* __restrict__ pad, float* __restrict__ u, int N) {
-    const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
-    if (gx >= N || gy >= N) return;
-    u[gy * N + gx] = pad[(gy + 1) * (N + 2) + gx + 1];
+// dst = src (N*N), or zero when src is NULL
+__global__ void k_copy_or_zero(const float* __restrict__ src, float* __restrict__ dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src ? src[i] : 0.f;
 }
 
 // Copies the final state out of the ping-pong buffers selected by the iteration count.
@@ -709,7 +672,7 @@ struct OutArgs {
     const float* XL[2];   // low words of the compensated primal pairs
     const float* Y[2];
     const float* q;
-    const float4* ubar_quad;
+    const float* ubar;
     const InfoDev* info;
     float* u_out;
     float* x_out;
@@ -737,8 +700,7 @@ __global__ void k_output(OutArgs a) {
             if (a.x_lo_out) a.x_lo_out[i] = xl[i];
             if (a.xbar_out) {
                 if (i < NN) {
-                    const int gx = (int)(i % N), gy = (int)(i / N);
-                    a.xbar_out[i] = a.ubar_quad[quad_index(gx + 1, gy + 1, N)].x;
+                    a.xbar_out[i] = a.ubar[i];
                 } else {
                     // vbar^I = v^I + theta (v^I - v^{I-1}) from the compensated pairs, the
                     // same expression as the update kernel's; with I = 0 the warm-start
@@ -768,9 +730,7 @@ struct Workspace {
     float* X[2] = {nullptr, nullptr};
     float* XL[2] = {nullptr, nullptr};   // low parts of the compensated primal pairs
     float* Y[2] = {nullptr, nullptr};
-    float *q = nullptr, *ubar_pad = nullptr, *vbar0 = nullptr;
-    float4* ubar_quad = nullptr;
-    float4* u_quad = nullptr;   // quads of u on gap iterations
+    float *q = nullptr, *ubar = nullptr, *vbar0 = nullptr;
     int* kt[2] = {nullptr, nullptr};   // fixed-point K^T q, by iteration parity
     float *tau_u = nullptr, *sig_q = nullptr, *sig_r = nullptr, *qw = nullptr;
     double *data_part = nullptr, *pix_part = nullptr;
@@ -783,16 +743,15 @@ static int pix_blocks(int N) { return std::min(4 * sm_count(), ceil_div((long lo
 static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaStream_t st) {
     const size_t N = g->desc.n, NN = N * N, S = (size_t)g->desc.n_det * g->desc.n_t;
     const size_t nx = NN * (reg == PAT_TGV ? 3 : 1), ny = NN * (reg == PAT_TGV ? 5 : 2);
-    const size_t P2 = (N + 2) * (N + 2);
-    ws.n_data = forward_row_blocks(g);
+    ws.n_data = g->fwd_n_ctas;   // one block of data-term sums per K CTA
     ws.n_pix = pix_blocks((int)N);
-    size_t off[19];
-    size_t sz[19] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, P2 * 4, NN * 4 * 2,
+    size_t off[17];
+    size_t sz[17] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, NN * 4, NN * 4 * 2,
                      (reg == PAT_TGV ? 2 * NN : 1) * 4,
                      NN * 4, S * 4, NN * 4, (size_t)ws.n_data * GAP_DATA_TERMS * 8, (size_t)ws.n_pix * GAP_PIX_TERMS * 8, sizeof(InfoDev),
-                     S * 4, nx * 4, nx * 4, quad_count((int)N) * 16, quad_count((int)N) * 16};
+                     S * 4, nx * 4, nx * 4};
     size_t total = 0;
-    for (int i = 0; i < 19; ++i) {
+    for (int i = 0; i < 17; ++i) {
         off[i] = total;
         total += align_up(sz[i]);
     }
@@ -804,7 +763,7 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     ws.Y[0] = (float*)(b + off[2]);
     ws.Y[1] = (float*)(b + off[3]);
     ws.q = (float*)(b + off[4]);
-    ws.ubar_pad = (float*)(b + off[5]);
+    ws.ubar = (float*)(b + off[5]);
     ws.kt[0] = (int*)(b + off[6]);
     ws.kt[1] = ws.kt[0] + NN;
     ws.vbar0 = (float*)(b + off[7]);
@@ -817,8 +776,6 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     ws.qw = (float*)(b + off[14]);
     ws.XL[0] = (float*)(b + off[15]);
     ws.XL[1] = (float*)(b + off[16]);
-    ws.ubar_quad = (float4*)(b + off[17]);
-    ws.u_quad = (float4*)(b + off[18]);
     return PAT_OK;
 }
 
@@ -910,41 +867,67 @@ struct Arena {
     }
 };
 
+// K launches of a batch: problems with the same cluster size (slabs) share a launch
+struct FwdGroup {
+    int cluster = 1, smem = 0, n = 0;   // CTAs per cluster, dynamic shared memory, CTAs
+    size_t map = 0;                     // (problem, CTA) pairs, cluster-major, rank-minor
+};
+
 struct GapPlan {
-    size_t map_fwd = 0, map_fin = 0;
+    FwdGroup fwd[FWD_MAX_CLUSTER];
+    int n_fwd_groups = 0;
+    size_t map_fin = 0;
     size_t map_pix[3] = {0, 0, 0};
-    int n_fwd = 0, n_fin = 0;
+    int n_fin = 0;
     int n_pix[3] = {0, 0, 0};
 };
 
-// (problem, row block) pairs of a batch's K launch, longest first: the blocks' angular
-// work differs several-fold, and the launch spans a few waves of resident blocks, so the
-// order sets the length of the last wave (each block's rows do not depend on it)
-static std::vector<int2> forward_block_map(const Prob* pr, int B) {
-    std::vector<std::pair<float, int2>> v;
-    for (int b = 0; b < B; ++b) {
-        const pat_geometry* g = pr[b].g;
-        const int nf = forward_row_blocks(g);
-        for (int i = 0; i < nf; ++i)
-            v.push_back({i < (int)g->fwd_block_cost.size() ? g->fwd_block_cost[i] : 0.f, make_int2(b, i)});
+// The K launch groups of a batch.  In each, clusters run longest first: their work differs
+// and a launch may span several waves, so the order sets the length of the last wave (each
+// cluster's rows do not depend on it).
+static void forward_groups(const Prob* pr, int B, Arena& ar, GapPlan& gp) {
+    gp.n_fwd_groups = 0;
+    for (int S = 1; S <= FWD_MAX_CLUSTER; ++S) {
+        std::vector<std::pair<float, int2>> v;   // (cost, (problem, cluster))
+        int smem = 0;
+        for (int b = 0; b < B; ++b) {
+            const pat_geometry* g = pr[b].g;
+            if (g->view.n_slabs != S) continue;
+            smem = std::max(smem, g->fwd_smem);
+            for (int c = 0; c < (int)g->fwd_cluster_cost.size(); ++c) v.push_back({g->fwd_cluster_cost[c], make_int2(b, c)});
+        }
+        if (v.empty()) continue;
+        std::stable_sort(v.begin(), v.end(), [](const std::pair<float, int2>& x, const std::pair<float, int2>& y) {
+            return x.first > y.first;
+        });
+        std::vector<int2> m;
+        m.reserve(v.size() * S);
+        for (auto& e : v)
+            for (int r = 0; r < S; ++r) m.push_back(make_int2(e.second.x, e.second.y * S + r));
+        FwdGroup& grp = gp.fwd[gp.n_fwd_groups++];
+        grp.cluster = S;
+        grp.smem = smem;
+        grp.n = (int)m.size();
+        grp.map = ar.put(m.data(), m.size());
     }
-    std::stable_sort(v.begin(), v.end(), [](const std::pair<float, int2>& x, const std::pair<float, int2>& y) {
-        return x.first > y.first;
-    });
-    std::vector<int2> m;
-    m.reserve(v.size());
-    for (auto& e : v) m.push_back(e.second);
-    return m;
+}
+
+static int launch_forward_groups(int epi, const FwdArgs* args, const GapPlan& gp, const char* base, cudaStream_t st) {
+    for (int i = 0; i < gp.n_fwd_groups; ++i) {
+        const FwdGroup& grp = gp.fwd[i];
+        const int rc = launch_forward_b(epi, args, (const int2*)(base + grp.map), grp.n, grp.cluster, grp.smem, st);
+        if (rc) return rc;
+    }
+    return PAT_OK;
 }
 
 static void build_gap_plan(const Prob* pr, int B, Arena& ar, GapPlan& gp) {
-    std::vector<int2> fwd = forward_block_map(pr, B), fin, pix[3];
+    std::vector<int2> fin, pix[3];
     for (int b = 0; b < B; ++b) {
         for (int i = 0; i < pr[b].ws.n_pix; ++i) pix[pr[b].p.reg].push_back(make_int2(b, i));
         for (int i = 0; i < GAP_FINAL_BLOCKS; ++i) fin.push_back(make_int2(b, i));
     }
-    gp.map_fwd = ar.put(fwd.data(), fwd.size());
-    gp.n_fwd = (int)fwd.size();
+    forward_groups(pr, B, ar, gp);
     gp.map_fin = ar.put(fin.data(), fin.size());
     gp.n_fin = (int)fin.size();
     for (int r = 0; r < 3; ++r) {
@@ -1001,8 +984,8 @@ static UpdateArgs make_update_args(const Prob& pr, int par, bool gap_iter) {
     a.x_out = ws.X[1 - par];
     a.xl_out = ws.XL[1 - par];
     a.y_out = ws.Y[1 - par];
-    a.ubar_quad = ws.ubar_quad;
-    a.u_quad = gap_iter ? ws.u_quad : nullptr;
+    a.ubar = ws.ubar;
+    (void)gap_iter;
     a.stop = &ws.info->stop;
     a.iter = &ws.info->iter;
     a.tiles_x = ceil_div(N, TX);
@@ -1023,10 +1006,10 @@ static int launch_update_b(int reg, const UpdateArgs* args, const int2* map, int
     return PAT_OK;
 }
 
-static int launch_gap_phase(const FwdGapArgs* fa, const GapArgs* ga, const FinalArgs* fi, const GapPlan& gp,
+static int launch_gap_phase(const FwdArgs* fa, const GapArgs* ga, const FinalArgs* fi, const GapPlan& gp,
                             const char* base, cudaStream_t st) {
     prof_mark(PAT_PHASE_GAP, st, true);
-    int rc = launch_forward_gap_b(fa, (const int2*)(base + gp.map_fwd), gp.n_fwd, st);
+    int rc = launch_forward_groups(FWD_GAP, fa, gp, base, st);
     if (rc) return rc;
     for (int r = 0; r < 3; ++r) {
         if (!gp.n_pix[r]) continue;
@@ -1047,30 +1030,43 @@ static int launch_gap_phase(const FwdGapArgs* fa, const GapArgs* ga, const Final
 
 struct IterPlan {
     size_t fwd[2] = {0, 0}, adj[2] = {0, 0}, upd[2][2] = {{0, 0}, {0, 0}}, fgap[2] = {0, 0}, gpix[2] = {0, 0};
-    size_t fin = 0, map_fwd = 0, map_adj = 0;
+    size_t fin = 0, map_adj = 0;
     size_t map_upd[3] = {0, 0, 0};
-    int n_fwd = 0, n_adj = 0;
+    int n_adj = 0;
     int n_upd[3] = {0, 0, 0};
     GapPlan gp;
 };
 
 static void build_iter_plan(const Prob* pr, int B, Arena& ar, IterPlan& ip, int* batch_stopped) {
     for (int par = 0; par < 2; ++par) {
-        std::vector<FwdProxArgs> fw;
+        std::vector<FwdArgs> fw;
         std::vector<AdjArgs> ad;
         std::vector<UpdateArgs> u0, u1;
-        std::vector<FwdGapArgs> fg;
+        std::vector<FwdArgs> fg;
         std::vector<GapArgs> gpx;
         for (int b = 0; b < B; ++b) {
             const Prob& q = pr[b];
             const Workspace& ws = q.ws;
-            fw.push_back(make_fwd_prox_args(q.g, ws.ubar_quad, ws.q, q.f, q.sc.sig_q >= 0 ? nullptr : ws.sig_q,
-                                            q.sc.sig_q, ws.info->step_mul, ws.qw, &ws.info->qmax_bits[par],
-                                            &ws.info->stop));
+            FwdArgs fa = make_fwd_args(q.g, ws.ubar);
+            fa.q = ws.q;
+            fa.f = q.f;
+            fa.sig_q = q.sc.sig_q >= 0 ? nullptr : ws.sig_q;
+            fa.sig_scalar = q.sc.sig_q;
+            fa.step_mul = ws.info->step_mul;
+            fa.qw = ws.qw;
+            fa.qmax_bits = &ws.info->qmax_bits[par];
+            fa.stop = &ws.info->stop;
+            fw.push_back(fa);
             ad.push_back(make_adj_args(q.g, ws.q, ws.qw, &ws.info->qmax_bits[par], ws.kt[par], &ws.info->stop));
             u0.push_back(make_update_args(q, par, false));
             u1.push_back(make_update_args(q, par, true));
-            fg.push_back(make_fwd_gap_args(q.g, ws.X[1 - par], ws.u_quad, ws.q, q.f, ws.data_part, &ws.info->stop));
+            // the gap's K u reads the high words of u^{n+1}, the FP32 value of the pair
+            FwdArgs ga = make_fwd_args(q.g, ws.X[1 - par]);
+            ga.q = ws.q;
+            ga.f = q.f;
+            ga.partials = ws.data_part;
+            ga.stop = &ws.info->stop;
+            fg.push_back(ga);
             gpx.push_back(make_gap_args(q, kt_view(q.g, ws.kt[par], &ws.info->qmax_bits[par]), ws.X[1 - par],
                                         ws.X[par], ws.Y[par]));
         }
@@ -1086,7 +1082,7 @@ static void build_iter_plan(const Prob* pr, int B, Arena& ar, IterPlan& ip, int*
     ip.fin = ar.put(fi.data(), fi.size());
     // maps: forward rows problem by problem; K^T items of all problems heaviest first;
     // update tiles grouped by regulariser
-    std::vector<int2> fwd, upd[3];
+    std::vector<int2> upd[3];
     std::vector<std::pair<float, int2>> adj;
     for (int b = 0; b < B; ++b) {
         const pat_geometry* g = pr[b].g;
@@ -1099,9 +1095,6 @@ static void build_iter_plan(const Prob* pr, int B, Arena& ar, IterPlan& ip, int*
     });
     std::vector<int2> adjm;
     for (auto& e : adj) adjm.push_back(e.second);
-    fwd = forward_block_map(pr, B);
-    ip.map_fwd = ar.put(fwd.data(), fwd.size());
-    ip.n_fwd = (int)fwd.size();
     ip.map_adj = ar.put(adjm.data(), adjm.size());
     ip.n_adj = (int)adjm.size();
     for (int r = 0; r < 3; ++r) {
@@ -1113,8 +1106,7 @@ static void build_iter_plan(const Prob* pr, int B, Arena& ar, IterPlan& ip, int*
 
 static int enqueue_iteration(const IterPlan& ip, const char* base, int it, bool gap_due, cudaStream_t st) {
     const int par = it & 1;
-    int rc = launch_forward_prox_b((const FwdProxArgs*)(base + ip.fwd[par]), (const int2*)(base + ip.map_fwd),
-                                   ip.n_fwd, st);
+    int rc = launch_forward_groups(FWD_PROX, (const FwdArgs*)(base + ip.fwd[par]), ip.gp, base, st);
     if (rc) return rc;
     rc = launch_adjoint_b((const AdjArgs*)(base + ip.adj[par]), (const int2*)(base + ip.map_adj), ip.n_adj, true, st);
     if (rc) return rc;
@@ -1124,7 +1116,7 @@ static int enqueue_iteration(const IterPlan& ip, const char* base, int it, bool 
         if (rc) return rc;
     }
     if (gap_due)
-        rc = launch_gap_phase((const FwdGapArgs*)(base + ip.fgap[par]), (const GapArgs*)(base + ip.gpix[par]),
+        rc = launch_gap_phase((const FwdArgs*)(base + ip.fgap[par]), (const GapArgs*)(base + ip.gpix[par]),
                               (const FinalArgs*)(base + ip.fin), ip.gp, base, st);
     return rc;
 }
@@ -1163,12 +1155,8 @@ static int init_problem(Prob& pr, cudaStream_t st) {
     else
         PAT_CUDA(cudaMemsetAsync(ws.XL[0], 0, nx * sizeof(float), st));
     const float* xb = p->xbar0_dev ? p->xbar0_dev : p->x0_dev;
-    dim3 blk(32, 8), grd(ceil_div(N + 2, 32), ceil_div(N + 2, 8));
-    k_pad<<<grd, blk, 0, st>>>(xb, ws.ubar_pad, N);
-    PAT_LAUNCH_CHECK("k_pad");
-    dim3 gq(ceil_div(N + 1, 32), ceil_div(N + 1, 8));
-    k_quads_from_pad<<<gq, blk, 0, st>>>(ws.ubar_pad, ws.ubar_quad, N);
-    PAT_LAUNCH_CHECK("k_quads_from_pad");
+    k_copy_or_zero<<<std::min(4 * sm_count(), ceil_div((long long)NN, 256)), 256, 0, st>>>(xb, ws.ubar, (long long)NN);
+    PAT_LAUNCH_CHECK("k_copy_or_zero");
     if (reg == PAT_TGV) {
         if (xb)
             PAT_CUDA(cudaMemcpyAsync(ws.vbar0, xb + NN, 2 * NN * 4, cudaMemcpyDeviceToDevice, st));
@@ -1177,8 +1165,8 @@ static int init_problem(Prob& pr, cudaStream_t st) {
     }
     // dual prologue: (r^1, s^1) from (r^0, s^0) and (ubar^0, vbar^0) into Y[0]
     DualArgs da{N, (float)p->alpha, (float)(p->alpha * p->beta), (float)p->gamma, pr.sc.sig2, mul[1], ws.sig_r,
-                p->xi_dev, ws.ubar_pad, ws.vbar0, ws.Y[1], ws.Y[0]};
-    dim3 g2(ceil_div(N, 32), ceil_div(N, 8));
+                p->xi_dev, ws.ubar, ws.vbar0, ws.Y[1], ws.Y[0]};
+    dim3 blk(32, 8), g2(ceil_div(N, 32), ceil_div(N, 8));
     if (reg == PAT_TV)
         k_dual_step<PAT_TV><<<g2, blk, 0, st>>>(da);
     else if (reg == PAT_TGV)
@@ -1207,7 +1195,7 @@ static int finish_problem(Prob& pr, cudaStream_t st) {
     oa.Y[0] = pr.ws.Y[0];
     oa.Y[1] = pr.ws.Y[1];
     oa.q = pr.ws.q;
-    oa.ubar_quad = pr.ws.ubar_quad;
+    oa.ubar = pr.ws.ubar;
     oa.info = pr.ws.info;
     oa.u_out = pr.u_out;
     oa.x_out = pr.p.x_out_dev;
@@ -1372,12 +1360,12 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
                        cudaStream_t st, const char* who) {
     const int N = g->desc.n, J = wav_levels_of(p);
     const long long NN = (long long)N * N, S = (long long)g->desc.n_det * g->desc.n_t;
-    const int n_data = forward_row_blocks(g);
+    const int n_data = g->fwd_n_ctas;
     const int n_pix = pix_blocks(N);
     // workspace
-    enum { U, UOLD, UBAR, UPAD, UQUAD, Q, QW, KT, R, WB, WTR, SCR, SCR2, WU, TAU, SIGR, SIGQ, DPART, PPART, INFO, NBUF };
+    enum { U, UOLD, UBAR, Q, QW, KT, R, WB, WTR, SCR, SCR2, WU, TAU, SIGR, SIGQ, DPART, PPART, INFO, NBUF };
     const size_t nn4 = (size_t)NN * 4;
-    size_t sz[NBUF] = {nn4, nn4, nn4, (size_t)(N + 2) * (N + 2) * 4, quad_count(N) * 16,
+    size_t sz[NBUF] = {nn4, nn4, nn4,
                        (size_t)S * 4, (size_t)S * 4, (size_t)NN * 8, nn4, nn4, nn4, nn4, nn4, nn4,
                        nn4, nn4, (size_t)S * 4, (size_t)n_data * GAP_DATA_TERMS * 8,
                        (size_t)n_pix * GAP_PIX_TERMS * 8, sizeof(InfoDev)};
@@ -1389,8 +1377,6 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
     char* b = nullptr;
     PAT_CUDA(cudaMallocAsync((void**)&b, total, st));
     float *u = (float*)(b + off[U]), *u_old = (float*)(b + off[UOLD]), *ubar = (float*)(b + off[UBAR]);
-    float* upad = (float*)(b + off[UPAD]);
-    float4* uquad = (float4*)(b + off[UQUAD]);
     float *q = (float*)(b + off[Q]), *qw = (float*)(b + off[QW]);
     int* kt = (int*)(b + off[KT]);
     float *r = (float*)(b + off[R]), *wb = (float*)(b + off[WB]), *wtr = (float*)(b + off[WTR]);
@@ -1421,12 +1407,6 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
         const float mul[2] = {(float)ratio, (float)(1.0 / ratio)};
         PAT_CUDA(cudaMemcpyAsync(in->step_mul, mul, sizeof mul, cudaMemcpyHostToDevice, st));
         PAT_CUDA(cudaMemsetAsync(kt, 0, NN * 8, st));
-        dim3 blk(32, 8), grd(ceil_div(N + 2, 32), ceil_div(N + 2, 8));
-        k_pad<<<grd, blk, 0, st>>>(ubar, upad, N);
-        PAT_LAUNCH_CHECK("k_pad");
-        dim3 gq(ceil_div(N + 1, 32), ceil_div(N + 1, 8));
-        k_quads_from_pad<<<gq, blk, 0, st>>>(upad, uquad, N);
-        PAT_LAUNCH_CHECK("k_quads_from_pad");
     }
     int* stopped = nullptr;
     void* dev = nullptr;
@@ -1438,26 +1418,40 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
     std::vector<char> host;
     Arena ar(host);
     size_t fw_off[2], ad_off[2], fg_off, fi_off, fmap_off, amap_off, finmap_off;
-    const int nf = forward_row_blocks(g);
+    const int nf = g->fwd_n_ctas;
     if (!rc) {
         for (int par = 0; par < 2; ++par) {
-            FwdProxArgs fa = make_fwd_prox_args(g, uquad, q, f, sigq, -1.f, in->step_mul, qw, &in->qmax_bits[par],
-                                                &in->stop);
+            FwdArgs fa = make_fwd_args(g, ubar);
+            fa.q = q;
+            fa.f = f;
+            fa.sig_q = sigq;
+            fa.sig_scalar = -1.f;
+            fa.step_mul = in->step_mul;
+            fa.qw = qw;
+            fa.qmax_bits = &in->qmax_bits[par];
+            fa.stop = &in->stop;
             fw_off[par] = ar.put(&fa, 1);
             AdjArgs aa = make_adj_args(g, q, qw, &in->qmax_bits[par], kt + (size_t)par * NN, &in->stop);
             ad_off[par] = ar.put(&aa, 1);
         }
-        FwdGapArgs ga = make_fwd_gap_args(g, u, nullptr, q, f, dpart, &in->stop);
+        FwdArgs ga = make_fwd_args(g, u);
+        ga.q = q;
+        ga.f = f;
+        ga.partials = dpart;
+        ga.stop = &in->stop;
         fg_off = ar.put(&ga, 1);
         FinalArgs fi{dpart, n_data, ppart, n_pix, p->alpha, 0.0, p->box_u, p->box_v, p->tol, PAT_WAV, PAT_ADAPT_NONE,
                      in, stopped};
         fi_off = ar.put(&fi, 1);
         std::vector<int2> fm(nf), am(g->adj_items), fin(GAP_FINAL_BLOCKS);
         {
-            std::vector<std::pair<float, int>> fo;   // row blocks of K, longest first
-            for (int i = 0; i < nf; ++i) fo.push_back({i < (int)g->fwd_block_cost.size() ? g->fwd_block_cost[i] : 0.f, i});
+            // K clusters longest first, the ranks of a cluster consecutive
+            const int S = g->view.n_slabs;
+            std::vector<std::pair<float, int>> fo;
+            for (int c = 0; c < (int)g->fwd_cluster_cost.size(); ++c) fo.push_back({g->fwd_cluster_cost[c], c});
             std::stable_sort(fo.begin(), fo.end(), [](const auto& a, const auto& c) { return a.first > c.first; });
-            for (int i = 0; i < nf; ++i) fm[i] = make_int2(0, fo[i].second);
+            for (size_t c = 0; c < fo.size(); ++c)
+                for (int r = 0; r < S; ++r) fm[c * S + r] = make_int2(0, fo[c].second * S + r);
         }
         std::vector<std::pair<float, int>> order;
         for (int i = 0; i < g->adj_items; ++i) order.push_back({g->adj_item_cost[i], i});
@@ -1472,7 +1466,8 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
     const char* base = (const char*)dev;
     auto iteration = [&](int it, bool gap, cudaStream_t s) -> int {
         const int par = it & 1;
-        int e = launch_forward_prox_b((const FwdProxArgs*)(base + fw_off[par]), (const int2*)(base + fmap_off), nf, s);
+        int e = launch_forward_b(FWD_PROX, (const FwdArgs*)(base + fw_off[par]), (const int2*)(base + fmap_off), nf,
+                                 g->view.n_slabs, g->fwd_smem, s);
         if (!e) e = launch_wav_analysis(ubar, N, J, wb, scr, &in->stop, s);
         if (!e) e = launch_wav_dual(r, wb, sigr, in->step_mul, (float)p->alpha, NN, &in->stop, s);
         if (!e)
@@ -1489,21 +1484,16 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
         pa.u = u;
         pa.u_old = gap ? u_old : nullptr;
         pa.ubar = ubar;
-        pa.ubar_pad = upad;
         pa.kt_clear = kt + (size_t)(1 - par) * NN;
         pa.qmax_next = &in->qmax_bits[1 - par];
         pa.stop = &in->stop;
         pa.iter = &in->iter;
         if (!e) e = launch_wav_primal(pa, s);
-        if (!e) {
-            dim3 blk(32, 8), gq(ceil_div(N + 1, 32), ceil_div(N + 1, 8));
-            k_quads_from_pad<<<gq, blk, 0, s>>>(upad, uquad, N);
-            count_launch();
-            if (cudaGetLastError() != cudaSuccess) e = fail(PAT_ERR_CUDA, "k_quads_from_pad");
-        }
         if (gap && !e) {
             e = launch_wav_analysis(u, N, J, wu, scr2, &in->stop, s);
-            if (!e) e = launch_forward_gap_b((const FwdGapArgs*)(base + fg_off), (const int2*)(base + fmap_off), nf, s);
+            if (!e)
+                e = launch_forward_b(FWD_GAP, (const FwdArgs*)(base + fg_off), (const int2*)(base + fmap_off), nf,
+                                     g->view.n_slabs, g->fwd_smem, s);
             WavGapArgs wg{N, GAP_PIX_TERMS, wu, pa.kt, wtr, u, u_old, ppart, &in->stop};
             if (!e) e = launch_wav_gap_pixels(wg, n_pix, s);
             if (!e) {
@@ -1764,8 +1754,7 @@ static int time_phases(int B, const pat_geometry* const* g, const float* const* 
         const int ph = order[oi];
         auto enqueue = [&]() -> int {
             if (ph == PAT_PHASE_FORWARD_PROX)
-                return launch_forward_prox_b((const FwdProxArgs*)(base + ip.fwd[0]), (const int2*)(base + ip.map_fwd),
-                                             ip.n_fwd, ls);
+                return launch_forward_groups(FWD_PROX, (const FwdArgs*)(base + ip.fwd[0]), ip.gp, base, ls);
             if (ph == PAT_PHASE_ADJOINT)
                 return launch_adjoint_b((const AdjArgs*)(base + ip.adj[0]), (const int2*)(base + ip.map_adj), ip.n_adj,
                                         true, ls);
@@ -1777,7 +1766,7 @@ static int time_phases(int B, const pat_geometry* const* g, const float* const* 
                 }
                 return PAT_OK;
             }
-            return launch_gap_phase((const FwdGapArgs*)(base + ip.fgap[0]), (const GapArgs*)(base + ip.gpix[0]),
+            return launch_gap_phase((const FwdArgs*)(base + ip.fgap[0]), (const GapArgs*)(base + ip.gpix[0]),
                                     (const FinalArgs*)(base + ip.fin), ip.gp, base, ls);
         };
         for (int b = 0; b < B; ++b) cudaMemsetAsync(&pr[b].ws.info->stop, 0, sizeof(int), ls);
@@ -1939,7 +1928,7 @@ int scalar2_steps(const pat_geometry* g, const pat_params* p, ScalarSteps& out, 
         k_scale<<<nb, 256, 0, st>>>(x, n, a0, nullptr); count_launch();
         for (int it = 0; it < kPowerIters; ++it) {
             if (op == 0) {
-                int rc = launch_forward(g, x, false, y, st);
+                int rc = launch_forward(g, x, y, st);
                 if (rc) return rc;
                 rc = launch_adjoint(g, y, x, st);
                 if (rc) return rc;
@@ -2258,7 +2247,10 @@ static int gap_impl(const pat_geometry* g, const float* f, const pat_params* p, 
         std::vector<int2> amap(g->adj_items);
         for (int i = 0; i < g->adj_items; ++i) amap[i] = make_int2(0, i);
         const size_t amap_off = ar.put(amap.data(), amap.size());
-        FwdGapArgs fa = make_fwd_gap_args(g, x, nullptr, y, f, pr.ws.data_part, nullptr);
+        FwdArgs fa = make_fwd_args(g, x);
+        fa.q = const_cast<float*>(y);   // read only by the gap epilogue
+        fa.f = f;
+        fa.partials = pr.ws.data_part;
         const size_t fa_off = ar.put(&fa, 1);
         GapArgs ga = make_gap_args(pr, kt_view(g, pr.ws.kt[0], &pr.ws.info->qmax_bits[0]), x, nullptr, y + S);
         const size_t ga_off = ar.put(&ga, 1);
@@ -2269,7 +2261,7 @@ static int gap_impl(const pat_geometry* g, const float* f, const pat_params* p, 
             char* b = (char*)dev;
             rc = launch_adjoint_b((const AdjArgs*)(b + adj_off), (const int2*)(b + amap_off), g->adj_items, false, st);
             if (!rc)
-                rc = launch_gap_phase((const FwdGapArgs*)(b + fa_off), (const GapArgs*)(b + ga_off),
+                rc = launch_gap_phase((const FwdArgs*)(b + fa_off), (const GapArgs*)(b + ga_off),
                                       (const FinalArgs*)(b + fi_off), gp, b, st);
         }
     }

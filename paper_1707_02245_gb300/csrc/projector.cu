@@ -1,148 +1,41 @@
 // Matrix-free circular-mean projector K and its exact transpose K^T (Sec. 3.3.1,
 // Sec. 4.2 eq. (K_def)), plus the fused data-row kernels of the PDHG iteration.
 //
-// Thread mapping of K: four lanes per data row (d, k), one per angular phase; a warp
-// holds 8 consecutive radii of one detector and walks the group's angular window in
-// lockstep, so at every step its 32 points form a 4-angle x 8-radius patch of the polar
-// grid (neighbouring lanes touch neighbouring pixels).  A block holds adjacent detectors
-// at the same radii, whose arcs cross the same pixels, so its warps share L1 lines.  Each
-// point is interpolated bilinearly between pixel centres.
-//
-// The hot path reads a zero-bordered copy of the image ((N+2)^2 floats, pixel (i, j) at
-// (j+1)(N+2) + i+1) so a point with taps i0, j0 in [-1, N-1] needs no per-tap test.
+// K: every point of circle (d, k) is interpolated bilinearly between pixel centres.  The
+// image is cut into horizontal slabs; a CTA copies one slab (with a zero border and one
+// extra row) into shared memory and evaluates the points of a list of work units (one
+// row group of 8 radii of one detector, restricted to that slab) from there, so each of
+// a point's four taps is a shared-memory load.  A warp holds the 8 radii of a row group
+// times 4 angular phases, so at every step its 32 points form a 4-angle x 8-radius patch
+// of the polar grid.  A row group's slabs are added by the last unit to finish, in slab
+// order, so the result does not depend on scheduling.
+#include <string.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "pat_internal.cuh"
 #include "reduce.cuh"
 
 namespace pat {
 
-template <bool PADDED>
-__device__ __forceinline__ float fetch4(const float* __restrict__ u, int N, const Taps& t, float& v10,
-                                        float& v01, float& v11) {
-    if (PADDED) {
-        const int P = N + 2;
-        const float* p = u + (t.j0 + 1) * P + (t.i0 + 1);
-        v10 = __ldg(p + 1);
-        v01 = __ldg(p + P);
-        v11 = __ldg(p + P + 1);
-        return __ldg(p);
-    } else {
-        const bool x0 = t.i0 >= 0, x1 = t.i0 + 1 < N, y0 = t.j0 >= 0, y1 = t.j0 + 1 < N;
-        const float* p = u + t.j0 * N + t.i0;
-        v10 = (x1 && y0) ? __ldg(p + 1) : 0.f;
-        v01 = (x0 && y1) ? __ldg(p + N) : 0.f;
-        v11 = (x1 && y1) ? __ldg(p + N + 1) : 0.f;
-        return (x0 && y0) ? __ldg(p) : 0.f;
-    }
+// Bilinear taps of a point from the plain N*N image in global memory, zero off the grid.
+__device__ __forceinline__ float fetch4_global(const float* __restrict__ u, int N, const Taps& t, float& v10,
+                                               float& v01, float& v11) {
+    const bool x0 = t.i0 >= 0, x1 = t.i0 + 1 < N, y0 = t.j0 >= 0, y1 = t.j0 + 1 < N;
+    const float* p = u + t.j0 * N + t.i0;
+    v10 = (x1 && y0) ? __ldg(p + 1) : 0.f;
+    v01 = (x0 && y1) ? __ldg(p + N) : 0.f;
+    v11 = (x1 && y1) ? __ldg(p + N + 1) : 0.f;
+    return (x0 && y0) ? __ldg(p) : 0.f;
 }
 
-// Row mapping of the projector kernels: a warp holds KGRP = 8 consecutive radii of one
-// detector times NPH = 4 angular phases; lane = ph * 8 + kl.  Phase ph walks the group's
-// angular window at m = m_first + ph, + ph + 4, ...  so at every step the warp evaluates
-// a 4 (angles) x 8 (radii) patch of the polar grid, which is a compact patch of pixels.
+// Lane mapping of a K unit: a warp holds the KGRP = 8 radii of one row group times NPH = 4
+// angular phases, lane = ph * 8 + kl.  Phase ph walks a window at m_first + ph,
+// m_first + ph + 4, ...  so at every step the warp evaluates a 4 (angles) x 8 (radii)
+// patch of the polar grid, a compact patch of pixels.
 constexpr int NPH = 4;
-// unroll factors of the forward's angular loop and of the K^T candidate loop (0: the
-// compiler's choice)
-#ifndef PAT_FWD_UNROLL
-#define PAT_FWD_UNROLL 0
-#endif
-#ifndef PAT_ADJ_UNROLL
-#define PAT_ADJ_UNROLL 0
-#endif
-#ifndef PAT_ADJ_RADIUS_FMA
-#define PAT_ADJ_RADIUS_FMA 1   // K^T evaluates r_k (one FMA) instead of gathering rk[k]
-#endif
-#if PAT_FWD_UNROLL > 0
-constexpr int FWD_UNROLL = PAT_FWD_UNROLL;
-#endif
-#if PAT_ADJ_UNROLL > 0
-constexpr int ADJ_UNROLL = PAT_ADJ_UNROLL;
-#endif
-// A row block is ROW_WARPS warps: FWD_DW adjacent detectors times FWD_KW groups of 8 radii.
-#ifndef PAT_FWD_DW
-#define PAT_FWD_DW 8
-#endif
-#ifndef PAT_FWD_WARPS
-#define PAT_FWD_WARPS 16
-#endif
-constexpr int ROW_WARPS = PAT_FWD_WARPS;
-constexpr int FWD_DW = PAT_FWD_DW;
-constexpr int FWD_KW = ROW_WARPS / FWD_DW;
-static_assert(FWD_DW * FWD_KW == ROW_WARPS, "FWD_DW must divide ROW_WARPS");
-constexpr int ROWS_PER_BLOCK = ROW_WARPS * KGRP;
-constexpr int ROW_THREADS = ROWS_PER_BLOCK * NPH;
-// resident row blocks per SM that the register budget must allow (0: the compiler's choice)
-#ifndef PAT_FWD_MIN_BLOCKS
-#define PAT_FWD_MIN_BLOCKS 0
-#endif
-#if PAT_FWD_MIN_BLOCKS > 0
-#define PAT_ROW_BOUNDS __launch_bounds__(ROW_THREADS, PAT_FWD_MIN_BLOCKS)
-#else
-#define PAT_ROW_BOUNDS __launch_bounds__(ROW_THREADS)
-#endif
-
-struct RowLane {
-    int d, k, ph;
-    bool valid;
-};
-
-// lane of row block (kb, db): warp w takes detector db FWD_DW + w / FWD_KW and the radii
-// group kb FWD_KW + w % FWD_KW; lanes past the last detector or radius are not valid
-// (their detector index is clamped so that table reads stay in range)
-__device__ __forceinline__ RowLane row_lane(const GeomView& g, int kb, int db) {
-    RowLane r;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int d = db * FWD_DW + warp / FWD_KW;
-    r.ph = lane >> 3;
-    r.k = (kb * FWD_KW + warp % FWD_KW) * KGRP + (lane & 7);
-    r.valid = r.k < g.n_t && d < g.n_det;
-    r.d = min(d, g.n_det - 1);
-    return r;
-}
-
-// row blocks along the radii (the grid's other dimension runs over detector groups)
-__device__ __forceinline__ int row_blocks(const GeomView& g) {
-    return (g.n_t + FWD_KW * KGRP - 1) / (FWD_KW * KGRP);
-}
-
-// Partial integral of the bilinear image over circle (d, k) for one angular phase.
-// QUAD: u points at the float4 quads (one load per point; layout quad_index); otherwise u is the plain
-// N*N image read with per-tap bounds tests.
-template <bool QUAD>
-__device__ __forceinline__ float circle_partial(const GeomView& g, const float* __restrict__ u, const RowLane& rl) {
-    const int2 w = __ldg(&g.win[rl.d * g.n_kgrp + min(rl.k / KGRP, g.n_kgrp - 1)]);
-    const float2 det = __ldg(&g.det[rl.d]);
-    const float r = rl.valid ? __ldg(&g.rk[rl.k]) : 0.f;
-    float acc = 0.f;
-    int m = w.x + rl.ph;
-    if (m >= g.quad_m) m -= g.quad_m;
-#if PAT_FWD_UNROLL > 0
-#pragma unroll FWD_UNROLL
-#endif
-    for (int j = rl.ph; j < w.y; j += NPH) {
-        const float2 cs = __ldg(&g.cs[m]);
-        m += NPH;
-        if (m >= g.quad_m) m -= g.quad_m;
-        Taps t;
-        if (point_taps(g, det, r, cs, t) && rl.valid) {
-            float v00, v10, v01, v11;
-            if (QUAD) {
-                const float4 v = __ldg(reinterpret_cast<const float4*>(u) + quad_index(t.i0 + 1, t.j0 + 1, g.n));
-                v00 = v.x;
-                v10 = v.y;
-                v01 = v.z;
-                v11 = v.w;
-            } else {
-                v00 = fetch4<false>(u, g.n, t, v10, v01, v11);
-            }
-            const float a = fmaf(t.ax, v10 - v00, v00);
-            const float b = fmaf(t.ax, v11 - v01, v01);
-            acc += fmaf(t.ay, b - a, a);
-        }
-    }
-    return acc;
-}
+constexpr int SLAB_WARPS = SLAB_THREADS / 32;
 
 // Sum over the four phases (lanes kl, kl+8, kl+16, kl+24); valid in every lane.
 __device__ __forceinline__ float phase_sum(float v) {
@@ -151,55 +44,299 @@ __device__ __forceinline__ float phase_sum(float v) {
     return v;
 }
 
-// y = K u
-__global__ void PAT_ROW_BOUNDS k_forward(GeomView g, const float* __restrict__ u, float* __restrict__ y) {
-    const RowLane rl = row_lane(g, blockIdx.x, blockIdx.y);
-    const float s = phase_sum(circle_partial<false>(g, u, rl));
-    if (rl.valid && rl.ph == 0) y[(size_t)rl.d * g.n_t + rl.k] = s * __ldg(&g.wk[rl.k]);
+// Shared-memory loads by 32-bit shared address.
+__device__ __forceinline__ float lds(unsigned a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ float2 lds2(unsigned a) {
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(a));
+    return v;
+}
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+
+// 16-byte asynchronous copy global -> shared (no register staging), and its completion.
+__device__ __forceinline__ void cp_async16(unsigned dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// Partial integral of the bilinear image over circle (d, k) for angular phase ph over the
+// unit's two windows (each m_first | count << 16), counting only the points whose upper
+// tap row j0 lies in [jlo, jlo + reff) and whose left tap column i0 lies in [-1, N-1].
+//  SMEM: rows jlo .. jlo + reff of the zero-bordered image are staged in shared memory at
+//  byte address img_s (column i at byte 4 (4 + i) of a row of W floats, with columns N and
+//  N + 1 of rows 0 and 1 zero), and cs_s holds the angle table twice over, so m never
+//  wraps.  The body has no branch: a point outside the slab or the grid reads the zero
+//  cell at columns N, N + 1 of rows 0, 1.  Two points per trip, with separate sums.
+//  Otherwise: taps and angles come from global memory.
+template <bool SMEM>
+__device__ __forceinline__ float unit_partial(const GeomView& g, unsigned cs_s, const float* __restrict__ img,
+                                              unsigned img_s, int jlo, int reff, unsigned w0, unsigned w1,
+                                              float2 det, float r, bool valid, int ph) {
+    const int N = g.n, M = g.quad_m, W = g.slab_stride;
+    const int c0 = (int)(w0 >> 16), tot = c0 + (int)(w1 >> 16);
+    const int m0 = (int)(w0 & 0xffffu), off1 = (int)(w1 & 0xffffu) - c0;   // m = j + (j < c0 ? m0 : off1)
+    float acc = 0.f;
+    if (SMEM) {
+        const unsigned W4 = 4u * (unsigned)W;
+        const unsigned base = img_s + 12u;                               // column i at base + 4 (i + 1)
+        const unsigned zero = base + 4u * (unsigned)(N + 1);            // columns N, N + 1 of rows 0, 1
+        const float2 rr = make_float2(r, r);
+        const float2 mone = make_float2(-1.f, -1.f);
+        const float2 magic = make_float2(FLOOR_MAGIC, FLOOR_MAGIC), nmagic = make_float2(-FLOOR_MAGIC, -FLOOR_MAGIC);
+        const int lbias = FLOOR_MAGIC_BITS - 1;     // li = floor(fx) + 1
+        const int jbias = FLOOR_MAGIC_BITS + jlo;   // lj = floor(fy) - jlo
+        float acc2 = 0.f;
+        for (int j = ph; j < tot; j += 2 * NPH) {
+            const int jb = j + NPH;
+            const bool vb = jb < tot;
+            const int ma = j + (j < c0 ? m0 : off1);
+            const int mb = vb ? jb + (jb < c0 ? m0 : off1) : ma;
+            const float2 csa = lds2(cs_s + 8u * (unsigned)ma);
+            const float2 csb = lds2(cs_s + 8u * (unsigned)mb);
+            // positions and taps; the FP32 arithmetic of the transpose (fx = fmaf(r, cs.x, det.x))
+            const float2 fa = __ffma2_rn(rr, csa, det), fb = __ffma2_rn(rr, csb, det);
+            // exact floors (see point_coords): ta = floor(fa) + 1.5 * 2^23
+            const float2 ta = __fadd2_rd(fa, magic), tb = __fadd2_rd(fb, magic);
+            const int lia = __float_as_int(ta.x) - lbias, lja = __float_as_int(ta.y) - jbias;
+            const int lib = __float_as_int(tb.x) - lbias, ljb = __float_as_int(tb.y) - jbias;
+            const bool ina = ((unsigned)lja < (unsigned)reff) & ((unsigned)lia <= (unsigned)N) & valid;
+            const bool inb = ((unsigned)ljb < (unsigned)reff) & ((unsigned)lib <= (unsigned)N) & valid & vb;
+            const unsigned aa = ina ? base + (unsigned)lja * W4 + 4u * (unsigned)lia : zero;   // li = i0 + 1
+            const unsigned ab = inb ? base + (unsigned)ljb * W4 + 4u * (unsigned)lib : zero;
+            const float2 loa = make_float2(lds(aa), lds(aa + W4)), hia = make_float2(lds(aa + 4u), lds(aa + W4 + 4u));
+            const float2 lob = make_float2(lds(ab), lds(ab + W4)), hib = make_float2(lds(ab + 4u), lds(ab + W4 + 4u));
+            // (ax, ay) = fa - floor(fa): floor(fa) = ta - C exactly, and the difference is exact
+            const float2 fra = __ffma2_rn(__fadd2_rn(ta, nmagic), mone, fa);
+            const float2 frb = __ffma2_rn(__fadd2_rn(tb, nmagic), mone, fb);
+            // rows j0 and j0 + 1 interpolated in x, then in y
+            const float2 pa = __ffma2_rn(make_float2(fra.x, fra.x), __ffma2_rn(loa, mone, hia), loa);
+            const float2 pb = __ffma2_rn(make_float2(frb.x, frb.x), __ffma2_rn(lob, mone, hib), lob);
+            acc += fmaf(fra.y, pa.y - pa.x, pa.x);
+            acc2 += fmaf(frb.y, pb.y - pb.x, pb.x);
+        }
+        acc += acc2;
+    } else {
+        for (int j = ph; j < tot; j += NPH) {
+            const int mm = j + (j < c0 ? m0 : off1);
+            const int m = mm >= M ? mm - M : mm;
+            Taps t;
+            point_coords(g, det, r, __ldg(&g.cs[m]), t);
+            if ((unsigned)(t.j0 + 1) <= (unsigned)N && (unsigned)(t.i0 + 1) <= (unsigned)N && valid) {
+                float v10, v01, v11;
+                const float v00 = fetch4_global(img, N, t, v10, v01, v11);
+                const float p = fmaf(t.ax, v10 - v00, v00);
+                const float q = fmaf(t.ax, v11 - v01, v01);
+                acc += fmaf(t.ay, q - p, p);
+            }
+        }
+    }
+    return acc;
 }
 
-// q <- prox_{sigma F1*}(q + sigma K ubar) = (q + sigma (K ubar - f)) / (1 + sigma)  (Sec. 3.2)
-// for the rows of row block kb of detector d.  Also records q w_k for the K^T that follows
-// and max |q| (as float bits) for its fixed-point scale.
-__device__ __forceinline__ void forward_prox_rows(const FwdProxArgs& a, int kb, int d) {
+// Issues the copy of image rows jlo .. jlo + nrow - 1 into the slab at s_img (row t at
+// float t W, column i at float t W + 4 + i): cp.async for rows inside the image when N is
+// a multiple of 4 and the image 16-byte aligned, plain loads otherwise; rows outside the
+// image and the columns -1 and N are zero.  Completed by cp_async_wait_all() and a barrier.
+__device__ __forceinline__ void stage_slab(const float* __restrict__ img, int N, int W, int jlo, int nrow,
+                                           float* s_img) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool vec = (N & 3) == 0 && ((reinterpret_cast<size_t>(img) & 15) == 0);
+    const unsigned base = smem_addr(s_img);
+    for (int t = warp; t < nrow; t += SLAB_WARPS) {
+        const int j = jlo + t;
+        float* row = s_img + t * W;
+        const bool in = j >= 0 && j < N;
+        if (vec && in) {
+            const float* src = img + (size_t)j * N;
+            for (int c = 4 * lane; c < N; c += 128) cp_async16(base + 4u * (unsigned)(t * W + 4 + c), src + c);
+        } else {
+            for (int c = lane; c < N; c += 32) row[4 + c] = in ? __ldg(img + (size_t)j * N + c) : 0.f;
+        }
+        if (lane == 0) {
+            row[3] = 0.f;
+            row[4 + N] = 0.f;
+            if (t < 2) row[5 + N] = 0.f;   // with column N: the zero cell of out-of-slab points
+        }
+    }
+}
+
+// Shared-memory layout of a K CTA (byte offsets; every part 16-byte aligned):
+//   slab image (R + 1) * W floats | the round's units (at most FWD_ROUND) | cs twice over
+//   (2M float2) | det (D float2) | the round's accumulators (FWD_ROUND * KGRP floats)
+struct FwdSmem {
+    int slab, units, cs, det, acc, total;
+};
+__host__ __device__ __forceinline__ int align16(int x) { return (x + 15) & ~15; }
+__host__ __device__ __forceinline__ FwdSmem fwd_smem_layout(int rows, int stride, int M, int D, bool staged) {
+    FwdSmem l;
+    l.slab = 0;
+    l.units = align16(rows > 0 ? (rows + 1) * stride * 4 : 0);
+    l.cs = l.units + FWD_ROUND * 16;
+    l.det = l.cs + (staged ? align16(2 * M * 8) : 0);   // the angle table twice over
+    l.acc = l.det + (staged ? align16(D * 8) : 0);
+    l.total = l.acc + FWD_ROUND * KGRP * 4;
+    return l;
+}
+
+// cluster helpers: rank in the cluster, barrier over the cluster's CTAs (orders shared
+// memory writes before the barrier with reads after it), and a load from the shared
+// memory of CTA `rank` at the offset of the local address p
+__device__ __forceinline__ unsigned cluster_rank() {
+    unsigned r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ float ld_cluster(const float* p, unsigned rank) {
+    unsigned a = smem_addr(p), ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(a), "r"(rank));
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(ra) : "memory");
+    return v;
+}
+
+// One round of a CTA: warps take the CTA's units of the round one at a time and store each
+// unit's row sums in the accumulators of its row group (one unit per row group and CTA).
+template <bool SMEM>
+__device__ __forceinline__ void forward_units(const FwdArgs& a, int ub, int ue, unsigned char* smem,
+                                              const FwdSmem& L, int jlo, int reff, int& s_next) {
     const GeomView& g = a.g;
-    const RowLane rl = row_lane(g, kb, d);
-    // issued before the circle sums so that its latency overlaps them
-    const float smul = a.step_mul ? __ldg(a.step_mul + 1) : 1.f;
-    const float s = phase_sum(circle_partial<true>(g, reinterpret_cast<const float*>(a.ubar_quad), rl));
-    float aq = 0.f;
-    if (rl.valid && rl.ph == 0) {
-        const size_t i = (size_t)rl.d * g.n_t + rl.k;
-        const float wk = __ldg(&g.wk[rl.k]);
-        const float ku = s * wk;
-        const float sg = (a.sig_q ? a.sig_q[i] : a.sig_scalar) * smul;
-        const float qn = (a.q[i] + sg * (ku - a.f[i])) / (1.f + sg);
-        a.q[i] = qn;
-        a.qw[i] = qn * wk;
-        aq = fabsf(qn);
-    }
-    // block max of |q| (a NaN's bits compare greater than every finite value's)
-    unsigned bits = __float_as_uint(aq);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) bits = max(bits, __shfl_xor_sync(0xffffffffu, bits, o));
-    __shared__ unsigned wmax[ROW_THREADS / 32];
-    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = bits;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        unsigned m = 0;
-        for (int w = 0; w < ROW_THREADS / 32; ++w) m = max(m, wmax[w]);
-        if (m) atomicMax(a.qmax_bits, m);
+    const int T = g.n_t;
+    const int4* s_units = reinterpret_cast<const int4*>(smem + L.units);
+    const float2* s_det = reinterpret_cast<const float2*>(smem + L.det);
+    float* s_acc = reinterpret_cast<float*>(smem + L.acc);
+    const unsigned img_s = smem_addr(smem + L.slab), cs_s = smem_addr(smem + L.cs);
+    const float dr_f = g.dr_f, rh_f = g.rh_f;
+    const int lane = threadIdx.x & 31, kl = lane & 7, ph = lane >> 3;
+    for (;;) {
+        int u = 0;
+        if (lane == 0) u = atomicAdd(&s_next, 1);
+        u = __shfl_sync(0xffffffffu, u, 0);
+        if (u >= ue) break;
+        const int4 un = s_units[u - ub];
+        const int d = un.x;
+        const int k = (un.w >> 16) * KGRP + kl;
+        const bool valid = k < T;
+        const float r = radius(valid ? k : 0, dr_f, rh_f);   // = rk[k], bit for bit
+        const float2 det = SMEM ? s_det[d] : __ldg(&g.det[d]);
+        const float acc = unit_partial<SMEM>(g, cs_s, a.img, img_s, jlo, reff, (unsigned)un.y, (unsigned)un.z, det, r,
+                                             valid, ph);
+        const float sum = phase_sum(acc);
+        if (ph == 0) s_acc[(un.w & 0xffff) * KGRP + kl] = sum;
     }
 }
 
-__global__ void PAT_ROW_BOUNDS k_forward_prox_b(const FwdProxArgs* __restrict__ args,
-                                                               const int2* __restrict__ map) {
+// K (Sec. 3.3.1, eq. (K_def)) for the row groups of one cluster, then the epilogue on
+// their rows.  The S partial sums of a row (one per slab) are added in rank (slab) order,
+// so the result does not depend on scheduling.
+template <int EPI>
+__global__ void __launch_bounds__(SLAB_THREADS, 2) k_forward_b(const FwdArgs* __restrict__ args,
+                                                           const int2* __restrict__ map) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ FwdArgs sa;
+    __shared__ int s_next;
+    __shared__ unsigned s_qmax;
     const int2 pm = map[blockIdx.x];
-    __shared__ FwdProxArgs sa;
-    const FwdProxArgs& a = stage_args(args, pm.x, sa);
+    const FwdArgs& a = stage_args(args, pm.x, sa);
+    // (every CTA of a cluster reads the same flag, so a stopped problem's clusters leave
+    // together, before any cluster barrier)
     if (a.stop && *(volatile const int*)a.stop) return;
-    const int nkb = row_blocks(a.g);
-    forward_prox_rows(a, pm.y % nkb, pm.y / nkb);
+    const GeomView& g = a.g;
+    const int N = g.n, T = g.n_t, S = g.n_slabs, M = g.quad_m, D = g.n_det;
+    const unsigned rank = S > 1 ? cluster_rank() : 0u;
+    const int4 cta = __ldg(&g.ctas[pm.y]);
+    const int rg0 = cta.x, n_rg = cta.y;
+    const int* roff = g.roff + cta.z;
+    const bool smem_img = g.slab_rows > 0;
+    const FwdSmem L = fwd_smem_layout(g.slab_rows, g.slab_stride, M, D, smem_img);
+    float* s_acc = reinterpret_cast<float*>(smem + L.acc);
+    int4* s_units = reinterpret_cast<int4*>(smem + L.units);
+    const int jlo = smem_img ? (int)rank * g.slab_rows - 1 : -1;
+    const int reff = smem_img ? min(g.slab_rows, N - jlo) : N + 1;
+    if (smem_img) {
+        float2* s_cs = reinterpret_cast<float2*>(smem + L.cs);
+        float2* s_det = reinterpret_cast<float2*>(smem + L.det);
+        for (int i = threadIdx.x; i < 2 * M; i += SLAB_THREADS) s_cs[i] = __ldg(&g.cs[i < M ? i : i - M]);
+        for (int i = threadIdx.x; i < D; i += SLAB_THREADS) s_det[i] = __ldg(&g.det[i]);
+        stage_slab(a.img, N, g.slab_stride, jlo, reff + 1, reinterpret_cast<float*>(smem + L.slab));
+    }
+    if (threadIdx.x == 0) s_qmax = 0u;
+    const int lane = threadIdx.x & 31;
+    const float smul = (EPI == FWD_PROX && a.step_mul) ? __ldg(a.step_mul + 1) : 1.f;
+    unsigned qbits = 0u;
+    float t[GAP_DATA_TERMS] = {0.f, 0.f, 0.f, 0.f};
+    const int n_rounds = (n_rg + FWD_ROUND - 1) / FWD_ROUND;
+    for (int rd = 0; rd < n_rounds; ++rd) {
+        const int ub = __ldg(&roff[rd]), ue = __ldg(&roff[rd + 1]);
+        const int nr = min(FWD_ROUND, n_rg - rd * FWD_ROUND);
+        for (int i = threadIdx.x; i < ue - ub; i += SLAB_THREADS) s_units[i] = __ldg(&g.units[ub + i]);
+        for (int i = threadIdx.x; i < nr * KGRP; i += SLAB_THREADS) s_acc[i] = 0.f;
+        if (threadIdx.x == 0) s_next = ub;
+        if (smem_img && rd == 0) cp_async_wait_all();
+        __syncthreads();
+        if (smem_img)
+            forward_units<true>(a, ub, ue, smem, L, jlo, reff, s_next);
+        else
+            forward_units<false>(a, ub, ue, smem, L, jlo, reff, s_next);
+        // all CTAs of the cluster have their partial sums of the round
+        if (S > 1) cluster_sync(); else __syncthreads();
+        // epilogue: the round's rows are split over the cluster's CTAs; row i of the round
+        // is row (i % KGRP) of row group rgs[rg0 + rd * FWD_ROUND + i / KGRP]
+        const int rows = nr * KGRP, per = (rows + S - 1) / S;
+        const int i0 = (int)rank * per, i1 = min(rows, i0 + per);
+        for (int i = i0 + threadIdx.x; i < i1; i += SLAB_THREADS) {
+            const int rg = __ldg(&g.rgs[rg0 + rd * FWD_ROUND + i / KGRP]);
+            const int d = rg / g.n_kgrp;
+            const int k = (rg - d * g.n_kgrp) * KGRP + (i & (KGRP - 1));
+            if (k >= T) continue;
+            float sum = 0.f;
+            for (int r = 0; r < S; ++r) sum += (S > 1) ? ld_cluster(&s_acc[i], (unsigned)r) : s_acc[i];
+            const size_t row = (size_t)d * T + k;
+            const float wk = __ldg(&g.wk[k]);
+            if (EPI == FWD_Y) {
+                a.y[row] = sum * wk;
+            } else if (EPI == FWD_PROX) {
+                // q <- prox_{sigma F1*}(q + sigma K ubar) = (q + sigma (K ubar - f)) / (1 + sigma)  (Sec. 3.2)
+                const float ku = sum * wk;
+                const float sg = (a.sig_q ? a.sig_q[row] : a.sig_scalar) * smul;
+                const float qn = (a.q[row] + sg * (ku - a.f[row])) / (1.f + sg);
+                a.q[row] = qn;
+                a.qw[row] = qn * wk;
+                qbits = max(qbits, __float_as_uint(fabsf(qn)));  // a NaN's bits exceed every finite value's
+            } else {
+                // per-row terms in FP32; the CTA's sums as FP32 pairs per warp, FP64 across warps
+                const float ku = sum * wk;
+                const float res = ku - a.f[row];
+                const float qi = a.q[row];
+                t[0] += res * res;
+                t[1] += qi * qi;
+                t[2] += qi * a.f[row];
+                t[3] += fabsf(qi - res);   // dual residual of the data term: q - dF1(Ku)
+            }
+        }
+        // the accumulators and units are reused by the next round, and no CTA may leave
+        // while another still reads its accumulators
+        if (S > 1) cluster_sync(); else __syncthreads();
+    }
+    if (EPI == FWD_PROX) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) qbits = max(qbits, __shfl_xor_sync(0xffffffffu, qbits, o));
+        if (lane == 0 && qbits) atomicMax(&s_qmax, qbits);
+        __syncthreads();
+        if (threadIdx.x == 0 && s_qmax) atomicMax(a.qmax_bits, s_qmax);
+    }
+    if (EPI == FWD_GAP) {
+        double sum[GAP_DATA_TERMS];
+        block_sum_pair<GAP_DATA_TERMS>(t, sum);
+        if (threadIdx.x == 0)
+            for (int c = 0; c < GAP_DATA_TERMS; ++c) a.partials[(size_t)GAP_DATA_TERMS * pm.y + c] = sum[c];
+    }
 }
 
 // max |y| over n values as float bits (atomicMax; *out must start at 0)
@@ -210,46 +347,6 @@ __global__ void k_absmax(const float* __restrict__ y, long long n, unsigned* __r
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
     if ((threadIdx.x & 31) == 0 && m) atomicMax(out, m);
-}
-
-// FP64 partial sums for the duality gap over data rows:
-//   {sum (K u - f)^2, sum q^2, sum q f}   one triple per (local) block lb
-template <bool QUAD>
-__device__ __forceinline__ void forward_gap_rows(const FwdGapArgs& a, int kb, int d, int lb) {
-    const GeomView& g = a.g;
-    const RowLane rl = row_lane(g, kb, d);
-    const float* img = QUAD ? reinterpret_cast<const float*>(a.u_quad) : a.u;
-    const float s = phase_sum(circle_partial<QUAD>(g, img, rl));
-    // per-row terms in FP32; warp sums as FP32 pairs, block sums in FP64 (GB300's FP64 pipe
-    // is 1/64 of FP32)
-    float t[GAP_DATA_TERMS] = {0.f, 0.f, 0.f, 0.f};
-    if (rl.valid && rl.ph == 0) {
-        const float ku = s * __ldg(&g.wk[rl.k]);
-        const size_t i = (size_t)rl.d * g.n_t + rl.k;
-        const float res = ku - a.f[i];
-        const float qi = a.q[i];
-        t[0] = res * res;
-        t[1] = qi * qi;
-        t[2] = qi * a.f[i];
-        t[3] = fabsf(qi - res);   // dual residual of the data term: q - dF1(Ku)
-    }
-    double sum[GAP_DATA_TERMS];
-    block_sum_pair<GAP_DATA_TERMS>(t, sum);
-    if (threadIdx.x == 0)
-        for (int c = 0; c < GAP_DATA_TERMS; ++c) a.partials[GAP_DATA_TERMS * lb + c] = sum[c];
-}
-
-__global__ void PAT_ROW_BOUNDS k_forward_gap_b(const FwdGapArgs* __restrict__ args,
-                                                              const int2* __restrict__ map) {
-    const int2 pm = map[blockIdx.x];
-    __shared__ FwdGapArgs sa;
-    const FwdGapArgs& a = stage_args(args, pm.x, sa);
-    if (a.stop && *(volatile const int*)a.stop) return;
-    const int nkb = row_blocks(a.g);
-    if (a.u_quad)
-        forward_gap_rows<true>(a, pm.y % nkb, pm.y / nkb, pm.y);
-    else
-        forward_gap_rows<false>(a, pm.y % nkb, pm.y / nkb, pm.y);
 }
 
 // ---------------------------------------------------------------------------------
@@ -462,83 +559,105 @@ __global__ void k_double_to_float(const double* __restrict__ a, float* __restric
     if (i < n) b[i] = (float)a[i];
 }
 
-static dim3 row_grid(const pat_geometry* g) {
-    return dim3(ceil_div(g->desc.n_t, FWD_KW * KGRP), ceil_div(g->desc.n_det, FWD_DW));
-}
-
-int forward_row_blocks(const pat_geometry* g) {
-    dim3 gr = row_grid(g);
-    return gr.x * gr.y;
-}
-
-std::vector<float> forward_block_costs(const pat_geometry_desc& d, const std::vector<int2>& win) {
-    const int D = d.n_det, n_kgrp = (d.n_t + KGRP - 1) / KGRP;
-    const int nkb = ceil_div(d.n_t, FWD_KW * KGRP), ndb = ceil_div(D, FWD_DW);
-    std::vector<float> cost((size_t)nkb * ndb, 0.f);
-    for (int db = 0; db < ndb; ++db)
-        for (int kb = 0; kb < nkb; ++kb) {
-            float c = 0.f;
-            for (int w = 0; w < ROW_WARPS; ++w) {   // the warp -> (detector, radii group) map of row_lane
-                const int det = db * FWD_DW + w / FWD_KW, kg = kb * FWD_KW + w % FWD_KW;
-                if (det < D && kg < n_kgrp) c += (float)win[(size_t)det * n_kgrp + kg].y;
-            }
-            cost[(size_t)db * nkb + kb] = c;   // local block index kb + nkb * db
-        }
-    return cost;
-}
-
-
-int launch_forward(const pat_geometry* g, const float* u, bool padded, float* y, cudaStream_t st) {
-    (void)padded;
-    k_forward<<<row_grid(g), ROW_THREADS, 0, st>>>(g->view, u, y);
-    PAT_LAUNCH_CHECK("k_forward");
-    return PAT_OK;
-}
-
-FwdProxArgs make_fwd_prox_args(const pat_geometry* g, const float4* ubar_quad, float* q, const float* f,
-                               const float* sig_q, float sig_scalar, const float* step_mul, float* qw,
-                               unsigned* qmax_bits, const int* stop) {
-    FwdProxArgs a;
+FwdArgs make_fwd_args(const pat_geometry* g, const float* img) {
+    FwdArgs a;
+    memset(&a, 0, sizeof a);
     a.g = g->view;
-    a.ubar_quad = ubar_quad;
-    a.q = q;
-    a.f = f;
-    a.sig_q = sig_q;
-    a.sig_scalar = sig_scalar;
-    a.step_mul = step_mul;
-    a.qw = qw;
-    a.qmax_bits = qmax_bits;
-    a.stop = stop;
+    a.img = img;
     return a;
 }
 
-FwdGapArgs make_fwd_gap_args(const pat_geometry* g, const float* u, const float4* u_quad, const float* q,
-                             const float* f, double* partials, const int* stop) {
-    FwdGapArgs a;
-    a.g = g->view;
-    a.u = u;
-    a.u_quad = u_quad;
-    a.q = q;
-    a.f = f;
-    a.partials = partials;
-    a.stop = stop;
-    return a;
+int forward_smem_bytes(int rows, int stride, int M, int D, bool staged) {
+    return fwd_smem_layout(rows, stride, M, D, staged).total;
 }
 
-int launch_forward_prox_b(const FwdProxArgs* args, const int2* map, int nblocks, cudaStream_t st) {
-    if (nblocks <= 0) return PAT_OK;
-    prof_mark(PAT_PHASE_FORWARD_PROX, st, true);
-    k_forward_prox_b<<<nblocks, ROW_THREADS, 0, st>>>(args, map);
-    PAT_LAUNCH_CHECK("k_forward_prox_b");
-    prof_mark(PAT_PHASE_FORWARD_PROX, st, false);
+// K launches may use up to FWD_SMEM_ONE bytes of dynamic shared memory; the attribute is
+// set once per kernel and device.
+static int forward_attributes() {
+    static std::mutex mtx;
+    static bool done[64] = {};
+    int dev = 0;
+    PAT_CUDA(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mtx);
+    if (dev >= 0 && dev < 64 && done[dev]) return PAT_OK;
+    constexpr int smem = FWD_SMEM_ONE;
+    PAT_CUDA(cudaFuncSetAttribute(k_forward_b<FWD_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PAT_CUDA(cudaFuncSetAttribute(k_forward_b<FWD_PROX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    PAT_CUDA(cudaFuncSetAttribute(k_forward_b<FWD_GAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    if (dev >= 0 && dev < 64) done[dev] = true;
     return PAT_OK;
 }
 
-int launch_forward_gap_b(const FwdGapArgs* args, const int2* map, int nblocks, cudaStream_t st) {
+static cudaLaunchConfig_t forward_config(int nblocks, int cluster, int smem, cudaStream_t st,
+                                         cudaLaunchAttribute* attr) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)nblocks);
+    cfg.blockDim = dim3(SLAB_THREADS);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cfg.stream = st;
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)cluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+int forward_clusters_per_gpu(int cluster, int smem) {
+    int n = 0;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = forward_config(cluster, cluster, smem, nullptr, attr);
+    if (forward_attributes() != PAT_OK ||
+        cudaOccupancyMaxActiveClusters(&n, (const void*)k_forward_b<FWD_PROX>, &cfg) != cudaSuccess || n < 1) {
+        cudaGetLastError();
+        n = std::max(1, sm_count() * (smem <= FWD_SMEM_TWO ? 2 : 1) / cluster);
+    }
+    return n;
+}
+
+int launch_forward_b(int epi, const FwdArgs* args, const int2* map, int nblocks, int cluster, int smem,
+                     cudaStream_t st) {
     if (nblocks <= 0) return PAT_OK;
-    k_forward_gap_b<<<nblocks, ROW_THREADS, 0, st>>>(args, map);
-    PAT_LAUNCH_CHECK("k_forward_gap_b");
+    const int arc = forward_attributes();
+    if (arc) return arc;
+    cudaLaunchAttribute attr[1];
+    cudaLaunchConfig_t cfg = forward_config(nblocks, cluster, smem, st, attr);
+    if (epi == FWD_PROX) prof_mark(PAT_PHASE_FORWARD_PROX, st, true);
+    cudaError_t e;
+    if (epi == FWD_Y)
+        e = cudaLaunchKernelEx(&cfg, k_forward_b<FWD_Y>, args, map);
+    else if (epi == FWD_PROX)
+        e = cudaLaunchKernelEx(&cfg, k_forward_b<FWD_PROX>, args, map);
+    else
+        e = cudaLaunchKernelEx(&cfg, k_forward_b<FWD_GAP>, args, map);
+    count_launch();
+    if (e != cudaSuccess) return cuda_fail(e, "k_forward_b");
+    if (epi == FWD_PROX) prof_mark(PAT_PHASE_FORWARD_PROX, st, false);
     return PAT_OK;
+}
+
+int launch_forward(const pat_geometry* g, const float* u, float* y, cudaStream_t st) {
+    const int nc = g->fwd_n_ctas;
+    const size_t map_off = (sizeof(FwdArgs) + 255) & ~(size_t)255;
+    const size_t bytes = map_off + (size_t)nc * sizeof(int2);
+    char* buf = nullptr;
+    PAT_CUDA(cudaMallocAsync((void**)&buf, bytes, st));
+    FwdArgs a = make_fwd_args(g, u);
+    a.y = y;
+    std::vector<int2> map(nc);
+    for (int i = 0; i < nc; ++i) map[i] = make_int2(0, i);
+    int rc = PAT_OK;
+    cudaError_t e = cudaMemcpyAsync(buf, &a, sizeof a, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(buf + map_off, map.data(), (size_t)nc * sizeof(int2), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) rc = cuda_fail(e, "launch_forward: arguments");
+    // (copies from pageable host memory are staged before cudaMemcpyAsync returns, so the
+    // host arguments may go out of scope)
+    if (!rc)
+        rc = launch_forward_b(FWD_Y, (const FwdArgs*)buf, (const int2*)(buf + map_off), nc, g->view.n_slabs,
+                              g->fwd_smem, st);
+    cudaFreeAsync(buf, st);
+    return rc;
 }
 
 int launch_absmax(const float* y, long long n, unsigned* out, cudaStream_t st) {
@@ -678,7 +797,7 @@ using namespace pat;
 
 extern "C" int pat_forward(const pat_geometry* g, const float* u_dev, float* y_dev, void* stream) {
     if (!g || !u_dev || !y_dev) return fail(PAT_ERR_INVALID_ARG, "pat_forward: NULL argument");
-    return launch_forward(g, u_dev, false, y_dev, (cudaStream_t)stream);
+    return launch_forward(g, u_dev, y_dev, (cudaStream_t)stream);
 }
 
 extern "C" int pat_adjoint(const pat_geometry* g, const float* y_dev, float* u_dev, void* stream) {

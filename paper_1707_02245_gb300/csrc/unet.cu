@@ -756,7 +756,7 @@ int pat_warm_start_state(const pat_geometry* g, const float* pred_dev, int out_c
     const long long S = (long long)g->desc.n_det * g->desc.n_t;
     NN_LAUNCH(k_state, NN, st, pred_dev, out_ch, NN, p->reg, (float)p->alpha, (float)(p->alpha * p->beta), x0_dev,
               y0_dev + S);
-    TRY(launch_forward(g, x0_dev, false, y0_dev, st));
+    TRY(launch_forward(g, x0_dev, y0_dev, st));
     NN_LAUNCH(k_sub_inplace, S, st, y0_dev, f_dev, S);
     return PAT_OK;
 }

@@ -111,7 +111,6 @@ __global__ void k_wav_primal(const WavPrimalArgs a) {
     const float ub = un + a.theta * (un - uo);
     a.u[gi] = un;
     a.ubar[gi] = ub;
-    a.ubar_pad[(gy + 1) * (N + 2) + gx + 1] = ub;
     a.kt_clear[gi] = 0;
 }
 
