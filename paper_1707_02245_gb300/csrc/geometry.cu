@@ -341,14 +341,23 @@ struct SlabPlan {
     long long evaluated = 0;
 };
 
+// images above this side use the global-memory variant of K
+// (on 16 x 512^2 batches the slab kernel, with its rounds of cluster barriers, measured
+// slower than the global variant: 584 against 501 us per launch)
+#ifndef PAT_FWD_SLAB_MAX_N
+#define PAT_FWD_SLAB_MAX_N 320
+#endif
+
 // Slab count S (= CTAs per cluster) and rows R of geometry d: the fewest slabs (at most
 // FWD_MAX_CLUSTER) whose CTA fits two per SM, else one per SM; budget_bytes > 0 instead
-// caps the staged image of a slab (for tests).  R = 0: the global-memory variant.
-static void slab_shape(const pat_geometry_desc& d, int budget_bytes, int& S, int& R, int& W, int& smem) {
+// caps the staged image of a slab (for tests).  R = 0: the global-memory variant.  With
+// check, a shape whose clusters the device cannot hold is skipped.
+static void slab_shape(const pat_geometry_desc& d, int budget_bytes, int& S, int& R, int& W, int& smem,
+                       bool check = false) {
     const int N = d.n, M = d.quad_m, D = d.n_det;
     W = (N + 6 + 3) / 4 * 4;   // columns -1 .. N + 1 at floats 3 .. N + 5
     if (W % 8 == 0) W += 4;   // W = 4 mod 8: 8 consecutive rows start in 8 different bank groups
-    const bool staged = M <= FWD_STAGE_MAX && D <= FWD_STAGE_MAX;
+    const bool staged = M <= FWD_STAGE_MAX && D <= FWD_STAGE_MAX && N <= PAT_FWD_SLAB_MAX_N;
     const int budgets[2] = {FWD_SMEM_TWO, FWD_SMEM_ONE};
     for (int bi = 0; bi < 2 && staged; ++bi)
         for (int s = 1; s <= FWD_MAX_CLUSTER; ++s) {
@@ -357,7 +366,7 @@ static void slab_shape(const pat_geometry_desc& d, int budget_bytes, int& S, int
             const int need = forward_smem_bytes(r, W, M, D, true);
             const bool fits = budget_bytes > 0 ? (r + 1) * W * 4 <= budget_bytes && need <= FWD_SMEM_ONE
                                                : need <= budgets[bi];
-            if (fits) {
+            if (fits && (!check || forward_clusters_per_gpu(s, need) > 0)) {
                 S = s;
                 R = r;
                 smem = need;
@@ -444,9 +453,9 @@ static void build_slab_plan(const pat_geometry_desc& d, const PointTables& pt, c
         for (int s = 0; s < S; ++s) rg_total[rg] += cost(rg, s);
     std::vector<int> order(n_rg);
     for (int i = 0; i < n_rg; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return rg_total[x] > rg_total[y]; });
     std::vector<double> load((size_t)n_clusters * S, 0.0);
     std::vector<std::vector<int>> members(n_clusters);
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return rg_total[x] > rg_total[y]; });
     for (int rg : order) {
         int best = 0;
         double best_max = 1e300;
@@ -766,8 +775,8 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     SlabPlan sp;
     {
         int S, R, W, smem;
-        slab_shape(d, 0, S, R, W, smem);
-        build_slab_plan(d, pt, win, forward_clusters_per_gpu(S, smem), 0, sp);
+        slab_shape(d, 0, S, R, W, smem, true);
+        build_slab_plan(d, pt, win, std::max(1, forward_clusters_per_gpu(S, smem)), 0, sp);
     }
     g->points_per_apply = sp.evaluated;
     g->fwd_evaluated = sp.evaluated;
@@ -857,9 +866,9 @@ extern "C" int pat_forward_plan(const pat_geometry_desc* desc, int budget_bytes,
     if (budget_bytes < 0 || budget_bytes > FWD_SMEM_ONE)
         return fail(PAT_ERR_INVALID_ARG, "pat_forward_plan: budget exceeds the K CTA's shared memory");
     int S, R, W, smem;
-    slab_shape(*desc, budget_bytes, S, R, W, smem);
+    slab_shape(*desc, budget_bytes, S, R, W, smem, sms <= 0);
     const int clusters = sms > 0 ? std::max(1, sms * (smem <= FWD_SMEM_TWO ? 2 : 1) / S)
-                                 : forward_clusters_per_gpu(S, smem);
+                                 : std::max(1, forward_clusters_per_gpu(S, smem));
     const PointTables pt = point_tables(*desc);
     const std::vector<int2> win = grid_windows(*desc, pt, nullptr);
     SlabPlan sp;

@@ -61,7 +61,7 @@ void prof_collect();
 // two circular angular windows) into its shared accumulators; after a cluster barrier the
 // rows' S partial sums are added in rank order through distributed shared memory and the
 // epilogue runs.  slab_rows = 0 marks the global-memory variant (S = 1, no staging) used
-// when the image does not fit a cluster of at most 8 CTAs.
+// when the image does not fit a cluster of at most FWD_MAX_CLUSTER CTAs.
 struct GeomView {
     int n, n_det, n_t, quad_m;
     int n_kgrp;          // k groups of KGRP consecutive radii per detector
@@ -94,7 +94,7 @@ constexpr int KGRP = 8;        // radii per angular-window group
 constexpr int SLAB_THREADS = 512;                // threads of a K CTA
 constexpr int FWD_SMEM_TWO = 112 * 1024;         // dynamic shared memory of a K CTA, two per SM
 constexpr int FWD_SMEM_ONE = 220 * 1024;         // ... one per SM
-constexpr int FWD_MAX_CLUSTER = 8;               // portable cluster size
+constexpr int FWD_MAX_CLUSTER = 16;              // largest (non-portable) cluster size
 constexpr int FWD_ROUND = 256;                   // row groups of a cluster per round
 constexpr int FWD_STAGE_MAX = 1024;              // slabs need the cs and det tables staged: M, D <= this
 constexpr int MAX_QUAD_M = 8192;

@@ -584,6 +584,10 @@ static int forward_attributes() {
     PAT_CUDA(cudaFuncSetAttribute(k_forward_b<FWD_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     PAT_CUDA(cudaFuncSetAttribute(k_forward_b<FWD_PROX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
     PAT_CUDA(cudaFuncSetAttribute(k_forward_b<FWD_GAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    // clusters of more than 8 CTAs (up to FWD_MAX_CLUSTER) where the device allows them
+    for (const void* k : {(const void*)k_forward_b<FWD_Y>, (const void*)k_forward_b<FWD_PROX>,
+                          (const void*)k_forward_b<FWD_GAP>})
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
     if (dev >= 0 && dev < 64) done[dev] = true;
     return PAT_OK;
 }
@@ -609,11 +613,11 @@ int forward_clusters_per_gpu(int cluster, int smem) {
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = forward_config(cluster, cluster, smem, nullptr, attr);
     if (forward_attributes() != PAT_OK ||
-        cudaOccupancyMaxActiveClusters(&n, (const void*)k_forward_b<FWD_PROX>, &cfg) != cudaSuccess || n < 1) {
+        cudaOccupancyMaxActiveClusters(&n, (const void*)k_forward_b<FWD_PROX>, &cfg) != cudaSuccess) {
         cudaGetLastError();
-        n = std::max(1, sm_count() * (smem <= FWD_SMEM_TWO ? 2 : 1) / cluster);
+        n = 0;
     }
-    return n;
+    return n;   // 0: clusters of this shape cannot run on the device
 }
 
 int launch_forward_b(int epi, const FwdArgs* args, const int2* map, int nblocks, int cluster, int smem,

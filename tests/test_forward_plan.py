@@ -55,7 +55,7 @@ def _check_plan(n, det_xy, n_t, r0, dr, quad_m, sms, budget=0, extent=(-1.0, 1.0
     D, T, M = det_xy.shape[0], n_t, quad_m
     n_kgrp = (T + KGRP - 1) // KGRP
     S, R, W = plan["slabs"], plan["rows"], plan["stride"]
-    assert 1 <= S <= 8
+    assert 1 <= S <= 16
     if R > 0:
         assert S * R >= n + 1 and (S - 1) * R < n + 1            # the slabs cover j0 in [-1, N-1]
         if budget:
