@@ -168,6 +168,8 @@ static void free_tables(pat_geometry* g) {
     cudaFree(g->pc.kcol);
     cudaFree(g->pc.tile_kmax);
     cudaFree(g->adj_rays);
+    cudaFree(g->adj_ray_geo);
+    g->adj_ray_geo = nullptr;
     cudaFree(g->adj_item);
     cudaFree(g->fwd_units);
     cudaFree(g->fwd_ctas);
@@ -816,6 +818,16 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     upload((void**)&g->fwd_rgs, sp.rgs.data(), sizeof(int) * sp.rgs.size());
     if (e == cudaSuccess) e = cudaMalloc(&g->adj_rays, sizeof(int4) * rays.size());
     if (e == cudaSuccess) e = cudaMemcpy(g->adj_rays, rays.data(), sizeof(int4) * rays.size(), cudaMemcpyHostToDevice);
+    {
+        // each segment's detector and direction next to it, so the K^T staging reads them
+        // in one coalesced pass (sentinels get zeros)
+        std::vector<float4> geo(rays.size());
+        for (size_t i = 0; i < rays.size(); ++i)
+            geo[i] = rays[i].x >= 0 ? make_float4(det[rays[i].x].x, det[rays[i].x].y, cs[rays[i].y].x, cs[rays[i].y].y)
+                                    : make_float4(0.f, 0.f, 0.f, 0.f);
+        if (e == cudaSuccess) e = cudaMalloc(&g->adj_ray_geo, sizeof(float4) * geo.size());
+        if (e == cudaSuccess) e = cudaMemcpy(g->adj_ray_geo, geo.data(), sizeof(float4) * geo.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = cudaMalloc(&g->adj_item, sizeof(AdjItem) * items.size());
     if (e == cudaSuccess)
         e = cudaMemcpy(g->adj_item, items.data(), sizeof(AdjItem) * items.size(), cudaMemcpyHostToDevice);
