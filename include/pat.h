@@ -80,6 +80,30 @@ typedef struct {
 int  pat_create_geometry(const pat_geometry_desc* desc, pat_geometry** out);
 void pat_destroy_geometry(pat_geometry* g);              /* NULL is ignored; synchronises */
 
+/* Launch shapes of a geometry's kernels (the engineering of the hot path, not Sec. 3).
+ * Every shape computes the same operators; K variants may differ in the FP32 rounding of
+ * a row's sum (different partial-sum orders), K^T waves and update tiles give the same
+ * bits.  pat_tune_shapes picks them by timing; pat_create_geometry starts with
+ * {PAT_FWD_AUTO resolved, 1, PAT_UPD_32X4}. */
+#define PAT_FWD_AUTO      -1  /* slab kernel for images up to 320 pixels, else global       */
+#define PAT_FWD_SLAB_TWO   0  /* K: image slabs in shared memory, two CTAs per SM           */
+#define PAT_FWD_SLAB_ONE   1  /* K: image slabs in shared memory, one CTA per SM            */
+#define PAT_FWD_GLOBAL     2  /* K: taps read from global memory                            */
+#define PAT_UPD_32X4       0  /* fused update tile of 32 x 4 pixels                         */
+#define PAT_UPD_32X8       1  /* 32 x 8                                                     */
+#define PAT_UPD_64X4       2  /* 64 x 4                                                     */
+typedef struct {
+    int forward;        /* PAT_FWD_*; get returns the variant in use (AUTO resolved; a slab
+                           variant that does not fit the device falls back to GLOBAL)      */
+    int adjoint_waves;  /* K^T work items fill this many waves of resident CTAs, 1..4     */
+    int update_tile;    /* PAT_UPD_*                                                        */
+} pat_shapes;
+/* Rebuilds the geometry's K plan and K^T work list for the shapes.  The call waits for the
+ * device to be idle; no other call may use the geometry meanwhile. */
+int  pat_geometry_set_shapes(pat_geometry* g, const pat_shapes* s);
+int  pat_geometry_get_shapes(const pat_geometry* g, pat_shapes* s);
+
+
 /* y = K u.  u_dev: N*N floats, y_dev: D*T floats (overwritten). */
 int  pat_forward(const pat_geometry* g, const float* u_dev, float* y_dev, void* stream);
 
@@ -208,6 +232,17 @@ int  pat_tune_step_ratio(const pat_geometry* g, const float* f_dev, const pat_pa
 int  pat_tune_step_ratio_batched(int count, const pat_geometry* const* g, const float* const* f_dev,
                                  const pat_params* p, const double* candidates_host, int n_candidates,
                                  int probe_iters, double* best_host, double* rel_gaps_host, void* stream);
+
+/* Launch-shape autotuner for `count` problems (arrays as in pat_reconstruct_batched; the
+ * geometries' shapes are changed, so no other call may use them meanwhile).  For each
+ * geometry whose key (N, D, T, M, regulariser, GPU name) the JSON file cache_path (NULL:
+ * no cache) does not hold yet, the K variants, then the K^T waves (1, 2), then the update
+ * tiles are timed on that problem (20 iterations, then each candidate's phase in a CUDA
+ * graph of `reps` launches, as pat_time_phases) and the fastest of each is kept; cached
+ * keys are applied without timing, and new ones are added to the file.  chosen_host (may
+ * be NULL) receives each geometry's shapes.  Synchronises `stream`. */
+int  pat_tune_shapes(int count, pat_geometry* const* g, const float* const* f_dev, const pat_params* p, int reps,
+                     const char* cache_path, pat_shapes* chosen_host, void* stream);
 
 /* Box-restricted duality gap (Sec. 3.3.3, FP64 accumulation) of a primal point x and a
  * dual-feasible point y in the layouts of pat_params.  out4_host receives

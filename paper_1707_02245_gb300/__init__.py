@@ -37,7 +37,7 @@ EXPORTED = [
     "pat_adjoint_worklist",
     "pat_profile_enable", "pat_profile_read", "pat_kernel_launches", "pat_adjoint_noalloc",
     "pat_tune_step_ratio", "pat_tune_step_ratio_batched", "pat_preprocess", "pat_wavelet_transform",
-    "pat_time_phases", "pat_forward_plan",
+    "pat_time_phases", "pat_forward_plan", "pat_geometry_set_shapes", "pat_geometry_get_shapes", "pat_tune_shapes",
     # learned warm start (include/pat_unet.h)
     "pat_conv3x3_forward", "pat_conv3x3_backward_data", "pat_conv3x3_backward_weight",
     "pat_unet_create", "pat_unet_destroy", "pat_unet_num_params", "pat_unet_get_params",
@@ -72,6 +72,17 @@ class pat_params(ctypes.Structure):
                 ("y_out_dev", ctypes.c_void_p), ("step_ratio", ctypes.c_double), ("adapt", ctypes.c_int),
                 ("wavelet_levels", ctypes.c_int), ("x_lo0_dev", ctypes.c_void_p),
                 ("x_lo_out_dev", ctypes.c_void_p)]
+
+
+class pat_shapes(ctypes.Structure):
+    _fields_ = [("forward", ctypes.c_int), ("adjoint_waves", ctypes.c_int), ("update_tile", ctypes.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+PAT_FWD_AUTO, PAT_FWD_SLAB_TWO, PAT_FWD_SLAB_ONE, PAT_FWD_GLOBAL = -1, 0, 1, 2
+PAT_UPD_32X4, PAT_UPD_32X8, PAT_UPD_64X4 = 0, 1, 2
 
 
 class pat_unet_desc(ctypes.Structure):
@@ -126,6 +137,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
                                     ctypes.POINTER(d), vp]),
         "pat_time_phases": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(pat_params), i,
                                 ctypes.POINTER(d), vp]),
+        "pat_geometry_set_shapes": (i, [vp, ctypes.POINTER(pat_shapes)]),
+        "pat_geometry_get_shapes": (i, [vp, ctypes.POINTER(pat_shapes)]),
+        "pat_tune_shapes": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(pat_params), i,
+                                ctypes.c_char_p, ctypes.POINTER(pat_shapes), vp]),
         "pat_error_string": (ctypes.c_char_p, [i]),
         "pat_last_error": (ctypes.c_char_p, []),
         "pat_geometry_info": (i, [vp, ctypes.POINTER(ctypes.c_longlong)]),
@@ -341,6 +356,32 @@ def pat_tune_step_ratio_batched(geoms, fs, params, candidates, probe_iters: int,
     _check(load().pat_tune_step_ratio_batched(n, G, F, Pp, C, c, probe_iters, best, gaps, _stream(stream)),
            "pat_tune_step_ratio_batched")
     return list(best), [list(gaps[i * c:(i + 1) * c]) for i in range(n)]
+
+
+def pat_geometry_set_shapes(g: int, forward: int = PAT_FWD_AUTO, adjoint_waves: int = 1,
+                            update_tile: int = PAT_UPD_32X4) -> None:
+    s = pat_shapes(forward, adjoint_waves, update_tile)
+    _check(load().pat_geometry_set_shapes(g, ctypes.byref(s)), "pat_geometry_set_shapes")
+
+
+def pat_geometry_get_shapes(g: int) -> dict:
+    s = pat_shapes()
+    _check(load().pat_geometry_get_shapes(g, ctypes.byref(s)), "pat_geometry_get_shapes")
+    return s.as_dict()
+
+
+def pat_tune_shapes(geoms, fs, params, reps: int = 50, cache_path=None, stream=None) -> list:
+    """Times the launch-shape candidates of every geometry on its problem (see
+    include/pat.h), keeps the fastest, caches them in the JSON file cache_path and returns
+    the chosen shapes per problem."""
+    n = len(geoms)
+    G = (ctypes.c_void_p * n)(*geoms)
+    F = (ctypes.c_void_p * n)(*[_ptr(f) for f in fs])
+    Pp = (pat_params * n)(*params)
+    out = (pat_shapes * n)()
+    path = cache_path.encode() if cache_path else None
+    _check(load().pat_tune_shapes(n, G, F, Pp, int(reps), path, out, _stream(stream)), "pat_tune_shapes")
+    return [out[i].as_dict() for i in range(n)]
 
 
 def pat_time_phases(geoms, fs, params, reps: int, stream=None) -> dict:

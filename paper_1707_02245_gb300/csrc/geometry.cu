@@ -350,18 +350,23 @@ struct SlabPlan {
 #define PAT_FWD_SLAB_MAX_N 320
 #endif
 
-// Slab count S (= CTAs per cluster) and rows R of geometry d: the fewest slabs (at most
-// FWD_MAX_CLUSTER) whose CTA fits two per SM, else one per SM; budget_bytes > 0 instead
-// caps the staged image of a slab (for tests).  R = 0: the global-memory variant.  With
-// check, a shape whose clusters the device cannot hold is skipped.
+// Slab count S (= CTAs per cluster) and rows R of geometry d for a K variant:
+//  PAT_FWD_SLAB_TWO: the fewest slabs (at most FWD_MAX_CLUSTER) whose CTA fits two per SM;
+//  PAT_FWD_SLAB_ONE: ... one per SM;
+//  PAT_FWD_AUTO: the first of the two that fits, for images up to PAT_FWD_SLAB_MAX_N;
+//  PAT_FWD_GLOBAL, or no slab shape fits: R = 0, the global-memory variant.
+// budget_bytes > 0 instead caps the staged image of a slab (for tests).  With check, a
+// shape whose clusters the device cannot hold is skipped.
 static void slab_shape(const pat_geometry_desc& d, int budget_bytes, int& S, int& R, int& W, int& smem,
-                       bool check = false) {
+                       bool check = false, int variant = PAT_FWD_AUTO) {
     const int N = d.n, M = d.quad_m, D = d.n_det;
     W = (N + 6 + 3) / 4 * 4;   // columns -1 .. N + 1 at floats 3 .. N + 5
     if (W % 8 == 0) W += 4;   // W = 4 mod 8: 8 consecutive rows start in 8 different bank groups
-    const bool staged = M <= FWD_STAGE_MAX && D <= FWD_STAGE_MAX && N <= PAT_FWD_SLAB_MAX_N;
+    const bool staged = M <= FWD_STAGE_MAX && D <= FWD_STAGE_MAX &&
+                        (variant != PAT_FWD_AUTO || N <= PAT_FWD_SLAB_MAX_N) && variant != PAT_FWD_GLOBAL;
     const int budgets[2] = {FWD_SMEM_TWO, FWD_SMEM_ONE};
-    for (int bi = 0; bi < 2 && staged; ++bi)
+    for (int bi = 0; bi < 2 && staged; ++bi) {
+        if ((variant == PAT_FWD_SLAB_TWO && bi != 0) || (variant == PAT_FWD_SLAB_ONE && bi != 1)) continue;
         for (int s = 1; s <= FWD_MAX_CLUSTER; ++s) {
             const int r = (N + 1 + s - 1) / s;
             if (r < 8) break;
@@ -375,6 +380,7 @@ static void slab_shape(const pat_geometry_desc& d, int budget_bytes, int& S, int
                 return;
             }
         }
+    }
     S = 1;
     R = 0;
     smem = forward_smem_bytes(0, W, M, D, false);
@@ -390,12 +396,13 @@ static void slab_shape(const pat_geometry_desc& d, int budget_bytes, int& S, int
 //    least loaded; each cluster's list is shuffled (a fixed generator) so that every round
 //    mixes detectors from all sides, and cut into rounds of FWD_ROUND.
 static void build_slab_plan(const pat_geometry_desc& d, const PointTables& pt, const std::vector<int2>& win,
-                            int n_clusters, int budget_bytes, SlabPlan& sp) {
+                            int n_clusters, int budget_bytes, SlabPlan& sp, int variant = PAT_FWD_AUTO,
+                            bool check = false) {
     const int N = d.n, D = d.n_det, T = d.n_t, M = d.quad_m;
     const int n_kgrp = (T + KGRP - 1) / KGRP, n_rg = D * n_kgrp;
     const double hx = (d.xmax - d.xmin) / N, hy = (d.ymax - d.ymin) / N;
     int S, R, W, smem;
-    slab_shape(d, budget_bytes, S, R, W, smem);
+    slab_shape(d, budget_bytes, S, R, W, smem, check, variant);
     sp.slabs = S;
     sp.rows = R;
     sp.stride = W;
@@ -519,7 +526,8 @@ struct AdjWork {
 };
 
 // The K^T work list of geometry d for a GPU that holds `slots` K^T CTAs at once.
-static int adjoint_worklist(const pat_geometry_desc& d, const PointTables& pt, double slots, AdjWork& w) {
+static int adjoint_worklist(const pat_geometry_desc& d, const PointTables& pt, double slots, AdjWork& w,
+                            int waves = ADJ_WAVES) {
     const int N = d.n, D = d.n_det, T = d.n_t, M = d.quad_m;
     const double hx = (d.xmax - d.xmin) / N, hy = (d.ymax - d.ymin) / N;
     const double ex = 1e-3 * hx, ey = 1e-3 * hy;
@@ -637,10 +645,10 @@ static int adjoint_worklist(const pat_geometry_desc& d, const PointTables& pt, d
         long long total = 0;
         for (int t = 0; t < tiles; ++t) total += tile_total[t];
         w.candidates = total;
-        // pieces per tile: ADJ_WAVES waves of resident CTAs (at least 1024 candidates a piece),
+        // pieces per tile: `waves` waves of resident CTAs (at least 1024 candidates a piece),
         // each piece going to the tile whose pieces are largest at that point, which
         // minimises the largest piece
-        const long long Q = std::max(1LL, std::min((long long)(ADJ_WAVES * slots), total / 1024));
+        const long long Q = std::max(1LL, std::min((long long)(waves * slots), total / 1024));
         std::vector<long long> n_piece(tiles, 0);
         {
             std::priority_queue<std::pair<double, int>> heap;   // (piece size, tile)
@@ -745,6 +753,110 @@ static std::vector<int2> grid_windows(const pat_geometry_desc& d, const PointTab
     return win;
 }
 
+// Builds the K plan of geometry g for `variant` and installs it (device arrays and view),
+// replacing a previous plan.  The caller makes sure no work on g is in flight.
+static int install_forward_plan(pat_geometry* g, const PointTables& pt, int variant) {
+    const pat_geometry_desc& d = g->desc;
+    pat_geometry_desc dd = d;
+    dd.det_xy_host = g->det_xy.data();
+    SlabPlan sp;
+    {
+        int S, R, W, smem;
+        slab_shape(dd, 0, S, R, W, smem, true, variant);
+        build_slab_plan(dd, pt, g->win_host, std::max(1, forward_clusters_per_gpu(S, smem)), 0, sp, variant, true);
+    }
+    int4 *units = nullptr, *ctas = nullptr;
+    int *roff = nullptr, *rgs = nullptr;
+    cudaError_t e = cudaSuccess;
+    auto upload = [&](void** dst, const void* src, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
+        if (e == cudaSuccess && bytes) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+    };
+    upload((void**)&units, sp.units.data(), sizeof(int4) * sp.units.size());
+    upload((void**)&ctas, sp.ctas.data(), sizeof(int4) * sp.ctas.size());
+    upload((void**)&roff, sp.roff.data(), sizeof(int) * sp.roff.size());
+    upload((void**)&rgs, sp.rgs.data(), sizeof(int) * sp.rgs.size());
+    if (e != cudaSuccess) {
+        cudaFree(units);
+        cudaFree(ctas);
+        cudaFree(roff);
+        cudaFree(rgs);
+        return cuda_fail(e, "K plan upload");
+    }
+    cudaFree(g->fwd_units);
+    cudaFree(g->fwd_ctas);
+    cudaFree(g->fwd_roff);
+    cudaFree(g->fwd_rgs);
+    g->fwd_units = units;
+    g->fwd_ctas = ctas;
+    g->fwd_roff = roff;
+    g->fwd_rgs = rgs;
+    g->points_per_apply = sp.evaluated;
+    g->fwd_evaluated = sp.evaluated;
+    g->fwd_cluster_cost = sp.cluster_cost;
+    g->fwd_n_ctas = (int)sp.ctas.size();
+    g->fwd_smem = sp.smem;
+    g->shapes.forward = sp.rows > 0 ? (sp.smem <= FWD_SMEM_TWO ? PAT_FWD_SLAB_TWO : PAT_FWD_SLAB_ONE) : PAT_FWD_GLOBAL;
+    GeomView& v = g->view;
+    v.n_slabs = sp.slabs;
+    v.slab_rows = sp.rows;
+    v.slab_stride = sp.stride;
+    v.smem_bytes = sp.smem;
+    v.units = g->fwd_units;
+    v.ctas = g->fwd_ctas;
+    v.roff = g->fwd_roff;
+    v.rgs = g->fwd_rgs;
+    return PAT_OK;
+}
+
+// Builds the K^T work list of geometry g for work items that fill `waves` waves of
+// resident CTAs and installs it, replacing a previous one.  No work on g may be in flight.
+static int install_adjoint_plan(pat_geometry* g, const PointTables& pt, int waves) {
+    pat_geometry_desc dd = g->desc;
+    dd.det_xy_host = g->det_xy.data();
+    AdjWork aw;
+    const int rc = adjoint_worklist(dd, pt, (double)sm_count() * adjoint_blocks_per_sm(), aw, waves);
+    if (rc) return rc;
+    const std::vector<int4>& rays = aw.rays;
+    const std::vector<AdjItem>& items = aw.items;
+    // each segment's detector and direction next to it, so the K^T staging reads them in
+    // one coalesced pass (sentinels get zeros)
+    std::vector<float4> geo(rays.size());
+    for (size_t i = 0; i < rays.size(); ++i)
+        geo[i] = rays[i].x >= 0
+                     ? make_float4(pt.det[rays[i].x].x, pt.det[rays[i].x].y, pt.cs[rays[i].y].x, pt.cs[rays[i].y].y)
+                     : make_float4(0.f, 0.f, 0.f, 0.f);
+    int4* r_dev = nullptr;
+    float4* geo_dev = nullptr;
+    AdjItem* it_dev = nullptr;
+    cudaError_t e = cudaMalloc(&r_dev, sizeof(int4) * std::max<size_t>(rays.size(), 1));
+    if (e == cudaSuccess) e = cudaMemcpy(r_dev, rays.data(), sizeof(int4) * rays.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&geo_dev, sizeof(float4) * std::max<size_t>(geo.size(), 1));
+    if (e == cudaSuccess) e = cudaMemcpy(geo_dev, geo.data(), sizeof(float4) * geo.size(), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMalloc(&it_dev, sizeof(AdjItem) * std::max<size_t>(items.size(), 1));
+    if (e == cudaSuccess) e = cudaMemcpy(it_dev, items.data(), sizeof(AdjItem) * items.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(r_dev);
+        cudaFree(geo_dev);
+        cudaFree(it_dev);
+        return cuda_fail(e, "K^T work list upload");
+    }
+    cudaFree(g->adj_rays);
+    cudaFree(g->adj_ray_geo);
+    cudaFree(g->adj_item);
+    g->adj_rays = r_dev;
+    g->adj_ray_geo = geo_dev;
+    g->adj_item = it_dev;
+    g->adj_tiles_x = aw.tiles_x;
+    g->adj_tiles = aw.tiles;
+    g->adj_wtiles_x = aw.wtiles_x;
+    g->adj_candidates = aw.candidates;
+    g->adj_item_cost = aw.cost;
+    g->adj_items = (int)items.size();
+    g->shapes.adjoint_waves = waves;
+    return PAT_OK;
+}
+
 extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry** out) {
     if (!desc || !out) return fail(PAT_ERR_INVALID_ARG, "pat_create_geometry: NULL argument");
     *out = nullptr;
@@ -758,83 +870,24 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     cudaGetDevice(&g->device);
 
     const int N = d.n, D = d.n_det, T = d.n_t, M = d.quad_m;
-    const double hx = (d.xmax - d.xmin) / N, hy = (d.ymax - d.ymin) / N;
     const int n_kgrp = (T + KGRP - 1) / KGRP;
-
     const PointTables pt = point_tables(d);
-    const std::vector<float2>& det = pt.det;
-    const std::vector<float2>& cs = pt.cs;
-    const std::vector<float>& rk = pt.rk;
-    const std::vector<float>& wk = pt.wk;
-    const std::vector<double>& cosd = pt.cosd;
-    const std::vector<double>& sind = pt.sind;
-    const std::vector<double>& rd = pt.rd;
 
     // angular windows of every (detector, radius group) over the grid
     long long on_grid = 0;
-    const std::vector<int2> win = grid_windows(d, pt, &on_grid);
+    g->win_host = grid_windows(d, pt, &on_grid);
     g->points_on_grid = on_grid;
-    SlabPlan sp;
-    {
-        int S, R, W, smem;
-        slab_shape(d, 0, S, R, W, smem, true);
-        build_slab_plan(d, pt, win, std::max(1, forward_clusters_per_gpu(S, smem)), 0, sp);
-    }
-    g->points_per_apply = sp.evaluated;
-    g->fwd_evaluated = sp.evaluated;
-    g->fwd_cluster_cost = sp.cluster_cost;
-    g->fwd_n_ctas = (int)sp.ctas.size();
+    const std::vector<int2>& win = g->win_host;
 
-    AdjWork aw;
-    {
-        const int rc = adjoint_worklist(d, pt, (double)sm_count() * adjoint_blocks_per_sm(), aw);
-        if (rc) {
-            delete g;
-            return rc;
-        }
-    }
-    g->adj_tiles_x = aw.tiles_x;
-    g->adj_tiles = aw.tiles;
-    g->adj_wtiles_x = aw.wtiles_x;
-    g->adj_candidates = aw.candidates;
-    g->adj_item_cost = aw.cost;
-    const std::vector<int4>& rays = aw.rays;
-    const std::vector<AdjItem>& items = aw.items;
-    g->adj_items = (int)items.size();
-
-    cudaError_t e = cudaSuccess;
-    e = cudaMalloc(&g->det, sizeof(float2) * D);
+    cudaError_t e = cudaMalloc(&g->det, sizeof(float2) * D);
     if (e == cudaSuccess) e = cudaMalloc(&g->cs, sizeof(float2) * M);
     if (e == cudaSuccess) e = cudaMalloc(&g->rk, sizeof(float) * T);
     if (e == cudaSuccess) e = cudaMalloc(&g->wk, sizeof(float) * T);
     if (e == cudaSuccess) e = cudaMalloc(&g->win, sizeof(int2) * win.size());
-    auto upload = [&](void** dst, const void* src, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMalloc(dst, std::max<size_t>(bytes, 16));
-        if (e == cudaSuccess && bytes) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
-    };
-    upload((void**)&g->fwd_units, sp.units.data(), sizeof(int4) * sp.units.size());
-    upload((void**)&g->fwd_ctas, sp.ctas.data(), sizeof(int4) * sp.ctas.size());
-    upload((void**)&g->fwd_roff, sp.roff.data(), sizeof(int) * sp.roff.size());
-    upload((void**)&g->fwd_rgs, sp.rgs.data(), sizeof(int) * sp.rgs.size());
-    if (e == cudaSuccess) e = cudaMalloc(&g->adj_rays, sizeof(int4) * rays.size());
-    if (e == cudaSuccess) e = cudaMemcpy(g->adj_rays, rays.data(), sizeof(int4) * rays.size(), cudaMemcpyHostToDevice);
-    {
-        // each segment's detector and direction next to it, so the K^T staging reads them
-        // in one coalesced pass (sentinels get zeros)
-        std::vector<float4> geo(rays.size());
-        for (size_t i = 0; i < rays.size(); ++i)
-            geo[i] = rays[i].x >= 0 ? make_float4(det[rays[i].x].x, det[rays[i].x].y, cs[rays[i].y].x, cs[rays[i].y].y)
-                                    : make_float4(0.f, 0.f, 0.f, 0.f);
-        if (e == cudaSuccess) e = cudaMalloc(&g->adj_ray_geo, sizeof(float4) * geo.size());
-        if (e == cudaSuccess) e = cudaMemcpy(g->adj_ray_geo, geo.data(), sizeof(float4) * geo.size(), cudaMemcpyHostToDevice);
-    }
-    if (e == cudaSuccess) e = cudaMalloc(&g->adj_item, sizeof(AdjItem) * items.size());
-    if (e == cudaSuccess)
-        e = cudaMemcpy(g->adj_item, items.data(), sizeof(AdjItem) * items.size(), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->det, det.data(), sizeof(float2) * D, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->cs, cs.data(), sizeof(float2) * M, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->rk, rk.data(), sizeof(float) * T, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(g->wk, wk.data(), sizeof(float) * T, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->det, pt.det.data(), sizeof(float2) * D, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->cs, pt.cs.data(), sizeof(float2) * M, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->rk, pt.rk.data(), sizeof(float) * T, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(g->wk, pt.wk.data(), sizeof(float) * T, cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(g->win, win.data(), sizeof(int2) * win.size(), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
         int rc = cuda_fail(e, "pat_create_geometry: table upload");
@@ -842,7 +895,6 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
         delete g;
         return rc;
     }
-
     GeomView& v = g->view;
     v.n = N;
     v.n_det = D;
@@ -856,16 +908,43 @@ extern "C" int pat_create_geometry(const pat_geometry_desc* desc, pat_geometry**
     v.dr_f = (float)d.dr;
     v.rh_f = (float)(d.r0 + 0.5 * d.dr);
     v.win = g->win;
-    v.n_slabs = sp.slabs;
-    v.slab_rows = sp.rows;
-    v.slab_stride = sp.stride;
-    v.smem_bytes = sp.smem;
-    v.units = g->fwd_units;
-    v.ctas = g->fwd_ctas;
-    v.roff = g->fwd_roff;
-    v.rgs = g->fwd_rgs;
-    g->fwd_smem = sp.smem;
+    g->shapes.update_tile = PAT_UPD_32X4;
+    int rc = install_forward_plan(g, pt, PAT_FWD_AUTO);
+    if (!rc) rc = install_adjoint_plan(g, pt, ADJ_WAVES);
+    if (rc) {
+        free_tables(g);
+        delete g;
+        return rc;
+    }
     *out = g;
+    return PAT_OK;
+}
+
+extern "C" int pat_geometry_set_shapes(pat_geometry* g, const pat_shapes* s) {
+    if (!g || !s) return fail(PAT_ERR_INVALID_ARG, "pat_geometry_set_shapes: NULL argument");
+    if (s->forward < PAT_FWD_AUTO || s->forward > PAT_FWD_GLOBAL)
+        return fail(PAT_ERR_INVALID_ARG, "pat_geometry_set_shapes: unknown K variant");
+    if (s->adjoint_waves < 1 || s->adjoint_waves > 4)
+        return fail(PAT_ERR_INVALID_ARG, "pat_geometry_set_shapes: adjoint_waves must be in [1, 4]");
+    if (s->update_tile < PAT_UPD_32X4 || s->update_tile > PAT_UPD_64X4)
+        return fail(PAT_ERR_INVALID_ARG, "pat_geometry_set_shapes: unknown update tile");
+    int dev = 0;
+    PAT_CUDA(cudaGetDevice(&dev));
+    if (dev != g->device) return fail(PAT_ERR_INVALID_ARG, "pat_geometry_set_shapes: the geometry belongs to another device");
+    std::lock_guard<std::mutex> lock(g->mtx);
+    PAT_CUDA(cudaDeviceSynchronize());   // the old plans may still be read by queued work
+    pat_geometry_desc dd = g->desc;
+    dd.det_xy_host = g->det_xy.data();
+    const PointTables pt = point_tables(dd);
+    int rc = install_forward_plan(g, pt, s->forward);
+    if (!rc && s->adjoint_waves != g->shapes.adjoint_waves) rc = install_adjoint_plan(g, pt, s->adjoint_waves);
+    if (!rc) g->shapes.update_tile = s->update_tile;
+    return rc;
+}
+
+extern "C" int pat_geometry_get_shapes(const pat_geometry* g, pat_shapes* s) {
+    if (!g || !s) return fail(PAT_ERR_INVALID_ARG, "pat_geometry_get_shapes: NULL argument");
+    *s = g->shapes;
     return PAT_OK;
 }
 
@@ -884,7 +963,7 @@ extern "C" int pat_forward_plan(const pat_geometry_desc* desc, int budget_bytes,
     const PointTables pt = point_tables(*desc);
     const std::vector<int2> win = grid_windows(*desc, pt, nullptr);
     SlabPlan sp;
-    build_slab_plan(*desc, pt, win, clusters, budget_bytes, sp);
+    build_slab_plan(*desc, pt, win, clusters, budget_bytes, sp, PAT_FWD_AUTO, sms <= 0);
     info8_host[0] = sp.slabs;
     info8_host[1] = sp.rows;
     info8_host[2] = sp.stride;

@@ -149,6 +149,8 @@ struct pat_geometry {
     long long fwd_evaluated = 0;       // quadrature points inside the units' windows
     std::vector<float> fwd_cluster_cost; // points each K cluster's slowest CTA evaluates (host)
     std::vector<double> det_xy;        // detector positions (host copy, 2 per detector)
+    std::vector<int2> win_host;        // angular windows over the grid (host copy)
+    pat_shapes shapes{};               // launch shapes in use (see pat_geometry_set_shapes)
     pat::GeomView view;
     // lazily computed preconditioner sums
     mutable std::mutex mtx;

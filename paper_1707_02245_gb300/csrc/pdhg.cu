@@ -26,14 +26,10 @@
 
 namespace pat {
 
-#ifndef PAT_UPD_TX
-#define PAT_UPD_TX 32
-#endif
-#ifndef PAT_UPD_TY
-#define PAT_UPD_TY 4
-#endif
-constexpr int TX = PAT_UPD_TX, TY = PAT_UPD_TY;   // update tile
-constexpr int LX = TX + 2, LY = TY + 2;   // tile plus one-pixel halo on each side
+// update tiles (pat_shapes.update_tile): {TX, TY} of PAT_UPD_32X4, PAT_UPD_32X8, PAT_UPD_64X4
+constexpr int UPD_TILES = 3;
+constexpr int upd_tx(int t) { return t == PAT_UPD_64X4 ? 64 : 32; }
+constexpr int upd_ty(int t) { return t == PAT_UPD_32X8 ? 8 : 4; }
 
 struct UpdateArgs {
     int n;
@@ -64,8 +60,9 @@ __device__ __forceinline__ float ld_img(const float* __restrict__ p, int N, int 
 }
 
 // One PDHG primal step plus the following dual step on a TX x TY tile.
-template <int REG>
+template <int REG, int TX, int TY>
 __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, const int by, const bool first) {
+    constexpr int LX = TX + 2, LY = TY + 2;   // tile plus one-pixel halo on each side
     const int N = a.n;
     const size_t NN = (size_t)N * N;
     const int x0 = bx * TX, y0 = by * TY;
@@ -99,12 +96,15 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
     constexpr int NCELL = (LX * LY + TX * TY - 1) / (TX * TY);   // staged cells per thread
     const float tmul = __ldg(a.step_mul), smul = __ldg(a.step_mul + 1);
 
-    // fixed-point scales of the (at most 2 x 2) K^T tiles that the cells of U touch (the
-    // update tile lies inside one K^T tile; its high halo may reach the next ones)
-    __shared__ float s_kinv[2][2];
-    if (tid < 4) {
-        const int ktx = x0 / ATILE + (tid & 1), kty = y0 / ATILE + (tid >> 1);
-        s_kinv[tid >> 1][tid & 1] = (ktx * ATILE < N && kty * ATILE < N) ? a.kt.inv_scale(ktx, kty) : 0.f;
+    // fixed-point scales of the K^T tiles that the cells of U (tile + high halo) touch: the
+    // tile's sides divide or are multiples of ATILE, so U spans ceil(T / ATILE) + 1 of them
+    static_assert(ATILE % TX == 0 || TX % ATILE == 0, "update tiles align with K^T tiles in x");
+    static_assert(ATILE % TY == 0 || TY % ATILE == 0, "update tiles align with K^T tiles in y");
+    constexpr int KNX = (TX + ATILE - 1) / ATILE + 1, KNY = (TY + ATILE - 1) / ATILE + 1;
+    __shared__ float s_kinv[KNY][KNX];
+    if (tid < KNX * KNY) {
+        const int ktx = x0 / ATILE + tid % KNX, kty = y0 / ATILE + tid / KNX;
+        s_kinv[tid / KNX][tid % KNX] = (ktx * ATILE < N && kty * ATILE < N) ? a.kt.inv_scale(ktx, kty) : 0.f;
     }
 
     // ---- stage 1: dual fields on the tile plus halo -------------------------------
@@ -259,12 +259,13 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
     }
 }
 
-template <int REG>
-__global__ void __launch_bounds__(TX* TY) k_update_b(const UpdateArgs* __restrict__ args, const int2* __restrict__ map) {
+template <int REG, int TILE>
+__global__ void __launch_bounds__(upd_tx(TILE) * upd_ty(TILE)) k_update_b(const UpdateArgs* __restrict__ args,
+                                                                          const int2* __restrict__ map) {
     const int2 pm = map[blockIdx.x];
     const UpdateArgs& a = args[pm.x];
     if (a.stop && *(volatile const int*)a.stop) return;
-    update_tile<REG>(a, pm.y % a.tiles_x, pm.y / a.tiles_x, pm.y == 0);
+    update_tile<REG, upd_tx(TILE), upd_ty(TILE)>(a, pm.y % a.tiles_x, pm.y / a.tiles_x, pm.y == 0);
 }
 
 // Dual step r, s <- prox(r, s + Sigma (A_reg (ubar, vbar))) used once before the first
@@ -988,19 +989,30 @@ static UpdateArgs make_update_args(const Prob& pr, int par, bool gap_iter) {
     (void)gap_iter;
     a.stop = &ws.info->stop;
     a.iter = &ws.info->iter;
-    a.tiles_x = ceil_div(N, TX);
+    a.tiles_x = ceil_div(N, upd_tx(pr.g->shapes.update_tile));
     return a;
 }
 
-static int launch_update_b(int reg, const UpdateArgs* args, const int2* map, int n, cudaStream_t st) {
+template <int TILE>
+static void launch_update_tile(int reg, const UpdateArgs* args, const int2* map, int n, cudaStream_t st) {
+    const dim3 blk(upd_tx(TILE), upd_ty(TILE));
+    if (reg == PAT_TV)
+        k_update_b<PAT_TV, TILE><<<n, blk, 0, st>>>(args, map);
+    else if (reg == PAT_TGV)
+        k_update_b<PAT_TGV, TILE><<<n, blk, 0, st>>>(args, map);
+    else
+        k_update_b<PAT_DTV, TILE><<<n, blk, 0, st>>>(args, map);
+}
+
+static int launch_update_b(int reg, int tile, const UpdateArgs* args, const int2* map, int n, cudaStream_t st) {
     if (n <= 0) return PAT_OK;
     prof_mark(PAT_PHASE_UPDATE, st, true);
-    if (reg == PAT_TV)
-        k_update_b<PAT_TV><<<n, dim3(TX, TY), 0, st>>>(args, map);
-    else if (reg == PAT_TGV)
-        k_update_b<PAT_TGV><<<n, dim3(TX, TY), 0, st>>>(args, map);
+    if (tile == PAT_UPD_64X4)
+        launch_update_tile<PAT_UPD_64X4>(reg, args, map, n, st);
+    else if (tile == PAT_UPD_32X8)
+        launch_update_tile<PAT_UPD_32X8>(reg, args, map, n, st);
     else
-        k_update_b<PAT_DTV><<<n, dim3(TX, TY), 0, st>>>(args, map);
+        launch_update_tile<PAT_UPD_32X4>(reg, args, map, n, st);
     PAT_LAUNCH_CHECK("k_update_b");
     prof_mark(PAT_PHASE_UPDATE, st, false);
     return PAT_OK;
@@ -1031,9 +1043,9 @@ static int launch_gap_phase(const FwdArgs* fa, const GapArgs* ga, const FinalArg
 struct IterPlan {
     size_t fwd[2] = {0, 0}, adj[2] = {0, 0}, upd[2][2] = {{0, 0}, {0, 0}}, fgap[2] = {0, 0}, gpix[2] = {0, 0};
     size_t fin = 0, map_adj = 0;
-    size_t map_upd[3] = {0, 0, 0};
+    size_t map_upd[3][UPD_TILES] = {};
     int n_adj = 0;
-    int n_upd[3] = {0, 0, 0};
+    int n_upd[3][UPD_TILES] = {};
     GapPlan gp;
 };
 
@@ -1082,13 +1094,14 @@ static void build_iter_plan(const Prob* pr, int B, Arena& ar, IterPlan& ip, int*
     ip.fin = ar.put(fi.data(), fi.size());
     // maps: forward rows problem by problem; K^T items of all problems heaviest first;
     // update tiles grouped by regulariser
-    std::vector<int2> upd[3];
+    std::vector<int2> upd[3][UPD_TILES];
     std::vector<std::pair<float, int2>> adj;
     for (int b = 0; b < B; ++b) {
         const pat_geometry* g = pr[b].g;
         for (int i = 0; i < g->adj_items; ++i) adj.push_back({g->adj_item_cost[i], make_int2(b, i)});
-        const int N = g->desc.n, nt = ceil_div(N, TX) * ceil_div(N, TY);
-        for (int i = 0; i < nt; ++i) upd[pr[b].p.reg].push_back(make_int2(b, i));
+        const int tile = g->shapes.update_tile;
+        const int N = g->desc.n, nt = ceil_div(N, upd_tx(tile)) * ceil_div(N, upd_ty(tile));
+        for (int i = 0; i < nt; ++i) upd[pr[b].p.reg][tile].push_back(make_int2(b, i));
     }
     std::stable_sort(adj.begin(), adj.end(), [](const std::pair<float, int2>& x, const std::pair<float, int2>& y) {
         return x.first > y.first;
@@ -1097,10 +1110,11 @@ static void build_iter_plan(const Prob* pr, int B, Arena& ar, IterPlan& ip, int*
     for (auto& e : adj) adjm.push_back(e.second);
     ip.map_adj = ar.put(adjm.data(), adjm.size());
     ip.n_adj = (int)adjm.size();
-    for (int r = 0; r < 3; ++r) {
-        ip.map_upd[r] = ar.put(upd[r].data(), upd[r].size());
-        ip.n_upd[r] = (int)upd[r].size();
-    }
+    for (int r = 0; r < 3; ++r)
+        for (int t = 0; t < UPD_TILES; ++t) {
+            ip.map_upd[r][t] = ar.put(upd[r][t].data(), upd[r][t].size());
+            ip.n_upd[r][t] = (int)upd[r][t].size();
+        }
     build_gap_plan(pr, B, ar, ip.gp);
 }
 
@@ -1111,10 +1125,11 @@ static int enqueue_iteration(const IterPlan& ip, const char* base, int it, bool 
     rc = launch_adjoint_b((const AdjArgs*)(base + ip.adj[par]), (const int2*)(base + ip.map_adj), ip.n_adj, true, st);
     if (rc) return rc;
     const UpdateArgs* ua = (const UpdateArgs*)(base + ip.upd[par][gap_due ? 1 : 0]);
-    for (int r = 0; r < 3; ++r) {
-        rc = launch_update_b(r, ua, (const int2*)(base + ip.map_upd[r]), ip.n_upd[r], st);
-        if (rc) return rc;
-    }
+    for (int r = 0; r < 3; ++r)
+        for (int t = 0; t < UPD_TILES; ++t) {
+            rc = launch_update_b(r, t, ua, (const int2*)(base + ip.map_upd[r][t]), ip.n_upd[r][t], st);
+            if (rc) return rc;
+        }
     if (gap_due)
         rc = launch_gap_phase((const FwdArgs*)(base + ip.fgap[par]), (const GapArgs*)(base + ip.gpix[par]),
                               (const FinalArgs*)(base + ip.fin), ip.gp, base, st);
@@ -1760,10 +1775,11 @@ static int time_phases(int B, const pat_geometry* const* g, const float* const* 
                                         true, ls);
             if (ph == PAT_PHASE_UPDATE) {
                 const UpdateArgs* ua = (const UpdateArgs*)(base + ip.upd[0][0]);
-                for (int r = 0; r < 3; ++r) {
-                    const int e = launch_update_b(r, ua, (const int2*)(base + ip.map_upd[r]), ip.n_upd[r], ls);
-                    if (e) return e;
-                }
+                for (int r = 0; r < 3; ++r)
+                    for (int t = 0; t < UPD_TILES; ++t) {
+                        const int e = launch_update_b(r, t, ua, (const int2*)(base + ip.map_upd[r][t]), ip.n_upd[r][t], ls);
+                        if (e) return e;
+                    }
                 return PAT_OK;
             }
             return launch_gap_phase((const FwdArgs*)(base + ip.fgap[0]), (const GapArgs*)(base + ip.gpix[0]),
@@ -1813,6 +1829,137 @@ static int time_phases(int B, const pat_geometry* const* g, const float* const* 
     for (cudaEvent_t ev : {fork, join, e0, e1})
         if (ev) cudaEventDestroy(ev);
     return rc;
+}
+
+// ---------------------------------------------------------------------------------
+// Launch-shape autotuner: per geometry, each kernel's candidate shapes are timed on the
+// problem itself (phase timing in graphs, as pat_time_phases), one kernel at a time with
+// the others at their current choice, and the fastest is kept.  Choices are cached in a
+// JSON file keyed by (N, D, T, M, regulariser, GPU name).
+// ---------------------------------------------------------------------------------
+struct ShapeEntry {
+    std::string key;
+    pat_shapes s;
+    double us[3];   // K, K^T, update: microseconds per launch of the chosen shapes
+};
+
+static std::string shape_key(const pat_geometry* g, int reg) {
+    cudaDeviceProp prop;
+    std::string gpu = "unknown";
+    if (cudaGetDeviceProperties(&prop, g->device) == cudaSuccess) gpu = prop.name;
+    else cudaGetLastError();
+    for (char& c : gpu)
+        if (c == '"' || c == '\\') c = '_';
+    char buf[160];
+    snprintf(buf, sizeof buf, "N=%d D=%d T=%d M=%d reg=%d", g->desc.n, g->desc.n_det, g->desc.n_t, g->desc.quad_m, reg);
+    return std::string(buf) + " gpu=" + gpu;
+}
+
+// The cache holds one entry per line inside {"entries": [ ... ]}; lines that do not parse
+// are ignored.
+static std::vector<ShapeEntry> read_shape_cache(const char* path) {
+    std::vector<ShapeEntry> out;
+    FILE* fp = path ? fopen(path, "r") : nullptr;
+    if (!fp) return out;
+    char line[1024];
+    while (fgets(line, sizeof line, fp)) {
+        const char* k = strstr(line, "\"key\": \"");
+        if (!k) continue;
+        k += 8;
+        const char* e = strchr(k, '"');
+        if (!e) continue;
+        ShapeEntry se;
+        se.key.assign(k, e);
+        if (sscanf(e, "\", \"forward\": %d, \"adjoint_waves\": %d, \"update_tile\": %d, \"us\": [%lf, %lf, %lf]",
+                   &se.s.forward, &se.s.adjoint_waves, &se.s.update_tile, &se.us[0], &se.us[1], &se.us[2]) == 6)
+            out.push_back(se);
+    }
+    fclose(fp);
+    return out;
+}
+
+static int write_shape_cache(const char* path, const std::vector<ShapeEntry>& entries) {
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE* fp = fopen(tmp.c_str(), "w");
+    if (!fp) return fail(PAT_ERR_INVALID_ARG, std::string("pat_tune_shapes: cannot write ") + tmp);
+    fprintf(fp, "{\"entries\": [\n");
+    for (size_t i = 0; i < entries.size(); ++i) {
+        const ShapeEntry& se = entries[i];
+        fprintf(fp, "  {\"key\": \"%s\", \"forward\": %d, \"adjoint_waves\": %d, \"update_tile\": %d, \"us\": [%.3f, %.3f, %.3f]}%s\n",
+                se.key.c_str(), se.s.forward, se.s.adjoint_waves, se.s.update_tile, se.us[0], se.us[1], se.us[2],
+                i + 1 < entries.size() ? "," : "");
+    }
+    fprintf(fp, "]}\n");
+    const bool ok = fclose(fp) == 0;
+    if (!ok || rename(tmp.c_str(), path) != 0) return fail(PAT_ERR_INVALID_ARG, std::string("pat_tune_shapes: cannot write ") + path);
+    return PAT_OK;
+}
+
+static int tune_one(pat_geometry* g, const float* f, const pat_params* p, int reps, cudaStream_t st, ShapeEntry& se) {
+    pat_params q = *p;
+    q.iters = 20;
+    q.gap_every = 10;
+    q.tol = 0.0;
+    q.adapt = PAT_ADAPT_NONE;
+    q.x_out_dev = q.xbar_out_dev = q.y_out_dev = q.x_lo_out_dev = nullptr;
+    const pat_geometry* gc = g;
+    double us[PAT_NPHASES];
+    pat_shapes cur = g->shapes;
+    auto time_with = [&](const pat_shapes& s) -> int {
+        int rc = pat_geometry_set_shapes(g, &s);
+        if (!rc) rc = time_phases(1, &gc, &f, &q, reps, us, st, "pat_tune_shapes");
+        return rc;
+    };
+    // K: the slab variants and the global one (variants that resolve alike are timed once)
+    double best = 1e300;
+    pat_shapes best_s = cur;
+    std::vector<int> seen;
+    for (int fv : {PAT_FWD_SLAB_TWO, PAT_FWD_SLAB_ONE, PAT_FWD_GLOBAL}) {
+        pat_shapes s = best_s;
+        s.forward = fv;
+        int rc = pat_geometry_set_shapes(g, &s);
+        if (rc) return rc;
+        const int resolved = g->shapes.forward;
+        if (std::find(seen.begin(), seen.end(), resolved) != seen.end()) continue;
+        seen.push_back(resolved);
+        rc = time_phases(1, &gc, &f, &q, reps, us, st, "pat_tune_shapes");
+        if (rc) return rc;
+        if (us[PAT_PHASE_FORWARD_PROX] < best) {
+            best = us[PAT_PHASE_FORWARD_PROX];
+            best_s = g->shapes;
+        }
+    }
+    se.us[0] = best;
+    // K^T: work items filling one or two waves
+    best = 1e300;
+    pat_shapes k_best = best_s;
+    for (int w : {1, 2}) {
+        pat_shapes s = k_best;
+        s.adjoint_waves = w;
+        const int rc = time_with(s);
+        if (rc) return rc;
+        if (us[PAT_PHASE_ADJOINT] < best) {
+            best = us[PAT_PHASE_ADJOINT];
+            best_s = g->shapes;
+        }
+    }
+    se.us[1] = best;
+    // fused update tile
+    best = 1e300;
+    k_best = best_s;
+    for (int t = 0; t < UPD_TILES; ++t) {
+        pat_shapes s = k_best;
+        s.update_tile = t;
+        const int rc = time_with(s);
+        if (rc) return rc;
+        if (us[PAT_PHASE_UPDATE] < best) {
+            best = us[PAT_PHASE_UPDATE];
+            best_s = g->shapes;
+        }
+    }
+    se.us[2] = best;
+    se.s = best_s;
+    return pat_geometry_set_shapes(g, &best_s);
 }
 
 // ---------------------------------------------------------------------------------
@@ -2156,6 +2303,41 @@ extern "C" int pat_time_phases(int count, const pat_geometry* const* g, const fl
             return fail(PAT_ERR_INVALID_ARG, "pat_time_phases: a batch needs equal iters and gap_every");
     }
     return time_phases(count, g, f_dev, p, reps, us_host, (cudaStream_t)stream, "pat_time_phases");
+}
+
+extern "C" int pat_tune_shapes(int count, pat_geometry* const* g, const float* const* f_dev, const pat_params* p,
+                               int reps, const char* cache_path, pat_shapes* chosen_host, void* stream) {
+    if (count < 1 || !g || !f_dev || !p || reps < 1 || reps > 100000)
+        return fail(PAT_ERR_INVALID_ARG, "pat_tune_shapes: bad count, pointer or reps");
+    if (prof_on()) return fail(PAT_ERR_INVALID_ARG, "pat_tune_shapes: turn the per-launch profiler off first");
+    for (int b = 0; b < count; ++b) {
+        const int rc = validate(g[b], &p[b], "pat_tune_shapes");
+        if (rc) return rc;
+        if (!f_dev[b]) return fail(PAT_ERR_INVALID_ARG, "pat_tune_shapes: NULL data");
+        if (p[b].reg == PAT_WAV) return fail(PAT_ERR_INVALID_ARG, "pat_tune_shapes: PAT_WAV has no batch engine");
+    }
+    std::vector<ShapeEntry> cache = read_shape_cache(cache_path);
+    bool dirty = false;
+    for (int b = 0; b < count; ++b) {
+        const std::string key = shape_key(g[b], p[b].reg);
+        auto it = std::find_if(cache.begin(), cache.end(), [&](const ShapeEntry& e) { return e.key == key; });
+        int rc;
+        if (it != cache.end()) {
+            rc = pat_geometry_set_shapes(g[b], &it->s);
+        } else {
+            ShapeEntry se;
+            se.key = key;
+            rc = tune_one(g[b], f_dev[b], &p[b], reps, (cudaStream_t)stream, se);
+            if (!rc) {
+                cache.push_back(se);
+                dirty = true;
+            }
+        }
+        if (rc) return rc;
+        if (chosen_host) chosen_host[b] = g[b]->shapes;
+    }
+    if (cache_path && dirty) return write_shape_cache(cache_path, cache);
+    return PAT_OK;
 }
 
 extern "C" int pat_steps(const pat_geometry* g, const pat_params* p, float* sig_q_dev, float* tau_u_dev,
