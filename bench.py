@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -269,6 +270,19 @@ def run_gb300(args) -> int:
                         iters=iters, gap_every=10, tol=0.0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=device)
 
+    # ---- launch shapes chosen by the library's autotuner (one-off, before the timed steps)
+    shapes = None
+    cache = SHAPE_CACHE[0] = None if args.no_tune else os.path.join(tempfile.mkdtemp(prefix="pat_shapes_"), "shapes.json")
+    if cache:
+        t0 = time.perf_counter()
+        chosen = P.pat_tune_shapes([geo.handle], [f], [prm], reps=50, cache_path=cache, stream=stream)
+        shapes = {"chosen": chosen[0], "tune_seconds": time.perf_counter() - t0,
+                  "timed_us": json.load(open(cache))["entries"][0]["us"],
+                  "how": "pat_tune_shapes: K variants, K^T waves (1, 2), update tiles (32x4, 32x8, 64x4), "
+                         "each timed in a CUDA graph of 50 launches on this problem; fastest kept"}
+    else:
+        shapes = {"chosen": P.pat_geometry_get_shapes(geo.handle), "tune_seconds": None}
+
     def step():
         return P.pat_reconstruct(geo.handle, f, prm, u, stream)
 
@@ -451,7 +465,7 @@ def run_gb300(args) -> int:
                 "config": {"workload": WORKLOAD_DESC, "iters_per_step": iters, "parallelism": f"replicas{world}",
                            "l2": "flushed before every step (256 MiB write outside the timed events)",
                            "points_on_grid_per_K": pts, "final_rel_gap": infos[-1]["rel_gap"]},
-                "roofline": roofline, "phases": phases, "phase_ms_per_step": phase_ms_per_step,
+                "roofline": roofline, "phases": phases, "phase_ms_per_step": phase_ms_per_step, "shapes": shapes,
                 "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": launches, "clocks": clocks, "time_to_gap": ttg,
                 "batched": batched, "mixed_batch": mixed, "warm_start": warm, "preprocess": prep, "wavelet": wav,
@@ -484,6 +498,21 @@ def make_problem(P, np, torch, device, stream, w):
     return geo, f, xi, u
 
 
+SHAPE_CACHE = [None]
+
+
+def tune(P, geos, fs, prms, reps, stream):
+    """Launch shapes of a set of problems by the library's autotuner, through the cache file
+    of this benchmark run (problems whose geometry key was seen before take the cached
+    shapes without timing).  Returns (chosen shapes, seconds), or the current shapes and
+    None under --no-tune."""
+    if SHAPE_CACHE[0] is None:
+        return [P.pat_geometry_get_shapes(g) for g in geos], None
+    t0 = time.perf_counter()
+    chosen = P.pat_tune_shapes(geos, fs, prms, reps=reps, cache_path=SHAPE_CACHE[0], stream=stream)
+    return chosen, time.perf_counter() - t0
+
+
 def run_update_hbm(P, S, np, torch, device, stream, flush, count=16, n=512, iters=40):
     """The fused update (k_update_b) where its state does not fit in L2: a lockstep batch
     of ``count`` TGV^2 problems of n x n (vessel phantoms, 128 detectors, T = 2n), ``iters``
@@ -495,6 +524,9 @@ def run_update_hbm(P, S, np, torch, device, stream, flush, count=16, n=512, iter
     prms = [P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], iters=iters, gap_every=10) for w in ws]
     geos, fs, us = [p[0].handle for p in probs], [p[1] for p in probs], [p[3] for p in probs]
     P.pat_reconstruct_batched(geos, fs, prms, us, stream)        # warm-up (K sums, kernels)
+    # launch shapes by the autotuner: the 16 geometries share one key, so one is timed and
+    # the others take its shapes from the cache
+    chosen, tune_s = tune(P, geos, fs, prms, 20, stream)
     px = count * n * n
     peaks = load_peaks()
     out = {"problems": count, "n": n, "pixels": px, "state_bytes": 29 * 4 * px}
@@ -507,7 +539,7 @@ def run_update_hbm(P, S, np, torch, device, stream, flush, count=16, n=512, iter
                              "frac": alg / peaks["hbm_gbs"], "bytes_per_pixel": 72},
                 "moved_gb_per_s": moved, "moved_frac": moved / peaks["hbm_gbs"],
                 "measured": "pat_time_phases: 20 launches in a CUDA graph after the batch's iterations",
-                "phases_us": phase_us})
+                "phases_us": phase_us, "shapes": chosen[0], "tune_seconds": tune_s})
     for p in probs:
         p[0].close()
     return out
@@ -520,6 +552,7 @@ def run_batched_tgv(P, S, np, torch, device, stream, count, iters, flush):
     prms = [P.make_params(reg=w0["reg"], alpha=w0["alpha"], beta=w0["beta"], iters=iters, gap_every=10)
             for _ in probs]
     geos, fs, us = [p[0].handle for p in probs], [p[1] for p in probs], [p[3] for p in probs]
+    chosen, tune_s = tune(P, geos, fs, prms, 50, stream)
     for _ in range(2):
         P.pat_reconstruct_batched(geos, fs, prms, us, stream)
     ms = []
@@ -535,7 +568,7 @@ def run_batched_tgv(P, S, np, torch, device, stream, count, iters, flush):
         p[0].close()
     t = sum(ms) / len(ms) / 1e3
     return {"problems": count, "iters_per_problem": iters, "ms_per_batch": 1e3 * t,
-            "value": count * iters / t, "unit": "problem-iters/s"}
+            "value": count * iters / t, "unit": "problem-iters/s", "shapes": chosen[0], "tune_seconds": tune_s}
 
 
 def run_mixed(P, S, np, torch, device, stream, flush, max_iters):
@@ -549,6 +582,7 @@ def run_mixed(P, S, np, torch, device, stream, flush, max_iters):
     P.pat_reconstruct_batched(geos, fs, [P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"],
                                                        gamma=w["gamma"], xi=p[2], iters=20, gap_every=10)
                                          for w, p in zip(ws, probs)], us, stream)
+    chosen, tune_s = tune(P, geos, fs, prms, 20, stream)
     flush.zero_()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -560,7 +594,8 @@ def run_mixed(P, S, np, torch, device, stream, flush, max_iters):
     conv = sum(1 for i in infos if i["status"] == P.PAT_STATUS_CONVERGED)
     out = {"problems": len(ws), "seconds": t, "converged": conv, "tol": 1e-4, "max_iters": max_iters,
            "iters_median": float(np.median(its)), "iters_max": int(max(its)),
-           "problem_iters_per_s": sum(its) / t, "step_ratio": 1.0,
+           "problem_iters_per_s": sum(its) / t, "step_ratio": 1.0, "tune_seconds": tune_s,
+           "shapes_used": sorted({(c["forward"], c["adjoint_waves"], c["update_tile"]) for c in chosen}),
            "pixels": int(sum(w["n"] ** 2 for w in ws)), "samples": int(sum(w["det_xy"].shape[0] * w["n_t"] for w in ws))}
     # the TGV problems with the balance picked by the batched probe tuner (TV and dTV keep
     # s = 1: short probes overshoot for them); probe time included
@@ -768,6 +803,7 @@ def main(argv=None) -> int:
     ap.add_argument("--no-prep", action="store_true")
     ap.add_argument("--no-wavelet", action="store_true")
     ap.add_argument("--no-update-hbm", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuner)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -936,7 +936,13 @@ extern "C" int pat_geometry_set_shapes(pat_geometry* g, const pat_shapes* s) {
     pat_geometry_desc dd = g->desc;
     dd.det_xy_host = g->det_xy.data();
     const PointTables pt = point_tables(dd);
-    int rc = install_forward_plan(g, pt, s->forward);
+    // plans are rebuilt only when their shape changes (a rebuild re-evaluates every
+    // quadrature point on the host)
+    int rc = PAT_OK;
+    if (s->forward != g->fwd_requested) {
+        rc = install_forward_plan(g, pt, s->forward);
+        if (!rc) g->fwd_requested = s->forward;
+    }
     if (!rc && s->adjoint_waves != g->shapes.adjoint_waves) rc = install_adjoint_plan(g, pt, s->adjoint_waves);
     if (!rc) g->shapes.update_tile = s->update_tile;
     return rc;

@@ -151,6 +151,7 @@ struct pat_geometry {
     std::vector<double> det_xy;        // detector positions (host copy, 2 per detector)
     std::vector<int2> win_host;        // angular windows over the grid (host copy)
     pat_shapes shapes{};               // launch shapes in use (see pat_geometry_set_shapes)
+    int fwd_requested = PAT_FWD_AUTO;  // the K variant last asked for (shapes.forward: resolved)
     pat::GeomView view;
     // lazily computed preconditioner sums
     mutable std::mutex mtx;
