@@ -272,12 +272,15 @@ def run_gb300(args) -> int:
 
     # ---- launch shapes chosen by the library's autotuner (one-off, before the timed steps)
     shapes = None
-    cache = SHAPE_CACHE[0] = None if args.no_tune else os.path.join(tempfile.mkdtemp(prefix="pat_shapes_"), "shapes.json")
+    cache = SHAPE_CACHE[0] = None if args.no_tune else (
+        args.shape_cache or os.path.join(tempfile.mkdtemp(prefix="pat_shapes_"), "shapes.json"))
     if cache:
         t0 = time.perf_counter()
         chosen = P.pat_tune_shapes([geo.handle], [f], [prm], reps=50, cache_path=cache, stream=stream)
         shapes = {"chosen": chosen[0], "tune_seconds": time.perf_counter() - t0,
-                  "timed_us": json.load(open(cache))["entries"][0]["us"],
+                  "timed_us": next((e["us"] for e in json.load(open(cache))["entries"]
+                                    if e["key"].startswith("N=%d D=%d T=%d " % (n, w["det_xy"].shape[0], w["n_t"]))),
+                                   None),
                   "how": "pat_tune_shapes: K variants, K^T waves (1, 2), update tiles (32x4, 32x8, 64x4), "
                          "each timed in a CUDA graph of 50 launches on this problem; fastest kept"}
     else:
@@ -804,6 +807,9 @@ def main(argv=None) -> int:
     ap.add_argument("--no-wavelet", action="store_true")
     ap.add_argument("--no-update-hbm", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default launch shapes (no autotuner)")
+    ap.add_argument("--shape-cache", default="",
+                    help="the autotuner's JSON cache (default: a fresh temporary file); shapes found in it are "
+                         "applied without timing")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

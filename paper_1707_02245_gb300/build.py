@@ -51,13 +51,16 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
     headers += [os.path.join(INCLUDE, h) for h in ("pat.h", "pat_unet.h")]
     flags = common_flags() + (extra or [])
+    # objects built with other flags (e.g. extra defines) are rebuilt
+    stamp = os.path.join(BUILD, "flags.txt")
+    same_flags = os.path.exists(stamp) and open(stamp).read() == " ".join(flags)
     objs = []
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
         o = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(o)
-        if _stale(o, [s] + headers + [__file__]):
+        if not same_flags or _stale(o, [s] + headers + [__file__]):
             jobs.append([nvcc()] + flags + ["-c", s, "-o", o])
 
     def run(cmd):
@@ -71,6 +74,9 @@ def build(verbose: bool = False, extra: list[str] | None = None) -> str:
 
     with ThreadPoolExecutor(max_workers=max(1, len(jobs))) as ex:
         list(ex.map(run, jobs))
+    if not same_flags:
+        with open(stamp, "w") as fh:
+            fh.write(" ".join(flags))
     out = lib_path()
     if jobs or _stale(out, objs):
         run([nvcc()] + ARCH + ["-shared", "-o", out] + objs + ["-lcudart"])

@@ -68,11 +68,7 @@ __device__ __forceinline__ void adjoint_item(const AdjArgs& a, int item_index) {
     // the scale of the ATILE tile that holds this work tile
     const float bound = __uint_as_float(*a.ymax_bits) * __ldg(&a.tile_kmax[(y0 / ATILE) * a.tiles_x + x0 / ATILE]);
     const float scale = 1073741824.0f / bound;  // 2^30 / bound
-#if PAT_ADJ_RADIUS_FMA
     const float dr_f = g.dr_f, rh_f = g.rh_f;
-#else
-    const float* __restrict__ rk = g.rk;
-#endif
     const float* __restrict__ wk = g.wk;
     const float* __restrict__ y = a.y;
     __syncthreads();
@@ -109,11 +105,7 @@ __device__ __forceinline__ void adjoint_item(const AdjArgs& a, int item_index) {
                     k = ray.z;
                 }
                 Taps t;
-#if PAT_ADJ_RADIUS_FMA
                 point_coords(g, det, radius(k, dr_f, rh_f), cs, t);   // = rk[k], bit for bit
-#else
-                point_coords(g, det, __ldg(&rk[k]), cs, t);
-#endif
                 // taps in the tile window (ring cells off the tile are dropped later)
                 const int li = t.i0 - x0 + 1, lj = t.j0 - y0 + 1;
                 if ((unsigned)li > (unsigned)WTILE || (unsigned)lj > (unsigned)WTILE) continue;

@@ -91,7 +91,8 @@ __host__ __device__ __forceinline__ float radius(int k, float dr_f, float rh_f) 
 }
 
 constexpr int KGRP = 8;        // radii per angular-window group
-constexpr int SLAB_THREADS = 512;                // threads of a K CTA
+constexpr int FWD_THREADS = 512;        // threads of a K CTA (two CTAs per SM)
+constexpr int FWD_THREADS_WIDE = 1024;  // threads of a K CTA that holds its SM alone
 constexpr int FWD_SMEM_TWO = 112 * 1024;         // dynamic shared memory of a K CTA, two per SM
 constexpr int FWD_SMEM_ONE = 220 * 1024;         // ... one per SM
 constexpr int FWD_MAX_CLUSTER = 16;              // largest (non-portable) cluster size
@@ -304,6 +305,7 @@ int launch_forward_b(int epi, const FwdArgs* args, const int2* map, int nblocks,
                      cudaStream_t st);
 int forward_smem_bytes(int rows, int stride, int M, int D, bool staged);
 int forward_clusters_per_gpu(int cluster, int smem);   // K clusters the GPU holds at once
+int forward_threads(int smem);                         // threads of a K CTA with this shared memory
 int launch_adjoint_b(const AdjArgs* args, const int2* map, int nblocks, bool premul, cudaStream_t st);
 // CTAs of the K^T kernel that one SM holds at once (sizes the work items)
 int adjoint_blocks_per_sm();

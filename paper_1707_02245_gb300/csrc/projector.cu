@@ -3,13 +3,15 @@
 // Its exact transpose K^T is in adjoint.cu.
 //
 // K: every point of circle (d, k) is interpolated bilinearly between pixel centres.  The
-// image is cut into horizontal slabs; a CTA copies one slab (with a zero border and one
-// extra row) into shared memory and evaluates the points of a list of work units (one
-// row group of 8 radii of one detector, restricted to that slab) from there, so each of
-// a point's four taps is a shared-memory load.  A warp holds the 8 radii of a row group
-// times 4 angular phases, so at every step its 32 points form a 4-angle x 8-radius patch
-// of the polar grid.  A row group's slabs are added by the last unit to finish, in slab
-// order, so the result does not depend on scheduling.
+// image is cut into S horizontal slabs, and a thread-block cluster of S CTAs holds the
+// whole image: CTA s copies slab s (with a zero border and one extra row) into its shared
+// memory and evaluates, for the cluster's row groups (8 radii of one detector), the
+// points whose taps lie in its slab, so each of a point's four taps is a shared-memory
+// load.  A warp holds the 8 radii of a row group times 4 angular phases, so at every step
+// its 32 points form a 4-angle x 8-radius patch of the polar grid.  After a cluster
+// barrier the S partial sums of a row are read through distributed shared memory and
+// added in slab order, so the result does not depend on scheduling.  Images too large
+// for the slabs of one cluster take the same units with taps from global memory.
 #include <string.h>
 
 #include <algorithm>
@@ -36,7 +38,10 @@ __device__ __forceinline__ float fetch4_global(const float* __restrict__ u, int 
 // m_first + ph + 4, ...  so at every step the warp evaluates a 4 (angles) x 8 (radii)
 // patch of the polar grid, a compact patch of pixels.
 constexpr int NPH = 4;
-constexpr int SLAB_WARPS = SLAB_THREADS / 32;
+#ifndef PAT_FWD_PTS
+#define PAT_FWD_PTS 2
+#endif
+constexpr int FWD_PTS = PAT_FWD_PTS;   // points per trip of the inner loop (independent sums)
 
 // Sum over the four phases (lanes kl, kl+8, kl+16, kl+24); valid in every lane.
 __device__ __forceinline__ float phase_sum(float v) {
@@ -71,7 +76,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 //  byte address img_s (column i at byte 4 (4 + i) of a row of W floats, with columns N and
 //  N + 1 of rows 0 and 1 zero), and cs_s holds the angle table twice over, so m never
 //  wraps.  The body has no branch: a point outside the slab or the grid reads the zero
-//  cell at columns N, N + 1 of rows 0, 1.  Two points per trip, with separate sums.
+//  cell at columns N, N + 1 of rows 0, 1.  FWD_PTS points per trip, with separate sums.
 //  Otherwise: taps and angles come from global memory.
 template <bool SMEM>
 __device__ __forceinline__ float unit_partial(const GeomView& g, unsigned cs_s, const float* __restrict__ img,
@@ -90,36 +95,42 @@ __device__ __forceinline__ float unit_partial(const GeomView& g, unsigned cs_s, 
         const float2 magic = make_float2(FLOOR_MAGIC, FLOOR_MAGIC), nmagic = make_float2(-FLOOR_MAGIC, -FLOOR_MAGIC);
         const int lbias = FLOOR_MAGIC_BITS - 1;     // li = floor(fx) + 1
         const int jbias = FLOOR_MAGIC_BITS + jlo;   // lj = floor(fy) - jlo
-        float acc2 = 0.f;
-        for (int j = ph; j < tot; j += 2 * NPH) {
-            const int jb = j + NPH;
-            const bool vb = jb < tot;
-            const int ma = j + (j < c0 ? m0 : off1);
-            const int mb = vb ? jb + (jb < c0 ? m0 : off1) : ma;
-            const float2 csa = lds2(cs_s + 8u * (unsigned)ma);
-            const float2 csb = lds2(cs_s + 8u * (unsigned)mb);
-            // positions and taps; the FP32 arithmetic of the transpose (fx = fmaf(r, cs.x, det.x))
-            const float2 fa = __ffma2_rn(rr, csa, det), fb = __ffma2_rn(rr, csb, det);
-            // exact floors (see point_coords): ta = floor(fa) + 1.5 * 2^23
-            const float2 ta = __fadd2_rd(fa, magic), tb = __fadd2_rd(fb, magic);
-            const int lia = __float_as_int(ta.x) - lbias, lja = __float_as_int(ta.y) - jbias;
-            const int lib = __float_as_int(tb.x) - lbias, ljb = __float_as_int(tb.y) - jbias;
-            const bool ina = ((unsigned)lja < (unsigned)reff) & ((unsigned)lia <= (unsigned)N) & valid;
-            const bool inb = ((unsigned)ljb < (unsigned)reff) & ((unsigned)lib <= (unsigned)N) & valid & vb;
-            const unsigned aa = ina ? base + (unsigned)lja * W4 + 4u * (unsigned)lia : zero;   // li = i0 + 1
-            const unsigned ab = inb ? base + (unsigned)ljb * W4 + 4u * (unsigned)lib : zero;
-            const float2 loa = make_float2(lds(aa), lds(aa + W4)), hia = make_float2(lds(aa + 4u), lds(aa + W4 + 4u));
-            const float2 lob = make_float2(lds(ab), lds(ab + W4)), hib = make_float2(lds(ab + 4u), lds(ab + W4 + 4u));
-            // (ax, ay) = fa - floor(fa): floor(fa) = ta - C exactly, and the difference is exact
-            const float2 fra = __ffma2_rn(__fadd2_rn(ta, nmagic), mone, fa);
-            const float2 frb = __ffma2_rn(__fadd2_rn(tb, nmagic), mone, fb);
-            // rows j0 and j0 + 1 interpolated in x, then in y
-            const float2 pa = __ffma2_rn(make_float2(fra.x, fra.x), __ffma2_rn(loa, mone, hia), loa);
-            const float2 pb = __ffma2_rn(make_float2(frb.x, frb.x), __ffma2_rn(lob, mone, hib), lob);
-            acc += fmaf(fra.y, pa.y - pa.x, pa.x);
-            acc2 += fmaf(frb.y, pb.y - pb.x, pb.x);
-        }
-        acc += acc2;
+        // FWD_PTS points per trip, each with its own partial sum (independent chains).  The
+        // two windows run one after the other; in each, the lane's points are the window's
+        // angles ph, ph + NPH, ... and their table entries are read at fixed offsets from
+        // one address per trip.  Rows k >= T are evaluated like the others (their radius
+        // is that of k = 0) and dropped at the end.
+        float part[FWD_PTS];
+#pragma unroll
+        for (int e = 0; e < FWD_PTS; ++e) part[e] = 0.f;
+        auto window = [&](int mstart, int cnt) {
+            unsigned csp = cs_s + 8u * (unsigned)(mstart + ph);
+            for (int j = ph; j < cnt; j += FWD_PTS * NPH, csp += 8u * FWD_PTS * NPH) {
+#pragma unroll
+                for (int e = 0; e < FWD_PTS; ++e) {
+                    const bool vj = e == 0 || j + e * NPH < cnt;
+                    const float2 cs = lds2(vj ? csp + 8u * NPH * e : csp);
+                    // position and taps; the FP32 arithmetic of the transpose (fx = fmaf(r, cs.x, det.x))
+                    const float2 fp = __ffma2_rn(rr, cs, det);
+                    // exact floor (see point_coords): tp = floor(fp) + 1.5 * 2^23
+                    const float2 tp = __fadd2_rd(fp, magic);
+                    const int li = __float_as_int(tp.x) - lbias, lj = __float_as_int(tp.y) - jbias;
+                    const bool in = ((unsigned)lj < (unsigned)reff) & ((unsigned)li <= (unsigned)N) & vj;
+                    const unsigned ad = in ? base + (unsigned)lj * W4 + 4u * (unsigned)li : zero;   // li = i0 + 1
+                    const float2 lo = make_float2(lds(ad), lds(ad + W4)), hi = make_float2(lds(ad + 4u), lds(ad + W4 + 4u));
+                    // (ax, ay) = fp - floor(fp): floor(fp) = tp - C exactly, and the difference is exact
+                    const float2 fr = __ffma2_rn(__fadd2_rn(tp, nmagic), mone, fp);
+                    // rows j0 and j0 + 1 interpolated in x, then in y
+                    const float2 pr = __ffma2_rn(make_float2(fr.x, fr.x), __ffma2_rn(lo, mone, hi), lo);
+                    part[e] += fmaf(fr.y, pr.y - pr.x, pr.x);
+                }
+            }
+        };
+        window(m0, c0);
+        window((int)(w1 & 0xffffu), (int)(w1 >> 16));
+#pragma unroll
+        for (int e = 1; e < FWD_PTS; ++e) part[0] += part[e];
+        acc = valid ? part[0] : 0.f;
     } else {
         for (int j = ph; j < tot; j += NPH) {
             const int mm = j + (j < c0 ? m0 : off1);
@@ -142,12 +153,13 @@ __device__ __forceinline__ float unit_partial(const GeomView& g, unsigned cs_s, 
 // float t W, column i at float t W + 4 + i): cp.async for rows inside the image when N is
 // a multiple of 4 and the image 16-byte aligned, plain loads otherwise; rows outside the
 // image and the columns -1 and N are zero.  Completed by cp_async_wait_all() and a barrier.
+template <int NT>
 __device__ __forceinline__ void stage_slab(const float* __restrict__ img, int N, int W, int jlo, int nrow,
                                            float* s_img) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const bool vec = (N & 3) == 0 && ((reinterpret_cast<size_t>(img) & 15) == 0);
     const unsigned base = smem_addr(s_img);
-    for (int t = warp; t < nrow; t += SLAB_WARPS) {
+    for (int t = warp; t < nrow; t += NT / 32) {
         const int j = jlo + t;
         float* row = s_img + t * W;
         const bool in = j >= 0 && j < N;
@@ -236,8 +248,8 @@ __device__ __forceinline__ void forward_units(const FwdArgs& a, int ub, int ue, 
 // K (Sec. 3.3.1, eq. (K_def)) for the row groups of one cluster, then the epilogue on
 // their rows.  The S partial sums of a row (one per slab) are added in rank (slab) order,
 // so the result does not depend on scheduling.
-template <int EPI>
-__global__ void __launch_bounds__(SLAB_THREADS, 2) k_forward_b(const FwdArgs* __restrict__ args,
+template <int EPI, int NT>
+__global__ void __launch_bounds__(NT, NT >= 1024 ? 1 : 2) k_forward_b(const FwdArgs* __restrict__ args,
                                                            const int2* __restrict__ map) {
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ FwdArgs sa;
@@ -263,9 +275,9 @@ __global__ void __launch_bounds__(SLAB_THREADS, 2) k_forward_b(const FwdArgs* __
     if (smem_img) {
         float2* s_cs = reinterpret_cast<float2*>(smem + L.cs);
         float2* s_det = reinterpret_cast<float2*>(smem + L.det);
-        for (int i = threadIdx.x; i < 2 * M; i += SLAB_THREADS) s_cs[i] = __ldg(&g.cs[i < M ? i : i - M]);
-        for (int i = threadIdx.x; i < D; i += SLAB_THREADS) s_det[i] = __ldg(&g.det[i]);
-        stage_slab(a.img, N, g.slab_stride, jlo, reff + 1, reinterpret_cast<float*>(smem + L.slab));
+        for (int i = threadIdx.x; i < 2 * M; i += NT) s_cs[i] = __ldg(&g.cs[i < M ? i : i - M]);
+        for (int i = threadIdx.x; i < D; i += NT) s_det[i] = __ldg(&g.det[i]);
+        stage_slab<NT>(a.img, N, g.slab_stride, jlo, reff + 1, reinterpret_cast<float*>(smem + L.slab));
     }
     if (threadIdx.x == 0) s_qmax = 0u;
     const int lane = threadIdx.x & 31;
@@ -276,8 +288,8 @@ __global__ void __launch_bounds__(SLAB_THREADS, 2) k_forward_b(const FwdArgs* __
     for (int rd = 0; rd < n_rounds; ++rd) {
         const int ub = __ldg(&roff[rd]), ue = __ldg(&roff[rd + 1]);
         const int nr = min(FWD_ROUND, n_rg - rd * FWD_ROUND);
-        for (int i = threadIdx.x; i < ue - ub; i += SLAB_THREADS) s_units[i] = __ldg(&g.units[ub + i]);
-        for (int i = threadIdx.x; i < nr * KGRP; i += SLAB_THREADS) s_acc[i] = 0.f;
+        for (int i = threadIdx.x; i < ue - ub; i += NT) s_units[i] = __ldg(&g.units[ub + i]);
+        for (int i = threadIdx.x; i < nr * KGRP; i += NT) s_acc[i] = 0.f;
         if (threadIdx.x == 0) s_next = ub;
         if (smem_img && rd == 0) cp_async_wait_all();
         __syncthreads();
@@ -291,7 +303,7 @@ __global__ void __launch_bounds__(SLAB_THREADS, 2) k_forward_b(const FwdArgs* __
         // is row (i % KGRP) of row group rgs[rg0 + rd * FWD_ROUND + i / KGRP]
         const int rows = nr * KGRP, per = (rows + S - 1) / S;
         const int i0 = (int)rank * per, i1 = min(rows, i0 + per);
-        for (int i = i0 + threadIdx.x; i < i1; i += SLAB_THREADS) {
+        for (int i = i0 + threadIdx.x; i < i1; i += NT) {
             const int rg = __ldg(&g.rgs[rg0 + rd * FWD_ROUND + i / KGRP]);
             const int d = rg / g.n_kgrp;
             const int k = (rg - d * g.n_kgrp) * KGRP + (i & (KGRP - 1));
@@ -423,6 +435,19 @@ int forward_smem_bytes(int rows, int stride, int M, int D, bool staged) {
 
 // K launches may use up to FWD_SMEM_ONE bytes of dynamic shared memory; the attribute is
 // set once per kernel and device.
+template <int NT>
+static cudaError_t forward_attributes_nt() {
+    const void* ks[3] = {(const void*)k_forward_b<FWD_Y, NT>, (const void*)k_forward_b<FWD_PROX, NT>,
+                         (const void*)k_forward_b<FWD_GAP, NT>};
+    for (const void* k : ks) {
+        const cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, FWD_SMEM_ONE);
+        if (e != cudaSuccess) return e;
+        // clusters of more than 8 CTAs (up to FWD_MAX_CLUSTER) where the device allows them
+        if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
+    }
+    return cudaSuccess;
+}
+
 static int forward_attributes() {
     static std::mutex mtx;
     static bool done[64] = {};
@@ -430,23 +455,21 @@ static int forward_attributes() {
     PAT_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(mtx);
     if (dev >= 0 && dev < 64 && done[dev]) return PAT_OK;
-    constexpr int smem = FWD_SMEM_ONE;
-    PAT_CUDA(cudaFuncSetAttribute(k_forward_b<FWD_Y>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    PAT_CUDA(cudaFuncSetAttribute(k_forward_b<FWD_PROX>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    PAT_CUDA(cudaFuncSetAttribute(k_forward_b<FWD_GAP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-    // clusters of more than 8 CTAs (up to FWD_MAX_CLUSTER) where the device allows them
-    for (const void* k : {(const void*)k_forward_b<FWD_Y>, (const void*)k_forward_b<FWD_PROX>,
-                          (const void*)k_forward_b<FWD_GAP>})
-        if (cudaFuncSetAttribute(k, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess) cudaGetLastError();
+    PAT_CUDA(forward_attributes_nt<FWD_THREADS>());
+    PAT_CUDA(forward_attributes_nt<FWD_THREADS_WIDE>());
     if (dev >= 0 && dev < 64) done[dev] = true;
     return PAT_OK;
 }
+
+// Threads of a K CTA: a CTA whose shared memory leaves no room for a second one on its SM
+// runs twice as many warps, so that the SM keeps the same number of warps in flight.
+int forward_threads(int smem) { return smem > FWD_SMEM_TWO ? FWD_THREADS_WIDE : FWD_THREADS; }
 
 static cudaLaunchConfig_t forward_config(int nblocks, int cluster, int smem, cudaStream_t st,
                                          cudaLaunchAttribute* attr) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)nblocks);
-    cfg.blockDim = dim3(SLAB_THREADS);
+    cfg.blockDim = dim3((unsigned)forward_threads(smem));
     cfg.dynamicSmemBytes = (size_t)smem;
     cfg.stream = st;
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -462,12 +485,20 @@ int forward_clusters_per_gpu(int cluster, int smem) {
     int n = 0;
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = forward_config(cluster, cluster, smem, nullptr, attr);
-    if (forward_attributes() != PAT_OK ||
-        cudaOccupancyMaxActiveClusters(&n, (const void*)k_forward_b<FWD_PROX>, &cfg) != cudaSuccess) {
+    const void* k = forward_threads(smem) == FWD_THREADS_WIDE ? (const void*)k_forward_b<FWD_PROX, FWD_THREADS_WIDE>
+                                                              : (const void*)k_forward_b<FWD_PROX, FWD_THREADS>;
+    if (forward_attributes() != PAT_OK || cudaOccupancyMaxActiveClusters(&n, k, &cfg) != cudaSuccess) {
         cudaGetLastError();
         n = 0;
     }
     return n;   // 0: clusters of this shape cannot run on the device
+}
+
+template <int NT>
+static cudaError_t launch_forward_nt(int epi, const cudaLaunchConfig_t& cfg, const FwdArgs* args, const int2* map) {
+    if (epi == FWD_Y) return cudaLaunchKernelEx(&cfg, k_forward_b<FWD_Y, NT>, args, map);
+    if (epi == FWD_PROX) return cudaLaunchKernelEx(&cfg, k_forward_b<FWD_PROX, NT>, args, map);
+    return cudaLaunchKernelEx(&cfg, k_forward_b<FWD_GAP, NT>, args, map);
 }
 
 int launch_forward_b(int epi, const FwdArgs* args, const int2* map, int nblocks, int cluster, int smem,
@@ -478,13 +509,8 @@ int launch_forward_b(int epi, const FwdArgs* args, const int2* map, int nblocks,
     cudaLaunchAttribute attr[1];
     cudaLaunchConfig_t cfg = forward_config(nblocks, cluster, smem, st, attr);
     if (epi == FWD_PROX) prof_mark(PAT_PHASE_FORWARD_PROX, st, true);
-    cudaError_t e;
-    if (epi == FWD_Y)
-        e = cudaLaunchKernelEx(&cfg, k_forward_b<FWD_Y>, args, map);
-    else if (epi == FWD_PROX)
-        e = cudaLaunchKernelEx(&cfg, k_forward_b<FWD_PROX>, args, map);
-    else
-        e = cudaLaunchKernelEx(&cfg, k_forward_b<FWD_GAP>, args, map);
+    const cudaError_t e = forward_threads(smem) == FWD_THREADS_WIDE ? launch_forward_nt<FWD_THREADS_WIDE>(epi, cfg, args, map)
+                                                                    : launch_forward_nt<FWD_THREADS>(epi, cfg, args, map);
     count_launch();
     if (e != cudaSuccess) return cuda_fail(e, "k_forward_b");
     if (epi == FWD_PROX) prof_mark(PAT_PHASE_FORWARD_PROX, st, false);

@@ -96,3 +96,19 @@ def test_unet_arguments_rejected_before_any_device_call(lib):
     with pytest.raises(P.PatError) as ei:
         P.pat_conv3x3_backward_weight(16, 16, 1, 4, 4, 8, 12, 16)
     assert ei.value.code == P.PAT_ERR_INVALID_ARG
+
+
+def test_header_shape_constants_match_the_binding():
+    """The launch-shape constants of include/pat.h and the pat_shapes layout are the ones
+    the Python binding passes."""
+    import ctypes
+    import re
+    hdr = open(os.path.join(ROOT, "include", "pat.h")).read()
+    consts = dict(re.findall(r"#define\s+(PAT_(?:FWD|UPD|ADJ)_\w+)\s+(-?\d+)", hdr))
+    assert len(consts) >= 7
+    for name, value in consts.items():
+        assert getattr(P, name) == int(value), name
+    body = re.search(r"typedef struct \{([^}]*)\} pat_shapes;", hdr).group(1)
+    fields = re.findall(r"int\s+(\w+);", body)
+    assert fields == [f for f, _ in P.pat_shapes._fields_]
+    assert ctypes.sizeof(P.pat_shapes) == 4 * len(fields)
