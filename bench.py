@@ -502,6 +502,7 @@ def make_problem(P, np, torch, device, stream, w):
 
 
 SHAPE_CACHE = [None]
+UPDATE_MOVED_TGV = 92   # bytes per pixel the TGV update kernel reads and writes
 
 
 def tune(P, geos, fs, prms, reps, stream):
@@ -519,9 +520,10 @@ def tune(P, geos, fs, prms, reps, stream):
 def run_update_hbm(P, S, np, torch, device, stream, flush, count=16, n=512, iters=40):
     """The fused update (k_update_b) where its state does not fit in L2: a lockstep batch
     of ``count`` TGV^2 problems of n x n (vessel phantoms, 128 detectors, T = 2n), ``iters``
-    iterations with per-phase CUDA events.  Bytes per pixel: the algorithmic 18 floats
-    (read u, v2, r2, s3, tau; write u, v2, r2, s3, ubar) and the 29 the kernel moves (the
-    compensated low words, the ubar quad and the K^T clear besides)."""
+    iterations, the update timed alone in a CUDA graph.  Bytes per pixel: the algorithmic
+    72 (18 floats: read u, v2, r2, s3, tau; write u, v2, r2, s3, ubar) and the 92 the
+    kernel moves (besides: read K^T q and clear the next iteration's buffer, 8 bytes; read
+    and write the bfloat16 low words of u, v2, 12 bytes)."""
     ws = [S.workload_warm(700000 + s, n=n, n_det=128) for s in range(count)]
     probs = [make_problem(P, np, torch, device, stream, w) for w in ws]
     prms = [P.make_params(reg=w["reg"], alpha=w["alpha"], beta=w["beta"], iters=iters, gap_every=10) for w in ws]
@@ -532,15 +534,15 @@ def run_update_hbm(P, S, np, torch, device, stream, flush, count=16, n=512, iter
     chosen, tune_s = tune(P, geos, fs, prms, 20, stream)
     px = count * n * n
     peaks = load_peaks()
-    out = {"problems": count, "n": n, "pixels": px, "state_bytes": 29 * 4 * px}
+    out = {"problems": count, "n": n, "pixels": px, "state_bytes": UPDATE_MOVED_TGV * px}
     phase_us = P.pat_time_phases(geos, fs, prms, 20, stream)
     avg_s = phase_us["update"] * 1e-6
     alg = 18 * 4 * px / avg_s / 1e9
-    moved = 29 * 4 * px / avg_s / 1e9
+    moved = UPDATE_MOVED_TGV * px / avg_s / 1e9
     out.update({"avg_us": avg_s * 1e6,
                 "roofline": {"bound": "hbm", "achieved": alg, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                              "frac": alg / peaks["hbm_gbs"], "bytes_per_pixel": 72},
-                "moved_gb_per_s": moved, "moved_frac": moved / peaks["hbm_gbs"],
+                "moved_gb_per_s": moved, "moved_frac": moved / peaks["hbm_gbs"], "moved_bytes_per_pixel": UPDATE_MOVED_TGV,
                 "measured": "pat_time_phases: 20 launches in a CUDA graph after the batch's iterations",
                 "phases_us": phase_us, "shapes": chosen[0], "tune_seconds": tune_s})
     for p in probs:

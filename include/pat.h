@@ -156,9 +156,11 @@ typedef struct {
     /* PAT_WAV: levels J of the transform, 1..12, with N divisible by 2^J (0: 4) */
     int    wavelet_levels;
     /* The primal iterates x = (u, v) are kept as compensated pairs hi + lo (every update
-       is added with an error-free two-sum), and x_out_dev receives the high words.
+       is added with an error-free two-sum), and x_out_dev receives the high words.  The
+       low word is stored as a bfloat16 (8 significant bits, so the pair holds about 32).
        x_lo_out_dev (layout of x, NULL = not written) receives the low words, and
-       x_lo0_dev (layout of x, NULL = zero) starts a run from them.  Passing x_out,
+       x_lo0_dev (layout of x, NULL = zero) starts a run from them, rounded to bfloat16
+       (exported words are bfloat16 values already).  Passing x_out,
        xbar_out, y_out and x_lo_out of one run as x0, xbar0, y0 and x_lo0 of the next
        continues it bit for bit (the gap schedule restarts at the resumed iteration).
        PAT_WAV iterates are plain FP32: its low words are zero.  Not Sec. 3: a numerical

@@ -44,10 +44,10 @@ struct UpdateArgs {
     int* kt_clear;         // the other fixed-point buffer, cleared here for the next iteration
     unsigned* qmax_next;   // max |q| slot of the next iteration, reset here
     const float* x_in;     // u, v1, v2
-    const float* xl_in;    // low parts of the compensated primal pair (u, v1, v2)
+    const unsigned short* xl_in;   // low words of the compensated primal pairs (u, v1, v2), bfloat16
     const float* y_in;     // r1, r2, s11, s22, s12
     float* x_out;
-    float* xl_out;
+    unsigned short* xl_out;
     float* y_out;
     float* ubar;           // N*N: ubar for the next K
     const int* stop;
@@ -70,7 +70,8 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
 
     __shared__ float s_r1m[LY][LX], s_r2m[LY][LX];   // r (dTV: D_xi r) masked for div
     __shared__ float s_ub[LY][LX];                   // ubar on U = tile + high halo
-    __shared__ float s_un[TY][TX], s_unl[TY][TX];    // u^{n+1} (high, low) on the tile
+    __shared__ float s_un[TY][TX];                   // u^{n+1} (high word) on the tile
+    __shared__ unsigned short s_unl[TY][TX];         // ... its low word (bfloat16)
     // TGV only (small arrays for TV / dTV)
     constexpr int VL = (REG == PAT_TGV) ? LY : 1;
     constexpr int VX = (REG == PAT_TGV) ? LX : 1;
@@ -78,7 +79,8 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
     constexpr int VTX = (REG == PAT_TGV) ? TX : 1;
     __shared__ float s_s11[VL][VX], s_s22[VL][VX], s_s12[VL][VX];
     __shared__ float s_vb1[VL][VX], s_vb2[VL][VX];   // vbar on V = tile + low halo
-    __shared__ float s_vn1[VT][VTX], s_vn2[VT][VTX], s_vnl1[VT][VTX], s_vnl2[VT][VTX];
+    __shared__ float s_vn1[VT][VTX], s_vn2[VT][VTX];
+    __shared__ unsigned short s_vnl1[VT][VTX], s_vnl2[VT][VTX];
 
     // plane pointers, formed once
     const float* u_in = a.x_in;
@@ -89,8 +91,8 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
     const float* s12_in = a.y_in + 4 * NN;
     const float* v1_in = a.x_in + NN;
     const float* v2_in = a.x_in + 2 * NN;
-    const float* v1l_in = a.xl_in + NN;
-    const float* v2l_in = a.xl_in + 2 * NN;
+    const unsigned short* v1l_in = a.xl_in + NN;
+    const unsigned short* v2l_in = a.xl_in + 2 * NN;
     const float* xi0_in = a.xi;
     const float* xi1_in = REG == PAT_DTV ? a.xi + NN : a.xi;
     constexpr int NCELL = (LX * LY + TX * TY - 1) / (TX * TY);   // staged cells per thread
@@ -115,8 +117,9 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
         const int lx = c % LX, ly = c / LX;
         const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
         const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
-        float r1 = in ? __ldg(r1_in + gy * N + gx) : 0.f;
-        float r2 = in ? __ldg(r2_in + gy * N + gx) : 0.f;
+        const int gi = in ? gy * N + gx : 0;
+        float r1 = in ? __ldg(r1_in + gi) : 0.f;
+        float r2 = in ? __ldg(r2_in + gi) : 0.f;
         if (REG == PAT_DTV) {
             const float xi0 = in ? __ldg(xi0_in + gy * N + gx) : 0.f;
             const float xi1 = in ? __ldg(xi1_in + gy * N + gx) : 0.f;
@@ -128,9 +131,9 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
         s_r1m[ly][lx] = (gx < N - 1) ? r1 : 0.f;
         s_r2m[ly][lx] = (gy < N - 1) ? r2 : 0.f;
         if (REG == PAT_TGV) {
-            s_s11[ly][lx] = in ? __ldg(s11_in + gy * N + gx) : 0.f;
-            s_s22[ly][lx] = in ? __ldg(s22_in + gy * N + gx) : 0.f;
-            s_s12[ly][lx] = in ? __ldg(s12_in + gy * N + gx) : 0.f;
+            s_s11[ly][lx] = in ? __ldg(s11_in + gi) : 0.f;
+            s_s22[ly][lx] = in ? __ldg(s22_in + gi) : 0.f;
+            s_s12[ly][lx] = in ? __ldg(s12_in + gi) : 0.f;
         }
     }
     __syncthreads();
@@ -148,16 +151,20 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
             if (in) {
                 const int gi = gy * N + gx;
                 const float divr = s_r1m[ly][lx] - s_r1m[ly][lx - 1] + s_r2m[ly][lx] - s_r2m[ly - 1][lx];
-                const float w = (float)__ldg(&a.kt.acc[(size_t)gy * N + gx]) *
-                                s_kinv[gy / ATILE - y0 / ATILE][gx / ATILE - x0 / ATILE];
-                const float uo = __ldg(u_in + gi), uol = __ldg(a.xl_in + gi);
-                const float tu = (a.tau >= 0.f ? a.tau : __ldg(a.tau_u + gi)) * tmul;
+                // (every rounding spelled out: a halo cell's value must equal, bit for
+                // bit, the one its own tile computes in another unrolled copy)
+                const float w = __fmul_rn((float)__ldg(&a.kt.acc[gi]),
+                                          s_kinv[gy / ATILE - y0 / ATILE][gx / ATILE - x0 / ATILE]);
+                const float uo = __ldg(u_in + gi), uol = lo_decode(__ldg(a.xl_in + gi));
+                const float tu = __fmul_rn(a.tau >= 0.f ? a.tau : __ldg(a.tau_u + gi), tmul);
                 float un = uo, unl = uol;
-                add_compensated(un, unl, -tu * (w - divr));
+                add_compensated(un, unl, -__fmul_rn(tu, __fsub_rn(w, divr)));
+                const unsigned short unq = lo_encode(unl);   // the stored pair, used from here on
+                unl = lo_decode(unq);
                 ub = fmaf(a.theta, (un - uo) + (unl - uol), un + unl);
                 if (lx <= TX && ly <= TY) {
                     s_un[ly - 1][lx - 1] = un;
-                    s_unl[ly - 1][lx - 1] = unl;
+                    s_unl[ly - 1][lx - 1] = unq;
                 }
             }
             s_ub[ly][lx] = ub;
@@ -172,23 +179,26 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
                 const float dy12 = by ? s_s12[ly + 1][lx] - s_s12[ly][lx] : 0.f;
                 const float dy22 = by ? s_s22[ly + 1][lx] - s_s22[ly][lx] : 0.f;
                 const float dx12 = ax ? s_s12[ly][lx + 1] - s_s12[ly][lx] : 0.f;
-                const float et1 = -dx11 - dy12 * kInvSqrt2f;
-                const float et2 = -dy22 - dx12 * kInvSqrt2f;
+                const float et1 = __fsub_rn(-dx11, __fmul_rn(dy12, kInvSqrt2f));
+                const float et2 = __fsub_rn(-dy22, __fmul_rn(dx12, kInvSqrt2f));
                 const float r1 = __ldg(r1_in + gi), r2 = __ldg(r2_in + gi);
                 const float v1o = __ldg(v1_in + gi), v2o = __ldg(v2_in + gi);
-                const float v1ol = __ldg(v1l_in + gi), v2ol = __ldg(v2l_in + gi);
-                const float t1 = (a.tau >= 0.f ? a.tau : tau_v1_tgv(gx, gy, N)) * tmul;
-                const float t2 = (a.tau >= 0.f ? a.tau : tau_v2_tgv(gx, gy, N)) * tmul;
+                const float v1ol = lo_decode(__ldg(v1l_in + gi)), v2ol = lo_decode(__ldg(v2l_in + gi));
+                const float t1 = __fmul_rn(a.tau >= 0.f ? a.tau : tau_v1_tgv(gx, gy, N), tmul);
+                const float t2 = __fmul_rn(a.tau >= 0.f ? a.tau : tau_v2_tgv(gx, gy, N), tmul);
                 float v1n = v1o, v1nl = v1ol, v2n = v2o, v2nl = v2ol;
-                add_compensated(v1n, v1nl, -t1 * (et1 - r1));
-                add_compensated(v2n, v2nl, -t2 * (et2 - r2));
+                add_compensated(v1n, v1nl, -__fmul_rn(t1, __fsub_rn(et1, r1)));
+                add_compensated(v2n, v2nl, -__fmul_rn(t2, __fsub_rn(et2, r2)));
+                const unsigned short v1q = lo_encode(v1nl), v2q = lo_encode(v2nl);
+                v1nl = lo_decode(v1q);
+                v2nl = lo_decode(v2q);
                 vb1 = fmaf(a.theta, (v1n - v1o) + (v1nl - v1ol), v1n + v1nl);
                 vb2 = fmaf(a.theta, (v2n - v2o) + (v2nl - v2ol), v2n + v2nl);
                 if (lx >= 1 && ly >= 1) {
                     s_vn1[ly - 1][lx - 1] = v1n;
                     s_vn2[ly - 1][lx - 1] = v2n;
-                    s_vnl1[ly - 1][lx - 1] = v1nl;
-                    s_vnl2[ly - 1][lx - 1] = v2nl;
+                    s_vnl1[ly - 1][lx - 1] = v1q;
+                    s_vnl2[ly - 1][lx - 1] = v2q;
                 }
             }
             s_vb1[ly][lx] = vb1;
@@ -664,13 +674,19 @@ __global__ void k_copy_or_zero(const float* __restrict__ src, float* __restrict_
         dst[i] = src ? src[i] : 0.f;
 }
 
+// Low words of a warm start, stored as the update stores them (bfloat16, see lo_encode).
+__global__ void k_lo_encode(const float* __restrict__ lo, unsigned short* __restrict__ q, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        q[i] = lo_encode(lo[i]);
+}
+
 // Copies the final state out of the ping-pong buffers selected by the iteration count.
 struct OutArgs {
     int n, reg;
     long long S;
     float theta;
     const float* X[2];
-    const float* XL[2];   // low words of the compensated primal pairs
+    const unsigned short* XL[2];   // low words of the compensated primal pairs (bfloat16)
     const float* Y[2];
     const float* q;
     const float* ubar;
@@ -688,8 +704,8 @@ __global__ void k_output(OutArgs a) {
     const int it = a.info->iter;
     const float* x = a.X[it & 1];
     const float* x_prev = a.X[(it + 1) & 1];
-    const float* xl = a.XL[it & 1];
-    const float* xl_prev = a.XL[(it + 1) & 1];
+    const unsigned short* xl = a.XL[it & 1];
+    const unsigned short* xl_prev = a.XL[(it + 1) & 1];
     const float* yrs = a.Y[(it + 1) & 1];  // r^I, s^I were read by the last update
     const int nv = a.reg == PAT_TGV ? 2 : 0;
     const long long nx = NN * (1 + nv), ny = NN * (a.reg == PAT_TGV ? 5 : 2);
@@ -698,7 +714,8 @@ __global__ void k_output(OutArgs a) {
         if (i < nx) {
             if (i < NN && a.u_out) a.u_out[i] = x[i];
             if (a.x_out) a.x_out[i] = x[i];
-            if (a.x_lo_out) a.x_lo_out[i] = xl[i];
+            const float lo = lo_decode(xl[i]);
+            if (a.x_lo_out) a.x_lo_out[i] = lo;
             if (a.xbar_out) {
                 if (i < NN) {
                     a.xbar_out[i] = a.ubar[i];
@@ -706,7 +723,8 @@ __global__ void k_output(OutArgs a) {
                     // vbar^I = v^I + theta (v^I - v^{I-1}) from the compensated pairs, the
                     // same expression as the update kernel's; with I = 0 the warm-start
                     // vbar is not recoverable here and v^0 is returned
-                    a.xbar_out[i] = it > 0 ? fmaf(a.theta, (x[i] - x_prev[i]) + (xl[i] - xl_prev[i]), x[i] + xl[i])
+                    const float lo_prev = lo_decode(xl_prev[i]);
+                    a.xbar_out[i] = it > 0 ? fmaf(a.theta, (x[i] - x_prev[i]) + (lo - lo_prev), x[i] + lo)
                                            : x[i];
                 }
             }
@@ -729,7 +747,7 @@ struct Workspace {
     void* base = nullptr;
     size_t bytes = 0;
     float* X[2] = {nullptr, nullptr};
-    float* XL[2] = {nullptr, nullptr};   // low parts of the compensated primal pairs
+    unsigned short* XL[2] = {nullptr, nullptr};   // low words of the compensated primal pairs (bfloat16)
     float* Y[2] = {nullptr, nullptr};
     float *q = nullptr, *ubar = nullptr, *vbar0 = nullptr;
     int* kt[2] = {nullptr, nullptr};   // fixed-point K^T q, by iteration parity
@@ -750,7 +768,7 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     size_t sz[17] = {nx * 4, nx * 4, ny * 4, ny * 4, S * 4, NN * 4, NN * 4 * 2,
                      (reg == PAT_TGV ? 2 * NN : 1) * 4,
                      NN * 4, S * 4, NN * 4, (size_t)ws.n_data * GAP_DATA_TERMS * 8, (size_t)ws.n_pix * GAP_PIX_TERMS * 8, sizeof(InfoDev),
-                     S * 4, nx * 4, nx * 4};
+                     S * 4, nx * 2, nx * 2};
     size_t total = 0;
     for (int i = 0; i < 17; ++i) {
         off[i] = total;
@@ -775,8 +793,8 @@ static int alloc_workspace(const pat_geometry* g, int reg, Workspace& ws, cudaSt
     ws.pix_part = (double*)(b + off[12]);
     ws.info = (InfoDev*)(b + off[13]);
     ws.qw = (float*)(b + off[14]);
-    ws.XL[0] = (float*)(b + off[15]);
-    ws.XL[1] = (float*)(b + off[16]);
+    ws.XL[0] = (unsigned short*)(b + off[15]);
+    ws.XL[1] = (unsigned short*)(b + off[16]);
     return PAT_OK;
 }
 
@@ -1165,10 +1183,13 @@ static int init_problem(Prob& pr, cudaStream_t st) {
     const float mul[2] = {(float)ratio, (float)(1.0 / ratio)};
     PAT_CUDA(cudaMemcpyAsync(ws.info->step_mul, mul, sizeof mul, cudaMemcpyHostToDevice, st));
     PAT_CUDA(cudaMemsetAsync(ws.kt[0], 0, 2 * NN * sizeof(int), st));
-    if (p->x_lo0_dev)
-        PAT_CUDA(cudaMemcpyAsync(ws.XL[0], p->x_lo0_dev, nx * 4, cudaMemcpyDeviceToDevice, st));
-    else
-        PAT_CUDA(cudaMemsetAsync(ws.XL[0], 0, nx * sizeof(float), st));
+    if (p->x_lo0_dev) {
+        k_lo_encode<<<std::min(4 * sm_count(), ceil_div((long long)nx, 256)), 256, 0, st>>>(p->x_lo0_dev, ws.XL[0],
+                                                                                            (long long)nx);
+        PAT_LAUNCH_CHECK("k_lo_encode");
+    } else {
+        PAT_CUDA(cudaMemsetAsync(ws.XL[0], 0, nx * sizeof(unsigned short), st));
+    }
     const float* xb = p->xbar0_dev ? p->xbar0_dev : p->x0_dev;
     k_copy_or_zero<<<std::min(4 * sm_count(), ceil_div((long long)NN, 256)), 256, 0, st>>>(xb, ws.ubar, (long long)NN);
     PAT_LAUNCH_CHECK("k_copy_or_zero");

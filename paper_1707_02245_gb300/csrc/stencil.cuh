@@ -8,6 +8,8 @@
 // Both backward differences and div read a field "masked" to zero on the last index:
 //   (d^- v)(i) = v'(i) - v'(i-1),  v'(i) = v(i) for 0 <= i < N-1, else 0.
 #pragma once
+
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace pat {
@@ -19,19 +21,22 @@ constexpr double kSqrt2 = 1.4142135623730951;
 // kept as it is; outside, the scale radius / |p| comes from one reciprocal square root
 // (a relative error of a few 1e-7, far inside the FP32 iterates' own).  With radius 0 the
 // result is 0.
+// Projections onto the balls of the pointwise dual constraints (Sec. 3.2).  Every rounding
+// is spelled out (no contraction into fused multiply-adds), so that each kernel, and each
+// unrolled copy within a kernel, that inlines them computes the same bits.
 __device__ __forceinline__ void proj2(float& a, float& b, float radius) {
-    const float n2 = a * a + b * b;
-    const float sc = n2 > radius * radius ? radius * rsqrtf(n2) : 1.f;
-    a *= sc;
-    b *= sc;
+    const float n2 = __fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b));
+    const float sc = n2 > __fmul_rn(radius, radius) ? __fmul_rn(radius, rsqrtf(n2)) : 1.f;
+    a = __fmul_rn(a, sc);
+    b = __fmul_rn(b, sc);
 }
 
 __device__ __forceinline__ void proj3(float& a, float& b, float& c, float radius) {
-    const float n2 = a * a + b * b + c * c;
-    const float sc = n2 > radius * radius ? radius * rsqrtf(n2) : 1.f;
-    a *= sc;
-    b *= sc;
-    c *= sc;
+    const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(a, a), __fmul_rn(b, b)), __fmul_rn(c, c));
+    const float sc = n2 > __fmul_rn(radius, radius) ? __fmul_rn(radius, rsqrtf(n2)) : 1.f;
+    a = __fmul_rn(a, sc);
+    b = __fmul_rn(b, sc);
+    c = __fmul_rn(c, sc);
 }
 
 // Inline diagonal steps of the Pock-Chambolle rule (alpha = 1) for the stencil rows.
@@ -85,6 +90,16 @@ __device__ __forceinline__ void add_compensated(float& hi, float& lo, float delt
     lo = __fsub_rn(t, __fsub_rn(h2, s));
     hi = h2;
 }
+
+// The low word of a compensated pair is stored in 16 bits as a bfloat16 (round to nearest
+// even): 8 significant bits of a word below half an ulp of the high word, so the pair
+// holds hi + lo to about 32 significant bits, and the conversions are single
+// instructions.  lo_round returns the stored value of lo.
+__device__ __forceinline__ unsigned short lo_encode(float lo) {
+    return __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+}
+__device__ __forceinline__ float lo_decode(unsigned short q) { return __bfloat162float(__ushort_as_bfloat16(q)); }
+__device__ __forceinline__ float lo_round(float lo) { return lo_decode(lo_encode(lo)); }
 
 // D_xi = I - gamma xi xi^T applied to p (symmetric).  The roundings are spelled out so
 // that every kernel that inlines this computes the same bits.
