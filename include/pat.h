@@ -43,10 +43,14 @@ extern "C" {
 #define PAT_TGV  1   /* R(u) = min_v ||grad u - v|| + beta ||E v||    Sec. 2.1, eq. (min_TGV) */
 #define PAT_DTV  2   /* R(u) = ||D_xi grad u||_{1,2}, D_xi = I - gamma xi xi^T (not in the
                         paper; the directional TV of Ehrhardt and Betcke)                  */
-#define PAT_WAV  3   /* R(u) = ||W u||_1, Sec. 2.2 eq. (min_wav): W an orthonormal 2-D
-                        wavelet transform (Daubechies-4, periodic, pat_params.wavelet_levels
-                        levels, Mallat layout) standing in for the paper's dual-tree complex
-                        transform; W^-1 = W^T as for the paper's tight frame              */
+#define PAT_WAV  3   /* R(u) = ||W u||_1, Sec. 2.2 eq. (min_wav), W a tight frame
+                        (W^-1 = W^T), periodic, pat_params.wavelet_levels levels:
+                        pat_params.wavelet_kind selects the paper's dual-tree complex
+                        transform (PAT_WAVELET_DTCWT; ||.||_1 sums complex moduli) or an
+                        orthonormal Daubechies-4 transform (PAT_WAVELET_DWT)             */
+#define PAT_WAVELET_DWT    0   /* orthonormal separable DWT, N*N coefficients             */
+#define PAT_WAVELET_DTCWT  1   /* dual-tree complex wavelet transform (Kingsbury), 4*N*N
+                                  real coefficients: see pat_dtcwt_transform            */
 
 #define PAT_PRECOND_DIAG     0  /* Pock-Chambolle diagonal steps (alpha = 1): sigma_i =
                                    1/sum_j|A_ij|, tau_j = 1/sum_i|A_ij|   Sec. 3.3.2      */
@@ -167,6 +171,14 @@ typedef struct {
        device of this library. */
     const float* x_lo0_dev;
     float* x_lo_out_dev;
+    /* PAT_WAV: PAT_WAVELET_DWT (default) or PAT_WAVELET_DTCWT.  With the DT-CWT, r in y
+       has 4*N*N entries (the layout of pat_dtcwt_transform's output), and the filters are
+       those of pat_dtcwt_transform (NULL: the closed-form defaults). */
+    int    wavelet_kind;
+    const double* dtcwt_h1_host;   /* level-1 low-pass, dtcwt_l1 taps (host memory)      */
+    int    dtcwt_l1;
+    const double* dtcwt_hq_host;   /* Q-shift low-pass of tree a, dtcwt_lq taps          */
+    int    dtcwt_lq;
 } pat_params;
 
 #define PAT_ADAPT_NONE     0
@@ -211,7 +223,8 @@ int  pat_reconstruct_batched(int count, const pat_geometry* const* g, const floa
                              void* stream);
 
 /* Step sizes that pat_reconstruct uses for (g, p) (Sec. 3.3.2), computed with FP64
- * sums: sig_q (D*T), tau_u (N*N), sig_r (N*N, one value per pointwise r group),
+ * sums: sig_q (D*T), tau_u (N*N), sig_r (N*N, one value per pointwise r group; PAT_WAV
+ * with the DT-CWT: 4*N*N, one value per coefficient, shared by the two of a complex pair),
  * sig_s (N*N, TGV; may be NULL otherwise), tau_v (2*N*N, TGV; may be NULL otherwise).
  * Output pointers are device memory and may be NULL to skip. */
 int  pat_steps(const pat_geometry* g, const pat_params* p, float* sig_q_dev, float* tau_u_dev,
@@ -256,6 +269,26 @@ int  pat_duality_gap(const pat_geometry* g, const float* f_dev, const pat_params
 /* out = W in (inverse = 0) or W^T in = W^-1 in (inverse != 0) for N x N images, with the
  * transform of PAT_WAV (`levels` levels).  in and out are distinct device buffers. */
 int  pat_wavelet_transform(int n, int levels, const float* in_dev, float* out_dev, int inverse, void* stream);
+
+/* The dual-tree complex wavelet transform (Sec. 2.2; Kingsbury's dual tree) of N x N
+ * images with `levels` levels (N divisible by 2^levels), periodic extension.
+ *  - Two orthonormal filter banks, trees a and b.  Level 1: low-pass h1_host (l1 taps) in
+ *    both trees, tree b's input index offset by one sample.  Levels >= 2: the Q-shift
+ *    low-pass hq_host (lq taps) in tree a and its time reverse in tree b.  High-pass
+ *    g[n] = (-1)^n h[L - 1 - n].  One step: a[k] = sum_n h[n] x[(2k + n + o) mod M].
+ *    NULL selects the closed-form defaults: Daubechies' 4-tap filter at level 1 and the
+ *    orthonormal 4-tap (5 - s15, 5 + s15, 3 + s15, 3 - s15) / (8 sqrt 2) (s15 = sqrt 15),
+ *    centre a quarter sample before its midpoint, at levels >= 2.  Filters must be
+ *    orthonormal (to 1e-6) with an even length 2..16.
+ *  - Four separable transforms T_t, t = 2 p + q (tree p along x, q along y), each in the
+ *    Mallat layout.  out (inverse = 0, 4*N*N floats, four planes): (1/2) T u with every
+ *    detail position changed to z1 = ((aa - bb) + i (ab + ba)) / sqrt 2 and
+ *    z2 = ((aa + bb) + i (ba - ab)) / sqrt 2 stored as (Re z1, Im z1, Re z2, Im z2); at
+ *    the LL positions of the last level plane c holds (1/2) T_c.  W^T W = I.
+ *  - inverse != 0: out (N*N) = W^T in (in: 4*N*N floats).
+ * in and out are distinct device buffers; filters are host arrays. */
+int  pat_dtcwt_transform(int n, int levels, const double* h1_host, int l1, const double* hq_host, int lq,
+                         const float* in_dev, float* out_dev, int inverse, void* stream);
 
 /* ---- measurement pre-processing (Sec. 4.3) ------------------------------------------ */
 /* Data f (D*T, detector-major) for the reconstruction from measured pressures p and the

@@ -37,6 +37,7 @@ EXPORTED = [
     "pat_adjoint_worklist",
     "pat_profile_enable", "pat_profile_read", "pat_kernel_launches", "pat_adjoint_noalloc",
     "pat_tune_step_ratio", "pat_tune_step_ratio_batched", "pat_preprocess", "pat_wavelet_transform",
+    "pat_dtcwt_transform",
     "pat_time_phases", "pat_forward_plan", "pat_geometry_set_shapes", "pat_geometry_get_shapes", "pat_tune_shapes",
     # learned warm start (include/pat_unet.h)
     "pat_conv3x3_forward", "pat_conv3x3_backward_data", "pat_conv3x3_backward_weight",
@@ -71,7 +72,9 @@ class pat_params(ctypes.Structure):
                 ("x_out_dev", ctypes.c_void_p), ("xbar_out_dev", ctypes.c_void_p),
                 ("y_out_dev", ctypes.c_void_p), ("step_ratio", ctypes.c_double), ("adapt", ctypes.c_int),
                 ("wavelet_levels", ctypes.c_int), ("x_lo0_dev", ctypes.c_void_p),
-                ("x_lo_out_dev", ctypes.c_void_p)]
+                ("x_lo_out_dev", ctypes.c_void_p), ("wavelet_kind", ctypes.c_int),
+                ("dtcwt_h1_host", ctypes.c_void_p), ("dtcwt_l1", ctypes.c_int),
+                ("dtcwt_hq_host", ctypes.c_void_p), ("dtcwt_lq", ctypes.c_int)]
 
 
 class pat_shapes(ctypes.Structure):
@@ -83,6 +86,7 @@ class pat_shapes(ctypes.Structure):
 
 PAT_FWD_AUTO, PAT_FWD_SLAB_TWO, PAT_FWD_SLAB_ONE, PAT_FWD_GLOBAL = -1, 0, 1, 2
 PAT_UPD_32X4, PAT_UPD_32X8, PAT_UPD_64X4 = 0, 1, 2
+PAT_WAVELET_DWT, PAT_WAVELET_DTCWT = 0, 1
 
 
 class pat_unet_desc(ctypes.Structure):
@@ -131,6 +135,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pat_duality_gap": (i, [vp, vp, ctypes.POINTER(pat_params), vp, vp, ctypes.POINTER(d), vp]),
         "pat_preprocess": (i, [vp, vp, vp, ctypes.POINTER(d), d, vp, vp]),
         "pat_wavelet_transform": (i, [i, i, vp, vp, i, vp]),
+        "pat_dtcwt_transform": (i, [i, i, vp, i, vp, i, vp, vp, i, vp]),
         "pat_tune_step_ratio_batched": (i, [i, ctypes.POINTER(vp), ctypes.POINTER(vp), ctypes.POINTER(pat_params),
                                             ctypes.POINTER(d), i, i, ctypes.POINTER(d), ctypes.POINTER(d), vp]),
         "pat_tune_step_ratio": (i, [vp, vp, ctypes.POINTER(pat_params), ctypes.POINTER(d), i, i, ctypes.POINTER(d),
@@ -288,7 +293,9 @@ def pat_params_default() -> pat_params:
 def make_params(reg=PAT_TV, alpha=0.05, beta=1.0, gamma=0.95, xi=None, iters=100, tol=0.0, gap_every=10,
                 precond=PAT_PRECOND_DIAG, theta=1.0, box_u=2.0, box_v=4.0, x0=None, xbar0=None, y0=None,
                 x_out=None, xbar_out=None, y_out=None, step_ratio=1.0, adapt=PAT_ADAPT_NONE,
-                wavelet_levels=4, x_lo0=None, x_lo_out=None) -> pat_params:
+                wavelet_levels=4, x_lo0=None, x_lo_out=None, wavelet_kind=0, dtcwt_filters=None) -> pat_params:
+    """dtcwt_filters: None (the closed-form defaults) or (level-1 low-pass, Q-shift low-pass of
+    tree a) as float64 sequences."""
     p = pat_params_default()
     p.reg, p.alpha, p.beta, p.gamma = reg, alpha, beta, gamma
     p.xi_dev = _ptr(xi)
@@ -298,8 +305,14 @@ def make_params(reg=PAT_TV, alpha=0.05, beta=1.0, gamma=0.95, xi=None, iters=100
     p.x_out_dev, p.xbar_out_dev, p.y_out_dev = _ptr(x_out), _ptr(xbar_out), _ptr(y_out)
     p.step_ratio, p.adapt, p.wavelet_levels = step_ratio, adapt, wavelet_levels
     p.x_lo0_dev, p.x_lo_out_dev = _ptr(x_lo0), _ptr(x_lo_out)
+    p.wavelet_kind = wavelet_kind
+    fl = None
+    if dtcwt_filters is not None:
+        fl = [(ctypes.c_double * len(h))(*[float(v) for v in h]) for h in dtcwt_filters]
+        p.dtcwt_h1_host, p.dtcwt_l1 = ctypes.cast(fl[0], ctypes.c_void_p).value, len(fl[0])
+        p.dtcwt_hq_host, p.dtcwt_lq = ctypes.cast(fl[1], ctypes.c_void_p).value, len(fl[1])
     # keep the buffers alive as long as the parameter block that points at them
-    p._keep = [xi, x0, xbar0, y0, x_out, xbar_out, y_out, x_lo0, x_lo_out]
+    p._keep = [xi, x0, xbar0, y0, x_out, xbar_out, y_out, x_lo0, x_lo_out, fl]
     return p
 
 
@@ -395,6 +408,20 @@ def pat_time_phases(geoms, fs, params, reps: int, stream=None) -> dict:
     us = (ctypes.c_double * len(PHASES))()
     _check(load().pat_time_phases(n, G, F, Pp, int(reps), us, _stream(stream)), "pat_time_phases")
     return {name: us[k] for k, name in enumerate(PHASES)}
+
+
+def pat_dtcwt_transform(n: int, levels: int, in_dev, out_dev, inverse: bool = False, filters=None,
+                        stream=None) -> None:
+    """W in (out: 4 n^2 floats) or W^T in (in: 4 n^2 floats, out: n^2) of the dual-tree
+    complex wavelet transform (see include/pat.h); filters: None or (h1, hq)."""
+    h1 = hq = None
+    l1 = lq = 0
+    if filters is not None:
+        h1 = (ctypes.c_double * len(filters[0]))(*[float(v) for v in filters[0]])
+        hq = (ctypes.c_double * len(filters[1]))(*[float(v) for v in filters[1]])
+        l1, lq = len(h1), len(hq)
+    _check(load().pat_dtcwt_transform(n, levels, h1, l1, hq, lq, _ptr(in_dev), _ptr(out_dev), 1 if inverse else 0,
+                                      _stream(stream)), "pat_dtcwt_transform")
 
 
 def pat_wavelet_transform(n: int, levels: int, in_dev, out_dev, inverse: bool = False, stream=None) -> None:

@@ -19,7 +19,7 @@ BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIBNAME = "libpat_pdhg.so"
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["geometry.cu", "projector.cu", "adjoint.cu", "pdhg.cu", "noalloc.cu", "conv.cu", "unet.cu", "preprocess.cu", "wavelet.cu"]
+SOURCES = ["geometry.cu", "projector.cu", "adjoint.cu", "pdhg.cu", "noalloc.cu", "conv.cu", "unet.cu", "preprocess.cu", "wavelet.cu", "dtcwt.cu"]
 
 
 def nvcc() -> str:

@@ -338,6 +338,37 @@ struct WavGapArgs {
     double* partials;
     const int* stop;
 };
+// the dual-tree complex wavelet transform (dtcwt.cu)
+constexpr int CWT_MAX_TAPS = 16;
+struct CwtBank {          // FP32 taps: level 1 (both trees), Q-shift tree a, Q-shift tree b
+    int l1, lq;
+    float h1[CWT_MAX_TAPS], g1[CWT_MAX_TAPS];
+    float ha[CWT_MAX_TAPS], ga[CWT_MAX_TAPS];
+    float hb[CWT_MAX_TAPS], gb[CWT_MAX_TAPS];
+};
+struct CwtGapArgs {
+    int n, terms, ll_side;
+    const float* tu;     // T planes of u (4 N^2)
+    KtView kt;
+    const float* wtr;    // W^T r
+    const float* u;
+    const float* u_old;
+    double* partials;
+    const int* stop;
+};
+int cwt_bank(const double* h1, int l1, const double* hq, int lq, CwtBank& bank, std::vector<double>* h1_out,
+             std::vector<double>* hq_out);
+void cwt_abs_sums(int n, int levels, const std::vector<double>& h1, const std::vector<double>& hq,
+                  std::vector<double>& rows, std::vector<double>& cols);
+int launch_cwt_analysis(const float* in, int N, int levels, const CwtBank& bank, float* out, float* scratch,
+                        const int* stop, cudaStream_t st);
+int launch_cwt_synthesis(float* in, int N, int levels, const CwtBank& bank, float* out, float* scratch,
+                         const int* stop, cudaStream_t st);
+int launch_cwt_dual(float* r, const float* T, const float* sig_r, const float* step_mul, float alpha, int N, int levels,
+                    const int* stop, cudaStream_t st);
+int launch_cwt_uncombine(const float* r, float* T, int N, int levels, const int* stop, cudaStream_t st);
+int launch_cwt_gap_pixels(const CwtGapArgs& a, int nblocks, cudaStream_t st);
+
 bool wav_levels_ok(int n, int levels);
 void wav_abs_sums(int n, int levels, std::vector<double>& rows, std::vector<double>& cols);
 int launch_wav_analysis(const float* in, int N, int levels, float* out, float* scratch, const int* stop, cudaStream_t st);

@@ -811,6 +811,13 @@ static int validate(const pat_geometry* g, const pat_params* p, const char* who)
         if (!wav_levels_ok(g->desc.n, J)) return bad("PAT_WAV needs 1..12 levels and N divisible by 2^levels");
         if (p->precond != PAT_PRECOND_DIAG) return bad("PAT_WAV uses the diagonal steps only");
         if (p->adapt != PAT_ADAPT_NONE) return bad("PAT_WAV has no adaptive balance");
+        if (p->wavelet_kind != PAT_WAVELET_DWT && p->wavelet_kind != PAT_WAVELET_DTCWT)
+            return bad("wavelet_kind must be PAT_WAVELET_DWT or PAT_WAVELET_DTCWT");
+        if (p->wavelet_kind == PAT_WAVELET_DTCWT) {
+            CwtBank bank;
+            const int frc = cwt_bank(p->dtcwt_h1_host, p->dtcwt_l1, p->dtcwt_hq_host, p->dtcwt_lq, bank, nullptr, nullptr);
+            if (frc) return frc;
+        }
     }
     if (!(p->alpha >= 0) || !std::isfinite(p->alpha)) return bad("alpha must be finite and >= 0");
     if (!(p->beta >= 0) || !std::isfinite(p->beta)) return bad("beta must be finite and >= 0");
@@ -1352,15 +1359,49 @@ static int run_iterations(const IterPlan& ip, const char* base, int iters, int g
 // ---------------------------------------------------------------------------------
 static int wav_levels_of(const pat_params* p) { return p->wavelet_levels > 0 ? p->wavelet_levels : 4; }
 
-// sigma_q, tau_u and sigma_r of the wavelet model: the alpha = 1 diagonal rule on A = (K; W)
-static int wav_steps(const pat_geometry* g, int levels, float* sig_q, float* tau_u, float* sig_r, double s_ratio,
-                     cudaStream_t st) {
+// The transform of a PAT_WAV problem: the orthonormal DWT (N^2 coefficients) or the
+// DT-CWT (4 N^2 coefficients, four planes) with its filter bank.
+struct WavModel {
+    int kind = PAT_WAVELET_DWT, J = 4, N = 0;
+    long long nr = 0;
+    CwtBank bank{};
+    std::vector<double> h1, hq;
+};
+
+static int wav_model(const pat_geometry* g, const pat_params* p, WavModel& m) {
+    m.kind = p->wavelet_kind;
+    m.J = wav_levels_of(p);
+    m.N = g->desc.n;
+    const long long NN = (long long)m.N * m.N;
+    m.nr = m.kind == PAT_WAVELET_DTCWT ? 4 * NN : NN;
+    if (m.kind == PAT_WAVELET_DTCWT)
+        return cwt_bank(p->dtcwt_h1_host, p->dtcwt_l1, p->dtcwt_hq_host, p->dtcwt_lq, m.bank, &m.h1, &m.hq);
+    return PAT_OK;
+}
+
+// sigma_q, tau_u and sigma_r of the wavelet model: the alpha = 1 diagonal rule on A = (K; W).
+// With the DT-CWT the two rows of a complex coefficient share one step, 1 / (the larger of
+// their row sums): the dual prox of a disc is the projection onto it only with one step.
+static int wav_steps(const pat_geometry* g, const WavModel& m, float* sig_q, float* tau_u, float* sig_r,
+                     double s_ratio, cudaStream_t st) {
     const int N = g->desc.n;
     const long long NN = (long long)N * N, S = (long long)g->desc.n_det * g->desc.n_t;
     int rc = ensure_precond(g, st);
     if (rc) return rc;
     std::vector<double> rows, cols;
-    wav_abs_sums(N, levels, rows, cols);
+    if (m.kind == PAT_WAVELET_DTCWT) {
+        cwt_abs_sums(N, m.J, m.h1, m.hq, rows, cols);
+        const int side = N >> m.J;
+        for (long long i = 0; i < NN; ++i) {
+            if ((int)(i % N) < side && (int)(i / N) < side) continue;   // LL: one row each
+            for (int a = 0; a < 4; a += 2) {
+                const double mx = std::max(rows[a * NN + i], rows[(a + 1) * NN + i]);
+                rows[a * NN + i] = rows[(a + 1) * NN + i] = mx;
+            }
+        }
+    } else {
+        wav_abs_sums(N, m.J, rows, cols);
+    }
     if (sig_q) {
         k_sig_q<<<ceil_div(S, 256), 256, 0, st>>>(g->pc.krow, sig_q, S);
         PAT_LAUNCH_CHECK("k_sig_q");
@@ -1384,9 +1425,9 @@ static int wav_steps(const pat_geometry* g, int levels, float* sig_q, float* tau
         }
     }
     if (sig_r) {
-        std::vector<float> h((size_t)NN);
-        for (long long i = 0; i < NN; ++i) h[i] = rows[i] > 0 ? (float)(1.0 / rows[i] / s_ratio) : 1.f;
-        PAT_CUDA(cudaMemcpyAsync(sig_r, h.data(), NN * sizeof(float), cudaMemcpyHostToDevice, st));
+        std::vector<float> h((size_t)m.nr);
+        for (long long i = 0; i < m.nr; ++i) h[i] = rows[i] > 0 ? (float)(1.0 / rows[i] / s_ratio) : 1.f;
+        PAT_CUDA(cudaMemcpyAsync(sig_r, h.data(), m.nr * sizeof(float), cudaMemcpyHostToDevice, st));
         PAT_CUDA(cudaStreamSynchronize(st));
     }
     return PAT_OK;
@@ -1398,13 +1439,17 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
     const long long NN = (long long)N * N, S = (long long)g->desc.n_det * g->desc.n_t;
     const int n_data = g->fwd_n_ctas;
     const int n_pix = pix_blocks(N);
-    // workspace
-    enum { U, UOLD, UBAR, Q, QW, KT, R, WB, WTR, SCR, SCR2, WU, TAU, SIGR, SIGQ, DPART, PPART, INFO, NBUF };
-    const size_t nn4 = (size_t)NN * 4;
+    WavModel wm;
+    if (int mrc = wav_model(g, p, wm)) return mrc;
+    const bool cwt = wm.kind == PAT_WAVELET_DTCWT;
+    const long long NR = wm.nr;   // coefficients of W u
+    // workspace (DT-CWT: R, WB, WU and SIGR hold 4 planes, SCRT the tree form of r)
+    enum { U, UOLD, UBAR, Q, QW, KT, R, WB, WTR, SCR, SCR2, WU, TAU, SIGR, SIGQ, DPART, PPART, INFO, SCRT, NBUF };
+    const size_t nn4 = (size_t)NN * 4, nr4 = (size_t)NR * 4;
     size_t sz[NBUF] = {nn4, nn4, nn4,
-                       (size_t)S * 4, (size_t)S * 4, (size_t)NN * 8, nn4, nn4, nn4, nn4, nn4, nn4,
-                       nn4, nn4, (size_t)S * 4, (size_t)n_data * GAP_DATA_TERMS * 8,
-                       (size_t)n_pix * GAP_PIX_TERMS * 8, sizeof(InfoDev)};
+                       (size_t)S * 4, (size_t)S * 4, (size_t)NN * 8, nr4, nr4, nn4, nn4, nn4, nr4,
+                       nn4, nr4, (size_t)S * 4, (size_t)n_data * GAP_DATA_TERMS * 8,
+                       (size_t)n_pix * GAP_PIX_TERMS * 8, sizeof(InfoDev), cwt ? nr4 : 16};
     size_t off[NBUF], total = 0;
     for (int i = 0; i < NBUF; ++i) {
         off[i] = total;
@@ -1419,12 +1464,13 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
     float *scr = (float*)(b + off[SCR]), *scr2 = (float*)(b + off[SCR2]), *wu = (float*)(b + off[WU]);
     float *tau = (float*)(b + off[TAU]), *sigr = (float*)(b + off[SIGR]), *sigq = (float*)(b + off[SIGQ]);
     double *dpart = (double*)(b + off[DPART]), *ppart = (double*)(b + off[PPART]);
+    float* scrt = (float*)(b + off[SCRT]);
     InfoDev* in = (InfoDev*)(b + off[INFO]);
     cudaEvent_t e0, e1;
     PAT_CUDA(cudaEventCreate(&e0));
     PAT_CUDA(cudaEventCreate(&e1));
     PAT_CUDA(cudaEventRecord(e0, st));
-    int rc = wav_steps(g, J, sigq, tau, sigr, 1.0, st);
+    int rc = wav_steps(g, wm, sigq, tau, sigr, 1.0, st);
     // start
     if (!rc) {
         auto cp = [&](float* dst, const float* src, long long n) -> int {
@@ -1435,7 +1481,7 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
         rc = cp(u, p->x0_dev, NN);
         if (!rc) rc = cp(ubar, p->xbar0_dev ? p->xbar0_dev : p->x0_dev, NN);
         if (!rc) rc = cp(q, p->y0_dev, S);
-        if (!rc) rc = cp(r, p->y0_dev ? p->y0_dev + S : nullptr, NN);
+        if (!rc) rc = cp(r, p->y0_dev ? p->y0_dev + S : nullptr, NR);
     }
     if (!rc) {
         PAT_CUDA(cudaMemsetAsync(in, 0, sizeof(InfoDev), st));
@@ -1504,12 +1550,22 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
         const int par = it & 1;
         int e = launch_forward_b(FWD_PROX, (const FwdArgs*)(base + fw_off[par]), (const int2*)(base + fmap_off), nf,
                                  g->view.n_slabs, g->fwd_smem, s);
-        if (!e) e = launch_wav_analysis(ubar, N, J, wb, scr, &in->stop, s);
-        if (!e) e = launch_wav_dual(r, wb, sigr, in->step_mul, (float)p->alpha, NN, &in->stop, s);
+        if (cwt) {
+            if (!e) e = launch_cwt_analysis(ubar, N, J, wm.bank, wb, scr, &in->stop, s);
+            if (!e) e = launch_cwt_dual(r, wb, sigr, in->step_mul, (float)p->alpha, N, J, &in->stop, s);
+        } else {
+            if (!e) e = launch_wav_analysis(ubar, N, J, wb, scr, &in->stop, s);
+            if (!e) e = launch_wav_dual(r, wb, sigr, in->step_mul, (float)p->alpha, NN, &in->stop, s);
+        }
         if (!e)
             e = launch_adjoint_b((const AdjArgs*)(base + ad_off[par]), (const int2*)(base + amap_off), g->adj_items,
                                  true, s);
-        if (!e) e = launch_wav_synthesis(r, N, J, wtr, scr, &in->stop, s);
+        if (cwt) {
+            if (!e) e = launch_cwt_uncombine(r, scrt, N, J, &in->stop, s);
+            if (!e) e = launch_cwt_synthesis(scrt, N, J, wm.bank, wtr, scr, &in->stop, s);
+        } else {
+            if (!e) e = launch_wav_synthesis(r, N, J, wtr, scr, &in->stop, s);
+        }
         WavPrimalArgs pa;
         pa.n = N;
         pa.theta = (float)p->theta;
@@ -1526,12 +1582,18 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
         pa.iter = &in->iter;
         if (!e) e = launch_wav_primal(pa, s);
         if (gap && !e) {
-            e = launch_wav_analysis(u, N, J, wu, scr2, &in->stop, s);
+            e = cwt ? launch_cwt_analysis(u, N, J, wm.bank, wu, scr2, &in->stop, s)
+                    : launch_wav_analysis(u, N, J, wu, scr2, &in->stop, s);
             if (!e)
                 e = launch_forward_b(FWD_GAP, (const FwdArgs*)(base + fg_off), (const int2*)(base + fmap_off), nf,
                                      g->view.n_slabs, g->fwd_smem, s);
-            WavGapArgs wg{N, GAP_PIX_TERMS, wu, pa.kt, wtr, u, u_old, ppart, &in->stop};
-            if (!e) e = launch_wav_gap_pixels(wg, n_pix, s);
+            if (cwt) {
+                CwtGapArgs cg{N, GAP_PIX_TERMS, N >> J, wu, pa.kt, wtr, u, u_old, ppart, &in->stop};
+                if (!e) e = launch_cwt_gap_pixels(cg, n_pix, s);
+            } else {
+                WavGapArgs wg{N, GAP_PIX_TERMS, wu, pa.kt, wtr, u, u_old, ppart, &in->stop};
+                if (!e) e = launch_wav_gap_pixels(wg, n_pix, s);
+            }
             if (!e) {
                 k_gap_final_b<<<GAP_FINAL_BLOCKS, GAP_FINAL_THREADS, 0, s>>>((const FinalArgs*)(base + fi_off),
                                                               (const int2*)(base + finmap_off));
@@ -1615,7 +1677,7 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
         if (p->xbar_out_dev) PAT_CUDA(cudaMemcpyAsync(p->xbar_out_dev, ubar, NN * 4, cudaMemcpyDeviceToDevice, st));
         if (p->y_out_dev) {
             PAT_CUDA(cudaMemcpyAsync(p->y_out_dev, q, S * 4, cudaMemcpyDeviceToDevice, st));
-            PAT_CUDA(cudaMemcpyAsync(p->y_out_dev + S, r, NN * 4, cudaMemcpyDeviceToDevice, st));
+            PAT_CUDA(cudaMemcpyAsync(p->y_out_dev + S, r, NR * 4, cudaMemcpyDeviceToDevice, st));
         }
     }
     InfoDev h{};
@@ -2366,7 +2428,11 @@ extern "C" int pat_steps(const pat_geometry* g, const pat_params* p, float* sig_
     int rc = validate(g, p, "pat_steps");
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    if (p->reg == PAT_WAV) return wav_steps(g, wav_levels_of(p), sig_q_dev, tau_u_dev, sig_r_dev, step_ratio_of(p), st);
+    if (p->reg == PAT_WAV) {
+        WavModel wm;
+        if (int mrc = wav_model(g, p, wm)) return mrc;
+        return wav_steps(g, wm, sig_q_dev, tau_u_dev, sig_r_dev, step_ratio_of(p), st);
+    }
     const int N = g->desc.n;
     const long long NN = (long long)N * N, S = (long long)g->desc.n_det * g->desc.n_t;
     if (p->precond == PAT_PRECOND_SCALAR2) {
