@@ -461,14 +461,6 @@ __device__ __forceinline__ void gap_pixels_block(const GapArgs& a, const int lb)
         for (int c = 0; c < GAP_PIX_TERMS; ++c) a.partials[GAP_PIX_TERMS * lb + c] = dacc[c];
 }
 
-template <int REG>
-__global__ void __launch_bounds__(256) k_gap_pixels_b(const GapArgs* __restrict__ args, const int2* __restrict__ map) {
-    const int2 pm = map[blockIdx.x];
-    __shared__ GapArgs sa;
-    const GapArgs& a = stage_args(args, pm.x, sa);
-    if (a.stop && *(volatile const int*)a.stop) return;
-    gap_pixels_block<REG>(a, pm.y);
-}
 
 constexpr int GAP_FINAL_BLOCKS = 32;
 constexpr int GAP_FINAL_THREADS = 32;   // one warp: the final sums are FP64, kept to few lanes
@@ -516,6 +508,8 @@ __device__ void balance_update(InfoDev* in, double primal_res, double dual_res) 
     in->n_adjust += 1;
 }
 
+__device__ __forceinline__ void gap_evaluate(const FinalArgs& a, const double (&t)[GAP_TERMS]);
+
 // Two-level FP64 reduction in a fixed order: each of GAP_FINAL_BLOCKS blocks sums a fixed
 // strided subset of the partials, the last block to finish adds the block sums in index
 // order and evaluates the gap, the residual and the stopping test.
@@ -551,6 +545,12 @@ __device__ __forceinline__ void gap_final_block(const FinalArgs& a, const int lb
     in->final_ticket = 0;
     double t[GAP_TERMS];
     for (int c = 0; c < GAP_TERMS; ++c) t[c] = s_tot[c];
+    gap_evaluate(a, t);
+}
+
+// The gap, the residual and the stopping test from the summed terms (one thread).
+__device__ __forceinline__ void gap_evaluate(const FinalArgs& a, const double (&t)[GAP_TERMS]) {
+    InfoDev* in = a.info;
     const double res2 = t[0], q2 = t[1], qf = t[2], dres_q = t[3];
     const double r1 = t[4], r2 = t[5], bu = t[6], bv = t[7], dx2 = t[8], x2 = t[9], dres_rs = t[10];
     const double reg = a.reg == PAT_TGV ? r1 + a.beta * r2 : r1;
@@ -584,6 +584,44 @@ __global__ void __launch_bounds__(GAP_FINAL_THREADS) k_gap_final_b(const FinalAr
     const FinalArgs& a = stage_args(args, pm.x, sa);
     if (*(volatile const int*)&a.info->stop) return;
     gap_final_block(a, pm.y);
+}
+
+// The gap's pixel pass with the final reduction in its last block: every block writes its
+// partial sums; the last of a problem's blocks to finish (a ticket) adds all the problem's
+// data and pixel partials in FP64 in a fixed order (thread t takes rows t, t + 256, ...,
+// then a fixed shuffle and warp tree) and evaluates the gap and the stopping test.
+template <int REG>
+__global__ void __launch_bounds__(256) k_gap_pixels_final_b(const GapArgs* __restrict__ args,
+                                                            const FinalArgs* __restrict__ fin,
+                                                            const int2* __restrict__ map) {
+    const int2 pm = map[blockIdx.x];
+    __shared__ GapArgs sa;
+    const GapArgs& a = stage_args(args, pm.x, sa);
+    if (a.stop && *(volatile const int*)a.stop) return;
+    gap_pixels_block<REG>(a, pm.y);
+    __shared__ bool s_last;
+    InfoDev* in = fin[pm.x].info;
+    if (threadIdx.x == 0) {
+        __threadfence();   // this block's partials before its ticket
+        s_last = atomicAdd(&in->final_ticket, 1u) == (unsigned)(a.nblocks - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    const FinalArgs f = fin[pm.x];
+    double acc[GAP_TERMS];
+#pragma unroll
+    for (int c = 0; c < GAP_TERMS; ++c) acc[c] = 0.0;
+    for (int b = threadIdx.x; b < f.n_data; b += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < GAP_DATA_TERMS; ++c) acc[c] += __ldcg(f.data_part + GAP_DATA_TERMS * b + c);
+    for (int b = threadIdx.x; b < f.n_pix; b += blockDim.x)
+#pragma unroll
+        for (int c = 0; c < GAP_PIX_TERMS; ++c) acc[GAP_DATA_TERMS + c] += __ldcg(f.pix_part + GAP_PIX_TERMS * b + c);
+    block_sum<GAP_TERMS>(acc);
+    if (threadIdx.x != 0) return;
+    in->final_ticket = 0;
+    gap_evaluate(f, acc);
 }
 
 // ---------------------------------------------------------------------------------
@@ -902,9 +940,7 @@ struct FwdGroup {
 struct GapPlan {
     FwdGroup fwd[FWD_MAX_CLUSTER];
     int n_fwd_groups = 0;
-    size_t map_fin = 0;
     size_t map_pix[3] = {0, 0, 0};
-    int n_fin = 0;
     int n_pix[3] = {0, 0, 0};
 };
 
@@ -948,14 +984,10 @@ static int launch_forward_groups(int epi, const FwdArgs* args, const GapPlan& gp
 }
 
 static void build_gap_plan(const Prob* pr, int B, Arena& ar, GapPlan& gp) {
-    std::vector<int2> fin, pix[3];
-    for (int b = 0; b < B; ++b) {
+    std::vector<int2> pix[3];
+    for (int b = 0; b < B; ++b)
         for (int i = 0; i < pr[b].ws.n_pix; ++i) pix[pr[b].p.reg].push_back(make_int2(b, i));
-        for (int i = 0; i < GAP_FINAL_BLOCKS; ++i) fin.push_back(make_int2(b, i));
-    }
     forward_groups(pr, B, ar, gp);
-    gp.map_fin = ar.put(fin.data(), fin.size());
-    gp.n_fin = (int)fin.size();
     for (int r = 0; r < 3; ++r) {
         gp.map_pix[r] = ar.put(pix[r].data(), pix[r].size());
         gp.n_pix[r] = (int)pix[r].size();
@@ -1052,15 +1084,13 @@ static int launch_gap_phase(const FwdArgs* fa, const GapArgs* ga, const FinalArg
         if (!gp.n_pix[r]) continue;
         const int2* map = (const int2*)(base + gp.map_pix[r]);
         if (r == PAT_TV)
-            k_gap_pixels_b<PAT_TV><<<gp.n_pix[r], 256, 0, st>>>(ga, map);
+            k_gap_pixels_final_b<PAT_TV><<<gp.n_pix[r], 256, 0, st>>>(ga, fi, map);
         else if (r == PAT_TGV)
-            k_gap_pixels_b<PAT_TGV><<<gp.n_pix[r], 256, 0, st>>>(ga, map);
+            k_gap_pixels_final_b<PAT_TGV><<<gp.n_pix[r], 256, 0, st>>>(ga, fi, map);
         else
-            k_gap_pixels_b<PAT_DTV><<<gp.n_pix[r], 256, 0, st>>>(ga, map);
-        PAT_LAUNCH_CHECK("k_gap_pixels_b");
+            k_gap_pixels_final_b<PAT_DTV><<<gp.n_pix[r], 256, 0, st>>>(ga, fi, map);
+        PAT_LAUNCH_CHECK("k_gap_pixels_final_b");
     }
-    k_gap_final_b<<<gp.n_fin, GAP_FINAL_THREADS, 0, st>>>(fi, (const int2*)(base + gp.map_fin));
-    PAT_LAUNCH_CHECK("k_gap_final_b");
     prof_mark(PAT_PHASE_GAP, st, false);
     return PAT_OK;
 }
