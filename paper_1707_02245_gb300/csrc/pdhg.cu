@@ -69,6 +69,7 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
     const int tid = threadIdx.y * TX + threadIdx.x;
 
     __shared__ float s_r1m[LY][LX], s_r2m[LY][LX];   // r (dTV: D_xi r) masked for div
+    __shared__ float s_r1[LY][LX], s_r2[LY][LX];     // r as stored (the V cells and the tile read it)
     __shared__ float s_ub[LY][LX];                   // ubar on U = tile + high halo
     __shared__ float s_un[TY][TX];                   // u^{n+1} (high word) on the tile
     __shared__ unsigned short s_unl[TY][TX];         // ... its low word (bfloat16)
@@ -110,16 +111,27 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
     }
 
     // ---- stage 1: dual fields on the tile plus halo -------------------------------
+    // Stage 2 visits the same cells.  The 32 x 8 tile (chosen for batches out of L2, where
+    // occupancy matters) recomputes their coordinates there; the other tiles keep them
+    // (measured at 256^2: 5.21 against 5.58 us; out of L2 the extra registers cost more).
+    constexpr bool KEEP = TY != 8;
+    int cl[NCELL], cgi[NCELL];   // cell (ly << 8 | lx) or -1; its global index or -1 off the grid
 #pragma unroll
     for (int kc = 0; kc < NCELL; ++kc) {
         const int c = tid + kc * TX * TY;
+        cl[kc] = -1;
+        cgi[kc] = -1;
         if (c >= LX * LY) break;
         const int lx = c % LX, ly = c / LX;
         const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
         const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
         const int gi = in ? gy * N + gx : 0;
+        cl[kc] = (ly << 8) | lx;
+        cgi[kc] = in ? gi : -1;
         float r1 = in ? __ldg(r1_in + gi) : 0.f;
         float r2 = in ? __ldg(r2_in + gi) : 0.f;
+        s_r1[ly][lx] = r1;
+        s_r2[ly][lx] = r2;
         if (REG == PAT_DTV) {
             const float xi0 = in ? __ldg(xi0_in + gy * N + gx) : 0.f;
             const float xi1 = in ? __ldg(xi1_in + gy * N + gx) : 0.f;
@@ -141,15 +153,27 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
     // ---- stage 2: primal step and extrapolation on U (u) and V (v) ------------------
 #pragma unroll
     for (int kc = 0; kc < NCELL; ++kc) {
-        const int c = tid + kc * TX * TY;
-        if (c >= LX * LY) break;
-        const int lx = c % LX, ly = c / LX;
+        int lx, ly, gi;
+        bool in;
+        if (KEEP) {
+            if (cl[kc] < 0) break;
+            lx = cl[kc] & 0xff;
+            ly = cl[kc] >> 8;
+            in = cgi[kc] >= 0;
+            gi = cgi[kc];
+        } else {
+            const int c = tid + kc * TX * TY;
+            if (c >= LX * LY) break;
+            lx = c % LX;
+            ly = c / LX;
+            const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
+            in = gx >= 0 && gx < N && gy >= 0 && gy < N;
+            gi = gy * N + gx;
+        }
         const int gx = x0 - 1 + lx, gy = y0 - 1 + ly;
-        const bool in = gx >= 0 && gx < N && gy >= 0 && gy < N;
         if (lx >= 1 && ly >= 1) {  // U: u^{n+1}, ubar
             float ub = 0.f;
             if (in) {
-                const int gi = gy * N + gx;
                 const float divr = s_r1m[ly][lx] - s_r1m[ly][lx - 1] + s_r2m[ly][lx] - s_r2m[ly - 1][lx];
                 // (every rounding spelled out: a halo cell's value must equal, bit for
                 // bit, the one its own tile computes in another unrolled copy)
@@ -172,7 +196,6 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
         if (REG == PAT_TGV && lx <= TX && ly <= TY) {  // V: v^{n+1}, vbar
             float vb1 = 0.f, vb2 = 0.f;
             if (in) {
-                const int gi = gy * N + gx;
                 const bool ax = gx < N - 1, by = gy < N - 1;
                 // E^T s = (-d_x^+ s11 - d_y^+ s12 / sqrt2, -d_y^+ s22 - d_x^+ s12 / sqrt2)
                 const float dx11 = ax ? s_s11[ly][lx + 1] - s_s11[ly][lx] : 0.f;
@@ -181,7 +204,7 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
                 const float dx12 = ax ? s_s12[ly][lx + 1] - s_s12[ly][lx] : 0.f;
                 const float et1 = __fsub_rn(-dx11, __fmul_rn(dy12, kInvSqrt2f));
                 const float et2 = __fsub_rn(-dy22, __fmul_rn(dx12, kInvSqrt2f));
-                const float r1 = __ldg(r1_in + gi), r2 = __ldg(r2_in + gi);
+                const float r1 = s_r1[ly][lx], r2 = s_r2[ly][lx];
                 const float v1o = __ldg(v1_in + gi), v2o = __ldg(v2_in + gi);
                 const float v1ol = lo_decode(__ldg(v1l_in + gi)), v2ol = lo_decode(__ldg(v2l_in + gi));
                 const float t1 = __fmul_rn(a.tau >= 0.f ? a.tau : tau_v1_tgv(gx, gy, N), tmul);
@@ -216,7 +239,7 @@ __device__ __forceinline__ void update_tile(const UpdateArgs& a, const int bx, c
         const float ub = s_ub[ly][lx];
         const float gu0 = ax ? s_ub[ly][lx + 1] - ub : 0.f;
         const float gu1 = by ? s_ub[ly + 1][lx] - ub : 0.f;
-        float r1 = __ldg(r1_in + gi), r2 = __ldg(r2_in + gi);
+        float r1 = s_r1[ly][lx], r2 = s_r2[ly][lx];
         if (REG == PAT_TV) {
             const float sr = (a.sig2 >= 0.f ? a.sig2 : sig_r_tv(gx, gy, N)) * smul;
             r1 = fmaf(sr, gu0, r1);
