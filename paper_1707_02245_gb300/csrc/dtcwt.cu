@@ -43,12 +43,21 @@ __device__ __forceinline__ AxisF axis_filters(const CwtBank& b, int tree, bool l
     return tree ? AxisF{b.hb, b.gb, b.lq, 0} : AxisF{b.ha, b.ga, b.lq, 0};
 }
 
+// In every kernel below, B problems whose buffers lie pb bytes apart (one workspace block per
+// problem) can share one grid: blockIdx.z = 4 b + t for the per-tree kernels (tree t of
+// problem b), blockIdx.z = b or blockIdx.y = b for the others.
+
 // One analysis level of the four trees: out plane t (stride so, plane stride ps) block
 // M x M from in (plane t at in + t * in_ps, stride si; in_ps = 0 reads one image for all).
 __global__ void k_cwt_analysis(const float* __restrict__ in, long long in_ps, int si, float* __restrict__ out,
-                               long long ps, int so, int M, int level1, const CwtBank bank, const int* stop) {
+                               long long ps, int so, int M, int level1, const CwtBank bank, const int* stop,
+                               long long pb) {
+    const long long po = pb * (blockIdx.z >> 2);
+    in = at_bytes(in, po);
+    out = at_bytes(out, po);
+    stop = stop ? at_bytes(stop, po) : stop;
     if (stop && *(volatile const int*)stop) return;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, t = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, t = blockIdx.z & 3;
     if (x >= M || y >= M) return;
     const AxisF fx = axis_filters(bank, t >> 1, level1), fy = axis_filters(bank, t & 1, level1);
     const int h2 = M >> 1;
@@ -92,9 +101,13 @@ __device__ __forceinline__ float cwt_synth_at(const float* __restrict__ c, int s
 // Levels >= 2: out plane t (M x M, stride so, plane stride ops) from in plane t (stride si,
 // plane stride ips).
 __global__ void k_cwt_synthesis(const float* __restrict__ in, long long ips, int si, float* __restrict__ out,
-                                long long ops, int so, int M, const CwtBank bank, const int* stop) {
+                                long long ops, int so, int M, const CwtBank bank, const int* stop, long long pb) {
+    const long long po = pb * (blockIdx.z >> 2);
+    in = at_bytes(in, po);
+    out = at_bytes(out, po);
+    stop = stop ? at_bytes(stop, po) : stop;
     if (stop && *(volatile const int*)stop) return;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, t = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, t = blockIdx.z & 3;
     if (x >= M || y >= M) return;
     const AxisF fx = axis_filters(bank, t >> 1, false), fy = axis_filters(bank, t & 1, false);
     out[ops * t + (size_t)y * so + x] = cwt_synth_at(in + ips * t, si, M, x, y, fx, fy);
@@ -102,7 +115,11 @@ __global__ void k_cwt_synthesis(const float* __restrict__ in, long long ips, int
 
 // Level 1 and the sum of the four trees: out (N x N) = sum_t T_t^T level 1 of plane t.
 __global__ void k_cwt_synthesis_sum(const float* __restrict__ in, long long ips, int si, float* __restrict__ out,
-                                    int N, const CwtBank bank, const int* stop) {
+                                    int N, const CwtBank bank, const int* stop, long long pb) {
+    const long long po = pb * blockIdx.z;
+    in = at_bytes(in, po);
+    out = at_bytes(out, po);
+    stop = stop ? at_bytes(stop, po) : stop;
     if (stop && *(volatile const int*)stop) return;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= N || y >= N) return;
@@ -115,9 +132,13 @@ __global__ void k_cwt_synthesis_sum(const float* __restrict__ in, long long ips,
 
 // out planes (M x M blocks, stride so) = in planes' top-left M x M blocks (stride si)
 __global__ void k_cwt_copy(const float* __restrict__ in, long long ips, int si, float* __restrict__ out, long long ops,
-                           int so, int M, const int* stop) {
+                           int so, int M, const int* stop, long long pb) {
+    const long long po = pb * (blockIdx.z >> 2);
+    in = at_bytes(in, po);
+    out = at_bytes(out, po);
+    stop = stop ? at_bytes(stop, po) : stop;
     if (stop && *(volatile const int*)stop) return;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, t = blockIdx.z;
+    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, t = blockIdx.z & 3;
     if (x < M && y < M) out[ops * t + (size_t)y * so + x] = in[ips * t + (size_t)y * si + x];
 }
 
@@ -141,11 +162,19 @@ __device__ __forceinline__ void combine_at(const float* __restrict__ T, long lon
 // detail coefficient onto the disc of radius alpha (its two rows share one step), every LL
 // coefficient clipped to [-alpha, alpha].
 __global__ void k_cwt_dual(float* __restrict__ r, const float* __restrict__ T, const float* __restrict__ sig_r,
-                           const float* step_mul, float alpha, int N, int ll_side, const int* stop) {
+                           const float* step_mul, const float* scal, int N, int ll_side, const int* stop,
+                           long long pb) {
+    const long long po = pb * blockIdx.y;
+    r = at_bytes(r, po);
+    T = at_bytes(T, po);
+    sig_r = at_bytes(sig_r, po);
+    step_mul = at_bytes(step_mul, po);
+    stop = stop ? at_bytes(stop, po) : stop;
     if (stop && *(volatile const int*)stop) return;
     const long long NN = (long long)N * N;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= NN) return;
+    const float alpha = *at_bytes(scal, po);
     const int x = (int)(i % N), y = (int)(i / N);
     const bool ll = x < ll_side && y < ll_side;
     float c[4];
@@ -174,7 +203,12 @@ __global__ void k_cwt_dual(float* __restrict__ r, const float* __restrict__ T, c
 
 // T planes of W^T: the coefficients r in tree form, each times 1/2 (the change back from the
 // complex pairs is the transpose of the change above)
-__global__ void k_cwt_uncombine(const float* __restrict__ r, float* __restrict__ T, int N, int ll_side, const int* stop) {
+__global__ void k_cwt_uncombine(const float* __restrict__ r, float* __restrict__ T, int N, int ll_side, const int* stop,
+                                long long pb) {
+    const long long po = pb * blockIdx.y;
+    r = at_bytes(r, po);
+    T = at_bytes(T, po);
+    stop = stop ? at_bytes(stop, po) : stop;
     if (stop && *(volatile const int*)stop) return;
     const long long NN = (long long)N * N;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -196,7 +230,17 @@ __global__ void k_cwt_uncombine(const float* __restrict__ r, float* __restrict__
 
 // per-block sums in the layout of the gap's pixel pass: {||W u||_1, 0, |K^T q + W^T r|_1, 0,
 // |u - u_old|^2, |u_old|^2, 0}; W u from the T planes of u
-__global__ void __launch_bounds__(256) k_cwt_gap_pixels(const CwtGapArgs a) {
+__global__ void __launch_bounds__(256) k_cwt_gap_pixels(CwtGapArgs a, long long pb) {
+    const long long po = pb * blockIdx.y;
+    a.tu = at_bytes(a.tu, po);
+    a.kt.acc = at_bytes(a.kt.acc, po);
+    a.kt.ymax_bits = at_bytes(a.kt.ymax_bits, po);
+    a.kt.tile_kmax = at_bytes(a.kt.tile_kmax, po);
+    a.wtr = at_bytes(a.wtr, po);
+    a.u = at_bytes(a.u, po);
+    if (a.u_old) a.u_old = at_bytes(a.u_old, po);
+    a.partials = at_bytes(a.partials, po);
+    if (a.stop) a.stop = at_bytes(a.stop, po);
     if (a.stop && *(volatile const int*)a.stop) return;
     const int N = a.n;
     const long long NN = (long long)N * N;
@@ -382,16 +426,16 @@ void cwt_abs_sums(int n, int levels, const std::vector<double>& h1, const std::v
 
 // out (4 T planes of N x N) = T in.  scratch: 4 (N/2)^2 floats.
 int launch_cwt_analysis(const float* in, int N, int levels, const CwtBank& bank, float* out, float* scratch,
-                        const int* stop, cudaStream_t st) {
+                        const int* stop, cudaStream_t st, int B, long long pb) {
     const dim3 blk(32, 8);
     const long long NN = (long long)N * N;
-    k_cwt_analysis<<<grid_of(N, 4), blk, 0, st>>>(in, 0, N, out, NN, N, N, 1, bank, stop);
+    k_cwt_analysis<<<grid_of(N, 4 * B), blk, 0, st>>>(in, 0, N, out, NN, N, N, 1, bank, stop, pb);
     PAT_LAUNCH_CHECK("k_cwt_analysis");
     for (int l = 2, M = N / 2; l <= levels; ++l, M /= 2) {
         const long long mm = (long long)M * M;
-        k_cwt_copy<<<grid_of(M, 4), blk, 0, st>>>(out, NN, N, scratch, mm, M, M, stop);
+        k_cwt_copy<<<grid_of(M, 4 * B), blk, 0, st>>>(out, NN, N, scratch, mm, M, M, stop, pb);
         PAT_LAUNCH_CHECK("k_cwt_copy");
-        k_cwt_analysis<<<grid_of(M, 4), blk, 0, st>>>(scratch, mm, M, out, NN, N, M, 0, bank, stop);
+        k_cwt_analysis<<<grid_of(M, 4 * B), blk, 0, st>>>(scratch, mm, M, out, NN, N, M, 0, bank, stop, pb);
         PAT_LAUNCH_CHECK("k_cwt_analysis");
     }
     return PAT_OK;
@@ -399,39 +443,41 @@ int launch_cwt_analysis(const float* in, int N, int levels, const CwtBank& bank,
 
 // out (N x N) = sum_t T_t^T of the T planes in.  in is overwritten; scratch: 4 (N/2)^2.
 int launch_cwt_synthesis(float* in, int N, int levels, const CwtBank& bank, float* out, float* scratch,
-                         const int* stop, cudaStream_t st) {
+                         const int* stop, cudaStream_t st, int B, long long pb) {
     const dim3 blk(32, 8);
     const long long NN = (long long)N * N;
     for (int l = levels; l >= 2; --l) {
         const int M = N >> (l - 1);
         const long long mm = (long long)M * M;
-        k_cwt_synthesis<<<grid_of(M, 4), blk, 0, st>>>(in, NN, N, scratch, mm, M, M, bank, stop);
+        k_cwt_synthesis<<<grid_of(M, 4 * B), blk, 0, st>>>(in, NN, N, scratch, mm, M, M, bank, stop, pb);
         PAT_LAUNCH_CHECK("k_cwt_synthesis");
-        k_cwt_copy<<<grid_of(M, 4), blk, 0, st>>>(scratch, mm, M, in, NN, N, M, stop);
+        k_cwt_copy<<<grid_of(M, 4 * B), blk, 0, st>>>(scratch, mm, M, in, NN, N, M, stop, pb);
         PAT_LAUNCH_CHECK("k_cwt_copy");
     }
-    k_cwt_synthesis_sum<<<grid_of(N, 1), blk, 0, st>>>(in, NN, N, out, N, bank, stop);
+    k_cwt_synthesis_sum<<<grid_of(N, B), blk, 0, st>>>(in, NN, N, out, N, bank, stop, pb);
     PAT_LAUNCH_CHECK("k_cwt_synthesis_sum");
     return PAT_OK;
 }
 
-int launch_cwt_dual(float* r, const float* T, const float* sig_r, const float* step_mul, float alpha, int N, int levels,
-                    const int* stop, cudaStream_t st) {
+int launch_cwt_dual(float* r, const float* T, const float* sig_r, const float* step_mul, const float* scal, int N,
+                    int levels, const int* stop, cudaStream_t st, int B, long long pb) {
     const long long NN = (long long)N * N;
-    k_cwt_dual<<<(unsigned)ceil_div(NN, 256), 256, 0, st>>>(r, T, sig_r, step_mul, alpha, N, N >> levels, stop);
+    k_cwt_dual<<<dim3((unsigned)ceil_div(NN, 256), B), 256, 0, st>>>(r, T, sig_r, step_mul, scal, N, N >> levels,
+                                                                     stop, pb);
     PAT_LAUNCH_CHECK("k_cwt_dual");
     return PAT_OK;
 }
 
-int launch_cwt_uncombine(const float* r, float* T, int N, int levels, const int* stop, cudaStream_t st) {
+int launch_cwt_uncombine(const float* r, float* T, int N, int levels, const int* stop, cudaStream_t st, int B,
+                         long long pb) {
     const long long NN = (long long)N * N;
-    k_cwt_uncombine<<<(unsigned)ceil_div(NN, 256), 256, 0, st>>>(r, T, N, N >> levels, stop);
+    k_cwt_uncombine<<<dim3((unsigned)ceil_div(NN, 256), B), 256, 0, st>>>(r, T, N, N >> levels, stop, pb);
     PAT_LAUNCH_CHECK("k_cwt_uncombine");
     return PAT_OK;
 }
 
-int launch_cwt_gap_pixels(const CwtGapArgs& a, int nblocks, cudaStream_t st) {
-    k_cwt_gap_pixels<<<nblocks, 256, 0, st>>>(a);
+int launch_cwt_gap_pixels(const CwtGapArgs& a, int nblocks, cudaStream_t st, int B, long long pb) {
+    k_cwt_gap_pixels<<<dim3(nblocks, B), 256, 0, st>>>(a, pb);
     PAT_LAUNCH_CHECK("k_cwt_gap_pixels");
     return PAT_OK;
 }
@@ -465,10 +511,10 @@ extern "C" int pat_dtcwt_transform(int n, int levels, const double* h1_host, int
     float* T = buf;
     float* scratch = buf + 4 * NN;
     if (inverse) {
-        rc = launch_cwt_uncombine(in_dev, T, n, levels, nullptr, st);
-        if (!rc) rc = launch_cwt_synthesis(T, n, levels, bank, out_dev, scratch, nullptr, st);
+        rc = launch_cwt_uncombine(in_dev, T, n, levels, nullptr, st, 1, 0);
+        if (!rc) rc = launch_cwt_synthesis(T, n, levels, bank, out_dev, scratch, nullptr, st, 1, 0);
     } else {
-        rc = launch_cwt_analysis(in_dev, n, levels, bank, T, scratch, nullptr, st);
+        rc = launch_cwt_analysis(in_dev, n, levels, bank, T, scratch, nullptr, st, 1, 0);
         if (!rc) {
             k_cwt_combine<<<(unsigned)ceil_div(NN, 256), 256, 0, st>>>(T, out_dev, n, n >> levels);
             count_launch();

@@ -228,6 +228,13 @@ __device__ __forceinline__ void point_coords(const G& g, float2 det, float r, fl
 // Launch helpers
 inline int ceil_div(long long a, long long b) { return (int)((a + b - 1) / b); }
 
+// p moved on by b bytes: problem k of a batch whose per-problem buffers lie a fixed byte
+// stride apart reads its buffers at the first problem's pointers plus k times that stride
+template <class T>
+__host__ __device__ __forceinline__ T* at_bytes(T* p, long long b) {
+    return (T*)((const char*)p + b);
+}
+
 // Copies problem p's argument struct into the block's shared copy (one word per thread)
 // so that field reads are shared-memory broadcasts; ends with a block barrier.
 template <class T>
@@ -315,7 +322,7 @@ int adjoint_blocks_per_sm();
 // ---- the wavelet model (wavelet.cu) ----
 struct WavPrimalArgs {   // u <- u - T (K^T q + W^T r) / s, ubar, and the next parity's reset
     int n;
-    float theta;
+    const float* scal;   // {alpha, theta}
     const float* tau_u;
     const float* step_mul;
     KtView kt;
@@ -361,23 +368,27 @@ int cwt_bank(const double* h1, int l1, const double* hq, int lq, CwtBank& bank, 
 void cwt_abs_sums(int n, int levels, const std::vector<double>& h1, const std::vector<double>& hq,
                   std::vector<double>& rows, std::vector<double>& cols);
 int launch_cwt_analysis(const float* in, int N, int levels, const CwtBank& bank, float* out, float* scratch,
-                        const int* stop, cudaStream_t st);
+                        const int* stop, cudaStream_t st, int B, long long ps);
 int launch_cwt_synthesis(float* in, int N, int levels, const CwtBank& bank, float* out, float* scratch,
-                         const int* stop, cudaStream_t st);
-int launch_cwt_dual(float* r, const float* T, const float* sig_r, const float* step_mul, float alpha, int N, int levels,
-                    const int* stop, cudaStream_t st);
-int launch_cwt_uncombine(const float* r, float* T, int N, int levels, const int* stop, cudaStream_t st);
-int launch_cwt_gap_pixels(const CwtGapArgs& a, int nblocks, cudaStream_t st);
-
+                         const int* stop, cudaStream_t st, int B, long long ps);
+int launch_cwt_dual(float* r, const float* T, const float* sig_r, const float* step_mul, const float* scal, int N,
+                    int levels, const int* stop, cudaStream_t st, int B, long long ps);
+int launch_cwt_uncombine(const float* r, float* T, int N, int levels, const int* stop, cudaStream_t st, int B,
+                         long long ps);
+int launch_cwt_gap_pixels(const CwtGapArgs& a, int nblocks, cudaStream_t st, int B, long long ps);
+// the orthonormal Daubechies-4 transform (wavelet.cu)
 bool wav_levels_ok(int n, int levels);
 void wav_abs_sums(int n, int levels, std::vector<double>& rows, std::vector<double>& cols);
-int launch_wav_analysis(const float* in, int N, int levels, float* out, float* scratch, const int* stop, cudaStream_t st);
+// The launches of the wavelet model cover B problems at once whose buffers (every pointer
+// argument, the alpha/theta pair scal included) lie ps bytes apart; B = 1, ps = 0 for one.
+int launch_wav_analysis(const float* in, int N, int levels, float* out, float* scratch, const int* stop, cudaStream_t st,
+                        int B, long long ps);
 int launch_wav_synthesis(const float* in, int N, int levels, float* out, float* scratch, const int* stop,
-                         cudaStream_t st);
-int launch_wav_dual(float* r, const float* wub, const float* sig_r, const float* step_mul, float alpha, long long nn,
-                    const int* stop, cudaStream_t st);
-int launch_wav_primal(const WavPrimalArgs& a, cudaStream_t st);
-int launch_wav_gap_pixels(const WavGapArgs& a, int nblocks, cudaStream_t st);
+                         cudaStream_t st, int B, long long ps);
+int launch_wav_dual(float* r, const float* wub, const float* sig_r, const float* step_mul, const float* scal,
+                    long long nn, const int* stop, cudaStream_t st, int B, long long ps);
+int launch_wav_primal(const WavPrimalArgs& a, cudaStream_t st, int B, long long ps);
+int launch_wav_gap_pixels(const WavGapArgs& a, int nblocks, cudaStream_t st, int B, long long ps);
 int launch_wav_tau(const float* kcol, const double* wcol, float* tau, long long nn, cudaStream_t st);
 
 int ensure_precond(const pat_geometry* g, cudaStream_t st);

@@ -1422,6 +1422,9 @@ struct WavModel {
     long long nr = 0;
     CwtBank bank{};
     std::vector<double> h1, hq;
+    // the |W| row sums (with the DT-CWT, paired per complex coefficient) and column sums,
+    // filled by the first wav_steps call and shared by the problems of a batch
+    std::vector<double> rows, cols;
 };
 
 static int wav_model(const pat_geometry* g, const pat_params* p, WavModel& m) {
@@ -1435,17 +1438,29 @@ static int wav_model(const pat_geometry* g, const pat_params* p, WavModel& m) {
     return PAT_OK;
 }
 
+// Two wavelet problems can share a batch when they have one N and one transform (kind,
+// levels and, for the DT-CWT, filters)
+static bool wav_same_batch(const pat_geometry* ga, const pat_params* pa, const pat_geometry* gb, const pat_params* pb) {
+    if (ga->desc.n != gb->desc.n || wav_levels_of(pa) != wav_levels_of(pb) || pa->wavelet_kind != pb->wavelet_kind)
+        return false;
+    if (pa->wavelet_kind != PAT_WAVELET_DTCWT) return true;
+    WavModel ma, mb;
+    if (wav_model(ga, pa, ma) || wav_model(gb, pb, mb)) return false;
+    return ma.h1 == mb.h1 && ma.hq == mb.hq;
+}
+
 // sigma_q, tau_u and sigma_r of the wavelet model: the alpha = 1 diagonal rule on A = (K; W).
 // With the DT-CWT the two rows of a complex coefficient share one step, 1 / (the larger of
 // their row sums): the dual prox of a disc is the projection onto it only with one step.
-static int wav_steps(const pat_geometry* g, const WavModel& m, float* sig_q, float* tau_u, float* sig_r,
+static int wav_steps(const pat_geometry* g, WavModel& m, float* sig_q, float* tau_u, float* sig_r,
                      double s_ratio, cudaStream_t st) {
     const int N = g->desc.n;
     const long long NN = (long long)N * N, S = (long long)g->desc.n_det * g->desc.n_t;
     int rc = ensure_precond(g, st);
     if (rc) return rc;
-    std::vector<double> rows, cols;
-    if (m.kind == PAT_WAVELET_DTCWT) {
+    std::vector<double>& rows = m.rows;
+    std::vector<double>& cols = m.cols;
+    if (rows.empty() && m.kind == PAT_WAVELET_DTCWT) {
         cwt_abs_sums(N, m.J, m.h1, m.hq, rows, cols);
         const int side = N >> m.J;
         for (long long i = 0; i < NN; ++i) {
@@ -1455,7 +1470,7 @@ static int wav_steps(const pat_geometry* g, const WavModel& m, float* sig_q, flo
                 rows[a * NN + i] = rows[(a + 1) * NN + i] = mx;
             }
         }
-    } else {
+    } else if (rows.empty()) {
         wav_abs_sums(N, m.J, rows, cols);
     }
     if (sig_q) {
@@ -1489,62 +1504,75 @@ static int wav_steps(const pat_geometry* g, const WavModel& m, float* sig_q, flo
     return PAT_OK;
 }
 
-static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* p, float* u_out, pat_info* info,
-                       cudaStream_t st, const char* who) {
-    const int N = g->desc.n, J = wav_levels_of(p);
-    const long long NN = (long long)N * N, S = (long long)g->desc.n_det * g->desc.n_t;
-    const int n_data = g->fwd_n_ctas;
+// B problems of the wavelet model that share N, the transform with its levels and filters,
+// the iteration count and the gap period advance in lockstep, as in the batch engine: K and
+// K^T launch once for all problems through (problem, block) maps (clusters and work items
+// of all problems heaviest first), and every wavelet kernel covers all problems through a
+// problem index in its grid, each problem's buffers in one workspace block at a fixed byte
+// stride.  A single reconstruction is a batch of one.
+static int run_wavelet(int B, const pat_geometry* const* g, const float* const* f, const pat_params* p,
+                       float* const* u_out, pat_info* infos, cudaStream_t st, const char* who) {
+    if (B <= 0) return PAT_OK;
+    const int N = g[0]->desc.n, J = wav_levels_of(&p[0]);
+    const long long NN = (long long)N * N;
     const int n_pix = pix_blocks(N);
     WavModel wm;
-    if (int mrc = wav_model(g, p, wm)) return mrc;
+    if (int mrc = wav_model(g[0], &p[0], wm)) return mrc;
     const bool cwt = wm.kind == PAT_WAVELET_DTCWT;
     const long long NR = wm.nr;   // coefficients of W u
-    // workspace (DT-CWT: R, WB, WU and SIGR hold 4 planes, SCRT the tree form of r)
-    enum { U, UOLD, UBAR, Q, QW, KT, R, WB, WTR, SCR, SCR2, WU, TAU, SIGR, SIGQ, DPART, PPART, INFO, SCRT, NBUF };
-    const size_t nn4 = (size_t)NN * 4, nr4 = (size_t)NR * 4;
-    size_t sz[NBUF] = {nn4, nn4, nn4,
-                       (size_t)S * 4, (size_t)S * 4, (size_t)NN * 8, nr4, nr4, nn4, nn4, nn4, nr4,
-                       nn4, nr4, (size_t)S * 4, (size_t)n_data * GAP_DATA_TERMS * 8,
-                       (size_t)n_pix * GAP_PIX_TERMS * 8, sizeof(InfoDev), cwt ? nr4 : 16};
-    size_t off[NBUF], total = 0;
-    for (int i = 0; i < NBUF; ++i) {
-        off[i] = total;
-        total += align_up(sz[i]);
+    long long S = 0;              // the largest data size and K CTA count of the batch
+    int n_data = 0;
+    for (int b = 0; b < B; ++b) {
+        if (g[b]->desc.n != N) return fail(PAT_ERR_INVALID_ARG, std::string(who) + ": a wavelet batch needs one N");
+        S = std::max(S, (long long)g[b]->desc.n_det * g[b]->desc.n_t);
+        n_data = std::max(n_data, g[b]->fwd_n_ctas);
     }
-    char* b = nullptr;
-    PAT_CUDA(cudaMallocAsync((void**)&b, total, st));
-    float *u = (float*)(b + off[U]), *u_old = (float*)(b + off[UOLD]), *ubar = (float*)(b + off[UBAR]);
-    float *q = (float*)(b + off[Q]), *qw = (float*)(b + off[QW]);
-    int* kt = (int*)(b + off[KT]);
-    float *r = (float*)(b + off[R]), *wb = (float*)(b + off[WB]), *wtr = (float*)(b + off[WTR]);
-    float *scr = (float*)(b + off[SCR]), *scr2 = (float*)(b + off[SCR2]), *wu = (float*)(b + off[WU]);
-    float *tau = (float*)(b + off[TAU]), *sigr = (float*)(b + off[SIGR]), *sigq = (float*)(b + off[SIGQ]);
-    double *dpart = (double*)(b + off[DPART]), *ppart = (double*)(b + off[PPART]);
-    float* scrt = (float*)(b + off[SCRT]);
-    InfoDev* in = (InfoDev*)(b + off[INFO]);
+    // one workspace block per problem (DT-CWT: R, WB, WU and SIGR hold 4 planes, SCRT the
+    // tree form of r); SCAL holds {alpha, theta}, TKM the geometry's K^T tile bounds
+    enum { U, UOLD, UBAR, Q, QW, KT, R, WB, WTR, SCR, SCR2, WU, TAU, SIGR, SIGQ, DPART, PPART, INFO, SCRT, SCAL, TKM,
+           NBUF };
+    const size_t nn4 = (size_t)NN * 4, nr4 = (size_t)NR * 4;
+    const size_t sz[NBUF] = {nn4, nn4, nn4, (size_t)S * 4, (size_t)S * 4, (size_t)NN * 8, nr4, nr4, nn4, nn4, nn4,
+                             nr4, nn4, nr4, (size_t)S * 4, (size_t)n_data * GAP_DATA_TERMS * 8,
+                             (size_t)n_pix * GAP_PIX_TERMS * 8, sizeof(InfoDev), cwt ? nr4 : 16, 2 * sizeof(float),
+                             (size_t)g[0]->adj_tiles * sizeof(float)};
+    size_t off[NBUF], PS = 0;
+    for (int i = 0; i < NBUF; ++i) {
+        off[i] = PS;
+        PS += align_up(sz[i]);
+    }
+    const long long ps = (long long)PS;
+    char* ws = nullptr;
+    PAT_CUDA(cudaMallocAsync((void**)&ws, PS * (size_t)B, st));
+    auto buf = [&](int b, int i) { return ws + (size_t)b * PS + off[i]; };
+    auto F = [&](int b, int i) { return (float*)buf(b, i); };
+    auto inf = [&](int b) { return (InfoDev*)buf(b, INFO); };
     cudaEvent_t e0, e1;
     PAT_CUDA(cudaEventCreate(&e0));
     PAT_CUDA(cudaEventCreate(&e1));
     PAT_CUDA(cudaEventRecord(e0, st));
-    int rc = wav_steps(g, wm, sigq, tau, sigr, 1.0, st);
-    // start
-    if (!rc) {
-        auto cp = [&](float* dst, const float* src, long long n) -> int {
-            if (src) PAT_CUDA(cudaMemcpyAsync(dst, src, n * 4, cudaMemcpyDeviceToDevice, st));
-            else PAT_CUDA(cudaMemsetAsync(dst, 0, n * 4, st));
-            return PAT_OK;
-        };
-        rc = cp(u, p->x0_dev, NN);
-        if (!rc) rc = cp(ubar, p->xbar0_dev ? p->xbar0_dev : p->x0_dev, NN);
-        if (!rc) rc = cp(q, p->y0_dev, S);
-        if (!rc) rc = cp(r, p->y0_dev ? p->y0_dev + S : nullptr, NR);
-    }
-    if (!rc) {
-        PAT_CUDA(cudaMemsetAsync(in, 0, sizeof(InfoDev), st));
-        const double ratio = step_ratio_of(p);
+    int rc = PAT_OK;
+    auto cp = [&](float* dst, const float* src, long long n) -> int {
+        if (src) PAT_CUDA(cudaMemcpyAsync(dst, src, n * 4, cudaMemcpyDeviceToDevice, st));
+        else PAT_CUDA(cudaMemsetAsync(dst, 0, n * 4, st));
+        return PAT_OK;
+    };
+    for (int b = 0; b < B && !rc; ++b) {
+        const long long Sb = (long long)g[b]->desc.n_det * g[b]->desc.n_t;
+        rc = wav_steps(g[b], wm, F(b, SIGQ), F(b, TAU), F(b, SIGR), 1.0, st);
+        if (!rc) rc = cp(F(b, U), p[b].x0_dev, NN);
+        if (!rc) rc = cp(F(b, UBAR), p[b].xbar0_dev ? p[b].xbar0_dev : p[b].x0_dev, NN);
+        if (!rc) rc = cp(F(b, Q), p[b].y0_dev, Sb);
+        if (!rc) rc = cp(F(b, R), p[b].y0_dev ? p[b].y0_dev + Sb : nullptr, NR);
+        if (rc) break;
+        PAT_CUDA(cudaMemsetAsync(inf(b), 0, sizeof(InfoDev), st));
+        const double ratio = step_ratio_of(&p[b]);
         const float mul[2] = {(float)ratio, (float)(1.0 / ratio)};
-        PAT_CUDA(cudaMemcpyAsync(in->step_mul, mul, sizeof mul, cudaMemcpyHostToDevice, st));
-        PAT_CUDA(cudaMemsetAsync(kt, 0, NN * 8, st));
+        PAT_CUDA(cudaMemcpyAsync(inf(b)->step_mul, mul, sizeof mul, cudaMemcpyHostToDevice, st));
+        const float scal[2] = {(float)p[b].alpha, (float)p[b].theta};
+        PAT_CUDA(cudaMemcpyAsync(F(b, SCAL), scal, sizeof scal, cudaMemcpyHostToDevice, st));
+        PAT_CUDA(cudaMemcpyAsync(F(b, TKM), g[b]->pc.tile_kmax, sz[TKM], cudaMemcpyDeviceToDevice, st));
+        PAT_CUDA(cudaMemsetAsync(buf(b, KT), 0, NN * 8, st));
     }
     int* stopped = nullptr;
     void* dev = nullptr;
@@ -1552,82 +1580,96 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
                           cudaMemsetAsync(stopped, 0, sizeof(int), st) == cudaSuccess
                       ? PAT_OK
                       : fail(PAT_ERR_CUDA, std::string(who) + ": stop counter");
-    // device argument blocks of the shared launchers (a batch of one)
+    // device argument blocks: K and K^T per problem, as the batch engine's
     std::vector<char> host;
     Arena ar(host);
-    size_t fw_off[2], ad_off[2], fg_off, fi_off, fmap_off, amap_off, finmap_off;
-    const int nf = g->fwd_n_ctas;
+    size_t fw_off[2] = {0, 0}, ad_off[2] = {0, 0}, fg_off = 0, fi_off = 0, amap_off = 0, finmap_off = 0;
+    GapPlan gp;
+    int n_adj = 0;
     if (!rc) {
+        std::vector<FwdArgs> fw[2], fg;
+        std::vector<AdjArgs> ad[2];
+        std::vector<FinalArgs> fi;
+        std::vector<std::pair<float, int2>> order;
+        std::vector<Prob> prs(B);
+        for (int b = 0; b < B; ++b) {
+            InfoDev* in = inf(b);
+            for (int par = 0; par < 2; ++par) {
+                FwdArgs fa = make_fwd_args(g[b], F(b, UBAR));
+                fa.q = F(b, Q);
+                fa.f = f[b];
+                fa.sig_q = F(b, SIGQ);
+                fa.sig_scalar = -1.f;
+                fa.step_mul = in->step_mul;
+                fa.qw = F(b, QW);
+                fa.qmax_bits = &in->qmax_bits[par];
+                fa.stop = &in->stop;
+                fw[par].push_back(fa);
+                ad[par].push_back(make_adj_args(g[b], F(b, Q), F(b, QW), &in->qmax_bits[par],
+                                                (int*)buf(b, KT) + (size_t)par * NN, &in->stop));
+            }
+            FwdArgs ga = make_fwd_args(g[b], F(b, U));
+            ga.q = F(b, Q);
+            ga.f = f[b];
+            ga.partials = (double*)buf(b, DPART);
+            ga.stop = &in->stop;
+            fg.push_back(ga);
+            fi.push_back(FinalArgs{(double*)buf(b, DPART), g[b]->fwd_n_ctas, (double*)buf(b, PPART), n_pix, p[b].alpha,
+                                   0.0, p[b].box_u, p[b].box_v, p[b].tol, PAT_WAV, PAT_ADAPT_NONE, in, stopped});
+            for (int i = 0; i < g[b]->adj_items; ++i) order.push_back({g[b]->adj_item_cost[i], make_int2(b, i)});
+            prs[b].g = g[b];
+        }
         for (int par = 0; par < 2; ++par) {
-            FwdArgs fa = make_fwd_args(g, ubar);
-            fa.q = q;
-            fa.f = f;
-            fa.sig_q = sigq;
-            fa.sig_scalar = -1.f;
-            fa.step_mul = in->step_mul;
-            fa.qw = qw;
-            fa.qmax_bits = &in->qmax_bits[par];
-            fa.stop = &in->stop;
-            fw_off[par] = ar.put(&fa, 1);
-            AdjArgs aa = make_adj_args(g, q, qw, &in->qmax_bits[par], kt + (size_t)par * NN, &in->stop);
-            ad_off[par] = ar.put(&aa, 1);
+            fw_off[par] = ar.put(fw[par].data(), fw[par].size());
+            ad_off[par] = ar.put(ad[par].data(), ad[par].size());
         }
-        FwdArgs ga = make_fwd_args(g, u);
-        ga.q = q;
-        ga.f = f;
-        ga.partials = dpart;
-        ga.stop = &in->stop;
-        fg_off = ar.put(&ga, 1);
-        FinalArgs fi{dpart, n_data, ppart, n_pix, p->alpha, 0.0, p->box_u, p->box_v, p->tol, PAT_WAV, PAT_ADAPT_NONE,
-                     in, stopped};
-        fi_off = ar.put(&fi, 1);
-        std::vector<int2> fm(nf), am(g->adj_items), fin(GAP_FINAL_BLOCKS);
-        {
-            // K clusters longest first, the ranks of a cluster consecutive
-            const int S = g->view.n_slabs;
-            std::vector<std::pair<float, int>> fo;
-            for (int c = 0; c < (int)g->fwd_cluster_cost.size(); ++c) fo.push_back({g->fwd_cluster_cost[c], c});
-            std::stable_sort(fo.begin(), fo.end(), [](const auto& a, const auto& c) { return a.first > c.first; });
-            for (size_t c = 0; c < fo.size(); ++c)
-                for (int r = 0; r < S; ++r) fm[c * S + r] = make_int2(0, fo[c].second * S + r);
-        }
-        std::vector<std::pair<float, int>> order;
-        for (int i = 0; i < g->adj_items; ++i) order.push_back({g->adj_item_cost[i], i});
-        std::stable_sort(order.begin(), order.end(), [](const auto& a, const auto& c) { return a.first > c.first; });
-        for (int i = 0; i < g->adj_items; ++i) am[i] = make_int2(0, order[i].second);
-        for (int i = 0; i < GAP_FINAL_BLOCKS; ++i) fin[i] = make_int2(0, i);
-        fmap_off = ar.put(fm.data(), fm.size());
+        fg_off = ar.put(fg.data(), fg.size());
+        fi_off = ar.put(fi.data(), fi.size());
+        forward_groups(prs.data(), B, ar, gp);
+        std::stable_sort(order.begin(), order.end(),
+                         [](const std::pair<float, int2>& x, const std::pair<float, int2>& y) { return x.first > y.first; });
+        std::vector<int2> am, fin;
+        for (auto& e : order) am.push_back(e.second);
+        n_adj = (int)am.size();
+        for (int b = 0; b < B; ++b)
+            for (int i = 0; i < GAP_FINAL_BLOCKS; ++i) fin.push_back(make_int2(b, i));
         amap_off = ar.put(am.data(), am.size());
         finmap_off = ar.put(fin.data(), fin.size());
         rc = ar.upload(&dev, st);
     }
     const char* base = (const char*)dev;
+    // the wavelet kernels take problem 0's pointers; problem b's lie b * ps bytes on
+    float *u = F(0, U), *u_old = F(0, UOLD), *ubar = F(0, UBAR), *r = F(0, R), *wb = F(0, WB), *wtr = F(0, WTR);
+    float *scr = F(0, SCR), *scr2 = F(0, SCR2), *wu = F(0, WU), *tau = F(0, TAU), *sigr = F(0, SIGR);
+    float *scrt = F(0, SCRT), *scal = F(0, SCAL);
+    int* kt = (int*)buf(0, KT);
+    double* ppart = (double*)buf(0, PPART);
+    InfoDev* in = inf(0);
+    const int tiles_x = g[0]->adj_tiles_x;
     auto iteration = [&](int it, bool gap, cudaStream_t s) -> int {
         const int par = it & 1;
-        int e = launch_forward_b(FWD_PROX, (const FwdArgs*)(base + fw_off[par]), (const int2*)(base + fmap_off), nf,
-                                 g->view.n_slabs, g->fwd_smem, s);
+        int e = launch_forward_groups(FWD_PROX, (const FwdArgs*)(base + fw_off[par]), gp, base, s);
         if (cwt) {
-            if (!e) e = launch_cwt_analysis(ubar, N, J, wm.bank, wb, scr, &in->stop, s);
-            if (!e) e = launch_cwt_dual(r, wb, sigr, in->step_mul, (float)p->alpha, N, J, &in->stop, s);
+            if (!e) e = launch_cwt_analysis(ubar, N, J, wm.bank, wb, scr, &in->stop, s, B, ps);
+            if (!e) e = launch_cwt_dual(r, wb, sigr, in->step_mul, scal, N, J, &in->stop, s, B, ps);
         } else {
-            if (!e) e = launch_wav_analysis(ubar, N, J, wb, scr, &in->stop, s);
-            if (!e) e = launch_wav_dual(r, wb, sigr, in->step_mul, (float)p->alpha, NN, &in->stop, s);
+            if (!e) e = launch_wav_analysis(ubar, N, J, wb, scr, &in->stop, s, B, ps);
+            if (!e) e = launch_wav_dual(r, wb, sigr, in->step_mul, scal, NN, &in->stop, s, B, ps);
         }
         if (!e)
-            e = launch_adjoint_b((const AdjArgs*)(base + ad_off[par]), (const int2*)(base + amap_off), g->adj_items,
-                                 true, s);
+            e = launch_adjoint_b((const AdjArgs*)(base + ad_off[par]), (const int2*)(base + amap_off), n_adj, true, s);
         if (cwt) {
-            if (!e) e = launch_cwt_uncombine(r, scrt, N, J, &in->stop, s);
-            if (!e) e = launch_cwt_synthesis(scrt, N, J, wm.bank, wtr, scr, &in->stop, s);
+            if (!e) e = launch_cwt_uncombine(r, scrt, N, J, &in->stop, s, B, ps);
+            if (!e) e = launch_cwt_synthesis(scrt, N, J, wm.bank, wtr, scr, &in->stop, s, B, ps);
         } else {
-            if (!e) e = launch_wav_synthesis(r, N, J, wtr, scr, &in->stop, s);
+            if (!e) e = launch_wav_synthesis(r, N, J, wtr, scr, &in->stop, s, B, ps);
         }
         WavPrimalArgs pa;
         pa.n = N;
-        pa.theta = (float)p->theta;
+        pa.scal = scal;
         pa.tau_u = tau;
         pa.step_mul = in->step_mul;
-        pa.kt = kt_view(g, kt + (size_t)par * NN, &in->qmax_bits[par]);
+        pa.kt = KtView{kt + (size_t)par * NN, &in->qmax_bits[par], F(0, TKM), tiles_x};
         pa.wtr = wtr;
         pa.u = u;
         pa.u_old = gap ? u_old : nullptr;
@@ -1636,30 +1678,30 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
         pa.qmax_next = &in->qmax_bits[1 - par];
         pa.stop = &in->stop;
         pa.iter = &in->iter;
-        if (!e) e = launch_wav_primal(pa, s);
+        if (!e) e = launch_wav_primal(pa, s, B, ps);
         if (gap && !e) {
-            e = cwt ? launch_cwt_analysis(u, N, J, wm.bank, wu, scr2, &in->stop, s)
-                    : launch_wav_analysis(u, N, J, wu, scr2, &in->stop, s);
-            if (!e)
-                e = launch_forward_b(FWD_GAP, (const FwdArgs*)(base + fg_off), (const int2*)(base + fmap_off), nf,
-                                     g->view.n_slabs, g->fwd_smem, s);
+            e = cwt ? launch_cwt_analysis(u, N, J, wm.bank, wu, scr2, &in->stop, s, B, ps)
+                    : launch_wav_analysis(u, N, J, wu, scr2, &in->stop, s, B, ps);
+            if (!e) e = launch_forward_groups(FWD_GAP, (const FwdArgs*)(base + fg_off), gp, base, s);
             if (cwt) {
                 CwtGapArgs cg{N, GAP_PIX_TERMS, N >> J, wu, pa.kt, wtr, u, u_old, ppart, &in->stop};
-                if (!e) e = launch_cwt_gap_pixels(cg, n_pix, s);
+                if (!e) e = launch_cwt_gap_pixels(cg, n_pix, s, B, ps);
             } else {
                 WavGapArgs wg{N, GAP_PIX_TERMS, wu, pa.kt, wtr, u, u_old, ppart, &in->stop};
-                if (!e) e = launch_wav_gap_pixels(wg, n_pix, s);
+                if (!e) e = launch_wav_gap_pixels(wg, n_pix, s, B, ps);
             }
             if (!e) {
-                k_gap_final_b<<<GAP_FINAL_BLOCKS, GAP_FINAL_THREADS, 0, s>>>((const FinalArgs*)(base + fi_off),
-                                                              (const int2*)(base + finmap_off));
+                k_gap_final_b<<<B * GAP_FINAL_BLOCKS, GAP_FINAL_THREADS, 0, s>>>((const FinalArgs*)(base + fi_off),
+                                                                                (const int2*)(base + finmap_off));
                 count_launch();
                 if (cudaGetLastError() != cudaSuccess) e = fail(PAT_ERR_CUDA, "k_gap_final_b");
             }
         }
         return e;
     };
-    const int iters = p->iters, ge = p->gap_every;
+    const int iters = p[0].iters, ge = p[0].gap_every;
+    bool can_stop = false;
+    for (int k = 0; k < B; ++k) can_stop = can_stop || p[k].tol > 0;
     if (!rc && iters > 0) {
         auto gap_due = [&](int it) { return (ge > 0 && (it + 1) % ge == 0) || it + 1 == iters; };
         const int P = ge > 0 ? (ge % 2 == 0 ? ge : 2 * ge) : 2;
@@ -1682,7 +1724,7 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
             if (ce == cudaSuccess) ce = e2;
             if (!rc && ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
             const long long per_period = pat_kernel_launches() - l0;
-            int* snap = p->tol > 0 ? stop_snapshots() : nullptr;
+            int* snap = can_stop ? stop_snapshots() : nullptr;
             cudaEvent_t ev[2] = {nullptr, nullptr};
             bool pending[2] = {false, false};
             if (snap)
@@ -1701,7 +1743,7 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
                 if (pending[prev] && ce == cudaSuccess) {
                     ce = cudaEventSynchronize(ev[prev]);
                     pending[prev] = false;
-                    if (ce == cudaSuccess && *(volatile int*)&snap[prev] >= 1) {
+                    if (ce == cudaSuccess && *(volatile int*)&snap[prev] >= B) {
                         all_stopped = true;
                         break;
                     }
@@ -1726,22 +1768,25 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
         for (int it = start; !rc && !all_stopped && it < iters; ++it) rc = iteration(it, gap_due(it), st);
     }
     // outputs: u, x = [u], xbar = [ubar], y = [q, r]
-    if (!rc) {
-        PAT_CUDA(cudaMemcpyAsync(u_out, u, NN * 4, cudaMemcpyDeviceToDevice, st));
-        if (p->x_out_dev) PAT_CUDA(cudaMemcpyAsync(p->x_out_dev, u, NN * 4, cudaMemcpyDeviceToDevice, st));
-        if (p->x_lo_out_dev) PAT_CUDA(cudaMemsetAsync(p->x_lo_out_dev, 0, NN * 4, st));
-        if (p->xbar_out_dev) PAT_CUDA(cudaMemcpyAsync(p->xbar_out_dev, ubar, NN * 4, cudaMemcpyDeviceToDevice, st));
-        if (p->y_out_dev) {
-            PAT_CUDA(cudaMemcpyAsync(p->y_out_dev, q, S * 4, cudaMemcpyDeviceToDevice, st));
-            PAT_CUDA(cudaMemcpyAsync(p->y_out_dev + S, r, NR * 4, cudaMemcpyDeviceToDevice, st));
+    for (int b = 0; b < B && !rc; ++b) {
+        const pat_params& pb = p[b];
+        const long long Sb = (long long)g[b]->desc.n_det * g[b]->desc.n_t;
+        PAT_CUDA(cudaMemcpyAsync(u_out[b], F(b, U), NN * 4, cudaMemcpyDeviceToDevice, st));
+        if (pb.x_out_dev) PAT_CUDA(cudaMemcpyAsync(pb.x_out_dev, F(b, U), NN * 4, cudaMemcpyDeviceToDevice, st));
+        if (pb.x_lo_out_dev) PAT_CUDA(cudaMemsetAsync(pb.x_lo_out_dev, 0, NN * 4, st));
+        if (pb.xbar_out_dev) PAT_CUDA(cudaMemcpyAsync(pb.xbar_out_dev, F(b, UBAR), NN * 4, cudaMemcpyDeviceToDevice, st));
+        if (pb.y_out_dev) {
+            PAT_CUDA(cudaMemcpyAsync(pb.y_out_dev, F(b, Q), Sb * 4, cudaMemcpyDeviceToDevice, st));
+            PAT_CUDA(cudaMemcpyAsync(pb.y_out_dev + Sb, F(b, R), NR * 4, cudaMemcpyDeviceToDevice, st));
         }
     }
-    InfoDev h{};
-    if (!rc) rc = cudaMemcpyAsync(&h, in, sizeof(InfoDev), cudaMemcpyDeviceToHost, st) == cudaSuccess ? 0 : PAT_ERR_CUDA;
+    std::vector<InfoDev> h(B);
+    for (int b = 0; b < B && !rc; ++b)
+        rc = cudaMemcpyAsync(&h[b], inf(b), sizeof(InfoDev), cudaMemcpyDeviceToHost, st) == cudaSuccess ? 0 : PAT_ERR_CUDA;
     cudaEventRecord(e1, st);
     if (dev) cudaFreeAsync(dev, st);
     if (stopped) cudaFreeAsync(stopped, st);
-    cudaFreeAsync(b, st);
+    cudaFreeAsync(ws, st);
     cudaError_t se = cudaStreamSynchronize(st);
     if (!rc && se != cudaSuccess) rc = cuda_fail(se, who);
     float ms = 0.f;
@@ -1750,18 +1795,23 @@ static int run_wavelet(const pat_geometry* g, const float* f, const pat_params* 
     cudaEventDestroy(e1);
     prof_collect();
     if (rc) return rc;
-    if (info) {
-        info->iters_done = iters == 0 ? 0 : h.iters_done;
-        info->status = h.stop ? h.status : PAT_STATUS_MAXITER;
-        info->primal = h.primal;
-        info->dual = h.dual;
-        info->gap = h.gap;
-        info->rel_gap = h.rel_gap;
-        info->residual = h.residual;
-        info->ms = ms;
-        info->step_ratio = (double)h.step_mul[0];
+    bool diverged = false;
+    for (int b = 0; b < B; ++b) {
+        if (infos) {
+            pat_info& io = infos[b];
+            io.iters_done = iters == 0 ? 0 : h[b].iters_done;
+            io.status = h[b].stop ? h[b].status : PAT_STATUS_MAXITER;
+            io.primal = h[b].primal;
+            io.dual = h[b].dual;
+            io.gap = h[b].gap;
+            io.rel_gap = h[b].rel_gap;
+            io.residual = h[b].residual;
+            io.ms = ms;
+            io.step_ratio = (double)h[b].step_mul[0];
+        }
+        diverged = diverged || h[b].status == PAT_STATUS_DIVERGED;
     }
-    if (h.status == PAT_STATUS_DIVERGED) return fail(PAT_ERR_NONFINITE, std::string(who) + ": duality gap not finite");
+    if (diverged) return fail(PAT_ERR_NONFINITE, std::string(who) + ": duality gap not finite");
     return PAT_OK;
 }
 
@@ -2272,7 +2322,7 @@ extern "C" int pat_reconstruct(const pat_geometry* g, const float* f_dev, const 
     int rc = validate(g, p, "pat_reconstruct");
     if (rc) return rc;
     if (!f_dev || !u_dev) return fail(PAT_ERR_INVALID_ARG, "pat_reconstruct: NULL data or output");
-    if (p->reg == PAT_WAV) return run_wavelet(g, f_dev, p, u_dev, info, (cudaStream_t)stream, "pat_reconstruct");
+    if (p->reg == PAT_WAV) return run_wavelet(1, &g, &f_dev, p, &u_dev, info, (cudaStream_t)stream, "pat_reconstruct");
     return run_batch(1, &g, &f_dev, p, &u_dev, info, (cudaStream_t)stream, "pat_reconstruct");
 }
 
@@ -2285,22 +2335,16 @@ extern "C" int pat_reconstruct_batched(int count, const pat_geometry* const* g, 
         if (rc) return rc;
         if (!f_dev[i] || !u_dev[i]) return fail(PAT_ERR_INVALID_ARG, "pat_reconstruct_batched: NULL data or output");
     }
-    // wavelet problems run one at a time; the others advance in lockstep, and those
-    // sharing (iters, gap_every) run as one batch
+    // problems advance in lockstep: those sharing (iters, gap_every) run as one batch, the
+    // wavelet problems among them in batches that also share N and the transform
     std::vector<char> done(count, 0);
-    for (int i = 0; i < count; ++i)
-        if (p[i].reg == PAT_WAV) {
-            pat_info ii{};
-            int rc = run_wavelet(g[i], f_dev[i], &p[i], u_dev[i], &ii, (cudaStream_t)stream, "pat_reconstruct_batched");
-            if (infos) infos[i] = ii;
-            if (rc) return rc;
-            done[i] = 1;
-        }
     for (int i = 0; i < count; ++i) {
         if (done[i]) continue;
         std::vector<int> idx;
         for (int j = i; j < count; ++j)
-            if (!done[j] && p[j].iters == p[i].iters && p[j].gap_every == p[i].gap_every) {
+            if (!done[j] && p[j].iters == p[i].iters && p[j].gap_every == p[i].gap_every &&
+                (p[i].reg == PAT_WAV) == (p[j].reg == PAT_WAV) &&
+                (p[i].reg != PAT_WAV || wav_same_batch(g[i], &p[i], g[j], &p[j]))) {
                 idx.push_back(j);
                 done[j] = 1;
             }
@@ -2315,8 +2359,10 @@ extern "C" int pat_reconstruct_batched(int count, const pat_geometry* const* g, 
             pp.push_back(p[j]);
             uu.push_back(u_dev[j]);
         }
-        int rc = run_batch((int)idx.size(), gg.data(), ff.data(), pp.data(), uu.data(), ii.data(),
-                           (cudaStream_t)stream, "pat_reconstruct_batched");
+        int rc = p[i].reg == PAT_WAV ? run_wavelet((int)idx.size(), gg.data(), ff.data(), pp.data(), uu.data(),
+                                                   ii.data(), (cudaStream_t)stream, "pat_reconstruct_batched")
+                                     : run_batch((int)idx.size(), gg.data(), ff.data(), pp.data(), uu.data(), ii.data(),
+                                                 (cudaStream_t)stream, "pat_reconstruct_batched");
         if (infos)
             for (size_t k = 0; k < idx.size(); ++k) infos[idx[k]] = ii[k];
         if (rc) return rc;
@@ -2346,30 +2392,36 @@ static int tune_impl(int count, const pat_geometry* const* g, const float* const
     bool any_wav = false;
     for (int b = 0; b < count; ++b) any_wav = any_wav || p[b].reg == PAT_WAV;
     if (any_wav) {
-        // wavelet problems have no batch engine: their probes run one after another
+        // with wavelet problems in the set, each problem's candidates run as one batch
         for (int b = 0; b < count; ++b) {
+            const size_t nn = (size_t)g[b]->desc.n * g[b]->desc.n;
             float* ub = nullptr;
-            PAT_CUDA(cudaMallocAsync(&ub, (size_t)g[b]->desc.n * g[b]->desc.n * sizeof(float), st));
-            int bi = 0;
-            std::vector<double> gc(n_cand);
-            int rc = PAT_OK;
-            for (int c = 0; c < n_cand && !rc; ++c) {
-                pat_params q = p[b];
+            PAT_CUDA(cudaMallocAsync(&ub, nn * n_cand * sizeof(float), st));
+            std::vector<const pat_geometry*> gb(n_cand, g[b]);
+            std::vector<const float*> fb(n_cand, f[b]);
+            std::vector<pat_params> qb(n_cand, p[b]);
+            std::vector<float*> ubs(n_cand);
+            std::vector<pat_info> ii(n_cand);
+            for (int c = 0; c < n_cand; ++c) {
+                pat_params& q = qb[c];
                 q.step_ratio = cand[c];
                 q.adapt = PAT_ADAPT_NONE;
                 q.iters = probe_iters;
                 q.tol = 0.0;
                 q.gap_every = 0;
                 q.x_out_dev = q.xbar_out_dev = q.y_out_dev = q.x_lo_out_dev = nullptr;
-                pat_info ii{};
-                rc = p[b].reg == PAT_WAV ? run_wavelet(g[b], f[b], &q, ub, &ii, st, who)
-                                         : run_batch(1, &g[b], &f[b], &q, &ub, &ii, st, who);
-                gc[c] = ii.rel_gap;
-                if (gaps) gaps[b * n_cand + c] = ii.rel_gap;
-                if (gc[c] < gc[bi]) bi = c;
+                ubs[c] = ub + nn * c;
             }
+            const int rc = p[b].reg == PAT_WAV
+                               ? run_wavelet(n_cand, gb.data(), fb.data(), qb.data(), ubs.data(), ii.data(), st, who)
+                               : run_batch(n_cand, gb.data(), fb.data(), qb.data(), ubs.data(), ii.data(), st, who);
             cudaFreeAsync(ub, st);
             if (rc) return rc;
+            int bi = 0;
+            for (int c = 0; c < n_cand; ++c) {
+                if (gaps) gaps[b * n_cand + c] = ii[c].rel_gap;
+                if (ii[c].rel_gap < ii[bi].rel_gap) bi = c;
+            }
             best[b] = cand[bi];
         }
         return PAT_OK;

@@ -29,7 +29,11 @@ __device__ __forceinline__ float wav_f(bool high, int n) { return high ? wav_g(n
 
 // out (M x M block, stride so) = one analysis level of in (M x M block, stride si)
 __global__ void k_wav_analysis(const float* __restrict__ in, int si, float* __restrict__ out, int so, int M,
-                               const int* stop) {
+                               const int* stop, long long ps) {
+    const long long po = ps * blockIdx.z;   // problem blockIdx.z of a batch: its buffers lie po bytes on
+    in = at_bytes(in, po);
+    out = at_bytes(out, po);
+    stop = stop ? at_bytes(stop, po) : stop;
     if (stop && *(volatile const int*)stop) return;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= M || y >= M) return;
@@ -52,7 +56,11 @@ __global__ void k_wav_analysis(const float* __restrict__ in, int si, float* __re
 // block in (M x M, stride si): out[y][x] = sum over the four quadrants and the taps that
 // reach (y, x) of f_y[y - 2k] f_x[x - 2m] c[k][m] (indices mod M).
 __global__ void k_wav_synthesis(const float* __restrict__ in, int si, float* __restrict__ out, int so, int M,
-                                const int* stop) {
+                                const int* stop, long long ps) {
+    const long long po = ps * blockIdx.z;
+    in = at_bytes(in, po);
+    out = at_bytes(out, po);
+    stop = stop ? at_bytes(stop, po) : stop;
     if (stop && *(volatile const int*)stop) return;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x >= M || y >= M) return;
@@ -76,26 +84,51 @@ __global__ void k_wav_synthesis(const float* __restrict__ in, int si, float* __r
 }
 
 __global__ void k_copy_block(const float* __restrict__ in, int si, float* __restrict__ out, int so, int M,
-                             const int* stop) {
+                             const int* stop, long long ps) {
+    const long long po = ps * blockIdx.z;
+    in = at_bytes(in, po);
+    out = at_bytes(out, po);
+    stop = stop ? at_bytes(stop, po) : stop;
     if (stop && *(volatile const int*)stop) return;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
     if (x < M && y < M) out[(size_t)y * so + x] = in[(size_t)y * si + x];
 }
 
-dim3 block_grid(int M) { return dim3(ceil_div(M, 32), ceil_div(M, 8)); }
 
 // r <- clip(r + sigma_r / s * W ubar, -alpha, alpha): the prox of F2* for the scalar
 // coefficients of the wavelet model (Sec. 3.2)
 __global__ void k_wav_dual(float* __restrict__ r, const float* __restrict__ wub, const float* __restrict__ sig_r,
-                           const float* step_mul, float alpha, long long nn, const int* stop) {
+                           const float* step_mul, const float* scal, long long nn, const int* stop, long long ps) {
+    const long long po = ps * blockIdx.y;
+    r = at_bytes(r, po);
+    wub = at_bytes(wub, po);
+    sig_r = at_bytes(sig_r, po);
+    step_mul = at_bytes(step_mul, po);
+    stop = stop ? at_bytes(stop, po) : stop;
     if (stop && *(volatile const int*)stop) return;
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= nn) return;
+    const float alpha = *at_bytes(scal, po);
     const float v = r[i] + __ldg(sig_r + i) * __ldg(step_mul + 1) * wub[i];
     r[i] = fminf(fmaxf(v, -alpha), alpha);
 }
 
-__global__ void k_wav_primal(const WavPrimalArgs a) {
+__global__ void k_wav_primal(WavPrimalArgs a, long long ps) {
+    const long long po = ps * blockIdx.z;   // every pointer of a is in the problem's workspace
+    a.tau_u = at_bytes(a.tau_u, po);
+    a.step_mul = at_bytes(a.step_mul, po);
+    a.scal = at_bytes(a.scal, po);
+    a.kt.acc = at_bytes(a.kt.acc, po);
+    a.kt.ymax_bits = at_bytes(a.kt.ymax_bits, po);
+    a.kt.tile_kmax = at_bytes(a.kt.tile_kmax, po);
+    a.wtr = at_bytes(a.wtr, po);
+    a.u = at_bytes(a.u, po);
+    if (a.u_old) a.u_old = at_bytes(a.u_old, po);
+    a.ubar = at_bytes(a.ubar, po);
+    a.kt_clear = at_bytes(a.kt_clear, po);
+    a.qmax_next = at_bytes(a.qmax_next, po);
+    if (a.stop) a.stop = at_bytes(a.stop, po);
+    if (a.iter) a.iter = at_bytes(a.iter, po);
     if (a.stop && *(volatile const int*)a.stop) return;
     const int N = a.n;
     const int gx = blockIdx.x * blockDim.x + threadIdx.x, gy = blockIdx.y * blockDim.y + threadIdx.y;
@@ -108,7 +141,7 @@ __global__ void k_wav_primal(const WavPrimalArgs a) {
     const float uo = a.u[gi];
     if (a.u_old) a.u_old[gi] = uo;
     const float un = uo - __ldg(a.tau_u + gi) * __ldg(a.step_mul) * (a.kt.at(gx, gy, N) + __ldg(a.wtr + gi));
-    const float ub = un + a.theta * (un - uo);
+    const float ub = un + __ldg(a.scal + 1) * (un - uo);
     a.u[gi] = un;
     a.ubar[gi] = ub;
     a.kt_clear[gi] = 0;
@@ -116,7 +149,17 @@ __global__ void k_wav_primal(const WavPrimalArgs a) {
 
 // per-block sums, in the layout of the gap's pixel pass: {|W u|_1, 0, |K^T q + W^T r|_1, 0,
 // |u - u_old|^2, |u_old|^2, 0}
-__global__ void __launch_bounds__(256) k_wav_gap_pixels(const WavGapArgs a) {
+__global__ void __launch_bounds__(256) k_wav_gap_pixels(WavGapArgs a, long long ps) {
+    const long long po = ps * blockIdx.y;
+    a.wu = at_bytes(a.wu, po);
+    a.kt.acc = at_bytes(a.kt.acc, po);
+    a.kt.ymax_bits = at_bytes(a.kt.ymax_bits, po);
+    a.kt.tile_kmax = at_bytes(a.kt.tile_kmax, po);
+    a.wtr = at_bytes(a.wtr, po);
+    a.u = at_bytes(a.u, po);
+    if (a.u_old) a.u_old = at_bytes(a.u_old, po);
+    a.partials = at_bytes(a.partials, po);
+    if (a.stop) a.stop = at_bytes(a.stop, po);
     if (a.stop && *(volatile const int*)a.stop) return;
     const int N = a.n;
     const long long NN = (long long)N * N;
@@ -218,16 +261,20 @@ void wav_abs_sums(int n, int levels, std::vector<double>& rows, std::vector<doub
     }
 }
 
+// In the launches below, B problems whose buffers lie ps bytes apart (one workspace block
+// per problem) run in one grid: the problem index is the grid's last dimension.
+static dim3 block_grid(int M, int B) { return dim3(ceil_div(M, 32), ceil_div(M, 8), B); }
+
 // out = W in.  scratch: N*N floats.
 int launch_wav_analysis(const float* in, int N, int levels, float* out, float* scratch, const int* stop,
-                        cudaStream_t st) {
+                        cudaStream_t st, int B, long long ps) {
     const dim3 blk(32, 8);
-    k_wav_analysis<<<block_grid(N), blk, 0, st>>>(in, N, out, N, N, stop);
+    k_wav_analysis<<<block_grid(N, B), blk, 0, st>>>(in, N, out, N, N, stop, ps);
     PAT_LAUNCH_CHECK("k_wav_analysis");
     for (int l = 1, M = N / 2; l < levels; ++l, M /= 2) {
-        k_copy_block<<<block_grid(M), blk, 0, st>>>(out, N, scratch, M, M, stop);
+        k_copy_block<<<block_grid(M, B), blk, 0, st>>>(out, N, scratch, M, M, stop, ps);
         PAT_LAUNCH_CHECK("k_copy_block");
-        k_wav_analysis<<<block_grid(M), blk, 0, st>>>(scratch, M, out, N, M, stop);
+        k_wav_analysis<<<block_grid(M, B), blk, 0, st>>>(scratch, M, out, N, M, stop, ps);
         PAT_LAUNCH_CHECK("k_wav_analysis");
     }
     return PAT_OK;
@@ -235,35 +282,35 @@ int launch_wav_analysis(const float* in, int N, int levels, float* out, float* s
 
 // out = W^T in.  scratch: N*N floats; out may not alias in.
 int launch_wav_synthesis(const float* in, int N, int levels, float* out, float* scratch, const int* stop,
-                         cudaStream_t st) {
+                         cudaStream_t st, int B, long long ps) {
     const dim3 blk(32, 8);
-    k_copy_block<<<block_grid(N), blk, 0, st>>>(in, N, out, N, N, stop);
+    k_copy_block<<<block_grid(N, B), blk, 0, st>>>(in, N, out, N, N, stop, ps);
     PAT_LAUNCH_CHECK("k_copy_block");
     for (int l = levels - 1; l >= 0; --l) {
         const int M = N >> l;
-        k_wav_synthesis<<<block_grid(M), blk, 0, st>>>(out, N, scratch, M, M, stop);
+        k_wav_synthesis<<<block_grid(M, B), blk, 0, st>>>(out, N, scratch, M, M, stop, ps);
         PAT_LAUNCH_CHECK("k_wav_synthesis");
-        k_copy_block<<<block_grid(M), blk, 0, st>>>(scratch, M, out, N, M, stop);
+        k_copy_block<<<block_grid(M, B), blk, 0, st>>>(scratch, M, out, N, M, stop, ps);
         PAT_LAUNCH_CHECK("k_copy_block");
     }
     return PAT_OK;
 }
 
-int launch_wav_dual(float* r, const float* wub, const float* sig_r, const float* step_mul, float alpha, long long nn,
-                    const int* stop, cudaStream_t st) {
-    k_wav_dual<<<(unsigned)ceil_div(nn, 256), 256, 0, st>>>(r, wub, sig_r, step_mul, alpha, nn, stop);
+int launch_wav_dual(float* r, const float* wub, const float* sig_r, const float* step_mul, const float* scal,
+                    long long nn, const int* stop, cudaStream_t st, int B, long long ps) {
+    k_wav_dual<<<dim3((unsigned)ceil_div(nn, 256), B), 256, 0, st>>>(r, wub, sig_r, step_mul, scal, nn, stop, ps);
     PAT_LAUNCH_CHECK("k_wav_dual");
     return PAT_OK;
 }
 
-int launch_wav_primal(const WavPrimalArgs& a, cudaStream_t st) {
-    k_wav_primal<<<dim3(ceil_div(a.n, 32), ceil_div(a.n, 8)), dim3(32, 8), 0, st>>>(a);
+int launch_wav_primal(const WavPrimalArgs& a, cudaStream_t st, int B, long long ps) {
+    k_wav_primal<<<dim3(ceil_div(a.n, 32), ceil_div(a.n, 8), B), dim3(32, 8), 0, st>>>(a, ps);
     PAT_LAUNCH_CHECK("k_wav_primal");
     return PAT_OK;
 }
 
-int launch_wav_gap_pixels(const WavGapArgs& a, int nblocks, cudaStream_t st) {
-    k_wav_gap_pixels<<<nblocks, 256, 0, st>>>(a);
+int launch_wav_gap_pixels(const WavGapArgs& a, int nblocks, cudaStream_t st, int B, long long ps) {
+    k_wav_gap_pixels<<<dim3(nblocks, B), 256, 0, st>>>(a, ps);
     PAT_LAUNCH_CHECK("k_wav_gap_pixels");
     return PAT_OK;
 }
@@ -286,8 +333,8 @@ extern "C" int pat_wavelet_transform(int n, int levels, const float* in_dev, flo
     cudaStream_t st = (cudaStream_t)stream;
     float* scratch = nullptr;
     PAT_CUDA(cudaMallocAsync(&scratch, (size_t)n * n * sizeof(float), st));
-    const int rc = inverse ? launch_wav_synthesis(in_dev, n, levels, out_dev, scratch, nullptr, st)
-                           : launch_wav_analysis(in_dev, n, levels, out_dev, scratch, nullptr, st);
+    const int rc = inverse ? launch_wav_synthesis(in_dev, n, levels, out_dev, scratch, nullptr, st, 1, 0)
+                           : launch_wav_analysis(in_dev, n, levels, out_dev, scratch, nullptr, st, 1, 0);
     cudaFreeAsync(scratch, st);
     return rc;
 }

@@ -151,3 +151,83 @@ def test_dtcwt_model_at_benchmark_size_reaches_tolerance():
     assert info["status"] == P.PAT_STATUS_CONVERGED and info["rel_gap"] <= 1e-3
     assert np.isfinite(host(u_d)).all()
     pg.close()
+
+
+def _problem_det(seed, n_det, n=16):
+    det = S.detectors_full_circle(n_det, 1.2)
+    r0, dr = S.radial_sampling(det, 24)
+    w = dict(n=n, det_xy=det, n_t=24, r0=r0, dr=dr, quad_m=48, n_fine=2 * n, quad_m_fine=96)
+    w["phantom_fine"] = S.rasterise_discs(S.disc_params(3, seed), 2 * n)
+    w["noise"] = S.standard_normal((n_det, 24), seed + 17)
+    w["noise_level"] = 0.02
+    return noisy_data(w), P.Geometry(n, det, 24, r0, dr, 48)
+
+
+@pytest.mark.parametrize("kind", [P.PAT_WAVELET_DWT, P.PAT_WAVELET_DTCWT])
+def test_wavelet_batch_gives_the_single_runs_bits(kind):
+    """Wavelet problems of one N and transform run as one lockstep batch (K, K^T and every
+    wavelet kernel launch once for all of them, each problem's buffers a fixed stride apart)
+    and give each problem's single-run image, dual state and gap bit for bit.  The batch mixes
+    geometries (10 and 12 detectors), alpha, theta and tolerances: the third problem meets its
+    tolerance (relative gap 2, near iteration 80 or 90 with a gap evaluation every 10) and stops while the
+    others go on.  A 32^2 wavelet problem and a TV problem in the same call run in batches
+    of their own."""
+    iters = 120
+    specs = [(1, 10, 16, 0.02, 1.0, 0.0), (2, 12, 16, 0.05, 0.8, 0.0), (3, 10, 16, 0.02, 1.0, 2.0),
+             (4, 10, 32, 0.03, 1.0, 0.0)]
+    probs = []
+    for seed, n_det, n, alpha, theta, tol in specs:
+        f, pg = _problem_det(seed, n_det, n)
+        fd = dev(f)
+        y = torch.zeros(f.size + 4 * n * n, device=DEV)
+        prm = P.make_params(reg=P.PAT_WAV, alpha=alpha, theta=theta, tol=tol, iters=iters, gap_every=10,
+                            wavelet_levels=2, wavelet_kind=kind, y_out=y)
+        u = torch.empty(n, n, device=DEV)
+        info = P.pat_reconstruct(pg.handle, fd, prm, u)
+        probs.append(dict(pg=pg, f=fd, n=n, u=host(u), y=host(y), info=info, tol=tol, alpha=alpha, theta=theta,
+                          kind=kind))
+    assert probs[2]["info"]["iters_done"] < iters and probs[0]["info"]["iters_done"] == iters
+    # a TV problem in the same call
+    ft, pt = _problem_det(5, 10, 16)
+    ftd = dev(ft)
+    ptv = P.make_params(reg=P.PAT_TV, alpha=0.02, iters=iters, gap_every=10)
+    ut = torch.empty(16, 16, device=DEV)
+    P.pat_reconstruct(pt.handle, ftd, ptv, ut)
+    ut_single = host(ut)
+    outs, ys, prms = [], [], []
+    for q in probs:
+        n = q["n"]
+        outs.append(torch.zeros(n, n, device=DEV))
+        ys.append(torch.zeros(q["y"].size, device=DEV))
+        prms.append(P.make_params(reg=P.PAT_WAV, alpha=q["alpha"], theta=q["theta"], tol=q["tol"], iters=iters,
+                                  gap_every=10, wavelet_levels=2, wavelet_kind=kind, y_out=ys[-1]))
+    ut_b = torch.zeros(16, 16, device=DEV)
+    infos = P.pat_reconstruct_batched([q["pg"].handle for q in probs] + [pt.handle], [q["f"] for q in probs] + [ftd],
+                                      prms + [ptv], outs + [ut_b])
+    for q, o, y, inf in zip(probs, outs, ys, infos):
+        assert inf["iters_done"] == q["info"]["iters_done"] and inf["status"] == q["info"]["status"]
+        assert np.array_equal(host(o), q["u"])
+        assert np.array_equal(host(y), q["y"])
+        assert inf["gap"] == q["info"]["gap"] and inf["rel_gap"] == q["info"]["rel_gap"]
+    assert np.array_equal(host(ut_b), ut_single)
+    for q in probs:
+        q["pg"].close()
+    pt.close()
+
+
+def test_wavelet_step_ratio_probes_run_as_one_batch():
+    """The balance probes of a wavelet problem run as one batch of candidates; each probe's
+    relative gap equals that of a single run with the candidate's step ratio."""
+    f, pg = _problem_det(1, 10, 16)
+    fd = dev(f)
+    prm = P.make_params(reg=P.PAT_WAV, alpha=0.02, iters=100, gap_every=10, wavelet_levels=2,
+                        wavelet_kind=P.PAT_WAVELET_DTCWT)
+    cands = [0.5, 1.0, 4.0]
+    best, gaps = P.pat_tune_step_ratio(pg.handle, fd, prm, cands, 30)
+    u = torch.empty(16, 16, device=DEV)
+    for c, gq in zip(cands, gaps):
+        q = P.make_params(reg=P.PAT_WAV, alpha=0.02, iters=30, gap_every=0, wavelet_levels=2,
+                          wavelet_kind=P.PAT_WAVELET_DTCWT, step_ratio=c)
+        assert P.pat_reconstruct(pg.handle, fd, q, u)["rel_gap"] == gq
+    assert best == cands[int(np.argmin(gaps))]
+    pg.close()
