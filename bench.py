@@ -643,7 +643,8 @@ def run_wavelet_leg(P, torch, geo, f, u, stream, flush, args):
     """PAT_WAV (Sec. 2.2, alpha 0.02, 4 levels) on the benchmark's geometry and data, with the
     paper's dual-tree complex wavelet transform and with the orthonormal DWT: 1000 fixed
     iterations (gap every 10), then the time to rel gap 1e-4 with the paper's steps and with
-    the probe-tuned balance (probe time included)."""
+    the probe-tuned balance (probe time included), and 1000 iterations of a lockstep batch of
+    copies of the problem."""
     def leg(kind):
         def run(iters, tol, ratio):
             prm = P.make_params(reg=P.PAT_WAV, alpha=0.02, iters=iters, tol=tol, gap_every=10, wavelet_levels=4,
@@ -653,6 +654,16 @@ def run_wavelet_leg(P, torch, geo, f, u, stream, flush, args):
         run(50, 0.0, 1.0)
         fixed = run(1000, 0.0, 1.0)
         out = {"alpha": 0.02, "levels": 4, "iters_per_s": 1000 / (fixed["ms"] / 1e3), "ms_per_1000_iters": fixed["ms"]}
+        if args.wavelet_batch > 1:
+            # B copies of the problem as one lockstep batch: 1000 iterations each
+            B = args.wavelet_batch
+            us = [torch.empty_like(u) for _ in range(B)]
+            prm = P.make_params(reg=P.PAT_WAV, alpha=0.02, iters=50, gap_every=10, wavelet_levels=4, wavelet_kind=kind)
+            P.pat_reconstruct_batched([geo.handle] * B, [f] * B, [prm] * B, us, stream)
+            prm = P.make_params(reg=P.PAT_WAV, alpha=0.02, iters=1000, gap_every=10, wavelet_levels=4, wavelet_kind=kind)
+            flush.zero_()
+            ms = P.pat_reconstruct_batched([geo.handle] * B, [f] * B, [prm] * B, us, stream)[0]["ms"]
+            out["batched"] = {"problems": B, "problem_iters_per_s": B * 1000 / (ms / 1e3), "ms_per_1000_iters": ms}
         paper = run(args.ttg_max_iters, 1e-4, 1.0)
         out["time_to_gap_paper_steps"] = {"iters": paper["iters_done"], "seconds": paper["ms"] / 1e3,
                                           "reached": paper["status"] == P.PAT_STATUS_CONVERGED}
@@ -805,6 +816,8 @@ def main(argv=None) -> int:
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--batch", type=int, default=16, help="TGV 256^2 problems in the lockstep batch (0: skip)")
     ap.add_argument("--mixed", type=int, default=1, help="run the 64-problem mixed batch (0: skip)")
+    ap.add_argument("--wavelet-batch", type=int, default=8,
+                    help="problems of the wavelet leg's lockstep batch (0 or 1: skip)")
     ap.add_argument("--mixed-max-iters", type=int, default=5000)
     ap.add_argument("--probe-iters", type=int, default=300, help="iterations of each step-ratio probe")
     ap.add_argument("--warm", type=int, default=1, help="run the learned warm-start leg (0: skip)")
