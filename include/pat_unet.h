@@ -53,7 +53,7 @@ extern "C" {
 
 /* y = conv3x3(x, w) + bias, then max(y, 0) if relu != 0.  x: batch x h x w x cin (bf16),
    w: cout x 3 x 3 x cin (bf16), bias: cout FP32 or NULL, y: batch x h x w x cout FP32.
-   cin and cout must be positive multiples of 8; x and w 16-byte aligned. */
+   cin and cout must be positive multiples of 8; x, w and y 16-byte aligned (checked). */
 int pat_conv3x3_forward(const uint16_t* x_dev, int batch, int h, int w, int cin,
                         const uint16_t* w_dev, const float* bias_dev, int cout, int relu,
                         float* y_dev, void* stream);
@@ -68,6 +68,13 @@ int pat_conv3x3_backward_data(const uint16_t* dy_dev, int batch, int h, int w, i
 int pat_conv3x3_backward_weight(const uint16_t* x_dev, const uint16_t* dy_dev, int batch, int h,
                                 int w, int cin, int cout, float* dw_dev, float* db_dev,
                                 void* stream);
+
+/* Number of bounded waits in the tensor-memory convolutions (pat_conv3x3_forward,
+   pat_conv3x3_backward_data and the network's forward and data-gradient passes) that ran
+   out since the library was loaded.  Each such wait ends its CTA early: it counts here,
+   drains its copies, frees its tensor memory and writes no output.  0 in normal operation.
+   Returns PAT_OK, or PAT_ERR_CUDA if the counter cannot be read; count receives it. */
+int pat_nn_wait_timeouts(unsigned* count);
 
 /* ---- the network ------------------------------------------------------------------ */
 typedef struct pat_unet pat_unet;   /* opaque */

@@ -40,7 +40,7 @@ EXPORTED = [
     "pat_dtcwt_transform",
     "pat_time_phases", "pat_forward_plan", "pat_geometry_set_shapes", "pat_geometry_get_shapes", "pat_tune_shapes",
     # learned warm start (include/pat_unet.h)
-    "pat_conv3x3_forward", "pat_conv3x3_backward_data", "pat_conv3x3_backward_weight",
+    "pat_conv3x3_forward", "pat_conv3x3_backward_data", "pat_conv3x3_backward_weight", "pat_nn_wait_timeouts",
     "pat_unet_create", "pat_unet_destroy", "pat_unet_num_params", "pat_unet_get_params",
     "pat_unet_set_params", "pat_unet_forward", "pat_unet_backward", "pat_unet_train_step",
     "pat_warm_start_features", "pat_warm_start_state", "pat_warm_start_target", "pat_warm_start",
@@ -160,6 +160,7 @@ def load(path: str | None = None) -> ctypes.CDLL:
         "pat_conv3x3_forward": (i, [vp, i, i, i, i, vp, vp, i, i, vp, vp]),
         "pat_conv3x3_backward_data": (i, [vp, i, i, i, i, vp, i, vp, vp]),
         "pat_conv3x3_backward_weight": (i, [vp, vp, i, i, i, i, i, vp, vp, vp]),
+        "pat_nn_wait_timeouts": (i, [ctypes.POINTER(ctypes.c_uint)]),
         "pat_unet_create": (i, [ctypes.POINTER(pat_unet_desc), ctypes.POINTER(vp)]),
         "pat_unet_destroy": (None, [vp]),
         "pat_unet_num_params": (ctypes.c_longlong, [vp]),
@@ -483,6 +484,13 @@ def pat_conv3x3_backward_data(dy_dev, batch, h, w, cout, w_dev, cin, dx_dev, str
 def pat_conv3x3_backward_weight(x_dev, dy_dev, batch, h, w, cin, cout, dw_dev, db_dev=None, stream=None) -> None:
     _check(load().pat_conv3x3_backward_weight(_ptr(x_dev), _ptr(dy_dev), batch, h, w, cin, cout, _ptr(dw_dev),
                                               _ptr(db_dev), _stream(stream)), "pat_conv3x3_backward_weight")
+
+
+def pat_nn_wait_timeouts() -> int:
+    """Bounded waits of the tensor-memory convolutions that ran out since the library loaded."""
+    v = ctypes.c_uint()
+    _check(load().pat_nn_wait_timeouts(ctypes.byref(v)), "pat_nn_wait_timeouts")
+    return int(v.value)
 
 
 def pat_unet_create(in_ch=8, out_ch=8, base_ch=32, levels=4, seed=0) -> int:

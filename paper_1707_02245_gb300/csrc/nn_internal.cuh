@@ -35,5 +35,9 @@ int conv3x3_wgrad(const View& x, const View& dz, int B, int H, int W, int cin, i
 // dL/dx from dL/dy.
 int flip_weights(const bf16* w, int cout, int cin, bf16* wflip, cudaStream_t st);
 
+// bounded waits of the tensor-memory convolutions that ran out since the library loaded
+// (~0u if it cannot be read)
+unsigned wait_timeouts();
+
 }  // namespace nn
 }  // namespace pat

@@ -532,6 +532,7 @@ int set_device(const pat_unet* net) {
 }
 
 bool mult8(int c) { return c > 0 && c % 8 == 0; }
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 }  // namespace
 
@@ -540,10 +541,18 @@ bool mult8(int c) { return c > 0 && c % 8 == 0; }
 // ---------------------------------------------------------------------------------------
 extern "C" {
 
+int pat_nn_wait_timeouts(unsigned* count) {
+    if (!count) return fail(PAT_ERR_INVALID_ARG, "pat_nn_wait_timeouts: null argument");
+    *count = nn::wait_timeouts();
+    return *count == ~0u ? fail(PAT_ERR_CUDA, "pat_nn_wait_timeouts: counter not readable") : PAT_OK;
+}
+
 int pat_conv3x3_forward(const uint16_t* x_dev, int batch, int h, int w, int cin, const uint16_t* w_dev,
                         const float* bias_dev, int cout, int relu, float* y_dev, void* stream) {
     if (!x_dev || !w_dev || !y_dev || batch < 0 || h < 0 || w < 0 || !mult8(cin) || !mult8(cout))
         return fail(PAT_ERR_INVALID_ARG, "pat_conv3x3_forward: null pointer, negative size or channels not a multiple of 8");
+    if (!aligned16(x_dev) || !aligned16(w_dev) || !aligned16(y_dev))
+        return fail(PAT_ERR_INVALID_ARG, "pat_conv3x3_forward: x, w and y must be 16-byte aligned");
     const View x{(bf16*)x_dev, cin};
     return nn::conv3x3_fwd(x, batch, h, w, cin, (const bf16*)w_dev, bias_dev, cout, relu != 0, View{nullptr, 0}, y_dev,
                            cout, (cudaStream_t)stream);
@@ -551,7 +560,8 @@ int pat_conv3x3_forward(const uint16_t* x_dev, int batch, int h, int w, int cin,
 
 int pat_conv3x3_backward_data(const uint16_t* dy_dev, int batch, int h, int w, int cout, const uint16_t* w_dev, int cin,
                               float* dx_dev, void* stream) {
-    if (!dy_dev || !w_dev || !dx_dev || batch < 0 || h < 0 || w < 0 || !mult8(cin) || !mult8(cout))
+    if (!dy_dev || !w_dev || !dx_dev || batch < 0 || h < 0 || w < 0 || !mult8(cin) || !mult8(cout) ||
+        !aligned16(dy_dev) || !aligned16(w_dev) || !aligned16(dx_dev))
         return fail(PAT_ERR_INVALID_ARG, "pat_conv3x3_backward_data: invalid argument");
     cudaStream_t st = (cudaStream_t)stream;
     bf16* wf = nullptr;

@@ -268,3 +268,9 @@ def test_warm_start_one_call_equals_its_steps():
     assert torch.equal(x0a, x0b) and torch.equal(y0a, y0b)
     net.close()
     g.close()
+
+
+def test_zz_no_tensor_memory_wait_ran_out():
+    """Every bounded mbarrier wait of the tensor-memory convolutions in this module's runs
+    completed (a wait that ran out would have ended its CTA without output)."""
+    assert P.pat_nn_wait_timeouts() == 0
