@@ -725,13 +725,290 @@ __global__ void __launch_bounds__(THREADS) k_conv_wgrad(const WgradArgs a) {
     if (do_bias && tid < BM && m0 + tid < a.cout) a.part_b[(size_t)blockIdx.z * a.cout + m0 + tid] = bsum;
 }
 
-// out[i] = sum_z part[z][i] in the order z = 0, 1, ...
+// ---------------------------------------------------------------------------------------
+// weight gradient on the 5th-generation tensor cores: the same pipeline as k_conv_fwd_tc
+// on the transposed problem  D[k][o] = sum_p X[p][k] dz[p][o],  k = (tap, channel) rows of
+// an M tile of 128, o = the BN output channels, p = pixels (the GEMM's K) in tiles of PT
+// (a wx x wy rectangle of one image, wx wy = PT).  Both operands are stored pixel-major,
+// so both are MN-major for the MMA: TMA writes the box {CB channels, wx, wy, 1} of x at
+// the tap's offset (zero fill outside the image) and the box {CBO channels, wx, wy, 1} of
+// dz as rows of CB (CBO) channels per pixel, swizzled by the row size (64 or 128 bytes).
+// An MN-major swizzle atom is 8 pixel rows; LBO steps from one channel box to the next,
+// SBO from one 8-pixel group to the next.  A work unit is (M tile, split of the pixel
+// tiles); the unit's partial D goes to part[split][o][k], summed over splits in a fixed
+// order by k_sum_splits.
+// ---------------------------------------------------------------------------------------
+// pixels per stage: 128 (eight MMAs of K = 16 per wait) except at BN = 256 (64: the B tile
+// of a stage is then 32 KB)
+template <int BN>
+constexpr int wg_pt() { return BN == 256 ? 64 : 128; }
+
+struct WgTcArgs {
+    int B, H, W, cin, cout;
+    int wx_log2, wy;        // pixel tile: 2^wx_log2 x wy
+    int ptiles_x, ptiles_y, n_ptiles;
+    int m_tiles, splits, per, total;
+    int cbx, cbo;           // channels per box of x and of dz: 32 or 64
+    float* part;            // [splits][cout][9 cin]
+};
+
+template <int BN>
+struct WgCfg {
+    static constexpr int PT = wg_pt<BN>();
+    static constexpr int A_BYTES = TBM * PT * 2;
+    static constexpr int STAGE = A_BYTES + BN * PT * 2;
+    static constexpr int STAGES = BN == 256 ? 4 : (BN == 128 ? 3 : 4);
+    static constexpr int NACC = BN == 256 ? 2 : 4;
+    static constexpr int BAR_OFF = STAGES * STAGE;
+    static constexpr int SLOT_OFF = BAR_OFF + 8 * (2 * STAGES + 2 * NACC + 1);
+    static constexpr int SMEM = SLOT_OFF + 16 + 1024;
+    static constexpr uint32_t NCOLS = NACC * BN;
+};
+
+// instruction descriptor of kind::f16 with both operands MN-major (bits 15, 16)
+constexpr uint32_t tc_idesc_mn(int M, int N) { return tc_idesc(M, N) | (1u << 15) | (1u << 16); }
+
+// pixel tile pt -> its image and first pixel
+__device__ __forceinline__ void wg_ptile(const WgTcArgs& a, int pt, int& n, int& x0, int& y0) {
+    const int tx = pt % a.ptiles_x, r = pt / a.ptiles_x;
+    x0 = tx << a.wx_log2;
+    y0 = (r % a.ptiles_y) * a.wy;
+    n = r / a.ptiles_y;
+}
+
+template <int BN>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_conv_wgrad_tc(const __grid_constant__ CUtensorMap tmX, const __grid_constant__ CUtensorMap tmD, const WgTcArgs a) {
+    using C = WgCfg<BN>;
+    constexpr int S = C::STAGES, NA = C::NACC;
+    constexpr uint32_t IDESC = tc_idesc_mn(TBM, BN);
+    static_assert(BN == 32 || BN == 64 || BN == 128 || BN == 256, "N of the MMA");
+    extern __shared__ unsigned char smem_raw[];
+    unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    const uint32_t sbase = smem_u32(smem);
+    const uint32_t bars = sbase + C::BAR_OFF;
+    auto full = [&](int s) { return bars + 8u * s; };
+    auto empty = [&](int s) { return bars + 8u * (S + s); };
+    auto accf = [&](int b) { return bars + 8u * (2 * S + b); };
+    auto acce = [&](int b) { return bars + 8u * (2 * S + NA + b); };
+    const uint32_t fin = bars + 8u * (2 * S + 2 * NA);
+    uint32_t* slot = reinterpret_cast<uint32_t*>(smem + C::SLOT_OFF);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(smem + C::SLOT_OFF + 4);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int K = 9 * a.cin;
+
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            mbar_init(full(s), 1);
+            mbar_init(empty(s), 1);
+        }
+        for (int b = 0; b < NA; ++b) {
+            mbar_init(accf(b), 1);
+            mbar_init(acce(b), 4);
+        }
+        mbar_init(fin, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(slot)),
+                     "r"(C::NCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *slot;
+    auto give_up = [&]() {
+        *abort_flag = 1;
+        atomicAdd(&g_tc_timeouts, 1u);
+    };
+    // the pixel tiles of unit u: [p_begin, p_end)
+    auto unit_range = [&](int u, int& mt, int& p_begin, int& p_end) {
+        mt = u % a.m_tiles;
+        const int z = u / a.m_tiles;
+        p_begin = z * a.per;
+        p_end = min(a.n_ptiles, p_begin + a.per);
+    };
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // ---- TMA producer ----
+            int it = 0;
+            const int qa = TBM / a.cbx, qb = BN / a.cbo;
+            const uint32_t a_box = C::PT * a.cbx * 2, b_box = C::PT * a.cbo * 2;
+            for (int u = blockIdx.x; u < a.total && !*abort_flag; u += gridDim.x) {
+                int mt, pb, pe;
+                unit_range(u, mt, pb, pe);
+                for (int pt = pb; pt < pe; ++pt, ++it) {
+                    const int s = it % S;
+                    if (!mbar_wait(empty(s), ((it / S) & 1) ^ 1)) {
+                        give_up();
+                        break;
+                    }
+                    mbar_expect_tx(full(s), (uint32_t)C::STAGE);
+                    int n, x0, y0;
+                    wg_ptile(a, pt, n, x0, y0);
+                    const uint32_t As = sbase + s * C::STAGE, Bs = As + C::A_BYTES;
+                    for (int q = 0; q < qa; ++q) {
+                        const int k = mt * TBM + q * a.cbx;
+                        int c = 0, x = 0, y = 0, nn = a.B;   // rows past K: zero fill
+                        if (k < K) {
+                            const int tap = k / a.cin;
+                            c = k - tap * a.cin;
+                            x = x0 + tap % 3 - 1;
+                            y = y0 + tap / 3 - 1;
+                            nn = n;
+                        }
+                        tma_load_4d(As + q * a_box, &tmX, c, x, y, nn, full(s));
+                    }
+                    for (int q = 0; q < qb; ++q)   // channels >= cout: zero fill
+                        tma_load_4d(Bs + q * b_box, &tmD, q * a.cbo, x0, y0, n, full(s));
+                }
+            }
+            for (int j = it - 1; j >= 0 && j >= it - S; --j)
+                if (!mbar_wait(full(j % S), (j / S) & 1)) {
+                    give_up();
+                    break;
+                }
+        }
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // ---- MMA issuer ----
+            // MN-major: LBO = the next channel box (next swizzle atom along M or N), SBO = the
+            // next 8 pixel rows; a K step of 16 pixels advances two 8-row groups
+            const uint32_t sbo_a = 8 * a.cbx * 2, sbo_b = 8 * a.cbo * 2;
+            const uint64_t da = tc_desc(0, C::PT * a.cbx * 2, sbo_a, a.cbx == 64 ? 2u : 4u);
+            const uint64_t db = tc_desc(0, C::PT * a.cbo * 2, sbo_b, a.cbo == 64 ? 2u : 4u);
+            int it = 0, tc = 0;
+            for (int u = blockIdx.x; u < a.total && !*abort_flag; u += gridDim.x, ++tc) {
+                int mt, pb, pe;
+                unit_range(u, mt, pb, pe);
+                const int b = tc % NA;
+                if (!mbar_wait(acce(b), ((tc / NA) & 1) ^ 1)) {
+                    give_up();
+                    break;
+                }
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * BN);
+                bool ok = true;
+                for (int pt = pb; pt < pe; ++pt, ++it) {
+                    const int s = it % S;
+                    if (!mbar_wait(full(s), (it / S) & 1)) {
+                        give_up();
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t As = sbase + s * C::STAGE, Bs = As + C::A_BYTES;
+#pragma unroll
+                    for (int k16 = 0; k16 < C::PT / 16; ++k16)
+                        tc_mma(d, da + ((As + k16 * 2 * sbo_a) >> 4), db + ((Bs + k16 * 2 * sbo_b) >> 4), IDESC,
+                               (pt != pb || k16 != 0) ? 1u : 0u);
+                    tc_commit(empty(s));
+                }
+                if (!ok) break;
+                tc_commit(accf(b));
+            }
+            tc_commit(fin);
+            if (!mbar_wait(fin, 0)) give_up();
+        }
+    } else {
+        // ---- epilogue: warps 2..5; TMEM lane = row k of the M tile ----
+        const int quarter = warp & 3, row = quarter * 32 + lane;
+        const uint32_t tl_lane = tmem + ((uint32_t)(quarter * 32) << 16);
+        int tc = 0;
+        for (int u = blockIdx.x; u < a.total; u += gridDim.x, ++tc) {
+            const int b = tc % NA;
+            int ok = 0;
+            if (lane == 0) ok = mbar_wait(accf(b), (tc / NA) & 1) ? 1 : 0;
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) {
+                if (lane == 0) give_up();
+                break;
+            }
+            tc_fence_after();
+            const int mt = u % a.m_tiles, z = u / a.m_tiles;
+            const int k = mt * TBM + row;
+            float* out = a.part + (size_t)z * a.cout * K;
+#pragma unroll
+            for (int cb16 = 0; cb16 < BN / 16; ++cb16) {
+                float v[16];
+                __syncwarp();
+                tc_ld16(tl_lane + (uint32_t)(b * BN + cb16 * 16), v);
+                if (k >= K) continue;
+#pragma unroll
+                for (int e = 0; e < 16; ++e) {
+                    const int o = cb16 * 16 + e;
+                    if (o < a.cout) out[(size_t)o * K + k] = v[e];
+                }
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(acce(b));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(C::NCOLS) : "memory");
+    }
+}
+
+// part[g][o] = sum of dz[p][o] over the pixel range g of G equal ranges (a fixed order:
+// 8-channel vectors by thread, rows strided by the block's row phases, then the phases in
+// order)
+__global__ void __launch_bounds__(256) k_colsum_part(const bf16* __restrict__ dz, int ps, long long P, int cout,
+                                                     float* __restrict__ part) {
+    __shared__ float sh[256][8];
+    const int g = blockIdx.x, G = gridDim.x;
+    const long long p0 = P * g / G, p1 = P * (g + 1) / G;
+    const int nv = cout / 8, tid = threadIdx.x;
+    const int phases = 256 / nv, v = tid % nv, ph = tid / nv;
+    float acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    if (ph < phases) {
+        for (long long p = p0 + ph; p < p1; p += phases) {
+            const uint4 q = __ldg(reinterpret_cast<const uint4*>(dz + p * ps) + v);
+            const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&q);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 f = __bfloat1622float2(h[e]);
+                acc[2 * e] += f.x;
+                acc[2 * e + 1] += f.y;
+            }
+        }
+    }
+#pragma unroll
+    for (int e = 0; e < 8; ++e) sh[tid][e] = acc[e];
+    __syncthreads();
+    if (tid < nv) {
+        float s[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (int r = 0; r < phases; ++r)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) s[e] += sh[r * nv + tid][e];
+#pragma unroll
+        for (int e = 0; e < 8; ++e) part[(size_t)g * cout + tid * 8 + e] = s[e];
+    }
+}
+
+// out[i] = sum_z part[z][i]
 __global__ void k_sum_splits(const float* __restrict__ part, int splits, long long n, float* __restrict__ out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    float s = 0.f;
-    for (int z = 0; z < splits; ++z) s += part[(size_t)z * n + i];
-    out[i] = s;
+    // eight running sums (split z into sum z mod 8), added in order at the end: a fixed
+    // order with eight loads in flight
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    int z = 0;
+    for (; z + 8 <= splits; z += 8)
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s[j] += __ldg(part + (size_t)(z + j) * n + i);
+    for (int j = 0; z < splits; ++z, ++j) s[j] += __ldg(part + (size_t)z * n + i);
+    float t = 0.f;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) t += s[j];
+    out[i] = t;
 }
 
 __global__ void k_flip_weights(const bf16* __restrict__ w, int cout, int cin, bf16* __restrict__ wf) {
@@ -849,6 +1126,71 @@ int launch_wgrad(const WgradArgs& a, int splits, cudaStream_t st) {
     return PAT_OK;
 }
 
+constexpr int COLSUM_BLOCKS = 1024;   // pixel ranges of the bias-gradient column sums
+
+template <int BN>
+int launch_wgrad_tc(const View& x, const View& dz, int B, int H, int W, int cin, int cout, float* dw, float* db,
+                    float* part, int max_splits, cudaStream_t st) {
+    using C = WgCfg<BN>;
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return fail(PAT_ERR_CUDA, "conv3x3_wgrad: cuTensorMapEncodeTiled is not available");
+    WgTcArgs a;
+    a.B = B;
+    a.H = H;
+    a.W = W;
+    a.cin = cin;
+    a.cout = cout;
+    int lg = 0;
+    while ((1 << lg) < W && (2 << lg) <= C::PT) ++lg;   // pixel tile width: the power of 2 >= W, at most PT
+    a.wx_log2 = lg;
+    a.wy = C::PT >> lg;
+    a.ptiles_x = (W + (1 << lg) - 1) >> lg;
+    a.ptiles_y = (H + a.wy - 1) / a.wy;
+    const long long npt = (long long)B * a.ptiles_x * a.ptiles_y;
+    const int K = 9 * cin;
+    a.m_tiles = (K + TBM - 1) / TBM;
+    if (npt > (1LL << 30)) return fail(PAT_ERR_INVALID_ARG, "conv3x3_wgrad: too many pixel tiles");
+    a.n_ptiles = (int)npt;
+    int splits = std::max(1, std::min(max_splits, (2 * sm_count() + a.m_tiles - 1) / a.m_tiles));
+    a.per = (a.n_ptiles + splits - 1) / splits;
+    a.splits = (a.n_ptiles + a.per - 1) / a.per;
+    a.total = a.m_tiles * a.splits;
+    a.cbx = cin % 64 == 0 ? 64 : 32;
+    a.cbo = cout % 64 == 0 ? 64 : 32;
+    a.part = part;
+    CUtensorMap mx, md;
+    const cuuint32_t es[4] = {1, 1, 1, 1};
+    auto map4 = [&](CUtensorMap* m, const View& v, int ch, int cb) {
+        const cuuint64_t ps = (cuuint64_t)v.ps * 2;
+        const cuuint64_t dims[4] = {(cuuint64_t)ch, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)B};
+        const cuuint64_t strides[3] = {ps, ps * W, ps * W * H};
+        const cuuint32_t box[4] = {(cuuint32_t)cb, (cuuint32_t)(1 << lg), (cuuint32_t)a.wy, 1};
+        return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)v.p, dims, strides, box, es,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, cb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    };
+    if (map4(&mx, x, cin, a.cbx) != CUDA_SUCCESS) return fail(PAT_ERR_CUDA, "conv3x3_wgrad: activation tensor map");
+    if (map4(&md, dz, cout, a.cbo) != CUDA_SUCCESS) return fail(PAT_ERR_CUDA, "conv3x3_wgrad: gradient tensor map");
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(k_conv_wgrad_tc<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+    PAT_CUDA(attr);
+    k_conv_wgrad_tc<BN><<<std::min(a.total, sm_count()), TC_THREADS, C::SMEM, st>>>(mx, md, a);
+    PAT_LAUNCH_CHECK("k_conv_wgrad_tc");
+    const long long nw = (long long)cout * K;
+    k_sum_splits<<<(unsigned)((nw + 255) / 256), 256, 0, st>>>(part, a.splits, nw, dw);
+    PAT_LAUNCH_CHECK("k_sum_splits");
+    if (db) {
+        const long long P = (long long)B * H * W;
+        const int G = (int)std::max<long long>(1, std::min<long long>(COLSUM_BLOCKS, (P + 63) / 64));
+        float* pb = part + (size_t)a.splits * nw;
+        k_colsum_part<<<G, 256, 0, st>>>(dz.p, dz.ps, P, cout, pb);
+        PAT_LAUNCH_CHECK("k_colsum_part");
+        k_sum_splits<<<(unsigned)((cout + 255) / 256), 256, 0, st>>>(pb, G, cout, db);
+        PAT_LAUNCH_CHECK("k_sum_splits");
+    }
+    return PAT_OK;
+}
+
 struct SplitPlan {
     int splits;
     long long per;
@@ -902,12 +1244,19 @@ int conv3x3_fwd(const View& x, int B, int H, int W, int cin, const bf16* w, cons
 
 size_t wgrad_partial_floats(int B, int H, int W, int cin, int cout) {
     const SplitPlan sp = plan_splits(B, H, W, cin, cout);
-    return (size_t)sp.splits * cout * (9 * (size_t)cin + 1);
+    return (size_t)sp.splits * cout * (9 * (size_t)cin + 1) + (size_t)COLSUM_BLOCKS * cout;
 }
 
 int conv3x3_wgrad(const View& x, const View& dz, int B, int H, int W, int cin, int cout, float* dw, float* db,
                   float* part, cudaStream_t st) {
     const SplitPlan sp = plan_splits(B, H, W, cin, cout);
+    // the tensor-memory kernel takes channel counts that fill 64- or 128-byte TMA rows
+    if (cin % 32 == 0 && cout % 32 == 0 && cout <= 256 && B > 0 && H > 0 && W > 0) {
+        if (cout <= 32) return launch_wgrad_tc<32>(x, dz, B, H, W, cin, cout, dw, db, part, sp.splits, st);
+        if (cout <= 64) return launch_wgrad_tc<64>(x, dz, B, H, W, cin, cout, dw, db, part, sp.splits, st);
+        if (cout <= 128) return launch_wgrad_tc<128>(x, dz, B, H, W, cin, cout, dw, db, part, sp.splits, st);
+        return launch_wgrad_tc<256>(x, dz, B, H, W, cin, cout, dw, db, part, sp.splits, st);
+    }
     const long long nw = (long long)cout * 9 * cin;
     WgradArgs a;
     a.x = x.p;
