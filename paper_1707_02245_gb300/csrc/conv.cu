@@ -993,6 +993,19 @@ __global__ void __launch_bounds__(256) k_colsum_part(const bf16* __restrict__ dz
     }
 }
 
+// out[c] = sum_g part[g][c], one warp per column: lane l adds rows l, l + 32, ... in order,
+// then a fixed butterfly over the lanes
+__global__ void __launch_bounds__(256) k_sum_cols(const float* __restrict__ part, int rows, int cols,
+                                                  float* __restrict__ out) {
+    const int c = blockIdx.x * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (c >= cols) return;
+    float s = 0.f;
+    for (int g = lane; g < rows; g += 32) s += __ldg(part + (size_t)g * cols + c);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) out[c] = s;
+}
+
 // out[i] = sum_z part[z][i]
 __global__ void k_sum_splits(const float* __restrict__ part, int splits, long long n, float* __restrict__ out) {
     const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1126,7 +1139,7 @@ int launch_wgrad(const WgradArgs& a, int splits, cudaStream_t st) {
     return PAT_OK;
 }
 
-constexpr int COLSUM_BLOCKS = 1024;   // pixel ranges of the bias-gradient column sums
+constexpr int COLSUM_BLOCKS = 512;   // pixel ranges of the bias-gradient column sums
 
 template <int BN>
 int launch_wgrad_tc(const View& x, const View& dz, int B, int H, int W, int cin, int cout, float* dw, float* db,
@@ -1185,8 +1198,8 @@ int launch_wgrad_tc(const View& x, const View& dz, int B, int H, int W, int cin,
         float* pb = part + (size_t)a.splits * nw;
         k_colsum_part<<<G, 256, 0, st>>>(dz.p, dz.ps, P, cout, pb);
         PAT_LAUNCH_CHECK("k_colsum_part");
-        k_sum_splits<<<(unsigned)((cout + 255) / 256), 256, 0, st>>>(pb, G, cout, db);
-        PAT_LAUNCH_CHECK("k_sum_splits");
+        k_sum_cols<<<(unsigned)((cout + 7) / 8), 256, 0, st>>>(pb, G, cout, db);
+        PAT_LAUNCH_CHECK("k_sum_cols");
     }
     return PAT_OK;
 }
