@@ -709,6 +709,53 @@ def run_preprocess(P, S, np, torch, device, stream, geo, w, flush):
     return {"detectors": D, "samples": T, "us_per_call": us, "gb_per_s": 3 * D * T * 4 / (us * 1e-6) / 1e9}
 
 
+def time_unet_step(P, WS, torch, net, x8, t8, cw, n, stream, steps=10):
+    """Tensor-core throughput of the U-Net training step (batch 8, n x n): CUDA events
+    around `steps` steps after 3 untimed ones."""
+    loss = torch.zeros(1, device=x8.device)
+    for _ in range(3):
+        P.pat_unet_train_step(net.handle, x8, t8, cw, 8, n, n, 1e-6, loss, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        P.pat_unet_train_step(net.handle, x8, t8, cw, 8, n, n, 1e-6, loss, stream)
+    e1.record(stream)
+    e1.synchronize()
+    step_ms = e0.elapsed_time(e1) / steps
+    fwd_fl, step_fl = WS.unet_flops(8, n, n)
+    peaks = load_peaks()
+    tf = step_fl / (step_ms * 1e-3) / 1e12
+    return {"step_ms": step_ms,
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                         "frac": tf / peaks["bf16_tflops"], "flop_per_step": step_fl,
+                         "kernels": "k_conv_fwd_tc / k_conv_wgrad_tc (tcgen05, TMEM accumulators, TMA) for the "
+                                    "layers with >= 32 channels on both sides (forward: >= 64 on one side), "
+                                    "k_conv_fwd / k_conv_wgrad (mma.sync) for the 8-channel input and output layers "
+                                    "and the 32 -> 32 forward",
+                         "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)"}}
+
+
+def run_unet_step_only(args):
+    """--unet-step: only the U-Net training-step timing on random bf16 inputs (base 32
+    channels, 4 levels, batch 8, 256 x 256), printed as one JSON line."""
+    import torch
+    import paper_1707_02245_gb300 as P
+    from paper_1707_02245_gb300 import build, warmstart as WS
+    build.build()
+    P.load()
+    device = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(device)
+    n = 256
+    g = torch.Generator(device="cpu").manual_seed(0)
+    x8 = torch.randn(8, n, n, 8, generator=g).to(torch.bfloat16).to(device)
+    t8 = torch.randn(8, n, n, 8, generator=g).to(device)
+    net = WS.UNet(base_ch=32, levels=4, seed=1)
+    out = time_unet_step(P, WS, torch, net, x8, t8, [1.0] * 8, n, stream, steps=args.unet_step)
+    out["nn_wait_timeouts"] = P.pat_nn_wait_timeouts()
+    print(json.dumps({"unet_step": out}))
+    return 0
+
+
 def run_warm_start(P, S, np, torch, device, stream, args):
     """The learned warm start on TGV^2 256^2 vessel problems with 128 detectors: training
     pairs from PDHG (the tuned balance s, rel gap 1e-5, at most --warm-label-iters), U-Net
@@ -739,25 +786,8 @@ def run_warm_start(P, S, np, torch, device, stream, args):
     cw = list((1.0 / np.maximum(e, 1e-12) / len(e)).astype(float))
     net = WS.UNet(base_ch=32, levels=4, seed=1)
     lg, tt = WS.train(torch, net, F, T, args.warm_steps, 8, 1e-3, cw, stream, log_every=max(1, args.warm_steps // 4))
-    # tensor-core throughput of the training step (timed separately, 10 steps)
-    x8, t8 = F[:8].contiguous(), T[:8].contiguous()
-    loss = torch.zeros(1, device=device)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(10):
-        P.pat_unet_train_step(net.handle, x8, t8, cw, 8, n, n, 1e-6, loss, stream)
-    e1.record(stream)
-    e1.synchronize()
-    step_ms = e0.elapsed_time(e1) / 10
-    fwd_fl, step_fl = WS.unet_flops(8, n, n)
-    peaks = load_peaks()
-    tf = step_fl / (step_ms * 1e-3) / 1e12
-    out["training"] = {"steps": args.warm_steps, "batch": 8, "seconds": tt, "loss_log": lg, "params": net.num_params,
-                       "step_ms": step_ms,
-                       "roofline": {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                                    "frac": tf / peaks["bf16_tflops"], "flop_per_step": step_fl,
-                                    "kernels": "k_conv_fwd / k_conv_wgrad (bf16 mma.sync, FP32 accumulate)",
-                                    "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)"}}
+    out["training"] = {"steps": args.warm_steps, "batch": 8, "seconds": tt, "loss_log": lg, "params": net.num_params}
+    out["training"].update(time_unet_step(P, WS, torch, net, F[:8].contiguous(), T[:8].contiguous(), cw, n, stream))
     prms = [P.make_params(reg=1, alpha=w["alpha"], beta=w["beta"]) for w in wv]
     # cold
     ci, us_c, ct = WS.solve(torch, geo, fv, wv, device, stream, tol=1e-4, max_iters=30000, step_ratio=sr)
@@ -821,6 +851,8 @@ def main(argv=None) -> int:
     ap.add_argument("--mixed-max-iters", type=int, default=5000)
     ap.add_argument("--probe-iters", type=int, default=300, help="iterations of each step-ratio probe")
     ap.add_argument("--warm", type=int, default=1, help="run the learned warm-start leg (0: skip)")
+    ap.add_argument("--unet-step", type=int, default=0,
+                    help="only time this many U-Net training steps (batch 8, 256^2) and print them (0: full run)")
     ap.add_argument("--warm-train", type=int, default=128)
     ap.add_argument("--warm-val", type=int, default=16)
     ap.add_argument("--warm-steps", type=int, default=2000)
@@ -837,6 +869,8 @@ def main(argv=None) -> int:
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.unet_step:
+        return run_unet_step_only(args)
     return run_gb300(args)
 
 
