@@ -792,6 +792,7 @@ def run_warm_start(P, S, np, torch, device, stream, args):
     # cold
     ci, us_c, ct = WS.solve(torch, geo, fv, wv, device, stream, tol=1e-4, max_iters=30000, step_ratio=sr)
     # warm: features (already computed in Fv) are part of the warm path, so time them again
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     feats = torch.empty_like(Fv)
     for k in range(len(wv)):
