@@ -68,6 +68,13 @@ CONV_CASES = [
     (1, 1, 1, 8, 8, False),
     (2, 5, 130, 16, 64, True),
     (1, 9, 7, 384, 128, False),
+    # shapes that take the tensor-memory kernels: every N tile width (32, 64, 128, 256 for
+    # the weight gradient), several tiles along x (W > 128) and ragged tiles
+    (2, 16, 20, 64, 32, True),
+    (1, 12, 10, 32, 64, False),
+    (1, 12, 10, 64, 256, True),
+    (1, 3, 200, 64, 64, False),
+    (2, 13, 17, 64, 64, True),
 ]
 
 
