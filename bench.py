@@ -728,10 +728,10 @@ def time_unet_step(P, WS, torch, net, x8, t8, cw, n, stream, steps=10):
     return {"step_ms": step_ms,
             "roofline": {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
                          "frac": tf / peaks["bf16_tflops"], "flop_per_step": step_fl,
-                         "kernels": "k_conv_fwd_tc / k_conv_wgrad_tc (tcgen05, TMEM accumulators, TMA) for the "
-                                    "layers with >= 32 channels on both sides (forward: >= 64 on one side), "
-                                    "k_conv_fwd / k_conv_wgrad (mma.sync) for the 8-channel input and output layers "
-                                    "and the 32 -> 32 forward",
+                         "kernels": "k_conv_wgrad_tc (tcgen05, TMEM accumulators, TMA) for every weight gradient; "
+                                    "k_conv_fwd_tc for the forward and data-gradient layers with 32-channel multiples "
+                                    "and >= 64 channels on one side; k_conv_fwd (mma.sync) for the 8-channel input "
+                                    "and output layers and the 32 -> 32 forward",
                          "peak_source": "measured bf16 burst (MEASURED_PEAKS.json)"}}
 
 

@@ -9,11 +9,11 @@
 //    warp-specialised and persistent (described at the kernel);
 //  - k_conv_fwd (the narrow layers): a three-stage cp.async ring feeding mma.sync
 //    m16n8k16 through ldmatrix; out-of-image taps are zero-filled by the copy itself.
-// Weight gradient: M = output channels, N = (tap, input channel), K = pixels.  Both
-// operands are stored pixel-major in memory and transposed by ldmatrix.trans (mma.sync).
-// The pixel range is split over the grid's z dimension.  Each split writes its own
-// partial tile, and a second kernel sums the splits in a fixed order, so the result is
-// deterministic.
+// Weight gradient: k_conv_wgrad_tc (tcgen05; every layer with at most 256 output
+// channels, described at the kernel), else k_conv_wgrad (mma.sync: M = output channels,
+// N = (tap, input channel), K = pixels, the pixel-major operands transposed by
+// ldmatrix.trans).  Both split the pixels; each split writes its own partial tile, and a
+// second kernel sums the splits in a fixed order, so the result is deterministic.
 #include <cuda.h>
 
 #include <algorithm>
@@ -732,9 +732,10 @@ __global__ void __launch_bounds__(THREADS) k_conv_wgrad(const WgradArgs a) {
 // (a wx x wy rectangle of one image, wx wy = PT).  Both operands are stored pixel-major,
 // so both are MN-major for the MMA: TMA writes the box {CB channels, wx, wy, 1} of x at
 // the tap's offset (zero fill outside the image) and the box {CBO channels, wx, wy, 1} of
-// dz as rows of CB (CBO) channels per pixel, swizzled by the row size (64 or 128 bytes).
-// An MN-major swizzle atom is 8 pixel rows; LBO steps from one channel box to the next,
-// SBO from one 8-pixel group to the next.  A work unit is (M tile, split of the pixel
+// dz as rows of CB (CBO) channels per pixel, swizzled by the row size (32, 64 or 128
+// bytes; 16-byte rows without swizzle).  An MN-major swizzle atom is 8 pixel rows; LBO
+// steps from one channel box to the next, SBO from one 8-pixel group to the next (without
+// swizzle the two swap).  A work unit is (M tile, split of the pixel
 // tiles); the unit's partial D goes to part[split][o][k], summed over splits in a fixed
 // order by k_sum_splits.
 // ---------------------------------------------------------------------------------------
@@ -748,7 +749,7 @@ struct WgTcArgs {
     int wx_log2, wy;        // pixel tile: 2^wx_log2 x wy
     int ptiles_x, ptiles_y, n_ptiles;
     int m_tiles, splits, per, total;
-    int cbx, cbo;           // channels per box of x and of dz: 32 or 64
+    int cbx, cbo;           // channels per box of x and of dz: 8, 16, 32 or 64
     float* part;            // [splits][cout][9 cin]
 };
 
@@ -878,9 +879,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
             // ---- MMA issuer ----
             // MN-major: LBO = the next channel box (next swizzle atom along M or N), SBO = the
             // next 8 pixel rows; a K step of 16 pixels advances two 8-row groups
-            const uint32_t sbo_a = 8 * a.cbx * 2, sbo_b = 8 * a.cbo * 2;
-            const uint64_t da = tc_desc(0, C::PT * a.cbx * 2, sbo_a, a.cbx == 64 ? 2u : 4u);
-            const uint64_t db = tc_desc(0, C::PT * a.cbo * 2, sbo_b, a.cbo == 64 ? 2u : 4u);
+            // Boxes of 8 channels (16-byte rows) use the MN-major layout without swizzle: an
+            // 8 x 8 core matrix is 8 pixel rows of 16 bytes, the next 8 pixels 128 bytes on
+            // (LBO), the next 8 channels one box on (SBO).
+            auto desc = [&](int cb, uint32_t& kstep) -> uint64_t {
+                if (cb == 8) {
+                    kstep = 256;
+                    return tc_desc(0, 128, C::PT * 16, 0u);
+                }
+                const uint32_t sbo = 8 * cb * 2;
+                kstep = 2 * sbo;
+                return tc_desc(0, C::PT * cb * 2, sbo, cb == 64 ? 2u : cb == 32 ? 4u : 6u);
+            };
+            uint32_t ks_a, ks_b;
+            const uint64_t da = desc(a.cbx, ks_a), db = desc(a.cbo, ks_b);
             int it = 0, tc = 0;
             for (int u = blockIdx.x; u < a.total && !*abort_flag; u += gridDim.x, ++tc) {
                 int mt, pb, pe;
@@ -904,7 +916,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
                     const uint32_t As = sbase + s * C::STAGE, Bs = As + C::A_BYTES;
 #pragma unroll
                     for (int k16 = 0; k16 < C::PT / 16; ++k16)
-                        tc_mma(d, da + ((As + k16 * 2 * sbo_a) >> 4), db + ((Bs + k16 * 2 * sbo_b) >> 4), IDESC,
+                        tc_mma(d, da + ((As + k16 * ks_a) >> 4), db + ((Bs + k16 * ks_b) >> 4), IDESC,
                                (pt != pb || k16 != 0) ? 1u : 0u);
                     tc_commit(empty(s));
                 }
@@ -1168,8 +1180,9 @@ int launch_wgrad_tc(const View& x, const View& dz, int B, int H, int W, int cin,
     a.per = (a.n_ptiles + splits - 1) / splits;
     a.splits = (a.n_ptiles + a.per - 1) / a.per;
     a.total = a.m_tiles * a.splits;
-    a.cbx = cin % 64 == 0 ? 64 : 32;
-    a.cbo = cout % 64 == 0 ? 64 : 32;
+    auto box_ch = [](int c) { return c % 64 == 0 ? 64 : c % 32 == 0 ? 32 : c % 16 == 0 ? 16 : 8; };
+    a.cbx = box_ch(cin);
+    a.cbo = box_ch(cout);
     a.part = part;
     CUtensorMap mx, md;
     const cuuint32_t es[4] = {1, 1, 1, 1};
@@ -1179,7 +1192,11 @@ int launch_wgrad_tc(const View& x, const View& dz, int B, int H, int W, int cin,
         const cuuint64_t strides[3] = {ps, ps * W, ps * W * H};
         const cuuint32_t box[4] = {(cuuint32_t)cb, (cuuint32_t)(1 << lg), (cuuint32_t)a.wy, 1};
         return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void*)v.p, dims, strides, box, es,
-                   CU_TENSOR_MAP_INTERLEAVE_NONE, cb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   cb == 64   ? CU_TENSOR_MAP_SWIZZLE_128B
+                   : cb == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                   : cb == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
+                              : CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     };
     if (map4(&mx, x, cin, a.cbx) != CUDA_SUCCESS) return fail(PAT_ERR_CUDA, "conv3x3_wgrad: activation tensor map");
@@ -1263,8 +1280,8 @@ size_t wgrad_partial_floats(int B, int H, int W, int cin, int cout) {
 int conv3x3_wgrad(const View& x, const View& dz, int B, int H, int W, int cin, int cout, float* dw, float* db,
                   float* part, cudaStream_t st) {
     const SplitPlan sp = plan_splits(B, H, W, cin, cout);
-    // the tensor-memory kernel takes channel counts that fill 64- or 128-byte TMA rows
-    if (cin % 32 == 0 && cout % 32 == 0 && cout <= 256 && B > 0 && H > 0 && W > 0) {
+    // the tensor-memory kernel (every layer with at most 256 output channels)
+    if (cout <= 256 && B > 0 && H > 0 && W > 0) {
         if (cout <= 32) return launch_wgrad_tc<32>(x, dz, B, H, W, cin, cout, dw, db, part, sp.splits, st);
         if (cout <= 64) return launch_wgrad_tc<64>(x, dz, B, H, W, cin, cout, dw, db, part, sp.splits, st);
         if (cout <= 128) return launch_wgrad_tc<128>(x, dz, B, H, W, cin, cout, dw, db, part, sp.splits, st);
