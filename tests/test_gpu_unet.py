@@ -165,6 +165,30 @@ def test_unet_forward_backward_match_oracle(levels):
     net.close()
 
 
+def test_benchmark_width_unet_matches_oracle_within_rounding_noise():
+    """The benchmark's network (C0 = 32, 4 levels: channels up to 384, the wide layers on
+    the tensor-memory kernels) against the oracle's bf16 emulation.  Rounding a stored
+    activation to bf16 turns an FP32-level difference in a convolution sum into a jump of
+    one bf16 ulp, and such flips propagate: perturbing every convolution output of the
+    oracle itself by a relative 3e-6 (the order of FP32 accumulation error over 9 x 384
+    terms) moves its output by 3-5e-3 and its gradients by 5-11e-2 at C0 = 8, 16 and 32.
+    The bounds below sit above that noise; a wiring error gives differences of order 1."""
+    B, H, W = 2, 16, 24
+    net, cfg, xt, x = _net_and_inputs(15, B, H, W, levels=4, base_ch=32)
+    y = torch.empty(B, H, W, cfg["out_ch"], device=DEV)
+    net.forward(xt, B, H, W, y)
+    prm = _oracle_params(net, cfg)
+    ref, cache = U.unet_forward(x, prm, 4, bf16=True)
+    assert rel_l2(host(y), ref) < 1e-2
+    dy = np.random.default_rng(5).standard_normal(ref.shape)
+    g = torch.empty(net.num_params, device=DEV)
+    P.pat_unet_backward(net.handle, dev(dy), g)
+    rg = U.params_flatten(U.unet_backward(dy.astype(np.float32).astype(np.float64), cache, 4, bf16=True),
+                          cfg["in_ch"], cfg["out_ch"], cfg["base_ch"], 4)
+    assert rel_l2(host(g), rg) < 0.15
+    net.close()
+
+
 def test_adam_first_step_and_training_reduces_loss():
     B, H, W = 2, 16, 16
     net, cfg, xt, x = _net_and_inputs(21, B, H, W)
