@@ -51,10 +51,11 @@ __device__ __forceinline__ AxisF axis_filters(const CwtBank& b, int tree, bool l
 // M x M from in (plane t at in + t * in_ps, stride si; in_ps = 0 reads one image for all).
 __global__ void k_cwt_analysis(const float* __restrict__ in, long long in_ps, int si, float* __restrict__ out,
                                long long ps, int so, int M, int level1, const CwtBank bank, const int* stop,
-                               long long pb) {
+                               long long pb, float* __restrict__ ll, long long ll_ps) {
     const long long po = pb * (blockIdx.z >> 2);
     in = at_bytes(in, po);
     out = at_bytes(out, po);
+    ll = ll ? at_bytes(ll, po) : ll;
     stop = stop ? at_bytes(stop, po) : stop;
     if (stop && *(volatile const int*)stop) return;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, t = blockIdx.z & 3;
@@ -74,12 +75,15 @@ __global__ void k_cwt_analysis(const float* __restrict__ in, long long in_ps, in
         acc = fmaf(fyv[a], r, acc);
     }
     out[ps * t + (size_t)y * so + x] = acc;
+    if (ll && !hx && !hy) ll[ll_ps * t + (size_t)y * h2 + x] = acc;   // the next level's input (stride M / 2)
 }
 
 // Transpose of one analysis level of tree t applied to the coefficient block (in plane t,
 // stride si, quadrants of size M/2): value at (y, x) of the M x M output.
-__device__ __forceinline__ float cwt_synth_at(const float* __restrict__ c, int si, int M, int x, int y,
-                                              const AxisF& fx, const AxisF& fy) {
+// The LL quadrant comes from ll (stride sl) and the three detail quadrants from c (stride
+// si); both are c itself for the coarsest level.
+__device__ __forceinline__ float cwt_synth_at(const float* __restrict__ ll, int sl, const float* __restrict__ c,
+                                              int si, int M, int x, int y, const AxisF& fx, const AxisF& fy) {
     const int h2 = M >> 1;
     float acc = 0.f;
     // taps a with y = 2 ky + a + off (mod M): a has the parity of y - off
@@ -90,7 +94,7 @@ __device__ __forceinline__ float cwt_synth_at(const float* __restrict__ c, int s
             const int kx = imod(x - b - fx.off, M) >> 1;
             const float* r0 = c + (size_t)ky * si;
             const float* r1 = c + (size_t)(ky + h2) * si;
-            lo = fmaf(fx.h[b], __ldg(r0 + kx), fmaf(fx.g[b], __ldg(r0 + kx + h2), lo));
+            lo = fmaf(fx.h[b], __ldg(ll + (size_t)ky * sl + kx), fmaf(fx.g[b], __ldg(r0 + kx + h2), lo));
             hi = fmaf(fx.h[b], __ldg(r1 + kx), fmaf(fx.g[b], __ldg(r1 + kx + h2), hi));
         }
         acc = fmaf(fy.h[a], lo, fmaf(fy.g[a], hi, acc));
@@ -98,11 +102,14 @@ __device__ __forceinline__ float cwt_synth_at(const float* __restrict__ c, int s
     return acc;
 }
 
-// Levels >= 2: out plane t (M x M, stride so, plane stride ops) from in plane t (stride si,
-// plane stride ips).
-__global__ void k_cwt_synthesis(const float* __restrict__ in, long long ips, int si, float* __restrict__ out,
-                                long long ops, int so, int M, const CwtBank bank, const int* stop, long long pb) {
+// Levels >= 2: out plane t (M x M, stride so, plane stride ops) from the detail quadrants
+// of in plane t (stride si, plane stride ips) and the LL quadrant in ll (stride sl, plane
+// stride lps: the level above's output, or in itself at the coarsest level).
+__global__ void k_cwt_synthesis(const float* __restrict__ ll, long long lps, int sl, const float* __restrict__ in,
+                                long long ips, int si, float* __restrict__ out, long long ops, int so, int M,
+                                const CwtBank bank, const int* stop, long long pb) {
     const long long po = pb * (blockIdx.z >> 2);
+    ll = at_bytes(ll, po);
     in = at_bytes(in, po);
     out = at_bytes(out, po);
     stop = stop ? at_bytes(stop, po) : stop;
@@ -110,13 +117,16 @@ __global__ void k_cwt_synthesis(const float* __restrict__ in, long long ips, int
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, t = blockIdx.z & 3;
     if (x >= M || y >= M) return;
     const AxisF fx = axis_filters(bank, t >> 1, false), fy = axis_filters(bank, t & 1, false);
-    out[ops * t + (size_t)y * so + x] = cwt_synth_at(in + ips * t, si, M, x, y, fx, fy);
+    out[ops * t + (size_t)y * so + x] = cwt_synth_at(ll + lps * t, sl, in + ips * t, si, M, x, y, fx, fy);
 }
 
-// Level 1 and the sum of the four trees: out (N x N) = sum_t T_t^T level 1 of plane t.
-__global__ void k_cwt_synthesis_sum(const float* __restrict__ in, long long ips, int si, float* __restrict__ out,
-                                    int N, const CwtBank bank, const int* stop, long long pb) {
+// Level 1 and the sum of the four trees: out (N x N) = sum_t T_t^T level 1 of plane t (LL
+// quadrants from ll, stride sl, plane stride lps).
+__global__ void k_cwt_synthesis_sum(const float* __restrict__ ll, long long lps, int sl, const float* __restrict__ in,
+                                    long long ips, int si, float* __restrict__ out, int N, const CwtBank bank,
+                                    const int* stop, long long pb) {
     const long long po = pb * blockIdx.z;
+    ll = at_bytes(ll, po);
     in = at_bytes(in, po);
     out = at_bytes(out, po);
     stop = stop ? at_bytes(stop, po) : stop;
@@ -126,21 +136,11 @@ __global__ void k_cwt_synthesis_sum(const float* __restrict__ in, long long ips,
     float acc = 0.f;
 #pragma unroll
     for (int t = 0; t < 4; ++t)
-        acc += cwt_synth_at(in + ips * t, si, N, x, y, axis_filters(bank, t >> 1, true), axis_filters(bank, t & 1, true));
+        acc += cwt_synth_at(ll + lps * t, sl, in + ips * t, si, N, x, y, axis_filters(bank, t >> 1, true),
+                            axis_filters(bank, t & 1, true));
     out[(size_t)y * N + x] = acc;
 }
 
-// out planes (M x M blocks, stride so) = in planes' top-left M x M blocks (stride si)
-__global__ void k_cwt_copy(const float* __restrict__ in, long long ips, int si, float* __restrict__ out, long long ops,
-                           int so, int M, const int* stop, long long pb) {
-    const long long po = pb * (blockIdx.z >> 2);
-    in = at_bytes(in, po);
-    out = at_bytes(out, po);
-    stop = stop ? at_bytes(stop, po) : stop;
-    if (stop && *(volatile const int*)stop) return;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y, t = blockIdx.z & 3;
-    if (x < M && y < M) out[ops * t + (size_t)y * so + x] = in[ips * t + (size_t)y * si + x];
-}
 
 // The four W-coefficients at one position from the T planes (each times 1/2).
 __device__ __forceinline__ void combine_at(const float* __restrict__ T, long long NN, long long i, bool ll, float c[4]) {
@@ -424,37 +424,51 @@ void cwt_abs_sums(int n, int levels, const std::vector<double>& h1, const std::v
     }
 }
 
-// out (4 T planes of N x N) = T in.  scratch: 4 (N/2)^2 floats.
+// The LL block a level passes to the next lives in scratch, so no level overwrites its own
+// input: level l >= 2 reads buffer X_l and writes X_{l+1}, X_l = scratch (4 (N/2)^2 floats)
+// for even l and scratch + N^2 (4 (N/4)^2 floats) for odd l.  scratch: 5 N^2 / 4 floats.
+static float* cwt_ll_buffer(float* scratch, int N, int l) { return (l & 1) ? scratch + (size_t)N * N : scratch; }
+
+// out (4 T planes of N x N) = T in.
 int launch_cwt_analysis(const float* in, int N, int levels, const CwtBank& bank, float* out, float* scratch,
                         const int* stop, cudaStream_t st, int B, long long pb) {
     const dim3 blk(32, 8);
     const long long NN = (long long)N * N;
-    k_cwt_analysis<<<grid_of(N, 4 * B), blk, 0, st>>>(in, 0, N, out, NN, N, N, 1, bank, stop, pb);
+    k_cwt_analysis<<<grid_of(N, 4 * B), blk, 0, st>>>(in, 0, N, out, NN, N, N, 1, bank, stop, pb,
+                                                      levels >= 2 ? cwt_ll_buffer(scratch, N, 2) : nullptr,
+                                                      (long long)(N / 2) * (N / 2));
     PAT_LAUNCH_CHECK("k_cwt_analysis");
     for (int l = 2, M = N / 2; l <= levels; ++l, M /= 2) {
         const long long mm = (long long)M * M;
-        k_cwt_copy<<<grid_of(M, 4 * B), blk, 0, st>>>(out, NN, N, scratch, mm, M, M, stop, pb);
-        PAT_LAUNCH_CHECK("k_cwt_copy");
-        k_cwt_analysis<<<grid_of(M, 4 * B), blk, 0, st>>>(scratch, mm, M, out, NN, N, M, 0, bank, stop, pb);
+        k_cwt_analysis<<<grid_of(M, 4 * B), blk, 0, st>>>(cwt_ll_buffer(scratch, N, l), mm, M, out, NN, N, M, 0, bank,
+                                                          stop, pb,
+                                                          l < levels ? cwt_ll_buffer(scratch, N, l + 1) : nullptr,
+                                                          (long long)(M / 2) * (M / 2));
         PAT_LAUNCH_CHECK("k_cwt_analysis");
     }
     return PAT_OK;
 }
 
-// out (N x N) = sum_t T_t^T of the T planes in.  in is overwritten; scratch: 4 (N/2)^2.
+// out (N x N) = sum_t T_t^T of the T planes in (not modified).  Level l >= 2 writes its
+// M x M block (M = N >> (l - 1)) into X_l, which the next finer level reads as its LL.
 int launch_cwt_synthesis(float* in, int N, int levels, const CwtBank& bank, float* out, float* scratch,
                          const int* stop, cudaStream_t st, int B, long long pb) {
     const dim3 blk(32, 8);
     const long long NN = (long long)N * N;
+    const float* ll = in;   // the coarsest level's LL is in the planes themselves
+    long long lps = NN;
+    int sl = N;
     for (int l = levels; l >= 2; --l) {
         const int M = N >> (l - 1);
         const long long mm = (long long)M * M;
-        k_cwt_synthesis<<<grid_of(M, 4 * B), blk, 0, st>>>(in, NN, N, scratch, mm, M, M, bank, stop, pb);
+        float* dst = cwt_ll_buffer(scratch, N, l);
+        k_cwt_synthesis<<<grid_of(M, 4 * B), blk, 0, st>>>(ll, lps, sl, in, NN, N, dst, mm, M, M, bank, stop, pb);
         PAT_LAUNCH_CHECK("k_cwt_synthesis");
-        k_cwt_copy<<<grid_of(M, 4 * B), blk, 0, st>>>(scratch, mm, M, in, NN, N, M, stop, pb);
-        PAT_LAUNCH_CHECK("k_cwt_copy");
+        ll = dst;
+        lps = mm;
+        sl = M;
     }
-    k_cwt_synthesis_sum<<<grid_of(N, B), blk, 0, st>>>(in, NN, N, out, N, bank, stop, pb);
+    k_cwt_synthesis_sum<<<grid_of(N, B), blk, 0, st>>>(ll, lps, sl, in, NN, N, out, N, bank, stop, pb);
     PAT_LAUNCH_CHECK("k_cwt_synthesis_sum");
     return PAT_OK;
 }
@@ -506,8 +520,8 @@ extern "C" int pat_dtcwt_transform(int n, int levels, const double* h1_host, int
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
     const long long NN = (long long)n * n;
-    float* buf = nullptr;   // 4 T planes + scratch
-    PAT_CUDA(cudaMallocAsync(&buf, (size_t)(4 * NN + NN) * sizeof(float), st));
+    float* buf = nullptr;   // 4 T planes + scratch (5 N^2 / 4)
+    PAT_CUDA(cudaMallocAsync(&buf, (size_t)(4 * NN + NN + NN / 4) * sizeof(float), st));
     float* T = buf;
     float* scratch = buf + 4 * NN;
     if (inverse) {

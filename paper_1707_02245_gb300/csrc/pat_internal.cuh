@@ -367,6 +367,7 @@ int cwt_bank(const double* h1, int l1, const double* hq, int lq, CwtBank& bank, 
              std::vector<double>* hq_out);
 void cwt_abs_sums(int n, int levels, const std::vector<double>& h1, const std::vector<double>& hq,
                   std::vector<double>& rows, std::vector<double>& cols);
+// the DT-CWT's T planes (analysis) and its transpose; scratch: 5 N^2 / 4 floats per problem
 int launch_cwt_analysis(const float* in, int N, int levels, const CwtBank& bank, float* out, float* scratch,
                         const int* stop, cudaStream_t st, int B, long long ps);
 int launch_cwt_synthesis(float* in, int N, int levels, const CwtBank& bank, float* out, float* scratch,

@@ -1531,8 +1531,9 @@ static int run_wavelet(int B, const pat_geometry* const* g, const float* const* 
     // tree form of r); SCAL holds {alpha, theta}, TKM the geometry's K^T tile bounds
     enum { U, UOLD, UBAR, Q, QW, KT, R, WB, WTR, SCR, SCR2, WU, TAU, SIGR, SIGQ, DPART, PPART, INFO, SCRT, SCAL, TKM,
            NBUF };
-    const size_t nn4 = (size_t)NN * 4, nr4 = (size_t)NR * 4;
-    const size_t sz[NBUF] = {nn4, nn4, nn4, (size_t)S * 4, (size_t)S * 4, (size_t)NN * 8, nr4, nr4, nn4, nn4, nn4,
+    // SCR, SCR2: transform scratch (DT-CWT: the LL blocks passed between levels, 5 N^2 / 4)
+    const size_t nn4 = (size_t)NN * 4, nr4 = (size_t)NR * 4, scr4 = cwt ? nn4 + nn4 / 4 : nn4;
+    const size_t sz[NBUF] = {nn4, nn4, nn4, (size_t)S * 4, (size_t)S * 4, (size_t)NN * 8, nr4, nr4, nn4, scr4, scr4,
                              nr4, nn4, nr4, (size_t)S * 4, (size_t)n_data * GAP_DATA_TERMS * 8,
                              (size_t)n_pix * GAP_PIX_TERMS * 8, sizeof(InfoDev), cwt ? nr4 : 16, 2 * sizeof(float),
                              (size_t)g[0]->adj_tiles * sizeof(float)};

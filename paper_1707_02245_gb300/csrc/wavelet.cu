@@ -28,11 +28,13 @@ __device__ __forceinline__ float wav_g(int n) { return (n & 1 ? -1.f : 1.f) * wa
 __device__ __forceinline__ float wav_f(bool high, int n) { return high ? wav_g(n) : wav_h(n); }
 
 // out (M x M block, stride so) = one analysis level of in (M x M block, stride si)
+// and, if ll is not NULL, its LL quadrant again into ll (stride M / 2): the next level's input
 __global__ void k_wav_analysis(const float* __restrict__ in, int si, float* __restrict__ out, int so, int M,
-                               const int* stop, long long ps) {
+                               const int* stop, long long ps, float* __restrict__ ll) {
     const long long po = ps * blockIdx.z;   // problem blockIdx.z of a batch: its buffers lie po bytes on
     in = at_bytes(in, po);
     out = at_bytes(out, po);
+    ll = ll ? at_bytes(ll, po) : ll;
     stop = stop ? at_bytes(stop, po) : stop;
     if (stop && *(volatile const int*)stop) return;
     const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
@@ -50,14 +52,17 @@ __global__ void k_wav_analysis(const float* __restrict__ in, int si, float* __re
         acc = fmaf(wav_f(hy, a), row, acc);
     }
     out[(size_t)y * so + x] = acc;
+    if (ll && !hx && !hy) ll[(size_t)y * h2 + x] = acc;
 }
 
 // out (M x M, stride so) = the transpose of one analysis level applied to the coefficient
-// block in (M x M, stride si): out[y][x] = sum over the four quadrants and the taps that
-// reach (y, x) of f_y[y - 2k] f_x[x - 2m] c[k][m] (indices mod M).
-__global__ void k_wav_synthesis(const float* __restrict__ in, int si, float* __restrict__ out, int so, int M,
-                                const int* stop, long long ps) {
+// block whose LL quadrant is in ll (stride sl) and whose detail quadrants are in in (stride
+// si): out[y][x] = sum over the four quadrants and the taps that reach (y, x) of
+// f_y[y - 2k] f_x[x - 2m] c[k][m] (indices mod M).
+__global__ void k_wav_synthesis(const float* __restrict__ ll, int sl, const float* __restrict__ in, int si,
+                                float* __restrict__ out, int so, int M, const int* stop, long long ps) {
     const long long po = ps * blockIdx.z;
+    ll = at_bytes(ll, po);
     in = at_bytes(in, po);
     out = at_bytes(out, po);
     stop = stop ? at_bytes(stop, po) : stop;
@@ -74,26 +79,14 @@ __global__ void k_wav_synthesis(const float* __restrict__ in, int si, float* __r
         for (int tb = 0; tb < 2; ++tb) {
             const int b = (x & 1) + 2 * tb;
             const int kx = ((x - b + M) % M) >> 1;
-            const float ll = __ldg(in + (size_t)ky * si + kx), hl = __ldg(in + (size_t)ky * si + kx + h2);
+            const float cll = __ldg(ll + (size_t)ky * sl + kx), hl = __ldg(in + (size_t)ky * si + kx + h2);
             const float lh = __ldg(in + (size_t)(ky + h2) * si + kx), hh = __ldg(in + (size_t)(ky + h2) * si + kx + h2);
             const float hya = wav_h(a), gya = wav_g(a), hxb = wav_h(b), gxb = wav_g(b);
-            acc += hya * (hxb * ll + gxb * hl) + gya * (hxb * lh + gxb * hh);
+            acc += hya * (hxb * cll + gxb * hl) + gya * (hxb * lh + gxb * hh);
         }
     }
     out[(size_t)y * so + x] = acc;
 }
-
-__global__ void k_copy_block(const float* __restrict__ in, int si, float* __restrict__ out, int so, int M,
-                             const int* stop, long long ps) {
-    const long long po = ps * blockIdx.z;
-    in = at_bytes(in, po);
-    out = at_bytes(out, po);
-    stop = stop ? at_bytes(stop, po) : stop;
-    if (stop && *(volatile const int*)stop) return;
-    const int x = blockIdx.x * blockDim.x + threadIdx.x, y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x < M && y < M) out[(size_t)y * so + x] = in[(size_t)y * si + x];
-}
-
 
 // r <- clip(r + sigma_r / s * W ubar, -alpha, alpha): the prox of F2* for the scalar
 // coefficients of the wavelet model (Sec. 3.2)
@@ -265,33 +258,41 @@ void wav_abs_sums(int n, int levels, std::vector<double>& rows, std::vector<doub
 // per problem) run in one grid: the problem index is the grid's last dimension.
 static dim3 block_grid(int M, int B) { return dim3(ceil_div(M, 32), ceil_div(M, 8), B); }
 
+// The LL block a level passes to the next lives in scratch, so no level overwrites its own
+// input: level l >= 2 reads X_l = scratch for even l and scratch + (N/2)^2 for odd l.
+static float* wav_ll_buffer(float* scratch, int N, int l) {
+    return (l & 1) ? scratch + (size_t)(N / 2) * (N / 2) : scratch;
+}
+
 // out = W in.  scratch: N*N floats.
 int launch_wav_analysis(const float* in, int N, int levels, float* out, float* scratch, const int* stop,
                         cudaStream_t st, int B, long long ps) {
     const dim3 blk(32, 8);
-    k_wav_analysis<<<block_grid(N, B), blk, 0, st>>>(in, N, out, N, N, stop, ps);
+    k_wav_analysis<<<block_grid(N, B), blk, 0, st>>>(in, N, out, N, N, stop, ps,
+                                                     levels >= 2 ? wav_ll_buffer(scratch, N, 2) : nullptr);
     PAT_LAUNCH_CHECK("k_wav_analysis");
-    for (int l = 1, M = N / 2; l < levels; ++l, M /= 2) {
-        k_copy_block<<<block_grid(M, B), blk, 0, st>>>(out, N, scratch, M, M, stop, ps);
-        PAT_LAUNCH_CHECK("k_copy_block");
-        k_wav_analysis<<<block_grid(M, B), blk, 0, st>>>(scratch, M, out, N, M, stop, ps);
+    for (int l = 2, M = N / 2; l <= levels; ++l, M /= 2) {
+        k_wav_analysis<<<block_grid(M, B), blk, 0, st>>>(wav_ll_buffer(scratch, N, l), M, out, N, M, stop, ps,
+                                                         l < levels ? wav_ll_buffer(scratch, N, l + 1) : nullptr);
         PAT_LAUNCH_CHECK("k_wav_analysis");
     }
     return PAT_OK;
 }
 
-// out = W^T in.  scratch: N*N floats; out may not alias in.
+// out = W^T in (in is not modified).  scratch: N*N floats; out may not alias in.  Level
+// l >= 2 writes its M x M block (M = N >> (l - 1)) into X_l, the next finer level's LL.
 int launch_wav_synthesis(const float* in, int N, int levels, float* out, float* scratch, const int* stop,
                          cudaStream_t st, int B, long long ps) {
     const dim3 blk(32, 8);
-    k_copy_block<<<block_grid(N, B), blk, 0, st>>>(in, N, out, N, N, stop, ps);
-    PAT_LAUNCH_CHECK("k_copy_block");
-    for (int l = levels - 1; l >= 0; --l) {
-        const int M = N >> l;
-        k_wav_synthesis<<<block_grid(M, B), blk, 0, st>>>(out, N, scratch, M, M, stop, ps);
+    const float* ll = in;   // the coarsest level's LL is in the coefficients themselves
+    int sl = N;
+    for (int l = levels; l >= 1; --l) {
+        const int M = N >> (l - 1);
+        float* dst = l == 1 ? out : wav_ll_buffer(scratch, N, l);
+        k_wav_synthesis<<<block_grid(M, B), blk, 0, st>>>(ll, sl, in, N, dst, l == 1 ? N : M, M, stop, ps);
         PAT_LAUNCH_CHECK("k_wav_synthesis");
-        k_copy_block<<<block_grid(M, B), blk, 0, st>>>(scratch, M, out, N, M, stop, ps);
-        PAT_LAUNCH_CHECK("k_copy_block");
+        ll = dst;
+        sl = M;
     }
     return PAT_OK;
 }
