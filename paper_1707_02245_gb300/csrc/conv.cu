@@ -232,9 +232,10 @@ __global__ void __launch_bounds__(THREADS) k_conv_fwd(const FwdArgs a) {
 //   weights.  TMA writes them in the MMA's K-major layout, with the swizzle whose span is
 //   the box's inner size (none for 16 bytes, else 32, 64 or 128 bytes).
 // - warp 1 (one lane) issues tcgen05.mma (kind::f16: bf16 x bf16 -> f32, K = 16) into one
-//   of four TMEM accumulators of BN columns (eight per stage: each wait on a barrier costs
-//   the issuing thread about 300 cycles, so a stage amortises it), commits every stage to the stage's `empty`
-//   barrier and every finished tile to its accumulator's `full` barrier.
+//   of four TMEM accumulators of BN columns, eight per stage (a wait on a barrier costs the
+//   issuing thread about 300 cycles even when the phase is complete; eight MMAs amortise
+//   it), and commits every stage to the stage's `empty` barrier and every finished tile to
+//   its accumulator's `full` barrier.
 // - warps 2..5 are the epilogue: warp w reads TMEM lanes 32 (w mod 4) + 0..31 (its pixels)
 //   with tcgen05.ld, adds the bias, applies ReLU, stores 16-byte vectors and releases the
 //   accumulator, so a tile's epilogue overlaps the next tile's loads and MMAs.
