@@ -93,6 +93,24 @@ def test_conv_forward_matches_oracle(case):
     assert np.all(err <= bound), float(np.max(err / bound))
 
 
+@pytest.mark.parametrize("case", [(2, 256, 256, 64, 64, True), (8, 64, 64, 128, 256, False)])
+def test_conv_forward_many_tiles_per_cta_matches_oracle(case):
+    """Shapes of the benchmark's network, where each persistent CTA of the tensor-memory
+    kernel takes many tiles (1 024 and 256 x 2), so its stage ring and its four TMEM
+    accumulators wrap around many times; every output is checked."""
+    B, H, W, ci, co, relu = case
+    rng = np.random.default_rng(7 + ci)
+    xt, x = bf16(rng.standard_normal((B, H, W, ci)))
+    wt, w = bf16(rng.standard_normal((co, 3, 3, ci)) * 0.1)
+    b = rng.standard_normal(co)
+    y = torch.empty(B, H, W, co, device=DEV)
+    P.pat_conv3x3_forward(xt, B, H, W, ci, wt, dev(b), co, relu, y)
+    ref = U.conv3x3(x, w, b.astype(np.float32).astype(np.float64), relu=relu)
+    bound = U.conv3x3(np.abs(x), np.abs(w), np.abs(b)) * 2e-5 + 1e-6
+    err = np.abs(host(y) - ref)
+    assert np.all(err <= bound), float(np.max(err / bound))
+
+
 @pytest.mark.parametrize("case", CONV_CASES)
 def test_conv_backward_data_matches_oracle(case):
     B, H, W, ci, co, _ = case
