@@ -96,8 +96,8 @@ def test_conv_forward_matches_oracle(case):
 @pytest.mark.parametrize("case", [(2, 256, 256, 64, 64, True), (8, 64, 64, 128, 256, False)])
 def test_conv_forward_many_tiles_per_cta_matches_oracle(case):
     """Shapes of the benchmark's network, where each persistent CTA of the tensor-memory
-    kernel takes many tiles (1 024 and 256 x 2), so its stage ring and its four TMEM
-    accumulators wrap around many times; every output is checked."""
+    kernel takes several tiles (1 024 and 256 x 2 tiles over 152 CTAs), so its stage ring
+    and its four TMEM accumulators wrap around; every output is checked."""
     B, H, W, ci, co, relu = case
     rng = np.random.default_rng(7 + ci)
     xt, x = bf16(rng.standard_normal((B, H, W, ci)))
