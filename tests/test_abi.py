@@ -96,6 +96,15 @@ def test_unet_arguments_rejected_before_any_device_call(lib):
     with pytest.raises(P.PatError) as ei:
         P.pat_conv3x3_backward_weight(16, 16, 1, 4, 4, 8, 12, 16)
     assert ei.value.code == P.PAT_ERR_INVALID_ARG
+    # the tensor-memory kernels read x and w, and write y, in 16-byte vectors and TMA boxes:
+    # pointers off a 16-byte boundary are refused before any device call
+    for x, w, y in [(24, 32, 48), (32, 40, 48), (32, 48, 56)]:
+        with pytest.raises(P.PatError) as ei:
+            P.pat_conv3x3_forward(x, 1, 4, 4, 8, w, None, 8, False, y)
+        assert ei.value.code == P.PAT_ERR_INVALID_ARG
+        with pytest.raises(P.PatError) as ei:
+            P.pat_conv3x3_backward_data(x, 1, 4, 4, 8, w, 8, y)
+        assert ei.value.code == P.PAT_ERR_INVALID_ARG
 
 
 def test_header_shape_constants_match_the_binding():
